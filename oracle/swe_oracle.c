@@ -1,0 +1,757 @@
+/*
+ * swe_oracle.c -- plain FP64 CPU oracle for the adjoint-guided shallow-water
+ * path (Davis & LeVeque, arXiv 1605.05320).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file; only the tests, the package smoke check and the bench's
+ * CPU-baseline leg do.  It shares no source with the CUDA library.
+ *
+ * Compiled with -O2 -ffp-contract=off so every operation rounds as written.
+ * Arrays are row-major with x fastest, index j*nx + i, no ghost cells; every
+ * routine builds its own ghost-padded copies (2 ghost layers).
+ *
+ * What each routine follows:
+ *   fwd_riemann      Sec. 6 (Roe solver for SWE plus bathymetry) applied to
+ *                    Eq. (swe_1d)/(swe): f-wave form, source folded into the
+ *                    momentum jump as g*hhat*(eta_R - eta_L).
+ *   orc_fwd_step     Godunov-type wave-propagation update, unsplit in 2D, with
+ *                    MC-limited second-order corrections (order 2).
+ *   orc_fwd_smax     CFL number sum_dir (|u|+c)/dx over interior cells.
+ *   orc_lin_step     first-order update of Eq. (hyp_linear) (and its 2D form,
+ *                    Sec. 5), used only by the adjoint-identity pins.
+ *   orc_adj_step     one step of the time-reversed adjoint of Sec. 4:
+ *                    q~_t - (A^T q~)_x [- (A_2^T q~)_y] = 0, f-wave form, walls
+ *                    at wet/dry edges (Sec. 5 boundary condition).
+ *   orc_flag         Eq. (ip_timepoint) (BRACKET) and Eq. (ip_timerange) with
+ *                    linear interpolation in time (INTERP), bilinear spatial
+ *                    interpolation of the adjoint (Sec. 4), zero where the
+ *                    adjoint is dry (Sec. 6).
+ *   orc_gauge        bilinear interpolation of cell-centre eta (Sec. 6 gauges).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define BC_EXTRAP 0
+#define BC_WALL 1
+
+#define FLAG_INTERP 0
+#define FLAG_BRACKET 1
+
+typedef struct {
+    int ndim;           /* 1 or 2 */
+    int nx, ny;         /* ny == 1 when ndim == 1 */
+    double x_lo, y_lo, dx, dy;
+    int order;          /* 1 or 2 */
+    int bc[4];          /* x_lo, x_hi, y_lo, y_hi */
+    double g, cfl, dry_tol;
+} orc_grid;
+
+#define NG 2
+
+/* ---------------------------------------------------------------- helpers */
+
+static double *padded(const orc_grid *G) {
+    size_t px = (size_t)G->nx + 2 * NG;
+    size_t py = (G->ndim == 2) ? (size_t)G->ny + 2 * NG : 1;
+    return (double *)calloc(px * py, sizeof(double));
+}
+
+/* index into a padded array: i in [-NG, nx+NG), j in [-NG, ny+NG) (2D) */
+static inline size_t pidx(const orc_grid *G, int i, int j) {
+    size_t px = (size_t)G->nx + 2 * NG;
+    if (G->ndim == 1) return (size_t)(i + NG);
+    return (size_t)(j + NG) * px + (size_t)(i + NG);
+}
+
+/*
+ * Copy an interior field into a padded array and fill its ghost cells.
+ * sign_x / sign_y: factor applied to mirrored ghosts at x walls / y walls
+ * (-1 for the momentum normal to that wall, +1 otherwise).  Extrapolation
+ * copies the nearest interior cell into both ghost layers.
+ */
+static void fill_padded(const orc_grid *G, const double *a, double *p,
+                        double sign_x, double sign_y) {
+    int nx = G->nx, ny = G->ny;
+    for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++)
+            p[pidx(G, i, j)] = a[(size_t)j * nx + i];
+    for (int j = 0; j < ny; j++) {
+        for (int k = 1; k <= NG; k++) {
+            /* low x */
+            if (G->bc[0] == BC_WALL)
+                p[pidx(G, -k, j)] = sign_x * a[(size_t)j * nx + (k - 1)];
+            else
+                p[pidx(G, -k, j)] = a[(size_t)j * nx + 0];
+            /* high x */
+            if (G->bc[1] == BC_WALL)
+                p[pidx(G, nx - 1 + k, j)] = sign_x * a[(size_t)j * nx + (nx - k)];
+            else
+                p[pidx(G, nx - 1 + k, j)] = a[(size_t)j * nx + (nx - 1)];
+        }
+    }
+    if (G->ndim == 2) {
+        for (int i = 0; i < nx; i++) {
+            for (int k = 1; k <= NG; k++) {
+                if (G->bc[2] == BC_WALL)
+                    p[pidx(G, i, -k)] = sign_y * a[(size_t)(k - 1) * nx + i];
+                else
+                    p[pidx(G, i, -k)] = a[i];
+                if (G->bc[3] == BC_WALL)
+                    p[pidx(G, i, ny - 1 + k)] = sign_y * a[(size_t)(ny - k) * nx + i];
+                else
+                    p[pidx(G, i, ny - 1 + k)] = a[(size_t)(ny - 1) * nx + i];
+            }
+        }
+    }
+}
+
+/* MC limiter phi(theta) = max(0, min((1+theta)/2, 2, 2 theta)) */
+static double mc_limiter(double theta) {
+    double a = 0.5 * (1.0 + theta);
+    double b = 2.0;
+    double c = 2.0 * theta;
+    double m = a;
+    if (b < m) m = b;
+    if (c < m) m = c;
+    if (m < 0.0) m = 0.0;
+    return m;
+}
+
+static double sgn(double s) { return (s > 0.0) ? 1.0 : ((s < 0.0) ? -1.0 : 0.0); }
+
+static double dot3(const double *a, const double *b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/*
+ * Generic 1D wave data at one edge: MW waves of 3 components each, speeds.
+ */
+typedef struct {
+    double s[3];
+    double Z[3][3];
+} edge_waves;
+
+/*
+ * Fluctuations and second-order correction for edge e given waves at e and at
+ * its neighbours em (edge to the left) and ep (edge to the right).
+ * apdq: goes to the right cell, amdq: to the left cell, F: correction flux.
+ * nu = dt/dx.  Order 1 leaves F = 0.
+ */
+static void edge_fluxes(int mw, const edge_waves *em, const edge_waves *e,
+                        const edge_waves *ep, double nu, int order,
+                        double amdq[3], double apdq[3], double F[3]) {
+    for (int m = 0; m < 3; m++) { amdq[m] = 0.0; apdq[m] = 0.0; F[m] = 0.0; }
+    for (int p = 0; p < mw; p++) {
+        double s = e->s[p];
+        for (int m = 0; m < 3; m++) {
+            if (s < 0.0) amdq[m] += e->Z[p][m];
+            else if (s > 0.0) apdq[m] += e->Z[p][m];
+            else { amdq[m] += 0.5 * e->Z[p][m]; apdq[m] += 0.5 * e->Z[p][m]; }
+        }
+    }
+    if (order < 2) return;
+    for (int p = 0; p < mw; p++) {
+        double s = e->s[p];
+        const edge_waves *up = (s > 0.0) ? em : ep;
+        double zz = dot3(e->Z[p], e->Z[p]);
+        double theta = 0.0;
+        if (zz != 0.0) theta = dot3(up->Z[p], e->Z[p]) / zz;
+        double phi = mc_limiter(theta);
+        double coef = 0.5 * sgn(s) * (1.0 - nu * fabs(s)) * phi;
+        for (int m = 0; m < 3; m++) F[m] += coef * e->Z[p][m];
+    }
+}
+
+/* ------------------------------------------------------- forward Riemann */
+
+/*
+ * f-wave Roe solver for the nonlinear SWE with bathymetry.  State components
+ * (h, normal momentum, tangential momentum); B is bottom elevation.
+ * Roe averages: hhat = (hL+hR)/2, uhat/vhat sqrt(h)-weighted, chat =
+ * sqrt(g hhat).  The flux jump includes the bathymetry source as
+ * g*hhat*(eta_R - eta_L) in the normal momentum so that the ocean at rest has
+ * zero jump (well balanced).  Eigenvectors (1, uhat-chat, vhat), (0,0,1),
+ * (1, uhat+chat, vhat).
+ */
+static void fwd_riemann(double g,
+                        double hL, double mnL, double mtL, double BL,
+                        double hR, double mnR, double mtR, double BR,
+                        edge_waves *w) {
+    double uL = mnL / hL, vL = mtL / hL;
+    double uR = mnR / hR, vR = mtR / hR;
+    double hhat = 0.5 * (hL + hR);
+    double sqL = sqrt(hL), sqR = sqrt(hR);
+    double uhat = (sqL * uL + sqR * uR) / (sqL + sqR);
+    double vhat = (sqL * vL + sqR * vR) / (sqL + sqR);
+    double chat = sqrt(g * hhat);
+    double s1 = uhat - chat, s2 = uhat, s3 = uhat + chat;
+    double etaL = hL + BL, etaR = hR + BR;
+    double df1 = mnR - mnL;
+    double df2 = (mnR * uR - mnL * uL) + g * hhat * (etaR - etaL);
+    double df3 = mnR * vR - mnL * vL;
+    double b1 = (s3 * df1 - df2) / (s3 - s1);
+    double b3 = (df2 - s1 * df1) / (s3 - s1);
+    double b2 = df3 - vhat * df1;
+    w->s[0] = s1; w->s[1] = s2; w->s[2] = s3;
+    w->Z[0][0] = b1;  w->Z[0][1] = b1 * s1;  w->Z[0][2] = b1 * vhat;
+    w->Z[1][0] = 0.0; w->Z[1][1] = 0.0;      w->Z[1][2] = b2;
+    w->Z[2][0] = b3;  w->Z[2][1] = b3 * s3;  w->Z[2][2] = b3 * vhat;
+}
+
+/* --------------------------------------------------------- forward step */
+
+/*
+ * One forward step of size dt, in place on (h, hu, hv).  hv may be NULL for
+ * ndim == 1 (treated as zero and not written).  Returns 0, or -5 when a
+ * non-positive or non-finite depth appears.
+ */
+int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
+                 const double *B, double dt) {
+    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+    size_t n = (size_t)nx * ny;
+    double *ph = padded(G), *pu = padded(G), *pv = padded(G), *pB = padded(G);
+    double *zero = NULL;
+    if (!hv) { zero = (double *)calloc(n, sizeof(double)); }
+    const double *hv_in = hv ? hv : zero;
+    fill_padded(G, h, ph, 1.0, 1.0);
+    fill_padded(G, hu, pu, -1.0, 1.0);
+    fill_padded(G, hv_in, pv, 1.0, -1.0);
+    fill_padded(G, B, pB, 1.0, 1.0);
+    double *nh = (double *)malloc(n * sizeof(double));
+    double *nu_ = (double *)malloc(n * sizeof(double));
+    double *nv = (double *)malloc(n * sizeof(double));
+    double nux = dt / G->dx, nuy = dt / G->dy;
+    int bad = 0;
+
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int j = 0; j < ny; j++) {
+        for (int i = 0; i < nx; i++) {
+            double q[3];
+            size_t c = pidx(G, i, j);
+            q[0] = ph[c]; q[1] = pu[c]; q[2] = pv[c];
+            /* x-edges i-3/2, i-1/2, i+1/2, i+3/2: edge k+1/2 between k, k+1 */
+            edge_waves wx[4];
+            for (int e = 0; e < 4; e++) {
+                int l = i - 2 + e, r = l + 1;
+                size_t a = pidx(G, l, j), b = pidx(G, r, j);
+                fwd_riemann(G->g, ph[a], pu[a], pv[a], pB[a],
+                            ph[b], pu[b], pv[b], pB[b], &wx[e]);
+            }
+            double amL[3], apL[3], FL[3], amR[3], apR[3], FR[3];
+            /* left edge i-1/2 = wx[1] (neighbours wx[0], wx[2]) */
+            edge_fluxes(3, &wx[0], &wx[1], &wx[2], nux, G->order, amL, apL, FL);
+            /* right edge i+1/2 = wx[2] (neighbours wx[1], wx[3]) */
+            edge_fluxes(3, &wx[1], &wx[2], &wx[3], nux, G->order, amR, apR, FR);
+            double dq[3];
+            for (int m = 0; m < 3; m++)
+                dq[m] = -nux * (apL[m] + amR[m]) - nux * (FR[m] - FL[m]);
+            if (two_d) {
+                /* y-edges with (h, hv, hu): normal momentum is hv */
+                edge_waves wy[4];
+                for (int e = 0; e < 4; e++) {
+                    int l = j - 2 + e, r = l + 1;
+                    size_t a = pidx(G, i, l), b = pidx(G, i, r);
+                    fwd_riemann(G->g, ph[a], pv[a], pu[a], pB[a],
+                                ph[b], pv[b], pu[b], pB[b], &wy[e]);
+                }
+                double bmL[3], bpL[3], GL[3], bmR[3], bpR[3], GR[3];
+                edge_fluxes(3, &wy[0], &wy[1], &wy[2], nuy, G->order, bmL, bpL, GL);
+                edge_fluxes(3, &wy[1], &wy[2], &wy[3], nuy, G->order, bmR, bpR, GR);
+                /* components of the y-waves are (h, hv, hu) */
+                double dy[3];
+                for (int m = 0; m < 3; m++)
+                    dy[m] = -nuy * (bpL[m] + bmR[m]) - nuy * (GR[m] - GL[m]);
+                dq[0] += dy[0];
+                dq[1] += dy[2];
+                dq[2] += dy[1];
+            }
+            size_t o = (size_t)j * nx + i;
+            nh[o] = q[0] + dq[0];
+            nu_[o] = q[1] + dq[1];
+            nv[o] = q[2] + dq[2];
+            if (!(nh[o] > 0.0) || !isfinite(nu_[o]) || !isfinite(nv[o])) bad = 1;
+        }
+    }
+    memcpy(h, nh, n * sizeof(double));
+    memcpy(hu, nu_, n * sizeof(double));
+    if (hv) memcpy(hv, nv, n * sizeof(double));
+    free(ph); free(pu); free(pv); free(pB); free(nh); free(nu_); free(nv);
+    free(zero);
+    return bad ? -5 : 0;
+}
+
+/* CFL number: max over interior cells of (|u|+c)/dx [+ (|v|+c)/dy]. */
+double orc_fwd_smax(const orc_grid *G, const double *h, const double *hu,
+                    const double *hv) {
+    double smax = 0.0;
+    size_t n = (size_t)G->nx * G->ny;
+    for (size_t k = 0; k < n; k++) {
+        double c = sqrt(G->g * h[k]);
+        double s = (fabs(hu[k] / h[k]) + c) / G->dx;
+        if (G->ndim == 2) s += (fabs(hv[k] / h[k]) + c) / G->dy;
+        if (s > smax) smax = s;
+    }
+    return smax;
+}
+
+/*
+ * Run up to max_steps CFL-limited steps, stopping at t_end:
+ * dt_n = min(cfl / smax(Q^n), t_end - t_n).  Updates *t; returns the number
+ * of steps taken, or a negative status.
+ */
+long orc_fwd_run(const orc_grid *G, double *h, double *hu, double *hv,
+                 const double *B, long max_steps, double t_end, double *t) {
+    long k;
+    for (k = 0; k < max_steps; k++) {
+        if (!(*t < t_end)) break;
+        double smax = orc_fwd_smax(G, h, hu, hv);
+        double dt = G->cfl / smax;
+        if (dt > t_end - *t) dt = t_end - *t;
+        int rc = orc_fwd_step(G, h, hu, hv, B, dt);
+        if (rc) return rc;
+        *t = *t + dt;
+    }
+    return k;
+}
+
+/* ------------------------------------------------- linear forward (tests) */
+
+/*
+ * First-order wave-propagation step for q_t + A(x) q_x (+ A_2 q_y) = 0,
+ * A = [[0,1],[g hbar,0]] (Eq. SWE_Aq), q = (eta, mu[, gamma]).  At an x-edge
+ * the jump (d_eta, d_mu) splits as a1 [1, -cL] + a2 [1, cR]; the left-going
+ * part moves at -cL, the right-going at +cR.  Walls mirror with the normal
+ * momentum negated.  Order 1 only; used by the adjoint-identity pins.
+ */
+int orc_lin_step(const orc_grid *G, double *eta, double *mu, double *gam,
+                 const double *hbar, double dt) {
+    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+    size_t n = (size_t)nx * ny;
+    double *pe = padded(G), *pm = padded(G), *pg = padded(G), *pc = padded(G);
+    double *zero = NULL;
+    if (!gam) zero = (double *)calloc(n, sizeof(double));
+    double *c = (double *)malloc(n * sizeof(double));
+    for (size_t k = 0; k < n; k++) c[k] = sqrt(G->g * hbar[k]);
+    fill_padded(G, eta, pe, 1.0, 1.0);
+    fill_padded(G, mu, pm, -1.0, 1.0);
+    fill_padded(G, gam ? gam : zero, pg, 1.0, -1.0);
+    fill_padded(G, c, pc, 1.0, 1.0);
+    double *ne = (double *)malloc(n * sizeof(double));
+    double *nm = (double *)malloc(n * sizeof(double));
+    double *ng = (double *)malloc(n * sizeof(double));
+    double nux = dt / G->dx, nuy = dt / G->dy;
+    for (int j = 0; j < ny; j++) {
+        for (int i = 0; i < nx; i++) {
+            size_t ci = pidx(G, i, j);
+            double de = 0.0, dm = 0.0, dg = 0.0;
+            /* edge i-1/2: right-going part enters cell i */
+            {
+                size_t a = pidx(G, i - 1, j);
+                double cL = pc[a], cR = pc[ci];
+                double dE = pe[ci] - pe[a], dM = pm[ci] - pm[a];
+                double a2 = (dM + cL * dE) / (cL + cR);
+                de -= nux * (cR * a2);
+                dm -= nux * (cR * a2 * cR);
+            }
+            /* edge i+1/2: left-going part enters cell i */
+            {
+                size_t b = pidx(G, i + 1, j);
+                double cL = pc[ci], cR = pc[b];
+                double dE = pe[b] - pe[ci], dM = pm[b] - pm[ci];
+                double a1 = (cR * dE - dM) / (cL + cR);
+                de -= nux * (-cL * a1);
+                dm -= nux * (-cL * a1 * (-cL));
+            }
+            if (two_d) {
+                {
+                    size_t a = pidx(G, i, j - 1);
+                    double cL = pc[a], cR = pc[ci];
+                    double dE = pe[ci] - pe[a], dG = pg[ci] - pg[a];
+                    double a2 = (dG + cL * dE) / (cL + cR);
+                    de -= nuy * (cR * a2);
+                    dg -= nuy * (cR * a2 * cR);
+                }
+                {
+                    size_t b = pidx(G, i, j + 1);
+                    double cL = pc[ci], cR = pc[b];
+                    double dE = pe[b] - pe[ci], dG = pg[b] - pg[ci];
+                    double a1 = (cR * dE - dG) / (cL + cR);
+                    de -= nuy * (-cL * a1);
+                    dg -= nuy * (-cL * a1 * (-cL));
+                }
+            }
+            size_t o = (size_t)j * nx + i;
+            ne[o] = pe[ci] + de;
+            nm[o] = pm[ci] + dm;
+            ng[o] = pg[ci] + dg;
+        }
+    }
+    memcpy(eta, ne, n * sizeof(double));
+    memcpy(mu, nm, n * sizeof(double));
+    if (gam) memcpy(gam, ng, n * sizeof(double));
+    free(pe); free(pm); free(pg); free(pc); free(c); free(ne); free(nm);
+    free(ng); free(zero);
+    return 0;
+}
+
+/* ----------------------------------------------------------- adjoint step */
+
+/*
+ * Adjoint Riemann solve at an edge of the time-reversed adjoint
+ * q~_t + F(q~, x)_x = 0, F = -A^T q~ = -(g hbar mu~, eta~) along the normal
+ * direction (the tangential component has no flux).  The flux Jacobian has
+ * eigenpairs (-c, [c, 1]) and (+c, [-c, 1]); with the left cell's left-going
+ * and the right cell's right-going eigenvector the flux jump splits as
+ *   dF = b1 [cL, 1] + b2 [-cR, 1].
+ * Components here are (eta~, normal, tangential).
+ */
+static void adj_riemann(double g, double eL, double mL, double hbL,
+                        double eR, double mR, double hbR, edge_waves *w) {
+    double cL = sqrt(g * hbL), cR = sqrt(g * hbR);
+    double FL1 = -(g * hbL * mL), FL2 = -eL;
+    double FR1 = -(g * hbR * mR), FR2 = -eR;
+    double dF1 = FR1 - FL1, dF2 = FR2 - FL2;
+    double b1 = (dF1 + cR * dF2) / (cL + cR);
+    double b2 = (cL * dF2 - dF1) / (cL + cR);
+    w->s[0] = -cL; w->s[1] = cR; w->s[2] = 0.0;
+    w->Z[0][0] = b1 * cL;  w->Z[0][1] = b1;  w->Z[0][2] = 0.0;
+    w->Z[1][0] = -b2 * cR; w->Z[1][1] = b2;  w->Z[1][2] = 0.0;
+    w->Z[2][0] = 0.0;      w->Z[2][1] = 0.0; w->Z[2][2] = 0.0;
+}
+
+/*
+ * Adjoint waves at the edge between padded cells a (left) and b (right),
+ * normal momentum array pm, with walls at wet/dry edges: a dry cell
+ * (hbar <= dry_tol) is replaced by the mirror image of its wet neighbour
+ * (same eta~ and hbar, normal momentum negated).  Both dry: no waves.
+ * Returns 1 for a wet/dry edge (a wall), 0 otherwise.  A wall edge carries
+ * no second-order correction, so nothing crosses it.
+ */
+static int adj_edge(const orc_grid *G, const double *pe, const double *pm,
+                    const double *phb, size_t a, size_t b, edge_waves *w) {
+    int dryL = !(phb[a] > G->dry_tol), dryR = !(phb[b] > G->dry_tol);
+    if (dryL && dryR) { memset(w, 0, sizeof(*w)); return 1; }
+    if (dryL) {
+        adj_riemann(G->g, pe[b], -pm[b], phb[b], pe[b], pm[b], phb[b], w);
+        return 1;
+    }
+    if (dryR) {
+        adj_riemann(G->g, pe[a], pm[a], phb[a], pe[a], -pm[a], phb[a], w);
+        return 1;
+    }
+    adj_riemann(G->g, pe[a], pm[a], phb[a], pe[b], pm[b], phb[b], w);
+    return 0;
+}
+
+/*
+ * One step of the time-reversed adjoint (Sec. 4) of size dt, in place on
+ * (eta~, mu~, gamma~); hbar = max(-B, 0) of the adjoint grid.  Dry cells are
+ * left unchanged.  gam may be NULL for ndim == 1.
+ */
+int orc_adj_step(const orc_grid *G, double *eta, double *mu, double *gam,
+                 const double *hbar, double dt) {
+    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+    size_t n = (size_t)nx * ny;
+    double *pe = padded(G), *pm = padded(G), *pg = padded(G), *phb = padded(G);
+    double *zero = NULL;
+    if (!gam) zero = (double *)calloc(n, sizeof(double));
+    fill_padded(G, eta, pe, 1.0, 1.0);
+    fill_padded(G, mu, pm, -1.0, 1.0);
+    fill_padded(G, gam ? gam : zero, pg, 1.0, -1.0);
+    fill_padded(G, hbar, phb, 1.0, 1.0);
+    double *ne = (double *)malloc(n * sizeof(double));
+    double *nm = (double *)malloc(n * sizeof(double));
+    double *ng = (double *)malloc(n * sizeof(double));
+    double nux = dt / G->dx, nuy = dt / G->dy;
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++) {
+        for (int i = 0; i < nx; i++) {
+            size_t ci = pidx(G, i, j);
+            size_t o = (size_t)j * nx + i;
+            if (!(phb[ci] > G->dry_tol)) {
+                ne[o] = pe[ci]; nm[o] = pm[ci]; ng[o] = pg[ci];
+                continue;
+            }
+            edge_waves wx[4];
+            int wallx[4];
+            for (int e = 0; e < 4; e++) {
+                int l = i - 2 + e;
+                wallx[e] = adj_edge(G, pe, pm, phb, pidx(G, l, j), pidx(G, l + 1, j), &wx[e]);
+            }
+            double amL[3], apL[3], FL[3], amR[3], apR[3], FR[3];
+            edge_fluxes(2, &wx[0], &wx[1], &wx[2], nux, wallx[1] ? 1 : G->order, amL, apL, FL);
+            edge_fluxes(2, &wx[1], &wx[2], &wx[3], nux, wallx[2] ? 1 : G->order, amR, apR, FR);
+            double de = -nux * (apL[0] + amR[0]) - nux * (FR[0] - FL[0]);
+            double dm = -nux * (apL[1] + amR[1]) - nux * (FR[1] - FL[1]);
+            double dg = 0.0;
+            if (two_d) {
+                edge_waves wy[4];
+                int wally[4];
+                for (int e = 0; e < 4; e++) {
+                    int l = j - 2 + e;
+                    wally[e] = adj_edge(G, pe, pg, phb, pidx(G, i, l), pidx(G, i, l + 1), &wy[e]);
+                }
+                double bmL[3], bpL[3], GL[3], bmR[3], bpR[3], GR[3];
+                edge_fluxes(2, &wy[0], &wy[1], &wy[2], nuy, wally[1] ? 1 : G->order, bmL, bpL, GL);
+                edge_fluxes(2, &wy[1], &wy[2], &wy[3], nuy, wally[2] ? 1 : G->order, bmR, bpR, GR);
+                de += -nuy * (bpL[0] + bmR[0]) - nuy * (GR[0] - GL[0]);
+                dg = -nuy * (bpL[1] + bmR[1]) - nuy * (GR[1] - GL[1]);
+            }
+            ne[o] = pe[ci] + de;
+            nm[o] = pm[ci] + dm;
+            ng[o] = pg[ci] + dg;
+        }
+    }
+    memcpy(eta, ne, n * sizeof(double));
+    memcpy(mu, nm, n * sizeof(double));
+    if (gam) memcpy(gam, ng, n * sizeof(double));
+    free(pe); free(pm); free(pg); free(phb); free(ne); free(nm); free(ng);
+    free(zero);
+    return 0;
+}
+
+/* Adjoint CFL number: max over wet cells of c/dx [+ c/dy], c = sqrt(g hbar). */
+double orc_adj_smax(const orc_grid *G, const double *hbar) {
+    double smax = 0.0;
+    size_t n = (size_t)G->nx * G->ny;
+    for (size_t k = 0; k < n; k++) {
+        if (!(hbar[k] > G->dry_tol)) continue;
+        double c = sqrt(G->g * hbar[k]);
+        double s = c / G->dx;
+        if (G->ndim == 2) s += c / G->dy;
+        if (s > smax) smax = s;
+    }
+    return smax;
+}
+
+/*
+ * Solve the time-reversed adjoint from q~(0) = phi over [0, t_f] with a fixed
+ * step dt = t_f / N, N = ceil(t_f * smax / cfl), saving a snapshot every
+ * `every` steps and always the last one.  Snapshot k holds q^(tau_k) with
+ * tau_k = t_f - (steps done) * dt (Sec. 4: q^(x, t_f - t) = q~(x, t)).
+ * snaps: [max_snaps][ncomp][n] with ncomp = ndim + 1; tau: [max_snaps].
+ * Returns the number of snapshots, or a negative status (-2 if max_snaps is
+ * too small).  *n_steps receives N and *dt_out the step.
+ */
+long orc_adj_run(const orc_grid *G, const double *hbar, const double *phi,
+                 double t_f, int every, long max_snaps, double *snaps,
+                 double *tau, long *n_steps, double *dt_out) {
+    size_t n = (size_t)G->nx * G->ny;
+    int nc = G->ndim + 1;
+    double smax = orc_adj_smax(G, hbar);
+    long N = (long)ceil(t_f * smax / G->cfl);
+    if (N < 1) N = 1;
+    double dt = t_f / (double)N;
+    double *e = (double *)malloc(n * sizeof(double));
+    double *m = (double *)malloc(n * sizeof(double));
+    double *gm = (double *)calloc(n, sizeof(double));
+    memcpy(e, phi, n * sizeof(double));
+    memcpy(m, phi + n, n * sizeof(double));
+    if (nc == 3) memcpy(gm, phi + 2 * n, n * sizeof(double));
+    long k = 0;
+    /* snapshot 0: tau = t_f */
+    if (k >= max_snaps) { free(e); free(m); free(gm); return -2; }
+    memcpy(snaps + (size_t)k * nc * n, e, n * sizeof(double));
+    memcpy(snaps + (size_t)k * nc * n + n, m, n * sizeof(double));
+    if (nc == 3) memcpy(snaps + (size_t)k * nc * n + 2 * n, gm, n * sizeof(double));
+    tau[k++] = t_f;
+    for (long s = 1; s <= N; s++) {
+        orc_adj_step(G, e, m, nc == 3 ? gm : NULL, hbar, dt);
+        if (s % every == 0 || s == N) {
+            if (k >= max_snaps) { free(e); free(m); free(gm); return -2; }
+            memcpy(snaps + (size_t)k * nc * n, e, n * sizeof(double));
+            memcpy(snaps + (size_t)k * nc * n + n, m, n * sizeof(double));
+            if (nc == 3) memcpy(snaps + (size_t)k * nc * n + 2 * n, gm, n * sizeof(double));
+            tau[k++] = t_f - (double)s * dt;
+        }
+    }
+    free(e); free(m); free(gm);
+    if (n_steps) *n_steps = N;
+    if (dt_out) *dt_out = dt;
+    return k;
+}
+
+/* ------------------------------------------------------------------ flag */
+
+/*
+ * Bilinear interpolation stencil of point (x, y) on the cell centres of grid
+ * A, the coordinate clamped to the outermost centres.  Returns the four cell
+ * indices and weights (1D: two, the others weight 0).
+ */
+static void bilinear(const orc_grid *A, double x, double y, size_t idx[4],
+                     double w[4]) {
+    double fx = (x - A->x_lo) / A->dx - 0.5;
+    if (fx < 0.0) fx = 0.0;
+    if (fx > (double)(A->nx - 1)) fx = (double)(A->nx - 1);
+    int i0 = (int)floor(fx);
+    if (i0 > A->nx - 2) i0 = A->nx - 2;
+    if (i0 < 0) i0 = 0;
+    double ax = fx - (double)i0;
+    int i1 = (A->nx > 1) ? i0 + 1 : i0;
+    if (A->nx == 1) ax = 0.0;
+    if (A->ndim == 1) {
+        idx[0] = (size_t)i0; idx[1] = (size_t)i1; idx[2] = 0; idx[3] = 0;
+        w[0] = 1.0 - ax; w[1] = ax; w[2] = 0.0; w[3] = 0.0;
+        return;
+    }
+    double fy = (y - A->y_lo) / A->dy - 0.5;
+    if (fy < 0.0) fy = 0.0;
+    if (fy > (double)(A->ny - 1)) fy = (double)(A->ny - 1);
+    int j0 = (int)floor(fy);
+    if (j0 > A->ny - 2) j0 = A->ny - 2;
+    if (j0 < 0) j0 = 0;
+    double ay = fy - (double)j0;
+    int j1 = (A->ny > 1) ? j0 + 1 : j0;
+    if (A->ny == 1) ay = 0.0;
+    idx[0] = (size_t)j0 * A->nx + i0; w[0] = (1.0 - ax) * (1.0 - ay);
+    idx[1] = (size_t)j0 * A->nx + i1; w[1] = ax * (1.0 - ay);
+    idx[2] = (size_t)j1 * A->nx + i0; w[2] = (1.0 - ax) * ay;
+    idx[3] = (size_t)j1 * A->nx + i1; w[3] = ax * ay;
+}
+
+/*
+ * Adjoint-weighted flagging of the forward state (h, hu, hv, B) at time t.
+ * snaps [K][ncomp][n_adj] with tau strictly decreasing (tau[0] = latest).
+ * Window (Eq. ip_timerange, read with tau running from t up to
+ * T = min(t + t_f - t_s, t_f)), clipped to [tau[K-1], tau[0]]:
+ *   INTERP : q^(tau) linear in tau between snapshots; the maximum of
+ *            |q^(tau).q| over the window of this piecewise-linear function is
+ *            taken at the window ends or at snapshot times inside it.
+ *   BRACKET: max over the snapshots from the latest one at or before t to the
+ *            earliest one at or after T (Eq. ip_timepoint when t_s = t_f).
+ * q = (eta = h + B, hu, hv); m = 0 where the forward cell is dry or any
+ * weighted adjoint stencil cell is dry.  flags[i] = (m >= tol).  m_out may be
+ * NULL.  Returns the number of flagged cells.
+ */
+long orc_flag(const orc_grid *F, const double *h, const double *hu,
+              const double *hv, const double *B, double t,
+              const orc_grid *A, const double *hbar_adj, const double *snaps,
+              const double *tau, long K, double t_s, double t_f, double tol,
+              int mode, uint8_t *flags, double *m_out) {
+    size_t n = (size_t)F->nx * F->ny;
+    size_t na = (size_t)A->nx * A->ny;
+    int nc = A->ndim + 1;
+    long count = 0;
+    /* t + (t_f - t_s): the window length is added to t, so that T >= t holds
+       exactly whenever t_s <= t_f (t_s = t_f gives the single time t) */
+    double T = t + (t_f - t_s);
+    if (T > t_f) T = t_f;
+    double lo = t, hi = T;
+    if (lo < tau[K - 1]) lo = tau[K - 1];
+    if (hi > tau[0]) hi = tau[0];
+    int empty = (K < 1) || (lo > hi) || (t > t_f);
+    for (int j = 0; j < F->ny; j++) {
+        for (int i = 0; i < F->nx; i++) {
+            size_t o = (size_t)j * F->nx + i;
+            double m = 0.0;
+            double q[3];
+            q[0] = h[o] + B[o];
+            q[1] = hu[o];
+            q[2] = (F->ndim == 2 && hv) ? hv[o] : 0.0;
+            int dry = !(h[o] > F->dry_tol);
+            double x = F->x_lo + ((double)i + 0.5) * F->dx;
+            double y = F->y_lo + ((double)j + 0.5) * F->dy;
+            size_t st[4];
+            double w[4];
+            bilinear(A, x, y, st, w);
+            for (int c = 0; c < 4; c++)
+                if (w[c] > 0.0 && !(hbar_adj[st[c]] > A->dry_tol)) dry = 1;
+            if (!empty && !dry) {
+                /* qhat_k . q at every snapshot, interpolated in space first */
+                double *d = (double *)malloc((size_t)K * sizeof(double));
+                for (long k = 0; k < K; k++) {
+                    double qh[3] = {0.0, 0.0, 0.0};
+                    for (int comp = 0; comp < nc; comp++) {
+                        const double *s = snaps + ((size_t)k * nc + comp) * na;
+                        double v = 0.0;
+                        for (int c = 0; c < 4; c++) v += w[c] * s[st[c]];
+                        qh[comp] = v;
+                    }
+                    if (A->ndim == 1) d[k] = qh[0] * q[0] + qh[1] * q[1];
+                    else d[k] = qh[0] * q[0] + qh[1] * q[1] + qh[2] * q[2];
+                }
+                if (mode == FLAG_BRACKET) {
+                    /* latest snapshot with tau <= lo, earliest with tau >= hi */
+                    long kb = K - 1, ke = 0;
+                    for (long k = 0; k < K; k++) if (tau[k] <= lo) { kb = k; break; }
+                    for (long k = K - 1; k >= 0; k--) if (tau[k] >= hi) { ke = k; break; }
+                    for (long k = ke; k <= kb; k++)
+                        if (fabs(d[k]) > m) m = fabs(d[k]);
+                } else {
+                    /* value of the time interpolant at lo and at hi */
+                    double ends[2] = {lo, hi};
+                    for (int e = 0; e < 2; e++) {
+                        double s = ends[e];
+                        long k = 0;
+                        while (k + 1 < K && tau[k + 1] > s) k++;
+                        /* tau[k] >= s >= tau[k+1] (or k == K-1) */
+                        double v;
+                        if (k + 1 >= K || tau[k] == s) v = d[k];
+                        else {
+                            double a = (s - tau[k + 1]) / (tau[k] - tau[k + 1]);
+                            /* interpolate the components, then dot */
+                            double qh[3];
+                            for (int comp = 0; comp < 3; comp++) qh[comp] = 0.0;
+                            for (int comp = 0; comp < nc; comp++) {
+                                const double *s0 = snaps + ((size_t)k * nc + comp) * na;
+                                const double *s1 = snaps + ((size_t)(k + 1) * nc + comp) * na;
+                                double v0 = 0.0, v1 = 0.0;
+                                for (int c = 0; c < 4; c++) {
+                                    v0 += w[c] * s0[st[c]];
+                                    v1 += w[c] * s1[st[c]];
+                                }
+                                qh[comp] = a * v0 + (1.0 - a) * v1;
+                            }
+                            v = qh[0] * q[0] + qh[1] * q[1] + qh[2] * q[2];
+                        }
+                        if (fabs(v) > m) m = fabs(v);
+                    }
+                    for (long k = 0; k < K; k++)
+                        if (tau[k] > lo && tau[k] < hi && fabs(d[k]) > m) m = fabs(d[k]);
+                }
+                free(d);
+            }
+            if (m_out) m_out[o] = m;
+            uint8_t f = (!empty && !dry && m >= tol) ? 1 : 0;
+            flags[o] = f;
+            count += f;
+        }
+    }
+    return count;
+}
+
+/* Gauges: eta = h + B at (x, y) by bilinear interpolation of cell centres. */
+void orc_gauge(const orc_grid *G, const double *h, const double *B, long ng,
+               const double *xy, double *out) {
+    for (long k = 0; k < ng; k++) {
+        size_t st[4];
+        double w[4];
+        bilinear(G, xy[2 * k], xy[2 * k + 1], st, w);
+        double v = 0.0;
+        for (int c = 0; c < 4; c++) v += w[c] * (h[st[c]] + B[st[c]]);
+        out[k] = v;
+    }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
