@@ -1,0 +1,479 @@
+#!/usr/bin/env python3
+"""Benchmark of the adjoint-guided shallow-water hot path on one GB300.
+
+One step = one whole tsunami scenario of the 2048 x 2048 basin workload
+(1 km cells, seeded synthetic bathymetry with a tanh shelf and 20 seamounts,
+1 m Gaussian source, 10 km Gaussian target on the shelf):
+  * the adjoint solved backward over [0, t_f] with a snapshot every 20 steps
+    (snapshot copy fused into the step kernel),
+  * the forward run to t_f (about 2000 CFL steps, time step reduced on the
+    device inside the step kernel),
+  * a gauge sample after every forward step,
+  * an adjoint-weighted flag pass every 10 forward steps over the time window
+    [t, min(t + t_f - t_s, t_f)], t_s = 0.32 t_f.
+The metric is cell-updates per second of the SWE steps (forward + adjoint)
+over the whole scenario time, flag passes and gauges included.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead (host cores, OpenMP).  Multi-GPU (torchrun): every rank runs
+its own scenario (independent problems, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FWD_BLOCK = 10      # forward steps between flag passes
+SNAP_EVERY = 20     # adjoint steps between snapshots
+N_GAUGES = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"swadj_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------------ our arm
+class Scenario:
+    def __init__(self, S, torch, sc, precision, device):
+        self.S, self.torch, self.sc = S, torch, sc
+        p = S.SWA_FP32 if precision == "fp32" else S.SWA_FP64
+        self.p = p
+        self.desc = S.make_desc(2, sc.grid.nx, sc.grid.ny, 0.0, 0.0, sc.grid.dx,
+                                sc.grid.dy, precision=p)
+        self.adesc = S.make_desc(2, sc.adj_grid.nx, sc.adj_grid.ny, 0.0, 0.0,
+                                 sc.adj_grid.dx, sc.adj_grid.dy, precision=p)
+        self.grid = S.Grid(self.desc, sc.B)
+        self.adj = S.Adjoint(self.adesc, sc.B_adj, sc.phi, sc.t_f)
+        self.N_adj, self.dt_adj, _ = self.adj.info()
+        self.K_max = self.N_adj // SNAP_EVERY + 3
+        self.store = S.SnapStore(self.adj, self.K_max, p)
+        n = sc.grid.n
+        f64 = dict(dtype=torch.float64, device=device)
+        self.eta_d = torch.tensor(sc.eta0, **f64)
+        self.hu_d = torch.tensor(sc.hu0, **f64)
+        self.hv_d = torch.tensor(sc.hv0, **f64)
+        self.phi_d = torch.tensor(sc.phi.reshape(-1), **f64)
+        pin = dict(dtype=torch.float64, pin_memory=True)
+        self.eta_h = torch.tensor(sc.eta0, **pin)
+        self.hu_h = torch.tensor(sc.hu0, **pin)
+        self.hv_h = torch.tensor(sc.hv0, **pin)
+        self.phi_h = torch.tensor(sc.phi.reshape(-1), **pin)
+        self.xy = torch.tensor(sc.gauges, **f64)
+        self.flags = torch.zeros(n, dtype=torch.uint8, device=device)
+        self.n = n
+        self.n_fwd = None
+
+    def measure_steps(self):
+        """Untimed: run the forward to t_f once to learn the step count and
+        the device time at each flag pass (for the snapshot window sizes)."""
+        S = self.S
+        self.grid.set_state(self.eta_d, self.hu_d, self.hv_d, 0.0)
+        ts = []
+        while True:
+            t, dt, ns = self.grid.time()
+            if ns % FWD_BLOCK == 0 and ns > 0:
+                ts.append(t)
+            if not (t < self.sc.t_f):
+                break
+            self.grid.step(1, self.sc.t_f)
+        self.n_fwd = ns
+        self.flag_times = ts
+        S.swa_sync_status()
+
+    def alloc_series(self):
+        torch = self.torch
+        self.series = torch.zeros((self.n_fwd, N_GAUGES), dtype=torch.float64,
+                                  device=self.flags.device)
+        self.counts = torch.zeros(self.n_fwd // FWD_BLOCK + 1, dtype=torch.int64,
+                                  device=self.flags.device)
+
+    def run(self, tstream, host_io=False, ev=None):
+        """One scenario on torch stream `tstream`.  ev: optional dict of event
+        lists for kernel timing (recorded on the same stream)."""
+        S, torch = self.S, self.torch
+        stream = tstream.cuda_stream
+        g, sc = self.grid, self.sc
+        launches = 0
+        if host_io:
+            S.swa_set_state(g.h, self.eta_h, self.hu_h, self.hv_h, 0.0, S.SWA_HOST, stream)
+            S.swa_set_adjoint_state(self.adj.h, self.phi_h, S.SWA_HOST, stream)
+        else:
+            S.swa_set_state(g.h, self.eta_d, self.hu_d, self.hv_d, 0.0, S.SWA_DEVICE, stream)
+            S.swa_set_adjoint_state(self.adj.h, self.phi_d, S.SWA_DEVICE, stream)
+        launches += 3 + 1 + 3
+        S.swa_snapstore_clear(self.store.h)
+        if ev is not None:
+            ev["adj"][0].record(tstream)
+        S.swa_run_adjoint(self.adj.h, self.store.h, SNAP_EVERY, stream)
+        if ev is not None:
+            ev["adj"][1].record(tstream)
+        launches += self.N_adj + 1
+        fp = 0
+        for s in range(self.n_fwd):
+            if ev is not None:
+                ev["fwd"][s][0].record(tstream)
+            S.swa_step_forward(g.h, 1, sc.t_f, stream)
+            if ev is not None:
+                ev["fwd"][s][1].record(tstream)
+            S.swa_gauge_sample(g.h, N_GAUGES, self.xy, self.series[s], stream)
+            launches += 2
+            if (s + 1) % FWD_BLOCK == 0:
+                if ev is not None:
+                    ev["flag"][fp][0].record(tstream)
+                S.swa_flag_cells(g.h, self.store.h, sc.t_s, sc.t_f, sc.tol,
+                                 S.SWA_FLAG_INTERP, self.flags, None,
+                                 self.counts[fp], stream)
+                if ev is not None:
+                    ev["flag"][fp][1].record(tstream)
+                fp += 1
+                launches += 1
+        if host_io:
+            out_series = self.series.to("cpu", non_blocking=True)
+            out_counts = self.counts.to("cpu", non_blocking=True)
+            return launches, out_series, out_counts
+        return launches, None, None
+
+
+def cell_updates(sc_obj):
+    return (sc_obj.n_fwd * sc_obj.n + sc_obj.N_adj * sc_obj.adj.n)
+
+
+def flag_bytes(sc_obj):
+    """Algorithmic bytes of each flag pass: forward q (3 words) and hbar or B
+    (1 word), the adjoint wet mask (1 byte), the snapshots in the window
+    (3 words each) and the flag byte."""
+    tau = np.array([sc_obj.sc.t_f - k * SNAP_EVERY * sc_obj.dt_adj
+                    for k in range(sc_obj.N_adj // SNAP_EVERY + 1)] + [0.0])
+    tau = np.unique(tau)[::-1]
+    w = 4 if sc_obj.p == sc_obj.S.SWA_FP32 else 8
+    out = []
+    t_f, t_s = sc_obj.sc.t_f, sc_obj.sc.t_s
+    K = len(tau)
+    for t in sc_obj.flag_times:
+        T = min(t + (t_f - t_s), t_f)
+        lo, hi = max(t, tau[-1]), min(T, tau[0])
+        if lo > hi:
+            k_eff = 0
+        else:
+            kh = next((k for k in range(K - 1) if tau[k + 1] <= hi), K - 1)
+            kl = next((k for k in range(K - 1) if tau[k + 1] <= lo), K - 1)
+            exact_l = kl + 1 >= K or tau[kl] == lo
+            k_eff = (kl if exact_l else kl + 1) - kh + 1
+        out.append(sc_obj.n * (4 * w + 1 + 1) + sc_obj.adj.n * 3 * w * k_eff)
+    return out
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    from paper_1605_05320_gb300 import build as B
+    B.build()
+    from paper_1605_05320_gb300 import swadj as S
+    from paper_1605_05320_gb300 import synth
+    S.load()
+    sc = synth.config2(n=args.n, L=args.n * 1e3)
+    scen = Scenario(S, torch, sc, args.precision, device)
+    scen.measure_steps()
+    scen.alloc_series()
+    stream = torch.cuda.current_stream(device)
+    hs = stream.cuda_stream
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        scen.run(stream)
+    torch.cuda.synchronize()
+    assert S.swa_sync_status(hs) == 0
+
+    # timed region: K scenarios, device-resident inputs, kernel events
+    n_flag = scen.n_fwd // FWD_BLOCK
+    evs = []
+    for _ in range(args.steps):
+        E = torch.cuda.Event
+        evs.append({"adj": (E(enable_timing=True), E(enable_timing=True)),
+                    "fwd": [(E(enable_timing=True), E(enable_timing=True))
+                            for _ in range(scen.n_fwd)],
+                    "flag": [(E(enable_timing=True), E(enable_timing=True))
+                             for _ in range(n_flag)]})
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    launches = 0
+    for k in range(args.steps):
+        nl, _, _ = scen.run(stream, ev=evs[k])
+        launches += nl
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    assert S.swa_sync_status(hs) == 0
+    ms_step = ms / args.steps
+    cu = cell_updates(scen)
+    value = cu * args.steps * world / (ms * 1e-3)
+
+    # kernel timings
+    fwd_ms = [e[0].elapsed_time(e[1]) for d in evs for e in d["fwd"]]
+    adj_ms = [d["adj"][0].elapsed_time(d["adj"][1]) for d in evs]
+    flag_ms = [e[0].elapsed_time(e[1]) for d in evs for e in d["flag"]]
+    w = 4 if args.precision == "fp32" else 8
+    fb = flag_bytes(scen)
+    peak, peak_kind = load_peaks()
+    kern = {
+        "fwd_step": {"launches": len(fwd_ms), "avg_us": 1e3 * np.mean(fwd_ms),
+                     "bytes_per_launch": 7 * w * scen.n,
+                     "total_ms": float(np.sum(fwd_ms)) / args.steps},
+        "adj_step": {"launches": scen.N_adj * args.steps,
+                     "avg_us": 1e3 * np.mean(adj_ms) / scen.N_adj,
+                     "bytes_per_launch": 7 * w * scen.adj.n
+                     + 3 * w * scen.adj.n / SNAP_EVERY,
+                     "total_ms": float(np.sum(adj_ms)) / args.steps},
+        "flag": {"launches": len(flag_ms), "avg_us": 1e3 * np.mean(flag_ms),
+                 "bytes_per_launch": float(np.mean(fb)) if fb else 0.0,
+                 "total_ms": float(np.sum(flag_ms)) / args.steps},
+    }
+    for k, v in kern.items():
+        v["gbs"] = v["bytes_per_launch"] / (v["avg_us"] * 1e-6) / 1e9 if v["avg_us"] > 0 else 0.0
+        v["frac"] = v["gbs"] / peak
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            key = f"{dom}_{args.precision}_{args.n}"
+            traffic = tr.get(key)
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom,
+                "achieved": round(kern[dom]["gbs"], 1), "peak": peak,
+                "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+                "frac": round(kern[dom]["frac"], 4), "traffic": traffic,
+                "bytes_per_launch": kern[dom]["bytes_per_launch"]}
+
+    # end-to-end through the C ABI with host buffers
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for k in range(args.steps):
+        _, s_out, c_out = scen.run(stream, host_io=True)
+        stream.synchronize()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = 3 * scen.n * 8 + 3 * scen.adj.n * 8
+    d2h = scen.series.numel() * 8 + scen.counts.numel() * 8
+    e2e = {"value": cu * args.steps * world / (ms_e2e * 1e-3), "unit": "cell-updates/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": ms_e2e / args.steps}
+
+    out = {
+        "metric": "SWE cell-updates/s (forward + adjoint steps, whole scenario incl. flag passes and gauges)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded basin bathymetry, Gaussian source and target)",
+        "config": {"workload": f"basin {args.n}x{args.n} 1 km, forward to t_f "
+                               f"({scen.n_fwd} steps) + adjoint ({scen.N_adj} steps, "
+                               f"snapshot every {SNAP_EVERY}) + flag every {FWD_BLOCK} "
+                               f"+ {N_GAUGES} gauges",
+                   "precision": args.precision, "cells": scen.n,
+                   "forward_steps": scen.n_fwd, "adjoint_steps": scen.N_adj,
+                   "snapshots": scen.store.info()[0], "flag_passes": n_flag,
+                   "l2": "inputs larger than L2 (snapshot store streamed by every flag pass)",
+                   "parallelism": f"replicas x{world} (independent scenarios)"},
+        "roofline": roofline,
+        "kernels": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv)
+                        for kk, vv in v.items()} for k, v in kern.items()},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "flags_last": int(scen.counts.sum().item()),
+    }
+    return out
+
+
+# ------------------------------------------------------------ oracle timing
+_ORACLE_CASE = {}
+
+
+def oracle_sample(n, steps):
+    """The FP64 oracle on a bounded sample of the same workload: `steps`
+    forward and `steps` adjoint steps on the n x n basin, OpenMP on all host
+    cores.  Returns (cell-updates/s, seconds, threads)."""
+    import oracle as O
+    from paper_1605_05320_gb300 import synth
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    if n not in _ORACLE_CASE:
+        sc = synth.config2(n=n, L=n * 1e3)
+        og = O.Grid.from_spec(sc.grid)
+        hbar = np.maximum(-sc.B_adj, 0.0)
+        smax = O.adj_smax(og, hbar)
+        _ORACLE_CASE[n] = (sc, og, hbar, sc.t_f / np.ceil(sc.t_f * smax / og.cfl))
+    sc, og, hbar, dt_adj = _ORACLE_CASE[n]
+    h0 = sc.eta0 - sc.B
+    t0 = time.perf_counter()
+    O.fwd_run(og, h0, sc.hu0, sc.hv0, sc.B, steps, sc.t_f)
+    e, m, gm = sc.phi[0], sc.phi[1], sc.phi[2]
+    for _ in range(steps):
+        e, m, gm = O.adj_step(og, e, m, gm, hbar, dt_adj)
+    sec = time.perf_counter() - t0
+    return 2 * steps * sc.grid.n / sec, sec, O.num_threads()
+
+
+def run_reference(args):
+    cores = os.cpu_count() or 1
+    n = args.n
+    per = 2
+    for _ in range(args.warmup):
+        oracle_sample(n, 1)
+    t0 = time.perf_counter()
+    cells = 0
+    for _ in range(args.steps):
+        v, sec, thr = oracle_sample(n, per)
+        cells += 2 * per * n * n
+    sec = time.perf_counter() - t0
+    value = cells / sec
+    sample = (f"{per} forward + {per} adjoint FP64 oracle steps on the {n}x{n} basin "
+              f"per step (OpenMP, {thr} threads)")
+    return {
+        "impl": "reference",
+        "metric": "SWE cell-updates/s (forward + adjoint steps, whole scenario incl. flag passes and gauges)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded basin bathymetry)",
+        "config": {"workload": f"basin {n}x{n} 1 km (bounded oracle sample)",
+                   "precision": "fp64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": thr,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, sec, thr = oracle_sample(args.n, 2)
+            out["cpu_baseline"] = {
+                "value": v, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
+                "sample": f"2 forward + 2 adjoint FP64 oracle steps on the {args.n}x{args.n} "
+                          f"basin ({sec:.1f} s, OpenMP)"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

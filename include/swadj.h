@@ -1,0 +1,231 @@
+/*
+ * swadj.h -- C ABI of libswadj.so: the data-parallel hot path of adjoint-guided
+ * refinement for tsunami modelling (Davis & LeVeque, arXiv 1605.05320) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Arrays are cell-centred, row-major with x fastest: index j*nx + i.
+ *  - "_host" pointers are host memory, "_dev" pointers are device memory of
+ *    the current CUDA device.  Where an argument takes either, `where` says
+ *    which (SWA_HOST / SWA_DEVICE).
+ *  - The library never allocates device memory.  Each object has a
+ *    *_workspace_bytes() query; the caller allocates that many bytes of
+ *    device memory (256-byte aligned) and passes it to *_create(); the object
+ *    carves its arrays out of it.  The caller keeps the workspace alive until
+ *    the object is destroyed and frees it afterwards.  Handles themselves are
+ *    small host structs owned by the library (freed by swa_destroy_*).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device work
+ *    is enqueued on it and the call returns without waiting, except where a
+ *    function says it synchronises.  Forward and adjoint stepping keep time,
+ *    time step and buffer parity on the device, so a sequence of calls can be
+ *    captured into a CUDA graph and replayed.
+ *  - Every function returns an int status (SWA_OK = 0 or a negative code).
+ *    swa_last_error() gives a message for the calling thread.  No C++
+ *    exception crosses the ABI.  Device-side problems (non-finite state,
+ *    non-positive depth) set a device error word that swa_sync_status()
+ *    reports.
+ */
+#ifndef SWADJ_H
+#define SWADJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SWA_OK 0
+#define SWA_EINVAL (-1)    /* bad argument */
+#define SWA_ENOMEM (-2)    /* workspace too small / capacity exceeded */
+#define SWA_ECUDA (-3)     /* a CUDA runtime call failed */
+#define SWA_ESTATE (-4)    /* call not valid in the object's state */
+#define SWA_EUNSTABLE (-5) /* device saw a non-finite value or depth <= 0 */
+#define SWA_ETIMEOUT (-6)  /* reserved: a bounded device wait expired */
+
+/* ---- enums ---- */
+#define SWA_FP64 0      /* state (h, hu, hv) and bathymetry B in double     */
+#define SWA_FP32 1      /* perturbation form: (eta, hu, hv) and hbar = -B in
+                           float; the time step is still reduced in double  */
+#define SWA_BC_EXTRAP 0 /* ghost cells copy the nearest interior cell        */
+#define SWA_BC_WALL 1   /* ghost cells mirror, normal momentum negated       */
+#define SWA_FLAG_INTERP 0  /* Eq. (ip_timerange), adjoint linear in time      */
+#define SWA_FLAG_BRACKET 1 /* max over bracketing snapshots, Eq. (ip_timepoint)
+                              when t_s = t_f                                  */
+#define SWA_HOST 0
+#define SWA_DEVICE 1
+
+/*
+ * Grid descriptor.  ndim = 1 (ny must be 1) or 2.  x_lo/y_lo: lower-left
+ * corner; dx/dy: cell size.  bc[] = {x_lo, x_hi, y_lo, y_hi}.  g: gravity
+ * (9.81); cfl: Courant number (0.75); dry_tol: depth at or below which a
+ * cell is dry (1e-3 m).  order: 1 (Godunov) or 2 (MC-limited corrections).
+ */
+typedef struct swa_grid_desc {
+    int ndim, nx, ny;
+    double x_lo, y_lo, dx, dy;
+    int precision;
+    int order;
+    int bc[4];
+    double g, cfl, dry_tol;
+} swa_grid_desc;
+
+typedef struct swa_grid swa_grid;
+typedef struct swa_adjoint swa_adjoint;
+typedef struct swa_snapstore swa_snapstore;
+
+const char *swa_version(void);
+/* Message of the last failing call on this thread ("" if none). */
+const char *swa_last_error(void);
+
+/*
+ * Synchronise `stream`, then read and clear the device error word shared by
+ * all objects on the current device.  Returns SWA_OK or SWA_EUNSTABLE.
+ */
+int swa_sync_status(void *stream);
+
+/* =========================== forward grid ================================
+ * The nonlinear shallow water equations with bathymetry, Eq. (swe_1d) in 1D
+ * and Eq. (swe) in 2D (Sec. 3, Sec. 5), solved by a Godunov-type finite
+ * volume method with a Roe-type Riemann solver per edge (Sec. 6).
+ */
+size_t swa_grid_workspace_bytes(const swa_grid_desc *desc);
+
+/*
+ * Create a forward grid in `ws` (ws_bytes >= swa_grid_workspace_bytes).
+ * bathy_host: nx*ny bottom elevations B (host, FP64, copied).  The state is
+ * the ocean at rest (eta = 0) until swa_set_state.
+ */
+int swa_create_grid(const swa_grid_desc *desc, const double *bathy_host,
+                    void *ws, size_t ws_bytes, void *stream, swa_grid **out);
+int swa_destroy_grid(swa_grid *grid);
+
+/*
+ * Set the state from surface elevation eta = h + B and momenta (FP64, n
+ * values each; hv may be NULL for ndim = 1), at time t.  Also computes the
+ * first time step from the CFL condition on the device.
+ */
+int swa_set_state(swa_grid *grid, const double *eta, const double *hu,
+                  const double *hv, double t, int where, void *stream);
+
+/*
+ * Read the state as FP64 arrays of n values: any of h, hu, hv, eta may be
+ * NULL.  where = SWA_HOST synchronises the stream.
+ */
+int swa_get_state(swa_grid *grid, double *h, double *hu, double *hv,
+                  double *eta, int where, void *stream);
+
+/*
+ * Take up to max_steps explicit steps, stopping at t_end: each step uses
+ * dt = min(cfl / s_max(Q^n), t_end - t_n), s_max = max over cells of
+ * (|u|+c)/dx + (|v|+c)/dy, c = sqrt(g h).  The update applies, at every
+ * edge, the f-wave Roe solution with the bathymetry source folded into the
+ * momentum jump (the ocean at rest is exact), the fluctuations of all edges
+ * of a cell (unsplit in 2D, no transverse terms) and, for order 2, MC-
+ * limited corrections.  The CFL maximum for the next step is reduced in the
+ * same kernel.  Steps past t_end are no-ops on the device.
+ */
+int swa_step_forward(swa_grid *grid, int max_steps, double t_end, void *stream);
+
+/* Synchronises; any pointer may be NULL. */
+int swa_get_time(swa_grid *grid, double *t, double *dt_next,
+                 long long *nsteps, void *stream);
+
+/*
+ * Device pointers of the current state arrays (read-only use), for gauge or
+ * diagnostic kernels of the caller.  Synchronises (the current buffer is
+ * device-resident).  precision tells the element type (double or float).
+ */
+int swa_grid_arrays(swa_grid *grid, const void **q0, const void **q1,
+                    const void **q2, const void **bath, void *stream);
+
+/* ============================== adjoint ==================================
+ * The time-reversed adjoint of Sec. 4: q~(x,t) = q^(x, t_f - t) solves
+ * q~_t - (A^T q~)_x [- (A_2^T q~)_y] = 0 forward in t with q~(0) = phi,
+ * A, A_2 from the linearisation about the ocean at rest (Sec. 3, Sec. 5),
+ * zero normal velocity at wet/dry edges (Sec. 5).  Fixed time step
+ * dt = t_f / N, N = ceil(t_f * max(c/dx + c/dy) / cfl), c = sqrt(g hbar).
+ */
+size_t swa_adjoint_workspace_bytes(const swa_grid_desc *desc);
+
+/*
+ * bathy_host: adjoint-grid B (FP64, copied); phi_host: (ndim+1) x n values
+ * of phi = q^(t_f) (component-major).  Synchronises once (to size N).
+ */
+int swa_create_adjoint(const swa_grid_desc *desc, const double *bathy_host,
+                       const double *phi_host, double t_f, void *ws,
+                       size_t ws_bytes, void *stream, swa_adjoint **out);
+int swa_destroy_adjoint(swa_adjoint *adj);
+/* N, dt and the number of steps taken so far. */
+int swa_adjoint_info(const swa_adjoint *adj, long long *n_steps, double *dt,
+                     long long *steps_done);
+/* Take nsteps adjoint steps (clamped to the remaining N - steps_done). */
+int swa_step_adjoint(swa_adjoint *adj, int nsteps, void *stream);
+/* Read the adjoint state (FP64, (ndim+1) x n, component-major). */
+int swa_get_adjoint_state(swa_adjoint *adj, double *q, int where, void *stream);
+/*
+ * Restart the adjoint from new data phi = q^(t_f) ((ndim+1) x n FP64,
+ * component-major, host or device): steps_done returns to 0, N and dt are
+ * kept (they depend only on the bathymetry).
+ */
+int swa_set_adjoint_state(swa_adjoint *adj, const double *phi, int where,
+                          void *stream);
+
+/* ============================= snapshots =================================
+ * Snapshots of the adjoint at regular times (Sec. 4), device resident:
+ * snapshot k holds q^(tau_k) = q~(t_f - tau_k), tau strictly decreasing.
+ * precision: SWA_FP64 or SWA_FP32 storage.
+ */
+size_t swa_snapstore_workspace_bytes(const swa_grid_desc *adj_desc,
+                                     int max_snaps, int precision);
+int swa_create_snapstore(const swa_adjoint *adj, int max_snaps, int precision,
+                         void *ws, size_t ws_bytes, swa_snapstore **out);
+int swa_destroy_snapstore(swa_snapstore *store);
+/* Append the current adjoint state with tau = t_f - steps_done * dt. */
+int swa_store_snapshot(swa_adjoint *adj, swa_snapstore *store, void *stream);
+/*
+ * Whole adjoint solve: snapshot at tau = t_f, then N steps with a snapshot
+ * every `every` steps and after the last; the snapshot copy is fused into
+ * the step that produces it.  Fails with SWA_ENOMEM before enqueuing
+ * anything if the store cannot hold them all.
+ */
+int swa_run_adjoint(swa_adjoint *adj, swa_snapstore *store, int every,
+                    void *stream);
+/* Forget all snapshots (the workspace is reused by the next ones). */
+int swa_snapstore_clear(swa_snapstore *store);
+/* Number of snapshots and (optionally) a host copy of their tau values. */
+int swa_snapstore_info(const swa_snapstore *store, int *count, double *tau_host,
+                       int tau_cap);
+
+/* =============================== flagging ================================
+ * Adjoint-weighted flagging (Sec. 4.1, 4.2, Sec. 6).  For the forward state
+ * at its device time t and q = (eta, hu, hv):
+ *   m(x) = max over tau in [t, T] of |q^(x, tau) . q(x, t)|,
+ *   T = min(t + (t_f - t_s), t_f), the window clipped to the stored taus;
+ * INTERP takes q^ piecewise linear in tau; BRACKET takes every snapshot from
+ * the latest at or before t to the earliest at or after T.  q^ is bilinearly
+ * interpolated from the adjoint grid's cell centres (clamped at the edge),
+ * component by component.  m = 0 where the forward cell is dry or an adjoint
+ * cell with positive weight is dry.  flags_dev[i] = (m >= tol); maxip_dev
+ * (nullable, float) receives m; *count_dev (device int64, overwritten)
+ * receives the number of flags.  t > t_f gives no flags.
+ */
+int swa_flag_cells(const swa_grid *grid, const swa_snapstore *store,
+                   double t_s, double t_f, double tol, int mode,
+                   uint8_t *flags_dev, float *maxip_dev, long long *count_dev,
+                   void *stream);
+
+/* ================================ gauges =================================
+ * Surface elevation eta = h + B at n points xy_dev[2k], xy_dev[2k+1]
+ * (device, FP64) by bilinear interpolation of cell centres, clamped to the
+ * outermost centres (Sec. 6 gauges); written to eta_dev[0..n).
+ */
+int swa_gauge_sample(const swa_grid *grid, int n, const double *xy_dev,
+                     double *eta_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWADJ_H */

@@ -1,0 +1,263 @@
+// adj.cu -- time-reversed linear adjoint step (Sec. 4, Sec. 5).
+//
+// q~ = (eta~, mu~, gamma~) solves q~_t + F_x + G_y = 0 with F = -A_1^T q~ =
+// -(g hbar mu~, eta~, 0) and G = -A_2^T q~ = -(g hbar gamma~, 0, eta~), the
+// transposed linearisation about the ocean at rest run forward in reversed
+// time (q^(x, t_f - t) = q~(x, t)).  At an edge the flux jump splits along
+// the left cell's left-going eigenvector [cL, 1] (speed -cL) and the right
+// cell's right-going one [-cR, 1] (speed +cR), c = sqrt(g hbar): an f-wave
+// form for spatially varying coefficients.  A wet/dry edge is a wall (zero
+// normal velocity, Sec. 5): the dry side is the mirror of the wet one, and
+// the edge carries no second-order correction.
+#include "adj.cuh"
+
+namespace swadj {
+
+template <typename R>
+struct AdjWave {
+    R b1, b2, cL, cR;
+    int wall;
+};
+
+// Waves at the edge between (eL, mL, cL) and (eR, mR, cR); normal component m.
+template <typename R>
+__device__ __forceinline__ AdjWave<R> adj_riemann(R eL, R mL, R cL, R eR, R mR,
+                                                  R cR) {
+    AdjWave<R> w;
+    const bool dL = !(cL > R(0)), dR = !(cR > R(0));
+    w.wall = (dL || dR) ? 1 : 0;
+    if (dL && dR) { w.b1 = R(0); w.b2 = R(0); w.cL = R(0); w.cR = R(0); return w; }
+    if (dL) { eL = eR; mL = -mR; cL = cR; }
+    if (dR) { eR = eL; mR = -mL; cR = cL; }
+    const R F1L = -(cL * cL * mL), F2L = -eL;
+    const R F1R = -(cR * cR * mR), F2R = -eR;
+    const R d1 = F1R - F1L, d2 = F2R - F2L;
+    const R s = cL + cR;
+    w.b1 = (d1 + cR * d2) / s;
+    w.b2 = (cL * d2 - d1) / s;
+    w.cL = cL;
+    w.cR = cR;
+    return w;
+}
+
+// Fluctuations and correction at edge w with neighbours wm (left), wp (right).
+// Wave 1: Z = b1 (cL, 1), speed -cL (to the left cell);
+// wave 2: Z = b2 (-cR, 1), speed +cR (to the right cell).
+template <typename R>
+__device__ __forceinline__ void adj_flux(const AdjWave<R> &wm, const AdjWave<R> &w,
+                                         const AdjWave<R> &wp, R nu, int order,
+                                         R am[2], R ap[2], R F[2]) {
+    const R Z1[2] = {w.b1 * w.cL, w.b1};
+    const R Z2[2] = {-w.b2 * w.cR, w.b2};
+    am[0] = Z1[0]; am[1] = Z1[1];
+    ap[0] = Z2[0]; ap[1] = Z2[1];
+    F[0] = R(0); F[1] = R(0);
+    if (order < 2 || w.wall) return;
+    {   // wave 1, upwind edge to the right
+        const R U[2] = {wp.b1 * wp.cL, wp.b1};
+        const R zz = Z1[0] * Z1[0] + Z1[1] * Z1[1];
+        R th = R(0);
+        if (zz != R(0)) th = (U[0] * Z1[0] + U[1] * Z1[1]) / zz;
+        const R coef = R(0.5) * R(-1) * (R(1) - nu * w.cL) * mc_phi(th);
+        F[0] += coef * Z1[0];
+        F[1] += coef * Z1[1];
+    }
+    {   // wave 2, upwind edge to the left
+        const R U[2] = {-wm.b2 * wm.cR, wm.b2};
+        const R zz = Z2[0] * Z2[0] + Z2[1] * Z2[1];
+        R th = R(0);
+        if (zz != R(0)) th = (U[0] * Z2[0] + U[1] * Z2[1]) / zz;
+        const R coef = R(0.5) * (R(1) - nu * w.cR) * mc_phi(th);
+        F[0] += coef * Z2[0];
+        F[1] += coef * Z2[1];
+    }
+}
+
+template <typename R, bool TWO_D, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
+    constexpr int HX = 2, HY = TWO_D ? 2 : 0;
+    constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY;
+    constexpr int NT = TX * TY;
+    constexpr int NEX = RX - 1;
+    constexpr int NEY = TWO_D ? RY - 1 : 1;
+    constexpr int WYC = TWO_D ? TX : 1;
+    __shared__ R s_e[RY][RX], s_m[RY][RX], s_g[RY][RX], s_c[RY][RX];
+    __shared__ AdjWave<R> wx[TY][NEX];
+    __shared__ AdjWave<R> wy[NEY][WYC];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + ty * TX;
+    const int nx = p.nx, ny = p.ny;
+    const int i0 = blockIdx.x * TX - HX, j0 = blockIdx.y * TY - HY;
+
+    for (int r = tid; r < RX * RY; r += NT) {
+        const int ry = r / RX, rx = r - ry * RX;
+        const bool xin = rx >= HX && rx < HX + TX;
+        const bool yin = ry >= HY && ry < HY + TY;
+        if (!xin && !yin) continue;
+        bool fx, fy = false;
+        const int ci = ghost_index(i0 + rx, nx, p.bc.lo_x, p.bc.hi_x, &fx);
+        int cj = 0;
+        if (TWO_D) cj = ghost_index(j0 + ry, ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        const size_t o = (size_t)cj * nx + ci;
+        R m = p.src[1][o], g = TWO_D ? p.src[2][o] : R(0);
+        if (fx) m = -m;
+        if (fy) g = -g;
+        s_e[ry][rx] = p.src[0][o];
+        s_m[ry][rx] = m;
+        s_g[ry][rx] = g;
+        s_c[ry][rx] = p.c[o];
+    }
+    __syncthreads();
+
+    for (int e = tid; e < TY * NEX; e += NT) {
+        const int row = e / NEX, k = e - row * NEX, ry = row + HY;
+        wx[row][k] = adj_riemann<R>(s_e[ry][k], s_m[ry][k], s_c[ry][k],
+                                    s_e[ry][k + 1], s_m[ry][k + 1], s_c[ry][k + 1]);
+    }
+    if (TWO_D) {
+        for (int e = tid; e < NEY * TX; e += NT) {
+            const int k = e / TX, col = e - k * TX, rx = col + HX;
+            wy[k][col] = adj_riemann<R>(s_e[k][rx], s_g[k][rx], s_c[k][rx],
+                                        s_e[k + 1][rx], s_g[k + 1][rx], s_c[k + 1][rx]);
+        }
+    }
+    __syncthreads();
+
+    const int gi = blockIdx.x * TX + tx, gj = blockIdx.y * TY + ty;
+    if (gi >= nx || gj >= ny) return;
+    const int cx = tx + HX, cy = ty + HY;
+    R ne = s_e[cy][cx], nm = s_m[cy][cx], ng = s_g[cy][cx];
+    if (s_c[cy][cx] > R(0)) {
+        R am0[2], ap0[2], F0[2], am1[2], ap1[2], F1[2];
+        adj_flux<R>(wx[ty][tx], wx[ty][tx + 1], wx[ty][tx + 2], p.nux, p.order, am0, ap0, F0);
+        adj_flux<R>(wx[ty][tx + 1], wx[ty][tx + 2], wx[ty][tx + 3], p.nux, p.order, am1, ap1, F1);
+        R de = -p.nux * (ap0[0] + am1[0]) - p.nux * (F1[0] - F0[0]);
+        const R dm = -p.nux * (ap0[1] + am1[1]) - p.nux * (F1[1] - F0[1]);
+        R dg = R(0);
+        if (TWO_D) {
+            R bm0[2], bp0[2], G0[2], bm1[2], bp1[2], G1[2];
+            adj_flux<R>(wy[ty][tx], wy[ty + 1][tx], wy[ty + 2][tx], p.nuy, p.order, bm0, bp0, G0);
+            adj_flux<R>(wy[ty + 1][tx], wy[ty + 2][tx], wy[ty + 3][tx], p.nuy, p.order, bm1, bp1, G1);
+            de += -p.nuy * (bp0[0] + bm1[0]) - p.nuy * (G1[0] - G0[0]);
+            dg = -p.nuy * (bp0[1] + bm1[1]) - p.nuy * (G1[1] - G0[1]);
+        }
+        ne += de;
+        nm += dm;
+        ng += dg;
+    }
+    const size_t o = (size_t)gj * nx + gi;
+    p.dst[0][o] = ne;
+    p.dst[1][o] = nm;
+    if (TWO_D) p.dst[2][o] = ng;
+    if (p.snap_f) {
+        p.snap_f[o] = (float)ne;
+        p.snap_f[p.snap_comp_stride + o] = (float)nm;
+        if (TWO_D) p.snap_f[2 * p.snap_comp_stride + o] = (float)ng;
+    } else if (p.snap_d) {
+        p.snap_d[o] = (double)ne;
+        p.snap_d[p.snap_comp_stride + o] = (double)nm;
+        if (TWO_D) p.snap_d[2 * p.snap_comp_stride + o] = (double)ng;
+    }
+    if ((p.snap_f || p.snap_d) && o == 0) *p.tau_dev = p.tau_val;
+}
+
+template <typename R, bool TWO_D, int TX, int TY>
+static int launch_adj(const AdjParams<R> &p, cudaStream_t st) {
+    dim3 grid((p.nx + TX - 1) / TX, TWO_D ? (p.ny + TY - 1) / TY : 1);
+    adj_step_kernel<R, TWO_D, TX, TY><<<grid, dim3(TX, TY), 0, st>>>(p);
+    return swadj_host::cuda_check(cudaGetLastError(), "adj_step_kernel");
+}
+
+template <>
+int adj_launch_step<double>(const AdjParams<double> &p, cudaStream_t st) {
+    if (p.two_d) return launch_adj<double, true, 32, 4>(p, st);
+    return launch_adj<double, false, 128, 1>(p, st);
+}
+
+template <>
+int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
+    if (p.two_d) return launch_adj<float, true, 32, 8>(p, st);
+    return launch_adj<float, false, 128, 1>(p, st);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
+    // non-negative doubles order like their bit patterns as unsigned integers
+    atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename R>
+__global__ void adj_init_kernel(const double *B, R *c, size_t n, int two_d,
+                                double g, double dx, double dy, double dry_tol,
+                                double *smax) {
+    double mx = 0.0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const double hb = -B[k] > 0.0 ? -B[k] : 0.0;
+        double cc = 0.0, s = 0.0;
+        if (hb > dry_tol) {
+            cc = sqrt(g * hb);
+            s = cc / dx;
+            if (two_d) s += cc / dy;
+        }
+        c[k] = (R)cc;
+        mx = s > mx ? s : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = w > mx ? w : mx;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(smax, mx);
+}
+
+template <typename R>
+int adj_launch_init(const double *B, R *c, size_t n, int two_d, double g,
+                    double dx, double dy, double dry_tol, double *smax,
+                    cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 2048) blocks = 2048;
+    adj_init_kernel<R><<<blocks, 256, 0, st>>>(B, c, n, two_d, g, dx, dy, dry_tol, smax);
+    return swadj_host::cuda_check(cudaGetLastError(), "adj_init_kernel");
+}
+
+template <typename R>
+__global__ void adj_store_kernel(const R *s0, const R *s1, const R *s2, int ncomp,
+                                 size_t n, float *sf, double *sd, size_t cs,
+                                 double *tau_dev, double tau_val) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        if (sf) {
+            sf[k] = (float)s0[k];
+            sf[cs + k] = (float)s1[k];
+            if (ncomp == 3) sf[2 * cs + k] = (float)s2[k];
+        } else {
+            sd[k] = (double)s0[k];
+            sd[cs + k] = (double)s1[k];
+            if (ncomp == 3) sd[2 * cs + k] = (double)s2[k];
+        }
+        if (k == 0) *tau_dev = tau_val;
+    }
+}
+
+template <typename R>
+int adj_launch_store(const R *const src[3], int ncomp, size_t n, float *snap_f,
+                     double *snap_d, size_t comp_stride, double *tau_dev,
+                     double tau_val, cudaStream_t st) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    adj_store_kernel<R><<<blocks, 256, 0, st>>>(src[0], src[1], src[2], ncomp, n,
+                                                snap_f, snap_d, comp_stride,
+                                                tau_dev, tau_val);
+    return swadj_host::cuda_check(cudaGetLastError(), "adj_store_kernel");
+}
+
+template int adj_launch_init<double>(const double *, double *, size_t, int, double,
+                                     double, double, double, double *, cudaStream_t);
+template int adj_launch_init<float>(const double *, float *, size_t, int, double,
+                                    double, double, double, double *, cudaStream_t);
+template int adj_launch_store<double>(const double *const[3], int, size_t, float *,
+                                      double *, size_t, double *, double, cudaStream_t);
+template int adj_launch_store<float>(const float *const[3], int, size_t, float *,
+                                     double *, size_t, double *, double, cudaStream_t);
+
+}  // namespace swadj

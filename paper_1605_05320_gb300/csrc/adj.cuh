@@ -1,0 +1,41 @@
+// adj.cuh -- adjoint-step kernel parameters and host launchers.
+#pragma once
+
+#include "swadj_internal.cuh"
+
+namespace swadj {
+
+template <typename R>
+struct AdjParams {
+    int nx, ny, two_d, order;
+    BcSpec bc;
+    R nux, nuy;          // dt/dx, dt/dy (fixed step)
+    const R *src[3];     // (eta~, mu~, gamma~) at step s
+    R *dst[3];           // at step s+1
+    const R *c;          // sqrt(g hbar), 0 where dry
+    // fused snapshot (optional): written with the new state when snap_f or
+    // snap_d is non-null
+    float *snap_f;
+    double *snap_d;
+    size_t snap_comp_stride;  // elements between components of one snapshot
+    double *tau_dev;
+    double tau_val;
+};
+
+template <typename R>
+int adj_launch_step(const AdjParams<R> &p, cudaStream_t st);
+
+// c = sqrt(g hbar) (0 where hbar <= dry_tol), hbar = max(-B, 0) computed from
+// the FP64 bathymetry in `B`; atomically maxes c/dx [+ c/dy] into *smax.
+template <typename R>
+int adj_launch_init(const double *B, R *c, size_t n, int two_d, double g,
+                    double dx, double dy, double dry_tol, double *smax,
+                    cudaStream_t st);
+
+// Copy the state into snapshot slot `k` (converted to the snapshot type).
+template <typename R>
+int adj_launch_store(const R *const src[3], int ncomp, size_t n, float *snap_f,
+                     double *snap_d, size_t comp_stride, double *tau_dev,
+                     double tau_val, cudaStream_t st);
+
+}  // namespace swadj

@@ -1,0 +1,252 @@
+// flag.cu -- adjoint-weighted flagging (Sec. 4.1, 4.2, Sec. 6) and gauges.
+//
+// For the forward state at its device time t and q = (eta, hu, hv) the pass
+// computes m = max over tau in [t, T] of |q^(tau) . q|, T = min(t + (t_f -
+// t_s), t_f), the window clipped to the stored snapshot times, with q^
+// bilinear in space (component by component, clamped at the outermost
+// adjoint cell centres) and either linear in time (INTERP: the maximum of a
+// piecewise-linear function sits at a window end or at a snapshot time inside
+// it) or taken over every bracketing snapshot (BRACKET, Eq. ip_timepoint).
+// m = 0 where the forward cell is dry or a positively weighted adjoint cell
+// is dry (Sec. 6).  The pass streams each snapshot once per cell: it is
+// bandwidth bound, so the snapshot loop is written for coalesced loads.
+#include <type_traits>
+
+#include "flag.cuh"
+
+namespace swadj {
+
+struct Window {
+    int empty;
+    int k0, k1;          // snapshots read: k0..k1 inclusive
+    int kh, kl;          // INTERP: bracket index at hi and at lo
+    int exact_h, exact_l;
+    double ah, al;       // weights on snapshot kh (resp. kl) at hi (lo)
+    double lo, hi;
+};
+
+// Index k of the snapshot interval holding s: the first k (from 0) whose
+// successor is no later than s, i.e. tau[k+1] <= s (K-1 if none).
+__device__ __forceinline__ int bracket_index(const double *tau, int K, double s) {
+    int a = 1, b = K;  // first j in [1, K) with tau[j] <= s, else K
+    while (a < b) {
+        const int m = (a + b) >> 1;
+        if (tau[m] > s) a = m + 1;
+        else b = m;
+    }
+    return a - 1;
+}
+
+__device__ Window make_window(const double *tau, int K, double t, double t_s,
+                              double t_f, int mode) {
+    Window w;
+    double T = t + (t_f - t_s);
+    if (T > t_f) T = t_f;
+    double lo = t, hi = T;
+    w.empty = 1;
+    w.k0 = 0; w.k1 = -1; w.kh = 0; w.kl = 0; w.exact_h = 1; w.exact_l = 1;
+    w.ah = 1.0; w.al = 1.0;
+    if (K < 1) return w;
+    if (lo < tau[K - 1]) lo = tau[K - 1];
+    if (hi > tau[0]) hi = tau[0];
+    w.lo = lo; w.hi = hi;
+    if (lo > hi || t > t_f) return w;
+    w.empty = 0;
+    if (mode == SWA_FLAG_BRACKET) {
+        int kb = K - 1, ke = 0;
+        for (int k = 0; k < K; k++) if (tau[k] <= lo) { kb = k; break; }
+        for (int k = K - 1; k >= 0; k--) if (tau[k] >= hi) { ke = k; break; }
+        w.k0 = ke; w.k1 = kb;
+        return w;
+    }
+    const int kh = bracket_index(tau, K, hi);
+    const int kl = bracket_index(tau, K, lo);
+    w.kh = kh; w.kl = kl;
+    w.exact_h = (kh + 1 >= K || tau[kh] == hi);
+    w.exact_l = (kl + 1 >= K || tau[kl] == lo);
+    if (!w.exact_h) w.ah = (hi - tau[kh + 1]) / (tau[kh] - tau[kh + 1]);
+    if (!w.exact_l) w.al = (lo - tau[kl + 1]) / (tau[kl] - tau[kl + 1]);
+    w.k0 = kh;
+    w.k1 = w.exact_l ? kl : kl + 1;
+    if (w.k1 < w.k0) w.k1 = w.k0;
+    return w;
+}
+
+// Products are accumulated in float when both the forward state and the
+// snapshots are float (the bandwidth-bound FP32 path; GB300's FP64 rate is a
+// small fraction of its FP32 rate) and in double otherwise.
+template <typename R, typename S, bool SAME>
+__global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
+    using A = typename std::conditional<sizeof(R) == 4 && sizeof(S) == 4, float,
+                                        double>::type;
+    __shared__ Window sw;
+    if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
+    __syncthreads();
+    const Window w = sw;
+    const int cur = p.clk->cur;
+    const R *q0 = p.q[cur][0], *q1 = p.q[cur][1], *q2 = p.q[cur][2];
+    const size_t n = (size_t)p.nx * p.ny;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    if (i < n) {
+        A m = A(0);
+        const R a = q0[i], b = p.bath[i];
+        R h, eta;
+        if (sizeof(R) == 4) { eta = a; h = a + b; }
+        else { h = a; eta = a + b; }
+        const A qe = (A)eta, qu = (A)q1[i];
+        const A qv = p.two_d ? (A)q2[i] : A(0);
+        bool dry = !(h > p.dry_tol);
+        size_t st[4] = {i, i, i, i};
+        A wt[4] = {A(1), A(0), A(0), A(0)};
+        if (!SAME) {
+            const int ix = (int)(i % p.nx), jy = (int)(i / p.nx);
+            const double x = p.x_lo + ((double)ix + 0.5) * p.dx;
+            const double y = p.y_lo + ((double)jy + 0.5) * p.dy;
+            double fx = (x - p.ax_lo) / p.adx - 0.5;
+            fx = fx < 0.0 ? 0.0 : (fx > (double)(p.anx - 1) ? (double)(p.anx - 1) : fx);
+            int i0 = (int)floor(fx);
+            if (i0 > p.anx - 2) i0 = p.anx - 2;
+            if (i0 < 0) i0 = 0;
+            double ax = fx - (double)i0;
+            const int i1 = p.anx > 1 ? i0 + 1 : i0;
+            if (p.anx == 1) ax = 0.0;
+            if (!p.two_d) {
+                st[0] = i0; st[1] = i1;
+                wt[0] = (A)(1.0 - ax); wt[1] = (A)ax;
+            } else {
+                double fy = (y - p.ay_lo) / p.ady - 0.5;
+                fy = fy < 0.0 ? 0.0 : (fy > (double)(p.any - 1) ? (double)(p.any - 1) : fy);
+                int j0 = (int)floor(fy);
+                if (j0 > p.any - 2) j0 = p.any - 2;
+                if (j0 < 0) j0 = 0;
+                double ay = fy - (double)j0;
+                const int j1 = p.any > 1 ? j0 + 1 : j0;
+                if (p.any == 1) ay = 0.0;
+                st[0] = (size_t)j0 * p.anx + i0; wt[0] = (A)((1.0 - ax) * (1.0 - ay));
+                st[1] = (size_t)j0 * p.anx + i1; wt[1] = (A)(ax * (1.0 - ay));
+                st[2] = (size_t)j1 * p.anx + i0; wt[2] = (A)((1.0 - ax) * ay);
+                st[3] = (size_t)j1 * p.anx + i1; wt[3] = (A)(ax * ay);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            if (wt[c] > A(0) && !p.awet[st[c]]) dry = true;
+        if (!w.empty && !dry) {
+            A dh0 = A(0), dh1 = A(0), dl0 = A(0), dl1 = A(0);
+            for (int k = w.k0; k <= w.k1; k++) {
+                const S *s = p.snaps + (size_t)k * p.snap_stride;
+                A v0, v1, v2 = A(0);
+                if (SAME) {
+                    v0 = (A)s[i];
+                    v1 = (A)s[p.na + i];
+                    if (p.ncomp == 3) v2 = (A)s[2 * p.na + i];
+                } else {
+                    v0 = A(0); v1 = A(0);
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        v0 += wt[c] * (A)s[st[c]];
+                        v1 += wt[c] * (A)s[p.na + st[c]];
+                        if (p.ncomp == 3) v2 += wt[c] * (A)s[2 * p.na + st[c]];
+                    }
+                }
+                const A d = v0 * qe + v1 * qu + v2 * qv;
+                if (p.mode == SWA_FLAG_BRACKET) {
+                    m = fabs(d) > m ? fabs(d) : m;
+                } else {
+                    if (k == w.kh) dh0 = d;
+                    if (k == w.kh + 1) dh1 = d;
+                    if (k == w.kl) dl0 = d;
+                    if (k == w.kl + 1) dl1 = d;
+                    const double tk = p.tau[k];
+                    if (tk > w.lo && tk < w.hi) m = fabs(d) > m ? fabs(d) : m;
+                }
+            }
+            if (p.mode != SWA_FLAG_BRACKET) {
+                const A ah = (A)w.ah, al = (A)w.al;
+                const A vh = w.exact_h ? dh0 : ah * dh0 + (A(1) - ah) * dh1;
+                const A vl = w.exact_l ? dl0 : al * dl0 + (A(1) - al) * dl1;
+                m = fabs(vh) > m ? fabs(vh) : m;
+                m = fabs(vl) > m ? fabs(vl) : m;
+            }
+        }
+        f = (!w.empty && !dry && (double)m >= p.tol) ? 1 : 0;
+        p.flags[i] = (uint8_t)f;
+        if (p.maxip) p.maxip[i] = (float)m;
+    }
+    const int cnt = __syncthreads_count(f);
+    if (threadIdx.x == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
+}
+
+template <typename R, typename S>
+int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
+    const size_t n = (size_t)p.nx * p.ny;
+    cudaError_t e = cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return swadj_host::cuda_check(e, "flag count reset");
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
+    else flag_kernel<R, S, false><<<blocks, 256, 0, st>>>(p);
+    return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");
+}
+
+template int flag_launch<double, double>(const FlagParams<double, double> &, cudaStream_t);
+template int flag_launch<double, float>(const FlagParams<double, float> &, cudaStream_t);
+template int flag_launch<float, float>(const FlagParams<float, float> &, cudaStream_t);
+template int flag_launch<float, double>(const FlagParams<float, double> &, cudaStream_t);
+
+template <typename R>
+__global__ void gauge_kernel(GaugeParams<R> p) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.n) return;
+    const int cur = p.clk->cur;
+    const R *q0 = p.q[cur][0];
+    const double x = p.xy[2 * k], y = p.xy[2 * k + 1];
+    double fx = (x - p.x_lo) / p.dx - 0.5;
+    fx = fx < 0.0 ? 0.0 : (fx > (double)(p.nx - 1) ? (double)(p.nx - 1) : fx);
+    int i0 = (int)floor(fx);
+    if (i0 > p.nx - 2) i0 = p.nx - 2;
+    if (i0 < 0) i0 = 0;
+    double ax = fx - (double)i0;
+    const int i1 = p.nx > 1 ? i0 + 1 : i0;
+    if (p.nx == 1) ax = 0.0;
+    size_t st[4];
+    double wt[4];
+    if (!p.two_d) {
+        st[0] = i0; st[1] = i1; st[2] = 0; st[3] = 0;
+        wt[0] = 1.0 - ax; wt[1] = ax; wt[2] = 0.0; wt[3] = 0.0;
+    } else {
+        double fy = (y - p.y_lo) / p.dy - 0.5;
+        fy = fy < 0.0 ? 0.0 : (fy > (double)(p.ny - 1) ? (double)(p.ny - 1) : fy);
+        int j0 = (int)floor(fy);
+        if (j0 > p.ny - 2) j0 = p.ny - 2;
+        if (j0 < 0) j0 = 0;
+        double ay = fy - (double)j0;
+        const int j1 = p.ny > 1 ? j0 + 1 : j0;
+        if (p.ny == 1) ay = 0.0;
+        st[0] = (size_t)j0 * p.nx + i0; wt[0] = (1.0 - ax) * (1.0 - ay);
+        st[1] = (size_t)j0 * p.nx + i1; wt[1] = ax * (1.0 - ay);
+        st[2] = (size_t)j1 * p.nx + i0; wt[2] = (1.0 - ax) * ay;
+        st[3] = (size_t)j1 * p.nx + i1; wt[3] = ax * ay;
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        double eta;
+        if (sizeof(R) == 4) eta = (double)q0[st[c]];
+        else eta = (double)q0[st[c]] + (double)p.bath[st[c]];
+        v += wt[c] * eta;
+    }
+    p.out[k] = v;
+}
+
+template <typename R>
+int gauge_launch(const GaugeParams<R> &p, cudaStream_t st) {
+    if (p.n <= 0) return 0;
+    gauge_kernel<R><<<(p.n + 127) / 128, 128, 0, st>>>(p);
+    return swadj_host::cuda_check(cudaGetLastError(), "gauge_kernel");
+}
+
+template int gauge_launch<double>(const GaugeParams<double> &, cudaStream_t);
+template int gauge_launch<float>(const GaugeParams<float> &, cudaStream_t);
+
+}  // namespace swadj

@@ -1,0 +1,52 @@
+// flag.cuh -- flag-pass and gauge kernel parameters.
+#pragma once
+
+#include "swadj_internal.cuh"
+
+namespace swadj {
+
+template <typename R, typename S>
+struct FlagParams {
+    // forward grid (state read from the buffer the device clock points at)
+    int nx, ny, two_d;
+    double x_lo, y_lo, dx, dy;
+    R dry_tol;
+    const R *q[2][3];
+    const R *bath;           // B (double) or hbar (float)
+    const DevClock *clk;
+    // adjoint grid and snapshots
+    int anx, any, same_grid;
+    double ax_lo, ay_lo, adx, ady;
+    const uint8_t *awet;     // 1 where the adjoint cell is wet
+    const S *snaps;          // [K][ncomp][na]
+    size_t snap_stride;      // ncomp * na
+    size_t na;
+    int ncomp;
+    const double *tau;       // [K], strictly decreasing
+    int K;
+    double t_s, t_f, tol;
+    int mode;
+    uint8_t *flags;
+    float *maxip;
+    unsigned long long *count;
+};
+
+template <typename R, typename S>
+int flag_launch(const FlagParams<R, S> &p, cudaStream_t st);
+
+template <typename R>
+struct GaugeParams {
+    int nx, ny, two_d;
+    double x_lo, y_lo, dx, dy;
+    const R *q[2][3];
+    const R *bath;
+    const DevClock *clk;
+    int n;
+    const double *xy;
+    double *out;
+};
+
+template <typename R>
+int gauge_launch(const GaugeParams<R> &p, cudaStream_t st);
+
+}  // namespace swadj

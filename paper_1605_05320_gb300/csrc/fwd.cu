@@ -1,0 +1,354 @@
+// fwd.cu -- forward nonlinear shallow-water step (Eq. swe_1d / swe, Sec. 3, 5)
+// with a Roe-type f-wave Riemann solve per edge (Sec. 6), fused ghost fill and
+// fused CFL max-reduction (next time step computed on the device).
+//
+// Storage per precision:
+//   double (SWA_FP64): q = (h, hu, hv), bath = B.  eta = h + B per cell.
+//   float  (SWA_FP32): q = (eta, hu, hv), bath = hbar = -B (perturbation
+//                      form: metre-scale eta is stored directly instead of as
+//                      the small difference of ~4000 m depths).
+#include <stdio.h>
+
+#include "fwd.cuh"
+
+namespace swadj {
+
+__device__ int g_err_fwd;
+
+// Roe f-wave decomposition at one edge in the edge's frame (normal, tangential).
+// Inputs per side: depth h, normal/tangential momentum mn/mt, normal/tangential
+// velocity un/ut, sqrt(h), surface eta.  The momentum jump carries the
+// bathymetry source as g*hhat*(eta_R - eta_L): zero jump for the ocean at rest.
+// Output: uhat, chat and the strengths b1 (speed uhat-chat, vector
+// (1, s1, vhat)), b2 (speed uhat, (0,0,1)), b3 (speed uhat+chat, (1, s3, vhat)).
+template <typename R>
+__device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
+                                          R sqL, R etaL, R hR, R mnR, R mtR,
+                                          R unR, R utR, R sqR, R etaR, R &uhat,
+                                          R &chat, R &b1, R &b2, R &b3, R &vhat) {
+    R hhat = R(0.5) * (hL + hR);
+    R den = sqL + sqR;
+    uhat = (sqL * unL + sqR * unR) / den;
+    vhat = (sqL * utL + sqR * utR) / den;
+    chat = sqrt(g * hhat);
+    R s1 = uhat - chat, s3 = uhat + chat;
+    R df1 = mnR - mnL;
+    R df2 = (mnR * unR - mnL * unL) + g * hhat * (etaR - etaL);
+    R df3 = mnR * utR - mnL * utL;
+    R w = s3 - s1;
+    b1 = (s3 * df1 - df2) / w;
+    b3 = (df2 - s1 * df1) / w;
+    b2 = df3 - vhat * df1;
+}
+
+// Fluctuations amdq (to the left cell), apdq (to the right cell) and the
+// second-order correction flux F at edge e, from the waves at e and at its
+// left/right neighbour edges (indices into wave arrays W[6][stride]).
+template <typename R>
+struct Wave6 {
+    R uh, ch, b1, b2, b3, vh;
+};
+
+template <typename R>
+__device__ __forceinline__ void wave_vec(const Wave6<R> &w, int p, R Z[3], R &s) {
+    if (p == 0) {
+        s = w.uh - w.ch;
+        Z[0] = w.b1; Z[1] = w.b1 * s; Z[2] = w.b1 * w.vh;
+    } else if (p == 1) {
+        s = w.uh;
+        Z[0] = R(0); Z[1] = R(0); Z[2] = w.b2;
+    } else {
+        s = w.uh + w.ch;
+        Z[0] = w.b3; Z[1] = w.b3 * s; Z[2] = w.b3 * w.vh;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void edge_flux(const Wave6<R> &wm, const Wave6<R> &w,
+                                          const Wave6<R> &wp, R nu, int order,
+                                          R am[3], R ap[3], R F[3]) {
+#pragma unroll
+    for (int m = 0; m < 3; m++) { am[m] = R(0); ap[m] = R(0); F[m] = R(0); }
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+        R Z[3], s;
+        wave_vec(w, p, Z, s);
+#pragma unroll
+        for (int m = 0; m < 3; m++) {
+            if (s < R(0)) am[m] += Z[m];
+            else if (s > R(0)) ap[m] += Z[m];
+            else { am[m] += R(0.5) * Z[m]; ap[m] += R(0.5) * Z[m]; }
+        }
+        if (order >= 2) {
+            R Zu[3], su;
+            wave_vec(s > R(0) ? wm : wp, p, Zu, su);
+            R zz = Z[0] * Z[0] + Z[1] * Z[1] + Z[2] * Z[2];
+            R theta = R(0);
+            if (zz != R(0)) theta = (Zu[0] * Z[0] + Zu[1] * Z[1] + Zu[2] * Z[2]) / zz;
+            R coef = R(0.5) * sgnr(s) * (R(1) - nu * fabs(s)) * mc_phi(theta);
+#pragma unroll
+            for (int m = 0; m < 3; m++) F[m] += coef * Z[m];
+        }
+    }
+}
+
+template <typename R, bool PERT, bool TWO_D, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY)
+fwd_step_kernel(FwdParams<R> p) {
+    constexpr int HX = 2, HY = TWO_D ? 2 : 0;
+    constexpr int RX = TX + 2 * HX, RY = TY + 2 * HY;
+    constexpr int NT = TX * TY;
+    constexpr int NEX = RX - 1;
+    constexpr int NEY = TWO_D ? RY - 1 : 1;
+    constexpr int WYC = TWO_D ? TX : 1;
+    __shared__ R s_h[RY][RX], s_mu[RY][RX], s_mv[RY][RX], s_eta[RY][RX];
+    __shared__ R s_u[RY][RX], s_v[RY][RX], s_sq[RY][RX];
+    __shared__ Wave6<R> wx[TY][NEX];
+    __shared__ Wave6<R> wy[NEY][WYC];
+    __shared__ double red[32];
+    __shared__ int am_last;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + ty * TX;
+    volatile DevClock *clk = p.clk;
+    const double t = clk->t;
+    double dt = clk->dt_cfl;
+    if (p.t_end - t < dt) dt = p.t_end - t;
+    if (!(dt > 0.0)) return;  // clock already at t_end: no-op step
+    const int cur = clk->cur;
+
+    const R *q0 = p.q[cur][0], *q1 = p.q[cur][1], *q2 = p.q[cur][2];
+    R *o0 = p.q[cur ^ 1][0], *o1 = p.q[cur ^ 1][1], *o2 = p.q[cur ^ 1][2];
+    const int nx = p.nx, ny = p.ny;
+    const int i0 = blockIdx.x * TX - HX, j0 = blockIdx.y * TY - HY;
+
+    // 1) tile + halo (no corners) into shared memory, ghost cells fused
+    for (int r = tid; r < RX * RY; r += NT) {
+        const int ry = r / RX, rx = r - ry * RX;
+        const bool xin = rx >= HX && rx < HX + TX;
+        const bool yin = ry >= HY && ry < HY + TY;
+        if (!xin && !yin) continue;
+        bool fx, fy = false;
+        const int ci = ghost_index(i0 + rx, nx, p.bc.lo_x, p.bc.hi_x, &fx);
+        int cj = 0;
+        if (TWO_D) cj = ghost_index(j0 + ry, ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        const size_t o = (size_t)cj * nx + ci;
+        R a = q0[o], mu = q1[o], mv = TWO_D ? q2[o] : R(0), b = p.bath[o];
+        if (fx) mu = -mu;
+        if (fy) mv = -mv;
+        R h, eta;
+        if (PERT) { eta = a; h = a + b; }
+        else { h = a; eta = a + b; }
+        s_h[ry][rx] = h;
+        s_mu[ry][rx] = mu;
+        s_mv[ry][rx] = mv;
+        s_eta[ry][rx] = eta;
+        s_u[ry][rx] = mu / h;
+        s_v[ry][rx] = mv / h;
+        s_sq[ry][rx] = sqrt(h);
+    }
+    __syncthreads();
+
+    // 2) edge waves: x-edges of the TY core rows, y-edges of the TX core columns
+    for (int e = tid; e < TY * NEX; e += NT) {
+        const int row = e / NEX, k = e - row * NEX, ry = row + HY;
+        Wave6<R> w;
+        fwave_roe<R>(p.g, s_h[ry][k], s_mu[ry][k], s_mv[ry][k], s_u[ry][k],
+                     s_v[ry][k], s_sq[ry][k], s_eta[ry][k], s_h[ry][k + 1],
+                     s_mu[ry][k + 1], s_mv[ry][k + 1], s_u[ry][k + 1],
+                     s_v[ry][k + 1], s_sq[ry][k + 1], s_eta[ry][k + 1], w.uh,
+                     w.ch, w.b1, w.b2, w.b3, w.vh);
+        wx[row][k] = w;
+    }
+    if (TWO_D) {
+        for (int e = tid; e < NEY * TX; e += NT) {
+            const int k = e / TX, col = e - k * TX, rx = col + HX;
+            Wave6<R> w;
+            fwave_roe<R>(p.g, s_h[k][rx], s_mv[k][rx], s_mu[k][rx], s_v[k][rx],
+                         s_u[k][rx], s_sq[k][rx], s_eta[k][rx], s_h[k + 1][rx],
+                         s_mv[k + 1][rx], s_mu[k + 1][rx], s_v[k + 1][rx],
+                         s_u[k + 1][rx], s_sq[k + 1][rx], s_eta[k + 1][rx], w.uh,
+                         w.ch, w.b1, w.b2, w.b3, w.vh);
+            wy[k][col] = w;
+        }
+    }
+    __syncthreads();
+
+    // 3) cell update from the fluctuations and corrections of its edges
+    const int gi = blockIdx.x * TX + tx, gj = blockIdx.y * TY + ty;
+    const bool valid = gi < nx && gj < ny;
+    double s_cell = 0.0;
+    {
+        const R nux = R(dt) / p.dx;
+        R am0[3], ap0[3], F0[3], am1[3], ap1[3], F1[3];
+        edge_flux<R>(wx[ty][tx], wx[ty][tx + 1], wx[ty][tx + 2], nux, p.order, am0, ap0, F0);
+        edge_flux<R>(wx[ty][tx + 1], wx[ty][tx + 2], wx[ty][tx + 3], nux, p.order, am1, ap1, F1);
+        R dq[3];
+#pragma unroll
+        for (int m = 0; m < 3; m++) dq[m] = -nux * (ap0[m] + am1[m]) - nux * (F1[m] - F0[m]);
+        if (TWO_D) {
+            const R nuy = R(dt) / p.dy;
+            R bm0[3], bp0[3], G0[3], bm1[3], bp1[3], G1[3];
+            edge_flux<R>(wy[ty][tx], wy[ty + 1][tx], wy[ty + 2][tx], nuy, p.order, bm0, bp0, G0);
+            edge_flux<R>(wy[ty + 1][tx], wy[ty + 2][tx], wy[ty + 3][tx], nuy, p.order, bm1, bp1, G1);
+            R d[3];
+#pragma unroll
+            for (int m = 0; m < 3; m++) d[m] = -nuy * (bp0[m] + bm1[m]) - nuy * (G1[m] - G0[m]);
+            dq[0] += d[0];
+            dq[1] += d[2];
+            dq[2] += d[1];
+        }
+        const int cx = tx + HX, cy = ty + HY;
+        const R a0 = PERT ? s_eta[cy][cx] : s_h[cy][cx];
+        const R n0 = a0 + dq[0];
+        const R n1 = s_mu[cy][cx] + dq[1];
+        const R n2 = s_mv[cy][cx] + dq[2];
+        if (valid) {
+            const size_t o = (size_t)gj * nx + gi;
+            const R hn = PERT ? n0 + p.bath[o] : n0;
+            o0[o] = n0;
+            o1[o] = n1;
+            if (TWO_D) o2[o] = n2;
+            if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(&g_err_fwd, ERR_UNSTABLE);
+            // CFL number of the new state (per-cell term in the compute type)
+            const R c = sqrt(p.g * hn);
+            R s = (fabs(n1 / hn) + c) / p.dx;
+            if (TWO_D) s += (fabs(n2 / hn) + c) / p.dy;
+            s_cell = (double)s;
+            if (!(s_cell >= 0.0)) s_cell = 0.0;
+        }
+    }
+
+    // 4) block max -> partial, last block reduces and advances the clock
+    const double bm = block_max<NT>(s_cell, red);
+    const int bid = blockIdx.x + blockIdx.y * gridDim.x;
+    if (tid == 0) {
+        p.partial[bid] = bm;
+        __threadfence();
+        const unsigned int tk = atomicAdd((unsigned int *)&p.clk->ticket, 1u);
+        am_last = (tk == (unsigned int)(p.nblocks - 1));
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        double m = 0.0;
+        for (int k = tid; k < p.nblocks; k += NT) {
+            const double v = __ldcg(p.partial + k);
+            m = v > m ? v : m;
+        }
+        m = block_max<NT>(m, red);
+        if (tid == 0) {
+            clk->t = t + dt;
+            clk->smax = m;
+            clk->dt_cfl = p.cfl / m;
+            clk->cur = cur ^ 1;
+            clk->nsteps = clk->nsteps + 1;
+            clk->ticket = 0u;
+        }
+    }
+}
+
+// Initial CFL reduction over the current state (set_state), same per-cell rule.
+template <typename R, bool PERT>
+__global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double t0) {
+    __shared__ double red[32];
+    __shared__ int am_last;
+    const int tid = threadIdx.x;
+    const size_t n = (size_t)p.nx * p.ny;
+    const R *q0 = p.q[0][0], *q1 = p.q[0][1], *q2 = p.q[0][2];
+    double mx = 0.0;
+    for (size_t k = (size_t)blockIdx.x * 256 + tid; k < n; k += (size_t)gridDim.x * 256) {
+        const R h = PERT ? q0[k] + p.bath[k] : q0[k];
+        const R c = sqrt(p.g * h);
+        R s = (fabs(q1[k] / h) + c) / p.dx;
+        if (p.two_d) s += (fabs(q2[k] / h) + c) / p.dy;
+        double sd = (double)s;
+        if (!(h > R(0))) atomicOr(&g_err_fwd, ERR_UNSTABLE);
+        mx = sd > mx ? sd : mx;
+    }
+    const double bm = block_max<256>(mx, red);
+    if (tid == 0) {
+        p.partial[blockIdx.x] = bm;
+        __threadfence();
+        const unsigned int tk = atomicAdd(&p.clk->ticket, 1u);
+        am_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        double m = 0.0;
+        for (int k = tid; k < (int)gridDim.x; k += 256) {
+            const double v = __ldcg(p.partial + k);
+            m = v > m ? v : m;
+        }
+        m = block_max<256>(m, red);
+        if (tid == 0) {
+            volatile DevClock *clk = p.clk;
+            clk->t = t0;
+            clk->smax = m;
+            clk->dt_cfl = p.cfl / m;
+            clk->cur = 0;
+            clk->nsteps = 0;
+            clk->ticket = 0u;
+        }
+    }
+}
+
+// ---- host launchers ----
+
+template <typename R, bool PERT, bool TWO_D, int TX, int TY>
+static int launch_step(FwdParams<R> p, cudaStream_t st) {
+    dim3 grid((p.nx + TX - 1) / TX, TWO_D ? (p.ny + TY - 1) / TY : 1);
+    p.nblocks = (int)(grid.x * grid.y);
+    fwd_step_kernel<R, PERT, TWO_D, TX, TY><<<grid, dim3(TX, TY), 0, st>>>(p);
+    return swadj_host::cuda_check(cudaGetLastError(), "fwd_step_kernel");
+}
+
+template <typename R>
+int fwd_step_blocks(const FwdParams<R> &p) {
+    if (p.two_d) {
+        if (sizeof(R) == 8) return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
+        return ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
+    }
+    return (p.nx + 127) / 128;
+}
+
+template <>
+int fwd_launch_step<double>(const FwdParams<double> &p, cudaStream_t st) {
+    if (p.two_d) return launch_step<double, false, true, 32, 4>(p, st);
+    return launch_step<double, false, false, 128, 1>(p, st);
+}
+
+template <>
+int fwd_launch_step<float>(const FwdParams<float> &p, cudaStream_t st) {
+    if (p.two_d) return launch_step<float, true, true, 32, 8>(p, st);
+    return launch_step<float, true, false, 128, 1>(p, st);
+}
+
+template <typename R>
+int fwd_launch_clock_init(const FwdParams<R> &p, double t0, cudaStream_t st) {
+    constexpr bool PERT = sizeof(R) == 4;
+    const size_t n = (size_t)p.nx * p.ny;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > kInitBlocks) blocks = kInitBlocks;
+    clock_init_kernel<R, PERT><<<blocks, 256, 0, st>>>(p, t0);
+    return swadj_host::cuda_check(cudaGetLastError(), "clock_init_kernel");
+}
+
+template int fwd_launch_clock_init<double>(const FwdParams<double> &, double, cudaStream_t);
+template int fwd_launch_clock_init<float>(const FwdParams<float> &, double, cudaStream_t);
+template int fwd_step_blocks<double>(const FwdParams<double> &);
+template int fwd_step_blocks<float>(const FwdParams<float> &);
+
+int fwd_read_clear_err(cudaStream_t st, int *out) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_err_fwd, sizeof(int), 0,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyToSymbolAsync(g_err_fwd, &zero, sizeof(int), 0,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return swadj_host::cuda_check(e, "read forward error word");
+}
+
+}  // namespace swadj

@@ -1,0 +1,92 @@
+// swadj_internal.cuh -- device-side definitions shared by the libswadj kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swadj.h"
+
+namespace swadj {
+
+// Device-resident clock of a forward grid.  Written only by the last block of
+// each step kernel (after every block has read it), read at the start of the
+// next one: time, step and buffer parity never leave the device, so step
+// sequences can be captured in a CUDA graph.
+struct DevClock {
+    double t;           // current time t_n
+    double dt_cfl;      // cfl / s_max(Q^n)
+    long long nsteps;   // steps taken
+    int cur;            // buffer index holding Q^n
+    unsigned int ticket;  // last-block-done counter, 0 between launches
+    double smax;        // s_max(Q^n)
+};
+
+// Bit set in the device error word.
+enum : int { ERR_UNSTABLE = 1 };
+
+struct BcSpec {
+    int lo_x, hi_x, lo_y, hi_y;
+};
+
+// Map a possibly out-of-range index onto the grid for ghost cells: copy the
+// nearest cell (extrapolation) or mirror it (wall, with *flip set so the
+// normal momentum is negated).  The result is clamped into [0, n).
+__device__ __forceinline__ int ghost_index(int g, int n, int bc_lo, int bc_hi,
+                                           bool *flip) {
+    *flip = false;
+    if (g < 0) {
+        if (bc_lo == SWA_BC_WALL) { g = -g - 1; *flip = true; }
+        else g = 0;
+    } else if (g >= n) {
+        if (bc_hi == SWA_BC_WALL) { g = 2 * n - 1 - g; *flip = true; }
+        else g = n - 1;
+    }
+    g = g < 0 ? 0 : (g >= n ? n - 1 : g);
+    return g;
+}
+
+// MC limiter: max(0, min((1+theta)/2, 2, 2 theta)).
+template <typename R>
+__device__ __forceinline__ R mc_phi(R theta) {
+    R a = R(0.5) * (R(1) + theta);
+    R m = a < R(2) ? a : R(2);
+    R c = R(2) * theta;
+    m = c < m ? c : m;
+    return m > R(0) ? m : R(0);
+}
+
+template <typename R>
+__device__ __forceinline__ R sgnr(R s) {
+    return s > R(0) ? R(1) : (s < R(0) ? R(-1) : R(0));
+}
+
+// Block-wide max of a non-negative double, result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = v > w ? v : w;
+    }
+    const int lane = threadIdx.x & 31;
+    const int wid = (threadIdx.x + threadIdx.y * blockDim.x) >> 5;
+    if (NT > 32) {
+        if (lane == 0) red[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            v = (lane < NT / 32) ? red[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                double w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = v > w ? v : w;
+            }
+        }
+    }
+    return v;
+}
+
+}  // namespace swadj
+
+// Host-side helpers shared by the translation units (defined in api.cu).
+namespace swadj_host {
+int set_error(int code, const char *fmt, ...);
+int cuda_check(cudaError_t e, const char *what);
+}  // namespace swadj_host

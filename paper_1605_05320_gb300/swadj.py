@@ -1,0 +1,401 @@
+"""Thin ctypes binding of libswadj.so (see include/swadj.h).
+
+Functions here carry the C names and only marshal arguments: every step of
+the method runs in the CUDA kernels of the library.  Device memory comes
+from PyTorch (CUDA tensors used as workspaces and buffers); streams are
+passed as raw cudaStream_t handles.  Importing this module on a machine
+without the built library raises; there is no CPU fallback.
+
+The small classes at the bottom (Grid, Adjoint, SnapStore) only allocate the
+workspaces with torch and keep them alive next to the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswadj.so")
+
+SWA_OK, SWA_EINVAL, SWA_ENOMEM, SWA_ECUDA, SWA_ESTATE, SWA_EUNSTABLE, SWA_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
+SWA_FP64, SWA_FP32 = 0, 1
+SWA_BC_EXTRAP, SWA_BC_WALL = 0, 1
+SWA_FLAG_INTERP, SWA_FLAG_BRACKET = 0, 1
+SWA_HOST, SWA_DEVICE = 0, 1
+
+# Every symbol declared in include/swadj.h.
+EXPORTS = [
+    "swa_version", "swa_last_error", "swa_sync_status",
+    "swa_grid_workspace_bytes", "swa_create_grid", "swa_destroy_grid",
+    "swa_set_state", "swa_get_state", "swa_step_forward", "swa_get_time",
+    "swa_grid_arrays",
+    "swa_adjoint_workspace_bytes", "swa_create_adjoint", "swa_destroy_adjoint",
+    "swa_adjoint_info", "swa_step_adjoint", "swa_get_adjoint_state",
+    "swa_set_adjoint_state", "swa_snapstore_clear",
+    "swa_snapstore_workspace_bytes", "swa_create_snapstore",
+    "swa_destroy_snapstore", "swa_store_snapshot", "swa_run_adjoint",
+    "swa_snapstore_info",
+    "swa_flag_cells", "swa_gauge_sample",
+]
+
+
+class SwaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swadj error {code}: {msg}")
+        self.code = code
+
+
+class swa_grid_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x_lo", ctypes.c_double), ("y_lo", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("precision", ctypes.c_int), ("order", ctypes.c_int),
+                ("bc", ctypes.c_int * 4),
+                ("g", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("dry_tol", ctypes.c_double)]
+
+
+def make_desc(ndim, nx, ny, x_lo, y_lo, dx, dy, precision=SWA_FP64, order=2,
+              bc=(SWA_BC_EXTRAP,) * 4, g=9.81, cfl=0.75, dry_tol=1e-3):
+    d = swa_grid_desc()
+    d.ndim, d.nx, d.ny = int(ndim), int(nx), int(ny)
+    d.x_lo, d.y_lo, d.dx, d.dy = float(x_lo), float(y_lo), float(dx), float(dy)
+    d.precision, d.order = int(precision), int(order)
+    for k in range(4):
+        d.bc[k] = int(bc[k])
+    d.g, d.cfl, d.dry_tol = float(g), float(cfl), float(dry_tol)
+    return d
+
+
+_lib = None
+_V = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_P = ctypes.POINTER
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (built beforehand by build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libswadj.so not built at {path}; run "
+                          "paper_1605_05320_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    D = _P(swa_grid_desc)
+    sig = {
+        "swa_version": ([], ctypes.c_char_p),
+        "swa_last_error": ([], ctypes.c_char_p),
+        "swa_sync_status": ([_V], _I),
+        "swa_grid_workspace_bytes": ([D], _SZ),
+        "swa_create_grid": ([D, _V, _V, _SZ, _V, _P(_V)], _I),
+        "swa_destroy_grid": ([_V], _I),
+        "swa_set_state": ([_V, _V, _V, _V, _D, _I, _V], _I),
+        "swa_get_state": ([_V, _V, _V, _V, _V, _I, _V], _I),
+        "swa_step_forward": ([_V, _I, _D, _V], _I),
+        "swa_get_time": ([_V, _P(_D), _P(_D), _P(ctypes.c_longlong), _V], _I),
+        "swa_grid_arrays": ([_V, _P(_V), _P(_V), _P(_V), _P(_V), _V], _I),
+        "swa_adjoint_workspace_bytes": ([D], _SZ),
+        "swa_create_adjoint": ([D, _V, _V, _D, _V, _SZ, _V, _P(_V)], _I),
+        "swa_destroy_adjoint": ([_V], _I),
+        "swa_adjoint_info": ([_V, _P(ctypes.c_longlong), _P(_D), _P(ctypes.c_longlong)], _I),
+        "swa_step_adjoint": ([_V, _I, _V], _I),
+        "swa_get_adjoint_state": ([_V, _V, _I, _V], _I),
+        "swa_set_adjoint_state": ([_V, _V, _I, _V], _I),
+        "swa_snapstore_clear": ([_V], _I),
+        "swa_snapstore_workspace_bytes": ([D, _I, _I], _SZ),
+        "swa_create_snapstore": ([_V, _I, _I, _V, _SZ, _P(_V)], _I),
+        "swa_destroy_snapstore": ([_V], _I),
+        "swa_store_snapshot": ([_V, _V, _V], _I),
+        "swa_run_adjoint": ([_V, _V, _I, _V], _I),
+        "swa_snapstore_info": ([_V, _P(_I), _V, _I], _I),
+        "swa_flag_cells": ([_V, _V, _D, _D, _D, _I, _V, _V, _V, _V], _I),
+        "swa_gauge_sample": ([_V, _I, _V, _V, _V], _I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _chk(rc):
+    if rc != SWA_OK:
+        raise SwaError(rc, load().swa_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------ same-name calls
+def swa_version():
+    return load().swa_version().decode()
+
+
+def swa_last_error():
+    return load().swa_last_error().decode()
+
+
+def swa_sync_status(stream=None):
+    return load().swa_sync_status(_stream(stream))
+
+
+def swa_grid_workspace_bytes(desc):
+    return int(load().swa_grid_workspace_bytes(ctypes.byref(desc)))
+
+
+def swa_create_grid(desc, bathy_host, ws, ws_bytes, stream=None):
+    out = _V()
+    _chk(load().swa_create_grid(ctypes.byref(desc), _ptr(bathy_host), _ptr(ws),
+                                ws_bytes, _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def swa_destroy_grid(h):
+    return _chk(load().swa_destroy_grid(h))
+
+
+def swa_set_state(h, eta, hu, hv, t, where, stream=None):
+    return _chk(load().swa_set_state(h, _ptr(eta), _ptr(hu), _ptr(hv), float(t),
+                                     where, _stream(stream)))
+
+
+def swa_get_state(h, hh, hu, hv, eta, where, stream=None):
+    return _chk(load().swa_get_state(h, _ptr(hh), _ptr(hu), _ptr(hv), _ptr(eta),
+                                     where, _stream(stream)))
+
+
+def swa_step_forward(h, max_steps, t_end, stream=None):
+    return _chk(load().swa_step_forward(h, int(max_steps), float(t_end), _stream(stream)))
+
+
+def swa_get_time(h, stream=None):
+    t, dt, n = _D(), _D(), ctypes.c_longlong()
+    _chk(load().swa_get_time(h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(n),
+                             _stream(stream)))
+    return t.value, dt.value, n.value
+
+
+def swa_grid_arrays(h, stream=None):
+    a = [_V() for _ in range(4)]
+    _chk(load().swa_grid_arrays(h, *[ctypes.byref(x) for x in a], _stream(stream)))
+    return [x.value for x in a]
+
+
+def swa_adjoint_workspace_bytes(desc):
+    return int(load().swa_adjoint_workspace_bytes(ctypes.byref(desc)))
+
+
+def swa_create_adjoint(desc, bathy_host, phi_host, t_f, ws, ws_bytes, stream=None):
+    out = _V()
+    _chk(load().swa_create_adjoint(ctypes.byref(desc), _ptr(bathy_host), _ptr(phi_host),
+                                   float(t_f), _ptr(ws), ws_bytes, _stream(stream),
+                                   ctypes.byref(out)))
+    return out.value
+
+
+def swa_destroy_adjoint(h):
+    return _chk(load().swa_destroy_adjoint(h))
+
+
+def swa_adjoint_info(h):
+    n, dt, s = ctypes.c_longlong(), _D(), ctypes.c_longlong()
+    _chk(load().swa_adjoint_info(h, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(s)))
+    return n.value, dt.value, s.value
+
+
+def swa_step_adjoint(h, nsteps, stream=None):
+    return _chk(load().swa_step_adjoint(h, int(nsteps), _stream(stream)))
+
+
+def swa_get_adjoint_state(h, q, where, stream=None):
+    return _chk(load().swa_get_adjoint_state(h, _ptr(q), where, _stream(stream)))
+
+
+def swa_set_adjoint_state(h, phi, where, stream=None):
+    return _chk(load().swa_set_adjoint_state(h, _ptr(phi), where, _stream(stream)))
+
+
+def swa_snapstore_clear(h):
+    return _chk(load().swa_snapstore_clear(h))
+
+
+def swa_snapstore_workspace_bytes(adj_desc, max_snaps, precision):
+    return int(load().swa_snapstore_workspace_bytes(ctypes.byref(adj_desc), int(max_snaps),
+                                                    int(precision)))
+
+
+def swa_create_snapstore(adj, max_snaps, precision, ws, ws_bytes):
+    out = _V()
+    _chk(load().swa_create_snapstore(adj, int(max_snaps), int(precision), _ptr(ws),
+                                     ws_bytes, ctypes.byref(out)))
+    return out.value
+
+
+def swa_destroy_snapstore(h):
+    return _chk(load().swa_destroy_snapstore(h))
+
+
+def swa_store_snapshot(adj, store, stream=None):
+    return _chk(load().swa_store_snapshot(adj, store, _stream(stream)))
+
+
+def swa_run_adjoint(adj, store, every, stream=None):
+    return _chk(load().swa_run_adjoint(adj, store, int(every), _stream(stream)))
+
+
+def swa_snapstore_info(store, cap=0):
+    cnt = _I()
+    buf = np.zeros(max(cap, 1))
+    _chk(load().swa_snapstore_info(store, ctypes.byref(cnt), buf.ctypes.data if cap else None,
+                                   int(cap)))
+    return cnt.value, buf[:min(cap, cnt.value)].copy()
+
+
+def swa_flag_cells(grid, store, t_s, t_f, tol, mode, flags_dev, maxip_dev, count_dev,
+                   stream=None):
+    return _chk(load().swa_flag_cells(grid, store, float(t_s), float(t_f), float(tol),
+                                      int(mode), _ptr(flags_dev), _ptr(maxip_dev),
+                                      _ptr(count_dev), _stream(stream)))
+
+
+def swa_gauge_sample(grid, n, xy_dev, eta_dev, stream=None):
+    return _chk(load().swa_gauge_sample(grid, int(n), _ptr(xy_dev), _ptr(eta_dev),
+                                        _stream(stream)))
+
+
+# ------------------------------------------------- workspace-owning helpers
+def _workspace(nbytes, device):
+    import torch
+    return torch.empty(int(nbytes), dtype=torch.uint8, device=device)
+
+
+class Grid:
+    """A forward grid whose workspace is a torch CUDA tensor."""
+
+    def __init__(self, desc, B, device="cuda", stream=None):
+        import torch
+        self.desc = desc
+        self.n = desc.nx * desc.ny
+        self.nbytes = swa_grid_workspace_bytes(desc)
+        if self.nbytes == 0:
+            raise SwaError(SWA_EINVAL, swa_last_error())
+        self.ws = _workspace(self.nbytes, device)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        self.h = swa_create_grid(desc, B, self.ws, self.nbytes, stream)
+        self.device = torch.device(device)
+
+    def set_state(self, eta, hu, hv=None, t=0.0, stream=None):
+        if isinstance(eta, np.ndarray):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+                    for a in (eta, hu, hv)]
+            swa_set_state(self.h, arrs[0], arrs[1], arrs[2], t, SWA_HOST, stream)
+        else:
+            swa_set_state(self.h, eta, hu, hv, t, SWA_DEVICE, stream)
+
+    def get_state(self, stream=None):
+        out = [np.zeros(self.n) for _ in range(4)]
+        swa_get_state(self.h, *out, SWA_HOST, stream)
+        return dict(h=out[0], hu=out[1], hv=out[2], eta=out[3])
+
+    def step(self, max_steps, t_end, stream=None):
+        swa_step_forward(self.h, max_steps, t_end, stream)
+
+    def time(self, stream=None):
+        return swa_get_time(self.h, stream)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                swa_destroy_grid(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Adjoint:
+    def __init__(self, desc, B, phi, t_f, device="cuda", stream=None):
+        self.desc = desc
+        self.n = desc.nx * desc.ny
+        self.nc = desc.ndim + 1
+        self.nbytes = swa_adjoint_workspace_bytes(desc)
+        if self.nbytes == 0:
+            raise SwaError(SWA_EINVAL, swa_last_error())
+        self.ws = _workspace(self.nbytes, device)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(self.nc, self.n))
+        self.h = swa_create_adjoint(desc, B, phi, t_f, self.ws, self.nbytes, stream)
+        self.t_f = t_f
+
+    def info(self):
+        return swa_adjoint_info(self.h)
+
+    def step(self, nsteps, stream=None):
+        swa_step_adjoint(self.h, nsteps, stream)
+
+    def get_state(self, stream=None):
+        q = np.zeros((self.nc, self.n))
+        swa_get_adjoint_state(self.h, q, SWA_HOST, stream)
+        return q
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                swa_destroy_adjoint(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class SnapStore:
+    def __init__(self, adj: Adjoint, max_snaps, precision, device="cuda"):
+        self.adj = adj
+        self.nbytes = swa_snapstore_workspace_bytes(adj.desc, max_snaps, precision)
+        if self.nbytes == 0:
+            raise SwaError(SWA_EINVAL, swa_last_error())
+        self.ws = _workspace(self.nbytes, device)
+        self.h = swa_create_snapstore(adj.h, max_snaps, precision, self.ws, self.nbytes)
+        self.max_snaps = max_snaps
+
+    def run_adjoint(self, every, stream=None):
+        swa_run_adjoint(self.adj.h, self.h, every, stream)
+
+    def store(self, stream=None):
+        swa_store_snapshot(self.adj.h, self.h, stream)
+
+    def info(self):
+        return swa_snapstore_info(self.h, self.max_snaps)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                swa_destroy_snapstore(self.h)
+                self.h = None
+        except Exception:
+            pass

@@ -1,0 +1,85 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/swadj.h declares; host-only logic (workspace sizing, descriptor
+checks) works without a GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1605_05320_gb300 import build as B
+from paper_1605_05320_gb300 import swadj as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "swadj.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(swa_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(S.EXPORTS) == decl
+
+
+def test_library_targets_sm_103a():
+    B.build()
+    assert "arch=compute_103a,code=sm_103a" in " ".join(B.NVCC_FLAGS)
+    data = open(B.LIB, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_workspace_sizes_and_descriptor_checks(lib):
+    d = S.make_desc(2, 2048, 2048, 0.0, 0.0, 1000.0, 1000.0, precision=S.SWA_FP32)
+    n = 2048 * 2048
+    ws = S.swa_grid_workspace_bytes(d)
+    # 2 x 3 state arrays + hbar (float) + FP64 staging + clock + partials
+    assert 7 * 4 * n + 8 * n <= ws <= 7 * 4 * n + 8 * n + 1 << 20
+    d64 = S.make_desc(2, 2048, 2048, 0.0, 0.0, 1000.0, 1000.0, precision=S.SWA_FP64)
+    assert S.swa_grid_workspace_bytes(d64) >= 7 * 8 * n + 8 * n
+    a = S.swa_adjoint_workspace_bytes(d)
+    assert a >= 7 * 4 * n + 8 * n
+    s = S.swa_snapstore_workspace_bytes(d, 101, S.SWA_FP32)
+    assert s >= 101 * 3 * 4 * n + n
+    bad = S.make_desc(2, 2048, 2048, 0.0, 0.0, 1000.0, 1000.0, order=3)
+    assert S.swa_grid_workspace_bytes(bad) == 0
+    assert "order" in S.swa_last_error()
+    bad1d = S.make_desc(1, 100, 2, 0.0, 0.0, 1.0, 1.0)
+    assert S.swa_grid_workspace_bytes(bad1d) == 0
+    assert "ny" in S.swa_last_error()
+
+
+def test_create_rejects_small_or_misaligned_workspace(lib):
+    import numpy as np
+    d = S.make_desc(2, 64, 64, 0.0, 0.0, 1000.0, 1000.0)
+    B0 = np.full(64 * 64, -100.0)
+    need = S.swa_grid_workspace_bytes(d)
+    out = ctypes.c_void_p()
+    rc = lib.swa_create_grid(ctypes.byref(d), B0.ctypes.data, ctypes.c_void_p(256),
+                             need - 1, None, ctypes.byref(out))
+    assert rc == S.SWA_ENOMEM
+    rc = lib.swa_create_grid(ctypes.byref(d), B0.ctypes.data, ctypes.c_void_p(257),
+                             need, None, ctypes.byref(out))
+    assert rc == S.SWA_EINVAL and "aligned" in S.swa_last_error()
+
+
+def test_product_path_does_not_touch_oracle():
+    """The library and its binding never import or link the oracle."""
+    pkg = os.path.join(ROOT, "paper_1605_05320_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "swe_oracle" not in txt and "liboracle" not in txt, f

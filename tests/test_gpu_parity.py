@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (error metric: per field max|gpu - ref| / max|ref|):
+  * FP64 forward: <= 1e-12 in h, hu, hv after 1000 steps; identical step
+    count and time (the CFL reduction is exact)
+  * FP64 adjoint: <= 1e-12 per component for every snapshot; identical tau
+  * FP64 flags: identical except cells with |m - tol| <= 1e-6 tol; m to 1e-12
+  * FP32 perturbation form: eta within 1e-5 m, momenta within 1e-5 of their
+    maximum, after 200 steps (decimetre waves, 4000 m depth)
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1605_05320_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1605_05320_gb300 import build
+    build.build()
+    from paper_1605_05320_gb300 import swadj
+    swadj.load()
+    assert torch.cuda.is_available()
+    return swadj
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+def bath_seen(B, precision_fp32):
+    """The bathymetry the GPU path works with: the FP32 path stores
+    hbar = float(-B), so the oracle is given B = -hbar to compare like with
+    like (eta is then exactly the same number on both sides)."""
+    if not precision_fp32:
+        return B
+    return -(np.float32(-B).astype(np.float64))
+
+
+def desc_of(S, spec, precision, order=2, bc=(0, 0, 0, 0)):
+    return S.make_desc(spec.ndim, spec.nx, spec.ny, spec.x_lo, spec.y_lo, spec.dx,
+                       spec.dy, precision=precision, order=order, bc=bc)
+
+
+def run_gpu_forward(S, sc, precision, order, bc, nsteps, t_end=1e12):
+    g = S.Grid(desc_of(S, sc.grid, precision, order, bc), sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0 if sc.grid.ndim == 2 else None, 0.0)
+    g.step(nsteps, t_end)
+    st = g.get_state()
+    t, dt, n = g.time()
+    assert S.swa_sync_status() == 0
+    return st, t, n
+
+
+def run_oracle_forward(sc, order, bc, nsteps, t_end=1e12, B=None):
+    og = O.Grid.from_spec(sc.grid, order=order, bc=bc)
+    B = sc.B if B is None else B
+    h0 = sc.eta0 - B
+    hv = sc.hv0 if sc.grid.ndim == 2 else None
+    return O.fwd_run(og, h0, sc.hu0, hv, B, nsteps, t_end)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (1, 0, 0, 1)])
+def test_fp64_forward_2d_1000_steps(S, order, bc):
+    # 150 x 97: several 32 x 4 tiles with ragged edges in both directions
+    sc = synth.small_2d(150, 97, seed=3)
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, order, bc, 1000)
+    h, hu, hv, t_ref, n_ref = run_oracle_forward(sc, order, bc, 1000)
+    assert n == n_ref == 1000
+    assert abs(t - t_ref) <= 1e-12 * t_ref
+    assert rel(st["h"], h) <= 1e-12
+    assert rel(st["hu"], hu) <= 1e-12
+    assert rel(st["hv"], hv) <= 1e-12
+
+
+def test_fp64_forward_1d_config1(S):
+    sc = synth.config1()
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, 2, (0, 0, 0, 0), 1000)
+    h, hu, _, t_ref, n_ref = run_oracle_forward(sc, 2, (0, 0, 0, 0), 1000)
+    assert n == n_ref
+    assert abs(t - t_ref) <= 1e-12 * t_ref
+    assert rel(st["h"], h) <= 1e-12 and rel(st["hu"], hu) <= 1e-12
+
+
+def test_forward_stops_at_t_end(S):
+    sc = synth.small_2d(40, 33, seed=4)
+    t_end = 37.5
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, 2, (0, 0, 0, 0), 500, t_end)
+    h, hu, hv, t_ref, n_ref = run_oracle_forward(sc, 2, (0, 0, 0, 0), 500, t_end)
+    assert t == t_end and t_ref == t_end and n == n_ref < 500
+    assert rel(st["h"], h) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_lake_at_rest_bit_exact(S, precision):
+    sc = synth.small_2d(70, 45, seed=5)
+    p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
+    g = S.Grid(desc_of(S, sc.grid, p, 2, (1, 0, 1, 0)), sc.B)
+    z = np.zeros(sc.grid.n)
+    g.set_state(z, z, z, 0.0)
+    g.step(300, 1e12)
+    st = g.get_state()
+    assert np.all(st["eta"] == 0.0) and np.all(st["hu"] == 0) and np.all(st["hv"] == 0)
+    assert g.time()[2] == 300
+
+
+def test_fp32_perturbation_forward_vs_fp64_oracle(S):
+    sc = synth.small_2d(130, 90, seed=6, amp=0.5)
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP32, 2, (0, 0, 0, 0), 200)
+    Bf = bath_seen(sc.B, True)
+    h, hu, hv, t_ref, n_ref = run_oracle_forward(sc, 2, (0, 0, 0, 0), 200, B=Bf)
+    assert n == n_ref
+    assert abs(t - t_ref) <= 1e-5 * t_ref
+    eta_ref = h + Bf
+    assert np.abs(st["eta"] - eta_ref).max() <= 1e-5
+    assert rel(st["hu"], hu) <= 1e-5 and rel(st["hv"], hv) <= 1e-5
+
+
+def _adjoint_pair(S, sc, precision, every, bc=(0, 0, 0, 0), order=2):
+    ad = desc_of(S, sc.adj_grid, precision, order, bc)
+    adj = S.Adjoint(ad, sc.B_adj, sc.phi, sc.t_f)
+    N, dt, _ = adj.info()
+    store = S.SnapStore(adj, N // every + 3, precision)
+    store.run_adjoint(every)
+    K, tau = store.info()
+    og = O.Grid.from_spec(sc.adj_grid, order=order, bc=bc)
+    hbar = np.maximum(-sc.B_adj, 0.0)
+    snaps, tau_ref, N_ref, dt_ref = O.adj_run(og, hbar, sc.phi, sc.t_f, every)
+    return adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref)
+
+
+def _read_snaps(S, store, precision, nc, n):
+    K = store.info()[0]
+    dt = np.float64 if precision == S.SWA_FP64 else np.float32
+    esz = 8 if precision == S.SWA_FP64 else 4
+    raw = store.ws[: K * nc * n * esz].cpu().numpy().view(dt)
+    return raw.reshape(K, nc, n).astype(np.float64)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_fp64_adjoint_snapshots(S, bc):
+    sc = synth.small_2d(96, 70, seed=7)
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+        _adjoint_pair(S, sc, S.SWA_FP64, 5, bc)
+    assert N == N_ref and dt == dt_ref
+    assert K == len(tau_ref) and np.array_equal(tau, tau_ref)
+    got = _read_snaps(S, store, S.SWA_FP64, 3, sc.adj_grid.n)
+    for k in range(K):
+        for c in range(3):
+            ref = snaps[k, c]
+            if np.abs(ref).max() == 0:
+                assert np.all(got[k, c] == 0)
+            else:
+                assert rel(got[k, c], ref) <= 1e-12, (k, c)
+
+
+def test_fp64_adjoint_1d_with_dry_cells(S):
+    sc = synth.config1(nx=600)
+    B = sc.B.copy()
+    B[550:] = 5.0   # land beyond x = 333 km: wet/dry wall
+    sc.B_adj = B
+    sc.phi[:, 550:] = 0.0
+    sc.t_f = 1800.0
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+        _adjoint_pair(S, sc, S.SWA_FP64, 10)
+    assert N == N_ref and np.array_equal(tau, tau_ref)
+    got = _read_snaps(S, store, S.SWA_FP64, 2, sc.adj_grid.n)
+    assert rel(got, snaps) <= 1e-12
+
+
+def _flag_compare(S, sc, precision, mode, t_s, nsteps, every=5):
+    """Both sides compute everything from the seeded inputs: adjoint with
+    snapshots, nsteps forward steps, then the flag pass."""
+    fp32 = precision == S.SWA_FP32
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, _, _) = \
+        _adjoint_pair(S, sc, precision, every)
+    g = S.Grid(desc_of(S, sc.grid, precision), sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    g.step(nsteps, sc.t_f)
+    n = sc.grid.n
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    m = torch.zeros(n, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    S.swa_flag_cells(g.h, store.h, t_s, sc.t_f, sc.tol, mode, flags, m, cnt)
+    torch.cuda.synchronize()
+    # oracle side
+    Bs = bath_seen(sc.B, fp32)
+    h, hu, hv, t_ref, _ = run_oracle_forward(sc, 2, (0, 0, 0, 0), nsteps, sc.t_f, B=Bs)
+    og = O.Grid.from_spec(sc.grid)
+    ag = O.Grid.from_spec(sc.adj_grid)
+    f_ref, m_ref, c_ref = O.flag(og, h, hu, hv, Bs, t_ref, ag,
+                                 np.maximum(-sc.B_adj, 0), snaps, tau_ref, t_s,
+                                 sc.t_f, sc.tol, mode)
+    return flags.cpu().numpy(), m.cpu().numpy(), int(cnt.item()), f_ref, m_ref, c_ref
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("t_s_frac", [0.32, 1.0])
+def test_fp64_flags_match_oracle(S, mode, t_s_frac):
+    sc = synth.small_2d(88, 61, seed=8)
+    f, m, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP64, mode,
+                                                 t_s_frac * sc.t_f, 150)
+    near = np.abs(m_ref - sc.tol) <= 1e-6 * sc.tol
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert c_ref > 0 and abs(c - c_ref) <= near.sum()
+    assert np.abs(m - m_ref).max() <= 1e-6 * m_ref.max() + 1e-30  # m is stored as float
+    assert f.sum() == c
+
+
+def test_fp32_flags_close_to_oracle(S):
+    sc = synth.small_2d(88, 61, seed=9)
+    f, m, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP32, 0, 0.32 * sc.t_f, 150)
+    near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert np.abs(m - m_ref).max() <= 1e-4 * m_ref.max()
+
+
+def test_coarse_adjoint_grid_flags(S):
+    """Adjoint on a coarser grid: bilinear interpolation onto forward cells."""
+    sc = synth.config2(n=96, L=96e3 * 4, adj_n=40, seed=11)
+    f, m, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP64, 0, sc.t_s, 100)
+    near = np.abs(m_ref - sc.tol) <= 1e-6 * sc.tol
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert np.abs(m - m_ref).max() <= 1e-6 * m_ref.max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gauges_match_oracle(S, precision):
+    sc = synth.small_2d(60, 50, seed=10)
+    p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
+    g = S.Grid(desc_of(S, sc.grid, p), sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    g.step(20, 1e12)
+    xy = np.array([[1.3e5, 2.2e5], [-5.0, 9e9], [5e5, 1e5], [3.333e5, 4.1e5]])
+    xy_d = torch.tensor(xy, dtype=torch.float64, device="cuda")
+    out = torch.zeros(len(xy), dtype=torch.float64, device="cuda")
+    S.swa_gauge_sample(g.h, len(xy), xy_d, out)
+    Bs = bath_seen(sc.B, p == S.SWA_FP32)
+    h, hu, hv, _, _ = run_oracle_forward(sc, 2, (0, 0, 0, 0), 20, B=Bs)
+    ref = O.gauge(O.Grid.from_spec(sc.grid), h, Bs, xy)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert np.abs(out.cpu().numpy() - ref).max() <= tol
+
+
+def test_mass_conserved_walls_fp64_full_size(S):
+    """Property at the full 2048^2 size: with walls the FP64 step conserves
+    mass to roundoff."""
+    sc = synth.config2()
+    g = S.Grid(desc_of(S, sc.grid, S.SWA_FP64, 2, (1, 1, 1, 1)), sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    m0 = g.get_state()["h"].sum()
+    g.step(20, 1e12)
+    m1 = g.get_state()["h"].sum()
+    assert abs(m1 - m0) / m0 <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_step_sampled_against_oracle_windows(S, precision):
+    """2048^2, the bench's launch configuration: one step from a perturbed
+    state, sampled cells compared with the oracle run on 9 x 9 windows around
+    them (a cell's update depends only on cells within 2 of it)."""
+    sc = synth.config2()
+    rng = np.random.default_rng(12)
+    hu = rng.uniform(-20, 20, sc.grid.n)
+    hv = rng.uniform(-20, 20, sc.grid.n)
+    p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
+    fp32 = p == S.SWA_FP32
+    g = S.Grid(desc_of(S, sc.grid, p), sc.B)
+    g.set_state(sc.eta0, hu, hv, 0.0)
+    g.step(1, 1e12)
+    s1 = g.get_state()
+    # the oracle's inputs: the seeded state as the storage precision holds it
+    Bs = bath_seen(sc.B, fp32)
+    if fp32:
+        eta = np.float32(sc.eta0).astype(np.float64)
+        hu = np.float32(hu).astype(np.float64)
+        hv = np.float32(hv).astype(np.float64)
+    else:
+        eta = sc.eta0
+    s0 = {"h": eta - Bs, "hu": hu, "hv": hv}
+    og = O.Grid.from_spec(sc.grid)
+    dt = og.cfl / O.fwd_smax(og, s0["h"], s0["hu"], s0["hv"])
+    nx = sc.grid.nx
+    cells = [(int(i), int(j)) for i, j in zip(rng.integers(0, nx, 200), rng.integers(0, nx, 200))]
+    cells += [(0, 0), (nx - 1, 5), (7, nx - 1), (nx - 1, nx - 1)]
+    for (i, j) in cells:
+        ii = np.clip(np.arange(i - 4, i + 5), 0, nx - 1)
+        jj = np.clip(np.arange(j - 4, j + 5), 0, nx - 1)
+        idx = (jj[:, None] * nx + ii[None, :]).ravel()
+        wg = O.Grid(2, 9, 9, 0.0, 0.0, sc.grid.dx, sc.grid.dy, order=2)
+        h, u, v = O.fwd_step(wg, s0["h"][idx], s0["hu"][idx], s0["hv"][idx], Bs[idx], dt)
+        o = (j * nx + i)
+        if precision == "fp64":
+            assert abs(s1["h"][o] - h[40]) <= 1e-12 * 4000
+            assert abs(s1["hu"][o] - u[40]) <= 1e-12 * 200
+            assert abs(s1["hv"][o] - v[40]) <= 1e-12 * 200
+        else:
+            assert abs(s1["eta"][o] - (h[40] + Bs[o])) <= 2e-6
+            assert abs(s1["hu"][o] - u[40]) <= 2e-5 and abs(s1["hv"][o] - v[40]) <= 2e-5
