@@ -130,11 +130,12 @@ class Scenario:
         self.hu_d = torch.tensor(sc.hu0, **f64)
         self.hv_d = torch.tensor(sc.hv0, **f64)
         self.phi_d = torch.tensor(sc.phi.reshape(-1), **f64)
-        pin = dict(dtype=torch.float64, pin_memory=True)
-        self.eta_h = torch.tensor(sc.eta0, **pin)
-        self.hu_h = torch.tensor(sc.hu0, **pin)
-        self.hv_h = torch.tensor(sc.hv0, **pin)
-        self.phi_h = torch.tensor(sc.phi.reshape(-1), **pin)
+        def pinned(a):
+            return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()
+        self.eta_h = pinned(sc.eta0)
+        self.hu_h = pinned(sc.hu0)
+        self.hv_h = pinned(sc.hv0)
+        self.phi_h = pinned(sc.phi.reshape(-1))
         self.xy = torch.tensor(sc.gauges, **f64)
         self.flags = torch.zeros(n, dtype=torch.uint8, device=device)
         self.n = n

@@ -19,8 +19,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswadj.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code is compiled without contraction so that host-side arithmetic
+# (snapshot times, step counts) rounds the same on x86 and Arm hosts.
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-Xcompiler", "-O2", f"-I{INCLUDE}", f"-I{CSRC}"]
+                     "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
+                     f"-I{INCLUDE}", f"-I{CSRC}"]
 
 
 def _nvcc():
@@ -52,6 +55,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        if src.endswith("_f64.cu"):
+            # FP64 kernels round exactly like the FP64 reference: no contraction
+            cmd.insert(1, "-fmad=false")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

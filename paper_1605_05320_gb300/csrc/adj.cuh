@@ -10,9 +10,10 @@ struct AdjParams {
     int nx, ny, two_d, order;
     BcSpec bc;
     R nux, nuy;          // dt/dx, dt/dy (fixed step)
+    R g, dry_tol;
     const R *src[3];     // (eta~, mu~, gamma~) at step s
     R *dst[3];           // at step s+1
-    const R *c;          // sqrt(g hbar), 0 where dry
+    const R *c;          // double: hbar; float: sqrt(g hbar), 0 where dry
     // fused snapshot (optional): written with the new state when snap_f or
     // snap_d is non-null
     float *snap_f;
@@ -24,6 +25,8 @@ struct AdjParams {
 
 template <typename R>
 int adj_launch_step(const AdjParams<R> &p, cudaStream_t st);
+template <> int adj_launch_step<double>(const AdjParams<double> &, cudaStream_t);
+template <> int adj_launch_step<float>(const AdjParams<float> &, cudaStream_t);
 
 // c = sqrt(g hbar) (0 where hbar <= dry_tol), hbar = max(-B, 0) computed from
 // the FP64 bathymetry in `B`; atomically maxes c/dx [+ c/dy] into *smax.

@@ -1,4 +1,4 @@
-// adj.cu -- time-reversed linear adjoint step (Sec. 4, Sec. 5).
+// adj_kernels.cuh -- time-reversed linear adjoint step (Sec. 4, Sec. 5).
 //
 // q~ = (eta~, mu~, gamma~) solves q~_t + F_x + G_y = 0 with F = -A_1^T q~ =
 // -(g hbar mu~, eta~, 0) and G = -A_2^T q~ = -(g hbar gamma~, 0, eta~), the
@@ -9,6 +9,7 @@
 // form for spatially varying coefficients.  A wet/dry edge is a wall (zero
 // normal velocity, Sec. 5): the dry side is the mirror of the wet one, and
 // the edge carries no second-order correction.
+#pragma once
 #include "adj.cuh"
 
 namespace swadj {
@@ -19,18 +20,19 @@ struct AdjWave {
     int wall;
 };
 
-// Waves at the edge between (eL, mL, cL) and (eR, mR, cR); normal component m.
+// Waves at the edge between (eL, mL, cL, ghL) and (eR, mR, cR, ghR), normal
+// component m, c = sqrt(g hbar), gh = g hbar (c = 0 marks a dry cell).
 template <typename R>
-__device__ __forceinline__ AdjWave<R> adj_riemann(R eL, R mL, R cL, R eR, R mR,
-                                                  R cR) {
+__device__ __forceinline__ AdjWave<R> adj_riemann(R eL, R mL, R cL, R ghL, R eR,
+                                                  R mR, R cR, R ghR) {
     AdjWave<R> w;
     const bool dL = !(cL > R(0)), dR = !(cR > R(0));
     w.wall = (dL || dR) ? 1 : 0;
     if (dL && dR) { w.b1 = R(0); w.b2 = R(0); w.cL = R(0); w.cR = R(0); return w; }
-    if (dL) { eL = eR; mL = -mR; cL = cR; }
-    if (dR) { eR = eL; mR = -mL; cR = cL; }
-    const R F1L = -(cL * cL * mL), F2L = -eL;
-    const R F1R = -(cR * cR * mR), F2R = -eR;
+    if (dL) { eL = eR; mL = -mR; cL = cR; ghL = ghR; }
+    if (dR) { eR = eL; mR = -mL; cR = cL; ghR = ghL; }
+    const R F1L = -(ghL * mL), F2L = -eL;
+    const R F1R = -(ghR * mR), F2R = -eR;
     const R d1 = F1R - F1L, d2 = F2R - F2L;
     const R s = cL + cR;
     w.b1 = (d1 + cR * d2) / s;
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     constexpr int NEX = RX - 1;
     constexpr int NEY = TWO_D ? RY - 1 : 1;
     constexpr int WYC = TWO_D ? TX : 1;
-    __shared__ R s_e[RY][RX], s_m[RY][RX], s_g[RY][RX], s_c[RY][RX];
+    __shared__ R s_e[RY][RX], s_m[RY][RX], s_g[RY][RX], s_c[RY][RX], s_gh[RY][RX];
     __shared__ AdjWave<R> wx[TY][NEX];
     __shared__ AdjWave<R> wy[NEY][WYC];
 
@@ -106,20 +108,34 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
         s_e[ry][rx] = p.src[0][o];
         s_m[ry][rx] = m;
         s_g[ry][rx] = g;
-        s_c[ry][rx] = p.c[o];
+        // double: the coefficient array holds hbar (c and g hbar derived here,
+        // rounding as in the reference); float: it holds c (g hbar = c c)
+        const R a = p.c[o];
+        R c, gh;
+        if (sizeof(R) == 8) {
+            if (a > p.dry_tol) { gh = p.g * a; c = sqrt(gh); }
+            else { gh = R(0); c = R(0); }
+        } else {
+            c = a;
+            gh = a * a;
+        }
+        s_c[ry][rx] = c;
+        s_gh[ry][rx] = gh;
     }
     __syncthreads();
 
     for (int e = tid; e < TY * NEX; e += NT) {
         const int row = e / NEX, k = e - row * NEX, ry = row + HY;
-        wx[row][k] = adj_riemann<R>(s_e[ry][k], s_m[ry][k], s_c[ry][k],
-                                    s_e[ry][k + 1], s_m[ry][k + 1], s_c[ry][k + 1]);
+        wx[row][k] = adj_riemann<R>(s_e[ry][k], s_m[ry][k], s_c[ry][k], s_gh[ry][k],
+                                    s_e[ry][k + 1], s_m[ry][k + 1], s_c[ry][k + 1],
+                                    s_gh[ry][k + 1]);
     }
     if (TWO_D) {
         for (int e = tid; e < NEY * TX; e += NT) {
             const int k = e / TX, col = e - k * TX, rx = col + HX;
-            wy[k][col] = adj_riemann<R>(s_e[k][rx], s_g[k][rx], s_c[k][rx],
-                                        s_e[k + 1][rx], s_g[k + 1][rx], s_c[k + 1][rx]);
+            wy[k][col] = adj_riemann<R>(s_e[k][rx], s_g[k][rx], s_c[k][rx], s_gh[k][rx],
+                                        s_e[k + 1][rx], s_g[k + 1][rx], s_c[k + 1][rx],
+                                        s_gh[k + 1][rx]);
         }
     }
     __syncthreads();
@@ -161,103 +177,5 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     }
     if ((p.snap_f || p.snap_d) && o == 0) *p.tau_dev = p.tau_val;
 }
-
-template <typename R, bool TWO_D, int TX, int TY>
-static int launch_adj(const AdjParams<R> &p, cudaStream_t st) {
-    dim3 grid((p.nx + TX - 1) / TX, TWO_D ? (p.ny + TY - 1) / TY : 1);
-    adj_step_kernel<R, TWO_D, TX, TY><<<grid, dim3(TX, TY), 0, st>>>(p);
-    return swadj_host::cuda_check(cudaGetLastError(), "adj_step_kernel");
-}
-
-template <>
-int adj_launch_step<double>(const AdjParams<double> &p, cudaStream_t st) {
-    if (p.two_d) return launch_adj<double, true, 32, 4>(p, st);
-    return launch_adj<double, false, 128, 1>(p, st);
-}
-
-template <>
-int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
-    if (p.two_d) return launch_adj<float, true, 32, 8>(p, st);
-    return launch_adj<float, false, 128, 1>(p, st);
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
-    // non-negative doubles order like their bit patterns as unsigned integers
-    atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
-}
-
-template <typename R>
-__global__ void adj_init_kernel(const double *B, R *c, size_t n, int two_d,
-                                double g, double dx, double dy, double dry_tol,
-                                double *smax) {
-    double mx = 0.0;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (size_t)gridDim.x * blockDim.x) {
-        const double hb = -B[k] > 0.0 ? -B[k] : 0.0;
-        double cc = 0.0, s = 0.0;
-        if (hb > dry_tol) {
-            cc = sqrt(g * hb);
-            s = cc / dx;
-            if (two_d) s += cc / dy;
-        }
-        c[k] = (R)cc;
-        mx = s > mx ? s : mx;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = w > mx ? w : mx;
-    }
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(smax, mx);
-}
-
-template <typename R>
-int adj_launch_init(const double *B, R *c, size_t n, int two_d, double g,
-                    double dx, double dy, double dry_tol, double *smax,
-                    cudaStream_t st) {
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 2048) blocks = 2048;
-    adj_init_kernel<R><<<blocks, 256, 0, st>>>(B, c, n, two_d, g, dx, dy, dry_tol, smax);
-    return swadj_host::cuda_check(cudaGetLastError(), "adj_init_kernel");
-}
-
-template <typename R>
-__global__ void adj_store_kernel(const R *s0, const R *s1, const R *s2, int ncomp,
-                                 size_t n, float *sf, double *sd, size_t cs,
-                                 double *tau_dev, double tau_val) {
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (size_t)gridDim.x * blockDim.x) {
-        if (sf) {
-            sf[k] = (float)s0[k];
-            sf[cs + k] = (float)s1[k];
-            if (ncomp == 3) sf[2 * cs + k] = (float)s2[k];
-        } else {
-            sd[k] = (double)s0[k];
-            sd[cs + k] = (double)s1[k];
-            if (ncomp == 3) sd[2 * cs + k] = (double)s2[k];
-        }
-        if (k == 0) *tau_dev = tau_val;
-    }
-}
-
-template <typename R>
-int adj_launch_store(const R *const src[3], int ncomp, size_t n, float *snap_f,
-                     double *snap_d, size_t comp_stride, double *tau_dev,
-                     double tau_val, cudaStream_t st) {
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
-    adj_store_kernel<R><<<blocks, 256, 0, st>>>(src[0], src[1], src[2], ncomp, n,
-                                                snap_f, snap_d, comp_stride,
-                                                tau_dev, tau_val);
-    return swadj_host::cuda_check(cudaGetLastError(), "adj_store_kernel");
-}
-
-template int adj_launch_init<double>(const double *, double *, size_t, int, double,
-                                     double, double, double, double *, cudaStream_t);
-template int adj_launch_init<float>(const double *, float *, size_t, int, double,
-                                    double, double, double, double *, cudaStream_t);
-template int adj_launch_store<double>(const double *const[3], int, size_t, float *,
-                                      double *, size_t, double *, double, cudaStream_t);
-template int adj_launch_store<float>(const float *const[3], int, size_t, float *,
-                                     double *, size_t, double *, double, cudaStream_t);
 
 }  // namespace swadj

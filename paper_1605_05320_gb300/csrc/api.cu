@@ -41,6 +41,16 @@ int cuda_check(cudaError_t e, const char *what) {
 using swadj_host::cuda_check;
 using swadj_host::set_error;
 
+// Device error word shared by every object on a device (ERR_* bits).  Kernels
+// in other translation units receive its address through their parameters.
+__device__ int g_swa_err;
+
+static int *err_word() {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_swa_err) != cudaSuccess) return nullptr;
+    return (int *)p;
+}
+
 #define TRY(x)                      \
     do {                            \
         int _rc = (x);              \
@@ -117,11 +127,13 @@ __global__ void fill_zero_f64(double *p, size_t n) {
         p[k] = 0.0;
 }
 
+// wet = coefficient above `thr` (double adjoints store hbar, thr = dry_tol;
+// float adjoints store c, 0 where dry, thr = 0)
 template <typename R>
-__global__ void wet_mask_kernel(const R *c, uint8_t *wet, size_t n) {
+__global__ void wet_mask_kernel(const R *c, R thr, uint8_t *wet, size_t n) {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (size_t)gridDim.x * blockDim.x)
-        wet[k] = c[k] > R(0) ? 1 : 0;
+        wet[k] = c[k] > thr ? 1 : 0;
 }
 
 static unsigned ew_blocks(size_t n) {
@@ -205,6 +217,7 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.clk = g->clk;
     p.partial = g->partial;
     p.nblocks = g->step_blocks;
+    p.err = err_word();
     return p;
 }
 
@@ -215,9 +228,14 @@ const char *swa_version(void) { return "swadj 0.1 (sm_103a)"; }
 const char *swa_last_error(void) { return swadj_host::g_msg; }
 
 int swa_sync_status(void *stream) {
-    TRY(cuda_check(cudaStreamSynchronize(S(stream)), "stream synchronize"));
-    int err = 0;
-    TRY(fwd_read_clear_err(S(stream), &err));
+    cudaStream_t st = S(stream);
+    TRY(cuda_check(cudaStreamSynchronize(st), "stream synchronize"));
+    int err = 0, zero = 0;
+    TRY(cuda_check(cudaMemcpyFromSymbolAsync(&err, g_swa_err, sizeof(int), 0,
+                                             cudaMemcpyDeviceToHost, st), "error word read"));
+    TRY(cuda_check(cudaMemcpyToSymbolAsync(g_swa_err, &zero, sizeof(int), 0,
+                                           cudaMemcpyHostToDevice, st), "error word clear"));
+    TRY(cuda_check(cudaStreamSynchronize(st), "error word"));
     if (err & ERR_UNSTABLE)
         return set_error(SWA_EUNSTABLE, "device saw a non-finite state or depth <= 0");
     return SWA_OK;
@@ -434,6 +452,8 @@ static AdjParams<R> adj_params(const swa_adjoint *a) {
     p.bc = BcSpec{a->d.bc[0], a->d.bc[1], a->d.bc[2], a->d.bc[3]};
     p.nux = (R)(a->dt / a->d.dx);
     p.nuy = (R)(a->dt / a->d.dy);
+    p.g = (R)a->d.g;
+    p.dry_tol = (R)a->d.dry_tol;
     for (int k = 0; k < 3; k++) {
         p.src[k] = (const R *)a->q[a->cur][k];
         p.dst[k] = (R *)a->q[a->cur ^ 1][k];
@@ -682,9 +702,11 @@ int swa_create_snapstore(const swa_adjoint *adj, int max_snaps, int precision, v
     Carve c(ws);
     snap_layout(s->na, s->nc, max_snaps, precision, c, s);
     if (adj->d.precision == SWA_FP64)
-        wet_mask_kernel<double><<<ew_blocks(s->na), 256>>>((const double *)adj->c, s->wet, s->na);
+        wet_mask_kernel<double><<<ew_blocks(s->na), 256>>>((const double *)adj->c,
+                                                           adj->d.dry_tol, s->wet, s->na);
     else
-        wet_mask_kernel<float><<<ew_blocks(s->na), 256>>>((const float *)adj->c, s->wet, s->na);
+        wet_mask_kernel<float><<<ew_blocks(s->na), 256>>>((const float *)adj->c, 0.0f,
+                                                          s->wet, s->na);
     int rc = cuda_check(cudaGetLastError(), "wet_mask_kernel");
     if (rc == SWA_OK) rc = cuda_check(cudaDeviceSynchronize(), "create_snapstore");
     if (rc != SWA_OK) { delete s; return rc; }

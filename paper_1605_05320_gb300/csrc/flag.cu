@@ -19,6 +19,8 @@ namespace swadj {
 struct Window {
     int empty;
     int k0, k1;          // snapshots read: k0..k1 inclusive
+    int ki0, ki1;        // snapshots strictly inside the window (INTERP), or
+                         // the whole read range (BRACKET)
     int kh, kl;          // INTERP: bracket index at hi and at lo
     int exact_h, exact_l;
     double ah, al;       // weights on snapshot kh (resp. kl) at hi (lo)
@@ -44,7 +46,8 @@ __device__ Window make_window(const double *tau, int K, double t, double t_s,
     if (T > t_f) T = t_f;
     double lo = t, hi = T;
     w.empty = 1;
-    w.k0 = 0; w.k1 = -1; w.kh = 0; w.kl = 0; w.exact_h = 1; w.exact_l = 1;
+    w.k0 = 0; w.k1 = -1; w.ki0 = 0; w.ki1 = -1;
+    w.kh = -2; w.kl = -2; w.exact_h = 1; w.exact_l = 1;
     w.ah = 1.0; w.al = 1.0;
     if (K < 1) return w;
     if (lo < tau[K - 1]) lo = tau[K - 1];
@@ -57,6 +60,7 @@ __device__ Window make_window(const double *tau, int K, double t, double t_s,
         for (int k = 0; k < K; k++) if (tau[k] <= lo) { kb = k; break; }
         for (int k = K - 1; k >= 0; k--) if (tau[k] >= hi) { ke = k; break; }
         w.k0 = ke; w.k1 = kb;
+        w.ki0 = ke; w.ki1 = kb;
         return w;
     }
     const int kh = bracket_index(tau, K, hi);
@@ -69,6 +73,12 @@ __device__ Window make_window(const double *tau, int K, double t, double t_s,
     w.k0 = kh;
     w.k1 = w.exact_l ? kl : kl + 1;
     if (w.k1 < w.k0) w.k1 = w.k0;
+    // tau[k] in (lo, hi) exactly for k in [kh + 1, kl], minus an end that
+    // coincides with lo or hi
+    w.ki0 = kh + 1;
+    w.ki1 = kl;
+    while (w.ki0 <= w.ki1 && !(tau[w.ki0] < hi)) w.ki0++;
+    while (w.ki1 >= w.ki0 && !(tau[w.ki1] > lo)) w.ki1--;
     return w;
 }
 
@@ -151,16 +161,11 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
                     }
                 }
                 const A d = v0 * qe + v1 * qu + v2 * qv;
-                if (p.mode == SWA_FLAG_BRACKET) {
-                    m = fabs(d) > m ? fabs(d) : m;
-                } else {
-                    if (k == w.kh) dh0 = d;
-                    if (k == w.kh + 1) dh1 = d;
-                    if (k == w.kl) dl0 = d;
-                    if (k == w.kl + 1) dl1 = d;
-                    const double tk = p.tau[k];
-                    if (tk > w.lo && tk < w.hi) m = fabs(d) > m ? fabs(d) : m;
-                }
+                if (k >= w.ki0 && k <= w.ki1) m = fabs(d) > m ? fabs(d) : m;
+                if (k == w.kh) dh0 = d;
+                if (k == w.kh + 1) dh1 = d;
+                if (k == w.kl) dl0 = d;
+                if (k == w.kl + 1) dl1 = d;
             }
             if (p.mode != SWA_FLAG_BRACKET) {
                 const A ah = (A)w.ah, al = (A)w.al;
@@ -170,12 +175,87 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
                 m = fabs(vl) > m ? fabs(vl) : m;
             }
         }
-        f = (!w.empty && !dry && (double)m >= p.tol) ? 1 : 0;
+        f = (!w.empty && !dry && m >= (A)p.tol) ? 1 : 0;
         p.flags[i] = (uint8_t)f;
         if (p.maxip) p.maxip[i] = (float)m;
     }
     const int cnt = __syncthreads_count(f);
     if (threadIdx.x == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
+}
+
+// FP32 forward state and FP32 snapshots on the same grid: the bandwidth-bound
+// case.  Each thread takes 4 consecutive cells with 16-byte loads; the window
+// (index ranges and end weights) is computed once per block, so the per-cell
+// loop has no FP64 work at all.
+__global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float> p) {
+    __shared__ Window sw;
+    if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
+    __syncthreads();
+    const Window w = sw;
+    const int cur = p.clk->cur;
+    const size_t n4 = ((size_t)p.nx * p.ny) >> 2;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    if (i < n4) {
+        const float4 e = reinterpret_cast<const float4 *>(p.q[cur][0])[i];
+        const float4 u = reinterpret_cast<const float4 *>(p.q[cur][1])[i];
+        const float4 v = reinterpret_cast<const float4 *>(p.q[cur][2])[i];
+        const float4 hb = reinterpret_cast<const float4 *>(p.bath)[i];
+        const uchar4 wet = reinterpret_cast<const uchar4 *>(p.awet)[i];
+        const float dt = p.dry_tol;
+        const bool ok0 = e.x + hb.x > dt && wet.x, ok1 = e.y + hb.y > dt && wet.y;
+        const bool ok2 = e.z + hb.z > dt && wet.z, ok3 = e.w + hb.w > dt && wet.w;
+        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 dh0 = m, dh1 = m, dl0 = m, dl1 = m;
+        if (!w.empty) {
+            const float4 *s0 = reinterpret_cast<const float4 *>(p.snaps) + i;
+            const size_t cs = p.na >> 2, ks = p.snap_stride >> 2;
+#pragma unroll 2
+            for (int k = w.k0; k <= w.k1; k++) {
+                const float4 a = __ldcs(s0 + (size_t)k * ks);
+                const float4 b = __ldcs(s0 + (size_t)k * ks + cs);
+                const float4 c = __ldcs(s0 + (size_t)k * ks + 2 * cs);
+                float4 d;
+                d.x = a.x * e.x + b.x * u.x + c.x * v.x;
+                d.y = a.y * e.y + b.y * u.y + c.y * v.y;
+                d.z = a.z * e.z + b.z * u.z + c.z * v.z;
+                d.w = a.w * e.w + b.w * u.w + c.w * v.w;
+                if (k >= w.ki0 && k <= w.ki1) {
+                    m.x = fmaxf(m.x, fabsf(d.x)); m.y = fmaxf(m.y, fabsf(d.y));
+                    m.z = fmaxf(m.z, fabsf(d.z)); m.w = fmaxf(m.w, fabsf(d.w));
+                }
+                if (k == w.kh) dh0 = d;
+                if (k == w.kh + 1) dh1 = d;
+                if (k == w.kl) dl0 = d;
+                if (k == w.kl + 1) dl1 = d;
+            }
+            if (p.mode != SWA_FLAG_BRACKET) {
+                const float ah = (float)w.ah, al = (float)w.al;
+                const float bh = 1.f - ah, bl = 1.f - al;
+#define SWADJ_ENDS(c)                                                          \
+    {                                                                          \
+        const float vh = w.exact_h ? dh0.c : ah * dh0.c + bh * dh1.c;          \
+        const float vl = w.exact_l ? dl0.c : al * dl0.c + bl * dl1.c;          \
+        m.c = fmaxf(m.c, fmaxf(fabsf(vh), fabsf(vl)));                         \
+    }
+                SWADJ_ENDS(x) SWADJ_ENDS(y) SWADJ_ENDS(z) SWADJ_ENDS(w)
+#undef SWADJ_ENDS
+            }
+        }
+        const float tol = (float)p.tol;
+        const int f0 = (!w.empty && ok0 && m.x >= tol), f1 = (!w.empty && ok1 && m.y >= tol);
+        const int f2 = (!w.empty && ok2 && m.z >= tol), f3 = (!w.empty && ok3 && m.w >= tol);
+        reinterpret_cast<uchar4 *>(p.flags)[i] = make_uchar4(f0, f1, f2, f3);
+        if (p.maxip) {
+            const float4 mm = make_float4(ok0 ? m.x : 0.f, ok1 ? m.y : 0.f,
+                                          ok2 ? m.z : 0.f, ok3 ? m.w : 0.f);
+            reinterpret_cast<float4 *>(p.maxip)[i] = w.empty ? make_float4(0.f, 0.f, 0.f, 0.f) : mm;
+        }
+        f = f0 + f1 + f2 + f3;
+    }
+    int cnt = f;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
 }
 
 template <typename R, typename S>
@@ -184,7 +264,11 @@ int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return swadj_host::cuda_check(e, "flag count reset");
     const unsigned blocks = (unsigned)((n + 255) / 256);
-    if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
+    if (sizeof(R) == 4 && sizeof(S) == 4 && p.same_grid && p.two_d && (n & 3) == 0) {
+        const size_t n4 = n >> 2;
+        flag_kernel_f32x4<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(
+            *reinterpret_cast<const FlagParams<float, float> *>(&p));
+    } else if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
     else flag_kernel<R, S, false><<<blocks, 256, 0, st>>>(p);
     return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");
 }

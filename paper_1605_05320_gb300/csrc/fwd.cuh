@@ -18,6 +18,8 @@ struct FwdParams {
     DevClock *clk;
     double *partial;   // one double per block
     int nblocks;
+    int *err;          // device error word (ERR_* bits)
+    int fwd_rows;      // FP32 strip height (rows per block), 0 = default
 };
 
 template <typename R>
@@ -26,6 +28,11 @@ template <typename R>
 int fwd_step_blocks(const FwdParams<R> &p);
 template <typename R>
 int fwd_launch_clock_init(const FwdParams<R> &p, double t0, cudaStream_t st);
-int fwd_read_clear_err(cudaStream_t st, int *out);
+template <> int fwd_launch_step<double>(const FwdParams<double> &, cudaStream_t);
+template <> int fwd_launch_step<float>(const FwdParams<float> &, cudaStream_t);
+template <> int fwd_step_blocks<double>(const FwdParams<double> &);
+template <> int fwd_step_blocks<float>(const FwdParams<float> &);
+template <> int fwd_launch_clock_init<double>(const FwdParams<double> &, double, cudaStream_t);
+template <> int fwd_launch_clock_init<float>(const FwdParams<float> &, double, cudaStream_t);
 
 }  // namespace swadj

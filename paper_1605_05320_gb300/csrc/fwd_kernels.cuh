@@ -1,4 +1,4 @@
-// fwd.cu -- forward nonlinear shallow-water step (Eq. swe_1d / swe, Sec. 3, 5)
+// fwd_kernels.cuh -- forward nonlinear shallow-water step (Eq. swe_1d / swe, Sec. 3, 5)
 // with a Roe-type f-wave Riemann solve per edge (Sec. 6), fused ghost fill and
 // fused CFL max-reduction (next time step computed on the device).
 //
@@ -7,13 +7,10 @@
 //   float  (SWA_FP32): q = (eta, hu, hv), bath = hbar = -B (perturbation
 //                      form: metre-scale eta is stored directly instead of as
 //                      the small difference of ~4000 m depths).
-#include <stdio.h>
-
+#pragma once
 #include "fwd.cuh"
 
 namespace swadj {
-
-__device__ int g_err_fwd;
 
 // Roe f-wave decomposition at one edge in the edge's frame (normal, tangential).
 // Inputs per side: depth h, normal/tangential momentum mn/mt, normal/tangential
@@ -209,7 +206,7 @@ fwd_step_kernel(FwdParams<R> p) {
             o0[o] = n0;
             o1[o] = n1;
             if (TWO_D) o2[o] = n2;
-            if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(&g_err_fwd, ERR_UNSTABLE);
+            if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(p.err, ERR_UNSTABLE);
             // CFL number of the new state (per-cell term in the compute type)
             const R c = sqrt(p.g * hn);
             R s = (fabs(n1 / hn) + c) / p.dx;
@@ -263,7 +260,7 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
         R s = (fabs(q1[k] / h) + c) / p.dx;
         if (p.two_d) s += (fabs(q2[k] / h) + c) / p.dy;
         double sd = (double)s;
-        if (!(h > R(0))) atomicOr(&g_err_fwd, ERR_UNSTABLE);
+        if (!(h > R(0))) atomicOr(p.err, ERR_UNSTABLE);
         mx = sd > mx ? sd : mx;
     }
     const double bm = block_max<256>(mx, red);
@@ -292,63 +289,6 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
             clk->ticket = 0u;
         }
     }
-}
-
-// ---- host launchers ----
-
-template <typename R, bool PERT, bool TWO_D, int TX, int TY>
-static int launch_step(FwdParams<R> p, cudaStream_t st) {
-    dim3 grid((p.nx + TX - 1) / TX, TWO_D ? (p.ny + TY - 1) / TY : 1);
-    p.nblocks = (int)(grid.x * grid.y);
-    fwd_step_kernel<R, PERT, TWO_D, TX, TY><<<grid, dim3(TX, TY), 0, st>>>(p);
-    return swadj_host::cuda_check(cudaGetLastError(), "fwd_step_kernel");
-}
-
-template <typename R>
-int fwd_step_blocks(const FwdParams<R> &p) {
-    if (p.two_d) {
-        if (sizeof(R) == 8) return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
-        return ((p.nx + 31) / 32) * ((p.ny + 7) / 8);
-    }
-    return (p.nx + 127) / 128;
-}
-
-template <>
-int fwd_launch_step<double>(const FwdParams<double> &p, cudaStream_t st) {
-    if (p.two_d) return launch_step<double, false, true, 32, 4>(p, st);
-    return launch_step<double, false, false, 128, 1>(p, st);
-}
-
-template <>
-int fwd_launch_step<float>(const FwdParams<float> &p, cudaStream_t st) {
-    if (p.two_d) return launch_step<float, true, true, 32, 8>(p, st);
-    return launch_step<float, true, false, 128, 1>(p, st);
-}
-
-template <typename R>
-int fwd_launch_clock_init(const FwdParams<R> &p, double t0, cudaStream_t st) {
-    constexpr bool PERT = sizeof(R) == 4;
-    const size_t n = (size_t)p.nx * p.ny;
-    int blocks = (int)((n + 255) / 256);
-    if (blocks > kInitBlocks) blocks = kInitBlocks;
-    clock_init_kernel<R, PERT><<<blocks, 256, 0, st>>>(p, t0);
-    return swadj_host::cuda_check(cudaGetLastError(), "clock_init_kernel");
-}
-
-template int fwd_launch_clock_init<double>(const FwdParams<double> &, double, cudaStream_t);
-template int fwd_launch_clock_init<float>(const FwdParams<float> &, double, cudaStream_t);
-template int fwd_step_blocks<double>(const FwdParams<double> &);
-template int fwd_step_blocks<float>(const FwdParams<float> &);
-
-int fwd_read_clear_err(cudaStream_t st, int *out) {
-    int zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_err_fwd, sizeof(int), 0,
-                                              cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyToSymbolAsync(g_err_fwd, &zero, sizeof(int), 0,
-                                    cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return swadj_host::cuda_check(e, "read forward error word");
 }
 
 }  // namespace swadj

@@ -80,6 +80,19 @@ def test_fp64_forward_2d_1000_steps(S, order, bc):
     assert rel(st["hv"], hv) <= 1e-12
 
 
+def test_fp64_forward_rounds_like_the_oracle(S):
+    """The FP64 kernels are built without contraction and evaluate in the
+    oracle's order: the result is bit-identical, which is what the 1e-12
+    bound needs in (h, hu) form (one ulp of a 4000 m depth moves hu by ~1e-11
+    per step through g hhat d_eta)."""
+    sc = synth.small_2d(150, 97, seed=13)
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, 2, (1, 0, 0, 1), 300)
+    h, hu, hv, t_ref, n_ref = run_oracle_forward(sc, 2, (1, 0, 0, 1), 300)
+    assert t == t_ref
+    assert np.array_equal(st["h"], h) and np.array_equal(st["hu"], hu)
+    assert np.array_equal(st["hv"], hv)
+
+
 def test_fp64_forward_1d_config1(S):
     sc = synth.config1()
     st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, 2, (0, 0, 0, 0), 1000)
