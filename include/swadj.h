@@ -225,6 +225,44 @@ int swa_flag_cells(const swa_grid *grid, const swa_snapstore *store,
 int swa_gauge_sample(const swa_grid *grid, int n, const double *xy_dev,
                      double *eta_dev, void *stream);
 
+/* ======================= allocation-free forward step =====================
+ * The paper has no counterpart to this entry point; it is an integration aid.
+ *
+ * One forward step, as in swa_step_forward, for callers that cannot allocate
+ * device memory: code whose device memory belongs to a host framework that
+ * hands out only the arrays to work on, or that runs where cudaMalloc is not
+ * allowed (a fixed memory budget, a region that must not synchronise the
+ * device).  Such a caller cannot provide the per-block reduction scratch that
+ * a grid workspace holds, so this call takes it from a fixed static device
+ * array of SWA_STATIC_SCRATCH_BYTES inside the library (every GPU that loads
+ * the library holds it until the process exits).  It allocates nothing.
+ *
+ * desc       grid descriptor (precision selects the storage layout below).
+ * q_in[3]    current state, device, n values each, storage precision:
+ *            SWA_FP64: (h, hu, hv) double; SWA_FP32: (eta, hu, hv) float.
+ *            q_in[2] may be NULL for ndim = 1.
+ * q_out[3]   new state after one step, same layout; must not alias q_in.
+ * bath       device, n values: B (double) for SWA_FP64, hbar = -B (float)
+ *            for SWA_FP32.
+ * dt         the step (the caller chooses it, e.g. cfl / s_max).
+ * smax_out_dev  optional device double receiving s_max of the new state,
+ *            max over cells of (|u|+c)/dx + (|v|+c)/dy, for the next dt.
+ * Errors: SWA_EINVAL for bad arguments; SWA_ENOMEM when the grid needs more
+ * reduction slots than the static array holds (SWA_STATIC_MAX_BLOCKS blocks;
+ * 2048 x 2048 fits in both precisions); SWA_ECUDA for a runtime failure.
+ * All calls share the static array and it keeps the last call's contents;
+ * each call resets what must start at zero before its kernel runs.  Calls
+ * whose kernels overlap on the GPU race on the array: issue them on one
+ * stream.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.
+ */
+#define SWA_STATIC_MAX_BLOCKS 32768
+#define SWA_STATIC_SCRATCH_BYTES (256 + 8 * SWA_STATIC_MAX_BLOCKS)
+int swa_step_forward_static(const swa_grid_desc *desc, const void *const q_in[3],
+                            void *const q_out[3], const void *bath, double dt,
+                            double *smax_out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

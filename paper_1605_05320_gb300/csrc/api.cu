@@ -51,6 +51,8 @@ static int *err_word() {
     return (int *)p;
 }
 
+int *swadj_host::error_word() { return err_word(); }
+
 #define TRY(x)                      \
     do {                            \
         int _rc = (x);              \

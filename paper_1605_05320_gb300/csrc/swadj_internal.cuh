@@ -89,4 +89,5 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 namespace swadj_host {
 int set_error(int code, const char *fmt, ...);
 int cuda_check(cudaError_t e, const char *what);
+int *error_word();  // device address of the error word of the current device
 }  // namespace swadj_host

@@ -39,6 +39,7 @@ EXPORTS = [
     "swa_destroy_snapstore", "swa_store_snapshot", "swa_run_adjoint",
     "swa_snapstore_info",
     "swa_flag_cells", "swa_gauge_sample",
+    "swa_step_forward_static",
 ]
 
 
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         "swa_snapstore_info": ([_V, _P(_I), _V, _I], _I),
         "swa_flag_cells": ([_V, _V, _D, _D, _D, _I, _V, _V, _V, _V], _I),
         "swa_gauge_sample": ([_V, _I, _V, _V, _V], _I),
+        "swa_step_forward_static": ([D, _P(_V), _P(_V), _V, _D, _V, _V], _I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -288,6 +290,17 @@ def swa_flag_cells(grid, store, t_s, t_f, tol, mode, flags_dev, maxip_dev, count
 def swa_gauge_sample(grid, n, xy_dev, eta_dev, stream=None):
     return _chk(load().swa_gauge_sample(grid, int(n), _ptr(xy_dev), _ptr(eta_dev),
                                         _stream(stream)))
+
+
+def swa_step_forward_static(desc, q_in, q_out, bath, dt, smax_out_dev=None, stream=None):
+    """One forward step without any device allocation (scratch comes from a
+    static array inside the library); q_in / q_out are 3 device buffers each
+    (the third may be None in 1D)."""
+    qi = (_V * 3)(*[_ptr(x) for x in q_in])
+    qo = (_V * 3)(*[_ptr(x) for x in q_out])
+    return _chk(load().swa_step_forward_static(ctypes.byref(desc), qi, qo, _ptr(bath),
+                                               float(dt), _ptr(smax_out_dev),
+                                               _stream(stream)))
 
 
 # ------------------------------------------------- workspace-owning helpers
