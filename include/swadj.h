@@ -134,6 +134,14 @@ int swa_get_time(swa_grid *grid, double *t, double *dt_next,
                  long long *nsteps, void *stream);
 
 /*
+ * Launch shape of the FP32 step kernel: the tile height in rows, 8 or 16
+ * (0 restores the default, 16).  Results do not depend on it; throughput
+ * does (the autotuner picks it per grid size).  FP64 grids ignore it.
+ */
+#define SWA_MIN_STRIP_ROWS 8
+int swa_grid_set_strip_rows(swa_grid *grid, int rows);
+
+/*
  * Device pointers of the current state arrays (read-only use), for gauge or
  * diagnostic kernels of the caller.  Synchronises (the current buffer is
  * device-resident).  precision tells the element type (double or float).

@@ -170,6 +170,7 @@ struct swa_grid {
     double *partial;
     int step_blocks;
     int state_set;
+    int strip_rows;        // FP32 launch shape (0 = default)
 };
 
 static int grid_step_blocks(const swa_grid_desc *d) {
@@ -183,6 +184,16 @@ static int grid_step_blocks(const swa_grid_desc *d) {
     return fwd_step_blocks<float>(p);
 }
 
+// Reduction slots for the smallest strip height the FP32 kernel accepts.
+static int grid_max_blocks(const swa_grid_desc *d) {
+    if (d->precision == SWA_FP32 && d->ndim == 2) {
+        FwdParams<float> p{};
+        p.nx = d->nx; p.ny = d->ny; p.two_d = 1; p.fwd_rows = SWA_MIN_STRIP_ROWS;
+        return fwd_step_blocks<float>(p);
+    }
+    return grid_step_blocks(d);
+}
+
 static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
     const size_t n = (size_t)d->nx * d->ny;
     const size_t esz = d->precision == SWA_FP64 ? 8 : 4;
@@ -192,7 +203,7 @@ static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
     void *bath = c.take(n * esz);
     double *staging = (double *)c.take(n * 8);
     DevClock *clk = (DevClock *)c.take(sizeof(DevClock));
-    int blocks = grid_step_blocks(d);
+    int blocks = grid_max_blocks(d);
     if (blocks < kInitBlocks) blocks = kInitBlocks;
     double *partial = (double *)c.take((size_t)blocks * 8);
     if (g) {
@@ -220,6 +231,7 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.partial = g->partial;
     p.nblocks = g->step_blocks;
     p.err = err_word();
+    p.fwd_rows = g->strip_rows;
     return p;
 }
 
@@ -393,6 +405,14 @@ int swa_get_time(swa_grid *g, double *t, double *dt_next, long long *nsteps, voi
     if (t) *t = clk.t;
     if (dt_next) *dt_next = clk.dt_cfl;
     if (nsteps) *nsteps = clk.nsteps;
+    return SWA_OK;
+}
+
+int swa_grid_set_strip_rows(swa_grid *g, int rows) {
+    if (!g) return set_error(SWA_EINVAL, "null grid");
+    if (rows != 0 && rows != 8 && rows != 16)
+        return set_error(SWA_EINVAL, "tile rows must be 0, 8 or 16");
+    g->strip_rows = rows;
     return SWA_OK;
 }
 

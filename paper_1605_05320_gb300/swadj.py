@@ -31,6 +31,7 @@ EXPORTS = [
     "swa_version", "swa_last_error", "swa_sync_status",
     "swa_grid_workspace_bytes", "swa_create_grid", "swa_destroy_grid",
     "swa_set_state", "swa_get_state", "swa_step_forward", "swa_get_time",
+    "swa_grid_set_strip_rows",
     "swa_grid_arrays",
     "swa_adjoint_workspace_bytes", "swa_create_adjoint", "swa_destroy_adjoint",
     "swa_adjoint_info", "swa_step_adjoint", "swa_get_adjoint_state",
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH):
         "swa_step_forward": ([_V, _I, _D, _V], _I),
         "swa_get_time": ([_V, _P(_D), _P(_D), _P(ctypes.c_longlong), _V], _I),
         "swa_grid_arrays": ([_V, _P(_V), _P(_V), _P(_V), _P(_V), _V], _I),
+        "swa_grid_set_strip_rows": ([_V, _I], _I),
         "swa_adjoint_workspace_bytes": ([D], _SZ),
         "swa_create_adjoint": ([D, _V, _V, _D, _V, _SZ, _V, _P(_V)], _I),
         "swa_destroy_adjoint": ([_V], _I),
@@ -202,6 +204,10 @@ def swa_get_time(h, stream=None):
     _chk(load().swa_get_time(h, ctypes.byref(t), ctypes.byref(dt), ctypes.byref(n),
                              _stream(stream)))
     return t.value, dt.value, n.value
+
+
+def swa_grid_set_strip_rows(h, rows):
+    return _chk(load().swa_grid_set_strip_rows(h, int(rows)))
 
 
 def swa_grid_arrays(h, stream=None):
