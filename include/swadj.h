@@ -233,6 +233,60 @@ int swa_flag_cells(const swa_grid *grid, const swa_snapstore *store,
 int swa_gauge_sample(const swa_grid *grid, int n, const double *xy_dev,
                      double *eta_dev, void *stream);
 
+/* ======================= batched uneven patches ===========================
+ * Many independent patches of refinement levels 1..SWA_MAX_LEVELS stepped
+ * together (the AMR hierarchy of Sec. 1 and Sec. 6 holds patches on levels
+ * with refinement ratios; here each patch is self-contained, with ghost
+ * cells from its own boundary conditions and no exchange between patches).
+ * FP32 perturbation form only.  One swa_step_level call enqueues one
+ * persistent kernel launch per step that walks the tiles of every patch of
+ * that level; all patches of a level share one time step, reduced on the
+ * device from their CFL maxima (dt_l = cfl / max over the level's cells),
+ * so a loop of level steps can be captured in a CUDA graph.
+ */
+#define SWA_MAX_LEVELS 8
+
+typedef struct swa_patch_desc {
+    int level;              /* 1 .. SWA_MAX_LEVELS                          */
+    int nx, ny;             /* cells, each >= 2                              */
+    double x_lo, y_lo;      /* lower-left corner                             */
+    double dx, dy;          /* cell size; equal for all patches of a level   */
+} swa_patch_desc;
+
+typedef struct swa_patchset swa_patchset;
+
+/* common: g, cfl, dry_tol, order, bc of every patch (ndim, nx, ny, x_lo,
+ * y_lo, dx, dy and precision of `common` are ignored). */
+size_t swa_patches_workspace_bytes(int n, const swa_patch_desc *patches,
+                                   const swa_grid_desc *common);
+/* bathy_host[k]: nx*ny bottom elevations of patch k (host FP64, copied).
+ * The state starts as the ocean at rest. */
+int swa_create_patches(int n, const swa_patch_desc *patches,
+                       const double *const *bathy_host, const swa_grid_desc *common,
+                       void *ws, size_t ws_bytes, void *stream, swa_patchset **out);
+int swa_destroy_patches(swa_patchset *ps);
+/* Set patch k from FP64 eta, hu, hv (host or device). */
+int swa_patches_set_state(swa_patchset *ps, int k, const double *eta,
+                          const double *hu, const double *hv, int where,
+                          void *stream);
+/* Restart the clock of `level` at time t, its first step from the CFL
+ * condition of the level's current state (call after setting its patches). */
+int swa_patches_start_level(swa_patchset *ps, int level, double t, void *stream);
+/* Read patch k as FP64 (any pointer may be NULL); where = SWA_HOST syncs. */
+int swa_patches_get_state(swa_patchset *ps, int k, double *h, double *hu,
+                          double *hv, double *eta, int where, void *stream);
+/* nsteps level steps, each stopping at t_end (steps past it are no-ops). */
+int swa_step_level(swa_patchset *ps, int level, int nsteps, double t_end,
+                   void *stream);
+/* Synchronises; any pointer may be NULL. */
+int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next,
+                         long long *nsteps, void *stream);
+/* Number of patches, tiles and cells of a level (host bookkeeping). */
+int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches,
+                           int *ntiles, long long *ncells);
+/* Tile height of the level's kernel: 8 or 16 (0 = default 16). */
+int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
+
 /* ======================= allocation-free forward step =====================
  * The paper has no counterpart to this entry point; it is an integration aid.
  *

@@ -14,6 +14,11 @@
 
 namespace swadj {
 
+// Division: IEEE in double (the FP64 path rounds like the reference), a
+// fast reciprocal-multiply in float.
+__device__ __forceinline__ double adj_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float adj_div(float a, float b) { return __fdividef(a, b); }
+
 template <typename R>
 struct AdjWave {
     R b1, b2, cL, cR;
@@ -35,8 +40,8 @@ __device__ __forceinline__ AdjWave<R> adj_riemann(R eL, R mL, R cL, R ghL, R eR,
     const R F1R = -(ghR * mR), F2R = -eR;
     const R d1 = F1R - F1L, d2 = F2R - F2L;
     const R s = cL + cR;
-    w.b1 = (d1 + cR * d2) / s;
-    w.b2 = (cL * d2 - d1) / s;
+    w.b1 = adj_div(d1 + cR * d2, s);
+    w.b2 = adj_div(cL * d2 - d1, s);
     w.cL = cL;
     w.cR = cR;
     return w;
@@ -59,7 +64,7 @@ __device__ __forceinline__ void adj_flux(const AdjWave<R> &wm, const AdjWave<R> 
         const R U[2] = {wp.b1 * wp.cL, wp.b1};
         const R zz = Z1[0] * Z1[0] + Z1[1] * Z1[1];
         R th = R(0);
-        if (zz != R(0)) th = (U[0] * Z1[0] + U[1] * Z1[1]) / zz;
+        if (zz != R(0)) th = adj_div(U[0] * Z1[0] + U[1] * Z1[1], zz);
         const R coef = R(0.5) * R(-1) * (R(1) - nu * w.cL) * mc_phi(th);
         F[0] += coef * Z1[0];
         F[1] += coef * Z1[1];
@@ -68,7 +73,7 @@ __device__ __forceinline__ void adj_flux(const AdjWave<R> &wm, const AdjWave<R> 
         const R U[2] = {-wm.b2 * wm.cR, wm.b2};
         const R zz = Z2[0] * Z2[0] + Z2[1] * Z2[1];
         R th = R(0);
-        if (zz != R(0)) th = (U[0] * Z2[0] + U[1] * Z2[1]) / zz;
+        if (zz != R(0)) th = adj_div(U[0] * Z2[0] + U[1] * Z2[1], zz);
         const R coef = R(0.5) * (R(1) - nu * w.cR) * mc_phi(th);
         F[0] += coef * Z2[0];
         F[1] += coef * Z2[1];

@@ -101,8 +101,7 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
         p.q[cur ^ 1][1][i] = nmu;
         const float hn = h[2] + d0;
         bad = !(hn > 0.f) || !isfinite(nmu);
-        const float q = rsqrtf(hn), gh = g * hn;
-        sm = (fabsf(nmu) * q * q + gh * rsqrtf(gh)) / p.dx;
+        sm = cfl_f32(hn, nmu, 0.f, g, 1.f / p.dx, 1.f / p.dy, 0);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,

@@ -41,6 +41,17 @@ __device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
 // Fluctuations amdq (to the left cell), apdq (to the right cell) and the
 // second-order correction flux F at edge e, from the waves at e and at its
 // left/right neighbour edges (indices into wave arrays W[6][stride]).
+// CFL number of one FP32 cell, the same expression wherever the FP32 path
+// reduces it: (|hu|/h + c)/dx + (|hv|/h + c)/dy, c = sqrt(g h).
+__device__ __forceinline__ float cfl_f32(float h, float hu, float hv, float g, float rdx,
+                                         float rdy, int two_d) {
+    const float q = rsqrtf(h), ih = q * q;
+    const float gh = g * h, cc = gh * rsqrtf(gh);
+    float s = (fabsf(hu) * ih + cc) * rdx;
+    if (two_d) s += (fabsf(hv) * ih + cc) * rdy;
+    return s;
+}
+
 template <typename R>
 struct Wave6 {
     R uh, ch, b1, b2, b3, vh;
@@ -256,10 +267,17 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
     double mx = 0.0;
     for (size_t k = (size_t)blockIdx.x * 256 + tid; k < n; k += (size_t)gridDim.x * 256) {
         const R h = PERT ? q0[k] + p.bath[k] : q0[k];
-        const R c = sqrt(p.g * h);
-        R s = (fabs(q1[k] / h) + c) / p.dx;
-        if (p.two_d) s += (fabs(q2[k] / h) + c) / p.dy;
-        double sd = (double)s;
+        double sd;
+        if (PERT) {
+            // the float rule of the fused step reduction (cfl_f32)
+            sd = (double)cfl_f32((float)h, (float)q1[k], p.two_d ? (float)q2[k] : 0.f,
+                                 (float)p.g, 1.f / (float)p.dx, 1.f / (float)p.dy, p.two_d);
+        } else {
+            const R c = sqrt(p.g * h);
+            R s = (fabs(q1[k] / h) + c) / p.dx;
+            if (p.two_d) s += (fabs(q2[k] / h) + c) / p.dy;
+            sd = (double)s;
+        }
         if (!(h > R(0))) atomicOr(p.err, ERR_UNSTABLE);
         mx = sd > mx ? sd : mx;
     }

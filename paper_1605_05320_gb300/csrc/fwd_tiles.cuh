@@ -297,9 +297,7 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
             V.o2[o] = nmv;
             const float h = own_h[k] + d0;
             bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
-            const float q = rsqrtf(h), ih = q * q;
-            const float gh = g * h, cc = gh * rsqrtf(gh);
-            smax = fmaxf(smax, (fabsf(nmu) * ih + cc) * rdx + (fabsf(nmv) * ih + cc) * rdy);
+            smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
         }
     }
     __syncthreads();  // the next tile overwrites the shared buffers

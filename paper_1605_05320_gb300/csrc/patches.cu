@@ -1,0 +1,492 @@
+// patches.cu -- batched uneven patches: one persistent launch per level step.
+//
+// Every patch of a level is cut into TX x TY tiles; the level's tile list
+// (patch, i0, j0) is built on the host at creation and kept on the device.
+// A level step runs the FP32 tile machinery of fwd_tiles.cuh over that list
+// with one block per SM slot, so small and large patches share the launch and
+// the tail of small patches does not leave SMs idle.  The level's clock
+// (time, step, buffer parity, next dt from the fused CFL reduction) lives on
+// the device, as for a single grid.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "fwd_tiles.cuh"
+
+namespace swadj {
+namespace patches {
+
+constexpr int TX = 32;
+constexpr int kMaxBlocks = 4096;  // reduction slots per level
+
+struct PatchDevice {
+    float *q[2][3];
+    const float *hb;
+    int nx, ny;
+    float dx, dy;
+    BcSpec bc;
+};
+
+struct LevelParams {
+    const PatchDevice *table;
+    const int4 *tiles;
+    int ntiles;
+    DevClock *clk;
+    double *partial;
+    int nblocks;
+    double t_end, cfl, dx, dy;
+    float g;
+    int order;
+    int *err;
+};
+
+struct PatchTiles {
+    const PatchDevice *table;
+    const int4 *tiles;
+    int n, cur;
+    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ void get(int k, tile::View &v, int &i0, int &j0) const {
+        const int4 t = tiles[k];
+        const PatchDevice &P = table[t.x];
+        v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
+        v.o0 = P.q[cur ^ 1][0]; v.o1 = P.q[cur ^ 1][1]; v.o2 = P.q[cur ^ 1][2];
+        v.nx = P.nx; v.ny = P.ny; v.dx = P.dx; v.dy = P.dy; v.bc = P.bc;
+        i0 = t.y;
+        j0 = t.z;
+    }
+};
+
+template <int TY>
+__global__ void __launch_bounds__(256) level_step_kernel(LevelParams p) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    tile::Smem<TX, TY> &S = *reinterpret_cast<tile::Smem<TX, TY> *>(dsm);
+    __shared__ float s_nu[2];
+    __shared__ int s_cur, s_run;
+    __shared__ float red[8];
+    __shared__ int am_last;
+    double t_now = 0.0, dt = 0.0;
+    if (!tile::begin_step(p.clk, p.t_end, p.dx, p.dy, s_nu, &s_cur, &s_run, t_now, dt)) return;
+    PatchTiles src{p.table, p.tiles, p.ntiles, s_cur};
+    bool bad = false;
+    const float sm = tile::run_tiles<TX, TY>(S, src, s_nu[0], s_nu[1], p.g, p.order, bad);
+    if (bad) atomicOr(p.err, ERR_UNSTABLE);
+    tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,
+                           s_cur);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
+    atomicMax((unsigned long long *)a, (unsigned long long)__double_as_longlong(v));
+}
+
+// CFL maximum of buffer 0 of every patch of the level (same per-cell rule as
+// the step's fused reduction), into *smax.
+__global__ void level_smax_kernel(LevelParams p, int TYr, double *smax) {
+    float m = 0.f;
+    for (int k = blockIdx.x; k < p.ntiles; k += gridDim.x) {
+        const int4 t = p.tiles[k];
+        const PatchDevice &P = p.table[t.x];
+        for (int c = threadIdx.x; c < TX * TYr; c += blockDim.x) {
+            const int i = t.y + c % TX, j = t.z + c / TX;
+            if (i >= P.nx || j >= P.ny) continue;
+            const size_t o = (size_t)j * P.nx + i;
+            const float h = P.q[0][0][o] + P.hb[o];
+            const float s = cfl_f32(h, P.q[0][1][o], P.q[0][2][o], p.g, 1.f / P.dx,
+                                    1.f / P.dy, 1);
+            if (!(h > 0.f)) atomicOr(p.err, ERR_UNSTABLE);
+            m = fmaxf(m, s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(smax, (double)m);
+}
+
+__global__ void level_clock_kernel(DevClock *clk, const double *smax, double t0, double cfl) {
+    clk->t = t0;
+    clk->smax = *smax;
+    clk->dt_cfl = cfl / *smax;
+    clk->cur = 0;
+    clk->nsteps = 0;
+    clk->ticket = 0u;
+}
+
+__global__ void to_float_kernel(const double *src, float *dst, const double *sub, int negate,
+                                size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        double v = src[k];
+        if (sub) v = v - sub[k];
+        if (negate) v = -v;
+        dst[k] = (float)v;
+    }
+}
+
+__global__ void to_double_kernel(const float *src, const float *add, double *dst, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        double v = (double)src[k];
+        if (add) v = v + (double)add[k];
+        dst[k] = v;
+    }
+}
+
+unsigned ew_blocks(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b));
+}
+
+struct Level {
+    int npatches = 0, ntiles16 = 0, ntiles8 = 0;
+    long long ncells = 0;
+    double dx = 0, dy = 0;
+    int4 *tiles16 = nullptr, *tiles8 = nullptr;
+    DevClock *clk = nullptr;
+    double *partial = nullptr;
+    double *smax = nullptr;
+    int rows = 0;
+    bool started = false;
+};
+
+template <int TY>
+int occupancy_blocks() {
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(level_step_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(tile::Smem<TX, TY>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_step_kernel<TY>, 256,
+                                                      sizeof(tile::Smem<TX, TY>));
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+    }
+    const int b = per_sm * sms;
+    return b < kMaxBlocks ? b : kMaxBlocks;
+}
+
+}  // namespace patches
+}  // namespace swadj
+
+using namespace swadj;
+using namespace swadj::patches;
+using swadj_host::cuda_check;
+using swadj_host::set_error;
+
+struct swa_patchset {
+    int n = 0;
+    swa_grid_desc common;
+    std::vector<swa_patch_desc> pd;
+    std::vector<PatchDevice> host_table;
+    PatchDevice *table = nullptr;
+    double *staging = nullptr;
+    size_t staging_n = 0;
+    Level lev[SWA_MAX_LEVELS + 1];
+};
+
+#define TRY(x)                          \
+    do {                                \
+        int _rc = (x);                  \
+        if (_rc != SWA_OK) return _rc;  \
+    } while (0)
+
+namespace {
+
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(void *b) : base((char *)b) {}
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+int check_patches(int n, const swa_patch_desc *p, const swa_grid_desc *c) {
+    if (n < 1 || !p || !c) return set_error(SWA_EINVAL, "need n >= 1 patches and a common descriptor");
+    double ldx[SWA_MAX_LEVELS + 1] = {0}, ldy[SWA_MAX_LEVELS + 1] = {0};
+    for (int k = 0; k < n; k++) {
+        if (p[k].level < 1 || p[k].level > SWA_MAX_LEVELS)
+            return set_error(SWA_EINVAL, "patch %d: level must be in [1, %d]", k, SWA_MAX_LEVELS);
+        if (p[k].nx < 2 || p[k].ny < 2) return set_error(SWA_EINVAL, "patch %d: nx, ny must be >= 2", k);
+        if (!(p[k].dx > 0) || !(p[k].dy > 0)) return set_error(SWA_EINVAL, "patch %d: dx, dy must be > 0", k);
+        const int l = p[k].level;
+        if (ldx[l] == 0) { ldx[l] = p[k].dx; ldy[l] = p[k].dy; }
+        else if (ldx[l] != p[k].dx || ldy[l] != p[k].dy)
+            return set_error(SWA_EINVAL, "patch %d: cell size differs from level %d's", k, l);
+    }
+    if (c->order != 1 && c->order != 2) return set_error(SWA_EINVAL, "order must be 1 or 2");
+    for (int k = 0; k < 4; k++)
+        if (c->bc[k] != SWA_BC_EXTRAP && c->bc[k] != SWA_BC_WALL)
+            return set_error(SWA_EINVAL, "bad boundary condition");
+    if (!(c->g > 0) || !(c->cfl > 0) || !(c->cfl <= 1.0)) return set_error(SWA_EINVAL, "need g > 0, 0 < cfl <= 1");
+    return SWA_OK;
+}
+
+void tiles_of(const swa_patch_desc &p, int k, int TY, std::vector<int4> &out) {
+    for (int j0 = 0; j0 < p.ny; j0 += TY)
+        for (int i0 = 0; i0 < p.nx; i0 += patches::TX) out.push_back(make_int4(k, i0, j0, 0));
+}
+
+void layout(int n, const swa_patch_desc *p, Carve &c, swa_patchset *ps) {
+    size_t maxn = 0;
+    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t8[SWA_MAX_LEVELS + 1];
+    for (int k = 0; k < n; k++) {
+        const size_t nn = (size_t)p[k].nx * p[k].ny;
+        if (nn > maxn) maxn = nn;
+        tiles_of(p[k], k, 16, t16[p[k].level]);
+        tiles_of(p[k], k, 8, t8[p[k].level]);
+    }
+    PatchDevice *table = (PatchDevice *)c.take(sizeof(PatchDevice) * n);
+    double *staging = (double *)c.take(maxn * 8);
+    if (ps) {
+        ps->table = table;
+        ps->staging = staging;
+        ps->staging_n = maxn;
+        ps->host_table.resize(n);
+    }
+    for (int k = 0; k < n; k++) {
+        const size_t nn = (size_t)p[k].nx * p[k].ny;
+        PatchDevice d{};
+        for (int b = 0; b < 2; b++)
+            for (int m = 0; m < 3; m++) d.q[b][m] = (float *)c.take(nn * 4);
+        d.hb = (const float *)c.take(nn * 4);
+        if (ps) {
+            d.nx = p[k].nx; d.ny = p[k].ny;
+            d.dx = (float)p[k].dx; d.dy = (float)p[k].dy;
+            d.bc = BcSpec{ps->common.bc[0], ps->common.bc[1], ps->common.bc[2], ps->common.bc[3]};
+            ps->host_table[k] = d;
+        }
+    }
+    for (int l = 1; l <= SWA_MAX_LEVELS; l++) {
+        int4 *a = (int4 *)c.take(sizeof(int4) * (t16[l].size() + 1));
+        int4 *b = (int4 *)c.take(sizeof(int4) * (t8[l].size() + 1));
+        DevClock *clk = (DevClock *)c.take(sizeof(DevClock));
+        double *part = (double *)c.take(8 * kMaxBlocks);
+        double *smax = (double *)c.take(8);
+        if (ps) {
+            Level &L = ps->lev[l];
+            L.tiles16 = a; L.tiles8 = b; L.clk = clk; L.partial = part; L.smax = smax;
+            L.ntiles16 = (int)t16[l].size();
+            L.ntiles8 = (int)t8[l].size();
+        }
+    }
+}
+
+}  // namespace
+
+static LevelParams level_params(const swa_patchset *ps, int l, double t_end, int &TY) {
+    const Level &L = ps->lev[l];
+    TY = L.rows == 8 ? 8 : 16;
+    LevelParams p{};
+    p.table = ps->table;
+    p.tiles = TY == 8 ? L.tiles8 : L.tiles16;
+    p.ntiles = TY == 8 ? L.ntiles8 : L.ntiles16;
+    p.clk = L.clk;
+    p.partial = L.partial;
+    p.t_end = t_end;
+    p.cfl = ps->common.cfl;
+    p.dx = L.dx;
+    p.dy = L.dy;
+    p.g = (float)ps->common.g;
+    p.order = ps->common.order;
+    p.err = swadj_host::error_word();
+    return p;
+}
+
+extern "C" {
+
+size_t swa_patches_workspace_bytes(int n, const swa_patch_desc *patches,
+                                   const swa_grid_desc *common) {
+    if (check_patches(n, patches, common) != SWA_OK) return 0;
+    Carve c(nullptr);
+    layout(n, patches, c, nullptr);
+    return c.off + 256;
+}
+
+int swa_create_patches(int n, const swa_patch_desc *patches, const double *const *bathy_host,
+                       const swa_grid_desc *common, void *ws, size_t ws_bytes, void *stream,
+                       swa_patchset **out) {
+    TRY(check_patches(n, patches, common));
+    if (!bathy_host || !ws || !out) return set_error(SWA_EINVAL, "null argument");
+    if (((uintptr_t)ws & 255) != 0) return set_error(SWA_EINVAL, "workspace must be 256-byte aligned");
+    const size_t need = swa_patches_workspace_bytes(n, patches, common);
+    if (ws_bytes < need)
+        return set_error(SWA_ENOMEM, "patch workspace %zu bytes < %zu needed", ws_bytes, need);
+    swa_patchset *ps = new (std::nothrow) swa_patchset();
+    if (!ps) return set_error(SWA_ENOMEM, "host allocation failed");
+    ps->n = n;
+    ps->common = *common;
+    ps->pd.assign(patches, patches + n);
+    Carve c(ws);
+    layout(n, patches, c, ps);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = cuda_check(cudaMemsetAsync(ws, 0, need - 256, st), "workspace clear");
+    // per-level bookkeeping and tile lists
+    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t8[SWA_MAX_LEVELS + 1];
+    for (int k = 0; k < n; k++) {
+        Level &L = ps->lev[patches[k].level];
+        L.npatches++;
+        L.ncells += (long long)patches[k].nx * patches[k].ny;
+        L.dx = patches[k].dx;
+        L.dy = patches[k].dy;
+        tiles_of(patches[k], k, 16, t16[patches[k].level]);
+        tiles_of(patches[k], k, 8, t8[patches[k].level]);
+    }
+    for (int l = 1; l <= SWA_MAX_LEVELS && rc == SWA_OK; l++) {
+        Level &L = ps->lev[l];
+        if (L.npatches == 0) continue;
+        rc = cuda_check(cudaMemcpyAsync(L.tiles16, t16[l].data(), sizeof(int4) * t16[l].size(),
+                                        cudaMemcpyHostToDevice, st), "tile list upload");
+        if (rc == SWA_OK)
+            rc = cuda_check(cudaMemcpyAsync(L.tiles8, t8[l].data(), sizeof(int4) * t8[l].size(),
+                                            cudaMemcpyHostToDevice, st), "tile list upload");
+    }
+    if (rc == SWA_OK)
+        rc = cuda_check(cudaMemcpyAsync(ps->table, ps->host_table.data(),
+                                        sizeof(PatchDevice) * n, cudaMemcpyHostToDevice, st),
+                        "patch table upload");
+    // bathymetry -> hbar, state -> ocean at rest (eta = 0, zero momenta from the clear)
+    for (int k = 0; k < n && rc == SWA_OK; k++) {
+        const size_t nn = (size_t)patches[k].nx * patches[k].ny;
+        if (!bathy_host[k]) { rc = set_error(SWA_EINVAL, "null bathymetry for patch %d", k); break; }
+        rc = cuda_check(cudaMemcpyAsync(ps->staging, bathy_host[k], nn * 8,
+                                        cudaMemcpyHostToDevice, st), "bathymetry upload");
+        if (rc != SWA_OK) break;
+        to_float_kernel<<<ew_blocks(nn), 256, 0, st>>>(ps->staging, (float *)ps->host_table[k].hb,
+                                                        nullptr, 1, nn);
+        rc = cuda_check(cudaGetLastError(), "bathymetry convert");
+    }
+    if (rc == SWA_OK) rc = cuda_check(cudaStreamSynchronize(st), "create_patches");
+    if (rc != SWA_OK) { delete ps; return rc; }
+    *out = ps;
+    return SWA_OK;
+}
+
+int swa_destroy_patches(swa_patchset *ps) {
+    delete ps;
+    return SWA_OK;
+}
+
+int swa_patches_set_state(swa_patchset *ps, int k, const double *eta, const double *hu,
+                          const double *hv, int where, void *stream) {
+    if (!ps || k < 0 || k >= ps->n || !eta || !hu || !hv) return set_error(SWA_EINVAL, "bad argument");
+    if (where != SWA_HOST && where != SWA_DEVICE) return set_error(SWA_EINVAL, "bad where");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nn = (size_t)ps->pd[k].nx * ps->pd[k].ny;
+    const double *src[3] = {eta, hu, hv};
+    for (int m = 0; m < 3; m++) {
+        const double *s = src[m];
+        if (where == SWA_HOST) {
+            TRY(cuda_check(cudaMemcpyAsync(ps->staging, s, nn * 8, cudaMemcpyHostToDevice, st),
+                           "state upload"));
+            s = ps->staging;
+        }
+        to_float_kernel<<<ew_blocks(nn), 256, 0, st>>>(s, ps->host_table[k].q[0][m], nullptr, 0, nn);
+        TRY(cuda_check(cudaGetLastError(), "state convert"));
+    }
+    ps->lev[ps->pd[k].level].started = false;
+    return SWA_OK;
+}
+
+int swa_patches_start_level(swa_patchset *ps, int level, double t, void *stream) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    Level &L = ps->lev[level];
+    if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
+    cudaStream_t st = (cudaStream_t)stream;
+    int TY;
+    LevelParams p = level_params(ps, level, 0.0, TY);
+    TRY(cuda_check(cudaMemsetAsync(L.smax, 0, 8, st), "smax clear"));
+    int blocks = p.ntiles < 2048 ? p.ntiles : 2048;
+    level_smax_kernel<<<blocks, 256, 0, st>>>(p, TY, L.smax);
+    TRY(cuda_check(cudaGetLastError(), "level_smax_kernel"));
+    level_clock_kernel<<<1, 1, 0, st>>>(L.clk, L.smax, t, ps->common.cfl);
+    TRY(cuda_check(cudaGetLastError(), "level_clock_kernel"));
+    L.started = true;
+    return SWA_OK;
+}
+
+int swa_patches_get_state(swa_patchset *ps, int k, double *h, double *hu, double *hv,
+                          double *eta, int where, void *stream) {
+    if (!ps || k < 0 || k >= ps->n) return set_error(SWA_EINVAL, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevClock clk;
+    TRY(cuda_check(cudaMemcpyAsync(&clk, ps->lev[ps->pd[k].level].clk, sizeof(clk),
+                                   cudaMemcpyDeviceToHost, st), "clock read"));
+    TRY(cuda_check(cudaStreamSynchronize(st), "clock read"));
+    const int cur = clk.cur;
+    const size_t nn = (size_t)ps->pd[k].nx * ps->pd[k].ny;
+    double *dst[4] = {h, hu, hv, eta};
+    const PatchDevice &P = ps->host_table[k];
+    for (int m = 0; m < 4; m++) {
+        if (!dst[m]) continue;
+        double *d = where == SWA_HOST ? ps->staging : dst[m];
+        const float *src = P.q[cur][m == 3 ? 0 : m];
+        to_double_kernel<<<ew_blocks(nn), 256, 0, st>>>(src, m == 0 ? P.hb : nullptr, d, nn);
+        TRY(cuda_check(cudaGetLastError(), "state convert"));
+        if (where == SWA_HOST) {
+            TRY(cuda_check(cudaMemcpyAsync(dst[m], ps->staging, nn * 8, cudaMemcpyDeviceToHost, st),
+                           "state download"));
+            TRY(cuda_check(cudaStreamSynchronize(st), "state download"));
+        }
+    }
+    return SWA_OK;
+}
+
+int swa_step_level(swa_patchset *ps, int level, int nsteps, double t_end, void *stream) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    Level &L = ps->lev[level];
+    if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
+    if (!L.started) return set_error(SWA_ESTATE, "level %d not started", level);
+    if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    int TY;
+    LevelParams p = level_params(ps, level, t_end, TY);
+    if (TY == 8) {
+        p.nblocks = occupancy_blocks<8>();
+        if (p.nblocks > p.ntiles) p.nblocks = p.ntiles;
+        for (int s = 0; s < nsteps; s++)
+            level_step_kernel<8><<<p.nblocks, 256, sizeof(tile::Smem<TX, 8>), st>>>(p);
+    } else {
+        p.nblocks = occupancy_blocks<16>();
+        if (p.nblocks > p.ntiles) p.nblocks = p.ntiles;
+        for (int s = 0; s < nsteps; s++)
+            level_step_kernel<16><<<p.nblocks, 256, sizeof(tile::Smem<TX, 16>), st>>>(p);
+    }
+    return cuda_check(cudaGetLastError(), "level_step_kernel");
+}
+
+int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next,
+                         long long *nsteps, void *stream) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    DevClock clk;
+    TRY(cuda_check(cudaMemcpyAsync(&clk, ps->lev[level].clk, sizeof(clk), cudaMemcpyDeviceToHost,
+                                   (cudaStream_t)stream), "clock read"));
+    TRY(cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "clock read"));
+    if (t) *t = clk.t;
+    if (dt_next) *dt_next = clk.dt_cfl;
+    if (nsteps) *nsteps = clk.nsteps;
+    return SWA_OK;
+}
+
+int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches, int *ntiles,
+                           long long *ncells) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    const Level &L = ps->lev[level];
+    if (npatches) *npatches = L.npatches;
+    if (ntiles) *ntiles = L.rows == 8 ? L.ntiles8 : L.ntiles16;
+    if (ncells) *ncells = L.ncells;
+    return SWA_OK;
+}
+
+int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    if (rows != 0 && rows != 8 && rows != 16) return set_error(SWA_EINVAL, "tile rows must be 0, 8 or 16");
+    ps->lev[level].rows = rows;
+    return SWA_OK;
+}
+
+}  // extern "C"

@@ -41,6 +41,10 @@ EXPORTS = [
     "swa_snapstore_info",
     "swa_flag_cells", "swa_gauge_sample",
     "swa_step_forward_static",
+    "swa_patches_workspace_bytes", "swa_create_patches", "swa_destroy_patches",
+    "swa_patches_set_state", "swa_patches_start_level", "swa_patches_get_state",
+    "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
+    "swa_patches_set_tile_rows",
 ]
 
 
@@ -58,6 +62,12 @@ class swa_grid_desc(ctypes.Structure):
                 ("bc", ctypes.c_int * 4),
                 ("g", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("dry_tol", ctypes.c_double)]
+
+
+class swa_patch_desc(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x_lo", ctypes.c_double), ("y_lo", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double)]
 
 
 def make_desc(ndim, nx, ny, x_lo, y_lo, dx, dy, precision=SWA_FP64, order=2,
@@ -120,6 +130,16 @@ def load(path: str = LIB_PATH):
         "swa_flag_cells": ([_V, _V, _D, _D, _D, _I, _V, _V, _V, _V], _I),
         "swa_gauge_sample": ([_V, _I, _V, _V, _V], _I),
         "swa_step_forward_static": ([D, _P(_V), _P(_V), _V, _D, _V, _V], _I),
+        "swa_patches_workspace_bytes": ([_I, _V, D], _SZ),
+        "swa_create_patches": ([_I, _V, _P(_V), D, _V, _SZ, _V, _P(_V)], _I),
+        "swa_destroy_patches": ([_V], _I),
+        "swa_patches_set_state": ([_V, _I, _V, _V, _V, _I, _V], _I),
+        "swa_patches_start_level": ([_V, _I, _D, _V], _I),
+        "swa_patches_get_state": ([_V, _I, _V, _V, _V, _V, _I, _V], _I),
+        "swa_step_level": ([_V, _I, _I, _D, _V], _I),
+        "swa_patches_get_time": ([_V, _I, _P(_D), _P(_D), _P(ctypes.c_longlong), _V], _I),
+        "swa_patches_level_info": ([_V, _I, _P(_I), _P(_I), _P(ctypes.c_longlong)], _I),
+        "swa_patches_set_tile_rows": ([_V, _I, _I], _I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -309,6 +329,73 @@ def swa_step_forward_static(desc, q_in, q_out, bath, dt, smax_out_dev=None, stre
                                                _stream(stream)))
 
 
+def _patch_array(patches):
+    arr = (swa_patch_desc * len(patches))()
+    for k, p in enumerate(patches):
+        lev, x0, y0, nx, ny, dx, dy = p
+        arr[k].level, arr[k].nx, arr[k].ny = int(lev), int(nx), int(ny)
+        arr[k].x_lo, arr[k].y_lo, arr[k].dx, arr[k].dy = float(x0), float(y0), float(dx), float(dy)
+    return arr
+
+
+def swa_patches_workspace_bytes(patches, common):
+    arr = _patch_array(patches)
+    return int(load().swa_patches_workspace_bytes(len(patches), ctypes.cast(arr, _V),
+                                                  ctypes.byref(common)))
+
+
+def swa_create_patches(patches, bathy_list, common, ws, ws_bytes, stream=None):
+    arr = _patch_array(patches)
+    bl = [np.ascontiguousarray(b, dtype=np.float64) for b in bathy_list]
+    ptrs = (_V * len(bl))(*[b.ctypes.data for b in bl])
+    out = _V()
+    _chk(load().swa_create_patches(len(patches), ctypes.cast(arr, _V), ptrs,
+                                   ctypes.byref(common), _ptr(ws), ws_bytes,
+                                   _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def swa_destroy_patches(h):
+    return _chk(load().swa_destroy_patches(h))
+
+
+def swa_patches_set_state(h, k, eta, hu, hv, where, stream=None):
+    return _chk(load().swa_patches_set_state(h, int(k), _ptr(eta), _ptr(hu), _ptr(hv), where,
+                                             _stream(stream)))
+
+
+def swa_patches_start_level(h, level, t=0.0, stream=None):
+    return _chk(load().swa_patches_start_level(h, int(level), float(t), _stream(stream)))
+
+
+def swa_patches_get_state(h, k, hh, hu, hv, eta, where, stream=None):
+    return _chk(load().swa_patches_get_state(h, int(k), _ptr(hh), _ptr(hu), _ptr(hv),
+                                             _ptr(eta), where, _stream(stream)))
+
+
+def swa_step_level(h, level, nsteps, t_end, stream=None):
+    return _chk(load().swa_step_level(h, int(level), int(nsteps), float(t_end),
+                                      _stream(stream)))
+
+
+def swa_patches_get_time(h, level, stream=None):
+    t, dt, n = _D(), _D(), ctypes.c_longlong()
+    _chk(load().swa_patches_get_time(h, int(level), ctypes.byref(t), ctypes.byref(dt),
+                                     ctypes.byref(n), _stream(stream)))
+    return t.value, dt.value, n.value
+
+
+def swa_patches_level_info(h, level):
+    a, b, c = _I(), _I(), ctypes.c_longlong()
+    _chk(load().swa_patches_level_info(h, int(level), ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def swa_patches_set_tile_rows(h, level, rows):
+    return _chk(load().swa_patches_set_tile_rows(h, int(level), int(rows)))
+
+
 # ------------------------------------------------- workspace-owning helpers
 def _workspace(nbytes, device):
     import torch
@@ -415,6 +502,50 @@ class SnapStore:
         try:
             if getattr(self, "h", None):
                 swa_destroy_snapstore(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class PatchSet:
+    """Batched patches; `patches` is a list of (level, x_lo, y_lo, nx, ny, dx, dy)."""
+
+    def __init__(self, patches, bathy_list, common, device="cuda", stream=None):
+        self.patches = list(patches)
+        self.nbytes = swa_patches_workspace_bytes(self.patches, common)
+        if self.nbytes == 0:
+            raise SwaError(SWA_EINVAL, swa_last_error())
+        self.ws = _workspace(self.nbytes, device)
+        self.h = swa_create_patches(self.patches, bathy_list, common, self.ws, self.nbytes,
+                                    stream)
+        self.levels = sorted({p[0] for p in self.patches})
+
+    def set_state(self, k, eta, hu, hv, stream=None):
+        if isinstance(eta, np.ndarray):
+            a = [np.ascontiguousarray(x, dtype=np.float64) for x in (eta, hu, hv)]
+            swa_patches_set_state(self.h, k, *a, SWA_HOST, stream)
+        else:
+            swa_patches_set_state(self.h, k, eta, hu, hv, SWA_DEVICE, stream)
+
+    def start(self, level, t=0.0, stream=None):
+        swa_patches_start_level(self.h, level, t, stream)
+
+    def step(self, level, nsteps, t_end=1e300, stream=None):
+        swa_step_level(self.h, level, nsteps, t_end, stream)
+
+    def get_state(self, k, stream=None):
+        lev, x0, y0, nx, ny, dx, dy = self.patches[k]
+        out = [np.zeros(nx * ny) for _ in range(4)]
+        swa_patches_get_state(self.h, k, *out, SWA_HOST, stream)
+        return dict(h=out[0], hu=out[1], hv=out[2], eta=out[3])
+
+    def time(self, level, stream=None):
+        return swa_patches_get_time(self.h, level, stream)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                swa_destroy_patches(self.h)
                 self.h = None
         except Exception:
             pass

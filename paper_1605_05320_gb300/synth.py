@@ -266,3 +266,15 @@ def config5_requests(seed: int = 2026, n: int = 512, rate: float = 20.0,
                     "width": float(rng.uniform(10e3, 60e3)),
                     "src_u": float(rng.uniform()), "src_v": float(rng.uniform())})
     return out
+
+
+def patch_fields(patch, L: float = 2048e3, seed: int = 1605, n_seamounts: int = 20,
+                 src=(700e3, 1024e3), amp: float = 1.0, width: float = 30e3):
+    """Bathymetry and initial surface of one patch (level, x_lo, y_lo, nx, ny,
+    dx, dy) sampled from the basin fields of the 2D configurations."""
+    lev, x0, y0, nx, ny, dx, dy = patch
+    g = GridSpec(2, nx, ny, x0, y0, dx, dy)
+    sm = seamounts(L, seed + 1, n_seamounts, 1600.0 / 2048.0)
+    B = basin_bathymetry(g, L, seed, n_seamounts, seamount_params=sm)
+    eta = gaussian_field(g, src[0], src[1], amp, width)
+    return B, eta
