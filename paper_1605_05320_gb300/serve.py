@@ -1,0 +1,235 @@
+"""Serving loop: many forward tsunami scenarios against one resident adjoint.
+
+One adjoint problem per target location (Sec. 2: one adjoint answers every
+forward problem with the same functional; Sec. 4: its snapshots are stored
+once) is solved at start-up and kept on the device with its snapshots.
+Scenario requests (grid size, source position, amplitude, width) arrive over
+time.  The loop admits a request when a slot is free and its device memory
+fits the HBM budget, gives each admitted scenario its own CUDA stream, and
+keeps enqueuing "macro steps" (10 forward steps, a gauge sample, one adjoint-
+weighted flag pass) round-robin over the active scenarios, so the work of
+requests that arrived at different times overlaps on the GPU (continuous
+batching).  Completion is detected by polling CUDA events, never by a
+device-wide synchronisation.  Results per request: gauge time series, flag
+counts per pass, latency (completion minus arrival).
+
+Everything on the numerical path runs in libswadj's kernels; this module only
+allocates workspaces (torch), orders work on streams and measures time.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import swadj as S
+from . import synth
+
+MACRO = 10          # forward steps per macro step (one flag pass each)
+AHEAD = 2           # macro steps kept in flight per scenario
+
+
+@dataclass
+class Request:
+    id: int
+    arrival: float
+    n: int
+    amp: float
+    width: float
+    src_u: float
+    src_v: float
+
+
+@dataclass
+class Result:
+    id: int
+    n: int
+    arrival: float
+    admitted: float
+    done: float
+    steps: int
+    gauges: np.ndarray
+    flag_counts: np.ndarray
+    latency: float = field(init=False)
+
+    def __post_init__(self):
+        self.latency = self.done - self.arrival
+
+
+class ResidentAdjoint:
+    """The adjoint for one target, solved once, snapshots kept on device."""
+
+    def __init__(self, n, L, t_f, t_s, tol, target, snaps=150, precision=S.SWA_FP32,
+                 seed=1605, n_seamounts=20, width=10e3):
+        dx = L / n
+        spec = synth.GridSpec(2, n, n, 0.0, 0.0, dx, dx)
+        sm = synth.seamounts(L, seed + 1, n_seamounts, 1600.0 / 2048.0)
+        B = synth.basin_bathymetry(spec, L, seed, n_seamounts, seamount_params=sm)
+        phi = np.zeros((3, spec.n))
+        phi[0] = synth.gaussian_field(spec, target[0], target[1], 1.0, width)
+        self.desc = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=precision)
+        self.adj = S.Adjoint(self.desc, B, phi, t_f)
+        N, dt, _ = self.adj.info()
+        every = max(1, math.ceil(N / (snaps - 1)))
+        self.store = S.SnapStore(self.adj, N // every + 3, precision)
+        self.store.run_adjoint(every)
+        self.t_f, self.t_s, self.tol = t_f, t_s, tol
+        self.L, self.seed, self.n_seamounts = L, seed, n_seamounts
+        self.bytes = self.adj.nbytes + self.store.nbytes
+
+
+class Scenario:
+    def __init__(self, req: Request, server: "Server", device):
+        import torch
+        self.req = req
+        L = server.adjoint.L
+        n = req.n
+        dx = L / n
+        self.desc = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=server.precision)
+        B = server.bathymetry(n)
+        self.stream = torch.cuda.Stream(device=device)
+        self.grid = S.Grid(self.desc, B, stream=self.stream)
+        self.t_f = server.adjoint.t_f
+        spec = synth.GridSpec(2, n, n, 0.0, 0.0, dx, dx)
+        sx = (0.1 + 0.6 * req.src_u) * L
+        sy = (0.1 + 0.8 * req.src_v) * L
+        eta = synth.gaussian_field(spec, sx, sy, req.amp, req.width)
+        z = np.zeros(spec.n)
+        self.grid.set_state(eta, z, z, 0.0, stream=self.stream)
+        _, dt0, _ = S.swa_get_time(self.grid.h, self.stream)
+        # macro steps to reach t_f with margin (steps past t_f are device no-ops)
+        self.n_macro = int(math.ceil(self.t_f / dt0 * 1.05 / MACRO)) + 1
+        ng = server.gauges.shape[0]
+        f64 = dict(dtype=torch.float64, device=device)
+        self.xy = torch.tensor(server.gauges, **f64)
+        self.series = torch.zeros((self.n_macro, ng), **f64)
+        self.counts = torch.zeros(self.n_macro, dtype=torch.int64, device=device)
+        self.flags = torch.zeros(spec.n, dtype=torch.uint8, device=device)
+        self.enqueued = 0
+        self.events = []
+        self.bytes = self.grid.nbytes + spec.n + self.series.numel() * 8
+
+    def enqueue_macro(self, server):
+        import torch
+        k = self.enqueued
+        st = self.stream
+        S.swa_step_forward(self.grid.h, MACRO, self.t_f, st)
+        S.swa_gauge_sample(self.grid.h, self.xy.shape[0], self.xy, self.series[k], st)
+        a = server.adjoint
+        S.swa_flag_cells(self.grid.h, a.store.h, a.t_s, a.t_f, a.tol, S.SWA_FLAG_INTERP,
+                         self.flags, None, self.counts[k], st)
+        ev = torch.cuda.Event()
+        ev.record(st)
+        self.events.append(ev)
+        self.enqueued += 1
+
+    def in_flight(self):
+        while self.events and self.events[0].query():
+            self.events.pop(0)
+        return len(self.events)
+
+    def finished(self):
+        return self.enqueued >= self.n_macro and self.in_flight() == 0
+
+
+class Server:
+    def __init__(self, adjoint: ResidentAdjoint, budget_bytes: float = 80e9,
+                 max_slots: int = 16, precision=S.SWA_FP32, n_gauges: int = 16,
+                 device="cuda", seed: int = 2026):
+        self.adjoint = adjoint
+        self.budget = budget_bytes
+        self.max_slots = max_slots
+        self.precision = precision
+        self.device = device
+        self._bathy = {}
+        rng = np.random.default_rng(seed)
+        L = adjoint.L
+        self.gauges = np.stack([rng.uniform(0.1 * L, 0.9 * L, n_gauges),
+                                rng.uniform(0.1 * L, 0.9 * L, n_gauges)], axis=1)
+
+    def bathymetry(self, n):
+        if n not in self._bathy:
+            a = self.adjoint
+            dx = a.L / n
+            spec = synth.GridSpec(2, n, n, 0.0, 0.0, dx, dx)
+            sm = synth.seamounts(a.L, a.seed + 1, a.n_seamounts, 1600.0 / 2048.0)
+            self._bathy[n] = synth.basin_bathymetry(spec, a.L, a.seed, a.n_seamounts,
+                                                    seamount_params=sm)
+        return self._bathy[n]
+
+    @staticmethod
+    def footprint(n, precision=S.SWA_FP32):
+        d = S.make_desc(2, n, n, 0.0, 0.0, 1.0, 1.0, precision=precision)
+        return S.swa_grid_workspace_bytes(d) + n * n
+
+    def run(self, requests, time_scale: float = 1.0, log=None):
+        """Serve `requests` (arrival times in seconds, compressed by
+        time_scale); returns (results, stats)."""
+        import torch
+        pending = sorted(requests, key=lambda r: r.arrival)
+        active = []
+        results = []
+        used = self.adjoint.bytes
+        t0 = time.perf_counter()
+        peak_active = 0
+        peak_bytes = used
+        while pending or active:
+            now = time.perf_counter() - t0
+            # admit
+            while (pending and pending[0].arrival * time_scale <= now
+                   and len(active) < self.max_slots
+                   and used + self.footprint(pending[0].n, self.precision) <= self.budget):
+                r = pending.pop(0)
+                sc = Scenario(r, self, self.device)
+                sc.admitted = time.perf_counter() - t0
+                used += sc.bytes
+                active.append(sc)
+            peak_active = max(peak_active, len(active))
+            peak_bytes = max(peak_bytes, used)
+            # keep every active scenario's queue topped up
+            progressed = False
+            for sc in active:
+                while sc.enqueued < sc.n_macro and sc.in_flight() < AHEAD:
+                    sc.enqueue_macro(self)
+                    progressed = True
+            # retire finished scenarios
+            still = []
+            for sc in active:
+                if sc.finished():
+                    done = time.perf_counter() - t0
+                    _, _, steps = S.swa_get_time(sc.grid.h, sc.stream)
+                    results.append(Result(sc.req.id, sc.req.n, sc.req.arrival * time_scale,
+                                          sc.admitted, done, steps,
+                                          sc.series.cpu().numpy(), sc.counts.cpu().numpy()))
+                    used -= sc.bytes
+                    if log:
+                        log(f"done {sc.req.id} n={sc.req.n} steps={steps} "
+                            f"latency={done - sc.req.arrival * time_scale:.3f}s")
+                else:
+                    still.append(sc)
+            active = still
+            if not progressed:
+                if active:
+                    active[0].events[0].synchronize() if active[0].events else None
+                elif pending:
+                    wait = pending[0].arrival * time_scale - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05))
+        wall = time.perf_counter() - t0
+        lat = np.array([r.latency for r in results])
+        stats = {"requests": len(results), "wall_s": wall,
+                 "scenarios_per_s": len(results) / wall if wall > 0 else 0.0,
+                 "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                 "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                 "peak_active": peak_active, "peak_bytes": peak_bytes,
+                 "cell_updates": float(sum(r.steps * r.n * r.n for r in results))}
+        stats["cell_updates_per_s"] = stats["cell_updates"] / wall if wall > 0 else 0.0
+        return results, stats
+
+
+def trace_from_config(n_req=512, rate=20.0, sizes=(512, 1024, 2048, 4096), seed=2026):
+    return [Request(r["id"], r["arrival"], r["n"], r["amp"], r["width"], r["src_u"],
+                    r["src_v"])
+            for r in synth.config5_requests(seed=seed, n=n_req, rate=rate, sizes=sizes)]
