@@ -233,3 +233,84 @@ def trace_from_config(n_req=512, rate=20.0, sizes=(512, 1024, 2048, 4096), seed=
     return [Request(r["id"], r["arrival"], r["n"], r["amp"], r["width"], r["src_u"],
                     r["src_v"])
             for r in synth.config5_requests(seed=seed, n=n_req, rate=rate, sizes=sizes)]
+
+
+def run_plain(adjoint: ResidentAdjoint, requests, precision=S.SWA_FP64, n_gauges=16,
+              device="cuda"):
+    """Plain per-grid runs, one request after another on one stream (no
+    admission, no overlap), in `precision`; returns (results, stats)."""
+    import torch
+    srv = Server(adjoint, precision=precision, n_gauges=n_gauges, device=device)
+    results = []
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        sc = Scenario(r, srv, device)
+        while sc.enqueued < sc.n_macro:
+            sc.enqueue_macro(srv)
+        sc.stream.synchronize()
+        _, _, steps = S.swa_get_time(sc.grid.h, sc.stream)
+        done = time.perf_counter() - t0
+        results.append(Result(r.id, r.n, 0.0, 0.0, done, steps, sc.series.cpu().numpy(),
+                              sc.counts.cpu().numpy()))
+        del sc
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    cu = float(sum(x.steps * x.n * x.n for x in results))
+    return results, {"requests": len(results), "wall_s": wall,
+                     "scenarios_per_s": len(results) / wall, "cell_updates": cu,
+                     "cell_updates_per_s": cu / wall}
+
+
+def main(argv=None):
+    """Serving benchmark: the served FP32 continuous-batching loop and the
+    plain per-grid FP64 form on the same request trace (basin workload,
+    resident 2048^2 adjoint with 150 FP32 snapshots).  Prints one JSON line."""
+    import argparse
+    import json
+
+    import torch
+    from . import build
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--sizes", default="512,1024")
+    ap.add_argument("--adjoint-n", type=int, default=2048)
+    ap.add_argument("--plain-requests", type=int, default=8)
+    a = ap.parse_args(argv)
+    build.build()
+    S.load()
+    sizes = tuple(int(x) for x in a.sizes.split(","))
+    L = 2048e3
+    sc2 = synth.config2(n=256, L=L)  # t_f, t_s, tol and target of the basin workload
+    t0 = time.perf_counter()
+    adj = ResidentAdjoint(a.adjoint_n, L, sc2.t_f, sc2.t_s, sc2.tol, sc2.meta["target"])
+    torch.cuda.synchronize()
+    adj_s = time.perf_counter() - t0
+    reqs = trace_from_config(a.requests, a.rate, sizes)
+    res, st = Server(adj).run(reqs)
+    lat_by = {}
+    for r in res:
+        lat_by.setdefault(r.n, []).append(r.latency)
+    st["p50_by_size_s"] = {str(k): float(np.percentile(v, 50)) for k, v in lat_by.items()}
+    sub = reqs[: a.plain_requests]
+    served_sub, sst = Server(adj).run([Request(r.id, 0.0, r.n, r.amp, r.width, r.src_u,
+                                               r.src_v) for r in sub])
+    _, pst = run_plain(adj, sub, precision=S.SWA_FP64)
+    # gauge error of the FP32 served results against the FP64 per-grid ones
+    plain64, _ = run_plain(adj, sub[:2], precision=S.SWA_FP64)
+    gerr = 0.0
+    for r in plain64:
+        s = next(x for x in served_sub if x.id == r.id)
+        k = min(len(s.gauges), len(r.gauges))
+        gerr = max(gerr, float(np.abs(s.gauges[:k] - r.gauges[:k]).max()))
+    print(json.dumps({"metric": "served scenarios/s (FP32 continuous batching) vs plain per-grid FP64",
+                      "adjoint_setup_s": adj_s, "served": st,
+                      "same_requests_served_fp32": sst, "plain_fp64": pst,
+                      "served_over_plain": sst["scenarios_per_s"] / pst["scenarios_per_s"],
+                      "gauge_max_abs_err_fp32_vs_fp64_m": gerr,
+                      "trace": {"requests": a.requests, "rate_per_s": a.rate,
+                                "sizes": sizes}}))
+
+
+if __name__ == "__main__":
+    main()
