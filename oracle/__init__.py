@@ -44,7 +44,7 @@ class _Grid(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("order", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("g", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("dry_tol", ctypes.c_double)]
+                ("dry_tol", ctypes.c_double), ("lin_nu", ctypes.c_double * 2)]
 
 
 @dataclass

@@ -14,14 +14,20 @@
  *   fwd_riemann      Sec. 6 (Roe solver for SWE plus bathymetry) applied to
  *                    Eq. (swe_1d)/(swe): f-wave form, source folded into the
  *                    momentum jump as g*hhat*(eta_R - eta_L).
- *   orc_fwd_step     Godunov-type wave-propagation update, unsplit in 2D, with
- *                    MC-limited second-order corrections (order 2).
- *   orc_fwd_smax     CFL number sum_dir (|u|+c)/dx over interior cells.
+ *   orc_fwd_step     Godunov-type wave-propagation update with MC-limited
+ *                    second-order corrections (order 2); in 2D dimensionally
+ *                    split: an x-sweep over every row, then a y-sweep over
+ *                    every column of the x-swept state.
+ *   orc_fwd_smax     CFL number max over cells of max_dir (|u|+c)/d_dir.
  *   orc_lin_step     first-order update of Eq. (hyp_linear) (and its 2D form,
- *                    Sec. 5), used only by the adjoint-identity pins.
+ *                    Sec. 5, x-sweep then y-sweep), used only by the
+ *                    adjoint-identity pins.
  *   orc_adj_step     one step of the time-reversed adjoint of Sec. 4:
  *                    q~_t - (A^T q~)_x [- (A_2^T q~)_y] = 0, f-wave form, walls
- *                    at wet/dry edges (Sec. 5 boundary condition).
+ *                    at wet/dry edges (Sec. 5 boundary condition); in 2D a
+ *                    y-sweep then an x-sweep (the transpose of the forward
+ *                    order, so one adjoint step is the transpose of one
+ *                    linear forward step).
  *   orc_flag         Eq. (ip_timepoint) (BRACKET) and Eq. (ip_timerange) with
  *                    linear interpolation in time (INTERP), bilinear spatial
  *                    interpolation of the adjoint (Sec. 4), zero where the
@@ -50,6 +56,7 @@ typedef struct {
     int order;          /* 1 or 2 */
     int bc[4];          /* x_lo, x_hi, y_lo, y_hi */
     double g, cfl, dry_tol;
+    double lin_nu[2];   /* internal: dt/dx, dt/dy of the linear sweeps */
 } orc_grid;
 
 #define NG 2
@@ -207,86 +214,82 @@ static void fwd_riemann(double g,
 /* --------------------------------------------------------- forward step */
 
 /*
- * One forward step of size dt, in place on (h, hu, hv).  hv may be NULL for
- * ndim == 1 (treated as zero and not written).  Returns 0, or -5 when a
- * non-positive or non-finite depth appears.
+ * One sweep of size dt along x (dir 0) or y (dir 1), in place on (h, hu, hv):
+ * every cell gets the fluctuations and corrections of its two edges in that
+ * direction.  Along y the edge frame is (h, hv, hu).
  */
-int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
-                 const double *B, double dt) {
-    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double *hv,
+                      const double *B, double dt) {
+    int nx = G->nx, ny = G->ny;
     size_t n = (size_t)nx * ny;
     double *ph = padded(G), *pu = padded(G), *pv = padded(G), *pB = padded(G);
-    double *zero = NULL;
-    if (!hv) { zero = (double *)calloc(n, sizeof(double)); }
-    const double *hv_in = hv ? hv : zero;
     fill_padded(G, h, ph, 1.0, 1.0);
     fill_padded(G, hu, pu, -1.0, 1.0);
-    fill_padded(G, hv_in, pv, 1.0, -1.0);
+    fill_padded(G, hv, pv, 1.0, -1.0);
     fill_padded(G, B, pB, 1.0, 1.0);
     double *nh = (double *)malloc(n * sizeof(double));
     double *nu_ = (double *)malloc(n * sizeof(double));
     double *nv = (double *)malloc(n * sizeof(double));
-    double nux = dt / G->dx, nuy = dt / G->dy;
-    int bad = 0;
+    double nu = dt / (dir == 0 ? G->dx : G->dy);
 
-#pragma omp parallel for schedule(static) reduction(| : bad)
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
-            double q[3];
             size_t c = pidx(G, i, j);
-            q[0] = ph[c]; q[1] = pu[c]; q[2] = pv[c];
-            /* x-edges i-3/2, i-1/2, i+1/2, i+3/2: edge k+1/2 between k, k+1 */
-            edge_waves wx[4];
+            /* edges k-3/2 .. k+3/2 around the cell along the sweep */
+            edge_waves w[4];
             for (int e = 0; e < 4; e++) {
-                int l = i - 2 + e, r = l + 1;
-                size_t a = pidx(G, l, j), b = pidx(G, r, j);
-                fwd_riemann(G->g, ph[a], pu[a], pv[a], pB[a],
-                            ph[b], pu[b], pv[b], pB[b], &wx[e]);
+                size_t a, b;
+                if (dir == 0) { a = pidx(G, i - 2 + e, j); b = pidx(G, i - 1 + e, j); }
+                else { a = pidx(G, i, j - 2 + e); b = pidx(G, i, j - 1 + e); }
+                if (dir == 0)
+                    fwd_riemann(G->g, ph[a], pu[a], pv[a], pB[a], ph[b], pu[b], pv[b], pB[b], &w[e]);
+                else
+                    fwd_riemann(G->g, ph[a], pv[a], pu[a], pB[a], ph[b], pv[b], pu[b], pB[b], &w[e]);
             }
             double amL[3], apL[3], FL[3], amR[3], apR[3], FR[3];
-            /* left edge i-1/2 = wx[1] (neighbours wx[0], wx[2]) */
-            edge_fluxes(3, &wx[0], &wx[1], &wx[2], nux, G->order, amL, apL, FL);
-            /* right edge i+1/2 = wx[2] (neighbours wx[1], wx[3]) */
-            edge_fluxes(3, &wx[1], &wx[2], &wx[3], nux, G->order, amR, apR, FR);
+            edge_fluxes(3, &w[0], &w[1], &w[2], nu, G->order, amL, apL, FL);
+            edge_fluxes(3, &w[1], &w[2], &w[3], nu, G->order, amR, apR, FR);
             double dq[3];
             for (int m = 0; m < 3; m++)
-                dq[m] = -nux * (apL[m] + amR[m]) - nux * (FR[m] - FL[m]);
-            if (two_d) {
-                /* y-edges with (h, hv, hu): normal momentum is hv */
-                edge_waves wy[4];
-                for (int e = 0; e < 4; e++) {
-                    int l = j - 2 + e, r = l + 1;
-                    size_t a = pidx(G, i, l), b = pidx(G, i, r);
-                    fwd_riemann(G->g, ph[a], pv[a], pu[a], pB[a],
-                                ph[b], pv[b], pu[b], pB[b], &wy[e]);
-                }
-                double bmL[3], bpL[3], GL[3], bmR[3], bpR[3], GR[3];
-                edge_fluxes(3, &wy[0], &wy[1], &wy[2], nuy, G->order, bmL, bpL, GL);
-                edge_fluxes(3, &wy[1], &wy[2], &wy[3], nuy, G->order, bmR, bpR, GR);
-                /* components of the y-waves are (h, hv, hu) */
-                double dy[3];
-                for (int m = 0; m < 3; m++)
-                    dy[m] = -nuy * (bpL[m] + bmR[m]) - nuy * (GR[m] - GL[m]);
-                dq[0] += dy[0];
-                dq[1] += dy[2];
-                dq[2] += dy[1];
-            }
+                dq[m] = -nu * (apL[m] + amR[m]) - nu * (FR[m] - FL[m]);
             size_t o = (size_t)j * nx + i;
-            nh[o] = q[0] + dq[0];
-            nu_[o] = q[1] + dq[1];
-            nv[o] = q[2] + dq[2];
-            if (!(nh[o] > 0.0) || !isfinite(nu_[o]) || !isfinite(nv[o])) bad = 1;
+            nh[o] = ph[c] + dq[0];
+            if (dir == 0) { nu_[o] = pu[c] + dq[1]; nv[o] = pv[c] + dq[2]; }
+            else { nv[o] = pv[c] + dq[1]; nu_[o] = pu[c] + dq[2]; }
         }
     }
     memcpy(h, nh, n * sizeof(double));
     memcpy(hu, nu_, n * sizeof(double));
-    if (hv) memcpy(hv, nv, n * sizeof(double));
+    memcpy(hv, nv, n * sizeof(double));
     free(ph); free(pu); free(pv); free(pB); free(nh); free(nu_); free(nv);
-    free(zero);
+}
+
+/*
+ * One forward step of size dt, in place on (h, hu, hv): in 1D a single
+ * x-sweep; in 2D an x-sweep of the whole grid, then a y-sweep of the x-swept
+ * state (dimensional splitting).  hv may be NULL for ndim == 1 (treated as
+ * zero and not written).  Returns 0, or -5 when a non-positive or
+ * non-finite depth appears.
+ */
+int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
+                 const double *B, double dt) {
+    size_t n = (size_t)G->nx * G->ny;
+    double *v = hv;
+    if (!hv) v = (double *)calloc(n, sizeof(double));
+    fwd_sweep(G, 0, h, hu, v, B, dt);
+    if (G->ndim == 2) fwd_sweep(G, 1, h, hu, v, B, dt);
+    int bad = 0;
+    for (size_t k = 0; k < n; k++)
+        if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(v[k])) bad = 1;
+    if (!hv) free(v);
     return bad ? -5 : 0;
 }
 
-/* CFL number: max over interior cells of (|u|+c)/dx [+ (|v|+c)/dy]. */
+/*
+ * CFL number: max over cells of (|u|+c)/dx [and (|v|+c)/dy]; with dimensional
+ * splitting each sweep is limited by its own Courant number.
+ */
 double orc_fwd_smax(const orc_grid *G, const double *h, const double *hu,
                     const double *hv) {
     double smax = 0.0;
@@ -294,7 +297,10 @@ double orc_fwd_smax(const orc_grid *G, const double *h, const double *hu,
     for (size_t k = 0; k < n; k++) {
         double c = sqrt(G->g * h[k]);
         double s = (fabs(hu[k] / h[k]) + c) / G->dx;
-        if (G->ndim == 2) s += (fabs(hv[k] / h[k]) + c) / G->dy;
+        if (G->ndim == 2) {
+            double sy = (fabs(hv[k] / h[k]) + c) / G->dy;
+            if (sy > s) s = sy;
+        }
         if (s > smax) smax = s;
     }
     return smax;
@@ -323,80 +329,72 @@ long orc_fwd_run(const orc_grid *G, double *h, double *hu, double *hv,
 /* ------------------------------------------------- linear forward (tests) */
 
 /*
- * First-order wave-propagation step for q_t + A(x) q_x (+ A_2 q_y) = 0,
- * A = [[0,1],[g hbar,0]] (Eq. SWE_Aq), q = (eta, mu[, gamma]).  At an x-edge
- * the jump (d_eta, d_mu) splits as a1 [1, -cL] + a2 [1, cR]; the left-going
- * part moves at -cL, the right-going at +cR.  Walls mirror with the normal
- * momentum negated.  Order 1 only; used by the adjoint-identity pins.
+ * First-order wave-propagation sweep for q_t + A(x) q_x = 0 along x (dir 0,
+ * components (eta, mu)) or the y analogue (dir 1, components (eta, gamma)),
+ * A = [[0,1],[g hbar,0]] (Eq. SWE_Aq).  At an edge the jump (d_eta, d_m)
+ * splits as a1 [1, -cL] + a2 [1, cR]; the left-going part moves at -cL, the
+ * right-going at +cR.  Walls mirror with the normal momentum negated.
  */
-int orc_lin_step(const orc_grid *G, double *eta, double *mu, double *gam,
-                 const double *hbar, double dt) {
-    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+static void lin_sweep(const orc_grid *G, int dir, double *eta, double *mu, double *gam,
+                      const double *c) {
+    (void)0;
+    int nx = G->nx, ny = G->ny;
     size_t n = (size_t)nx * ny;
     double *pe = padded(G), *pm = padded(G), *pg = padded(G), *pc = padded(G);
-    double *zero = NULL;
-    if (!gam) zero = (double *)calloc(n, sizeof(double));
-    double *c = (double *)malloc(n * sizeof(double));
-    for (size_t k = 0; k < n; k++) c[k] = sqrt(G->g * hbar[k]);
     fill_padded(G, eta, pe, 1.0, 1.0);
     fill_padded(G, mu, pm, -1.0, 1.0);
-    fill_padded(G, gam ? gam : zero, pg, 1.0, -1.0);
+    fill_padded(G, gam, pg, 1.0, -1.0);
     fill_padded(G, c, pc, 1.0, 1.0);
     double *ne = (double *)malloc(n * sizeof(double));
     double *nm = (double *)malloc(n * sizeof(double));
     double *ng = (double *)malloc(n * sizeof(double));
-    double nux = dt / G->dx, nuy = dt / G->dy;
+    double *pn = dir == 0 ? pm : pg;  /* normal component */
     for (int j = 0; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
             size_t ci = pidx(G, i, j);
-            double de = 0.0, dm = 0.0, dg = 0.0;
-            /* edge i-1/2: right-going part enters cell i */
-            {
-                size_t a = pidx(G, i - 1, j);
-                double cL = pc[a], cR = pc[ci];
-                double dE = pe[ci] - pe[a], dM = pm[ci] - pm[a];
+            size_t lo = dir == 0 ? pidx(G, i - 1, j) : pidx(G, i, j - 1);
+            size_t hi = dir == 0 ? pidx(G, i + 1, j) : pidx(G, i, j + 1);
+            double de = 0.0, dn = 0.0;
+            {   /* edge below/left: right-going part enters the cell */
+                double cL = pc[lo], cR = pc[ci];
+                double dE = pe[ci] - pe[lo], dM = pn[ci] - pn[lo];
                 double a2 = (dM + cL * dE) / (cL + cR);
-                de -= nux * (cR * a2);
-                dm -= nux * (cR * a2 * cR);
+                de -= G->lin_nu[dir] * (cR * a2);
+                dn -= G->lin_nu[dir] * (cR * a2 * cR);
             }
-            /* edge i+1/2: left-going part enters cell i */
-            {
-                size_t b = pidx(G, i + 1, j);
-                double cL = pc[ci], cR = pc[b];
-                double dE = pe[b] - pe[ci], dM = pm[b] - pm[ci];
+            {   /* edge above/right: left-going part enters the cell */
+                double cL = pc[ci], cR = pc[hi];
+                double dE = pe[hi] - pe[ci], dM = pn[hi] - pn[ci];
                 double a1 = (cR * dE - dM) / (cL + cR);
-                de -= nux * (-cL * a1);
-                dm -= nux * (-cL * a1 * (-cL));
-            }
-            if (two_d) {
-                {
-                    size_t a = pidx(G, i, j - 1);
-                    double cL = pc[a], cR = pc[ci];
-                    double dE = pe[ci] - pe[a], dG = pg[ci] - pg[a];
-                    double a2 = (dG + cL * dE) / (cL + cR);
-                    de -= nuy * (cR * a2);
-                    dg -= nuy * (cR * a2 * cR);
-                }
-                {
-                    size_t b = pidx(G, i, j + 1);
-                    double cL = pc[ci], cR = pc[b];
-                    double dE = pe[b] - pe[ci], dG = pg[b] - pg[ci];
-                    double a1 = (cR * dE - dG) / (cL + cR);
-                    de -= nuy * (-cL * a1);
-                    dg -= nuy * (-cL * a1 * (-cL));
-                }
+                de -= G->lin_nu[dir] * (-cL * a1);
+                dn -= G->lin_nu[dir] * (-cL * a1 * (-cL));
             }
             size_t o = (size_t)j * nx + i;
             ne[o] = pe[ci] + de;
-            nm[o] = pm[ci] + dm;
-            ng[o] = pg[ci] + dg;
+            if (dir == 0) { nm[o] = pm[ci] + dn; ng[o] = pg[ci]; }
+            else { ng[o] = pg[ci] + dn; nm[o] = pm[ci]; }
         }
     }
     memcpy(eta, ne, n * sizeof(double));
     memcpy(mu, nm, n * sizeof(double));
-    if (gam) memcpy(gam, ng, n * sizeof(double));
-    free(pe); free(pm); free(pg); free(pc); free(c); free(ne); free(nm);
-    free(ng); free(zero);
+    memcpy(gam, ng, n * sizeof(double));
+    free(pe); free(pm); free(pg); free(pc); free(ne); free(nm); free(ng);
+}
+
+/* One linear step: x-sweep, then (2D) y-sweep.  Order 1 only. */
+int orc_lin_step(const orc_grid *G0, double *eta, double *mu, double *gam,
+                 const double *hbar, double dt) {
+    orc_grid G = *G0;
+    size_t n = (size_t)G.nx * G.ny;
+    double *c = (double *)malloc(n * sizeof(double));
+    for (size_t k = 0; k < n; k++) c[k] = sqrt(G.g * hbar[k]);
+    double *gm = gam ? gam : (double *)calloc(n, sizeof(double));
+    G.lin_nu[0] = dt / G.dx;
+    G.lin_nu[1] = dt / G.dy;
+    lin_sweep(&G, 0, eta, mu, gm, c);
+    if (G.ndim == 2) lin_sweep(&G, 1, eta, mu, gm, c);
+    if (!gam) free(gm);
+    free(c);
     return 0;
 }
 
@@ -450,74 +448,72 @@ static int adj_edge(const orc_grid *G, const double *pe, const double *pm,
 }
 
 /*
- * One step of the time-reversed adjoint (Sec. 4) of size dt, in place on
- * (eta~, mu~, gamma~); hbar = max(-B, 0) of the adjoint grid.  Dry cells are
- * left unchanged.  gam may be NULL for ndim == 1.
+ * One adjoint sweep along x (dir 0, components (eta~, mu~)) or y (dir 1,
+ * (eta~, gamma~)), in place.  Dry cells are left unchanged.
  */
-int orc_adj_step(const orc_grid *G, double *eta, double *mu, double *gam,
-                 const double *hbar, double dt) {
-    int nx = G->nx, ny = G->ny, two_d = (G->ndim == 2);
+static void adj_sweep(const orc_grid *G, int dir, double *eta, double *mu, double *gam,
+                      const double *hbar, double dt) {
+    int nx = G->nx, ny = G->ny;
     size_t n = (size_t)nx * ny;
     double *pe = padded(G), *pm = padded(G), *pg = padded(G), *phb = padded(G);
-    double *zero = NULL;
-    if (!gam) zero = (double *)calloc(n, sizeof(double));
     fill_padded(G, eta, pe, 1.0, 1.0);
     fill_padded(G, mu, pm, -1.0, 1.0);
-    fill_padded(G, gam ? gam : zero, pg, 1.0, -1.0);
+    fill_padded(G, gam, pg, 1.0, -1.0);
     fill_padded(G, hbar, phb, 1.0, 1.0);
     double *ne = (double *)malloc(n * sizeof(double));
     double *nm = (double *)malloc(n * sizeof(double));
     double *ng = (double *)malloc(n * sizeof(double));
-    double nux = dt / G->dx, nuy = dt / G->dy;
+    double nu = dt / (dir == 0 ? G->dx : G->dy);
+    const double *pn = dir == 0 ? pm : pg;
 
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
             size_t ci = pidx(G, i, j);
             size_t o = (size_t)j * nx + i;
-            if (!(phb[ci] > G->dry_tol)) {
-                ne[o] = pe[ci]; nm[o] = pm[ci]; ng[o] = pg[ci];
-                continue;
-            }
-            edge_waves wx[4];
-            int wallx[4];
+            ne[o] = pe[ci]; nm[o] = pm[ci]; ng[o] = pg[ci];
+            if (!(phb[ci] > G->dry_tol)) continue;
+            edge_waves w[4];
+            int wall[4];
             for (int e = 0; e < 4; e++) {
-                int l = i - 2 + e;
-                wallx[e] = adj_edge(G, pe, pm, phb, pidx(G, l, j), pidx(G, l + 1, j), &wx[e]);
+                size_t a, b;
+                if (dir == 0) { a = pidx(G, i - 2 + e, j); b = pidx(G, i - 1 + e, j); }
+                else { a = pidx(G, i, j - 2 + e); b = pidx(G, i, j - 1 + e); }
+                wall[e] = adj_edge(G, pe, pn, phb, a, b, &w[e]);
             }
             double amL[3], apL[3], FL[3], amR[3], apR[3], FR[3];
-            edge_fluxes(2, &wx[0], &wx[1], &wx[2], nux, wallx[1] ? 1 : G->order, amL, apL, FL);
-            edge_fluxes(2, &wx[1], &wx[2], &wx[3], nux, wallx[2] ? 1 : G->order, amR, apR, FR);
-            double de = -nux * (apL[0] + amR[0]) - nux * (FR[0] - FL[0]);
-            double dm = -nux * (apL[1] + amR[1]) - nux * (FR[1] - FL[1]);
-            double dg = 0.0;
-            if (two_d) {
-                edge_waves wy[4];
-                int wally[4];
-                for (int e = 0; e < 4; e++) {
-                    int l = j - 2 + e;
-                    wally[e] = adj_edge(G, pe, pg, phb, pidx(G, i, l), pidx(G, i, l + 1), &wy[e]);
-                }
-                double bmL[3], bpL[3], GL[3], bmR[3], bpR[3], GR[3];
-                edge_fluxes(2, &wy[0], &wy[1], &wy[2], nuy, wally[1] ? 1 : G->order, bmL, bpL, GL);
-                edge_fluxes(2, &wy[1], &wy[2], &wy[3], nuy, wally[2] ? 1 : G->order, bmR, bpR, GR);
-                de += -nuy * (bpL[0] + bmR[0]) - nuy * (GR[0] - GL[0]);
-                dg = -nuy * (bpL[1] + bmR[1]) - nuy * (GR[1] - GL[1]);
-            }
+            edge_fluxes(2, &w[0], &w[1], &w[2], nu, wall[1] ? 1 : G->order, amL, apL, FL);
+            edge_fluxes(2, &w[1], &w[2], &w[3], nu, wall[2] ? 1 : G->order, amR, apR, FR);
+            double de = -nu * (apL[0] + amR[0]) - nu * (FR[0] - FL[0]);
+            double dn = -nu * (apL[1] + amR[1]) - nu * (FR[1] - FL[1]);
             ne[o] = pe[ci] + de;
-            nm[o] = pm[ci] + dm;
-            ng[o] = pg[ci] + dg;
+            if (dir == 0) nm[o] = pm[ci] + dn;
+            else ng[o] = pg[ci] + dn;
         }
     }
     memcpy(eta, ne, n * sizeof(double));
     memcpy(mu, nm, n * sizeof(double));
-    if (gam) memcpy(gam, ng, n * sizeof(double));
+    memcpy(gam, ng, n * sizeof(double));
     free(pe); free(pm); free(pg); free(phb); free(ne); free(nm); free(ng);
-    free(zero);
+}
+
+/*
+ * One step of the time-reversed adjoint (Sec. 4) of size dt, in place on
+ * (eta~, mu~, gamma~); hbar = max(-B, 0) of the adjoint grid.  2D: a y-sweep,
+ * then an x-sweep (the reverse of the forward order).  gam may be NULL for
+ * ndim == 1.
+ */
+int orc_adj_step(const orc_grid *G, double *eta, double *mu, double *gam,
+                 const double *hbar, double dt) {
+    size_t n = (size_t)G->nx * G->ny;
+    double *gm = gam ? gam : (double *)calloc(n, sizeof(double));
+    if (G->ndim == 2) adj_sweep(G, 1, eta, mu, gm, hbar, dt);
+    adj_sweep(G, 0, eta, mu, gm, hbar, dt);
+    if (!gam) free(gm);
     return 0;
 }
 
-/* Adjoint CFL number: max over wet cells of c/dx [+ c/dy], c = sqrt(g hbar). */
+/* Adjoint CFL number: max over wet cells of c/dx [and c/dy], c = sqrt(g hbar). */
 double orc_adj_smax(const orc_grid *G, const double *hbar) {
     double smax = 0.0;
     size_t n = (size_t)G->nx * G->ny;
@@ -525,7 +521,7 @@ double orc_adj_smax(const orc_grid *G, const double *hbar) {
         if (!(hbar[k] > G->dry_tol)) continue;
         double c = sqrt(G->g * hbar[k]);
         double s = c / G->dx;
-        if (G->ndim == 2) s += c / G->dy;
+        if (G->ndim == 2 && c / G->dy > s) s = c / G->dy;
         if (s > smax) smax = s;
     }
     return smax;

@@ -8,8 +8,9 @@ paper and by the mathematics (no GPU).
     (Eq. swe_1d_linearized) with first order (order 1) and better than
     first order (order 2, limited corrections) convergence
   * the 1D wet dam break converges to the exact Riemann solution (Stoker)
-  * 2D reduces to 1D for y-uniform data; transposing the input transposes the
-    output bit-exactly; the x -> -x mirror holds to roundoff
+  * 2D reduces to 1D for y-uniform and for x-uniform data, bit for bit; the
+    x -> -x mirror holds to roundoff
+  * the split order-2 scheme is stable at cfl 0.75 (noise does not grow)
 """
 import numpy as np
 import pytest
@@ -46,10 +47,15 @@ def test_mass_conservation_walls(order):
     rng = np.random.default_rng(12)
     nx, ny = 30, 22
     g = O.Grid(2, nx, ny, 0.0, 0.0, 1000.0, 1000.0, order=order, bc=(1, 1, 1, 1))
-    B = -rng.uniform(100.0, 4000.0, nx * ny)
     xc = (np.arange(nx) + 0.5) * 1000.0
     yc = (np.arange(ny) + 0.5) * 1000.0
     X, Y = np.meshgrid(xc, yc)
+    # smooth random bathymetry between ~200 m and 4000 m
+    B = -4000.0 + np.zeros_like(X)
+    for _ in range(6):
+        cx, cy = rng.uniform(0, 30e3), rng.uniform(0, 22e3)
+        B += rng.uniform(500, 1900) * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (4e3) ** 2)
+    B = np.minimum(B, -200.0).ravel()
     eta = 2.0 * np.exp(-((X - 12e3) ** 2 + (Y - 9e3) ** 2) / (4e3) ** 2).ravel()
     h = eta - B
     hu = rng.uniform(-3, 3, h.size)
@@ -196,27 +202,39 @@ def test_2d_reduces_to_1d_for_y_uniform_data():
     assert np.all(v2 == 0)
 
 
-def test_transpose_bit_exact_and_mirror():
+def test_y_sweep_reduces_to_1d_and_mirror():
+    """x-uniform data with hu = 0: the x-sweep changes nothing and the y-sweep
+    is the 1D solver along y, bit for bit.  The x -> -x mirror holds to
+    roundoff."""
+    nx, ny = 5, 80
+    rng = np.random.default_rng(3)
+    B1 = -rng.uniform(200.0, 4000.0, ny)
+    eta1 = 0.5 * np.exp(-((np.arange(ny) - 30.0) / 6.0) ** 2)
+    hv1 = rng.uniform(-2, 2, ny)
+    g1 = O.Grid(1, ny, 1, 0.0, 0.0, 1500.0, 1.0, order=2, bc=(1, 0, 0, 0))
+    g2 = O.Grid(2, nx, ny, 0.0, 0.0, 2000.0, 1500.0, order=2, bc=(0, 0, 1, 0))
+    h1, v1 = eta1 - B1, hv1.copy()
+    h2 = np.repeat(h1, nx)
+    v2 = np.repeat(v1, nx)
+    u2 = np.zeros(nx * ny)
+    B2 = np.repeat(B1, nx)
+    for _ in range(50):
+        h1, v1, _ = O.fwd_step(g1, h1, v1, None, B1, 2.0)
+        h2, u2, v2 = O.fwd_step(g2, h2, u2, v2, B2, 2.0)
+    for i in range(nx):
+        assert np.array_equal(h2[i::nx], h1)
+        assert np.array_equal(v2[i::nx], v1)
+    assert np.all(u2 == 0)
+    # mirror x -> -x: h even, hu odd
     nx, ny = 23, 31
-    rng = np.random.default_rng(5)
     B = -rng.uniform(100.0, 4000.0, (ny, nx))
     eta = rng.uniform(-1, 1, (ny, nx))
     hu = rng.uniform(-5, 5, (ny, nx))
     hv = rng.uniform(-5, 5, (ny, nx))
     ga = O.Grid(2, nx, ny, 0.0, 0.0, 1000.0, 1000.0, order=2, bc=(1, 0, 0, 1))
-    gb = O.Grid(2, ny, nx, 0.0, 0.0, 1000.0, 1000.0, order=2, bc=(0, 1, 1, 0))
-    a = ((eta - B).ravel(), hu.ravel(), hv.ravel())
-    b = ((eta - B).T.ravel(), hv.T.ravel(), hu.T.ravel())
-    for _ in range(20):
-        a = O.fwd_step(ga, *a, B.ravel(), 3.0)
-        b = O.fwd_step(gb, *b, B.T.ravel(), 3.0)
-    assert np.array_equal(a[0].reshape(ny, nx).T, b[0].reshape(nx, ny))
-    assert np.array_equal(a[1].reshape(ny, nx).T, b[2].reshape(nx, ny))
-    assert np.array_equal(a[2].reshape(ny, nx).T, b[1].reshape(nx, ny))
-    # mirror x -> -x: h even, hu odd
     gm = O.Grid(2, nx, ny, 0.0, 0.0, 1000.0, 1000.0, order=2, bc=(0, 1, 0, 1))
-    c = ((eta - B)[:, ::-1].ravel(), -hu[:, ::-1].ravel(), hv[:, ::-1].ravel())
     a = ((eta - B).ravel(), hu.ravel(), hv.ravel())
+    c = ((eta - B)[:, ::-1].ravel(), -hu[:, ::-1].ravel(), hv[:, ::-1].ravel())
     for _ in range(20):
         a = O.fwd_step(ga, *a, B.ravel(), 3.0)
         c = O.fwd_step(gm, *c, B[:, ::-1].ravel(), 3.0)
@@ -225,11 +243,34 @@ def test_transpose_bit_exact_and_mirror():
     assert np.abs(a[1].reshape(ny, nx)[:, ::-1] + c[1].reshape(ny, nx)).max() <= 1e-9
 
 
+def test_split_scheme_is_stable_at_cfl_075():
+    """Dimensional splitting keeps the order-2 scheme stable at cfl 0.75:
+    grid-scale noise of 1e-8 m on a flat 4000 m basin with a smooth 5 cm wave
+    stays bounded over 3000 steps, and a 1e-9 perturbation does not grow.
+    (Without splitting or transverse corrections, the unsplit second-order
+    update lacks the cross-derivative term and this noise grows by orders of
+    magnitude.)"""
+    rng = np.random.default_rng(0)
+    n = 64
+    g = O.Grid(2, n, n, 0, 0, 1000., 1000., order=2, cfl=0.75, bc=(1, 1, 1, 1))
+    B = np.full(n * n, -4000.0)
+    x = (np.arange(n) + 0.5) * 1000.
+    X, Y = np.meshgrid(x, x)
+    eta = 0.05 * np.exp(-((X - 20e3) ** 2 + (Y - 30e3) ** 2) / (6e3) ** 2).ravel()
+    eta = eta + 1e-8 * rng.standard_normal(n * n)
+    z = np.zeros(n * n)
+    h2, _, _, _, _ = O.fwd_run(g, eta - B, z, z, B, 3000, 1e12)
+    e2 = eta + 1e-9 * rng.standard_normal(n * n)
+    h3, _, _, _, _ = O.fwd_run(g, e2 - B, z, z, B, 3000, 1e12)
+    assert np.abs(h2 + B).max() < 0.05
+    assert np.abs(h2 - h3).max() < 1e-8
+
+
 def test_cfl_number_closed_form():
     g = O.Grid(2, 3, 2, 0.0, 0.0, 1000.0, 500.0)
     h = np.array([100.0, 400.0, 900.0, 100.0, 100.0, 100.0])
     hu = np.array([100.0, -400.0, 0.0, 0.0, 0.0, 0.0])
     hv = np.array([0.0, 800.0, 0.0, 0.0, 0.0, 0.0])
-    s = [(abs(hu[k] / h[k]) + np.sqrt(G * h[k])) / 1000.0
-         + (abs(hv[k] / h[k]) + np.sqrt(G * h[k])) / 500.0 for k in range(6)]
+    s = [max((abs(hu[k] / h[k]) + np.sqrt(G * h[k])) / 1000.0,
+             (abs(hv[k] / h[k]) + np.sqrt(G * h[k])) / 500.0) for k in range(6)]
     assert O.fwd_smax(g, h, hu, hv) == max(s)
