@@ -120,12 +120,13 @@ int swa_get_state(swa_grid *grid, double *h, double *hu, double *hv,
 /*
  * Take up to max_steps explicit steps, stopping at t_end: each step uses
  * dt = min(cfl / s_max(Q^n), t_end - t_n), s_max = max over cells of
- * (|u|+c)/dx + (|v|+c)/dy, c = sqrt(g h).  The update applies, at every
+ * max((|u|+c)/dx, (|v|+c)/dy), c = sqrt(g h).  The update applies, at every
  * edge, the f-wave Roe solution with the bathymetry source folded into the
- * momentum jump (the ocean at rest is exact), the fluctuations of all edges
- * of a cell (unsplit in 2D, no transverse terms) and, for order 2, MC-
- * limited corrections.  The CFL maximum for the next step is reduced in the
- * same kernel.  Steps past t_end are no-ops on the device.
+ * momentum jump (the ocean at rest is exact), the fluctuations of the cell's
+ * edges and, for order 2, MC-limited corrections; in 2D the step is
+ * dimensionally split (an x-sweep of every row, then a y-sweep of the
+ * x-swept state).  The CFL maximum for the next step is reduced in the same
+ * kernel.  Steps past t_end are no-ops on the device.
  */
 int swa_step_forward(swa_grid *grid, int max_steps, double t_end, void *stream);
 
@@ -154,7 +155,9 @@ int swa_grid_arrays(swa_grid *grid, const void **q0, const void **q1,
  * q~_t - (A^T q~)_x [- (A_2^T q~)_y] = 0 forward in t with q~(0) = phi,
  * A, A_2 from the linearisation about the ocean at rest (Sec. 3, Sec. 5),
  * zero normal velocity at wet/dry edges (Sec. 5).  Fixed time step
- * dt = t_f / N, N = ceil(t_f * max(c/dx + c/dy) / cfl), c = sqrt(g hbar).
+ * dt = t_f / N, N = ceil(t_f * max(c/dx, c/dy) / cfl), c = sqrt(g hbar).
+ * In 2D a step is a y-sweep then an x-sweep (the reverse of the forward
+ * order, so that with walls it is the transpose of a linear forward step).
  */
 size_t swa_adjoint_workspace_bytes(const swa_grid_desc *desc);
 

@@ -22,7 +22,7 @@ __global__ void adj_init_kernel(const double *B, R *c, size_t n, int two_d,
         if (hb > dry_tol) {
             cc = sqrt(g * hb);
             s = cc / dx;
-            if (two_d) s += cc / dy;
+            if (two_d && cc / dy > s) s = cc / dy;
         }
         c[k] = sizeof(R) == 8 ? (R)hb : (R)cc;
         mx = s > mx ? s : mx;

@@ -80,6 +80,13 @@ __device__ __forceinline__ void adj_flux(const AdjWave<R> &wm, const AdjWave<R> 
     }
 }
 
+// One adjoint step of a TX x TY tile, dimensionally split in the reverse of
+// the forward order: a y-sweep of every staged column, then an x-sweep of the
+// y-swept state.  The tile and a 2-cell halo with corners are staged; the
+// x-halo columns of the y-swept state come from y-sweeping index-mapped
+// columns (the tangential component mu~ is passive in the y-sweep, so this is
+// exactly the copy/mirror of the y-swept interior).  With walls the two
+// sweeps are the transposes of the linear forward sweeps.
 template <typename R, bool TWO_D, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     constexpr int HX = 2, HY = TWO_D ? 2 : 0;
@@ -87,10 +94,11 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     constexpr int NT = TX * TY;
     constexpr int NEX = RX - 1;
     constexpr int NEY = TWO_D ? RY - 1 : 1;
-    constexpr int WYC = TWO_D ? TX : 1;
     __shared__ R s_e[RY][RX], s_m[RY][RX], s_g[RY][RX], s_c[RY][RX], s_gh[RY][RX];
-    __shared__ AdjWave<R> wx[TY][NEX];
-    __shared__ AdjWave<R> wy[NEY][WYC];
+    __shared__ union WaveBuf {
+        AdjWave<R> y[NEY][RX];
+        AdjWave<R> x[TY][NEX];
+    } wb;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + ty * TX;
@@ -99,9 +107,6 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
 
     for (int r = tid; r < RX * RY; r += NT) {
         const int ry = r / RX, rx = r - ry * RX;
-        const bool xin = rx >= HX && rx < HX + TX;
-        const bool yin = ry >= HY && ry < HY + TY;
-        if (!xin && !yin) continue;
         bool fx, fy = false;
         const int ci = ghost_index(i0 + rx, nx, p.bc.lo_x, p.bc.hi_x, &fx);
         int cj = 0;
@@ -129,19 +134,48 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     }
     __syncthreads();
 
+    if (TWO_D) {
+        // y-edge waves of every staged column (edge k between rows k, k+1)
+        for (int e = tid; e < NEY * RX; e += NT) {
+            const int k = e / RX, rx = e - k * RX;
+            wb.y[k][rx] = adj_riemann<R>(s_e[k][rx], s_g[k][rx], s_c[k][rx], s_gh[k][rx],
+                                         s_e[k + 1][rx], s_g[k + 1][rx], s_c[k + 1][rx],
+                                         s_gh[k + 1][rx]);
+        }
+        __syncthreads();
+        // y-sweep of the tile rows in every staged column
+        R ye[(TY * RX + NT - 1) / NT], yg[(TY * RX + NT - 1) / NT];
+        int k = 0;
+        for (int i = tid; i < TY * RX; i += NT, k++) {
+            const int row = i / RX, rx = i - row * RX, ry = row + HY;
+            ye[k] = s_e[ry][rx];
+            yg[k] = s_g[ry][rx];
+            if (s_c[ry][rx] > R(0)) {
+                R bm0[2], bp0[2], G0[2], bm1[2], bp1[2], G1[2];
+                adj_flux<R>(wb.y[ry - 2][rx], wb.y[ry - 1][rx], wb.y[ry][rx], p.nuy, p.order, bm0, bp0, G0);
+                adj_flux<R>(wb.y[ry - 1][rx], wb.y[ry][rx], wb.y[ry + 1][rx], p.nuy, p.order, bm1, bp1, G1);
+                const R de = -p.nuy * (bp0[0] + bm1[0]) - p.nuy * (G1[0] - G0[0]);
+                const R dg = -p.nuy * (bp0[1] + bm1[1]) - p.nuy * (G1[1] - G0[1]);
+                ye[k] = ye[k] + de;
+                yg[k] = yg[k] + dg;
+            }
+        }
+        __syncthreads();  // every y-wave read before the union is reused
+        k = 0;
+        for (int i = tid; i < TY * RX; i += NT, k++) {
+            const int row = i / RX, rx = i - row * RX, ry = row + HY;
+            s_e[ry][rx] = ye[k];
+            s_g[ry][rx] = yg[k];
+        }
+        __syncthreads();
+    }
+
+    // x-edge waves of the (y-swept) tile rows
     for (int e = tid; e < TY * NEX; e += NT) {
         const int row = e / NEX, k = e - row * NEX, ry = row + HY;
-        wx[row][k] = adj_riemann<R>(s_e[ry][k], s_m[ry][k], s_c[ry][k], s_gh[ry][k],
-                                    s_e[ry][k + 1], s_m[ry][k + 1], s_c[ry][k + 1],
-                                    s_gh[ry][k + 1]);
-    }
-    if (TWO_D) {
-        for (int e = tid; e < NEY * TX; e += NT) {
-            const int k = e / TX, col = e - k * TX, rx = col + HX;
-            wy[k][col] = adj_riemann<R>(s_e[k][rx], s_g[k][rx], s_c[k][rx], s_gh[k][rx],
-                                        s_e[k + 1][rx], s_g[k + 1][rx], s_c[k + 1][rx],
-                                        s_gh[k + 1][rx]);
-        }
+        wb.x[row][k] = adj_riemann<R>(s_e[ry][k], s_m[ry][k], s_c[ry][k], s_gh[ry][k],
+                                      s_e[ry][k + 1], s_m[ry][k + 1], s_c[ry][k + 1],
+                                      s_gh[ry][k + 1]);
     }
     __syncthreads();
 
@@ -151,21 +185,12 @@ __global__ void __launch_bounds__(TX *TY) adj_step_kernel(AdjParams<R> p) {
     R ne = s_e[cy][cx], nm = s_m[cy][cx], ng = s_g[cy][cx];
     if (s_c[cy][cx] > R(0)) {
         R am0[2], ap0[2], F0[2], am1[2], ap1[2], F1[2];
-        adj_flux<R>(wx[ty][tx], wx[ty][tx + 1], wx[ty][tx + 2], p.nux, p.order, am0, ap0, F0);
-        adj_flux<R>(wx[ty][tx + 1], wx[ty][tx + 2], wx[ty][tx + 3], p.nux, p.order, am1, ap1, F1);
-        R de = -p.nux * (ap0[0] + am1[0]) - p.nux * (F1[0] - F0[0]);
+        adj_flux<R>(wb.x[ty][tx], wb.x[ty][tx + 1], wb.x[ty][tx + 2], p.nux, p.order, am0, ap0, F0);
+        adj_flux<R>(wb.x[ty][tx + 1], wb.x[ty][tx + 2], wb.x[ty][tx + 3], p.nux, p.order, am1, ap1, F1);
+        const R de = -p.nux * (ap0[0] + am1[0]) - p.nux * (F1[0] - F0[0]);
         const R dm = -p.nux * (ap0[1] + am1[1]) - p.nux * (F1[1] - F0[1]);
-        R dg = R(0);
-        if (TWO_D) {
-            R bm0[2], bp0[2], G0[2], bm1[2], bp1[2], G1[2];
-            adj_flux<R>(wy[ty][tx], wy[ty + 1][tx], wy[ty + 2][tx], p.nuy, p.order, bm0, bp0, G0);
-            adj_flux<R>(wy[ty + 1][tx], wy[ty + 2][tx], wy[ty + 3][tx], p.nuy, p.order, bm1, bp1, G1);
-            de += -p.nuy * (bp0[0] + bm1[0]) - p.nuy * (G1[0] - G0[0]);
-            dg = -p.nuy * (bp0[1] + bm1[1]) - p.nuy * (G1[1] - G0[1]);
-        }
-        ne += de;
-        nm += dm;
-        ng += dg;
+        ne = ne + de;
+        nm = nm + dm;
     }
     const size_t o = (size_t)gj * nx + gi;
     p.dst[0][o] = ne;

@@ -42,13 +42,14 @@ __device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
 // second-order correction flux F at edge e, from the waves at e and at its
 // left/right neighbour edges (indices into wave arrays W[6][stride]).
 // CFL number of one FP32 cell, the same expression wherever the FP32 path
-// reduces it: (|hu|/h + c)/dx + (|hv|/h + c)/dy, c = sqrt(g h).
+// reduces it: max((|hu|/h + c)/dx, (|hv|/h + c)/dy), c = sqrt(g h) (each
+// sweep of the split step is limited by its own Courant number).
 __device__ __forceinline__ float cfl_f32(float h, float hu, float hv, float g, float rdx,
                                          float rdy, int two_d) {
     const float q = rsqrtf(h), ih = q * q;
     const float gh = g * h, cc = gh * rsqrtf(gh);
     float s = (fabsf(hu) * ih + cc) * rdx;
-    if (two_d) s += (fabsf(hv) * ih + cc) * rdy;
+    if (two_d) s = fmaxf(s, (fabsf(hv) * ih + cc) * rdy);
     return s;
 }
 
@@ -100,6 +101,14 @@ __device__ __forceinline__ void edge_flux(const Wave6<R> &wm, const Wave6<R> &w,
     }
 }
 
+// One forward step of a TX x TY tile, dimensionally split (x-sweep of every
+// row, then y-sweep of the x-swept state).  The tile and a 2-cell halo
+// *including corners* are staged: the y-sweep of the tile needs the x-swept
+// state in its two halo rows, and x-sweeping a halo row needs its corner
+// cells.  Halo rows outside the grid come from index mapping, so their
+// x-sweep equals the x-sweep of the mirrored/copied interior row, which is
+// what ghost cells of the x-swept state hold.  Expressions follow the FP64
+// reference in order, so with contraction disabled the rounding matches it.
 template <typename R, bool PERT, bool TWO_D, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY)
 fwd_step_kernel(FwdParams<R> p) {
@@ -110,9 +119,11 @@ fwd_step_kernel(FwdParams<R> p) {
     constexpr int NEY = TWO_D ? RY - 1 : 1;
     constexpr int WYC = TWO_D ? TX : 1;
     __shared__ R s_h[RY][RX], s_mu[RY][RX], s_mv[RY][RX], s_eta[RY][RX];
-    __shared__ R s_u[RY][RX], s_v[RY][RX], s_sq[RY][RX];
-    __shared__ Wave6<R> wx[TY][NEX];
-    __shared__ Wave6<R> wy[NEY][WYC];
+    __shared__ R s_u[RY][RX], s_v[RY][RX], s_sq[RY][RX], s_b[RY][RX];
+    __shared__ union WaveBuf {
+        Wave6<R> x[RY][NEX];
+        Wave6<R> y[NEY][WYC];
+    } wb;
     __shared__ double red[32];
     __shared__ int am_last;
 
@@ -130,12 +141,9 @@ fwd_step_kernel(FwdParams<R> p) {
     const int nx = p.nx, ny = p.ny;
     const int i0 = blockIdx.x * TX - HX, j0 = blockIdx.y * TY - HY;
 
-    // 1) tile + halo (no corners) into shared memory, ghost cells fused
+    // 1) tile + halo with corners into shared memory, ghost cells by mapping
     for (int r = tid; r < RX * RY; r += NT) {
         const int ry = r / RX, rx = r - ry * RX;
-        const bool xin = rx >= HX && rx < HX + TX;
-        const bool yin = ry >= HY && ry < HY + TY;
-        if (!xin && !yin) continue;
         bool fx, fy = false;
         const int ci = ghost_index(i0 + rx, nx, p.bc.lo_x, p.bc.hi_x, &fx);
         int cj = 0;
@@ -154,21 +162,77 @@ fwd_step_kernel(FwdParams<R> p) {
         s_u[ry][rx] = mu / h;
         s_v[ry][rx] = mv / h;
         s_sq[ry][rx] = sqrt(h);
+        s_b[ry][rx] = b;
     }
     __syncthreads();
 
-    // 2) edge waves: x-edges of the TY core rows, y-edges of the TX core columns
-    for (int e = tid; e < TY * NEX; e += NT) {
-        const int row = e / NEX, k = e - row * NEX, ry = row + HY;
+    // 2) x-edge waves of every staged row
+    for (int e = tid; e < RY * NEX; e += NT) {
+        const int ry = e / NEX, k = e - ry * NEX;
         Wave6<R> w;
         fwave_roe<R>(p.g, s_h[ry][k], s_mu[ry][k], s_mv[ry][k], s_u[ry][k],
                      s_v[ry][k], s_sq[ry][k], s_eta[ry][k], s_h[ry][k + 1],
                      s_mu[ry][k + 1], s_mv[ry][k + 1], s_u[ry][k + 1],
                      s_v[ry][k + 1], s_sq[ry][k + 1], s_eta[ry][k + 1], w.uh,
                      w.ch, w.b1, w.b2, w.b3, w.vh);
-        wx[row][k] = w;
+        wb.x[ry][k] = w;
     }
+    __syncthreads();
+
+    // 3) x-sweep of the tile's columns in every staged row (in place)
+    const R nux = R(dt) / p.dx;
+    R xs[3][(RY + TY - 1) / TY];
+    int nrow = 0;
+    for (int ry = ty; ry < RY; ry += TY) {
+        const int cx = tx + HX;
+        R am0[3], ap0[3], F0[3], am1[3], ap1[3], F1[3];
+        edge_flux<R>(wb.x[ry][tx], wb.x[ry][tx + 1], wb.x[ry][tx + 2], nux, p.order, am0, ap0, F0);
+        edge_flux<R>(wb.x[ry][tx + 1], wb.x[ry][tx + 2], wb.x[ry][tx + 3], nux, p.order, am1, ap1, F1);
+        R dq[3];
+#pragma unroll
+        for (int m = 0; m < 3; m++) dq[m] = -nux * (ap0[m] + am1[m]) - nux * (F1[m] - F0[m]);
+        const R a0 = PERT ? s_eta[ry][cx] : s_h[ry][cx];
+        xs[0][nrow] = a0 + dq[0];
+        xs[1][nrow] = s_mu[ry][cx] + dq[1];
+        xs[2][nrow] = s_mv[ry][cx] + dq[2];
+        nrow++;
+    }
+    __syncthreads();  // all x-waves read; the cell arrays now take the x-swept state
+    {
+        int k = 0;
+        for (int ry = ty; ry < RY; ry += TY) {
+            const int cx = tx + HX;
+            R h, eta;
+            if (PERT) {
+                eta = xs[0][k];
+                h = eta + s_b[ry][cx];
+            } else {
+                h = xs[0][k];
+                eta = h + s_b[ry][cx];
+            }
+            const R mu = xs[1][k], mv = xs[2][k];
+            k++;
+            if (!TWO_D) {  // 1D: the x-swept state is the new state
+                s_h[ry][cx] = h; s_eta[ry][cx] = eta; s_mu[ry][cx] = mu; s_mv[ry][cx] = mv;
+                continue;
+            }
+            s_h[ry][cx] = h;
+            s_mu[ry][cx] = mu;
+            s_mv[ry][cx] = mv;
+            s_eta[ry][cx] = eta;
+            s_u[ry][cx] = mu / h;
+            s_v[ry][cx] = mv / h;
+            s_sq[ry][cx] = sqrt(h);
+        }
+    }
+    __syncthreads();
+
+    const int gi = blockIdx.x * TX + tx, gj = blockIdx.y * TY + ty;
+    const bool valid = gi < nx && gj < ny;
+    const int cx = tx + HX, cy = ty + HY;
+    R n0, n1, n2;
     if (TWO_D) {
+        // 4) y-edge waves of the x-swept state, tile columns
         for (int e = tid; e < NEY * TX; e += NT) {
             const int k = e / TX, col = e - k * TX, rx = col + HX;
             Wave6<R> w;
@@ -177,57 +241,47 @@ fwd_step_kernel(FwdParams<R> p) {
                          s_mv[k + 1][rx], s_mu[k + 1][rx], s_v[k + 1][rx],
                          s_u[k + 1][rx], s_sq[k + 1][rx], s_eta[k + 1][rx], w.uh,
                          w.ch, w.b1, w.b2, w.b3, w.vh);
-            wy[k][col] = w;
+            wb.y[k][col] = w;
         }
-    }
-    __syncthreads();
-
-    // 3) cell update from the fluctuations and corrections of its edges
-    const int gi = blockIdx.x * TX + tx, gj = blockIdx.y * TY + ty;
-    const bool valid = gi < nx && gj < ny;
-    double s_cell = 0.0;
-    {
-        const R nux = R(dt) / p.dx;
-        R am0[3], ap0[3], F0[3], am1[3], ap1[3], F1[3];
-        edge_flux<R>(wx[ty][tx], wx[ty][tx + 1], wx[ty][tx + 2], nux, p.order, am0, ap0, F0);
-        edge_flux<R>(wx[ty][tx + 1], wx[ty][tx + 2], wx[ty][tx + 3], nux, p.order, am1, ap1, F1);
-        R dq[3];
+        __syncthreads();
+        // 5) y-sweep (edge frame (h, hv, hu))
+        const R nuy = R(dt) / p.dy;
+        R bm0[3], bp0[3], G0[3], bm1[3], bp1[3], G1[3];
+        edge_flux<R>(wb.y[ty][tx], wb.y[ty + 1][tx], wb.y[ty + 2][tx], nuy, p.order, bm0, bp0, G0);
+        edge_flux<R>(wb.y[ty + 1][tx], wb.y[ty + 2][tx], wb.y[ty + 3][tx], nuy, p.order, bm1, bp1, G1);
+        R d[3];
 #pragma unroll
-        for (int m = 0; m < 3; m++) dq[m] = -nux * (ap0[m] + am1[m]) - nux * (F1[m] - F0[m]);
-        if (TWO_D) {
-            const R nuy = R(dt) / p.dy;
-            R bm0[3], bp0[3], G0[3], bm1[3], bp1[3], G1[3];
-            edge_flux<R>(wy[ty][tx], wy[ty + 1][tx], wy[ty + 2][tx], nuy, p.order, bm0, bp0, G0);
-            edge_flux<R>(wy[ty + 1][tx], wy[ty + 2][tx], wy[ty + 3][tx], nuy, p.order, bm1, bp1, G1);
-            R d[3];
-#pragma unroll
-            for (int m = 0; m < 3; m++) d[m] = -nuy * (bp0[m] + bm1[m]) - nuy * (G1[m] - G0[m]);
-            dq[0] += d[0];
-            dq[1] += d[2];
-            dq[2] += d[1];
-        }
-        const int cx = tx + HX, cy = ty + HY;
+        for (int m = 0; m < 3; m++) d[m] = -nuy * (bp0[m] + bm1[m]) - nuy * (G1[m] - G0[m]);
         const R a0 = PERT ? s_eta[cy][cx] : s_h[cy][cx];
-        const R n0 = a0 + dq[0];
-        const R n1 = s_mu[cy][cx] + dq[1];
-        const R n2 = s_mv[cy][cx] + dq[2];
-        if (valid) {
-            const size_t o = (size_t)gj * nx + gi;
-            const R hn = PERT ? n0 + p.bath[o] : n0;
-            o0[o] = n0;
-            o1[o] = n1;
-            if (TWO_D) o2[o] = n2;
-            if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(p.err, ERR_UNSTABLE);
-            // CFL number of the new state (per-cell term in the compute type)
-            const R c = sqrt(p.g * hn);
-            R s = (fabs(n1 / hn) + c) / p.dx;
-            if (TWO_D) s += (fabs(n2 / hn) + c) / p.dy;
-            s_cell = (double)s;
-            if (!(s_cell >= 0.0)) s_cell = 0.0;
-        }
+        n0 = a0 + d[0];
+        n2 = s_mv[cy][cx] + d[1];
+        n1 = s_mu[cy][cx] + d[2];
+    } else {
+        n0 = PERT ? s_eta[cy][cx] : s_h[cy][cx];
+        n1 = s_mu[cy][cx];
+        n2 = R(0);
     }
 
-    // 4) block max -> partial, last block reduces and advances the clock
+    double s_cell = 0.0;
+    if (valid) {
+        const size_t o = (size_t)gj * nx + gi;
+        const R hn = PERT ? n0 + p.bath[o] : n0;
+        o0[o] = n0;
+        o1[o] = n1;
+        if (TWO_D) o2[o] = n2;
+        if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(p.err, ERR_UNSTABLE);
+        // CFL number of the new state: max over directions of (|u|+c)/d
+        const R c = sqrt(p.g * hn);
+        R s = (fabs(n1 / hn) + c) / p.dx;
+        if (TWO_D) {
+            const R sy = (fabs(n2 / hn) + c) / p.dy;
+            if (sy > s) s = sy;
+        }
+        s_cell = (double)s;
+        if (!(s_cell >= 0.0)) s_cell = 0.0;
+    }
+
+    // 6) block max -> partial, last block reduces and advances the clock
     const double bm = block_max<NT>(s_cell, red);
     const int bid = blockIdx.x + blockIdx.y * gridDim.x;
     if (tid == 0) {
@@ -275,7 +329,10 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
         } else {
             const R c = sqrt(p.g * h);
             R s = (fabs(q1[k] / h) + c) / p.dx;
-            if (p.two_d) s += (fabs(q2[k] / h) + c) / p.dy;
+            if (p.two_d) {
+                const R sy = (fabs(q2[k] / h) + c) / p.dy;
+                if (sy > s) s = sy;
+            }
             sd = (double)s;
         }
         if (!(h > R(0))) atomicOr(p.err, ERR_UNSTABLE);

@@ -1,13 +1,17 @@
 // fwd_tiles.cuh -- FP32 tile machinery of the forward step, shared by the
 // single-grid step (fwd_f32.cu) and the batched patch step (patches.cu).
 //
-// A tile is TX x TY cells of one grid ("view").  Phases per tile: (0) stage
-// the tile and a 2-cell halo (no corners) as derived cell data in shared
-// memory, (1) solve every x- and y-edge the tile needs, (2) form every
-// edge's net fluxes, limiter evaluated once per edge, (3) update the cells.
-// Each phase is a flat loop of independent items over 256 threads.  A
-// persistent block walks its share of a tile list; the raw values of the
-// next tile are loaded into registers while the current one is computed.
+// A tile is TX x TY cells of one grid ("view").  The step is dimensionally
+// split (x-sweep, then y-sweep of the x-swept state).  Phases per tile:
+// (0) stage the tile and a 2-cell halo including corners as derived cell
+// data in shared memory; (1) x-edge waves of every staged row; (2) their net
+// fluxes (limiter once per edge); (3) x-sweep of the tile's columns in every
+// staged row, in place (the y-sweep needs the x-swept state in the two halo
+// rows); (4) y-edge waves of the x-swept state; (5) their net fluxes;
+// (6) y-sweep update of the tile's cells.  Each phase is a flat loop of
+// independent items over 256 threads.  A persistent block walks its share of
+// a tile list; the raw values of the next tile are loaded into registers
+// while the current one is computed.
 //
 // The MC-limited correction needs no division by the wave norm: for
 // Z = b (1, s, vhat) and its upwind neighbour Zu = bu (1, su, vu),
@@ -129,18 +133,16 @@ template <int TX, int TY>
 struct Smem {
     static constexpr int RX = TX + 4, RY = TY + 4;
     static constexpr int NEX = TX + 3, NEY = TY + 3;
-    union U {   // cell data of tile + halo; reused for the net fluxes
-        struct C {
-            float h[RY][RX], mu[RY][RX], mv[RY][RX], u[RY][RX], v[RY][RX], sq[RY][RX],
-                eta[RY][RX];
-        } c;
-        struct N {
-            float xl[3][TY][TX + 1], xr[3][TY][TX + 1];
-            float yl[3][TY + 1][TX], yr[3][TY + 1][TX];
-        } n;
-    } u;
-    float xw[6][TY][NEX];
-    float yw[6][NEY][TX];
+    // cell data of the tile + halo (with corners); x-swept in place
+    float h[RY][RX], mu[RY][RX], mv[RY][RX], u[RY][RX], v[RY][RX], sq[RY][RX], eta[RY][RX];
+    union W {   // edge waves: x (phases 1-2), then y (phases 4-5)
+        float x[6][RY][NEX];
+        float y[6][NEY][TX];
+    } w;
+    union N {   // net fluxes: x (phases 2-3), then y (phases 5-6)
+        struct X { float l[3][RY][TX + 1], r[3][RY][TX + 1]; } x;
+        struct Y { float l[3][TY + 1][TX], r[3][TY + 1][TX]; } y;
+    } n;
 };
 
 // Raw values of a thread's share of a tile's staged region (RPT items).
@@ -159,9 +161,8 @@ __device__ __forceinline__ void load_raw(const View &V, int i0, int j0, Raw<TX, 
 #pragma unroll
     for (int k = 0; k < Raw<TX, TY>::RPT; k++) {
         const int r = threadIdx.x + k * NT;
+        if (r >= RX * RY) continue;
         const int ry = r / RX, rx = r - ry * RX;
-        const bool xin = rx >= 2 && rx < TX + 2, yin = ry >= 2 && ry < TY + 2;
-        if (r >= RX * RY || (!xin && !yin)) continue;
         int ci = i0 + rx - 2, cj = j0 + ry - 2;
         bool fx = false, fy = false;
         if (!interior) {
@@ -177,7 +178,36 @@ __device__ __forceinline__ void load_raw(const View &V, int i0, int j0, Raw<TX, 
     }
 }
 
-// Phases 0-3 for one tile whose raw values are in R.  Returns the tile's
+template <typename SM>
+__device__ __forceinline__ void put_cell(SM &S, int ry, int rx, float eta, float h, float mu,
+                                         float mv) {
+    const float q = rsqrtf(h);
+    const float ih = q * q;
+    S.h[ry][rx] = h;
+    S.mu[ry][rx] = mu;
+    S.mv[ry][rx] = mv;
+    S.u[ry][rx] = mu * ih;
+    S.v[ry][rx] = mv * ih;
+    S.sq[ry][rx] = h * q;
+    S.eta[ry][rx] = eta;
+}
+
+// Net fluxes of edges e-1, e, e+1 (waves w[q][row][*]) -> L/R of edge e.
+template <typename WA>
+__device__ __forceinline__ void net_at(const WA &w, int row, int e, float nu, int order,
+                                       float L[3], float Rr[3]) {
+    EdgeS a, b, c;
+    a.s1 = w[0][row][e - 1]; a.s3 = w[1][row][e - 1]; a.vh = w[2][row][e - 1];
+    a.b1 = w[3][row][e - 1]; a.b2 = w[4][row][e - 1]; a.b3 = w[5][row][e - 1];
+    b.s1 = w[0][row][e]; b.s3 = w[1][row][e]; b.vh = w[2][row][e];
+    b.b1 = w[3][row][e]; b.b2 = w[4][row][e]; b.b3 = w[5][row][e];
+    c.s1 = w[0][row][e + 1]; c.s3 = w[1][row][e + 1]; c.vh = w[2][row][e + 1];
+    c.b1 = w[3][row][e + 1]; c.b2 = w[4][row][e + 1]; c.b3 = w[5][row][e + 1];
+    if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nu, order, L, Rr);
+    else net1<false>(a, b, c, nu, order, L, Rr);
+}
+
+// Phases 0-6 for one tile whose raw values are in R.  Returns the tile's
 // maximum CFL number over its new cells.
 template <int TX, int TY>
 __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, int i0, int j0,
@@ -185,117 +215,93 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
                                               float g, int order, bool &bad) {
     constexpr int RX = TX + 4, RY = TY + 4, NEX = TX + 3, NEY = TY + 3;
     const int tid = threadIdx.x;
-    // phase 0: derived cell data
+    // phase 0: derived cell data of the whole staged region
 #pragma unroll
     for (int k = 0; k < Raw<TX, TY>::RPT; k++) {
         const int r = tid + k * NT;
+        if (r >= RX * RY) continue;
         const int ry = r / RX, rx = r - ry * RX;
-        const bool xin = rx >= 2 && rx < TX + 2, yin = ry >= 2 && ry < TY + 2;
-        if (r >= RX * RY || (!xin && !yin)) continue;
-        const float h = R.eta[k] + R.hb[k];
-        const float q = rsqrtf(h);
-        const float ih = q * q;
-        S.u.c.h[ry][rx] = h;
-        S.u.c.mu[ry][rx] = R.mu[k];
-        S.u.c.mv[ry][rx] = R.mv[k];
-        S.u.c.u[ry][rx] = R.mu[k] * ih;
-        S.u.c.v[ry][rx] = R.mv[k] * ih;
-        S.u.c.sq[ry][rx] = h * q;
-        S.u.c.eta[ry][rx] = R.eta[k];
+        put_cell(S, ry, rx, R.eta[k], R.eta[k] + R.hb[k], R.mu[k], R.mv[k]);
     }
     __syncthreads();
-    constexpr int CPT = TX * TY / NT;
-    float own_eta[CPT], own_mu[CPT], own_mv[CPT], own_h[CPT];
-#pragma unroll
-    for (int k = 0; k < CPT; k++) {
-        const int c = tid + k * NT, ry = c / TX + 2, rx = c % TX + 2;
-        own_eta[k] = S.u.c.eta[ry][rx];
-        own_mu[k] = S.u.c.mu[ry][rx];
-        own_mv[k] = S.u.c.mv[ry][rx];
-        own_h[k] = S.u.c.h[ry][rx];
-    }
-    // phase 1: edge waves
-    for (int i = tid; i < TY * NEX + NEY * TX; i += NT) {
-        if (i < TY * NEX) {
-            const int row = i / NEX, e = i - row * NEX, ry = row + 2;
-            const EdgeS w = solve1(g, S.u.c.h[ry][e], S.u.c.mu[ry][e], S.u.c.mv[ry][e],
-                                   S.u.c.u[ry][e], S.u.c.v[ry][e], S.u.c.sq[ry][e],
-                                   S.u.c.eta[ry][e], S.u.c.h[ry][e + 1], S.u.c.mu[ry][e + 1],
-                                   S.u.c.mv[ry][e + 1], S.u.c.u[ry][e + 1], S.u.c.v[ry][e + 1],
-                                   S.u.c.sq[ry][e + 1], S.u.c.eta[ry][e + 1]);
-            S.xw[0][row][e] = w.s1; S.xw[1][row][e] = w.s3; S.xw[2][row][e] = w.vh;
-            S.xw[3][row][e] = w.b1; S.xw[4][row][e] = w.b2; S.xw[5][row][e] = w.b3;
-        } else {
-            const int k = i - TY * NEX, e = k / TX, col = k - e * TX, rx = col + 2;
-            const EdgeS w = solve1(g, S.u.c.h[e][rx], S.u.c.mv[e][rx], S.u.c.mu[e][rx],
-                                   S.u.c.v[e][rx], S.u.c.u[e][rx], S.u.c.sq[e][rx],
-                                   S.u.c.eta[e][rx], S.u.c.h[e + 1][rx], S.u.c.mv[e + 1][rx],
-                                   S.u.c.mu[e + 1][rx], S.u.c.v[e + 1][rx], S.u.c.u[e + 1][rx],
-                                   S.u.c.sq[e + 1][rx], S.u.c.eta[e + 1][rx]);
-            S.yw[0][e][col] = w.s1; S.yw[1][e][col] = w.s3; S.yw[2][e][col] = w.vh;
-            S.yw[3][e][col] = w.b1; S.yw[4][e][col] = w.b2; S.yw[5][e][col] = w.b3;
-        }
+    // phase 1: x-edge waves of every staged row (edge e between cols e, e+1)
+    for (int i = tid; i < RY * NEX; i += NT) {
+        const int ry = i / NEX, e = i - ry * NEX;
+        const EdgeS w = solve1(g, S.h[ry][e], S.mu[ry][e], S.mv[ry][e], S.u[ry][e], S.v[ry][e],
+                               S.sq[ry][e], S.eta[ry][e], S.h[ry][e + 1], S.mu[ry][e + 1],
+                               S.mv[ry][e + 1], S.u[ry][e + 1], S.v[ry][e + 1],
+                               S.sq[ry][e + 1], S.eta[ry][e + 1]);
+        S.w.x[0][ry][e] = w.s1; S.w.x[1][ry][e] = w.s3; S.w.x[2][ry][e] = w.vh;
+        S.w.x[3][ry][e] = w.b1; S.w.x[4][ry][e] = w.b2; S.w.x[5][ry][e] = w.b3;
     }
     __syncthreads();
-    // phase 2: net fluxes (the cell data are dead; their space holds the nets)
-    for (int i = tid; i < TY * (TX + 1) + (TY + 1) * TX; i += NT) {
-        EdgeS a, b, c;
-        float nu;
-        const bool isx = i < TY * (TX + 1);
-        int row = 0, e = 0, col = 0;
-        if (isx) {
-            row = i / (TX + 1);
-            e = 1 + (i - row * (TX + 1));
-#define SWADJ_LOADX(W, E)                                                         \
-    W.s1 = S.xw[0][row][E]; W.s3 = S.xw[1][row][E]; W.vh = S.xw[2][row][E];     \
-    W.b1 = S.xw[3][row][E]; W.b2 = S.xw[4][row][E]; W.b3 = S.xw[5][row][E];
-            SWADJ_LOADX(a, e - 1) SWADJ_LOADX(b, e) SWADJ_LOADX(c, e + 1)
-#undef SWADJ_LOADX
-            nu = nux;
-        } else {
-            const int k = i - TY * (TX + 1);
-            e = 1 + k / TX;
-            col = k - (e - 1) * TX;
-#define SWADJ_LOADY(W, E)                                                         \
-    W.s1 = S.yw[0][E][col]; W.s3 = S.yw[1][E][col]; W.vh = S.yw[2][E][col];     \
-    W.b1 = S.yw[3][E][col]; W.b2 = S.yw[4][E][col]; W.b3 = S.yw[5][E][col];
-            SWADJ_LOADY(a, e - 1) SWADJ_LOADY(b, e) SWADJ_LOADY(c, e + 1)
-#undef SWADJ_LOADY
-            nu = nuy;
-        }
+    // phase 2: x net fluxes of edges 1 .. TX+1 in every staged row
+    for (int i = tid; i < RY * (TX + 1); i += NT) {
+        const int ry = i / (TX + 1), e = 1 + (i - ry * (TX + 1));
         float L[3], Rr[3];
-        if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nu, order, L, Rr);
-        else net1<false>(a, b, c, nu, order, L, Rr);
-        if (isx) {
+        net_at(S.w.x, ry, e, nux, order, L, Rr);
 #pragma unroll
-            for (int m = 0; m < 3; m++) { S.u.n.xl[m][row][e - 1] = L[m]; S.u.n.xr[m][row][e - 1] = Rr[m]; }
-        } else {
-#pragma unroll
-            for (int m = 0; m < 3; m++) { S.u.n.yl[m][e - 1][col] = L[m]; S.u.n.yr[m][e - 1][col] = Rr[m]; }
-        }
+        for (int m = 0; m < 3; m++) { S.n.x.l[m][ry][e - 1] = L[m]; S.n.x.r[m][ry][e - 1] = Rr[m]; }
     }
     __syncthreads();
-    // phase 3: update; x nets: left edge -> R at index col, right edge -> L at
-    // col + 1; y nets are in (h, hv, hu) order
+    // phase 3: x-sweep of the tile's columns in every staged row, in place
+    for (int i = tid; i < RY * TX; i += NT) {
+        const int ry = i / TX, col = i - ry * TX, rx = col + 2;
+        // left edge of column col -> R at index col, right edge -> L at col + 1
+        const float d0 = -nux * (S.n.x.r[0][ry][col] + S.n.x.l[0][ry][col + 1]);
+        const float d1 = -nux * (S.n.x.r[1][ry][col] + S.n.x.l[1][ry][col + 1]);
+        const float d2 = -nux * (S.n.x.r[2][ry][col] + S.n.x.l[2][ry][col + 1]);
+        put_cell(S, ry, rx, S.eta[ry][rx] + d0, S.h[ry][rx] + d0, S.mu[ry][rx] + d1,
+                 S.mv[ry][rx] + d2);
+    }
+    __syncthreads();
+    // phase 4: y-edge waves of the x-swept state, tile columns (frame (h, hv, hu))
+    for (int i = tid; i < NEY * TX; i += NT) {
+        const int e = i / TX, col = i - e * TX, rx = col + 2;
+        const EdgeS w = solve1(g, S.h[e][rx], S.mv[e][rx], S.mu[e][rx], S.v[e][rx], S.u[e][rx],
+                               S.sq[e][rx], S.eta[e][rx], S.h[e + 1][rx], S.mv[e + 1][rx],
+                               S.mu[e + 1][rx], S.v[e + 1][rx], S.u[e + 1][rx],
+                               S.sq[e + 1][rx], S.eta[e + 1][rx]);
+        S.w.y[0][e][col] = w.s1; S.w.y[1][e][col] = w.s3; S.w.y[2][e][col] = w.vh;
+        S.w.y[3][e][col] = w.b1; S.w.y[4][e][col] = w.b2; S.w.y[5][e][col] = w.b3;
+    }
+    __syncthreads();
+    // phase 5: y net fluxes of edges 1 .. TY+1 (transposed indexing)
+    for (int i = tid; i < (TY + 1) * TX; i += NT) {
+        const int e = 1 + i / TX, col = i - (e - 1) * TX;
+        EdgeS a, b, c;
+#define SWADJ_LOADY(W, E)                                                            \
+    W.s1 = S.w.y[0][E][col]; W.s3 = S.w.y[1][E][col]; W.vh = S.w.y[2][E][col];     \
+    W.b1 = S.w.y[3][E][col]; W.b2 = S.w.y[4][E][col]; W.b3 = S.w.y[5][E][col];
+        SWADJ_LOADY(a, e - 1) SWADJ_LOADY(b, e) SWADJ_LOADY(c, e + 1)
+#undef SWADJ_LOADY
+        float L[3], Rr[3];
+        if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nuy, order, L, Rr);
+        else net1<false>(a, b, c, nuy, order, L, Rr);
+#pragma unroll
+        for (int m = 0; m < 3; m++) { S.n.y.l[m][e - 1][col] = L[m]; S.n.y.r[m][e - 1][col] = Rr[m]; }
+    }
+    __syncthreads();
+    // phase 6: y-sweep update of the tile's cells; y nets are in (h, hv, hu)
+    // order, lower edge of row -> R at index row, upper edge -> L at row + 1
     float smax = 0.f;
     const float rdx = 1.f / V.dx, rdy = 1.f / V.dy;
+    constexpr int CPT = TX * TY / NT;
 #pragma unroll
     for (int k = 0; k < CPT; k++) {
         const int c = tid + k * NT, row = c / TX, col = c % TX;
         const int gi = i0 + col, gj = j0 + row;
+        const int ry = row + 2, rx = col + 2;
         if (gi < V.nx && gj < V.ny) {
-            const float d0 = -nux * (S.u.n.xr[0][row][col] + S.u.n.xl[0][row][col + 1])
-                             - nuy * (S.u.n.yr[0][row][col] + S.u.n.yl[0][row + 1][col]);
-            const float d1 = -nux * (S.u.n.xr[1][row][col] + S.u.n.xl[1][row][col + 1])
-                             - nuy * (S.u.n.yr[2][row][col] + S.u.n.yl[2][row + 1][col]);
-            const float d2 = -nux * (S.u.n.xr[2][row][col] + S.u.n.xl[2][row][col + 1])
-                             - nuy * (S.u.n.yr[1][row][col] + S.u.n.yl[1][row + 1][col]);
-            const float ne = own_eta[k] + d0, nmu = own_mu[k] + d1, nmv = own_mv[k] + d2;
+            const float d0 = -nuy * (S.n.y.r[0][row][col] + S.n.y.l[0][row + 1][col]);
+            const float d2 = -nuy * (S.n.y.r[1][row][col] + S.n.y.l[1][row + 1][col]);
+            const float d1 = -nuy * (S.n.y.r[2][row][col] + S.n.y.l[2][row + 1][col]);
+            const float ne = S.eta[ry][rx] + d0, nmu = S.mu[ry][rx] + d1, nmv = S.mv[ry][rx] + d2;
             const size_t o = (size_t)gj * V.nx + gi;
             V.o0[o] = ne;
             V.o1[o] = nmu;
             V.o2[o] = nmv;
-            const float h = own_h[k] + d0;
+            const float h = S.h[ry][rx] + d0;
             bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
             smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
         }

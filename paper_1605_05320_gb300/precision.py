@@ -62,7 +62,7 @@ def main(argv=None):
     L = a.n * 1e3
     sc = synth.config2(n=a.n, L=L, seed=4096, n_seamounts=40, amp=0.2, adj_n=a.adj_n,
                        n_gauges=16, shelf_frac=0.85)
-    dt0 = 0.75 / (2.0 * np.sqrt(synth.G * 4000.0) / sc.grid.dx)
+    dt0 = 0.75 / (np.sqrt(synth.G * 4000.0) / sc.grid.dx)
     sc.t_f = a.steps * dt0 * 1.001
     sc.t_s = 0.32 * sc.t_f
     t0 = time.perf_counter()

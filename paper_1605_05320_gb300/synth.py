@@ -157,14 +157,16 @@ def config2(n: int = 2048, L: float = 2048e3, seed: int = 1605,
             shelf_frac: float = 1740.0 / 2048.0) -> Scenario:
     """2D n x n grid on [0, L]^2 (1 km cells at n = 2048).  Gaussian source of
     amplitude `amp` and width 30 km at a seeded basin point 300-700 km from the
-    target; adjoint data a 10 km Gaussian in eta at a shelf point; t_s / t_f
+    target; adjoint data a 10 km Gaussian in eta at the shelf break; t_s / t_f
     set to the paper's ratio 3.5 h / 11 h."""
     rng = np.random.default_rng(seed)
     grid = GridSpec(2, n, n, 0.0, 0.0, L / n, L / n)
     sm = seamounts(L, seed + 1, n_seamounts, 1600.0 / 2048.0)
     B = basin_bathymetry(grid, L, seed, n_seamounts, shelf_frac=shelf_frac,
                          seamount_params=sm)
-    target = (1900.0 / 2048.0 * L, 0.5 * L)
+    # target at the shelf break: waves from 300-700 km away reach it within
+    # the time window [t_s, t_f]
+    target = (shelf_frac * L, 0.5 * L)
     sx, sy = source_point(rng, target, L)
     eta0 = gaussian_field(grid, sx, sy, amp, src_width)
     eta0 = np.where(eta0 < 1e-12, 0.0, eta0)
@@ -175,9 +177,10 @@ def config2(n: int = 2048, L: float = 2048e3, seed: int = 1605,
                              shelf_frac=shelf_frac, seamount_params=sm)
     phi = np.zeros((3, adj_grid.n))
     phi[0] = gaussian_field(adj_grid, target[0], target[1], 1.0, 10e3)
-    # dt0 ~ 0.75 / (2 sqrt(g 4000) / dx) is the first CFL step in the basin;
-    # t_f spans 2000 such steps, so the forward run to t_f is ~2000 steps.
-    dt0 = 0.75 / (2.0 * np.sqrt(G * 4000.0) / grid.dx)
+    # dt0 ~ 0.75 / (sqrt(g 4000) / dx) is the first CFL step in the basin
+    # (per-direction Courant number of the split step); t_f spans 2000 such
+    # steps, so the forward run to t_f is ~2000 steps.
+    dt0 = 0.75 / (np.sqrt(G * 4000.0) / grid.dx)
     t_f = 2000.0 * dt0
     gx = np.concatenate([rng.uniform(0.1 * L, 0.7 * L, n_gauges // 2),
                          target[0] - rng.uniform(5e3, 100e3, n_gauges - n_gauges // 2)])
