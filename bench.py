@@ -51,6 +51,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Maximum of a per-rank number over all ranks (a timing taken on every
+    rank; the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, steps: int, world: int, ms_max: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak
+    scaling: every rank processes the same independent workload)."""
+    return units_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -291,15 +309,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end), world, device)
     assert S.swa_sync_status(hs) == 0
     ms_step = ms / args.steps
     cu = cell_updates(scen)
-    value = cu * args.steps * world / (ms * 1e-3)
+    value = whole_job_rate(cu, args.steps, world, ms)
 
     # kernel timings
     fwd_ms = [e[0].elapsed_time(e[1]) for d in evs for e in d["fwd"]]
@@ -350,14 +364,10 @@ def run_ours(args, rank, world, local_rank):
         stream.synchronize()
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, device)
     h2d = 3 * scen.n * 8 + 3 * scen.adj.n * 8
     d2h = scen.series.numel() * 8 + scen.counts.numel() * 8
-    e2e = {"value": cu * args.steps * world / (ms_e2e * 1e-3), "unit": "cell-updates/s",
+    e2e = {"value": whole_job_rate(cu, args.steps, world, ms_e2e), "unit": "cell-updates/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "ms_per_step": ms_e2e / args.steps}
 

@@ -228,6 +228,15 @@ int swa_flag_cells(const swa_grid *grid, const swa_snapstore *store,
                    uint8_t *flags_dev, float *maxip_dev, long long *count_dev,
                    void *stream);
 
+/*
+ * Surface flagging, the default criterion the paper compares adjoint
+ * flagging against (Sec. 6): flags_dev[i] = 1 where the cell is wet and its
+ * surface elevation relative to sea level exceeds tol, |eta| > tol.
+ * *count_dev (device int64, overwritten) receives the number of flags.
+ */
+int swa_flag_surface(const swa_grid *grid, double tol, uint8_t *flags_dev,
+                     long long *count_dev, void *stream);
+
 /* ================================ gauges =================================
  * Surface elevation eta = h + B at n points xy_dev[2k], xy_dev[2k+1]
  * (device, FP64) by bilinear interpolation of cell centres, clamped to the

@@ -114,6 +114,9 @@ def _load():
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_uint8), _D]
         lib.orc_flag.restype = ctypes.c_long
+        lib.orc_flag_surface.argtypes = [G, _D, _D, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_uint8)]
+        lib.orc_flag_surface.restype = ctypes.c_long
         lib.orc_gauge.argtypes = [G, _D, _D, ctypes.c_long, _D, _D]
         lib.orc_gauge.restype = None
         lib.orc_num_threads.restype = ctypes.c_int
@@ -234,6 +237,15 @@ def flag(fgrid: Grid, h, hu, hv, B, t, agrid: Grid, hbar_adj, snaps, tau,
                            flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                            _p(m))
     return flags, m, int(cnt)
+
+
+def flag_surface(grid: Grid, h, B, tol):
+    """Surface flags |eta| > tol (uint8 [n]) and their count."""
+    flags = np.zeros(grid.n, dtype=np.uint8)
+    g = grid.c()
+    c = _load().orc_flag_surface(ctypes.byref(g), _p(_f64(h)), _p(_f64(B)), float(tol),
+                                 flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+    return flags, int(c)
 
 
 def gauge(grid: Grid, h, B, xy):

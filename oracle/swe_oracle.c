@@ -32,6 +32,7 @@
  *                    linear interpolation in time (INTERP), bilinear spatial
  *                    interpolation of the adjoint (Sec. 4), zero where the
  *                    adjoint is dry (Sec. 6).
+ *   orc_flag_surface surface flagging |eta| > tol (Sec. 6 comparator).
  *   orc_gauge        bilinear interpolation of cell-centre eta (Sec. 6 gauges).
  */
 #include <math.h>
@@ -719,6 +720,24 @@ long orc_flag(const orc_grid *F, const double *h, const double *hu,
             flags[o] = f;
             count += f;
         }
+    }
+    return count;
+}
+
+/*
+ * Surface flagging (the default refinement criterion the paper compares
+ * against, Sec. 6): flag a wet cell when its surface elevation relative to sea
+ * level exceeds the tolerance, |eta| > tol, eta = h + B.  Returns the count.
+ */
+long orc_flag_surface(const orc_grid *G, const double *h, const double *B, double tol,
+                      uint8_t *flags) {
+    size_t n = (size_t)G->nx * G->ny;
+    long count = 0;
+    for (size_t k = 0; k < n; k++) {
+        double eta = h[k] + B[k];
+        uint8_t f = (h[k] > G->dry_tol && fabs(eta) > tol) ? 1 : 0;
+        flags[k] = f;
+        count += f;
     }
     return count;
 }

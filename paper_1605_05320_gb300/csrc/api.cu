@@ -842,6 +842,35 @@ int swa_flag_cells(const swa_grid *g, const swa_snapstore *s, double t_s, double
     return flag_dispatch<float, float>(g, s, t_s, t_f, tol, mode, flags_dev, maxip_dev, count_dev, st);
 }
 
+}  // extern "C"
+
+template <typename R>
+static int surface_dispatch(const swa_grid *g, double tol, uint8_t *flags, long long *count,
+                            cudaStream_t st) {
+    SurfParams<R> p{};
+    p.n = g->n;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) p.q[b][k] = (const R *)g->q[b][k];
+    p.bath = (const R *)g->bath;
+    p.clk = g->clk;
+    p.tol = (R)tol;
+    p.dry_tol = (R)g->d.dry_tol;
+    p.flags = flags;
+    p.count = (unsigned long long *)count;
+    return surface_launch<R>(p, st);
+}
+
+extern "C" {
+
+int swa_flag_surface(const swa_grid *g, double tol, uint8_t *flags_dev, long long *count_dev,
+                     void *stream) {
+    if (!g || !flags_dev || !count_dev) return set_error(SWA_EINVAL, "null argument");
+    if (!(tol >= 0)) return set_error(SWA_EINVAL, "tol must be >= 0");
+    if (g->d.precision == SWA_FP64)
+        return surface_dispatch<double>(g, tol, flags_dev, count_dev, S(stream));
+    return surface_dispatch<float>(g, tol, flags_dev, count_dev, S(stream));
+}
+
 // ------------------------------------------------------------------ gauges
 int swa_gauge_sample(const swa_grid *g, int n, const double *xy_dev, double *eta_dev,
                      void *stream) {

@@ -278,6 +278,35 @@ template int flag_launch<double, float>(const FlagParams<double, float> &, cudaS
 template int flag_launch<float, float>(const FlagParams<float, float> &, cudaStream_t);
 template int flag_launch<float, double>(const FlagParams<float, double> &, cudaStream_t);
 
+// |eta| > tol on wet cells, eta stored (float) or h + B (double).
+template <typename R>
+__global__ void __launch_bounds__(256) surface_kernel(SurfParams<R> p) {
+    const int cur = p.clk->cur;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    if (i < p.n) {
+        const R a = p.q[cur][0][i], b = p.bath[i];
+        R h, eta;
+        if (sizeof(R) == 4) { eta = a; h = a + b; }
+        else { h = a; eta = a + b; }
+        f = (h > p.dry_tol && fabs(eta) > p.tol) ? 1 : 0;
+        p.flags[i] = (uint8_t)f;
+    }
+    const int cnt = __syncthreads_count(f);
+    if (threadIdx.x == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
+}
+
+template <typename R>
+int surface_launch(const SurfParams<R> &p, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return swadj_host::cuda_check(e, "surface count reset");
+    surface_kernel<R><<<(unsigned)((p.n + 255) / 256), 256, 0, st>>>(p);
+    return swadj_host::cuda_check(cudaGetLastError(), "surface_kernel");
+}
+
+template int surface_launch<double>(const SurfParams<double> &, cudaStream_t);
+template int surface_launch<float>(const SurfParams<float> &, cudaStream_t);
+
 template <typename R>
 __global__ void gauge_kernel(GaugeParams<R> p) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;

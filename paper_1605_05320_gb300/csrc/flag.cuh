@@ -35,6 +35,20 @@ template <typename R, typename S>
 int flag_launch(const FlagParams<R, S> &p, cudaStream_t st);
 
 template <typename R>
+struct SurfParams {
+    size_t n;
+    const R *q[2][3];
+    const R *bath;
+    const DevClock *clk;
+    R tol, dry_tol;
+    uint8_t *flags;
+    unsigned long long *count;
+};
+
+template <typename R>
+int surface_launch(const SurfParams<R> &p, cudaStream_t st);
+
+template <typename R>
 struct GaugeParams {
     int nx, ny, two_d;
     double x_lo, y_lo, dx, dy;

@@ -39,7 +39,7 @@ EXPORTS = [
     "swa_snapstore_workspace_bytes", "swa_create_snapstore",
     "swa_destroy_snapstore", "swa_store_snapshot", "swa_run_adjoint",
     "swa_snapstore_info",
-    "swa_flag_cells", "swa_gauge_sample",
+    "swa_flag_cells", "swa_flag_surface", "swa_gauge_sample",
     "swa_step_forward_static",
     "swa_patches_workspace_bytes", "swa_create_patches", "swa_destroy_patches",
     "swa_patches_set_state", "swa_patches_start_level", "swa_patches_get_state",
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
         "swa_snapstore_info": ([_V, _P(_I), _V, _I], _I),
         "swa_flag_cells": ([_V, _V, _D, _D, _D, _I, _V, _V, _V, _V], _I),
         "swa_gauge_sample": ([_V, _I, _V, _V, _V], _I),
+        "swa_flag_surface": ([_V, _D, _V, _V, _V], _I),
         "swa_step_forward_static": ([D, _P(_V), _P(_V), _V, _D, _V, _V], _I),
         "swa_patches_workspace_bytes": ([_I, _V, D], _SZ),
         "swa_create_patches": ([_I, _V, _P(_V), D, _V, _SZ, _V, _P(_V)], _I),
@@ -311,6 +312,11 @@ def swa_flag_cells(grid, store, t_s, t_f, tol, mode, flags_dev, maxip_dev, count
     return _chk(load().swa_flag_cells(grid, store, float(t_s), float(t_f), float(tol),
                                       int(mode), _ptr(flags_dev), _ptr(maxip_dev),
                                       _ptr(count_dev), _stream(stream)))
+
+
+def swa_flag_surface(grid, tol, flags_dev, count_dev, stream=None):
+    return _chk(load().swa_flag_surface(grid, float(tol), _ptr(flags_dev), _ptr(count_dev),
+                                        _stream(stream)))
 
 
 def swa_gauge_sample(grid, n, xy_dev, eta_dev, stream=None):

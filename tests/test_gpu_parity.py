@@ -317,3 +317,24 @@ def test_full_size_step_sampled_against_oracle_windows(S, precision):
         else:
             assert abs(s1["eta"][o] - (h[40] + Bs[o])) <= 2e-6
             assert abs(s1["hu"][o] - u[40]) <= 2e-5 and abs(s1["hv"][o] - v[40]) <= 2e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_surface_flags_match_oracle(S, precision):
+    sc = synth.small_2d(120, 80, seed=14, amp=0.6)
+    p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
+    g = S.Grid(desc_of(S, sc.grid, p), sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    g.step(30, 1e12)
+    flags = torch.zeros(sc.grid.n, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    S.swa_flag_surface(g.h, 0.09, flags, cnt)
+    torch.cuda.synchronize()
+    Bs = bath_seen(sc.B, p == S.SWA_FP32)
+    h, hu, hv, _, _ = run_oracle_forward(sc, 2, (0, 0, 0, 0), 30, B=Bs)
+    f_ref, c_ref = O.flag_surface(O.Grid.from_spec(sc.grid), h, Bs, 0.09)
+    f = flags.cpu().numpy()
+    eta = h + Bs
+    near = np.abs(np.abs(eta) - 0.09) <= (1e-12 if precision == "fp64" else 1e-5)
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert c_ref > 0 and int(cnt.item()) == int(f.sum())

@@ -161,3 +161,27 @@ def test_gauge_bilinear_and_clamp():
     xcl = np.clip(xy[:, 0], xc[0], xc[-1])
     ycl = np.clip(xy[:, 1], yc[0], yc[-1])
     assert np.allclose(got, f(xcl, ycl), rtol=0, atol=1e-12)
+
+
+def test_surface_flags_are_the_disc_of_a_gaussian_hump():
+    """|eta| > tol for eta = A exp(-r^2/w^2) is the disc r < w sqrt(ln(A/tol)):
+    the flagged cells are exactly the cell centres inside it; a dry cell is
+    never flagged, and a trough flags like a crest."""
+    n, d = 80, 1000.0
+    g = O.Grid(2, n, n, 0.0, 0.0, d, d)
+    xc = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(xc, xc)
+    A, w, tol = 0.5, 12e3, 0.14
+    r2 = (X - 37.3e3) ** 2 + (Y - 41.9e3) ** 2
+    eta = A * np.exp(-r2 / w ** 2)
+    B = np.full(n * n, -3000.0)
+    f, c = O.flag_surface(g, eta.ravel() - B, B, tol)
+    inside = (r2 < w ** 2 * np.log(A / tol)).ravel()
+    assert np.array_equal(f.astype(bool), inside) and c == inside.sum() > 0
+    f2, c2 = O.flag_surface(g, -eta.ravel() - B, B, tol)
+    assert np.array_equal(f2, f)
+    h = eta.ravel() - B
+    k = int(np.argmax(inside))
+    h[k] = 0.0005
+    f3, c3 = O.flag_surface(g, h, B, tol)
+    assert f3[k] == 0 and c3 == c - 1
