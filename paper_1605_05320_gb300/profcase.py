@@ -1,0 +1,76 @@
+"""Small fixed cases of each hot kernel, sized for profiler captures.
+
+Each case runs one kernel family of the scenario path on the 2048 x 2048
+basin (1 km cells) through the public binding, with far less device memory
+than the full scenario (no 101-snapshot store), so that a capture that saves
+and restores device memory between passes stays small:
+
+  fwd   FP32 forward steps (fwd_f32_tiles), ~120 MB on the device
+  adj   the full FP32 adjoint run (adj_step_kernel, ~2000 launches) with a
+        fused snapshot every 100 steps, ~1.3 GB
+  flag  FP32 adjoint-weighted flag passes (flag_kernel_f32x4) against a
+        store of one snapshot every 100 adjoint steps, ~1.3 GB
+
+Launch counts (for a profiler's -s / -c): `fwd` runs 1 initial-CFL launch then
+`--steps` step launches; `adj` runs 1 init launch then every adjoint step to
+t_f; `flag` runs `--steps` flag passes after its set-up launches.
+
+    python -m paper_1605_05320_gb300.profcase fwd --steps 120
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main(argv=None):
+    import torch
+
+    from . import build
+    from . import swadj as S
+    from . import synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument("kernel", choices=["fwd", "adj", "flag"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--steps", type=int, default=120)
+    a = ap.parse_args(argv)
+    build.build()
+    S.load()
+    n = a.n
+    sc = synth.config2(n=n, L=n * 1e3)
+    d = S.make_desc(2, n, n, 0.0, 0.0, sc.grid.dx, sc.grid.dy, precision=S.SWA_FP32)
+    out = {}
+    if a.kernel == "fwd":
+        g = S.Grid(d, sc.B)
+        g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+        g.step(a.steps, sc.t_f)
+        out["t"] = g.time()[0]
+    elif a.kernel == "adj":
+        adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+        N, _, _ = adj.info()
+        st = S.SnapStore(adj, N // 100 + 3, S.SWA_FP32)
+        st.run_adjoint(100)
+        out["steps"] = N
+        out["snaps"] = st.info()[0]
+    else:
+        adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+        N, _, _ = adj.info()
+        st = S.SnapStore(adj, N // 100 + 3, S.SWA_FP32)
+        st.run_adjoint(100)
+        g = S.Grid(d, sc.B)
+        g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+        g.step(300, sc.t_f)
+        fl = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        for _ in range(a.steps):
+            S.swa_flag_cells(g.h, st.h, sc.t_s, sc.t_f, sc.tol, S.SWA_FLAG_INTERP, fl,
+                             None, cnt)
+        out["snaps"] = st.info()[0]
+        out["flags"] = cnt
+    torch.cuda.synchronize()
+    if S.swa_sync_status() != 0:
+        raise RuntimeError("device status nonzero after the profiling case")
+    print(a.kernel, {k: (int(v.item()) if hasattr(v, "item") else v) for k, v in out.items()})
+
+
+if __name__ == "__main__":
+    main()

@@ -154,7 +154,8 @@ def source_point(rng, target, L, rmin=300e3, rmax=700e3, basin_frac=1600.0 / 204
 def config2(n: int = 2048, L: float = 2048e3, seed: int = 1605,
             n_seamounts: int = 20, amp: float = 1.0, src_width: float = 30e3,
             adj_n: int | None = None, n_gauges: int = 2,
-            shelf_frac: float = 1740.0 / 2048.0) -> Scenario:
+            shelf_frac: float = 1740.0 / 2048.0,
+            src_r: tuple = (300e3, 700e3)) -> Scenario:
     """2D n x n grid on [0, L]^2 (1 km cells at n = 2048).  Gaussian source of
     amplitude `amp` and width 30 km at a seeded basin point 300-700 km from the
     target; adjoint data a 10 km Gaussian in eta at the shelf break; t_s / t_f
@@ -167,7 +168,7 @@ def config2(n: int = 2048, L: float = 2048e3, seed: int = 1605,
     # target at the shelf break: waves from 300-700 km away reach it within
     # the time window [t_s, t_f]
     target = (shelf_frac * L, 0.5 * L)
-    sx, sy = source_point(rng, target, L)
+    sx, sy = source_point(rng, target, L, rmin=src_r[0], rmax=src_r[1])
     eta0 = gaussian_field(grid, sx, sy, amp, src_width)
     eta0 = np.where(eta0 < 1e-12, 0.0, eta0)
     if adj_n is None:
@@ -194,13 +195,24 @@ def config2(n: int = 2048, L: float = 2048e3, seed: int = 1605,
                           "snap_every": 20, "flag_every": 10, "steps": 2000})
 
 
-def config4(n: int = 4096, adj_n: int = 1024) -> Scenario:
-    """Precision study: 4096^2 on [0, 4096 km]^2, 40 seamounts, shelf at
-    0.85 L, source amplitude 0.2 m, adjoint on a coarser 1024^2 grid, 16
-    gauges."""
-    L = 4096e3
-    return config2(n=n, L=L, seed=4096, n_seamounts=40, amp=0.2,
-                   adj_n=adj_n, n_gauges=16, shelf_frac=0.85)
+def config4(n: int = 4096, adj_n: int = 1024, steps: int = 5000) -> Scenario:
+    """Precision study: n^2 on [0, n km]^2, 40 seamounts, shelf at 0.85 L,
+    source amplitude 0.2 m, adjoint on a coarser adj_n^2 grid, 16 gauges,
+    t_f spanning `steps` basin CFL steps.  The source sits at the distance a
+    4000 m-deep wave covers in 0.55-0.75 t_f, so the first arrival at the
+    target falls inside the window [t_s, t_f] and the flag sets are not
+    empty."""
+    L = n * 1e3
+    dt0 = 0.75 / (np.sqrt(G * 4000.0) / (L / n))
+    t_f = steps * dt0 * 1.001
+    c = np.sqrt(G * 4000.0)
+    sc = config2(n=n, L=L, seed=4096, n_seamounts=40, amp=0.2, adj_n=adj_n,
+                 n_gauges=16, shelf_frac=0.85,
+                 src_r=(0.55 * c * t_f, 0.75 * c * t_f))
+    sc.t_f = t_f
+    sc.t_s = 0.32 * t_f
+    sc.meta["steps"] = steps
+    return sc
 
 
 def small_2d(nx: int, ny: int, seed: int = 7, L: float | None = None,
