@@ -187,7 +187,11 @@ int swa_set_adjoint_state(swa_adjoint *adj, const double *phi, int where,
 /* ============================= snapshots =================================
  * Snapshots of the adjoint at regular times (Sec. 4), device resident:
  * snapshot k holds q^(tau_k) = q~(t_f - tau_k), tau strictly decreasing.
- * precision: SWA_FP64 or SWA_FP32 storage.
+ * precision: SWA_FP64 or SWA_FP32 storage.  FP32 stores of a 2D grid with
+ * nx % 4 == 0 also keep an envelope (not in the paper; an exact pruning aid
+ * of the flag pass): per group of 8 consecutive snapshots and per quad of 4
+ * consecutive cells, the maximum |component| of each component, updated on
+ * every store; it adds 3 * (n / 4) floats per group to the workspace.
  */
 size_t swa_snapstore_workspace_bytes(const swa_grid_desc *adj_desc,
                                      int max_snaps, int precision);
@@ -222,6 +226,12 @@ int swa_snapstore_info(const swa_snapstore *store, int *count, double *tau_host,
  * cell with positive weight is dry.  flags_dev[i] = (m >= tol); maxip_dev
  * (nullable, float) receives m; *count_dev (device int64, overwritten)
  * receives the number of flags.  t > t_f gives no flags.
+ * When maxip_dev is null and the store has an envelope (FP32 forward grid
+ * and FP32 snapshots on the same 2D grid), a snapshot group is read for a
+ * cell only if its envelope bound on |q^ . q| reaches tol (1 - 1e-5) there;
+ * the flags and the count are identical to the full pass (every product the
+ * pruned pass forms is the one the full pass forms; skipped products are
+ * provably below tol), so only the optional m output needs the full pass.
  */
 int swa_flag_cells(const swa_grid *grid, const swa_snapstore *store,
                    double t_s, double t_f, double tol, int mode,

@@ -495,16 +495,39 @@ struct swa_snapstore {
     void *data;
     double *tau_dev;
     uint8_t *wet;
+    float *env;   // snapshot envelope (FP32 2D stores with nx % 4 == 0), else null
     std::vector<double> tau_host;
 };
 
-static void snap_layout(size_t na, int nc, int max_snaps, int prec, Carve &c,
+// FP32 snapshots of a 2D grid whose rows split into quads of 4 cells carry an
+// envelope: per group of kEnvGroup snapshots and per quad, the maximum
+// |component| of each component, which lets the flag pass skip groups.
+static bool snap_has_env(const swa_grid_desc *d, int prec) {
+    return prec == SWA_FP32 && d->ndim == 2 && d->nx % 4 == 0;
+}
+
+static void snap_layout(const swa_grid_desc *d, int max_snaps, int prec, Carve &c,
                         swa_snapstore *s) {
+    const size_t na = (size_t)d->nx * d->ny;
+    const int nc = d->ndim + 1;
     const size_t esz = prec == SWA_FP64 ? 8 : 4;
     void *data = c.take((size_t)max_snaps * nc * na * esz);
     double *tau = (double *)c.take((size_t)max_snaps * 8);
     uint8_t *wet = (uint8_t *)c.take(na);
-    if (s) { s->data = data; s->tau_dev = tau; s->wet = wet; }
+    float *env = nullptr;
+    if (snap_has_env(d, prec)) {
+        const size_t groups = (size_t)(max_snaps + kEnvGroup - 1) / kEnvGroup;
+        env = (float *)c.take(groups * 3 * (na / 4) * sizeof(float));
+    }
+    if (s) { s->data = data; s->tau_dev = tau; s->wet = wet; s->env = env; }
+}
+
+// Fold snapshot slot k (just written on stream st) into its envelope group.
+static int env_fold(swa_snapstore *s, int k, cudaStream_t st) {
+    if (!s->env) return SWA_OK;
+    const float *slot = (const float *)s->data + (size_t)k * s->nc * s->na;
+    float *grp = s->env + (size_t)(k / kEnvGroup) * 3 * (s->na / 4);
+    return env_launch_update(slot, s->na, grp, k % kEnvGroup == 0, st);
 }
 
 static int store_into(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
@@ -524,6 +547,7 @@ static int store_into(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
                                (const float *)a->q[a->cur][2]};
         TRY(adj_launch_store<float>(src, a->nc, a->n, sf, sd, a->n, s->tau_dev + s->count, tau, st));
     }
+    TRY(env_fold(s, s->count, st));
     s->tau_host.push_back(tau);
     s->count++;
     return SWA_OK;
@@ -555,6 +579,7 @@ static int adj_one_step(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
         p.tau_val = tau;
         TRY(adj_launch_step<float>(p, st));
     }
+    if (s) TRY(env_fold(s, s->count, st));
     a->cur ^= 1;
     a->steps_done++;
     if (s) { s->tau_host.push_back(tau); s->count++; }
@@ -698,8 +723,7 @@ size_t swa_snapstore_workspace_bytes(const swa_grid_desc *adj_desc, int max_snap
     if (check_desc(adj_desc) != SWA_OK || max_snaps < 1) return 0;
     if (precision != SWA_FP64 && precision != SWA_FP32) return 0;
     Carve c(nullptr);
-    snap_layout((size_t)adj_desc->nx * adj_desc->ny, adj_desc->ndim + 1, max_snaps,
-                precision, c, nullptr);
+    snap_layout(adj_desc, max_snaps, precision, c, nullptr);
     return c.off + 256;
 }
 
@@ -722,7 +746,7 @@ int swa_create_snapstore(const swa_adjoint *adj, int max_snaps, int precision, v
     s->na = adj->n;
     s->nc = adj->nc;
     Carve c(ws);
-    snap_layout(s->na, s->nc, max_snaps, precision, c, s);
+    snap_layout(&adj->d, max_snaps, precision, c, s);
     if (adj->d.precision == SWA_FP64)
         wet_mask_kernel<double><<<ew_blocks(s->na), 256>>>((const double *)adj->c,
                                                            adj->d.dry_tol, s->wet, s->na);
@@ -819,6 +843,7 @@ static int flag_dispatch(const swa_grid *g, const swa_snapstore *s, double t_s, 
     p.t_s = t_s; p.t_f = t_f; p.tol = tol; p.mode = mode;
     p.flags = flags;
     p.maxip = maxip;
+    p.env = p.same_grid ? s->env : nullptr;
     p.count = (unsigned long long *)count;
     return flag_launch<R, SN>(p, st);
 }

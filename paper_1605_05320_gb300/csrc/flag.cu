@@ -187,6 +187,22 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
 // case.  Each thread takes 4 consecutive cells with 16-byte loads; the window
 // (index ranges and end weights) is computed once per block, so the per-cell
 // loop has no FP64 work at all.
+//
+// PRUNE (no maxip output requested, envelope present): a group of snapshots
+// is read only where it can matter.  For a cell with forward state q and a
+// group whose per-component maxima over the cell's quad are (Me, Mu, Mv),
+// every product satisfies |q^ . q| <= Me |eta| + Mu |hu| + Mv |hv| =: bnd.
+// If bnd < tol (1 - 1e-5) for every wet cell of the quad, no product of the
+// group can reach tol even after float rounding (the products and bnd carry
+// relative errors of a few 1e-7), and neither can a time-interpolated end
+// value built from two such products; the group is skipped.  An end value
+// (INTERP) is computed from both of its snapshots whenever either of their
+// groups is read.  Every product that is formed is the one the unpruned pass
+// forms, so the flags and the count are identical to the unpruned pass; only
+// m differs (it may omit values below tol), hence PRUNE only without maxip.
+// Ahead of the forward wave q = 0 exactly and every group is skipped, so the
+// pass then reads the state and the envelope only.
+template <bool PRUNE>
 __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float> p) {
     __shared__ Window sw;
     if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
@@ -207,11 +223,42 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
         const bool ok2 = e.z + hb.z > dt && wet.z, ok3 = e.w + hb.w > dt && wet.w;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 dh0 = m, dh1 = m, dl0 = m, dl1 = m;
-        if (!w.empty) {
+        // skip test of envelope group gb (PRUNE only)
+        const float tolp = (float)(p.tol * (1.0 - 1e-5));
+        auto skip = [&](int gb) -> bool {
+            const float *eg = p.env + (size_t)gb * 3 * n4;
+            const float Me = __ldg(eg + i), Mu = __ldg(eg + n4 + i), Mv = __ldg(eg + 2 * n4 + i);
+            const float b0 = Me * fabsf(e.x) + Mu * fabsf(u.x) + Mv * fabsf(v.x);
+            const float b1 = Me * fabsf(e.y) + Mu * fabsf(u.y) + Mv * fabsf(v.y);
+            const float b2 = Me * fabsf(e.z) + Mu * fabsf(u.z) + Mv * fabsf(v.z);
+            const float b3 = Me * fabsf(e.w) + Mu * fabsf(u.w) + Mv * fabsf(v.w);
+            return (!ok0 || b0 < tolp) && (!ok1 || b1 < tolp) && (!ok2 || b2 < tolp) &&
+                   (!ok3 || b3 < tolp);
+        };
+        if (!w.empty && (ok0 || ok1 || ok2 || ok3 || !PRUNE)) {
             const float4 *s0 = reinterpret_cast<const float4 *>(p.snaps) + i;
             const size_t cs = p.na >> 2, ks = p.snap_stride >> 2;
+            const bool interp = p.mode != SWA_FLAG_BRACKET;
+            bool need_h = true, need_l = true;
+            if (PRUNE && interp) {
+                const int kh1 = w.exact_h ? w.kh : w.kh + 1;
+                const int kl1 = w.exact_l ? w.kl : w.kl + 1;
+                need_h = !(skip(w.kh / kEnvGroup) && skip(kh1 / kEnvGroup));
+                need_l = !(skip(w.kl / kEnvGroup) && skip(kl1 / kEnvGroup));
+            }
+            int gcur = -1;
+            bool gskip = false;
 #pragma unroll 2
             for (int k = w.k0; k <= w.k1; k++) {
+                if (PRUNE) {
+                    const int gb = k / kEnvGroup;
+                    if (gb != gcur) { gcur = gb; gskip = skip(gb); }
+                    if (gskip) {
+                        const bool end = interp && ((need_h && (k == w.kh || k == w.kh + 1)) ||
+                                                    (need_l && (k == w.kl || k == w.kl + 1)));
+                        if (!end) continue;
+                    }
+                }
                 const float4 a = __ldcs(s0 + (size_t)k * ks);
                 const float4 b = __ldcs(s0 + (size_t)k * ks + cs);
                 const float4 c = __ldcs(s0 + (size_t)k * ks + 2 * cs);
@@ -229,7 +276,7 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
                 if (k == w.kl) dl0 = d;
                 if (k == w.kl + 1) dl1 = d;
             }
-            if (p.mode != SWA_FLAG_BRACKET) {
+            if (interp) {
                 const float ah = (float)w.ah, al = (float)w.al;
                 const float bh = 1.f - ah, bl = 1.f - al;
 #define SWADJ_ENDS(c)                                                          \
@@ -246,7 +293,7 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
         const int f0 = (!w.empty && ok0 && m.x >= tol), f1 = (!w.empty && ok1 && m.y >= tol);
         const int f2 = (!w.empty && ok2 && m.z >= tol), f3 = (!w.empty && ok3 && m.w >= tol);
         reinterpret_cast<uchar4 *>(p.flags)[i] = make_uchar4(f0, f1, f2, f3);
-        if (p.maxip) {
+        if (!PRUNE && p.maxip) {
             const float4 mm = make_float4(ok0 ? m.x : 0.f, ok1 ? m.y : 0.f,
                                           ok2 ? m.z : 0.f, ok3 ? m.w : 0.f);
             reinterpret_cast<float4 *>(p.maxip)[i] = w.empty ? make_float4(0.f, 0.f, 0.f, 0.f) : mm;
@@ -258,6 +305,33 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
 }
 
+// Envelope of one stored snapshot, folded into its group: one thread per
+// quad of 4 consecutive cells.
+__global__ void __launch_bounds__(256) env_update_kernel(const float *slot, size_t na,
+                                                         float *env, int first) {
+    const size_t n4 = na >> 2;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+         q += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float4 a = __ldcg(reinterpret_cast<const float4 *>(slot + c * na) + q);
+            const float mx = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+            float *o = env + c * n4 + q;
+            *o = first ? mx : fmaxf(*o, mx);
+        }
+    }
+}
+
+int env_launch_update(const float *slot, size_t na, float *env_group, int first,
+                      cudaStream_t st) {
+    const size_t n4 = na >> 2;
+    size_t blocks = (n4 + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    env_update_kernel<<<(unsigned)blocks, 256, 0, st>>>(slot, na, env_group, first);
+    return swadj_host::cuda_check(cudaGetLastError(), "env_update_kernel");
+}
+
 template <typename R, typename S>
 int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     const size_t n = (size_t)p.nx * p.ny;
@@ -266,8 +340,11 @@ int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     const unsigned blocks = (unsigned)((n + 255) / 256);
     if (sizeof(R) == 4 && sizeof(S) == 4 && p.same_grid && p.two_d && (n & 3) == 0) {
         const size_t n4 = n >> 2;
-        flag_kernel_f32x4<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(
-            *reinterpret_cast<const FlagParams<float, float> *>(&p));
+        const FlagParams<float, float> &pf = *reinterpret_cast<const FlagParams<float, float> *>(&p);
+        if (p.env && !p.maxip)
+            flag_kernel_f32x4<true><<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(pf);
+        else
+            flag_kernel_f32x4<false><<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(pf);
     } else if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
     else flag_kernel<R, S, false><<<blocks, 256, 0, st>>>(p);
     return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");

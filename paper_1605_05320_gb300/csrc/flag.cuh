@@ -29,10 +29,22 @@ struct FlagParams {
     uint8_t *flags;
     float *maxip;
     unsigned long long *count;
+    // snapshot envelope (FP32 2D stores, or null): per group of kEnvGroup
+    // consecutive snapshots and per quad of 4 consecutive cells, the maximum
+    // |component| of each component, [group][ncomp][na / 4]
+    const float *env;
 };
+
+// Snapshots per envelope group.
+constexpr int kEnvGroup = 8;
 
 template <typename R, typename S>
 int flag_launch(const FlagParams<R, S> &p, cudaStream_t st);
+
+// Fold snapshot slot `slot` ([3][na] floats, na % 4 == 0) into its envelope
+// group `env_group` ([3][na / 4]): overwrite when `first`, else max.
+int env_launch_update(const float *slot, size_t na, float *env_group, int first,
+                      cudaStream_t st);
 
 template <typename R>
 struct SurfParams {

@@ -6,10 +6,12 @@ than the full scenario (no 101-snapshot store), so that a capture that saves
 and restores device memory between passes stays small:
 
   fwd   FP32 forward steps (fwd_f32_tiles), ~120 MB on the device
-  adj   the full FP32 adjoint run (adj_step_kernel, ~2000 launches) with a
+  adj   the full FP32 adjoint run (adj_f32_tiles, ~2000 launches) with a
         fused snapshot every 100 steps, ~1.3 GB
-  flag  FP32 adjoint-weighted flag passes (flag_kernel_f32x4) against a
-        store of one snapshot every 100 adjoint steps, ~1.3 GB
+  flag  FP32 adjoint-weighted flag passes without the m output (the
+        envelope-pruned flag_kernel_f32x4) against a store of one snapshot
+        every 100 adjoint steps, ~1.3 GB; `--full` requests m as well, which
+        runs the full pass
 
 Launch counts (for a profiler's -s / -c): `fwd` runs 1 initial-CFL launch then
 `--steps` step launches; `adj` runs 1 init launch then every adjoint step to
@@ -32,6 +34,7 @@ def main(argv=None):
     ap.add_argument("kernel", choices=["fwd", "adj", "flag"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=120)
+    ap.add_argument("--full", action="store_true")
     a = ap.parse_args(argv)
     build.build()
     S.load()
@@ -61,9 +64,10 @@ def main(argv=None):
         g.step(300, sc.t_f)
         fl = torch.zeros(n * n, dtype=torch.uint8, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        m = torch.zeros(n * n, dtype=torch.float32, device="cuda") if a.full else None
         for _ in range(a.steps):
             S.swa_flag_cells(g.h, st.h, sc.t_s, sc.t_f, sc.tol, S.SWA_FLAG_INTERP, fl,
-                             None, cnt)
+                             m, cnt)
         out["snaps"] = st.info()[0]
         out["flags"] = cnt
     torch.cuda.synchronize()

@@ -51,7 +51,10 @@ def test_workspace_sizes_and_descriptor_checks(lib):
     a = S.swa_adjoint_workspace_bytes(d)
     assert a >= 7 * 4 * n + 8 * n
     s = S.swa_snapstore_workspace_bytes(d, 101, S.SWA_FP32)
-    assert s >= 101 * 3 * 4 * n + n
+    # snapshots, tau, wet mask and the envelope (13 groups of 8, 3 x n/4 floats)
+    assert s >= 101 * 3 * 4 * n + 101 * 8 + n + 13 * 3 * (n // 4) * 4
+    s64 = S.swa_snapstore_workspace_bytes(d, 101, S.SWA_FP64)
+    assert 101 * 3 * 8 * n + n <= s64 < 101 * 3 * 8 * n + n + 4096
     bad = S.make_desc(2, 2048, 2048, 0.0, 0.0, 1000.0, 1000.0, order=3)
     assert S.swa_grid_workspace_bytes(bad) == 0
     assert "order" in S.swa_last_error()

@@ -188,7 +188,48 @@ def test_fp64_adjoint_1d_with_dry_cells(S):
     assert rel(got, snaps) <= 1e-12
 
 
-def _flag_compare(S, sc, precision, mode, t_s, nsteps, every=5):
+def _with_island(sc):
+    """Dry adjoint cells (B > 0) in a disc of radius 8 cells in mid-basin: the
+    edges around it are wet/dry walls of the adjoint (Sec. 5)."""
+    xc, yc = sc.adj_grid.centres()
+    X, Y = np.meshgrid(xc, yc)
+    L, Ly = sc.adj_grid.nx * sc.adj_grid.dx, sc.adj_grid.ny * sc.adj_grid.dy
+    r = np.hypot(X - 0.6 * L, Y - 0.5 * Ly).ravel()
+    sc.B_adj = np.where(r < 8 * sc.adj_grid.dx, 10.0, sc.B_adj)
+    sc.phi[:, r < 8 * sc.adj_grid.dx] = 0.0
+    return sc
+
+
+def test_fp64_adjoint_2d_with_island(S):
+    sc = _with_island(synth.small_2d(96, 70, seed=7))
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+        _adjoint_pair(S, sc, S.SWA_FP64, 5, (1, 0, 0, 1))
+    assert N == N_ref and np.array_equal(tau, tau_ref)
+    got = _read_snaps(S, store, S.SWA_FP64, 3, sc.adj_grid.n)
+    for c in range(3):
+        assert rel(got[:, c], snaps[:, c]) <= 1e-12, c
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (1, 0, 0, 1)])
+def test_fp32_adjoint_snapshots_vs_oracle(S, order, bc):
+    """FP32 adjoint (c = sqrt(g hbar) rounded to float, float arithmetic)
+    against the FP64 oracle on a 96 x 70 grid (ragged in both tile
+    directions) with an island: every snapshot, every component, within
+    2e-5 of the component's maximum over the run."""
+    sc = _with_island(synth.small_2d(96, 70, seed=7))
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+        _adjoint_pair(S, sc, S.SWA_FP32, 5, bc, order)
+    assert N == N_ref and np.array_equal(tau, tau_ref)
+    got = _read_snaps(S, store, S.SWA_FP32, 3, sc.adj_grid.n)
+    dry = sc.B_adj > 0
+    for c in range(3):
+        err = rel(got[:, c], snaps[:, c])
+        assert err <= 2e-5, (c, err)
+        assert np.all(got[:, c][:, dry] == 0)
+
+
+def _flag_compare(S, sc, precision, mode, t_s, nsteps, every=5, with_m=True):
     """Both sides compute everything from the seeded inputs: adjoint with
     snapshots, nsteps forward steps, then the flag pass."""
     fp32 = precision == S.SWA_FP32
@@ -199,7 +240,7 @@ def _flag_compare(S, sc, precision, mode, t_s, nsteps, every=5):
     g.step(nsteps, sc.t_f)
     n = sc.grid.n
     flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
-    m = torch.zeros(n, dtype=torch.float32, device="cuda")
+    m = torch.zeros(n, dtype=torch.float32, device="cuda") if with_m else None
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     S.swa_flag_cells(g.h, store.h, t_s, sc.t_f, sc.tol, mode, flags, m, cnt)
     torch.cuda.synchronize()
@@ -211,7 +252,8 @@ def _flag_compare(S, sc, precision, mode, t_s, nsteps, every=5):
     f_ref, m_ref, c_ref = O.flag(og, h, hu, hv, Bs, t_ref, ag,
                                  np.maximum(-sc.B_adj, 0), snaps, tau_ref, t_s,
                                  sc.t_f, sc.tol, mode)
-    return flags.cpu().numpy(), m.cpu().numpy(), int(cnt.item()), f_ref, m_ref, c_ref
+    m = None if m is None else m.cpu().numpy()
+    return flags.cpu().numpy(), m, int(cnt.item()), f_ref, m_ref, c_ref
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -233,6 +275,67 @@ def test_fp32_flags_close_to_oracle(S):
     near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
     assert np.array_equal(f[~near], f_ref[~near])
     assert np.abs(m - m_ref).max() <= 1e-4 * m_ref.max()
+
+
+def _flags_pruned_and_full(S, g, store, t_s, t_f, tol, mode):
+    n = g.desc.nx * g.desc.ny
+    out = []
+    for with_m in (False, True):
+        flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        m = torch.zeros(n, dtype=torch.float32, device="cuda") if with_m else None
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        S.swa_flag_cells(g.h, store.h, t_s, t_f, tol, mode, flags, m, cnt)
+        torch.cuda.synchronize()
+        out.append((flags.cpu().numpy(), int(cnt.item()), None if m is None else m.cpu().numpy()))
+    assert S.swa_sync_status() == 0
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pruned_flag_pass_identical_to_full_pass(S, mode):
+    """The envelope-pruned pass (no m output) against the full pass (m
+    requested) on the same device data: identical flags and count at several
+    forward times, window widths down to less than one snapshot interval, and
+    tolerances spanning the range of m.  The source is a bump on an ocean at
+    rest, so most of the grid is quiet ahead of the wave front."""
+    sc = synth.small_2d(256, 160, seed=12)
+    sc.hu0[:] = 0.0
+    sc.hv0[:] = 0.0
+    d = desc_of(S, sc.grid, S.SWA_FP32)
+    adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+    N, dt, _ = adj.info()
+    store = S.SnapStore(adj, N // 5 + 3, S.SWA_FP32)
+    store.run_adjoint(5)
+    g = S.Grid(d, sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    done, seen = 0, 0
+    for target in (10, 60, 140, 260, 400):
+        g.step(target - done, sc.t_f)
+        done = target
+        for t_s in (0.32 * sc.t_f, 0.95 * sc.t_f, sc.t_f - 0.5 * dt):
+            (fp, cp, _), (ff, cf, m) = _flags_pruned_and_full(S, g, store, t_s, sc.t_f,
+                                                                sc.tol, mode)
+            assert np.array_equal(fp, ff) and cp == cf, (target, t_s)
+            seen += cf
+            pos = m[m > 0]
+            for tol in (np.quantile(pos, [0.1, 0.5, 0.9, 0.999]) if pos.size else []):
+                (fp, cp, _), (ff, cf, _) = _flags_pruned_and_full(S, g, store, t_s, sc.t_f,
+                                                                  float(tol), mode)
+                assert np.array_equal(fp, ff) and cp == cf and cf > 0, (target, t_s, tol)
+    assert seen > 0
+
+
+def test_pruned_flags_match_oracle(S):
+    """The pruned pass (no m output) against the oracle's flags."""
+    sc = synth.small_2d(88, 60, seed=9)
+    sc.hu0[:] = 0.0
+    sc.hv0[:] = 0.0
+    f, _, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP32, 0, 0.32 * sc.t_f, 150,
+                                                 with_m=False)
+    near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
+    assert c_ref > 0
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert f.sum() == c
 
 
 def test_coarse_adjoint_grid_flags(S):
