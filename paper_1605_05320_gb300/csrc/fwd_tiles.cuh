@@ -9,9 +9,11 @@
 // staged row, in place (the y-sweep needs the x-swept state in the two halo
 // rows); (4) y-edge waves of the x-swept state; (5) their net fluxes;
 // (6) y-sweep update of the tile's cells.  Each phase is a flat loop of
-// independent items over 256 threads.  A persistent block walks its share of
-// a tile list; the raw values of the next tile are loaded into registers
-// while the current one is computed.
+// independent items over 256 threads.  Cell data, edge waves and net fluxes
+// are kept as 16- and 8-byte records so that each item moves them with a few
+// vector shared-memory accesses.  A persistent block walks its share of a
+// tile list; the raw values of the next tile are loaded into registers while
+// the current one is computed.
 //
 // The MC-limited correction needs no division by the wave norm: for
 // Z = b (1, s, vhat) and its upwind neighbour Zu = bu (1, su, vu),
@@ -133,15 +135,17 @@ template <int TX, int TY>
 struct Smem {
     static constexpr int RX = TX + 4, RY = TY + 4;
     static constexpr int NEX = TX + 3, NEY = TY + 3;
-    // cell data of the tile + halo (with corners); x-swept in place
-    float h[RY][RX], mu[RY][RX], mv[RY][RX], u[RY][RX], v[RY][RX], sq[RY][RX], eta[RY][RX];
-    union W {   // edge waves: x (phases 1-2), then y (phases 4-5)
-        float x[6][RY][NEX];
-        float y[6][NEY][TX];
+    // cell data of the tile + halo (with corners), x-swept in place, as two
+    // 16-byte records read with one vector load each:
+    // a = (h, hu, hv, eta), b = (u, v, sqrt(h), unused)
+    float4 a[RY][RX], b[RY][RX];
+    union W {   // edge waves p = (s1, s3, vhat, b1), q = (b2, b3): x (phases 1-2), then y (4-5)
+        struct X { float4 p[RY][NEX]; float2 q[RY][NEX]; } x;
+        struct Y { float4 p[NEY][TX]; float2 q[NEY][TX]; } y;
     } w;
-    union N {   // net fluxes: x (phases 2-3), then y (phases 5-6)
-        struct X { float l[3][RY][TX + 1], r[3][RY][TX + 1]; } x;
-        struct Y { float l[3][TY + 1][TX], r[3][TY + 1][TX]; } y;
+    union N {   // net fluxes lr = (L0, L1, L2, R0), r = (R1, R2): x (phases 2-3), then y (5-6)
+        struct X { float4 lr[RY][TX + 1]; float2 r[RY][TX + 1]; } x;
+        struct Y { float4 lr[TY + 1][TX]; float2 r[TY + 1][TX]; } y;
     } n;
 };
 
@@ -183,28 +187,25 @@ __device__ __forceinline__ void put_cell(SM &S, int ry, int rx, float eta, float
                                          float mv) {
     const float q = rsqrtf(h);
     const float ih = q * q;
-    S.h[ry][rx] = h;
-    S.mu[ry][rx] = mu;
-    S.mv[ry][rx] = mv;
-    S.u[ry][rx] = mu * ih;
-    S.v[ry][rx] = mv * ih;
-    S.sq[ry][rx] = h * q;
-    S.eta[ry][rx] = eta;
+    S.a[ry][rx] = make_float4(h, mu, mv, eta);
+    S.b[ry][rx] = make_float4(mu * ih, mv * ih, h * q, 0.f);
 }
 
-// Net fluxes of edges e-1, e, e+1 (waves w[q][row][*]) -> L/R of edge e.
-template <typename WA>
-__device__ __forceinline__ void net_at(const WA &w, int row, int e, float nu, int order,
-                                       float L[3], float Rr[3]) {
-    EdgeS a, b, c;
-    a.s1 = w[0][row][e - 1]; a.s3 = w[1][row][e - 1]; a.vh = w[2][row][e - 1];
-    a.b1 = w[3][row][e - 1]; a.b2 = w[4][row][e - 1]; a.b3 = w[5][row][e - 1];
-    b.s1 = w[0][row][e]; b.s3 = w[1][row][e]; b.vh = w[2][row][e];
-    b.b1 = w[3][row][e]; b.b2 = w[4][row][e]; b.b3 = w[5][row][e];
-    c.s1 = w[0][row][e + 1]; c.s3 = w[1][row][e + 1]; c.vh = w[2][row][e + 1];
-    c.b1 = w[3][row][e + 1]; c.b2 = w[4][row][e + 1]; c.b3 = w[5][row][e + 1];
+__device__ __forceinline__ EdgeS edge_of(const float4 &p, const float2 &q) {
+    EdgeS w;
+    w.s1 = p.x; w.s3 = p.y; w.vh = p.z; w.b1 = p.w; w.b2 = q.x; w.b3 = q.y;
+    return w;
+}
+
+// Net fluxes L (into the left / lower cell) and R (into the right / upper
+// cell) of the middle edge b, neighbours a and c.
+__device__ __forceinline__ void net_of(const EdgeS &a, const EdgeS &b, const EdgeS &c, float nu,
+                                       int order, float4 &lr, float2 &r) {
+    float L[3], Rr[3];
     if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nu, order, L, Rr);
     else net1<false>(a, b, c, nu, order, L, Rr);
+    lr = make_float4(L[0], L[1], L[2], Rr[0]);
+    r = make_float2(Rr[1], Rr[2]);
 }
 
 // Phases 0-6 for one tile whose raw values are in R.  Returns the tile's
@@ -227,59 +228,53 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
     // phase 1: x-edge waves of every staged row (edge e between cols e, e+1)
     for (int i = tid; i < RY * NEX; i += NT) {
         const int ry = i / NEX, e = i - ry * NEX;
-        const EdgeS w = solve1(g, S.h[ry][e], S.mu[ry][e], S.mv[ry][e], S.u[ry][e], S.v[ry][e],
-                               S.sq[ry][e], S.eta[ry][e], S.h[ry][e + 1], S.mu[ry][e + 1],
-                               S.mv[ry][e + 1], S.u[ry][e + 1], S.v[ry][e + 1],
-                               S.sq[ry][e + 1], S.eta[ry][e + 1]);
-        S.w.x[0][ry][e] = w.s1; S.w.x[1][ry][e] = w.s3; S.w.x[2][ry][e] = w.vh;
-        S.w.x[3][ry][e] = w.b1; S.w.x[4][ry][e] = w.b2; S.w.x[5][ry][e] = w.b3;
+        const float4 aL = S.a[ry][e], bL = S.b[ry][e], aR = S.a[ry][e + 1], bR = S.b[ry][e + 1];
+        const EdgeS w = solve1(g, aL.x, aL.y, aL.z, bL.x, bL.y, bL.z, aL.w, aR.x, aR.y, aR.z,
+                               bR.x, bR.y, bR.z, aR.w);
+        S.w.x.p[ry][e] = make_float4(w.s1, w.s3, w.vh, w.b1);
+        S.w.x.q[ry][e] = make_float2(w.b2, w.b3);
     }
     __syncthreads();
     // phase 2: x net fluxes of edges 1 .. TX+1 in every staged row
     for (int i = tid; i < RY * (TX + 1); i += NT) {
         const int ry = i / (TX + 1), e = 1 + (i - ry * (TX + 1));
-        float L[3], Rr[3];
-        net_at(S.w.x, ry, e, nux, order, L, Rr);
-#pragma unroll
-        for (int m = 0; m < 3; m++) { S.n.x.l[m][ry][e - 1] = L[m]; S.n.x.r[m][ry][e - 1] = Rr[m]; }
+        const EdgeS wa = edge_of(S.w.x.p[ry][e - 1], S.w.x.q[ry][e - 1]);
+        const EdgeS wb = edge_of(S.w.x.p[ry][e], S.w.x.q[ry][e]);
+        const EdgeS wc = edge_of(S.w.x.p[ry][e + 1], S.w.x.q[ry][e + 1]);
+        net_of(wa, wb, wc, nux, order, S.n.x.lr[ry][e - 1], S.n.x.r[ry][e - 1]);
     }
     __syncthreads();
     // phase 3: x-sweep of the tile's columns in every staged row, in place
     for (int i = tid; i < RY * TX; i += NT) {
         const int ry = i / TX, col = i - ry * TX, rx = col + 2;
         // left edge of column col -> R at index col, right edge -> L at col + 1
-        const float d0 = -nux * (S.n.x.r[0][ry][col] + S.n.x.l[0][ry][col + 1]);
-        const float d1 = -nux * (S.n.x.r[1][ry][col] + S.n.x.l[1][ry][col + 1]);
-        const float d2 = -nux * (S.n.x.r[2][ry][col] + S.n.x.l[2][ry][col + 1]);
-        put_cell(S, ry, rx, S.eta[ry][rx] + d0, S.h[ry][rx] + d0, S.mu[ry][rx] + d1,
-                 S.mv[ry][rx] + d2);
+        const float4 le = S.n.x.lr[ry][col];
+        const float2 lr = S.n.x.r[ry][col];
+        const float4 re = S.n.x.lr[ry][col + 1];
+        const float4 c = S.a[ry][rx];
+        const float d0 = -nux * (le.w + re.x);
+        const float d1 = -nux * (lr.x + re.y);
+        const float d2 = -nux * (lr.y + re.z);
+        put_cell(S, ry, rx, c.w + d0, c.x + d0, c.y + d1, c.z + d2);
     }
     __syncthreads();
     // phase 4: y-edge waves of the x-swept state, tile columns (frame (h, hv, hu))
     for (int i = tid; i < NEY * TX; i += NT) {
         const int e = i / TX, col = i - e * TX, rx = col + 2;
-        const EdgeS w = solve1(g, S.h[e][rx], S.mv[e][rx], S.mu[e][rx], S.v[e][rx], S.u[e][rx],
-                               S.sq[e][rx], S.eta[e][rx], S.h[e + 1][rx], S.mv[e + 1][rx],
-                               S.mu[e + 1][rx], S.v[e + 1][rx], S.u[e + 1][rx],
-                               S.sq[e + 1][rx], S.eta[e + 1][rx]);
-        S.w.y[0][e][col] = w.s1; S.w.y[1][e][col] = w.s3; S.w.y[2][e][col] = w.vh;
-        S.w.y[3][e][col] = w.b1; S.w.y[4][e][col] = w.b2; S.w.y[5][e][col] = w.b3;
+        const float4 aL = S.a[e][rx], bL = S.b[e][rx], aR = S.a[e + 1][rx], bR = S.b[e + 1][rx];
+        const EdgeS w = solve1(g, aL.x, aL.z, aL.y, bL.y, bL.x, bL.z, aL.w, aR.x, aR.z, aR.y,
+                               bR.y, bR.x, bR.z, aR.w);
+        S.w.y.p[e][col] = make_float4(w.s1, w.s3, w.vh, w.b1);
+        S.w.y.q[e][col] = make_float2(w.b2, w.b3);
     }
     __syncthreads();
-    // phase 5: y net fluxes of edges 1 .. TY+1 (transposed indexing)
+    // phase 5: y net fluxes of edges 1 .. TY+1
     for (int i = tid; i < (TY + 1) * TX; i += NT) {
         const int e = 1 + i / TX, col = i - (e - 1) * TX;
-        EdgeS a, b, c;
-#define SWADJ_LOADY(W, E)                                                            \
-    W.s1 = S.w.y[0][E][col]; W.s3 = S.w.y[1][E][col]; W.vh = S.w.y[2][E][col];     \
-    W.b1 = S.w.y[3][E][col]; W.b2 = S.w.y[4][E][col]; W.b3 = S.w.y[5][E][col];
-        SWADJ_LOADY(a, e - 1) SWADJ_LOADY(b, e) SWADJ_LOADY(c, e + 1)
-#undef SWADJ_LOADY
-        float L[3], Rr[3];
-        if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nuy, order, L, Rr);
-        else net1<false>(a, b, c, nuy, order, L, Rr);
-#pragma unroll
-        for (int m = 0; m < 3; m++) { S.n.y.l[m][e - 1][col] = L[m]; S.n.y.r[m][e - 1][col] = Rr[m]; }
+        const EdgeS wa = edge_of(S.w.y.p[e - 1][col], S.w.y.q[e - 1][col]);
+        const EdgeS wb = edge_of(S.w.y.p[e][col], S.w.y.q[e][col]);
+        const EdgeS wc = edge_of(S.w.y.p[e + 1][col], S.w.y.q[e + 1][col]);
+        net_of(wa, wb, wc, nuy, order, S.n.y.lr[e - 1][col], S.n.y.r[e - 1][col]);
     }
     __syncthreads();
     // phase 6: y-sweep update of the tile's cells; y nets are in (h, hv, hu)
@@ -293,15 +288,19 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
         const int gi = i0 + col, gj = j0 + row;
         const int ry = row + 2, rx = col + 2;
         if (gi < V.nx && gj < V.ny) {
-            const float d0 = -nuy * (S.n.y.r[0][row][col] + S.n.y.l[0][row + 1][col]);
-            const float d2 = -nuy * (S.n.y.r[1][row][col] + S.n.y.l[1][row + 1][col]);
-            const float d1 = -nuy * (S.n.y.r[2][row][col] + S.n.y.l[2][row + 1][col]);
-            const float ne = S.eta[ry][rx] + d0, nmu = S.mu[ry][rx] + d1, nmv = S.mv[ry][rx] + d2;
+            const float4 lo = S.n.y.lr[row][col];
+            const float2 lr = S.n.y.r[row][col];
+            const float4 up = S.n.y.lr[row + 1][col];
+            const float4 cc = S.a[ry][rx];
+            const float d0 = -nuy * (lo.w + up.x);
+            const float d2 = -nuy * (lr.x + up.y);
+            const float d1 = -nuy * (lr.y + up.z);
+            const float ne = cc.w + d0, nmu = cc.y + d1, nmv = cc.z + d2;
             const size_t o = (size_t)gj * V.nx + gi;
             V.o0[o] = ne;
             V.o1[o] = nmu;
             V.o2[o] = nmv;
-            const float h = S.h[ry][rx] + d0;
+            const float h = cc.x + d0;
             bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
             smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
         }

@@ -308,7 +308,7 @@ def test_pruned_flag_pass_identical_to_full_pass(S, mode):
     store.run_adjoint(5)
     g = S.Grid(d, sc.B)
     g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
-    done, seen = 0, 0
+    done, checked = 0, 0
     for target in (10, 60, 140, 260, 400):
         g.step(target - done, sc.t_f)
         done = target
@@ -316,13 +316,14 @@ def test_pruned_flag_pass_identical_to_full_pass(S, mode):
             (fp, cp, _), (ff, cf, m) = _flags_pruned_and_full(S, g, store, t_s, sc.t_f,
                                                                 sc.tol, mode)
             assert np.array_equal(fp, ff) and cp == cf, (target, t_s)
-            seen += cf
             pos = m[m > 0]
             for tol in (np.quantile(pos, [0.1, 0.5, 0.9, 0.999]) if pos.size else []):
                 (fp, cp, _), (ff, cf, _) = _flags_pruned_and_full(S, g, store, t_s, sc.t_f,
                                                                   float(tol), mode)
                 assert np.array_equal(fp, ff) and cp == cf and cf > 0, (target, t_s, tol)
-    assert seen > 0
+                checked += 1
+    # flagged sets were compared at most (time, window) pairs
+    assert checked >= 20
 
 
 def test_pruned_flags_match_oracle(S):
