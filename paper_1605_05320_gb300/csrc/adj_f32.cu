@@ -36,6 +36,7 @@ __device__ __forceinline__ float mc1(float b, float r) {
 
 struct EdgeA {   // waves of one edge: strengths and the (substituted) speeds
     float b1, b2, cl, cr;
+    bool wall;     // a wet / dry edge: no second-order correction
 };
 
 // Waves at the edge between (eL, mL, cL) and (eR, mR, cR), m the normal
@@ -44,6 +45,7 @@ __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR,
                                          float cR) {
     EdgeA w;
     const bool dL = !(cL > 0.f), dR = !(cR > 0.f);
+    w.wall = dL || dR;
     if (dL && dR) { w.b1 = 0.f; w.b2 = 0.f; w.cl = 0.f; w.cr = 0.f; return w; }
     if (dL) { eL = eR; mL = -mR; cL = cR; }
     if (dR) { eR = eL; mR = -mL; cR = cL; }
@@ -58,13 +60,25 @@ __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR,
     return w;
 }
 
-// Net fluxes of edge w (neighbour edges wl, wr): L into the left cell, R into
-// the right cell (Q -= nu * net); components (eta~, normal).  `wall`: a wet /
-// dry edge, which carries no second-order correction.
-__device__ __forceinline__ void net_a(const EdgeA &wl, const EdgeA &w, const EdgeA &wr,
-                                      float nu, int order, bool wall, float L[2], float R[2]) {
+// Shared-memory record of an edge, (b1, b2, cl, cr) with the wall flag in
+// the sign bit of cl (cl >= 0, so |cl| restores it exactly).
+__device__ __forceinline__ float4 pack_edge(const EdgeA &w) {
+    return make_float4(w.b1, w.b2, w.wall ? -w.cl : w.cl, w.cr);
+}
+__device__ __forceinline__ EdgeA unpack_edge(const float4 &r) {
+    EdgeA w;
+    w.b1 = r.x; w.b2 = r.y; w.cl = fabsf(r.z); w.cr = r.w;
+    w.wall = signbit(r.z);
+    return w;
+}
+
+// Net fluxes of edge w (neighbour edges wl, wr) as (L0, L1, R0, R1): L into
+// the left cell, R into the right cell (Q -= nu * net); components
+// (eta~, normal).
+__device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const EdgeA &wr,
+                                        float nu, int order) {
     float F0 = 0.f, F1 = 0.f;
-    if (order >= 2 && !wall) {
+    if (order >= 2 && !w.wall) {
         // wave 1 (speed -cl) is upwinded from the right edge, wave 2 (+cr)
         // from the left edge
         const float r1 = wr.b1 * fmaf(wr.cl, w.cl, 1.f) * rcpf(fmaf(w.cl, w.cl, 1.f));
@@ -74,23 +88,20 @@ __device__ __forceinline__ void net_a(const EdgeA &wl, const EdgeA &w, const Edg
         F0 = k1 * w.cl - k2 * w.cr;
         F1 = k1 + k2;
     }
-    L[0] = w.b1 * w.cl + F0;
-    L[1] = w.b1 + F1;
-    R[0] = -(w.b2 * w.cr) - F0;
-    R[1] = w.b2 - F1;
+    return make_float4(w.b1 * w.cl + F0, w.b1 + F1, -(w.b2 * w.cr) - F0, w.b2 - F1);
 }
 
 template <int TX, int TY>
 struct Smem {
     static constexpr int RX = TX + 4, RY = TY + 4, NEX = TX + 3, NEY = TY + 3;
-    float e[RY][RX], m[RY][RX], g[RY][RX], c[RY][RX];
-    union W {   // edge waves (b1, b2, cl, cr): y (phases 1-2), then x (4-5)
-        float y[4][NEY][RX];
-        float x[4][TY][NEX];
+    float4 q[RY][RX];   // cell records (eta~, mu~, gamma~, c)
+    union W {           // edge records: y (phases 1-2), then x (4-5)
+        float4 y[NEY][RX];
+        float4 x[TY][NEX];
     } w;
-    union N {   // net fluxes: y (phases 2-3), then x (5-6)
-        struct Y { float l[2][TY + 1][RX], r[2][TY + 1][RX]; } y;
-        struct X { float l[2][TY][TX + 1], r[2][TY][TX + 1]; } x;
+    union N {           // net fluxes (L0, L1, R0, R1): y (phases 2-3), then x (5-6)
+        float4 y[TY + 1][RX];
+        float4 x[TY][TX + 1];
     } n;
 };
 
@@ -119,9 +130,9 @@ __device__ __forceinline__ void load_raw(const AdjParams<float> &p, int i0, int 
             cj = ghost_index(cj, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
         }
         const size_t o = (size_t)cj * p.nx + ci;
-        R.e[k] = __ldg(p.src[0] + o);
-        R.c[k] = __ldg(p.c + o);
-        const float mu = __ldg(p.src[1] + o), ga = __ldg(p.src[2] + o);
+        R.e[k] = ld_early(p.src[0] + o);
+        R.c[k] = ld_early(p.c + o);
+        const float mu = ld_early(p.src[1] + o), ga = ld_early(p.src[2] + o);
         R.m[k] = fx ? -mu : mu;
         R.g[k] = fy ? -ga : ga;
     }
@@ -140,72 +151,48 @@ __device__ __forceinline__ void tile_compute(Smem<TX, TY> &S, const AdjParams<fl
         const int r = tid + k * NT;
         if (r >= RX * RY) continue;
         const int ry = r / RX, rx = r - ry * RX;
-        S.e[ry][rx] = R.e[k];
-        S.m[ry][rx] = R.m[k];
-        S.g[ry][rx] = R.g[k];
-        S.c[ry][rx] = R.c[k];
+        S.q[ry][rx] = make_float4(R.e[k], R.m[k], R.g[k], R.c[k]);
     }
     __syncthreads();
     // phase 1: y-edge waves of every staged column (edge k between rows k, k+1)
     for (int i = tid; i < NEY * RX; i += NT) {
         const int k = i / RX, rx = i - k * RX;
-        const EdgeA w = solve_a(S.e[k][rx], S.g[k][rx], S.c[k][rx], S.e[k + 1][rx],
-                                S.g[k + 1][rx], S.c[k + 1][rx]);
-        S.w.y[0][k][rx] = w.b1; S.w.y[1][k][rx] = w.b2;
-        S.w.y[2][k][rx] = w.cl; S.w.y[3][k][rx] = w.cr;
+        const float4 a = S.q[k][rx], b = S.q[k + 1][rx];
+        S.w.y[k][rx] = pack_edge(solve_a(a.x, a.z, a.w, b.x, b.z, b.w));
     }
     __syncthreads();
     // phase 2: y net fluxes of edges 1 .. TY+1 in every staged column
     for (int i = tid; i < (TY + 1) * RX; i += NT) {
         const int e = 1 + i / RX, rx = i - (e - 1) * RX;
-        EdgeA a, b, c;
-        a.b1 = S.w.y[0][e - 1][rx]; a.b2 = S.w.y[1][e - 1][rx];
-        a.cl = S.w.y[2][e - 1][rx]; a.cr = S.w.y[3][e - 1][rx];
-        b.b1 = S.w.y[0][e][rx]; b.b2 = S.w.y[1][e][rx];
-        b.cl = S.w.y[2][e][rx]; b.cr = S.w.y[3][e][rx];
-        c.b1 = S.w.y[0][e + 1][rx]; c.b2 = S.w.y[1][e + 1][rx];
-        c.cl = S.w.y[2][e + 1][rx]; c.cr = S.w.y[3][e + 1][rx];
-        const bool wall = !(S.c[e][rx] > 0.f) || !(S.c[e + 1][rx] > 0.f);
-        float L[2], Rr[2];
-        net_a(a, b, c, nuy, order, wall, L, Rr);
-        S.n.y.l[0][e - 1][rx] = L[0]; S.n.y.l[1][e - 1][rx] = L[1];
-        S.n.y.r[0][e - 1][rx] = Rr[0]; S.n.y.r[1][e - 1][rx] = Rr[1];
+        S.n.y[e - 1][rx] = net_a(unpack_edge(S.w.y[e - 1][rx]), unpack_edge(S.w.y[e][rx]),
+                                 unpack_edge(S.w.y[e + 1][rx]), nuy, order);
     }
     __syncthreads();
     // phase 3: y-sweep of the tile rows in every staged column, in place;
     // lower edge of row -> R at index row, upper edge -> L at row + 1
     for (int i = tid; i < TY * RX; i += NT) {
         const int row = i / RX, rx = i - row * RX, ry = row + 2;
-        if (S.c[ry][rx] > 0.f) {
-            S.e[ry][rx] += -nuy * (S.n.y.r[0][row][rx] + S.n.y.l[0][row + 1][rx]);
-            S.g[ry][rx] += -nuy * (S.n.y.r[1][row][rx] + S.n.y.l[1][row + 1][rx]);
+        float4 c = S.q[ry][rx];
+        if (c.w > 0.f) {
+            const float4 lo = S.n.y[row][rx], up = S.n.y[row + 1][rx];
+            c.x += -nuy * (lo.z + up.x);
+            c.z += -nuy * (lo.w + up.y);
+            S.q[ry][rx] = c;
         }
     }
     __syncthreads();
     // phase 4: x-edge waves of the y-swept tile rows (edge k between cols k, k+1)
     for (int i = tid; i < TY * NEX; i += NT) {
         const int row = i / NEX, k = i - row * NEX, ry = row + 2;
-        const EdgeA w = solve_a(S.e[ry][k], S.m[ry][k], S.c[ry][k], S.e[ry][k + 1],
-                                S.m[ry][k + 1], S.c[ry][k + 1]);
-        S.w.x[0][row][k] = w.b1; S.w.x[1][row][k] = w.b2;
-        S.w.x[2][row][k] = w.cl; S.w.x[3][row][k] = w.cr;
+        const float4 a = S.q[ry][k], b = S.q[ry][k + 1];
+        S.w.x[row][k] = pack_edge(solve_a(a.x, a.y, a.w, b.x, b.y, b.w));
     }
     __syncthreads();
     // phase 5: x net fluxes of edges 1 .. TX+1 of the tile rows
     for (int i = tid; i < TY * (TX + 1); i += NT) {
-        const int row = i / (TX + 1), e = 1 + (i - row * (TX + 1)), ry = row + 2;
-        EdgeA a, b, c;
-        a.b1 = S.w.x[0][row][e - 1]; a.b2 = S.w.x[1][row][e - 1];
-        a.cl = S.w.x[2][row][e - 1]; a.cr = S.w.x[3][row][e - 1];
-        b.b1 = S.w.x[0][row][e]; b.b2 = S.w.x[1][row][e];
-        b.cl = S.w.x[2][row][e]; b.cr = S.w.x[3][row][e];
-        c.b1 = S.w.x[0][row][e + 1]; c.b2 = S.w.x[1][row][e + 1];
-        c.cl = S.w.x[2][row][e + 1]; c.cr = S.w.x[3][row][e + 1];
-        const bool wall = !(S.c[ry][e] > 0.f) || !(S.c[ry][e + 1] > 0.f);
-        float L[2], Rr[2];
-        net_a(a, b, c, nux, order, wall, L, Rr);
-        S.n.x.l[0][row][e - 1] = L[0]; S.n.x.l[1][row][e - 1] = L[1];
-        S.n.x.r[0][row][e - 1] = Rr[0]; S.n.x.r[1][row][e - 1] = Rr[1];
+        const int row = i / (TX + 1), e = 1 + (i - row * (TX + 1));
+        S.n.x[row][e - 1] = net_a(unpack_edge(S.w.x[row][e - 1]), unpack_edge(S.w.x[row][e]),
+                                  unpack_edge(S.w.x[row][e + 1]), nux, order);
     }
     __syncthreads();
     // phase 6: x-sweep of the tile cells -> new state (+ snapshot)
@@ -216,11 +203,13 @@ __device__ __forceinline__ void tile_compute(Smem<TX, TY> &S, const AdjParams<fl
         const int gi = i0 + col, gj = j0 + row;
         const int ry = row + 2, rx = col + 2;
         if (gi < p.nx && gj < p.ny) {
-            float ne = S.e[ry][rx], nm = S.m[ry][rx];
-            const float ng = S.g[ry][rx];
-            if (S.c[ry][rx] > 0.f) {
-                ne += -nux * (S.n.x.r[0][row][col] + S.n.x.l[0][row][col + 1]);
-                nm += -nux * (S.n.x.r[1][row][col] + S.n.x.l[1][row][col + 1]);
+            const float4 c = S.q[ry][rx];
+            float ne = c.x, nm = c.y;
+            const float ng = c.z;
+            if (c.w > 0.f) {
+                const float4 le = S.n.x[row][col], re = S.n.x[row][col + 1];
+                ne += -nux * (le.z + re.x);
+                nm += -nux * (le.w + re.y);
             }
             const size_t o = (size_t)gj * p.nx + gi;
             p.dst[0][o] = ne;

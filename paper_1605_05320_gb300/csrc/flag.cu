@@ -207,12 +207,18 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
     __shared__ Window sw;
     if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
     __syncthreads();
-    const Window w = sw;
+    const Window &w = sw;   // read from shared memory where used
     const int cur = p.clk->cur;
     const size_t n4 = ((size_t)p.nx * p.ny) >> 2;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool interp = p.mode != SWA_FLAG_BRACKET;
+    const float tol = (float)p.tol;
+    const float tolp = (float)(p.tol * (1.0 - 1e-5));
+    const int gb0 = w.k0 / kEnvGroup, gb1 = w.k1 / kEnvGroup;
+    const size_t cs = p.na >> 2, ks = p.snap_stride >> 2;
     int f = 0;
-    if (i < n4) {
+    // persistent grid: each block walks quads i, i + gridDim.x * 256, ...
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
         const float4 e = reinterpret_cast<const float4 *>(p.q[cur][0])[i];
         const float4 u = reinterpret_cast<const float4 *>(p.q[cur][1])[i];
         const float4 v = reinterpret_cast<const float4 *>(p.q[cur][2])[i];
@@ -223,8 +229,8 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
         const bool ok2 = e.z + hb.z > dt && wet.z, ok3 = e.w + hb.w > dt && wet.w;
         float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 dh0 = m, dh1 = m, dl0 = m, dl1 = m;
-        // skip test of envelope group gb (PRUNE only)
-        const float tolp = (float)(p.tol * (1.0 - 1e-5));
+        // envelope test of group gb (PRUNE only): true when no product of the
+        // group can reach tol in any wet cell of the quad
         auto skip = [&](int gb) -> bool {
             const float *eg = p.env + (size_t)gb * 3 * n4;
             const float Me = __ldg(eg + i), Mu = __ldg(eg + n4 + i), Mv = __ldg(eg + 2 * n4 + i);
@@ -237,44 +243,61 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
         };
         if (!w.empty && (ok0 || ok1 || ok2 || ok3 || !PRUNE)) {
             const float4 *s0 = reinterpret_cast<const float4 *>(p.snaps) + i;
-            const size_t cs = p.na >> 2, ks = p.snap_stride >> 2;
-            const bool interp = p.mode != SWA_FLAG_BRACKET;
+            // skip bits of the first 32 groups of the window (256 snapshots),
+            // their loads issued independently of one another
+            unsigned mask = 0u;
+            if (PRUNE) {
+                const int ng = gb1 - gb0 + 1 < 32 ? gb1 - gb0 + 1 : 32;
+#pragma unroll 2
+                for (int j = 0; j < ng; j++)
+                    if (skip(gb0 + j)) mask |= 1u << j;
+            }
+            // groups past the first 32 of the window are always read
+            auto skipped = [&](int gb) -> bool {
+                const int j = gb - gb0;
+                return j < 32 && ((mask >> j) & 1u) != 0u;
+            };
             bool need_h = true, need_l = true;
             if (PRUNE && interp) {
                 const int kh1 = w.exact_h ? w.kh : w.kh + 1;
                 const int kl1 = w.exact_l ? w.kl : w.kl + 1;
-                need_h = !(skip(w.kh / kEnvGroup) && skip(kh1 / kEnvGroup));
-                need_l = !(skip(w.kl / kEnvGroup) && skip(kl1 / kEnvGroup));
+                need_h = !(skipped(w.kh / kEnvGroup) && skipped(kh1 / kEnvGroup));
+                need_l = !(skipped(w.kl / kEnvGroup) && skipped(kl1 / kEnvGroup));
             }
-            int gcur = -1;
-            bool gskip = false;
+            for (int gb = gb0; gb <= gb1; gb++) {
+                const bool gs = PRUNE && skipped(gb);
+                const int ka = w.k0 > gb * kEnvGroup ? w.k0 : gb * kEnvGroup;
+                const int kb = w.k1 < gb * kEnvGroup + kEnvGroup - 1 ? w.k1
+                                                                    : gb * kEnvGroup + kEnvGroup - 1;
+                if (gs) {
+                    // a skipped group can only supply the snapshots of a
+                    // needed end pair
+                    const bool hh = need_h && w.kh <= kb && w.kh + 1 >= ka;
+                    const bool ll = need_l && w.kl <= kb && w.kl + 1 >= ka;
+                    if (!interp || !(hh || ll)) continue;
+                }
 #pragma unroll 2
-            for (int k = w.k0; k <= w.k1; k++) {
-                if (PRUNE) {
-                    const int gb = k / kEnvGroup;
-                    if (gb != gcur) { gcur = gb; gskip = skip(gb); }
-                    if (gskip) {
-                        const bool end = interp && ((need_h && (k == w.kh || k == w.kh + 1)) ||
-                                                    (need_l && (k == w.kl || k == w.kl + 1)));
-                        if (!end) continue;
+                for (int k = ka; k <= kb; k++) {
+                    if (gs && !((need_h && (k == w.kh || k == w.kh + 1)) ||
+                                (need_l && (k == w.kl || k == w.kl + 1))))
+                        continue;
+                    const float4 a = __ldcs(s0 + (size_t)k * ks);
+                    const float4 b = __ldcs(s0 + (size_t)k * ks + cs);
+                    const float4 c = __ldcs(s0 + (size_t)k * ks + 2 * cs);
+                    float4 d;
+                    d.x = a.x * e.x + b.x * u.x + c.x * v.x;
+                    d.y = a.y * e.y + b.y * u.y + c.y * v.y;
+                    d.z = a.z * e.z + b.z * u.z + c.z * v.z;
+                    d.w = a.w * e.w + b.w * u.w + c.w * v.w;
+                    if (k >= w.ki0 && k <= w.ki1) {
+                        m.x = fmaxf(m.x, fabsf(d.x)); m.y = fmaxf(m.y, fabsf(d.y));
+                        m.z = fmaxf(m.z, fabsf(d.z)); m.w = fmaxf(m.w, fabsf(d.w));
                     }
+                    if (k == w.kh) dh0 = d;
+                    if (k == w.kh + 1) dh1 = d;
+                    if (k == w.kl) dl0 = d;
+                    if (k == w.kl + 1) dl1 = d;
                 }
-                const float4 a = __ldcs(s0 + (size_t)k * ks);
-                const float4 b = __ldcs(s0 + (size_t)k * ks + cs);
-                const float4 c = __ldcs(s0 + (size_t)k * ks + 2 * cs);
-                float4 d;
-                d.x = a.x * e.x + b.x * u.x + c.x * v.x;
-                d.y = a.y * e.y + b.y * u.y + c.y * v.y;
-                d.z = a.z * e.z + b.z * u.z + c.z * v.z;
-                d.w = a.w * e.w + b.w * u.w + c.w * v.w;
-                if (k >= w.ki0 && k <= w.ki1) {
-                    m.x = fmaxf(m.x, fabsf(d.x)); m.y = fmaxf(m.y, fabsf(d.y));
-                    m.z = fmaxf(m.z, fabsf(d.z)); m.w = fmaxf(m.w, fabsf(d.w));
-                }
-                if (k == w.kh) dh0 = d;
-                if (k == w.kh + 1) dh1 = d;
-                if (k == w.kl) dl0 = d;
-                if (k == w.kl + 1) dl1 = d;
             }
             if (interp) {
                 const float ah = (float)w.ah, al = (float)w.al;
@@ -289,7 +312,6 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
 #undef SWADJ_ENDS
             }
         }
-        const float tol = (float)p.tol;
         const int f0 = (!w.empty && ok0 && m.x >= tol), f1 = (!w.empty && ok1 && m.y >= tol);
         const int f2 = (!w.empty && ok2 && m.z >= tol), f3 = (!w.empty && ok3 && m.w >= tol);
         reinterpret_cast<uchar4 *>(p.flags)[i] = make_uchar4(f0, f1, f2, f3);
@@ -298,7 +320,7 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
                                           ok2 ? m.z : 0.f, ok3 ? m.w : 0.f);
             reinterpret_cast<float4 *>(p.maxip)[i] = w.empty ? make_float4(0.f, 0.f, 0.f, 0.f) : mm;
         }
-        f = f0 + f1 + f2 + f3;
+        f += f0 + f1 + f2 + f3;
     }
     int cnt = f;
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -332,6 +354,22 @@ int env_launch_update(const float *slot, size_t na, float *env_group, int first,
     return swadj_host::cuda_check(cudaGetLastError(), "env_update_kernel");
 }
 
+// Blocks of the persistent FP32 flag pass: every SM filled with as many
+// blocks as fit.
+template <bool PRUNE>
+static size_t persistent_flag_blocks() {
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flag_kernel_f32x4<PRUNE>, 256, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+    }
+    return (size_t)per_sm * (size_t)sms;
+}
+
 template <typename R, typename S>
 int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     const size_t n = (size_t)p.nx * p.ny;
@@ -341,10 +379,14 @@ int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     if (sizeof(R) == 4 && sizeof(S) == 4 && p.same_grid && p.two_d && (n & 3) == 0) {
         const size_t n4 = n >> 2;
         const FlagParams<float, float> &pf = *reinterpret_cast<const FlagParams<float, float> *>(&p);
-        if (p.env && !p.maxip)
-            flag_kernel_f32x4<true><<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(pf);
-        else
-            flag_kernel_f32x4<false><<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(pf);
+        const size_t need = (n4 + 255) / 256;
+        if (p.env && !p.maxip) {
+            const size_t b = persistent_flag_blocks<true>();
+            flag_kernel_f32x4<true><<<(unsigned)(need < b ? need : b), 256, 0, st>>>(pf);
+        } else {
+            const size_t b = persistent_flag_blocks<false>();
+            flag_kernel_f32x4<false><<<(unsigned)(need < b ? need : b), 256, 0, st>>>(pf);
+        }
     } else if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
     else flag_kernel<R, S, false><<<blocks, 256, 0, st>>>(p);
     return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");

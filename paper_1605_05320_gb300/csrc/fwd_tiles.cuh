@@ -174,9 +174,9 @@ __device__ __forceinline__ void load_raw(const View &V, int i0, int j0, Raw<TX, 
             cj = ghost_index(cj, V.ny, V.bc.lo_y, V.bc.hi_y, &fy);
         }
         const size_t o = (size_t)cj * V.nx + ci;
-        R.eta[k] = __ldg(V.q0 + o);
-        R.hb[k] = __ldg(V.hb + o);
-        const float mu = __ldg(V.q1 + o), mv = __ldg(V.q2 + o);
+        R.eta[k] = ld_early(V.q0 + o);
+        R.hb[k] = ld_early(V.hb + o);
+        const float mu = ld_early(V.q1 + o), mv = ld_early(V.q2 + o);
         R.mu[k] = fx ? -mu : mu;
         R.mv[k] = fy ? -mv : mv;
     }

@@ -45,6 +45,16 @@ __device__ __forceinline__ int ghost_index(int g, int n, int bc_lo, int bc_hi,
     return g;
 }
 
+// Read-only global load as volatile inline PTX: it stays ahead of the
+// barriers that follow it in program order, so a register prefetch of the
+// next tile is issued before the current tile's work instead of being moved
+// next to its first use.
+__device__ __forceinline__ float ld_early(const float *p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // MC limiter: max(0, min((1+theta)/2, 2, 2 theta)).
 template <typename R>
 __device__ __forceinline__ R mc_phi(R theta) {
