@@ -135,11 +135,12 @@ int swa_get_time(swa_grid *grid, double *t, double *dt_next,
                  long long *nsteps, void *stream);
 
 /*
- * Launch shape of the FP32 step kernel: the tile height in rows, 8 or 16
- * (0 restores the default, 16).  Results do not depend on it; throughput
- * does (the autotuner picks it per grid size).  FP64 grids ignore it.
+ * Launch shape of the FP32 2D step kernel: the height in rows of the strip a
+ * warp walks, 16, 32 or 64 (0 restores the default, 32).  Results do not
+ * depend on it; throughput does (the autotuner picks it per grid size).
+ * FP64 and 1D grids ignore it.
  */
-#define SWA_MIN_STRIP_ROWS 8
+#define SWA_MIN_STRIP_ROWS 16
 int swa_grid_set_strip_rows(swa_grid *grid, int rows);
 
 /*

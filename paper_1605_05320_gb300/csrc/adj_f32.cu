@@ -1,16 +1,10 @@
 // adj_f32.cu -- FP32 adjoint step (Sec. 4; the time-reversed linear adjoint
 // of adj_kernels.cuh, dimensionally split y then x).
 //
-// 2D grids run a persistent tile kernel in the style of the forward step:
-// a TX x TY tile and a 2-cell halo with corners are staged in shared memory;
-// phases (1) y-edge waves of every staged column, (2) their net fluxes (the
-// limiter once per edge), (3) y-sweep of the tile rows in every staged
-// column, in place (the x-sweep needs the y-swept state in the halo
-// columns), (4) x-edge waves of the tile rows, (5) their net fluxes, (6)
-// x-sweep update, written to the new state and, every snapshot step, to the
-// snapshot slot.  The raw values of the next tile are loaded into registers
-// while the current one is computed.  1D grids keep the one-tile-per-block
-// kernel of adj_kernels.cuh.
+// 2D grids run the warp-strip kernel below: per edge the same waves and
+// limited net fluxes as the FP64 kernel, each edge solved once, the y-sweep
+// in registers and the x-sweep across a warp by shuffles.  1D grids keep the
+// one-tile-per-block kernel of adj_kernels.cuh.
 //
 // The limiter needs no division by the wave norm: for Z = b (c, 1) and its
 // upwind neighbour Zu = bu (cu, 1), theta b = bu (cu c + 1) / (c^2 + 1), and
@@ -20,8 +14,6 @@
 
 namespace swadj {
 namespace adjt {
-
-constexpr int NT = 256;
 
 __device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
 
@@ -60,18 +52,6 @@ __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR,
     return w;
 }
 
-// Shared-memory record of an edge, (b1, b2, cl, cr) with the wall flag in
-// the sign bit of cl (cl >= 0, so |cl| restores it exactly).
-__device__ __forceinline__ float4 pack_edge(const EdgeA &w) {
-    return make_float4(w.b1, w.b2, w.wall ? -w.cl : w.cl, w.cr);
-}
-__device__ __forceinline__ EdgeA unpack_edge(const float4 &r) {
-    EdgeA w;
-    w.b1 = r.x; w.b2 = r.y; w.cl = fabsf(r.z); w.cr = r.w;
-    w.wall = signbit(r.z);
-    return w;
-}
-
 // Net fluxes of edge w (neighbour edges wl, wr) as (L0, L1, R0, R1): L into
 // the left cell, R into the right cell (Q -= nu * net); components
 // (eta~, normal).
@@ -91,206 +71,126 @@ __device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const E
     return make_float4(w.b1 * w.cl + F0, w.b1 + F1, -(w.b2 * w.cr) - F0, w.b2 - F1);
 }
 
-template <int TX, int TY>
-struct Smem {
-    static constexpr int RX = TX + 4, RY = TY + 4, NEX = TX + 3, NEY = TY + 3;
-    float4 q[RY][RX];   // cell records (eta~, mu~, gamma~, c)
-    union W {           // edge records: y (phases 1-2), then x (4-5)
-        float4 y[NEY][RX];
-        float4 x[TY][NEX];
-    } w;
-    union N {           // net fluxes (L0, L1, R0, R1): y (phases 2-3), then x (5-6)
-        float4 y[TY + 1][RX];
-        float4 x[TY][TX + 1];
-    } n;
+// ---------------------------------------------------------------- strips
+// A warp owns a strip of 32 columns (lanes) of which the middle 28 are its
+// output, and SH output rows, which it walks downwards.  The y-sweep runs in
+// registers with a sliding window over rows (each y-edge solved and limited
+// once); every y-swept row is then x-swept across the warp with shuffles
+// (each x-edge solved and limited once by the lane on its left).  Lanes 0-1
+// and 30-31 are the x-halo: their y-swept values feed the output lanes' x
+// edges.  No shared memory and no barriers.
+constexpr int kLanes = 32;
+constexpr int kOut = kLanes - 4;   // output columns per strip
+constexpr int kRows = 16;          // output rows per strip
+constexpr unsigned kFull = 0xffffffffu;
+
+struct CellA {
+    float e, m, g, c;   // eta~, mu~, gamma~, c = sqrt(g hbar) (0 if dry)
 };
 
-template <int TX, int TY>
-struct Raw {
-    static constexpr int RX = TX + 4, RY = TY + 4;
-    static constexpr int RPT = (RX * RY + NT - 1) / NT;
-    float e[RPT], m[RPT], g[RPT], c[RPT];
-};
-
-template <int TX, int TY>
-__device__ __forceinline__ void load_raw(const AdjParams<float> &p, int i0, int j0,
-                                         Raw<TX, TY> &R) {
-    constexpr int RX = TX + 4, RY = TY + 4;
-    const bool interior = i0 - 2 >= 0 && i0 + TX + 2 <= p.nx && j0 - 2 >= 0 &&
-                          j0 + TY + 2 <= p.ny;
-#pragma unroll
-    for (int k = 0; k < Raw<TX, TY>::RPT; k++) {
-        const int r = threadIdx.x + k * NT;
-        if (r >= RX * RY) continue;
-        const int ry = r / RX, rx = r - ry * RX;
-        int ci = i0 + rx - 2, cj = j0 + ry - 2;
-        bool fx = false, fy = false;
-        if (!interior) {
-            ci = ghost_index(ci, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
-            cj = ghost_index(cj, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
-        }
-        const size_t o = (size_t)cj * p.nx + ci;
-        R.e[k] = ld_early(p.src[0] + o);
-        R.c[k] = ld_early(p.c + o);
-        const float mu = ld_early(p.src[1] + o), ga = ld_early(p.src[2] + o);
-        R.m[k] = fx ? -mu : mu;
-        R.g[k] = fy ? -ga : ga;
-    }
+__device__ __forceinline__ CellA load_cell(const AdjParams<float> &p, int col, bool fx, int row,
+                                           bool fy) {
+    const size_t o = (size_t)row * p.nx + col;
+    CellA q;
+    q.e = __ldg(p.src[0] + o);
+    const float mu = __ldg(p.src[1] + o), ga = __ldg(p.src[2] + o);
+    q.m = fx ? -mu : mu;
+    q.g = fy ? -ga : ga;
+    q.c = __ldg(p.c + o);
+    return q;
 }
 
-template <int TX, int TY>
-__device__ __forceinline__ void tile_compute(Smem<TX, TY> &S, const AdjParams<float> &p,
-                                             int i0, int j0, const Raw<TX, TY> &R) {
-    constexpr int RX = TX + 4, RY = TY + 4, NEX = TX + 3, NEY = TY + 3;
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
+    const int lane = threadIdx.x & 31;
+    const int nsx = (p.nx + kOut - 1) / kOut, nsy = (p.ny + kRows - 1) / kRows;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if ((p.snap_f || p.snap_d) && blockIdx.x == 0 && threadIdx.x == 0) *p.tau_dev = p.tau_val;
+    if (unit >= nsx * nsy) return;   // warp-uniform
+    const int sy = unit / nsx, sx = unit - sy * nsx;
+    const int x0 = sx * kOut, y0 = sy * kRows;
+    const int ylast = (y0 + kRows < p.ny ? y0 + kRows : p.ny) - 1;
+    const int gi = x0 - 2 + lane;
+    bool fx;
+    const int col = ghost_index(gi, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
+    const bool out = lane >= 2 && lane < kLanes - 2 && gi < p.nx;
     const float nux = p.nux, nuy = p.nuy;
     const int order = p.order;
-    // phase 0: stage
-#pragma unroll
-    for (int k = 0; k < Raw<TX, TY>::RPT; k++) {
-        const int r = tid + k * NT;
-        if (r >= RX * RY) continue;
-        const int ry = r / RX, rx = r - ry * RX;
-        S.q[ry][rx] = make_float4(R.e[k], R.m[k], R.g[k], R.c[k]);
-    }
-    __syncthreads();
-    // phase 1: y-edge waves of every staged column (edge k between rows k, k+1)
-    for (int i = tid; i < NEY * RX; i += NT) {
-        const int k = i / RX, rx = i - k * RX;
-        const float4 a = S.q[k][rx], b = S.q[k + 1][rx];
-        S.w.y[k][rx] = pack_edge(solve_a(a.x, a.z, a.w, b.x, b.z, b.w));
-    }
-    __syncthreads();
-    // phase 2: y net fluxes of edges 1 .. TY+1 in every staged column
-    for (int i = tid; i < (TY + 1) * RX; i += NT) {
-        const int e = 1 + i / RX, rx = i - (e - 1) * RX;
-        S.n.y[e - 1][rx] = net_a(unpack_edge(S.w.y[e - 1][rx]), unpack_edge(S.w.y[e][rx]),
-                                 unpack_edge(S.w.y[e + 1][rx]), nuy, order);
-    }
-    __syncthreads();
-    // phase 3: y-sweep of the tile rows in every staged column, in place;
-    // lower edge of row -> R at index row, upper edge -> L at row + 1
-    for (int i = tid; i < TY * RX; i += NT) {
-        const int row = i / RX, rx = i - row * RX, ry = row + 2;
-        float4 c = S.q[ry][rx];
-        if (c.w > 0.f) {
-            const float4 lo = S.n.y[row][rx], up = S.n.y[row + 1][rx];
-            c.x += -nuy * (lo.z + up.x);
-            c.z += -nuy * (lo.w + up.y);
-            S.q[ry][rx] = c;
+    CellA A = {0.f, 0.f, 0.f, 0.f}, B = A;   // rows j-2, j-1
+    EdgeA W1 = {0.f, 0.f, 0.f, 0.f, false}, W2 = W1;   // y-edges (j-3|j-2), (j-2|j-1)
+    float rp0 = 0.f, rp1 = 0.f;   // R part of the y-net of edge (j-3|j-2)
+    // rows are loaded one iteration ahead of their use
+    bool fy;
+    int row = ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+    CellA Cn = load_cell(p, col, fx, row, fy);
+    for (int j = y0 - 2; j <= ylast + 2; j++) {
+        const CellA C = Cn;
+        if (j < ylast + 2) {
+            row = ghost_index(j + 1, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+            Cn = load_cell(p, col, fx, row, fy);
         }
-    }
-    __syncthreads();
-    // phase 4: x-edge waves of the y-swept tile rows (edge k between cols k, k+1)
-    for (int i = tid; i < TY * NEX; i += NT) {
-        const int row = i / NEX, k = i - row * NEX, ry = row + 2;
-        const float4 a = S.q[ry][k], b = S.q[ry][k + 1];
-        S.w.x[row][k] = pack_edge(solve_a(a.x, a.y, a.w, b.x, b.y, b.w));
-    }
-    __syncthreads();
-    // phase 5: x net fluxes of edges 1 .. TX+1 of the tile rows
-    for (int i = tid; i < TY * (TX + 1); i += NT) {
-        const int row = i / (TX + 1), e = 1 + (i - row * (TX + 1));
-        S.n.x[row][e - 1] = net_a(unpack_edge(S.w.x[row][e - 1]), unpack_edge(S.w.x[row][e]),
-                                  unpack_edge(S.w.x[row][e + 1]), nux, order);
-    }
-    __syncthreads();
-    // phase 6: x-sweep of the tile cells -> new state (+ snapshot)
-    constexpr int CPT = TX * TY / NT;
-#pragma unroll
-    for (int k = 0; k < CPT; k++) {
-        const int cidx = tid + k * NT, row = cidx / TX, col = cidx % TX;
-        const int gi = i0 + col, gj = j0 + row;
-        const int ry = row + 2, rx = col + 2;
-        if (gi < p.nx && gj < p.ny) {
-            const float4 c = S.q[ry][rx];
-            float ne = c.x, nm = c.y;
-            const float ng = c.z;
-            if (c.w > 0.f) {
-                const float4 le = S.n.x[row][col], re = S.n.x[row][col + 1];
-                ne += -nux * (le.z + re.x);
-                nm += -nux * (le.w + re.y);
+        EdgeA Wn = W2;
+        if (j >= y0 - 1) Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);   // edge (j-1|j)
+        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j >= y0 + 1) nn = net_a(W1, W2, Wn, nuy, order);           // edge (j-2|j-1)
+        if (j >= y0 + 2) {
+            // y-sweep of row r = j - 2: lower edge -> R of the previous net,
+            // upper edge -> L of this one
+            float e = A.e, g = A.g;
+            const float m = A.m, c = A.c;
+            if (c > 0.f) {
+                e += -nuy * (rp0 + nn.x);
+                g += -nuy * (rp1 + nn.y);
             }
-            const size_t o = (size_t)gj * p.nx + gi;
-            p.dst[0][o] = ne;
-            p.dst[1][o] = nm;
-            p.dst[2][o] = ng;
-            if (p.snap_f) {
-                __stcs(p.snap_f + o, ne);
-                __stcs(p.snap_f + p.snap_comp_stride + o, nm);
-                __stcs(p.snap_f + 2 * p.snap_comp_stride + o, ng);
-            } else if (p.snap_d) {
-                __stcs(p.snap_d + o, (double)ne);
-                __stcs(p.snap_d + p.snap_comp_stride + o, (double)nm);
-                __stcs(p.snap_d + 2 * p.snap_comp_stride + o, (double)ng);
+            // x-sweep of row r: lane l solves edge (l|l+1)
+            const float eR = __shfl_down_sync(kFull, e, 1);
+            const float mR = __shfl_down_sync(kFull, m, 1);
+            const float cR = __shfl_down_sync(kFull, c, 1);
+            const EdgeA X = solve_a(e, m, c, eR, mR, cR);
+            EdgeA XL = X, XR = X;   // only the fields net_a reads are exchanged
+            XL.b2 = __shfl_up_sync(kFull, X.b2, 1);
+            XL.cr = __shfl_up_sync(kFull, X.cr, 1);
+            XR.b1 = __shfl_down_sync(kFull, X.b1, 1);
+            XR.cl = __shfl_down_sync(kFull, X.cl, 1);
+            const float4 xn = net_a(XL, X, XR, nux, order);
+            const float xr0 = __shfl_up_sync(kFull, xn.z, 1);   // R of edge (l-1|l)
+            const float xr1 = __shfl_up_sync(kFull, xn.w, 1);
+            float ne = e, nm = m;
+            if (c > 0.f) {
+                ne += -nux * (xr0 + xn.x);
+                nm += -nux * (xr1 + xn.y);
+            }
+            if (out) {
+                const size_t o = (size_t)(j - 2) * p.nx + gi;
+                p.dst[0][o] = ne;
+                p.dst[1][o] = nm;
+                p.dst[2][o] = g;
+                if (p.snap_f) {
+                    __stcs(p.snap_f + o, ne);
+                    __stcs(p.snap_f + p.snap_comp_stride + o, nm);
+                    __stcs(p.snap_f + 2 * p.snap_comp_stride + o, g);
+                } else if (p.snap_d) {
+                    __stcs(p.snap_d + o, (double)ne);
+                    __stcs(p.snap_d + p.snap_comp_stride + o, (double)nm);
+                    __stcs(p.snap_d + 2 * p.snap_comp_stride + o, (double)g);
+                }
             }
         }
-    }
-    __syncthreads();  // the next tile overwrites the shared buffers
-}
-
-template <int TX, int TY>
-__global__ void __launch_bounds__(NT) adj_f32_tiles(AdjParams<float> p) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    Smem<TX, TY> &S = *reinterpret_cast<Smem<TX, TY> *>(dsm);
-    const int ntx = (p.nx + TX - 1) / TX;
-    const int n = ntx * ((p.ny + TY - 1) / TY);
-    if ((p.snap_f || p.snap_d) && blockIdx.x == 0 && threadIdx.x == 0) *p.tau_dev = p.tau_val;
-    int k = blockIdx.x;
-    if (k >= n) return;
-    int ty = k / ntx;
-    int i0 = (k - ty * ntx) * TX, j0 = ty * TY;
-    Raw<TX, TY> cur;
-    load_raw<TX, TY>(p, i0, j0, cur);
-    while (true) {
-        const int kn = k + gridDim.x;
-        int in0 = 0, jn0 = 0;
-        Raw<TX, TY> nxt;
-        if (kn < n) {
-            const int tyn = kn / ntx;
-            in0 = (kn - tyn * ntx) * TX;
-            jn0 = tyn * TY;
-            load_raw<TX, TY>(p, in0, jn0, nxt);
-        }
-        tile_compute<TX, TY>(S, p, i0, j0, cur);
-        if (kn >= n) break;
-        k = kn; i0 = in0; j0 = jn0; cur = nxt;
+        A = B; B = C;
+        W1 = W2; W2 = Wn;
+        rp0 = nn.z; rp1 = nn.w;
     }
 }
 
 }  // namespace adjt
 
-constexpr int kATX = 32, kATY = 16;
-
-// Blocks of the persistent launch: every SM filled with as many blocks as
-// fit, never more than there are tiles.
-static int adj_persistent_blocks(int ntiles) {
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(adjt::adj_f32_tiles<kATX, kATY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(adjt::Smem<kATX, kATY>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, adjt::adj_f32_tiles<kATX, kATY>, adjt::NT,
-            sizeof(adjt::Smem<kATX, kATY>));
-        if (per_sm < 1) per_sm = 1;
-        if (sms < 1) sms = 1;
-    }
-    const int b = per_sm * sms;
-    return ntiles < b ? ntiles : b;
-}
-
 template <>
 int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
     if (p.two_d) {
-        const int ntiles = ((p.nx + kATX - 1) / kATX) * ((p.ny + kATY - 1) / kATY);
-        const int blocks = adj_persistent_blocks(ntiles);
-        adjt::adj_f32_tiles<kATX, kATY>
-            <<<blocks, adjt::NT, sizeof(adjt::Smem<kATX, kATY>), st>>>(p);
-        return swadj_host::cuda_check(cudaGetLastError(), "adj_f32_tiles");
+        const long long units = (long long)((p.nx + adjt::kOut - 1) / adjt::kOut) *
+                                ((p.ny + adjt::kRows - 1) / adjt::kRows);
+        const unsigned blocks = (unsigned)((units + 7) / 8);
+        adjt::adj_f32_strips<<<blocks, 256, 0, st>>>(p);
+        return swadj_host::cuda_check(cudaGetLastError(), "adj_f32_strips");
     }
     dim3 grid((p.nx + 127) / 128, 1);
     adj_step_kernel<float, false, 128, 1><<<grid, dim3(128, 1), 0, st>>>(p);

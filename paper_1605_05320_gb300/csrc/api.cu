@@ -410,8 +410,8 @@ int swa_get_time(swa_grid *g, double *t, double *dt_next, long long *nsteps, voi
 
 int swa_grid_set_strip_rows(swa_grid *g, int rows) {
     if (!g) return set_error(SWA_EINVAL, "null grid");
-    if (rows != 0 && rows != 8 && rows != 16)
-        return set_error(SWA_EINVAL, "tile rows must be 0, 8 or 16");
+    if (rows != 0 && rows != 16 && rows != 32 && rows != 64)
+        return set_error(SWA_EINVAL, "strip rows must be 0, 16, 32 or 64");
     g->strip_rows = rows;
     return SWA_OK;
 }

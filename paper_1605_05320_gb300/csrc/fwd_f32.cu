@@ -6,8 +6,8 @@
 // bathymetry-balanced momentum flux is taken from eta directly, so decimetre
 // waves on 4000 m are resolved to float precision of eta, not of h.
 //
-// 2D grids run the persistent tile kernel of fwd_tiles.cuh over the grid's
-// tiles; 1D grids run a one-thread-per-cell kernel.  The CFL maximum is
+// 2D grids run the warp-strip kernel below (per edge the arithmetic of
+// fwd_tiles.cuh); 1D grids run a one-thread-per-cell kernel.  The CFL maximum is
 // reduced in float (max is exact); the last block to finish turns it into the
 // next time step in double.
 #include "fwd_tiles.cuh"
@@ -15,23 +15,87 @@
 namespace swadj {
 namespace f32 {
 
-// Tiles of one grid, row-major.
-struct GridTiles {
-    tile::View v;
-    int ntx, nty, TX, TY;
-    __device__ __forceinline__ int count() const { return ntx * nty; }
-    __device__ __forceinline__ void get(int k, tile::View &out, int &i0, int &j0) const {
-        out = v;
-        const int ty = k / ntx;
-        i0 = (k - ty * ntx) * TX;
-        j0 = ty * TY;
-    }
+// ------------------------------------------------------------ warp strips
+// 2D grids.  A warp owns a strip of 32 columns (lanes), the middle 28 its
+// output, and `rows` output rows, and walks them downwards.  Each loaded row
+// (the output rows and two halo rows above and below) is x-swept across the
+// warp with shuffles, lane l solving and limiting edge (l|l+1) once; the
+// y-sweep of the x-swept rows runs in registers over a sliding window of
+// rows, each y-edge solved and limited once.  Per edge the arithmetic is the
+// tile machinery's (solve1, net1), so results do not depend on the launch
+// shape.  No shared memory and no barriers except the CFL reduction.
+namespace strip {
+
+constexpr int kLanes = 32;
+constexpr int kOut = kLanes - 4;   // output columns per strip
+constexpr unsigned kFull = 0xffffffffu;
+
+struct XCell {   // derived cell data, as put_cell forms it
+    float h, mu, mv, u, v, sq, eta;
 };
 
-template <int TX, int TY>
-__global__ void __launch_bounds__(256) fwd_f32_tiles(FwdParams<float> p) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    tile::Smem<TX, TY> &S = *reinterpret_cast<tile::Smem<TX, TY> *>(dsm);
+__device__ __forceinline__ XCell derive(float eta, float h, float mu, float mv) {
+    const float q = rsqrtf(h);
+    const float ih = q * q;
+    XCell c;
+    c.h = h; c.mu = mu; c.mv = mv; c.u = mu * ih; c.v = mv * ih; c.sq = h * q; c.eta = eta;
+    return c;
+}
+
+__device__ __forceinline__ float dn(float x) { return __shfl_down_sync(kFull, x, 1); }
+__device__ __forceinline__ float up(float x) { return __shfl_up_sync(kFull, x, 1); }
+
+__device__ __forceinline__ tile::EdgeS edge_dn(const tile::EdgeS &w) {
+    tile::EdgeS r;
+    r.s1 = dn(w.s1); r.s3 = dn(w.s3); r.vh = dn(w.vh);
+    r.b1 = dn(w.b1); r.b2 = dn(w.b2); r.b3 = dn(w.b3);
+    return r;
+}
+__device__ __forceinline__ tile::EdgeS edge_up(const tile::EdgeS &w) {
+    tile::EdgeS r;
+    r.s1 = up(w.s1); r.s3 = up(w.s3); r.vh = up(w.vh);
+    r.b1 = up(w.b1); r.b2 = up(w.b2); r.b3 = up(w.b3);
+    return r;
+}
+
+// x-sweep of one row held across the warp; valid in lanes 2..29.
+__device__ __forceinline__ XCell xsweep(const XCell &c, float g, float nux, int order) {
+    const tile::EdgeS w = tile::solve1(g, c.h, c.mu, c.mv, c.u, c.v, c.sq, c.eta, dn(c.h),
+                                       dn(c.mu), dn(c.mv), dn(c.u), dn(c.v), dn(c.sq),
+                                       dn(c.eta));   // edge (l|l+1)
+    float4 lr;
+    float2 r;
+    tile::net_of(edge_up(w), w, edge_dn(w), nux, order, lr, r);
+    // left edge of the cell -> R of edge (l-1|l), right edge -> L of edge (l|l+1)
+    const float d0 = -nux * (up(lr.w) + lr.x);
+    const float d1 = -nux * (up(r.x) + lr.y);
+    const float d2 = -nux * (up(r.y) + lr.z);
+    return derive(c.eta + d0, c.h + d0, c.mu + d1, c.mv + d2);
+}
+
+// y-edge waves between x-swept cells a (below) and b (above), frame (h, hv, hu)
+__device__ __forceinline__ tile::EdgeS ysolve(const XCell &a, const XCell &b, float g) {
+    return tile::solve1(g, a.h, a.mv, a.mu, a.v, a.u, a.sq, a.eta, b.h, b.mv, b.mu, b.v, b.u,
+                        b.sq, b.eta);
+}
+
+struct Raw4 {
+    float eta, mu, mv, hb;
+};
+
+__device__ __forceinline__ Raw4 load_raw(const FwdParams<float> &p, int cur, int col, bool fx,
+                                         int row, bool fy) {
+    const size_t o = (size_t)row * p.nx + col;
+    Raw4 r;
+    r.eta = __ldg(p.q[cur][0] + o);
+    r.hb = __ldg(p.bath + o);
+    const float mu = __ldg(p.q[cur][1] + o), mv = __ldg(p.q[cur][2] + o);
+    r.mu = fx ? -mu : mu;
+    r.mv = fy ? -mv : mv;
+    return r;
+}
+
+__global__ void __launch_bounds__(256) fwd_f32_strips(FwdParams<float> p, int rows) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
     __shared__ float red[8];
@@ -41,20 +105,68 @@ __global__ void __launch_bounds__(256) fwd_f32_tiles(FwdParams<float> p) {
                           t_now, dt))
         return;
     const int cur = s_cur;
-    GridTiles src;
-    src.v.q0 = p.q[cur][0]; src.v.q1 = p.q[cur][1]; src.v.q2 = p.q[cur][2]; src.v.hb = p.bath;
-    src.v.o0 = p.q[cur ^ 1][0]; src.v.o1 = p.q[cur ^ 1][1]; src.v.o2 = p.q[cur ^ 1][2];
-    src.v.nx = p.nx; src.v.ny = p.ny; src.v.dx = p.dx; src.v.dy = p.dy; src.v.bc = p.bc;
-    src.ntx = (p.nx + TX - 1) / TX;
-    src.nty = (p.ny + TY - 1) / TY;
-    src.TX = TX;
-    src.TY = TY;
+    const float nux = s_nu[0], nuy = s_nu[1], g = p.g;
+    const float rdx = 1.f / p.dx, rdy = 1.f / p.dy;
+    const int lane = threadIdx.x & 31;
+    const int nsx = (p.nx + kOut - 1) / kOut, nsy = (p.ny + rows - 1) / rows;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    float smax = 0.f;
     bool bad = false;
-    const float sm = tile::run_tiles<TX, TY>(S, src, s_nu[0], s_nu[1], p.g, p.order, bad);
+    if (unit < nsx * nsy) {   // warp-uniform
+        const int sy = unit / nsx, sx = unit - sy * nsx;
+        const int x0 = sx * kOut, y0 = sy * rows;
+        const int ylast = (y0 + rows < p.ny ? y0 + rows : p.ny) - 1;
+        const int gi = x0 - 2 + lane;
+        bool fx, fy;
+        const int col = ghost_index(gi, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
+        const bool out = lane >= 2 && lane < kLanes - 2 && gi < p.nx;
+        float *const o0 = p.q[cur ^ 1][0], *const o1 = p.q[cur ^ 1][1], *const o2 = p.q[cur ^ 1][2];
+        XCell A = {}, B = {};           // x-swept rows j-2, j-1
+        tile::EdgeS W1 = {}, W2 = {};   // y-edges (j-3|j-2), (j-2|j-1)
+        float4 nlr = make_float4(0.f, 0.f, 0.f, 0.f);   // y-net of edge (j-3|j-2)
+        float2 nr = make_float2(0.f, 0.f);
+        // rows are loaded one iteration ahead of their use
+        int row = ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        Raw4 Rn = load_raw(p, cur, col, fx, row, fy);
+        for (int j = y0 - 2; j <= ylast + 2; j++) {
+            const Raw4 Rc = Rn;
+            if (j < ylast + 2) {
+                row = ghost_index(j + 1, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+                Rn = load_raw(p, cur, col, fx, row, fy);
+            }
+            const XCell C = xsweep(derive(Rc.eta, Rc.eta + Rc.hb, Rc.mu, Rc.mv), g, nux,
+                                   p.order);
+            tile::EdgeS Wn = W2;
+            if (j >= y0 - 1) Wn = ysolve(B, C, g);   // edge (j-1|j)
+            float4 lr = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 r = make_float2(0.f, 0.f);
+            if (j >= y0 + 1) tile::net_of(W1, W2, Wn, nuy, p.order, lr, r);   // edge (j-2|j-1)
+            if (j >= y0 + 2 && out) {
+                // y-sweep of row j-2: lower edge -> R of the previous net,
+                // upper edge -> L of this one; nets are in (h, hv, hu) order
+                const float d0 = -nuy * (nlr.w + lr.x);
+                const float d2 = -nuy * (nr.x + lr.y);
+                const float d1 = -nuy * (nr.y + lr.z);
+                const float ne = A.eta + d0, nmu = A.mu + d1, nmv = A.mv + d2;
+                const size_t o = (size_t)(j - 2) * p.nx + gi;
+                o0[o] = ne;
+                o1[o] = nmu;
+                o2[o] = nmv;
+                const float h = A.h + d0;
+                bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
+                smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
+            }
+            A = B; B = C;
+            W1 = W2; W2 = Wn;
+            nlr = lr; nr = r;
+        }
+    }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
-    tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,
+    tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last, t_now, dt,
                            cur);
 }
+
+}  // namespace strip
 
 // 1D grids: one thread per cell, solving the four edges it needs itself
 // (1D grids are small; the redundancy costs nothing that matters).
@@ -92,8 +204,10 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
             w[k] = tile::solve1(g, h[k], mu[k], 0.f, u[k], 0.f, sq[k], eta[k], h[k + 1],
                                 mu[k + 1], 0.f, u[k + 1], 0.f, sq[k + 1], eta[k + 1]);
         float L0[3], R0[3], L1[3], R1[3];
-        tile::net1<false>(w[0], w[1], w[2], nux, p.order, L0, R0);
-        tile::net1<false>(w[1], w[2], w[3], nux, p.order, L1, R1);
+        if (tile::sub1(w[1])) tile::net1<true>(w[0], w[1], w[2], nux, p.order, L0, R0);
+        else tile::net1<false>(w[0], w[1], w[2], nux, p.order, L0, R0);
+        if (tile::sub1(w[2])) tile::net1<true>(w[1], w[2], w[3], nux, p.order, L1, R1);
+        else tile::net1<false>(w[1], w[2], w[3], nux, p.order, L1, R1);
         const float d0 = -nux * (R0[0] + L1[0]);
         const float ne = eta[2] + d0;
         const float nmu = mu[2] - nux * (R0[1] + L1[1]);
@@ -110,45 +224,27 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
 
 }  // namespace f32
 
-constexpr int kTX = 32;
-
-// Tile height of the FP32 step: 16 rows by default, 8 on request (the
-// autotuner's choice); both give the same results.
-static int tile_rows(const FwdParams<float> &p) { return p.fwd_rows == 8 ? 8 : 16; }
-
-// Blocks of the persistent launch: every SM filled with as many blocks as
-// fit, never more than there are tiles.
-template <int TY>
-static int persistent_blocks(int ntiles) {
-    static int per_sm = 0, sms = 0;
-    if (per_sm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(f32::fwd_f32_tiles<kTX, TY>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(tile::Smem<kTX, TY>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, f32::fwd_f32_tiles<kTX, TY>, 256, sizeof(tile::Smem<kTX, TY>));
-        if (per_sm < 1) per_sm = 1;
-        if (sms < 1) sms = 1;
-    }
-    const int b = per_sm * sms;
-    return ntiles < b ? ntiles : b;
+// Strip height of the FP32 2D step: 32 rows by default, 16 or 64 on request
+// (the autotuner's choice); all give the same results.
+static int strip_rows(const FwdParams<float> &p) {
+    return (p.fwd_rows == 16 || p.fwd_rows == 64) ? p.fwd_rows : 32;
 }
 
-template <int TY>
-static int launch_tiles(FwdParams<float> p, cudaStream_t st) {
-    const int ntiles = ((p.nx + kTX - 1) / kTX) * ((p.ny + TY - 1) / TY);
-    p.nblocks = persistent_blocks<TY>(ntiles);
-    f32::fwd_f32_tiles<kTX, TY><<<p.nblocks, 256, sizeof(tile::Smem<kTX, TY>), st>>>(p);
-    return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_tiles");
+static int strip_blocks(int nx, int ny, int rows) {
+    const long long units = (long long)((nx + f32::strip::kOut - 1) / f32::strip::kOut) *
+                            ((ny + rows - 1) / rows);
+    return (int)((units + 7) / 8);
 }
 
 template <>
 int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
     FwdParams<float> p = p0;
-    if (p.two_d) return tile_rows(p) == 8 ? launch_tiles<8>(p, st) : launch_tiles<16>(p, st);
+    if (p.two_d) {
+        const int rows = strip_rows(p);
+        p.nblocks = strip_blocks(p.nx, p.ny, rows);
+        f32::strip::fwd_f32_strips<<<p.nblocks, 256, 0, st>>>(p, rows);
+        return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
+    }
     dim3 grid((p.nx + 255) / 256, 1);
     p.nblocks = (int)grid.x;
     f32::fwd_f32_1d<<<grid, 256, 0, st>>>(p);
@@ -157,11 +253,8 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
 
 template <>
 int fwd_step_blocks<float>(const FwdParams<float> &p) {
-    if (p.two_d) {
-        // at most one reduction slot per tile (the persistent grid is smaller)
-        const int TY = tile_rows(p);
-        return ((p.nx + kTX - 1) / kTX) * ((p.ny + TY - 1) / TY);
-    }
+    // one reduction slot per block of the launch shape p.fwd_rows selects
+    if (p.two_d) return strip_blocks(p.nx, p.ny, strip_rows(p));
     return (p.nx + 255) / 256;
 }
 

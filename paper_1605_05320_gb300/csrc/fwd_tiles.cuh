@@ -73,8 +73,10 @@ __device__ __forceinline__ EdgeS solve1(float g, float hL, float mnL, float mtL,
 }
 
 // Net fluxes of edge w (neighbours wl, wr): L into the left cell, R into the
-// right cell (Q -= nu * net).  SUB: every edge of the warp is subsonic
-// (s1 < 0 < s3), so the sign logic of waves 1 and 3 is fixed; same numbers.
+// right cell (Q -= nu * net).  SUB: the edge is subsonic (s1 < 0 < s3), so
+// the sign logic of waves 1 and 3 is fixed.  The two forms round
+// differently, so callers pick SUB exactly when sub1(w) holds: the result of
+// an edge then depends on that edge alone, not on its warp.
 template <bool SUB>
 __device__ __forceinline__ void net1(const EdgeS &wl, const EdgeS &w, const EdgeS &wr, float nu,
                                      int order, float L[3], float R[3]) {
@@ -202,7 +204,7 @@ __device__ __forceinline__ EdgeS edge_of(const float4 &p, const float2 &q) {
 __device__ __forceinline__ void net_of(const EdgeS &a, const EdgeS &b, const EdgeS &c, float nu,
                                        int order, float4 &lr, float2 &r) {
     float L[3], Rr[3];
-    if (__all_sync(__activemask(), sub1(b))) net1<true>(a, b, c, nu, order, L, Rr);
+    if (sub1(b)) net1<true>(a, b, c, nu, order, L, Rr);
     else net1<false>(a, b, c, nu, order, L, Rr);
     lr = make_float4(L[0], L[1], L[2], Rr[0]);
     r = make_float2(Rr[1], Rr[2]);

@@ -1,6 +1,8 @@
-"""Autotuner for the FP32 tile height (8 or 16 rows) of the step kernels.
+"""Autotuner for the FP32 launch shapes of the step kernels: the strip height
+of a grid's step (16, 32 or 64 rows) and the tile height of a patch level's
+step (8 or 16 rows).
 
-The tile height changes only throughput, never results.  The tuner times
+The launch shape changes only throughput, never results.  The tuner times
 each candidate with CUDA events on a few steps and keeps the faster one,
 caching the choice per shape signature (grid size, or the histogram of patch
 sizes of a level) for the life of the process.
@@ -12,7 +14,8 @@ from __future__ import annotations
 
 from . import swadj as S
 
-CANDIDATES = (16, 8)
+CANDIDATES = (16, 8)          # patch tile heights
+GRID_CANDIDATES = (32, 16, 64)  # grid strip heights
 _cache: dict = {}
 
 
@@ -30,11 +33,11 @@ def _time(fn, steps):
 
 
 def tune_grid(grid: "S.Grid", steps: int = 10) -> int:
-    """Pick the tile height for a FP32 grid; returns it and applies it."""
+    """Pick the strip height for a FP32 grid; returns it and applies it."""
     key = ("grid", grid.desc.nx, grid.desc.ny)
     if key not in _cache:
         best, best_t = None, None
-        for rows in CANDIDATES:
+        for rows in GRID_CANDIDATES:
             S.swa_grid_set_strip_rows(grid.h, rows)
             t = _time(lambda n: grid.step(n, 1e300), steps)
             if best_t is None or t < best_t:

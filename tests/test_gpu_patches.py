@@ -93,6 +93,54 @@ def test_single_patch_is_bit_identical_to_grid(S):
     assert ps.time(1)[0] == g.time()[0]
 
 
+def test_single_patch_matches_grid_with_supersonic_band(S):
+    """Shallow (10 m) water with a band flowing at 1.5 c among subsonic cells:
+    warps mix subsonic and supersonic edges differently in the grid's strips
+    and the patch's tiles; each edge's arithmetic must not depend on that."""
+    nx, ny = 150, 97
+    p = (1, 0.0, 0.0, nx, ny, 1000.0, 1000.0)
+    rng = np.random.default_rng(17)
+    B = np.full(nx * ny, -10.0)
+    eta = 0.2 * rng.standard_normal(nx * ny)
+    hu = 2.0 * rng.standard_normal(nx * ny)
+    hv = 2.0 * rng.standard_normal(nx * ny)
+    band = (np.arange(nx * ny) % nx >= 40) & (np.arange(nx * ny) % nx < 75)
+    hu[band] += 1.5 * 10.0 * np.sqrt(9.81 * 10.0)
+    common = S.make_desc(2, 2, 2, 0, 0, 1, 1, precision=S.SWA_FP32)
+    ps = S.PatchSet([p], [B], common)
+    ps.set_state(0, eta, hu, hv)
+    ps.start(1)
+    ps.step(1, 20)
+    d = S.make_desc(2, nx, ny, 0.0, 0.0, 1000.0, 1000.0, precision=S.SWA_FP32)
+    g = S.Grid(d, B)
+    g.set_state(eta, hu, hv, 0.0)
+    g.step(20, 1e300)
+    assert S.swa_sync_status() == 0
+    a, b = ps.get_state(0), g.get_state()
+    for f in ("eta", "hu", "hv"):
+        assert np.array_equal(a[f], b[f]), f
+    assert ps.time(1)[0] == g.time()[0]
+
+
+def test_grid_strip_height_does_not_change_results(S):
+    """Strip heights 16, 32 and 64 on a ragged grid with walls and momenta."""
+    sc = synth.small_2d(97, 45, seed=21)
+    res = []
+    for rows in (16, 32, 64):
+        d = S.make_desc(2, 97, 45, 0.0, 0.0, sc.grid.dx, sc.grid.dy, precision=S.SWA_FP32,
+                        bc=(1, 0, 1, 0))
+        g = S.Grid(d, sc.B)
+        S.swa_grid_set_strip_rows(g.h, rows)
+        g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+        g.step(40, 1e300)
+        res.append((g.get_state(), g.time()))
+    assert S.swa_sync_status() == 0
+    for st, t in res[1:]:
+        for f in ("eta", "hu", "hv"):
+            assert np.array_equal(st[f], res[0][0][f]), f
+        assert t == res[0][1]
+
+
 def test_tile_height_does_not_change_results(S):
     patches = make_patches(seed=5)
     fields = [synth.patch_fields(p, src=(600e3, 950e3), amp=0.5, width=60e3) for p in patches]
