@@ -16,14 +16,19 @@ namespace swadj {
 namespace adjt {
 
 __device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
+// Rounded single operations that the compiler never fuses (with explicit
+// fmaf the rounding of every expression is fixed in the source).
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 
 // phi(theta) b for the MC limiter, r = theta b
 __device__ __forceinline__ float mc1(float b, float r) {
     const float sg = b < 0.f ? -1.f : 1.f;
-    const float B = fabsf(b), Rr = sg * r;
-    float m = fminf(0.5f * (B + Rr), 2.f * B);
-    m = fminf(m, 2.f * Rr);
-    return sg * fmaxf(m, 0.f);
+    const float B = fabsf(b), Rr = mul(sg, r);
+    float m = fminf(mul(0.5f, add(B, Rr)), mul(2.f, B));
+    m = fminf(m, mul(2.f, Rr));
+    return mul(sg, fmaxf(m, 0.f));
 }
 
 struct EdgeA {   // waves of one edge: strengths and the (substituted) speeds
@@ -42,11 +47,11 @@ __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR,
     if (dL) { eL = eR; mL = -mR; cL = cR; }
     if (dR) { eR = eL; mR = -mL; cR = cL; }
     // flux jump of F = -(g hbar m, eta), g hbar = c^2
-    const float d1 = cL * cL * mL - cR * cR * mR;
-    const float d2 = eL - eR;
-    const float rs = rcpf(cL + cR);
-    w.b1 = (d1 + cR * d2) * rs;
-    w.b2 = (cL * d2 - d1) * rs;
+    const float d1 = fmaf(mul(cL, cL), mL, -mul(mul(cR, cR), mR));
+    const float d2 = sub(eL, eR);
+    const float rs = rcpf(add(cL, cR));
+    w.b1 = mul(fmaf(cR, d2, d1), rs);
+    w.b2 = mul(fmaf(cL, d2, -d1), rs);
     w.cl = cL;
     w.cr = cR;
     return w;
@@ -61,14 +66,15 @@ __device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const E
     if (order >= 2 && !w.wall) {
         // wave 1 (speed -cl) is upwinded from the right edge, wave 2 (+cr)
         // from the left edge
-        const float r1 = wr.b1 * fmaf(wr.cl, w.cl, 1.f) * rcpf(fmaf(w.cl, w.cl, 1.f));
-        const float r2 = wl.b2 * fmaf(wl.cr, w.cr, 1.f) * rcpf(fmaf(w.cr, w.cr, 1.f));
-        const float k1 = -0.5f * fmaf(-nu, w.cl, 1.f) * mc1(w.b1, r1);
-        const float k2 = 0.5f * fmaf(-nu, w.cr, 1.f) * mc1(w.b2, r2);
-        F0 = k1 * w.cl - k2 * w.cr;
-        F1 = k1 + k2;
+        const float r1 = mul(mul(wr.b1, fmaf(wr.cl, w.cl, 1.f)), rcpf(fmaf(w.cl, w.cl, 1.f)));
+        const float r2 = mul(mul(wl.b2, fmaf(wl.cr, w.cr, 1.f)), rcpf(fmaf(w.cr, w.cr, 1.f)));
+        const float k1 = mul(mul(-0.5f, fmaf(-nu, w.cl, 1.f)), mc1(w.b1, r1));
+        const float k2 = mul(mul(0.5f, fmaf(-nu, w.cr, 1.f)), mc1(w.b2, r2));
+        F0 = fmaf(k1, w.cl, -mul(k2, w.cr));
+        F1 = add(k1, k2);
     }
-    return make_float4(w.b1 * w.cl + F0, w.b1 + F1, -(w.b2 * w.cr) - F0, w.b2 - F1);
+    return make_float4(fmaf(w.b1, w.cl, F0), add(w.b1, F1), sub(-mul(w.b2, w.cr), F0),
+                       sub(w.b2, F1));
 }
 
 // ---------------------------------------------------------------- strips
@@ -138,8 +144,8 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
             float e = A.e, g = A.g;
             const float m = A.m, c = A.c;
             if (c > 0.f) {
-                e += -nuy * (rp0 + nn.x);
-                g += -nuy * (rp1 + nn.y);
+                e = add(e, mul(-nuy, add(rp0, nn.x)));
+                g = add(g, mul(-nuy, add(rp1, nn.y)));
             }
             // x-sweep of row r: lane l solves edge (l|l+1)
             const float eR = __shfl_down_sync(kFull, e, 1);
@@ -156,8 +162,8 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
             const float xr1 = __shfl_up_sync(kFull, xn.w, 1);
             float ne = e, nm = m;
             if (c > 0.f) {
-                ne += -nux * (xr0 + xn.x);
-                nm += -nux * (xr1 + xn.y);
+                ne = add(ne, mul(-nux, add(xr0, xn.x)));
+                nm = add(nm, mul(-nux, add(xr1, xn.y)));
             }
             if (out) {
                 const size_t o = (size_t)(j - 2) * p.nx + gi;

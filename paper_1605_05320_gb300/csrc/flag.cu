@@ -285,10 +285,11 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
                     const float4 b = __ldcs(s0 + (size_t)k * ks + cs);
                     const float4 c = __ldcs(s0 + (size_t)k * ks + 2 * cs);
                     float4 d;
-                    d.x = a.x * e.x + b.x * u.x + c.x * v.x;
-                    d.y = a.y * e.y + b.y * u.y + c.y * v.y;
-                    d.z = a.z * e.z + b.z * u.z + c.z * v.z;
-                    d.w = a.w * e.w + b.w * u.w + c.w * v.w;
+                    // rounding fixed in the source, identical in both variants
+                    d.x = fmaf(c.x, v.x, fmaf(b.x, u.x, __fmul_rn(a.x, e.x)));
+                    d.y = fmaf(c.y, v.y, fmaf(b.y, u.y, __fmul_rn(a.y, e.y)));
+                    d.z = fmaf(c.z, v.z, fmaf(b.z, u.z, __fmul_rn(a.z, e.z)));
+                    d.w = fmaf(c.w, v.w, fmaf(b.w, u.w, __fmul_rn(a.w, e.w)));
                     if (k >= w.ki0 && k <= w.ki1) {
                         m.x = fmaxf(m.x, fabsf(d.x)); m.y = fmaxf(m.y, fabsf(d.y));
                         m.z = fmaxf(m.z, fabsf(d.z)); m.w = fmaxf(m.w, fabsf(d.w));
@@ -304,8 +305,8 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
                 const float bh = 1.f - ah, bl = 1.f - al;
 #define SWADJ_ENDS(c)                                                          \
     {                                                                          \
-        const float vh = w.exact_h ? dh0.c : ah * dh0.c + bh * dh1.c;          \
-        const float vl = w.exact_l ? dl0.c : al * dl0.c + bl * dl1.c;          \
+        const float vh = w.exact_h ? dh0.c : fmaf(ah, dh0.c, __fmul_rn(bh, dh1.c)); \
+        const float vl = w.exact_l ? dl0.c : fmaf(al, dl0.c, __fmul_rn(bl, dl1.c)); \
         m.c = fmaxf(m.c, fmaxf(fabsf(vh), fabsf(vl)));                         \
     }
                 SWADJ_ENDS(x) SWADJ_ENDS(y) SWADJ_ENDS(z) SWADJ_ENDS(w)

@@ -36,9 +36,11 @@ struct XCell {   // derived cell data, as put_cell forms it
 
 __device__ __forceinline__ XCell derive(float eta, float h, float mu, float mv) {
     const float q = rsqrtf(h);
-    const float ih = q * q;
+    const float ih = tile::mul(q, q);
     XCell c;
-    c.h = h; c.mu = mu; c.mv = mv; c.u = mu * ih; c.v = mv * ih; c.sq = h * q; c.eta = eta;
+    c.h = h; c.mu = mu; c.mv = mv;
+    c.u = tile::mul(mu, ih); c.v = tile::mul(mv, ih); c.sq = tile::mul(h, q);
+    c.eta = eta;
     return c;
 }
 
@@ -67,10 +69,11 @@ __device__ __forceinline__ XCell xsweep(const XCell &c, float g, float nux, int 
     float2 r;
     tile::net_of(edge_up(w), w, edge_dn(w), nux, order, lr, r);
     // left edge of the cell -> R of edge (l-1|l), right edge -> L of edge (l|l+1)
-    const float d0 = -nux * (up(lr.w) + lr.x);
-    const float d1 = -nux * (up(r.x) + lr.y);
-    const float d2 = -nux * (up(r.y) + lr.z);
-    return derive(c.eta + d0, c.h + d0, c.mu + d1, c.mv + d2);
+    const float d0 = tile::mul(-nux, tile::add(up(lr.w), lr.x));
+    const float d1 = tile::mul(-nux, tile::add(up(r.x), lr.y));
+    const float d2 = tile::mul(-nux, tile::add(up(r.y), lr.z));
+    return derive(tile::add(c.eta, d0), tile::add(c.h, d0), tile::add(c.mu, d1),
+                  tile::add(c.mv, d2));
 }
 
 // y-edge waves between x-swept cells a (below) and b (above), frame (h, hv, hu)
@@ -95,10 +98,12 @@ __device__ __forceinline__ Raw4 load_raw(const FwdParams<float> &p, int cur, int
     return r;
 }
 
-__global__ void __launch_bounds__(256) fwd_f32_strips(FwdParams<float> p, int rows) {
+constexpr int kStripThreads = 128;   // 4 warps: at ~90 registers, 5 blocks per SM
+
+__global__ void __launch_bounds__(kStripThreads) fwd_f32_strips(FwdParams<float> p, int rows) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
-    __shared__ float red[8];
+    __shared__ float red[kStripThreads / 32];
     __shared__ int am_last;
     double t_now = 0.0, dt = 0.0;
     if (!tile::begin_step(p.clk, p.t_end, (double)p.dx, (double)p.dy, s_nu, &s_cur, &s_run,
@@ -144,15 +149,16 @@ __global__ void __launch_bounds__(256) fwd_f32_strips(FwdParams<float> p, int ro
             if (j >= y0 + 2 && out) {
                 // y-sweep of row j-2: lower edge -> R of the previous net,
                 // upper edge -> L of this one; nets are in (h, hv, hu) order
-                const float d0 = -nuy * (nlr.w + lr.x);
-                const float d2 = -nuy * (nr.x + lr.y);
-                const float d1 = -nuy * (nr.y + lr.z);
-                const float ne = A.eta + d0, nmu = A.mu + d1, nmv = A.mv + d2;
+                const float d0 = tile::mul(-nuy, tile::add(nlr.w, lr.x));
+                const float d2 = tile::mul(-nuy, tile::add(nr.x, lr.y));
+                const float d1 = tile::mul(-nuy, tile::add(nr.y, lr.z));
+                const float ne = tile::add(A.eta, d0), nmu = tile::add(A.mu, d1);
+                const float nmv = tile::add(A.mv, d2);
                 const size_t o = (size_t)(j - 2) * p.nx + gi;
                 o0[o] = ne;
                 o1[o] = nmu;
                 o2[o] = nmv;
-                const float h = A.h + d0;
+                const float h = tile::add(A.h, d0);
                 bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
                 smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
             }
@@ -162,8 +168,8 @@ __global__ void __launch_bounds__(256) fwd_f32_strips(FwdParams<float> p, int ro
         }
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
-    tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last, t_now, dt,
-                           cur);
+    tile::finish_step<kStripThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,
+                                     t_now, dt, cur);
 }
 
 }  // namespace strip
@@ -195,8 +201,8 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
             mu[k] = fx ? -q1[c] : q1[c];
             h[k] = eta[k] + p.bath[c];
             const float q = rsqrtf(h[k]);
-            sq[k] = h[k] * q;
-            u[k] = mu[k] * q * q;
+            sq[k] = tile::mul(h[k], q);
+            u[k] = tile::mul(mu[k], tile::mul(q, q));
         }
         tile::EdgeS w[4];
 #pragma unroll
@@ -208,12 +214,12 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
         else tile::net1<false>(w[0], w[1], w[2], nux, p.order, L0, R0);
         if (tile::sub1(w[2])) tile::net1<true>(w[1], w[2], w[3], nux, p.order, L1, R1);
         else tile::net1<false>(w[1], w[2], w[3], nux, p.order, L1, R1);
-        const float d0 = -nux * (R0[0] + L1[0]);
-        const float ne = eta[2] + d0;
-        const float nmu = mu[2] - nux * (R0[1] + L1[1]);
+        const float d0 = tile::mul(-nux, tile::add(R0[0], L1[0]));
+        const float ne = tile::add(eta[2], d0);
+        const float nmu = tile::add(mu[2], tile::mul(-nux, tile::add(R0[1], L1[1])));
         p.q[cur ^ 1][0][i] = ne;
         p.q[cur ^ 1][1][i] = nmu;
-        const float hn = h[2] + d0;
+        const float hn = tile::add(h[2], d0);
         bad = !(hn > 0.f) || !isfinite(nmu);
         sm = cfl_f32(hn, nmu, 0.f, g, 1.f / p.dx, 1.f / p.dy, 0);
     }
@@ -233,7 +239,8 @@ static int strip_rows(const FwdParams<float> &p) {
 static int strip_blocks(int nx, int ny, int rows) {
     const long long units = (long long)((nx + f32::strip::kOut - 1) / f32::strip::kOut) *
                             ((ny + rows - 1) / rows);
-    return (int)((units + 7) / 8);
+    constexpr int wpb = f32::strip::kStripThreads / 32;
+    return (int)((units + wpb - 1) / wpb);
 }
 
 template <>
@@ -242,7 +249,7 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
     if (p.two_d) {
         const int rows = strip_rows(p);
         p.nblocks = strip_blocks(p.nx, p.ny, rows);
-        f32::strip::fwd_f32_strips<<<p.nblocks, 256, 0, st>>>(p, rows);
+        f32::strip::fwd_f32_strips<<<p.nblocks, f32::strip::kStripThreads, 0, st>>>(p, rows);
         return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
     }
     dim3 grid((p.nx + 255) / 256, 1);

@@ -46,10 +46,11 @@ __device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
 // sweep of the split step is limited by its own Courant number).
 __device__ __forceinline__ float cfl_f32(float h, float hu, float hv, float g, float rdx,
                                          float rdy, int two_d) {
-    const float q = rsqrtf(h), ih = q * q;
-    const float gh = g * h, cc = gh * rsqrtf(gh);
-    float s = (fabsf(hu) * ih + cc) * rdx;
-    if (two_d) s = fmaxf(s, (fabsf(hv) * ih + cc) * rdy);
+    // rounding fixed in the source (no compiler fusion), as in the step
+    const float q = rsqrtf(h), ih = __fmul_rn(q, q);
+    const float gh = __fmul_rn(g, h), cc = __fmul_rn(gh, rsqrtf(gh));
+    float s = __fmul_rn(fmaf(fabsf(hu), ih, cc), rdx);
+    if (two_d) s = fmaxf(s, __fmul_rn(fmaf(fabsf(hv), ih, cc), rdy));
     return s;
 }
 

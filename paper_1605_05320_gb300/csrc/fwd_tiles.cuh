@@ -29,6 +29,12 @@ namespace tile {
 constexpr int NT = 256;  // threads per block
 
 __device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
+// Rounded single operations that the compiler never fuses: with these and
+// explicit fmaf the rounding of every expression below is fixed in the
+// source, so an edge's numbers do not depend on the kernel that inlines it.
+__device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
 // 1 if s > 0, 0 if s < 0, 1/2 if s == 0 (an f-wave of speed 0 is split)
 __device__ __forceinline__ float pos1(float s) { return s > 0.f ? 1.f : (s < 0.f ? 0.f : 0.5f); }
 // sign(s) / 2
@@ -36,10 +42,10 @@ __device__ __forceinline__ float hsg1(float s) { return s > 0.f ? 0.5f : (s < 0.
 // phi(theta) b for the MC limiter, r = theta b
 __device__ __forceinline__ float mc1(float b, float r) {
     const float sg = b < 0.f ? -1.f : 1.f;
-    const float B = fabsf(b), Rr = sg * r;
-    float m = fminf(0.5f * (B + Rr), 2.f * B);
-    m = fminf(m, 2.f * Rr);
-    return sg * fmaxf(m, 0.f);
+    const float B = fabsf(b), Rr = mul(sg, r);
+    float m = fminf(mul(0.5f, add(B, Rr)), mul(2.f, B));
+    m = fminf(m, mul(2.f, Rr));
+    return mul(sg, fmaxf(m, 0.f));
 }
 
 struct EdgeS {           // wave data of one edge
@@ -51,24 +57,24 @@ __device__ __forceinline__ EdgeS solve1(float g, float hL, float mnL, float mtL,
                                         float utL, float sqL, float etaL, float hR, float mnR,
                                         float mtR, float unR, float utR, float sqR, float etaR) {
     EdgeS w;
-    const float hh = 0.5f * (hL + hR);
-    const float rd = rcpf(sqL + sqR);
-    const float uh = (sqL * unL + sqR * unR) * rd;
-    const float vh = (sqL * utL + sqR * utR) * rd;
-    const float gh = g * hh;
+    const float hh = mul(0.5f, add(hL, hR));
+    const float rd = rcpf(add(sqL, sqR));
+    const float uh = mul(fmaf(sqL, unL, mul(sqR, unR)), rd);
+    const float vh = mul(fmaf(sqL, utL, mul(sqR, utR)), rd);
+    const float gh = mul(g, hh);
     const float rc = rsqrtf(gh);
-    const float ch = gh * rc;
-    const float s1 = uh - ch, s3 = uh + ch;
-    const float df1 = mnR - mnL;
-    const float df2 = (mnR * unR - mnL * unL) + gh * (etaR - etaL);
-    const float df3 = mnR * utR - mnL * utL;
-    const float hr = 0.5f * rc;  // 1 / (s3 - s1)
+    const float ch = mul(gh, rc);
+    const float s1 = sub(uh, ch), s3 = add(uh, ch);
+    const float df1 = sub(mnR, mnL);
+    const float df2 = fmaf(gh, sub(etaR, etaL), fmaf(mnR, unR, -mul(mnL, unL)));
+    const float df3 = fmaf(mnR, utR, -mul(mnL, utL));
+    const float hr = mul(0.5f, rc);  // 1 / (s3 - s1)
     w.s1 = s1;
     w.s3 = s3;
     w.vh = vh;
-    w.b1 = (s3 * df1 - df2) * hr;
-    w.b3 = (df2 - s1 * df1) * hr;
-    w.b2 = df3 - vh * df1;
+    w.b1 = mul(fmaf(s3, df1, -df2), hr);
+    w.b3 = mul(fmaf(-s1, df1, df2), hr);
+    w.b2 = fmaf(-vh, df1, df3);
     return w;
 }
 
@@ -80,19 +86,19 @@ __device__ __forceinline__ EdgeS solve1(float g, float hL, float mnL, float mtL,
 template <bool SUB>
 __device__ __forceinline__ void net1(const EdgeS &wl, const EdgeS &w, const EdgeS &wr, float nu,
                                      int order, float L[3], float R[3]) {
-    const float s2 = 0.5f * (w.s1 + w.s3);
+    const float s2 = mul(0.5f, add(w.s1, w.s3));
     const float p2 = pos1(s2);
     float ap0, ap1, ap2, am0, am1, am2;
     if (SUB) {
-        ap0 = w.b3; ap1 = w.b3 * w.s3; ap2 = w.b3 * w.vh + p2 * w.b2;
-        am0 = w.b1; am1 = w.b1 * w.s1; am2 = w.b1 * w.vh + (w.b2 - p2 * w.b2);
+        ap0 = w.b3; ap1 = mul(w.b3, w.s3); ap2 = fmaf(p2, w.b2, mul(w.b3, w.vh));
+        am0 = w.b1; am1 = mul(w.b1, w.s1); am2 = add(mul(w.b1, w.vh), fmaf(-p2, w.b2, w.b2));
     } else {
-        const float a1 = pos1(w.s1) * w.b1, a3 = pos1(w.s3) * w.b3;
-        ap0 = a1 + a3; ap1 = a1 * w.s1 + a3 * w.s3; ap2 = (a1 + a3) * w.vh + p2 * w.b2;
-        const float t0 = w.b1 + w.b3;
-        am0 = t0 - ap0;
-        am1 = (w.b1 * w.s1 + w.b3 * w.s3) - ap1;
-        am2 = (t0 * w.vh + w.b2) - ap2;
+        const float a1 = mul(pos1(w.s1), w.b1), a3 = mul(pos1(w.s3), w.b3);
+        ap0 = add(a1, a3); ap1 = fmaf(a1, w.s1, mul(a3, w.s3)); ap2 = fmaf(p2, w.b2, mul(ap0, w.vh));
+        const float t0 = add(w.b1, w.b3);
+        am0 = sub(t0, ap0);
+        am1 = sub(fmaf(w.b1, w.s1, mul(w.b3, w.s3)), ap1);
+        am2 = sub(fmaf(t0, w.vh, w.b2), ap2);
     }
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
     if (order >= 2) {
@@ -100,26 +106,26 @@ __device__ __forceinline__ void net1(const EdgeS &wl, const EdgeS &w, const Edge
         const EdgeS &u3 = (SUB || w.s3 > 0.f) ? wl : wr;
         const float m1 = fmaf(w.s1, w.s1, fmaf(w.vh, w.vh, 1.f));
         const float d1 = fmaf(u1.s1, w.s1, fmaf(u1.vh, w.vh, 1.f));
-        const float l1 = mc1(w.b1, u1.b1 * d1 * rcpf(m1));
+        const float l1 = mc1(w.b1, mul(mul(u1.b1, d1), rcpf(m1)));
         const float m3 = fmaf(w.s3, w.s3, fmaf(w.vh, w.vh, 1.f));
         const float d3 = fmaf(u3.s3, w.s3, fmaf(u3.vh, w.vh, 1.f));
-        const float l3 = mc1(w.b3, u3.b3 * d3 * rcpf(m3));
+        const float l3 = mc1(w.b3, mul(mul(u3.b3, d3), rcpf(m3)));
         const float l2 = mc1(w.b2, s2 > 0.f ? wl.b2 : wr.b2);
         float c1, c3;
         if (SUB) {
-            c1 = -0.5f * fmaf(nu, w.s1, 1.f) * l1;
-            c3 = 0.5f * fmaf(-nu, w.s3, 1.f) * l3;
+            c1 = mul(mul(-0.5f, fmaf(nu, w.s1, 1.f)), l1);
+            c3 = mul(mul(0.5f, fmaf(-nu, w.s3, 1.f)), l3);
         } else {
-            c1 = hsg1(w.s1) * fmaf(-nu, fabsf(w.s1), 1.f) * l1;
-            c3 = hsg1(w.s3) * fmaf(-nu, fabsf(w.s3), 1.f) * l3;
+            c1 = mul(mul(hsg1(w.s1), fmaf(-nu, fabsf(w.s1), 1.f)), l1);
+            c3 = mul(mul(hsg1(w.s3), fmaf(-nu, fabsf(w.s3), 1.f)), l3);
         }
-        const float c2 = hsg1(s2) * fmaf(-nu, fabsf(s2), 1.f) * l2;
-        F0 = c1 + c3;
-        F1 = c1 * w.s1 + c3 * w.s3;
-        F2 = F0 * w.vh + c2;
+        const float c2 = mul(mul(hsg1(s2), fmaf(-nu, fabsf(s2), 1.f)), l2);
+        F0 = add(c1, c3);
+        F1 = fmaf(c1, w.s1, mul(c3, w.s3));
+        F2 = fmaf(F0, w.vh, c2);
     }
-    L[0] = am0 + F0; L[1] = am1 + F1; L[2] = am2 + F2;
-    R[0] = ap0 - F0; R[1] = ap1 - F1; R[2] = ap2 - F2;
+    L[0] = add(am0, F0); L[1] = add(am1, F1); L[2] = add(am2, F2);
+    R[0] = sub(ap0, F0); R[1] = sub(ap1, F1); R[2] = sub(ap2, F2);
 }
 
 __device__ __forceinline__ bool sub1(const EdgeS &w) { return w.s1 < 0.f && w.s3 > 0.f; }
@@ -188,9 +194,9 @@ template <typename SM>
 __device__ __forceinline__ void put_cell(SM &S, int ry, int rx, float eta, float h, float mu,
                                          float mv) {
     const float q = rsqrtf(h);
-    const float ih = q * q;
+    const float ih = mul(q, q);
     S.a[ry][rx] = make_float4(h, mu, mv, eta);
-    S.b[ry][rx] = make_float4(mu * ih, mv * ih, h * q, 0.f);
+    S.b[ry][rx] = make_float4(mul(mu, ih), mul(mv, ih), mul(h, q), 0.f);
 }
 
 __device__ __forceinline__ EdgeS edge_of(const float4 &p, const float2 &q) {
@@ -254,10 +260,10 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
         const float2 lr = S.n.x.r[ry][col];
         const float4 re = S.n.x.lr[ry][col + 1];
         const float4 c = S.a[ry][rx];
-        const float d0 = -nux * (le.w + re.x);
-        const float d1 = -nux * (lr.x + re.y);
-        const float d2 = -nux * (lr.y + re.z);
-        put_cell(S, ry, rx, c.w + d0, c.x + d0, c.y + d1, c.z + d2);
+        const float d0 = mul(-nux, add(le.w, re.x));
+        const float d1 = mul(-nux, add(lr.x, re.y));
+        const float d2 = mul(-nux, add(lr.y, re.z));
+        put_cell(S, ry, rx, add(c.w, d0), add(c.x, d0), add(c.y, d1), add(c.z, d2));
     }
     __syncthreads();
     // phase 4: y-edge waves of the x-swept state, tile columns (frame (h, hv, hu))
@@ -294,15 +300,15 @@ __device__ __forceinline__ float tile_compute(Smem<TX, TY> &S, const View &V, in
             const float2 lr = S.n.y.r[row][col];
             const float4 up = S.n.y.lr[row + 1][col];
             const float4 cc = S.a[ry][rx];
-            const float d0 = -nuy * (lo.w + up.x);
-            const float d2 = -nuy * (lr.x + up.y);
-            const float d1 = -nuy * (lr.y + up.z);
-            const float ne = cc.w + d0, nmu = cc.y + d1, nmv = cc.z + d2;
+            const float d0 = mul(-nuy, add(lo.w, up.x));
+            const float d2 = mul(-nuy, add(lr.x, up.y));
+            const float d1 = mul(-nuy, add(lr.y, up.z));
+            const float ne = add(cc.w, d0), nmu = add(cc.y, d1), nmv = add(cc.z, d2);
             const size_t o = (size_t)gj * V.nx + gi;
             V.o0[o] = ne;
             V.o1[o] = nmu;
             V.o2[o] = nmv;
-            const float h = cc.x + d0;
+            const float h = add(cc.x, d0);
             bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
             smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, rdx, rdy, 1));
         }

@@ -5,8 +5,8 @@ basin (1 km cells) through the public binding, with far less device memory
 than the full scenario (no 101-snapshot store), so that a capture that saves
 and restores device memory between passes stays small:
 
-  fwd   FP32 forward steps (fwd_f32_tiles), ~120 MB on the device
-  adj   the full FP32 adjoint run (adj_f32_tiles, ~2000 launches) with a
+  fwd   FP32 forward steps (fwd_f32_strips), ~120 MB on the device
+  adj   the full FP32 adjoint run (adj_f32_strips, ~2000 launches) with a
         fused snapshot every 100 steps, ~1.3 GB
   flag  FP32 adjoint-weighted flag passes without the m output (the
         envelope-pruned flag_kernel_f32x4) against a store of one snapshot
