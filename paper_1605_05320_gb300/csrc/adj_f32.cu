@@ -15,7 +15,7 @@
 namespace swadj {
 namespace adjt {
 
-__device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcpf(float x) { return rcp_ftz(x); }
 // Rounded single operations that the compiler never fuses (with explicit
 // fmaf the rounding of every expression is fixed in the source).
 __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
@@ -98,11 +98,11 @@ __device__ __forceinline__ CellA load_cell(const AdjParams<float> &p, int col, b
                                            bool fy) {
     const size_t o = (size_t)row * p.nx + col;
     CellA q;
-    q.e = __ldg(p.src[0] + o);
-    const float mu = __ldg(p.src[1] + o), ga = __ldg(p.src[2] + o);
+    q.e = ld_early(p.src[0] + o);
+    const float mu = ld_early(p.src[1] + o), ga = ld_early(p.src[2] + o);
     q.m = fx ? -mu : mu;
     q.g = fy ? -ga : ga;
-    q.c = __ldg(p.c + o);
+    q.c = ld_early(p.c + o);
     return q;
 }
 
@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     bool fy;
     int row = ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
     CellA Cn = load_cell(p, col, fx, row, fy);
+#pragma unroll 3
     for (int j = y0 - 2; j <= ylast + 2; j++) {
         const CellA C = Cn;
         if (j < ylast + 2) {

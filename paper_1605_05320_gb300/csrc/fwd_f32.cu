@@ -35,7 +35,7 @@ struct XCell {   // derived cell data, as put_cell forms it
 };
 
 __device__ __forceinline__ XCell derive(float eta, float h, float mu, float mv) {
-    const float q = rsqrtf(h);
+    const float q = rsqrt_ftz(h);
     const float ih = tile::mul(q, q);
     XCell c;
     c.h = h; c.mu = mu; c.mv = mv;
@@ -90,9 +90,9 @@ __device__ __forceinline__ Raw4 load_raw(const FwdParams<float> &p, int cur, int
                                          int row, bool fy) {
     const size_t o = (size_t)row * p.nx + col;
     Raw4 r;
-    r.eta = __ldg(p.q[cur][0] + o);
-    r.hb = __ldg(p.bath + o);
-    const float mu = __ldg(p.q[cur][1] + o), mv = __ldg(p.q[cur][2] + o);
+    r.eta = ld_early(p.q[cur][0] + o);
+    r.hb = ld_early(p.bath + o);
+    const float mu = ld_early(p.q[cur][1] + o), mv = ld_early(p.q[cur][2] + o);
     r.mu = fx ? -mu : mu;
     r.mv = fy ? -mv : mv;
     return r;
@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kStripThreads) fwd_f32_strips(FwdParams<float>
         // rows are loaded one iteration ahead of their use
         int row = ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
         Raw4 Rn = load_raw(p, cur, col, fx, row, fy);
+#pragma unroll 3
         for (int j = y0 - 2; j <= ylast + 2; j++) {
             const Raw4 Rc = Rn;
             if (j < ylast + 2) {
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
             eta[k] = q0[c];
             mu[k] = fx ? -q1[c] : q1[c];
             h[k] = eta[k] + p.bath[c];
-            const float q = rsqrtf(h[k]);
+            const float q = rsqrt_ftz(h[k]);
             sq[k] = tile::mul(h[k], q);
             u[k] = tile::mul(mu[k], tile::mul(q, q));
         }
@@ -230,12 +231,6 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
 
 }  // namespace f32
 
-// Strip height of the FP32 2D step: 32 rows by default, 16 or 64 on request
-// (the autotuner's choice); all give the same results.
-static int strip_rows(const FwdParams<float> &p) {
-    return (p.fwd_rows == 16 || p.fwd_rows == 64) ? p.fwd_rows : 32;
-}
-
 static int strip_blocks(int nx, int ny, int rows) {
     const long long units = (long long)((nx + f32::strip::kOut - 1) / f32::strip::kOut) *
                             ((ny + rows - 1) / rows);
@@ -243,11 +238,42 @@ static int strip_blocks(int nx, int ny, int rows) {
     return (int)((units + wpb - 1) / wpb);
 }
 
+// Strip height requested for the FP32 2D step (16, 32 or 64), else 0.
+static int requested_rows(const FwdParams<float> &p) {
+    return (p.fwd_rows == 16 || p.fwd_rows == 32 || p.fwd_rows == 64) ? p.fwd_rows : 0;
+}
+
+// Default strip height: the one minimising (waves of strips) x (rows + 4),
+// the rows a strip x-sweeps, with a wave = the warps resident on all SMs.
+// All heights give the same results.
+static int default_rows(int nx, int ny) {
+    static long long slots = 0;
+    if (slots == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32::strip::fwd_f32_strips,
+                                                      f32::strip::kStripThreads, 0);
+        slots = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) *
+                (f32::strip::kStripThreads / 32);
+    }
+    int best = 32;
+    long long best_cost = -1;
+    for (int rows : {64, 32, 16}) {
+        const long long units = (long long)((nx + f32::strip::kOut - 1) / f32::strip::kOut) *
+                                ((ny + rows - 1) / rows);
+        const long long cost = ((units + slots - 1) / slots) * (rows + 4);
+        if (best_cost < 0 || cost < best_cost) { best = rows; best_cost = cost; }
+    }
+    return best;
+}
+
 template <>
 int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
     FwdParams<float> p = p0;
     if (p.two_d) {
-        const int rows = strip_rows(p);
+        const int req = requested_rows(p);
+        const int rows = req ? req : default_rows(p.nx, p.ny);
         p.nblocks = strip_blocks(p.nx, p.ny, rows);
         f32::strip::fwd_f32_strips<<<p.nblocks, f32::strip::kStripThreads, 0, st>>>(p, rows);
         return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
@@ -260,8 +286,12 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
 
 template <>
 int fwd_step_blocks<float>(const FwdParams<float> &p) {
-    // one reduction slot per block of the launch shape p.fwd_rows selects
-    if (p.two_d) return strip_blocks(p.nx, p.ny, strip_rows(p));
+    // one reduction slot per block: of the requested strip height, else of
+    // the lowest one (an upper bound for the default)
+    if (p.two_d) {
+        const int req = requested_rows(p);
+        return strip_blocks(p.nx, p.ny, req ? req : 16);
+    }
     return (p.nx + 255) / 256;
 }
 

@@ -47,8 +47,8 @@ __device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
 __device__ __forceinline__ float cfl_f32(float h, float hu, float hv, float g, float rdx,
                                          float rdy, int two_d) {
     // rounding fixed in the source (no compiler fusion), as in the step
-    const float q = rsqrtf(h), ih = __fmul_rn(q, q);
-    const float gh = __fmul_rn(g, h), cc = __fmul_rn(gh, rsqrtf(gh));
+    const float q = rsqrt_ftz(h), ih = __fmul_rn(q, q);
+    const float gh = __fmul_rn(g, h), cc = __fmul_rn(gh, rsqrt_ftz(gh));
     float s = __fmul_rn(fmaf(fabsf(hu), ih, cc), rdx);
     if (two_d) s = fmaxf(s, __fmul_rn(fmaf(fabsf(hv), ih, cc), rdy));
     return s;

@@ -28,7 +28,7 @@ namespace tile {
 
 constexpr int NT = 256;  // threads per block
 
-__device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcpf(float x) { return rcp_ftz(x); }
 // Rounded single operations that the compiler never fuses: with these and
 // explicit fmaf the rounding of every expression below is fixed in the
 // source, so an edge's numbers do not depend on the kernel that inlines it.
@@ -62,7 +62,7 @@ __device__ __forceinline__ EdgeS solve1(float g, float hL, float mnL, float mtL,
     const float uh = mul(fmaf(sqL, unL, mul(sqR, unR)), rd);
     const float vh = mul(fmaf(sqL, utL, mul(sqR, utR)), rd);
     const float gh = mul(g, hh);
-    const float rc = rsqrtf(gh);
+    const float rc = rsqrt_ftz(gh);
     const float ch = mul(gh, rc);
     const float s1 = sub(uh, ch), s3 = add(uh, ch);
     const float df1 = sub(mnR, mnL);
@@ -193,7 +193,7 @@ __device__ __forceinline__ void load_raw(const View &V, int i0, int j0, Raw<TX, 
 template <typename SM>
 __device__ __forceinline__ void put_cell(SM &S, int ry, int rx, float eta, float h, float mu,
                                          float mv) {
-    const float q = rsqrtf(h);
+    const float q = rsqrt_ftz(h);
     const float ih = mul(q, q);
     S.a[ry][rx] = make_float4(h, mu, mv, eta);
     S.b[ry][rx] = make_float4(mul(mu, ih), mul(mv, ih), mul(h, q), 0.f);

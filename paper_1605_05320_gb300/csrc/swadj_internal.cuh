@@ -55,6 +55,21 @@ __device__ __forceinline__ float ld_early(const float *p) {
     return v;
 }
 
+// One-instruction approximate reciprocal and reciprocal square root
+// (hand-written PTX) with subnormals flushed to zero.  Their inputs in the
+// FP32 kernels are positive normal numbers: depths, sums of square roots of
+// depths, 1 + s^2 terms.
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // MC limiter: max(0, min((1+theta)/2, 2, 2 theta)).
 template <typename R>
 __device__ __forceinline__ R mc_phi(R theta) {
