@@ -256,6 +256,25 @@ int swa_flag_surface(const swa_grid *grid, double tol, uint8_t *flags_dev,
 int swa_gauge_sample(const swa_grid *grid, int n, const double *xy_dev,
                      double *eta_dev, void *stream);
 
+/*
+ * Gauge recording fused into the forward step.  After every step of
+ * swa_step_forward that advances the grid (no-op steps past t_end record
+ * nothing), the block that closes the step samples eta at the n points
+ * xy_dev (device FP64, [n][2], as swa_gauge_sample) from the new state and
+ * writes row r of series_dev (device FP64, [capacity][n], row-major) and,
+ * if times_dev (device FP64, [capacity]) is not NULL, the new time to
+ * times_dev[r]; r counts the recorded steps from 0 and is reset to 0 by
+ * this call (stream-ordered).  Rows past capacity are not written.  The
+ * arrays are the caller's and must stay valid while recording is on;
+ * n = 0 or capacity = 0 turns recording off.  Replaces one gauge launch
+ * per step.
+ */
+int swa_grid_record_gauges(swa_grid *grid, int n, const double *xy_dev,
+                           double *series_dev, double *times_dev,
+                           long long capacity, void *stream);
+/* Rows recorded since the last swa_grid_record_gauges (synchronises). */
+int swa_grid_gauge_rows(const swa_grid *grid, long long *rows, void *stream);
+
 /* ======================= batched uneven patches ===========================
  * Many independent patches of refinement levels 1..SWA_MAX_LEVELS stepped
  * together (the AMR hierarchy of Sec. 1 and Sec. 6 holds patches on levels

@@ -171,6 +171,8 @@ struct swa_grid {
     int step_blocks;
     int state_set;
     int strip_rows;        // FP32 launch shape (0 = default)
+    long long *gauge_row;  // device row counter of the fused gauge recording
+    GaugeRec gauges;       // fused gauge recording (n = 0: off)
 };
 
 static int grid_step_blocks(const swa_grid_desc *d) {
@@ -203,6 +205,7 @@ static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
     void *bath = c.take(n * esz);
     double *staging = (double *)c.take(n * 8);
     DevClock *clk = (DevClock *)c.take(sizeof(DevClock));
+    long long *grow = (long long *)c.take(sizeof(long long));
     int blocks = grid_max_blocks(d);
     if (blocks < kInitBlocks) blocks = kInitBlocks;
     double *partial = (double *)c.take((size_t)blocks * 8);
@@ -214,6 +217,7 @@ static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
         g->clk = clk;
         g->partial = partial;
         g->step_blocks = grid_step_blocks(d);
+        g->gauge_row = grow;
     }
 }
 
@@ -232,6 +236,7 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.nblocks = g->step_blocks;
     p.err = err_word();
     p.fwd_rows = g->strip_rows;
+    p.gauges = g->gauges;
     return p;
 }
 
@@ -897,6 +902,35 @@ int swa_flag_surface(const swa_grid *g, double tol, uint8_t *flags_dev, long lon
 }
 
 // ------------------------------------------------------------------ gauges
+int swa_grid_record_gauges(swa_grid *g, int n, const double *xy_dev, double *series_dev,
+                           double *times_dev, long long capacity, void *stream) {
+    if (!g) return set_error(SWA_EINVAL, "null grid");
+    if (n < 0 || capacity < 0) return set_error(SWA_EINVAL, "n and capacity must be >= 0");
+    if (n > 0 && (!xy_dev || !series_dev)) return set_error(SWA_EINVAL, "null argument");
+    GaugeRec r{};
+    if (n > 0 && capacity > 0) {
+        r.n = n;
+        r.xy = xy_dev;
+        r.series = series_dev;
+        r.times = times_dev;
+        r.cap = capacity;
+        r.row = g->gauge_row;
+        r.x_lo = g->d.x_lo; r.y_lo = g->d.y_lo; r.dx = g->d.dx; r.dy = g->d.dy;
+    }
+    TRY(cuda_check(cudaMemsetAsync(g->gauge_row, 0, sizeof(long long), S(stream)),
+                   "gauge row reset"));
+    g->gauges = r;
+    return SWA_OK;
+}
+
+int swa_grid_gauge_rows(const swa_grid *g, long long *rows, void *stream) {
+    if (!g || !rows) return set_error(SWA_EINVAL, "null argument");
+    cudaStream_t st = S(stream);
+    TRY(cuda_check(cudaMemcpyAsync(rows, g->gauge_row, sizeof(long long),
+                                   cudaMemcpyDeviceToHost, st), "gauge rows"));
+    return cuda_check(cudaStreamSynchronize(st), "gauge rows");
+}
+
 int swa_gauge_sample(const swa_grid *g, int n, const double *xy_dev, double *eta_dev,
                      void *stream) {
     if (!g || (n > 0 && (!xy_dev || !eta_dev))) return set_error(SWA_EINVAL, "null argument");

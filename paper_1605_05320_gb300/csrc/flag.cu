@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "flag.cuh"
+#include "gauge.cuh"
 
 namespace swadj {
 
@@ -432,44 +433,8 @@ __global__ void gauge_kernel(GaugeParams<R> p) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.n) return;
     const int cur = p.clk->cur;
-    const R *q0 = p.q[cur][0];
-    const double x = p.xy[2 * k], y = p.xy[2 * k + 1];
-    double fx = (x - p.x_lo) / p.dx - 0.5;
-    fx = fx < 0.0 ? 0.0 : (fx > (double)(p.nx - 1) ? (double)(p.nx - 1) : fx);
-    int i0 = (int)floor(fx);
-    if (i0 > p.nx - 2) i0 = p.nx - 2;
-    if (i0 < 0) i0 = 0;
-    double ax = fx - (double)i0;
-    const int i1 = p.nx > 1 ? i0 + 1 : i0;
-    if (p.nx == 1) ax = 0.0;
-    size_t st[4];
-    double wt[4];
-    if (!p.two_d) {
-        st[0] = i0; st[1] = i1; st[2] = 0; st[3] = 0;
-        wt[0] = 1.0 - ax; wt[1] = ax; wt[2] = 0.0; wt[3] = 0.0;
-    } else {
-        double fy = (y - p.y_lo) / p.dy - 0.5;
-        fy = fy < 0.0 ? 0.0 : (fy > (double)(p.ny - 1) ? (double)(p.ny - 1) : fy);
-        int j0 = (int)floor(fy);
-        if (j0 > p.ny - 2) j0 = p.ny - 2;
-        if (j0 < 0) j0 = 0;
-        double ay = fy - (double)j0;
-        const int j1 = p.ny > 1 ? j0 + 1 : j0;
-        if (p.ny == 1) ay = 0.0;
-        st[0] = (size_t)j0 * p.nx + i0; wt[0] = (1.0 - ax) * (1.0 - ay);
-        st[1] = (size_t)j0 * p.nx + i1; wt[1] = ax * (1.0 - ay);
-        st[2] = (size_t)j1 * p.nx + i0; wt[2] = (1.0 - ax) * ay;
-        st[3] = (size_t)j1 * p.nx + i1; wt[3] = ax * ay;
-    }
-    double v = 0.0;
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        double eta;
-        if (sizeof(R) == 4) eta = (double)q0[st[c]];
-        else eta = (double)q0[st[c]] + (double)p.bath[st[c]];
-        v += wt[c] * eta;
-    }
-    p.out[k] = v;
+    p.out[k] = gauge_eta<R>(p.q[cur][0], p.bath, p.nx, p.ny, p.two_d, p.x_lo, p.y_lo, p.dx,
+                            p.dy, p.xy[2 * k], p.xy[2 * k + 1]);
 }
 
 template <typename R>

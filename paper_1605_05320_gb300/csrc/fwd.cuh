@@ -1,6 +1,7 @@
 // fwd.cuh -- forward-step kernel parameters and host launchers.
 #pragma once
 
+#include "gauge.cuh"
 #include "swadj_internal.cuh"
 
 namespace swadj {
@@ -20,6 +21,7 @@ struct FwdParams {
     int nblocks;
     int *err;          // device error word (ERR_* bits)
     int fwd_rows;      // FP32 strip height (rows per block), 0 = default
+    GaugeRec gauges;   // fused gauge recording (n = 0: off)
 };
 
 template <typename R>

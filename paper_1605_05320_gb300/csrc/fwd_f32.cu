@@ -170,7 +170,10 @@ __global__ void __launch_bounds__(kStripThreads) fwd_f32_strips(FwdParams<float>
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     tile::finish_step<kStripThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,
-                                     t_now, dt, cur);
+                                     t_now, dt, cur, p.gauges.n > 0);
+    if (p.gauges.n > 0 && am_last)
+        record_gauges<float, kStripThreads>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, 1,
+                                            t_now + dt);
 }
 
 }  // namespace strip
@@ -226,7 +229,10 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,
-                           cur);
+                           cur, p.gauges.n > 0);
+    if (p.gauges.n > 0 && am_last)
+        record_gauges<float, 256>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, 0,
+                                  t_now + dt);
 }
 
 }  // namespace f32

@@ -283,6 +283,9 @@ fwd_step_kernel(FwdParams<R> p) {
     }
 
     // 6) block max -> partial, last block reduces and advances the clock
+    // (with fused gauges every thread first makes its writes visible: the
+    // last block reads the new state of all blocks)
+    if (p.gauges.n > 0) __threadfence();
     const double bm = block_max<NT>(s_cell, red);
     const int bid = blockIdx.x + blockIdx.y * gridDim.x;
     if (tid == 0) {
@@ -308,6 +311,9 @@ fwd_step_kernel(FwdParams<R> p) {
             clk->nsteps = clk->nsteps + 1;
             clk->ticket = 0u;
         }
+        if (p.gauges.n > 0)
+            record_gauges<R, NT>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, p.two_d,
+                                 t + dt);
     }
 }
 

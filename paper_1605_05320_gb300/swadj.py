@@ -40,6 +40,7 @@ EXPORTS = [
     "swa_destroy_snapstore", "swa_store_snapshot", "swa_run_adjoint",
     "swa_snapstore_info",
     "swa_flag_cells", "swa_flag_surface", "swa_gauge_sample",
+    "swa_grid_record_gauges", "swa_grid_gauge_rows",
     "swa_step_forward_static",
     "swa_patches_workspace_bytes", "swa_create_patches", "swa_destroy_patches",
     "swa_patches_set_state", "swa_patches_start_level", "swa_patches_get_state",
@@ -129,6 +130,8 @@ def load(path: str = LIB_PATH):
         "swa_snapstore_info": ([_V, _P(_I), _V, _I], _I),
         "swa_flag_cells": ([_V, _V, _D, _D, _D, _I, _V, _V, _V, _V], _I),
         "swa_gauge_sample": ([_V, _I, _V, _V, _V], _I),
+        "swa_grid_record_gauges": ([_V, _I, _V, _V, _V, ctypes.c_longlong, _V], _I),
+        "swa_grid_gauge_rows": ([_V, _P(ctypes.c_longlong), _V], _I),
         "swa_flag_surface": ([_V, _D, _V, _V, _V], _I),
         "swa_step_forward_static": ([D, _P(_V), _P(_V), _V, _D, _V, _V], _I),
         "swa_patches_workspace_bytes": ([_I, _V, D], _SZ),
@@ -322,6 +325,17 @@ def swa_flag_surface(grid, tol, flags_dev, count_dev, stream=None):
 def swa_gauge_sample(grid, n, xy_dev, eta_dev, stream=None):
     return _chk(load().swa_gauge_sample(grid, int(n), _ptr(xy_dev), _ptr(eta_dev),
                                         _stream(stream)))
+
+
+def swa_grid_record_gauges(grid, n, xy_dev, series_dev, times_dev, capacity, stream=None):
+    return _chk(load().swa_grid_record_gauges(grid, int(n), _ptr(xy_dev), _ptr(series_dev),
+                                              _ptr(times_dev), int(capacity), _stream(stream)))
+
+
+def swa_grid_gauge_rows(grid, stream=None):
+    r = ctypes.c_longlong()
+    _chk(load().swa_grid_gauge_rows(grid, ctypes.byref(r), _stream(stream)))
+    return int(r.value)
 
 
 def swa_step_forward_static(desc, q_in, q_out, bath, dt, smax_out_dev=None, stream=None):

@@ -442,3 +442,45 @@ def test_surface_flags_match_oracle(S, precision):
     near = np.abs(np.abs(eta) - 0.09) <= (1e-12 if precision == "fp64" else 1e-5)
     assert np.array_equal(f[~near], f_ref[~near])
     assert c_ref > 0 and int(cnt.item()) == int(f.sum())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_gauge_recording_matches_per_step_sampling(S, precision):
+    """Gauges recorded by the step kernel equal swa_gauge_sample after each
+    step; rows stop at capacity; steps past t_end record nothing."""
+    sc = synth.small_2d(90, 64, seed=31)
+    p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
+    d = desc_of(S, sc.grid, p)
+    xy = torch.tensor(np.concatenate([sc.gauges, [[0.5e6, 0.2e6], [0.01e6, 0.6e6]]]),
+                      dtype=torch.float64, device="cuda")
+    ng, nsteps, cap = xy.shape[0], 30, 25
+    # reference: one sample after every step
+    g1 = S.Grid(d, sc.B)
+    g1.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    ref = torch.zeros((nsteps, ng), dtype=torch.float64, device="cuda")
+    tref = []
+    for s in range(nsteps):
+        g1.step(1, 1e300)
+        S.swa_gauge_sample(g1.h, ng, xy, ref[s])
+        tref.append(g1.time()[0])
+    # fused
+    g2 = S.Grid(d, sc.B)
+    g2.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    series = torch.full((cap, ng), -7.0, dtype=torch.float64, device="cuda")
+    times = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    S.swa_grid_record_gauges(g2.h, ng, xy, series, times, cap)
+    g2.step(nsteps, 1e300)
+    assert S.swa_grid_gauge_rows(g2.h) == nsteps
+    torch.cuda.synchronize()
+    assert torch.equal(series, ref[:cap])
+    assert np.array_equal(times.cpu().numpy(), np.array(tref[:cap]))
+    # steps past t_end are no-ops and record nothing
+    S.swa_grid_record_gauges(g2.h, ng, xy, series, times, cap)
+    t_now = g2.time()[0]
+    g2.step(5, t_now)
+    assert S.swa_grid_gauge_rows(g2.h) == 0
+    # off
+    S.swa_grid_record_gauges(g2.h, 0, None, None, None, 0)
+    g2.step(2, 1e300)
+    assert S.swa_grid_gauge_rows(g2.h) == 0
+    assert S.swa_sync_status() == 0
