@@ -449,7 +449,7 @@ def run_ours(args, rank, world, local_rank):
 def run_patches(level_steps=100, graph_steps=10, seed=5320):
     """The batched uneven-patch workload: 1500 patches on 3 levels (sides
     16..256, cell size 1 km / 4^(level-1)), FP32, bathymetry and source from
-    the basin fields; tile height autotuned per level; each level's steps
+    the basin fields; strip height autotuned per level; each level's steps
     replayed from a captured CUDA graph.  Returns per-level throughput."""
     import torch
     from paper_1605_05320_gb300 import swadj as S
@@ -485,7 +485,7 @@ def run_patches(level_steps=100, graph_steps=10, seed=5320):
             ps.step(lev, graph_steps, stream=stream)
         graphs[lev] = g
     for lev in ps.levels:
-        npat, ntiles, ncells = S.swa_patches_level_info(ps.h, lev)
+        npat, nstrips, ncells = S.swa_patches_level_info(ps.h, lev)
         reps = max(1, level_steps // graph_steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):  # replays and events on one stream
@@ -499,7 +499,7 @@ def run_patches(level_steps=100, graph_steps=10, seed=5320):
         ms = e0.elapsed_time(e1)
         nst = reps * graph_steps
         out["levels"][str(lev)] = {
-            "patches": npat, "tiles": ntiles, "cells": ncells, "tile_rows": rows[lev],
+            "patches": npat, "strips": nstrips, "cells": ncells, "strip_rows": rows[lev],
             "us_per_level_step": round(1e3 * ms / nst, 2),
             "cell_updates_per_s": ncells * nst / (ms * 1e-3),
             "hbm_frac_of_measured": (28.0 * ncells * nst / (ms * 1e-3)) / 1e9 / load_peaks()[0]}

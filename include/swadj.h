@@ -281,8 +281,9 @@ int swa_grid_gauge_rows(const swa_grid *grid, long long *rows, void *stream);
  * with refinement ratios; here each patch is self-contained, with ghost
  * cells from its own boundary conditions and no exchange between patches).
  * FP32 perturbation form only.  One swa_step_level call enqueues one
- * persistent kernel launch per step that walks the tiles of every patch of
- * that level; all patches of a level share one time step, reduced on the
+ * kernel launch per step whose resident warps walk the strips (28 columns x
+ * 16 or 32 rows) of every patch of that level; results do not depend on the
+ * strip height.  All patches of a level share one time step, reduced on the
  * device from their CFL maxima (dt_l = cfl / max over the level's cells),
  * so a loop of level steps can be captured in a CUDA graph.
  */
@@ -323,10 +324,12 @@ int swa_step_level(swa_patchset *ps, int level, int nsteps, double t_end,
 /* Synchronises; any pointer may be NULL. */
 int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next,
                          long long *nsteps, void *stream);
-/* Number of patches, tiles and cells of a level (host bookkeeping). */
+/* Number of patches, strips (work units of one warp, at the level's current
+ * strip height) and cells of a level (host bookkeeping). */
 int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches,
                            int *ntiles, long long *ncells);
-/* Tile height of the level's kernel: 8 or 16 (0 = default 16). */
+/* Strip height of the level's kernel in rows: 16 or 32 (0 = default 32).
+ * Results do not depend on it; throughput does (the autotuner picks it). */
 int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
 
 /* ======================= allocation-free forward step =====================

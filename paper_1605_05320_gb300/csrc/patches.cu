@@ -1,38 +1,37 @@
-// patches.cu -- batched uneven patches: one persistent launch per level step.
+// patches.cu -- batched uneven patches: one launch per level step.
 //
-// Every patch of a level is cut into TX x TY tiles; the level's tile list
-// (patch, i0, j0) is built on the host at creation and kept on the device.
-// A level step runs the FP32 tile machinery of fwd_tiles.cuh over that list
-// with one block per SM slot, so small and large patches share the launch and
-// the tail of small patches does not leave SMs idle.  The level's clock
-// (time, step, buffer parity, next dt from the fused CFL reduction) lives on
-// the device, as for a single grid.
+// Every patch of a level is cut into warp strips (28 output columns x `rows`
+// rows, strips.cuh); the level's strip list (patch, x0, y0) is built on the
+// host at creation and kept on the device.  A level step is one launch of
+// resident warps that walk that list, so small and large patches share the
+// launch and the tail of small patches does not leave SMs idle.  The
+// level's clock (time, step, buffer parity, next dt from the fused CFL
+// reduction) lives on the device, as for a single grid.
 #include <math.h>
 #include <string.h>
 
 #include <new>
 #include <vector>
 
-#include "fwd_tiles.cuh"
+#include "strips.cuh"
 
 namespace swadj {
 namespace patches {
 
-constexpr int TX = 32;
 constexpr int kMaxBlocks = 4096;  // reduction slots per level
 
 struct PatchDevice {
     float *q[2][3];
     const float *hb;
     int nx, ny;
-    float dx, dy;
+    float dx, dy, rdx, rdy;
     BcSpec bc;
 };
 
 struct LevelParams {
     const PatchDevice *table;
-    const int4 *tiles;
-    int ntiles;
+    const int4 *units;   // (patch, x0, y0, 0)
+    int nunits, rows;
     DevClock *clk;
     double *partial;
     int nblocks;
@@ -42,38 +41,30 @@ struct LevelParams {
     int *err;
 };
 
-struct PatchTiles {
-    const PatchDevice *table;
-    const int4 *tiles;
-    int n, cur;
-    __device__ __forceinline__ int count() const { return n; }
-    __device__ __forceinline__ void get(int k, tile::View &v, int &i0, int &j0) const {
-        const int4 t = tiles[k];
-        const PatchDevice &P = table[t.x];
-        v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
-        v.o0 = P.q[cur ^ 1][0]; v.o1 = P.q[cur ^ 1][1]; v.o2 = P.q[cur ^ 1][2];
-        v.nx = P.nx; v.ny = P.ny; v.dx = P.dx; v.dy = P.dy; v.bc = P.bc;
-        i0 = t.y;
-        j0 = t.z;
-    }
-};
-
-template <int TY>
-__global__ void __launch_bounds__(256) level_step_kernel(LevelParams p) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    tile::Smem<TX, TY> &S = *reinterpret_cast<tile::Smem<TX, TY> *>(dsm);
+__global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelParams p) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
-    __shared__ float red[8];
+    __shared__ float red[strip::kThreads / 32];
     __shared__ int am_last;
     double t_now = 0.0, dt = 0.0;
-    if (!tile::begin_step(p.clk, p.t_end, p.dx, p.dy, s_nu, &s_cur, &s_run, t_now, dt)) return;
-    PatchTiles src{p.table, p.tiles, p.ntiles, s_cur};
+    if (!fwave::begin_step(p.clk, p.t_end, p.dx, p.dy, s_nu, &s_cur, &s_run, t_now, dt)) return;
+    const int cur = s_cur;
+    const int wpb = blockDim.x >> 5;
+    float smax = 0.f;
     bool bad = false;
-    const float sm = tile::run_tiles<TX, TY>(S, src, s_nu[0], s_nu[1], p.g, p.order, bad);
+    // warp-uniform walk of the level's strip list
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < p.nunits; u += gridDim.x * wpb) {
+        const int4 t = p.units[u];
+        const PatchDevice &P = p.table[t.x];
+        strip::View v;
+        v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
+        v.o0 = P.q[cur ^ 1][0]; v.o1 = P.q[cur ^ 1][1]; v.o2 = P.q[cur ^ 1][2];
+        v.nx = P.nx; v.ny = P.ny; v.rdx = P.rdx; v.rdy = P.rdy; v.bc = P.bc;
+        strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order, smax, bad);
+    }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
-    tile::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,
-                           s_cur);
+    fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
+                                        &am_last, t_now, dt, s_cur);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
@@ -82,18 +73,17 @@ __device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
 
 // CFL maximum of buffer 0 of every patch of the level (same per-cell rule as
 // the step's fused reduction), into *smax.
-__global__ void level_smax_kernel(LevelParams p, int TYr, double *smax) {
+__global__ void level_smax_kernel(LevelParams p, double *smax) {
     float m = 0.f;
-    for (int k = blockIdx.x; k < p.ntiles; k += gridDim.x) {
-        const int4 t = p.tiles[k];
+    for (int k = blockIdx.x; k < p.nunits; k += gridDim.x) {
+        const int4 t = p.units[k];
         const PatchDevice &P = p.table[t.x];
-        for (int c = threadIdx.x; c < TX * TYr; c += blockDim.x) {
-            const int i = t.y + c % TX, j = t.z + c / TX;
+        for (int c = threadIdx.x; c < strip::kOut * p.rows; c += blockDim.x) {
+            const int i = t.y + c % strip::kOut, j = t.z + c / strip::kOut;
             if (i >= P.nx || j >= P.ny) continue;
             const size_t o = (size_t)j * P.nx + i;
             const float h = P.q[0][0][o] + P.hb[o];
-            const float s = cfl_f32(h, P.q[0][1][o], P.q[0][2][o], p.g, 1.f / P.dx,
-                                    1.f / P.dy, 1);
+            const float s = cfl_f32(h, P.q[0][1][o], P.q[0][2][o], p.g, P.rdx, P.rdy, 1);
             if (!(h > 0.f)) atomicOr(p.err, ERR_UNSTABLE);
             m = fmaxf(m, s);
         }
@@ -137,28 +127,25 @@ unsigned ew_blocks(size_t n) {
 }
 
 struct Level {
-    int npatches = 0, ntiles16 = 0, ntiles8 = 0;
+    int npatches = 0, nunits16 = 0, nunits32 = 0;
     long long ncells = 0;
     double dx = 0, dy = 0;
-    int4 *tiles16 = nullptr, *tiles8 = nullptr;
+    int4 *units16 = nullptr, *units32 = nullptr;
     DevClock *clk = nullptr;
     double *partial = nullptr;
     double *smax = nullptr;
-    int rows = 0;
+    int rows = 0;   // requested strip height (16 or 32), 0 = default 32
     bool started = false;
 };
 
-template <int TY>
 int occupancy_blocks() {
     static int per_sm = 0, sms = 0;
     if (per_sm == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(level_step_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(tile::Smem<TX, TY>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_step_kernel<TY>, 256,
-                                                      sizeof(tile::Smem<TX, TY>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_strip_kernel,
+                                                      strip::kThreads, 0);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
     }
@@ -226,19 +213,19 @@ int check_patches(int n, const swa_patch_desc *p, const swa_grid_desc *c) {
     return SWA_OK;
 }
 
-void tiles_of(const swa_patch_desc &p, int k, int TY, std::vector<int4> &out) {
-    for (int j0 = 0; j0 < p.ny; j0 += TY)
-        for (int i0 = 0; i0 < p.nx; i0 += patches::TX) out.push_back(make_int4(k, i0, j0, 0));
+void strips_of(const swa_patch_desc &p, int k, int rows, std::vector<int4> &out) {
+    for (int j0 = 0; j0 < p.ny; j0 += rows)
+        for (int i0 = 0; i0 < p.nx; i0 += strip::kOut) out.push_back(make_int4(k, i0, j0, 0));
 }
 
 void layout(int n, const swa_patch_desc *p, Carve &c, swa_patchset *ps) {
     size_t maxn = 0;
-    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t8[SWA_MAX_LEVELS + 1];
+    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t32[SWA_MAX_LEVELS + 1];
     for (int k = 0; k < n; k++) {
         const size_t nn = (size_t)p[k].nx * p[k].ny;
         if (nn > maxn) maxn = nn;
-        tiles_of(p[k], k, 16, t16[p[k].level]);
-        tiles_of(p[k], k, 8, t8[p[k].level]);
+        strips_of(p[k], k, 16, t16[p[k].level]);
+        strips_of(p[k], k, 32, t32[p[k].level]);
     }
     PatchDevice *table = (PatchDevice *)c.take(sizeof(PatchDevice) * n);
     double *staging = (double *)c.take(maxn * 8);
@@ -257,34 +244,35 @@ void layout(int n, const swa_patch_desc *p, Carve &c, swa_patchset *ps) {
         if (ps) {
             d.nx = p[k].nx; d.ny = p[k].ny;
             d.dx = (float)p[k].dx; d.dy = (float)p[k].dy;
+            d.rdx = 1.f / d.dx; d.rdy = 1.f / d.dy;
             d.bc = BcSpec{ps->common.bc[0], ps->common.bc[1], ps->common.bc[2], ps->common.bc[3]};
             ps->host_table[k] = d;
         }
     }
     for (int l = 1; l <= SWA_MAX_LEVELS; l++) {
         int4 *a = (int4 *)c.take(sizeof(int4) * (t16[l].size() + 1));
-        int4 *b = (int4 *)c.take(sizeof(int4) * (t8[l].size() + 1));
+        int4 *b = (int4 *)c.take(sizeof(int4) * (t32[l].size() + 1));
         DevClock *clk = (DevClock *)c.take(sizeof(DevClock));
         double *part = (double *)c.take(8 * kMaxBlocks);
         double *smax = (double *)c.take(8);
         if (ps) {
             Level &L = ps->lev[l];
-            L.tiles16 = a; L.tiles8 = b; L.clk = clk; L.partial = part; L.smax = smax;
-            L.ntiles16 = (int)t16[l].size();
-            L.ntiles8 = (int)t8[l].size();
+            L.units16 = a; L.units32 = b; L.clk = clk; L.partial = part; L.smax = smax;
+            L.nunits16 = (int)t16[l].size();
+            L.nunits32 = (int)t32[l].size();
         }
     }
 }
 
 }  // namespace
 
-static LevelParams level_params(const swa_patchset *ps, int l, double t_end, int &TY) {
+static LevelParams level_params(const swa_patchset *ps, int l, double t_end) {
     const Level &L = ps->lev[l];
-    TY = L.rows == 8 ? 8 : 16;
     LevelParams p{};
     p.table = ps->table;
-    p.tiles = TY == 8 ? L.tiles8 : L.tiles16;
-    p.ntiles = TY == 8 ? L.ntiles8 : L.ntiles16;
+    p.rows = L.rows == 16 ? 16 : 32;
+    p.units = p.rows == 16 ? L.units16 : L.units32;
+    p.nunits = p.rows == 16 ? L.nunits16 : L.nunits32;
     p.clk = L.clk;
     p.partial = L.partial;
     p.t_end = t_end;
@@ -325,25 +313,25 @@ int swa_create_patches(int n, const swa_patch_desc *patches, const double *const
     layout(n, patches, c, ps);
     cudaStream_t st = (cudaStream_t)stream;
     int rc = cuda_check(cudaMemsetAsync(ws, 0, need - 256, st), "workspace clear");
-    // per-level bookkeeping and tile lists
-    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t8[SWA_MAX_LEVELS + 1];
+    // per-level bookkeeping and strip lists
+    std::vector<int4> t16[SWA_MAX_LEVELS + 1], t32[SWA_MAX_LEVELS + 1];
     for (int k = 0; k < n; k++) {
         Level &L = ps->lev[patches[k].level];
         L.npatches++;
         L.ncells += (long long)patches[k].nx * patches[k].ny;
         L.dx = patches[k].dx;
         L.dy = patches[k].dy;
-        tiles_of(patches[k], k, 16, t16[patches[k].level]);
-        tiles_of(patches[k], k, 8, t8[patches[k].level]);
+        strips_of(patches[k], k, 16, t16[patches[k].level]);
+        strips_of(patches[k], k, 32, t32[patches[k].level]);
     }
     for (int l = 1; l <= SWA_MAX_LEVELS && rc == SWA_OK; l++) {
         Level &L = ps->lev[l];
         if (L.npatches == 0) continue;
-        rc = cuda_check(cudaMemcpyAsync(L.tiles16, t16[l].data(), sizeof(int4) * t16[l].size(),
-                                        cudaMemcpyHostToDevice, st), "tile list upload");
+        rc = cuda_check(cudaMemcpyAsync(L.units16, t16[l].data(), sizeof(int4) * t16[l].size(),
+                                        cudaMemcpyHostToDevice, st), "strip list upload");
         if (rc == SWA_OK)
-            rc = cuda_check(cudaMemcpyAsync(L.tiles8, t8[l].data(), sizeof(int4) * t8[l].size(),
-                                            cudaMemcpyHostToDevice, st), "tile list upload");
+            rc = cuda_check(cudaMemcpyAsync(L.units32, t32[l].data(), sizeof(int4) * t32[l].size(),
+                                            cudaMemcpyHostToDevice, st), "strip list upload");
     }
     if (rc == SWA_OK)
         rc = cuda_check(cudaMemcpyAsync(ps->table, ps->host_table.data(),
@@ -397,11 +385,10 @@ int swa_patches_start_level(swa_patchset *ps, int level, double t, void *stream)
     Level &L = ps->lev[level];
     if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
     cudaStream_t st = (cudaStream_t)stream;
-    int TY;
-    LevelParams p = level_params(ps, level, 0.0, TY);
+    LevelParams p = level_params(ps, level, 0.0);
     TRY(cuda_check(cudaMemsetAsync(L.smax, 0, 8, st), "smax clear"));
-    int blocks = p.ntiles < 2048 ? p.ntiles : 2048;
-    level_smax_kernel<<<blocks, 256, 0, st>>>(p, TY, L.smax);
+    int blocks = p.nunits < 2048 ? p.nunits : 2048;
+    level_smax_kernel<<<blocks, 256, 0, st>>>(p, L.smax);
     TRY(cuda_check(cudaGetLastError(), "level_smax_kernel"));
     level_clock_kernel<<<1, 1, 0, st>>>(L.clk, L.smax, t, ps->common.cfl);
     TRY(cuda_check(cudaGetLastError(), "level_clock_kernel"));
@@ -443,20 +430,14 @@ int swa_step_level(swa_patchset *ps, int level, int nsteps, double t_end, void *
     if (!L.started) return set_error(SWA_ESTATE, "level %d not started", level);
     if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
     cudaStream_t st = (cudaStream_t)stream;
-    int TY;
-    LevelParams p = level_params(ps, level, t_end, TY);
-    if (TY == 8) {
-        p.nblocks = occupancy_blocks<8>();
-        if (p.nblocks > p.ntiles) p.nblocks = p.ntiles;
-        for (int s = 0; s < nsteps; s++)
-            level_step_kernel<8><<<p.nblocks, 256, sizeof(tile::Smem<TX, 8>), st>>>(p);
-    } else {
-        p.nblocks = occupancy_blocks<16>();
-        if (p.nblocks > p.ntiles) p.nblocks = p.ntiles;
-        for (int s = 0; s < nsteps; s++)
-            level_step_kernel<16><<<p.nblocks, 256, sizeof(tile::Smem<TX, 16>), st>>>(p);
-    }
-    return cuda_check(cudaGetLastError(), "level_step_kernel");
+    LevelParams p = level_params(ps, level, t_end);
+    constexpr int wpb = strip::kThreads / 32;
+    const int need = (p.nunits + wpb - 1) / wpb;
+    p.nblocks = occupancy_blocks();
+    if (p.nblocks > need) p.nblocks = need;
+    for (int s = 0; s < nsteps; s++)
+        level_strip_kernel<<<p.nblocks, strip::kThreads, 0, st>>>(p);
+    return cuda_check(cudaGetLastError(), "level_strip_kernel");
 }
 
 int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next,
@@ -477,14 +458,15 @@ int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches, int
     if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
     const Level &L = ps->lev[level];
     if (npatches) *npatches = L.npatches;
-    if (ntiles) *ntiles = L.rows == 8 ? L.ntiles8 : L.ntiles16;
+    if (ntiles) *ntiles = L.rows == 16 ? L.nunits16 : L.nunits32;
     if (ncells) *ncells = L.ncells;
     return SWA_OK;
 }
 
 int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows) {
     if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
-    if (rows != 0 && rows != 8 && rows != 16) return set_error(SWA_EINVAL, "tile rows must be 0, 8 or 16");
+    if (rows != 0 && rows != 16 && rows != 32)
+        return set_error(SWA_EINVAL, "strip rows must be 0, 16 or 32");
     ps->lev[level].rows = rows;
     return SWA_OK;
 }

@@ -1,6 +1,6 @@
 """Autotuner for the FP32 launch shapes of the step kernels: the strip height
-of a grid's step (16, 32 or 64 rows) and the tile height of a patch level's
-step (8 or 16 rows).
+of a grid's step (16, 32 or 64 rows) and of a patch level's step (16 or 32
+rows).
 
 The launch shape changes only throughput, never results.  The tuner times
 each candidate with CUDA events on a few steps and keeps the faster one,
@@ -14,7 +14,7 @@ from __future__ import annotations
 
 from . import swadj as S
 
-CANDIDATES = (16, 8)          # patch tile heights
+CANDIDATES = (32, 16)         # patch-level strip heights
 GRID_CANDIDATES = (32, 16, 64)  # grid strip heights
 _cache: dict = {}
 
@@ -57,7 +57,7 @@ def _level_signature(ps: "S.PatchSet", level: int):
 
 
 def tune_patches(ps: "S.PatchSet", steps: int = 5) -> dict:
-    """Pick the tile height of every level of a patch set (levels must have
+    """Pick the strip height of every level of a patch set (levels must have
     been started); returns {level: rows} and applies it."""
     out = {}
     for level in ps.levels:

@@ -94,9 +94,10 @@ def test_single_patch_is_bit_identical_to_grid(S):
 
 
 def test_single_patch_matches_grid_with_supersonic_band(S):
-    """Shallow (10 m) water with a band flowing at 1.5 c among subsonic cells:
-    warps mix subsonic and supersonic edges differently in the grid's strips
-    and the patch's tiles; each edge's arithmetic must not depend on that."""
+    """Shallow (10 m) water with a band flowing at 1.5 c among subsonic cells,
+    stepped as a grid (strips of 64 rows) and as one patch (strips of 16
+    rows): warps group subsonic and supersonic edges differently, and each
+    edge's arithmetic must not depend on that."""
     nx, ny = 150, 97
     p = (1, 0.0, 0.0, nx, ny, 1000.0, 1000.0)
     rng = np.random.default_rng(17)
@@ -108,11 +109,13 @@ def test_single_patch_matches_grid_with_supersonic_band(S):
     hu[band] += 1.5 * 10.0 * np.sqrt(9.81 * 10.0)
     common = S.make_desc(2, 2, 2, 0, 0, 1, 1, precision=S.SWA_FP32)
     ps = S.PatchSet([p], [B], common)
+    S.swa_patches_set_tile_rows(ps.h, 1, 16)
     ps.set_state(0, eta, hu, hv)
     ps.start(1)
     ps.step(1, 20)
     d = S.make_desc(2, nx, ny, 0.0, 0.0, 1000.0, 1000.0, precision=S.SWA_FP32)
     g = S.Grid(d, B)
+    S.swa_grid_set_strip_rows(g.h, 64)
     g.set_state(eta, hu, hv, 0.0)
     g.step(20, 1e300)
     assert S.swa_sync_status() == 0
@@ -141,12 +144,12 @@ def test_grid_strip_height_does_not_change_results(S):
         assert t == res[0][1]
 
 
-def test_tile_height_does_not_change_results(S):
+def test_strip_height_does_not_change_results(S):
     patches = make_patches(seed=5)
     fields = [synth.patch_fields(p, src=(600e3, 950e3), amp=0.5, width=60e3) for p in patches]
     common = S.make_desc(2, 2, 2, 0, 0, 1, 1, precision=S.SWA_FP32)
     res = []
-    for rows in (16, 8):
+    for rows in (32, 16):
         ps = S.PatchSet(patches, [f[0] for f in fields], common)
         for k, (B, eta) in enumerate(fields):
             z = np.zeros(B.size)
