@@ -8,7 +8,8 @@ One step = one whole tsunami scenario of the 2048 x 2048 basin workload
     (snapshot copy fused into the step kernel),
   * the forward run to t_f (about 2000 CFL steps, time step reduced on the
     device inside the step kernel),
-  * a gauge sample after every forward step (recorded by the step kernel),
+  * a gauge sample at every forward step (recorded by the step kernel) and
+    of the final state,
   * an adjoint-weighted flag pass every 10 forward steps over the time window
     [t, min(t + t_f - t_s, t_f)], t_s = 0.32 t_f.
 The metric is cell-updates per second of the SWE steps (forward + adjoint)
@@ -179,7 +180,7 @@ class Scenario:
 
     def alloc_series(self):
         torch = self.torch
-        self.series = torch.zeros((self.n_fwd, N_GAUGES), dtype=torch.float64,
+        self.series = torch.zeros((self.n_fwd + 1, N_GAUGES), dtype=torch.float64,
                                   device=self.flags.device)
         self.counts = torch.zeros(self.n_fwd // FWD_BLOCK + 1, dtype=torch.int64,
                                   device=self.flags.device)
@@ -206,7 +207,8 @@ class Scenario:
             ev["adj"][1].record(tstream)
         launches += self.N_adj + 1
         fp = 0
-        # gauges are sampled by the step kernel itself after every step
+        # gauges are sampled by the step kernels themselves (the state each
+        # step starts from); the final state is sampled after the loop
         S.swa_grid_record_gauges(g.h, N_GAUGES, self.xy, self.series, None, self.n_fwd,
                                  stream)
         for s in range(self.n_fwd):
@@ -226,6 +228,8 @@ class Scenario:
                     ev["flag"][fp][1].record(tstream)
                 fp += 1
                 launches += 1
+        S.swa_gauge_sample(g.h, N_GAUGES, self.xy, self.series[self.n_fwd], stream)
+        launches += 1
         if host_io:
             out_series = self.series.to("cpu", non_blocking=True)
             out_counts = self.counts.to("cpu", non_blocking=True)

@@ -257,17 +257,19 @@ int swa_gauge_sample(const swa_grid *grid, int n, const double *xy_dev,
                      double *eta_dev, void *stream);
 
 /*
- * Gauge recording fused into the forward step.  After every step of
+ * Gauge recording fused into the forward step.  Every step of
  * swa_step_forward that advances the grid (no-op steps past t_end record
- * nothing), the block that closes the step samples eta at the n points
- * xy_dev (device FP64, [n][2], as swa_gauge_sample) from the new state and
- * writes row r of series_dev (device FP64, [capacity][n], row-major) and,
- * if times_dev (device FP64, [capacity]) is not NULL, the new time to
- * times_dev[r]; r counts the recorded steps from 0 and is reset to 0 by
- * this call (stream-ordered).  Rows past capacity are not written.  The
- * arrays are the caller's and must stay valid while recording is on;
- * n = 0 or capacity = 0 turns recording off.  Replaces one gauge launch
- * per step.
+ * nothing) samples eta at the n points xy_dev (device FP64, [n][2], as
+ * swa_gauge_sample) from the state the step starts from, with one block
+ * working beside the step's own, and writes row r of series_dev (device
+ * FP64, [capacity][n], row-major) and, if times_dev (device FP64,
+ * [capacity]) is not NULL, that state's time to times_dev[r]; r counts the
+ * recorded steps from 0 and is reset to 0 by this call (stream-ordered).
+ * So after k steps rows 0..k-1 hold the states at t_0 .. t_{k-1}; sample
+ * the final state with swa_gauge_sample.  Rows past capacity are not
+ * written.  The arrays are the caller's and must stay valid while
+ * recording is on; n = 0 or capacity = 0 turns recording off.  Replaces one
+ * gauge launch per step; values equal swa_gauge_sample's bit for bit.
  */
 int swa_grid_record_gauges(swa_grid *grid, int n, const double *xy_dev,
                            double *series_dev, double *times_dev,

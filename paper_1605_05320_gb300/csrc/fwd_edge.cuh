@@ -152,12 +152,8 @@ __device__ __forceinline__ bool begin_step(DevClock *clkp, double t_end, double 
 template <int NTH>
 __device__ __forceinline__ void finish_step(DevClock *clkp, double *partial, int nblocks,
                                             double cfl, float sm, float *red, int *am_last,
-                                            double t_now, double dt, int cur,
-                                            bool fence_all = false) {
+                                            double t_now, double dt, int cur) {
     const int t = threadIdx.x;
-    // with fused gauges the last block reads the new state of every block:
-    // each thread makes its own writes visible before the block signals
-    if (fence_all) __threadfence();
     for (int o = 16; o > 0; o >>= 1) sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
     if ((t & 31) == 0) red[t >> 5] = sm;
     __syncthreads();

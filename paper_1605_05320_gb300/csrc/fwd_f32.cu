@@ -26,6 +26,11 @@ __global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<f
                            t_now, dt))
         return;
     const int cur = s_cur;
+    // with gauge recording, one extra block (the last) samples the state the
+    // step starts from while the others step it
+    if (p.gauges.n > 0 && blockIdx.x == gridDim.x - 1)
+        record_gauges<float, strip::kThreads>(p.gauges, p.q[cur][0], p.bath, p.nx, p.ny, 1,
+                                              t_now);
     const int nsx = (p.nx + strip::kOut - 1) / strip::kOut, nsy = (p.ny + rows - 1) / rows;
     const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     float smax = 0.f;
@@ -43,10 +48,7 @@ __global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<f
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
-                                        &am_last, t_now, dt, cur, p.gauges.n > 0);
-    if (p.gauges.n > 0 && am_last)
-        record_gauges<float, strip::kThreads>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, 1,
-                                              t_now + dt);
+                                        &am_last, t_now, dt, cur);
 }
 
 // 1D grids: one thread per cell, solving the four edges it needs itself
@@ -61,6 +63,8 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
                           t_now, dt))
         return;
     const int cur = s_cur;
+    if (p.gauges.n > 0 && blockIdx.x == 0)   // the state this step starts from
+        record_gauges<float, 256>(p.gauges, p.q[cur][0], p.bath, p.nx, p.ny, 0, t_now);
     const float nux = s_nu[0], g = p.g;
     const float *q0 = p.q[cur][0], *q1 = p.q[cur][1];
     const int i = blockIdx.x * 256 + threadIdx.x;
@@ -100,10 +104,7 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<256>(p.clk, p.partial, p.nblocks, p.cfl, sm, red, &am_last, t_now, dt,
-                           cur, p.gauges.n > 0);
-    if (p.gauges.n > 0 && am_last)
-        record_gauges<float, 256>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, 0,
-                                  t_now + dt);
+                            cur);
 }
 
 }  // namespace f32
@@ -151,7 +152,7 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
     if (p.two_d) {
         const int req = requested_rows(p);
         const int rows = req ? req : default_rows(p.nx, p.ny);
-        p.nblocks = strip_blocks(p.nx, p.ny, rows);
+        p.nblocks = strip_blocks(p.nx, p.ny, rows) + (p.gauges.n > 0 ? 1 : 0);
         f32::fwd_f32_strips<<<p.nblocks, strip::kThreads, 0, st>>>(p, rows);
         return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
     }
@@ -164,10 +165,10 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
 template <>
 int fwd_step_blocks<float>(const FwdParams<float> &p) {
     // one reduction slot per block: of the requested strip height, else of
-    // the lowest one (an upper bound for the default)
+    // the lowest one (an upper bound for the default), and the gauge block
     if (p.two_d) {
         const int req = requested_rows(p);
-        return strip_blocks(p.nx, p.ny, req ? req : 16);
+        return strip_blocks(p.nx, p.ny, req ? req : 16) + 1;   // + the gauge block
     }
     return (p.nx + 255) / 256;
 }

@@ -136,6 +136,8 @@ fwd_step_kernel(FwdParams<R> p) {
     if (p.t_end - t < dt) dt = p.t_end - t;
     if (!(dt > 0.0)) return;  // clock already at t_end: no-op step
     const int cur = clk->cur;
+    if (p.gauges.n > 0 && blockIdx.x == 0 && blockIdx.y == 0)   // the state this step starts from
+        record_gauges<R, NT>(p.gauges, p.q[cur][0], p.bath, p.nx, p.ny, p.two_d, t);
 
     const R *q0 = p.q[cur][0], *q1 = p.q[cur][1], *q2 = p.q[cur][2];
     R *o0 = p.q[cur ^ 1][0], *o1 = p.q[cur ^ 1][1], *o2 = p.q[cur ^ 1][2];
@@ -283,9 +285,6 @@ fwd_step_kernel(FwdParams<R> p) {
     }
 
     // 6) block max -> partial, last block reduces and advances the clock
-    // (with fused gauges every thread first makes its writes visible: the
-    // last block reads the new state of all blocks)
-    if (p.gauges.n > 0) __threadfence();
     const double bm = block_max<NT>(s_cell, red);
     const int bid = blockIdx.x + blockIdx.y * gridDim.x;
     if (tid == 0) {
@@ -311,9 +310,6 @@ fwd_step_kernel(FwdParams<R> p) {
             clk->nsteps = clk->nsteps + 1;
             clk->ticket = 0u;
         }
-        if (p.gauges.n > 0)
-            record_gauges<R, NT>(p.gauges, p.q[cur ^ 1][0], p.bath, p.nx, p.ny, p.two_d,
-                                 t + dt);
     }
 }
 

@@ -12,8 +12,8 @@ namespace swadj {
 struct GaugeRec {
     int n;                // gauges
     const double *xy;     // [n][2] coordinates
-    double *series;       // [cap][n] surface elevation after each step
-    double *times;        // [cap] time after each step, or null
+    double *series;       // [cap][n] surface elevation at the start of each step
+    double *times;        // [cap] time at the start of each step, or null
     long long cap;        // rows of the series
     long long *row;       // device row counter (rows recorded so far)
     double x_lo, y_lo, dx, dy;   // geometry of the grid
@@ -52,24 +52,26 @@ __device__ __forceinline__ double gauge_eta(const R *q0, const R *bath, int nx, 
         st[2] = (size_t)j1 * nx + i0; wt[2] = (1.0 - ax) * ay;
         st[3] = (size_t)j1 * nx + i1; wt[3] = ax * ay;
     }
+    // rounded operations (never fused), so every translation unit gives the
+    // same number, and the one an unfused FP64 evaluation gives
     double v = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         double eta;
         if (sizeof(R) == 4) eta = (double)__ldcg(q0 + st[c]);
-        else eta = (double)__ldcg(q0 + st[c]) + (double)bath[st[c]];
-        v += wt[c] * eta;
+        else eta = __dadd_rn((double)__ldcg(q0 + st[c]), (double)bath[st[c]]);
+        v = __dadd_rn(v, __dmul_rn(wt[c], eta));
     }
     return v;
 }
 
-// Called by every thread of the block that has just advanced the clock to
-// time t_new with the new state in q0 (block-uniform call, after a
-// __syncthreads that follows the clock update).  Writes the next row of the
-// series; rows past cap are not written.
+// Called by every thread of one block of a step kernel (block-uniform call)
+// with the state the step starts from (q0, complete since the previous
+// launch) and its time t.  Writes the next row of the series; rows past cap
+// are not written.
 template <typename R, int NTH>
 __device__ __forceinline__ void record_gauges(const GaugeRec &g, const R *q0, const R *bath,
-                                              int nx, int ny, int two_d, double t_new) {
+                                              int nx, int ny, int two_d, double t) {
     __shared__ long long s_row;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         s_row = *g.row;
@@ -82,7 +84,7 @@ __device__ __forceinline__ void record_gauges(const GaugeRec &g, const R *q0, co
     for (int k = tid; k < g.n; k += NTH)
         g.series[r * g.n + k] = gauge_eta<R>(q0, bath, nx, ny, two_d, g.x_lo, g.y_lo, g.dx,
                                              g.dy, g.xy[2 * k], g.xy[2 * k + 1]);
-    if (tid == 0 && g.times) g.times[r] = t_new;
+    if (tid == 0 && g.times) g.times[r] = t;
 }
 
 }  // namespace swadj

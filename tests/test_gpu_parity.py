@@ -446,8 +446,9 @@ def test_surface_flags_match_oracle(S, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_gauge_recording_matches_per_step_sampling(S, precision):
-    """Gauges recorded by the step kernel equal swa_gauge_sample after each
-    step; rows stop at capacity; steps past t_end record nothing."""
+    """Gauges recorded by the step kernel (the state each step starts from)
+    equal swa_gauge_sample before each step; rows stop at capacity; steps
+    past t_end record nothing."""
     sc = synth.small_2d(90, 64, seed=31)
     p = S.SWA_FP64 if precision == "fp64" else S.SWA_FP32
     d = desc_of(S, sc.grid, p)
@@ -460,9 +461,9 @@ def test_fused_gauge_recording_matches_per_step_sampling(S, precision):
     ref = torch.zeros((nsteps, ng), dtype=torch.float64, device="cuda")
     tref = []
     for s in range(nsteps):
-        g1.step(1, 1e300)
         S.swa_gauge_sample(g1.h, ng, xy, ref[s])
         tref.append(g1.time()[0])
+        g1.step(1, 1e300)
     # fused
     g2 = S.Grid(d, sc.B)
     g2.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
