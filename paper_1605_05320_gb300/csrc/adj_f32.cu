@@ -125,14 +125,17 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     EdgeA W1 = {0.f, 0.f, 0.f, 0.f, false}, W2 = W1;   // y-edges (j-3|j-2), (j-2|j-1)
     float rp0 = 0.f, rp1 = 0.f;   // R part of the y-net of edge (j-3|j-2)
     // rows are loaded one iteration ahead of their use
-    bool fy;
-    int row = ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+    // strips away from the lower and upper boundary need no row mapping
+    const bool yin = y0 - 2 >= 0 && ylast + 2 < p.ny;
+    bool fy = false;
+    int row = yin ? y0 - 2 : ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
     CellA Cn = load_cell(p, col, fx, row, fy);
 #pragma unroll 3
     for (int j = y0 - 2; j <= ylast + 2; j++) {
         const CellA C = Cn;
         if (j < ylast + 2) {
-            row = ghost_index(j + 1, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+            if (yin) row = j + 1;
+            else row = ghost_index(j + 1, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
             Cn = load_cell(p, col, fx, row, fy);
         }
         EdgeA Wn = W2;

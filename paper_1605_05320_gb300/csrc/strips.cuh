@@ -118,13 +118,17 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
     fwave::EdgeS W1 = {}, W2 = {};   // y-edges (j-3|j-2), (j-2|j-1)
     float4 nlr = make_float4(0.f, 0.f, 0.f, 0.f);   // y-net of edge (j-3|j-2)
     float2 nr = make_float2(0.f, 0.f);
-    int row = ghost_index(y0 - 2, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+    // strips away from the lower and upper boundary need no row mapping
+    const bool yin = y0 - 2 >= 0 && ylast + 2 < v.ny;
+    fy = false;
+    int row = yin ? y0 - 2 : ghost_index(y0 - 2, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
     Raw4 Rn = load_raw(v, col, fx, row, fy);
 #pragma unroll 3
     for (int j = y0 - 2; j <= ylast + 2; j++) {
         const Raw4 Rc = Rn;
         if (j < ylast + 2) {
-            row = ghost_index(j + 1, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+            if (yin) row = j + 1;
+            else row = ghost_index(j + 1, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
             Rn = load_raw(v, col, fx, row, fy);
         }
         const XCell C = xsweep(derive(Rc.eta, Rc.eta + Rc.hb, Rc.mu, Rc.mv), g, nux, order);
