@@ -355,7 +355,8 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  *            for SWA_FP32.
  * dt         the step (the caller chooses it, e.g. cfl / s_max).
  * smax_out_dev  optional device double receiving s_max of the new state,
- *            max over cells of (|u|+c)/dx + (|v|+c)/dy, for the next dt.
+ *            max over cells of max((|u|+c)/dx, (|v|+c)/dy) (the split
+ *            step's CFL rule, as in swa_step_forward), for the next dt.
  * Errors: SWA_EINVAL for bad arguments; SWA_ENOMEM when the grid needs more
  * reduction slots than the static array holds (SWA_STATIC_MAX_BLOCKS blocks;
  * 2048 x 2048 fits in both precisions); SWA_ECUDA for a runtime failure.
