@@ -201,8 +201,7 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
 // groups is read.  Every product that is formed is the one the unpruned pass
 // forms, so the flags and the count are identical to the unpruned pass; only
 // m differs (it may omit values below tol), hence PRUNE only without maxip.
-// Ahead of the forward wave q = 0 exactly and every group is skipped, so the
-// pass then reads the state and the envelope only.
+// Ahead of the forward wave q = 0 exactly: such a quad reads its state only.
 template <bool PRUNE>
 __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float> p) {
     __shared__ Window sw;
@@ -242,7 +241,13 @@ __global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float
             return (!ok0 || b0 < tolp) && (!ok1 || b1 < tolp) && (!ok2 || b2 < tolp) &&
                    (!ok3 || b3 < tolp);
         };
-        if (!w.empty && (ok0 || ok1 || ok2 || ok3 || !PRUNE)) {
+        // PRUNE: a quad whose forward state is exactly zero (the ocean at rest
+        // ahead of the wave) has every product exactly zero, m = 0 as in the
+        // full pass, so even its envelope is not read
+        const bool rest = e.x == 0.f && e.y == 0.f && e.z == 0.f && e.w == 0.f &&
+                          u.x == 0.f && u.y == 0.f && u.z == 0.f && u.w == 0.f &&
+                          v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f;
+        if (!w.empty && (!PRUNE || ((ok0 || ok1 || ok2 || ok3) && !rest))) {
             const float4 *s0 = reinterpret_cast<const float4 *>(p.snaps) + i;
             // skip bits of the first 32 groups of the window (256 snapshots),
             // their loads issued independently of one another
