@@ -121,8 +121,11 @@ static int requested_rows(const FwdParams<float> &p) {
     return (p.fwd_rows == 16 || p.fwd_rows == 32 || p.fwd_rows == 64) ? p.fwd_rows : 0;
 }
 
-// Default strip height: the one minimising (waves of strips) x (rows + 4),
-// the rows a strip x-sweeps, with a wave = the warps resident on all SMs.
+// Default strip height.  Warps of one resident wave (all SMs full) hide
+// each other's latency best, so the default is the lowest height (at least
+// 16 rows) whose strips all fit in one wave, one block kept for the gauge
+// block; when none does (very large grids), the one of 16 .. 256 rows
+// minimising (waves of strips) x (rows + 4), the rows a strip x-sweeps.
 // All heights give the same results.
 static int default_rows(int nx, int ny) {
     static long long slots = 0;
@@ -135,11 +138,17 @@ static int default_rows(int nx, int ny) {
         slots = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) *
                 (strip::kThreads / 32);
     }
+    const long long nsx = (nx + strip::kOut - 1) / strip::kOut;
+    const long long per_col = (slots - strip::kThreads / 32) / nsx;   // strips down a column
+    if (per_col >= 1) {
+        long long rows = (ny + per_col - 1) / per_col;
+        if (rows < 16) rows = 16;
+        if (rows <= 256) return (int)rows;
+    }
     int best = 32;
     long long best_cost = -1;
-    for (int rows : {64, 32, 16}) {
-        const long long units = (long long)((nx + strip::kOut - 1) / strip::kOut) *
-                                ((ny + rows - 1) / rows);
+    for (int rows : {256, 128, 64, 32, 16}) {
+        const long long units = nsx * ((ny + rows - 1) / rows);
         const long long cost = ((units + slots - 1) / slots) * (rows + 4);
         if (best_cost < 0 || cost < best_cost) { best = rows; best_cost = cost; }
     }
