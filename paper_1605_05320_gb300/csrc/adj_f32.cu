@@ -87,7 +87,7 @@ __device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const E
 // edges.  No shared memory and no barriers.
 constexpr int kLanes = 32;
 constexpr int kOut = kLanes - 4;   // output columns per strip
-constexpr int kRows = 16;          // output rows per strip
+constexpr int kRows = 32;          // output rows per strip
 constexpr unsigned kFull = 0xffffffffu;
 
 struct CellA {
