@@ -237,6 +237,39 @@ class Scenario:
         return launches, None, None
 
 
+SURFACE_TOLS = (0.14, 0.09)   # the paper's two surface-flagging tolerances (Sec. 6), metres
+
+
+def compare_flags(scen, tstream):
+    """Untimed: one more scenario with, every FWD_BLOCK forward steps, the
+    adjoint-weighted flag pass and surface flagging (|eta| > tol) at the
+    paper's two tolerances; returns the flagged-cell counts per pass
+    (mean, max, and the fraction of passes with any flag)."""
+    S, torch = scen.S, scen.torch
+    stream = tstream.cuda_stream
+    g, sc = scen.grid, scen.sc
+    S.swa_set_state(g.h, scen.eta_d, scen.hu_d, scen.hv_d, 0.0, S.SWA_DEVICE, stream)
+    S.swa_set_adjoint_state(scen.adj.h, scen.phi_d, S.SWA_DEVICE, stream)
+    S.swa_snapstore_clear(scen.store.h)
+    S.swa_run_adjoint(scen.adj.h, scen.store.h, SNAP_EVERY, stream)
+    npass = scen.n_fwd // FWD_BLOCK
+    dev = scen.flags.device
+    cnt = torch.zeros((1 + len(SURFACE_TOLS), npass), dtype=torch.int64, device=dev)
+    for k in range(npass):
+        S.swa_step_forward(g.h, FWD_BLOCK, sc.t_f, stream)
+        S.swa_flag_cells(g.h, scen.store.h, sc.t_s, sc.t_f, sc.tol, S.SWA_FLAG_INTERP,
+                         scen.flags, None, cnt[0, k], stream)
+        for j, tol in enumerate(SURFACE_TOLS):
+            S.swa_flag_surface(g.h, tol, scen.flags, cnt[1 + j, k], stream)
+    torch.cuda.synchronize()
+    c = cnt.cpu().numpy()
+    names = [f"adjoint_tol_{sc.tol:g}"] + [f"surface_tol_{t:g}_m" for t in SURFACE_TOLS]
+    return {"passes": npass, "every_steps": FWD_BLOCK,
+            "counts": {nm: {"mean": float(c[i].mean()), "max": int(c[i].max()),
+                            "passes_with_flags": float((c[i] > 0).mean())}
+                       for i, nm in enumerate(names)}}
+
+
 def cell_updates(sc_obj):
     return (sc_obj.n_fwd * sc_obj.n + sc_obj.N_adj * sc_obj.adj.n)
 
@@ -444,8 +477,11 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
-        "flags_last": int(scen.counts.sum().item()),
+        "flagged_cells_per_pass_mean": float(scen.counts.double().mean().item()),
     }
+    if rank == 0:
+        with torch.cuda.stream(stream):
+            out["flag_comparison"] = compare_flags(scen, stream)
     return out
 
 
