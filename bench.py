@@ -462,15 +462,10 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic (seeded basin bathymetry, Gaussian source and target)",
-        "config": {"workload": f"basin {args.n}x{args.n} 1 km, forward to t_f "
-                               f"({scen.n_fwd} steps) + adjoint ({scen.N_adj} steps, "
-                               f"snapshot every {SNAP_EVERY}) + flag every {FWD_BLOCK} "
-                               f"+ {N_GAUGES} gauges",
-                   "precision": args.precision, "cells": scen.n,
-                   "forward_steps": scen.n_fwd, "adjoint_steps": scen.N_adj,
-                   "snapshots": scen.store.info()[0], "flag_passes": n_flag,
-                   "l2": "inputs larger than L2 (snapshot store streamed by every flag pass)",
-                   "parallelism": f"replicas x{world} (independent scenarios)"},
+        "config": workload_config(args.n, world),
+        "scenario": {"precision": args.precision, "forward_steps": scen.n_fwd,
+                     "adjoint_steps": scen.N_adj, "snapshots": scen.store.info()[0],
+                     "flag_passes": n_flag},
         "roofline": roofline,
         "kernels": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv)
                         for kk, vv in v.items()} for k, v in kern.items()},
@@ -579,7 +574,18 @@ def oracle_sample(n, steps):
     return 2 * steps * sc.grid.n / sec, sec, O.num_threads()
 
 
-def run_reference(args):
+def workload_config(n, world):
+    """The workload both arms report (the reference arm times a bounded
+    sample of it)."""
+    return {"workload": f"basin {n}x{n} 1 km, forward to t_f + adjoint (snapshot every "
+                        f"{SNAP_EVERY} steps) + adjoint-weighted flag pass every "
+                        f"{FWD_BLOCK} forward steps + {N_GAUGES} gauges",
+            "cells": n * n,
+            "l2": "inputs larger than L2 (snapshot store streamed by every flag pass)",
+            "parallelism": f"replicas x{world} (independent scenarios)"}
+
+
+def run_reference(args, world=1):
     cores = os.cpu_count() or 1
     n = args.n
     per = 2
@@ -600,9 +606,8 @@ def run_reference(args):
         "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic (seeded basin bathymetry)",
-        "config": {"workload": f"basin {n}x{n} 1 km (bounded oracle sample)",
-                   "precision": "fp64", "parallelism": "host cores"},
+        "dtype": "f64", "data": "synthetic (seeded basin bathymetry, Gaussian source and target)",
+        "config": workload_config(n, world),
         "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": thr,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
@@ -617,7 +622,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args)))
+            print(json.dumps(run_reference(args, world)))
         return
     if world > 1:
         import torch
