@@ -121,28 +121,42 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     const bool out = lane >= 2 && lane < kLanes - 2 && gi < p.nx;
     const float nux = p.nux, nuy = p.nuy;
     const int order = p.order;
-    CellA A = {0.f, 0.f, 0.f, 0.f}, B = A;   // rows j-2, j-1
-    EdgeA W1 = {0.f, 0.f, 0.f, 0.f, false}, W2 = W1;   // y-edges (j-3|j-2), (j-2|j-1)
-    float rp0 = 0.f, rp1 = 0.f;   // R part of the y-net of edge (j-3|j-2)
-    // rows are loaded one iteration ahead of their use
-    // strips away from the lower and upper boundary need no row mapping
+    // row j of the strip, index-mapped (strips away from the lower and
+    // upper boundary need no mapping; past the last row the load is clamped
+    // and its values unused)
     const bool yin = y0 - 2 >= 0 && ylast + 2 < p.ny;
-    bool fy = false;
-    int row = yin ? y0 - 2 : ghost_index(y0 - 2, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
-    CellA Cn = load_cell(p, col, fx, row, fy);
+    auto load = [&](int j) -> CellA {
+        bool fy = false;
+        int row;
+        if (yin) row = j < p.ny ? j : p.ny - 1;
+        else row = ghost_index(j, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        return load_cell(p, col, fx, row, fy);
+    };
+    // prologue, rows y0-2 .. y0+1 (rows are loaded one step ahead of use)
+    CellA Cn = load(y0 - 1);
+    CellA A = load(y0 - 2);                                  // row y0-2
+    CellA B = Cn;                                            // row y0-1
+    Cn = load(y0);
+    EdgeA W1 = solve_a(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-2|y0-1)
+    A = B;
+    B = Cn;                                                  // row y0
+    Cn = load(y0 + 1);
+    EdgeA W2 = solve_a(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-1|y0)
+    CellA C = Cn;                                            // row y0+1
+    Cn = load(y0 + 2);
+    EdgeA Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);        // edge (y0|y0+1)
+    float4 nn = net_a(W1, W2, Wn, nuy, order);               // edge (y0-1|y0)
+    A = B; B = C;                                            // rows j-2, j-1
+    W1 = W2; W2 = Wn;                                        // y-edges (j-3|j-2), (j-2|j-1)
+    float rp0 = nn.z, rp1 = nn.w;   // R part of the y-net of edge (j-3|j-2)
+    // main loop without branches on j
 #pragma unroll 3
-    for (int j = y0 - 2; j <= ylast + 2; j++) {
-        const CellA C = Cn;
-        if (j < ylast + 2) {
-            if (yin) row = j + 1;
-            else row = ghost_index(j + 1, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
-            Cn = load_cell(p, col, fx, row, fy);
-        }
-        EdgeA Wn = W2;
-        if (j >= y0 - 1) Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);   // edge (j-1|j)
-        float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j >= y0 + 1) nn = net_a(W1, W2, Wn, nuy, order);           // edge (j-2|j-1)
-        if (j >= y0 + 2) {
+    for (int j = y0 + 2; j <= ylast + 2; j++) {
+        C = Cn;
+        Cn = load(j + 1);
+        Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);          // edge (j-1|j)
+        nn = net_a(W1, W2, Wn, nuy, order);                  // edge (j-2|j-1)
+        {
             // y-sweep of row r = j - 2: lower edge -> R of the previous net,
             // upper edge -> L of this one
             float e = A.e, g = A.g;
