@@ -86,3 +86,29 @@ def test_product_path_does_not_touch_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "swe_oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_launch_shape_and_gauge_calls_check_their_arguments(lib):
+    """Argument checks that need no GPU: null handles and strip heights the
+    kernels do not offer are rejected before anything is enqueued."""
+    assert lib.swa_grid_set_strip_rows(None, 32) == S.SWA_EINVAL
+    assert lib.swa_patches_set_tile_rows(None, 1, 32) == S.SWA_EINVAL
+    assert lib.swa_grid_record_gauges(None, 2, None, None, None, 10, None) == S.SWA_EINVAL
+    rows = ctypes.c_longlong()
+    assert lib.swa_grid_gauge_rows(None, ctypes.byref(rows), None) == S.SWA_EINVAL
+    # the static step's scratch holds a 2048^2 FP64 step (64 x 512 tiles of
+    # 32 x 4 cells, one reduction slot each)
+    hdr = open(os.path.join(ROOT, "include", "swadj.h")).read()
+    assert int(re.search(r"#define SWA_STATIC_MAX_BLOCKS (\d+)", hdr).group(1)) >= 64 * 512
+
+
+def test_bench_arms_report_the_same_workload():
+    """Both arms of bench.py name the same workload config."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    a, b = bench.workload_config(2048, 1), bench.workload_config(2048, 1)
+    assert a == b and a["cells"] == 2048 * 2048
+    assert "flag pass every 10" in a["workload"]
+    assert bench.whole_job_rate(100.0, 4, 2, 1000.0) == 800.0
