@@ -139,6 +139,14 @@ def gaussian_field(grid: GridSpec, cx: float, cy: float, amp: float,
     return (amp * np.exp(-(((X - cx) ** 2 + (Y - cy) ** 2) / (width * width)))).ravel()
 
 
+def disc_indicator(grid: GridSpec, cx: float, cy: float, radius: float) -> np.ndarray:
+    """1 at cell centres within `radius` of (cx, cy), else 0: an indicator
+    target region, as the paper's examples use for the adjoint data."""
+    xc, yc = grid.centres()
+    X, Y = np.meshgrid(xc, yc)
+    return (((X - cx) ** 2 + (Y - cy) ** 2) <= radius * radius).astype(np.float64).ravel()
+
+
 def source_point(rng, target, L, rmin=300e3, rmax=700e3, basin_frac=1600.0 / 2048.0):
     """A seeded basin point between rmin and rmax from the target."""
     for _ in range(10000):

@@ -210,6 +210,24 @@ def test_fp64_adjoint_2d_with_island(S):
         assert rel(got[:, c], snaps[:, c]) <= 1e-12, c
 
 
+def test_adjoint_with_indicator_target(S):
+    """Adjoint data an indicator of a disc (discontinuous, as the target
+    regions of the paper's examples): FP64 snapshots within 1e-12 of the
+    oracle, FP32 within 5e-5 of each component's maximum over the run."""
+    sc = synth.small_2d(96, 70, seed=7)
+    L = sc.adj_grid.nx * sc.adj_grid.dx
+    Ly = sc.adj_grid.ny * sc.adj_grid.dy
+    sc.phi[:] = 0.0
+    sc.phi[0] = synth.disc_indicator(sc.adj_grid, 0.8 * L, 0.5 * Ly, 6 * sc.adj_grid.dx)
+    for prec, bound in ((S.SWA_FP64, 1e-12), (S.SWA_FP32, 5e-5)):
+        adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+            _adjoint_pair(S, sc, prec, 5, (1, 1, 1, 1))
+        assert N == N_ref and np.array_equal(tau, tau_ref)
+        got = _read_snaps(S, store, prec, 3, sc.adj_grid.n)
+        for c in range(3):
+            assert rel(got[:, c], snaps[:, c]) <= bound, (prec, c, rel(got[:, c], snaps[:, c]))
+
+
 @pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (1, 0, 0, 1)])
 def test_fp32_adjoint_snapshots_vs_oracle(S, order, bc):
