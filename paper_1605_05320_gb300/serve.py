@@ -292,24 +292,25 @@ def main(argv=None):
     for r in res:
         lat_by.setdefault(r.n, []).append(r.latency)
     st["p50_by_size_s"] = {str(k): float(np.percentile(v, 50)) for k, v in lat_by.items()}
-    sub = reqs[: a.plain_requests]
-    served_sub, sst = Server(adj).run([Request(r.id, 0.0, r.n, r.amp, r.width, r.src_u,
-                                               r.src_v) for r in sub])
-    _, pst = run_plain(adj, sub, precision=S.SWA_FP64)
-    # gauge error of the FP32 served results against the FP64 per-grid ones
-    plain64, _ = run_plain(adj, sub[:2], precision=S.SWA_FP64)
-    gerr = 0.0
-    for r in plain64:
-        s = next(x for x in served_sub if x.id == r.id)
-        k = min(len(s.gauges), len(r.gauges))
-        gerr = max(gerr, float(np.abs(s.gauges[:k] - r.gauges[:k]).max()))
-    print(json.dumps({"metric": "served scenarios/s (FP32 continuous batching) vs plain per-grid FP64",
-                      "adjoint_setup_s": adj_s, "served": st,
-                      "same_requests_served_fp32": sst, "plain_fp64": pst,
-                      "served_over_plain": sst["scenarios_per_s"] / pst["scenarios_per_s"],
-                      "gauge_max_abs_err_fp32_vs_fp64_m": gerr,
-                      "trace": {"requests": a.requests, "rate_per_s": a.rate,
-                                "sizes": sizes}}))
+    out = {"metric": "served scenarios/s (FP32 continuous batching) vs plain per-grid FP64",
+           "adjoint_setup_s": adj_s, "served": st,
+           "trace": {"requests": a.requests, "rate_per_s": a.rate, "sizes": sizes}}
+    if a.plain_requests > 0:   # 0 skips the (slow) per-grid FP64 comparison
+        sub = reqs[: a.plain_requests]
+        served_sub, sst = Server(adj).run([Request(r.id, 0.0, r.n, r.amp, r.width, r.src_u,
+                                                   r.src_v) for r in sub])
+        _, pst = run_plain(adj, sub, precision=S.SWA_FP64)
+        # gauge error of the FP32 served results against the FP64 per-grid ones
+        plain64, _ = run_plain(adj, sub[:2], precision=S.SWA_FP64)
+        gerr = 0.0
+        for r in plain64:
+            s = next(x for x in served_sub if x.id == r.id)
+            k = min(len(s.gauges), len(r.gauges))
+            gerr = max(gerr, float(np.abs(s.gauges[:k] - r.gauges[:k]).max()))
+        out.update({"same_requests_served_fp32": sst, "plain_fp64": pst,
+                    "served_over_plain": sst["scenarios_per_s"] / pst["scenarios_per_s"],
+                    "gauge_max_abs_err_fp32_vs_fp64_m": gerr})
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
