@@ -228,8 +228,10 @@ int swa_snapstore_info(const swa_snapstore *store, int *count, double *tau_host,
  * (nullable, float) receives m; *count_dev (device int64, overwritten)
  * receives the number of flags.  t > t_f gives no flags.
  * When maxip_dev is null and the store has an envelope (FP32 forward grid
- * and FP32 snapshots on the same 2D grid), a snapshot group is read for a
- * cell only if its envelope bound on |q^ . q| reaches tol (1 - 1e-5) there;
+ * and FP32 snapshots of a 2D adjoint grid, the same grid or another one), a
+ * snapshot group is read for a cell only if its envelope bound on
+ * |q^ . q| reaches tol (1 - 1e-5) there (on another grid: the largest
+ * envelope entry over the quads of the cell's bilinear stencil);
  * the flags and the count are identical to the full pass (every product the
  * pruned pass forms is the one the full pass forms; skipped products are
  * provably below tol), so only the optional m output needs the full pass.

@@ -848,7 +848,7 @@ static int flag_dispatch(const swa_grid *g, const swa_snapstore *s, double t_s, 
     p.t_s = t_s; p.t_f = t_f; p.tol = tol; p.mode = mode;
     p.flags = flags;
     p.maxip = maxip;
-    p.env = p.same_grid ? s->env : nullptr;
+    p.env = s->env;   // the envelope is on the adjoint grid (same or coarser)
     p.count = (unsigned long long *)count;
     return flag_launch<R, SN>(p, st);
 }

@@ -83,17 +83,44 @@ __device__ Window make_window(const double *tau, int K, double t, double t_s,
     return w;
 }
 
+// Arithmetic of the flag products.  In float every rounding is fixed in the
+// source (fmaf and unfused multiplies), so the pruned and the full variant
+// form the same numbers; double keeps the plain expressions.
+__device__ __forceinline__ float acc(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double acc(double a, double b, double c) { return a * b + c; }
+__device__ __forceinline__ float dot3(float a, float x, float b, float y, float c, float z) {
+    return fmaf(c, z, fmaf(b, y, __fmul_rn(a, x)));
+}
+__device__ __forceinline__ double dot3(double a, double x, double b, double y, double c,
+                                       double z) {
+    return a * x + b * y + c * z;
+}
+__device__ __forceinline__ float lerp2(float a, float x, float b, float y) {
+    return fmaf(a, x, __fmul_rn(b, y));
+}
+__device__ __forceinline__ double lerp2(double a, double x, double b, double y) {
+    return a * x + b * y;
+}
+
 // Products are accumulated in float when both the forward state and the
 // snapshots are float (the bandwidth-bound FP32 path; GB300's FP64 rate is a
 // small fraction of its FP32 rate) and in double otherwise.
-template <typename R, typename S, bool SAME>
+//
+// PRUNE (float, 2D, adjoint on another grid, envelope present, no maxip
+// output): the rule of flag_kernel_f32x4<true> below with the bilinear
+// stencil.  The interpolated snapshot value of a component is a convex
+// combination of its stencil cells' values, so its magnitude is at most the
+// largest envelope entry M_c over the quads holding the stencil cells with
+// positive weight; a group is skipped where M_e |eta| + M_u |hu| + M_v |hv|
+// < tol (1 - 1e-5).  Flags and count equal the full pass's.
+template <typename R, typename S, bool SAME, bool PRUNE>
 __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
     using A = typename std::conditional<sizeof(R) == 4 && sizeof(S) == 4, float,
                                         double>::type;
     __shared__ Window sw;
     if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
     __syncthreads();
-    const Window w = sw;
+    const Window &w = sw;
     const int cur = p.clk->cur;
     const R *q0 = p.q[cur][0], *q1 = p.q[cur][1], *q2 = p.q[cur][2];
     const size_t n = (size_t)p.nx * p.ny;
@@ -143,42 +170,94 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
 #pragma unroll
         for (int c = 0; c < 4; c++)
             if (wt[c] > A(0) && !p.awet[st[c]]) dry = true;
-        if (!w.empty && !dry) {
-            A dh0 = A(0), dh1 = A(0), dl0 = A(0), dl1 = A(0);
-            for (int k = w.k0; k <= w.k1; k++) {
-                const S *s = p.snaps + (size_t)k * p.snap_stride;
-                A v0, v1, v2 = A(0);
-                if (SAME) {
-                    v0 = (A)s[i];
-                    v1 = (A)s[p.na + i];
-                    if (p.ncomp == 3) v2 = (A)s[2 * p.na + i];
-                } else {
-                    v0 = A(0); v1 = A(0);
+        // PRUNE: a cell at rest (q = 0) has every product zero, m = 0
+        const bool rest = PRUNE && qe == A(0) && qu == A(0) && qv == A(0);
+        if (!w.empty && !dry && !rest) {
+            const bool interp = p.mode != SWA_FLAG_BRACKET;
+            const int gb0 = w.k0 / kEnvGroup, gb1 = w.k1 / kEnvGroup;
+            unsigned mask = 0u;
+            bool need_h = true, need_l = true;
+            if (PRUNE) {
+                const size_t na4 = p.na >> 2;
+                const float tolp = (float)(p.tol * (1.0 - 1e-5));
+                const A ae = fabs(qe), au = fabs(qu), av = fabs(qv);
+                const int ng = gb1 - gb0 + 1 < 32 ? gb1 - gb0 + 1 : 32;
+                for (int j = 0; j < ng; j++) {
+                    const float *eg = p.env + (size_t)(gb0 + j) * 3 * na4;
+                    float Me = 0.f, Mu = 0.f, Mv = 0.f;
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
-                        v0 += wt[c] * (A)s[st[c]];
-                        v1 += wt[c] * (A)s[p.na + st[c]];
-                        if (p.ncomp == 3) v2 += wt[c] * (A)s[2 * p.na + st[c]];
+                        if (!(wt[c] > A(0))) continue;
+                        const size_t q = st[c] >> 2;
+                        Me = fmaxf(Me, __ldg(eg + q));
+                        Mu = fmaxf(Mu, __ldg(eg + na4 + q));
+                        Mv = fmaxf(Mv, __ldg(eg + 2 * na4 + q));
                     }
+                    const float bnd = (float)(Me * ae + Mu * au + Mv * av);
+                    if (bnd < tolp) mask |= 1u << j;
                 }
-                const A d = v0 * qe + v1 * qu + v2 * qv;
-                if (k >= w.ki0 && k <= w.ki1) m = fabs(d) > m ? fabs(d) : m;
-                if (k == w.kh) dh0 = d;
-                if (k == w.kh + 1) dh1 = d;
-                if (k == w.kl) dl0 = d;
-                if (k == w.kl + 1) dl1 = d;
+                // groups past the first 32 of the window are always read
+                auto skipped = [&](int gb) -> bool {
+                    const int jj = gb - gb0;
+                    return jj < 32 && ((mask >> jj) & 1u) != 0u;
+                };
+                if (interp) {
+                    const int kh1 = w.exact_h ? w.kh : w.kh + 1;
+                    const int kl1 = w.exact_l ? w.kl : w.kl + 1;
+                    need_h = !(skipped(w.kh / kEnvGroup) && skipped(kh1 / kEnvGroup));
+                    need_l = !(skipped(w.kl / kEnvGroup) && skipped(kl1 / kEnvGroup));
+                }
             }
-            if (p.mode != SWA_FLAG_BRACKET) {
+            A dh0 = A(0), dh1 = A(0), dl0 = A(0), dl1 = A(0);
+            for (int gb = gb0; gb <= gb1; gb++) {
+                const int jj = gb - gb0;
+                const bool gs = PRUNE && jj < 32 && ((mask >> jj) & 1u) != 0u;
+                const int ka = w.k0 > gb * kEnvGroup ? w.k0 : gb * kEnvGroup;
+                const int kb = w.k1 < gb * kEnvGroup + kEnvGroup - 1 ? w.k1
+                                                                    : gb * kEnvGroup + kEnvGroup - 1;
+                if (gs) {
+                    const bool hh = need_h && w.kh <= kb && w.kh + 1 >= ka;
+                    const bool ll = need_l && w.kl <= kb && w.kl + 1 >= ka;
+                    if (!interp || !(hh || ll)) continue;
+                }
+                for (int k = ka; k <= kb; k++) {
+                    if (gs && !((need_h && (k == w.kh || k == w.kh + 1)) ||
+                                (need_l && (k == w.kl || k == w.kl + 1))))
+                        continue;
+                    const S *s = p.snaps + (size_t)k * p.snap_stride;
+                    A v0, v1, v2 = A(0);
+                    if (SAME) {
+                        v0 = (A)s[i];
+                        v1 = (A)s[p.na + i];
+                        if (p.ncomp == 3) v2 = (A)s[2 * p.na + i];
+                    } else {
+                        v0 = A(0); v1 = A(0);
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            v0 = acc(wt[c], (A)s[st[c]], v0);
+                            v1 = acc(wt[c], (A)s[p.na + st[c]], v1);
+                            if (p.ncomp == 3) v2 = acc(wt[c], (A)s[2 * p.na + st[c]], v2);
+                        }
+                    }
+                    const A d = dot3(v0, qe, v1, qu, v2, qv);
+                    if (k >= w.ki0 && k <= w.ki1) m = fabs(d) > m ? fabs(d) : m;
+                    if (k == w.kh) dh0 = d;
+                    if (k == w.kh + 1) dh1 = d;
+                    if (k == w.kl) dl0 = d;
+                    if (k == w.kl + 1) dl1 = d;
+                }
+            }
+            if (interp) {
                 const A ah = (A)w.ah, al = (A)w.al;
-                const A vh = w.exact_h ? dh0 : ah * dh0 + (A(1) - ah) * dh1;
-                const A vl = w.exact_l ? dl0 : al * dl0 + (A(1) - al) * dl1;
+                const A vh = w.exact_h ? dh0 : lerp2(ah, dh0, A(1) - ah, dh1);
+                const A vl = w.exact_l ? dl0 : lerp2(al, dl0, A(1) - al, dl1);
                 m = fabs(vh) > m ? fabs(vh) : m;
                 m = fabs(vl) > m ? fabs(vl) : m;
             }
         }
         f = (!w.empty && !dry && m >= (A)p.tol) ? 1 : 0;
         p.flags[i] = (uint8_t)f;
-        if (p.maxip) p.maxip[i] = (float)m;
+        if (!PRUNE && p.maxip) p.maxip[i] = (float)m;
     }
     const int cnt = __syncthreads_count(f);
     if (threadIdx.x == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
@@ -394,8 +473,14 @@ int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
             const size_t b = persistent_flag_blocks<false>();
             flag_kernel_f32x4<false><<<(unsigned)(need < b ? need : b), 256, 0, st>>>(pf);
         }
-    } else if (p.same_grid) flag_kernel<R, S, true><<<blocks, 256, 0, st>>>(p);
-    else flag_kernel<R, S, false><<<blocks, 256, 0, st>>>(p);
+    } else if (p.same_grid) {
+        flag_kernel<R, S, true, false><<<blocks, 256, 0, st>>>(p);
+    } else if (sizeof(R) == 4 && sizeof(S) == 4 && p.two_d && p.env && !p.maxip) {
+        flag_kernel<float, float, false, true><<<blocks, 256, 0, st>>>(
+            *reinterpret_cast<const FlagParams<float, float> *>(&p));
+    } else {
+        flag_kernel<R, S, false, false><<<blocks, 256, 0, st>>>(p);
+    }
     return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");
 }
 

@@ -344,6 +344,45 @@ def test_pruned_flag_pass_identical_to_full_pass(S, mode):
     assert checked >= 20
 
 
+def test_pruned_flags_on_a_coarser_adjoint_grid(S):
+    """FP32 forward grid with the adjoint on a coarser grid (bilinear
+    stencil): the envelope-pruned pass equals the full pass bit for bit at
+    several times, windows and tolerances, and matches the oracle."""
+    sc = synth.config2(n=96, L=96e3 * 4, adj_n=40, seed=11)
+    sc.hu0[:] = 0.0
+    sc.hv0[:] = 0.0
+    d = desc_of(S, sc.grid, S.SWA_FP32)
+    ad = desc_of(S, sc.adj_grid, S.SWA_FP32)
+    adj = S.Adjoint(ad, sc.B_adj, sc.phi, sc.t_f)
+    N, dt, _ = adj.info()
+    store = S.SnapStore(adj, N // 5 + 3, S.SWA_FP32)
+    store.run_adjoint(5)
+    g = S.Grid(d, sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    done, checked = 0, 0
+    for target in (10, 60, 140):
+        g.step(target - done, sc.t_f)
+        done = target
+        for t_s in (sc.t_s, 0.95 * sc.t_f, sc.t_f - 0.5 * dt):
+            for mode in (0, 1):
+                (fp, cp, _), (ff, cf, m) = _flags_pruned_and_full(S, g, store, t_s, sc.t_f,
+                                                                    sc.tol, mode)
+                assert np.array_equal(fp, ff) and cp == cf, (target, t_s, mode)
+                pos = m[m > 0]
+                for tol in (np.quantile(pos, [0.1, 0.5, 0.9]) if pos.size else []):
+                    (fp, cp, _), (ff, cf, _) = _flags_pruned_and_full(
+                        S, g, store, t_s, sc.t_f, float(tol), mode)
+                    assert np.array_equal(fp, ff) and cp == cf and cf > 0
+                    checked += 1
+    assert checked >= 12
+    # against the oracle, from the seeded inputs
+    f, _, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP32, 0, sc.t_s, 100,
+                                                 with_m=False)
+    near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
+    assert np.array_equal(f[~near], f_ref[~near])
+    assert f.sum() == c
+
+
 def test_pruned_flags_match_oracle(S):
     """The pruned pass (no m output) against the oracle's flags."""
     sc = synth.small_2d(88, 60, seed=9)
