@@ -281,7 +281,12 @@ def main(argv=None):
     S.load()
     sizes = tuple(int(x) for x in a.sizes.split(","))
     L = 2048e3
-    sc2 = synth.config2(n=256, L=L)  # t_f, t_s, tol and target of the basin workload
+    # tol and target of the basin workload; its time window is the one of the
+    # 1 km grid (t_f = 2000 basin CFL steps of 1 km cells), whatever the
+    # size of the grid built here to read them
+    sc2 = synth.config2(n=256, L=L)
+    sc2.t_f = 2000.0 * 0.75 * 1e3 / np.sqrt(synth.G * 4000.0)
+    sc2.t_s = 0.32 * sc2.t_f
     t0 = time.perf_counter()
     adj = ResidentAdjoint(a.adjoint_n, L, sc2.t_f, sc2.t_s, sc2.tol, sc2.meta["target"])
     torch.cuda.synchronize()
