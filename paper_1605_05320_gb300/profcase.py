@@ -11,7 +11,8 @@ and restores device memory between passes stays small:
   flag  FP32 adjoint-weighted flag passes without the m output (the
         envelope-pruned flag_kernel_f32x4) against a store of one snapshot
         every 100 adjoint steps, ~1.3 GB; `--full` requests m as well, which
-        runs the full pass
+        runs the full pass; `--adj-n 1024` puts the adjoint on a coarser
+        1024^2 grid (the pruned bilinear flag_kernel)
 
 Launch counts (for a profiler's -s / -c): `fwd` runs 1 initial-CFL launch then
 `--steps` step launches; `adj` runs 1 init launch then every adjoint step to
@@ -35,6 +36,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--full", action="store_true")
+    ap.add_argument("--adj-n", type=int, default=0,
+                    help="flag: adjoint on a coarser adj_n^2 grid (bilinear stencil)")
     a = ap.parse_args(argv)
     build.build()
     S.load()
@@ -55,7 +58,12 @@ def main(argv=None):
         out["steps"] = N
         out["snaps"] = st.info()[0]
     else:
-        adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+        ad = d
+        if a.adj_n:
+            sc = synth.config2(n=n, L=n * 1e3, adj_n=a.adj_n)
+            ad = S.make_desc(2, a.adj_n, a.adj_n, 0.0, 0.0, sc.adj_grid.dx, sc.adj_grid.dy,
+                             precision=S.SWA_FP32)
+        adj = S.Adjoint(ad, sc.B_adj, sc.phi, sc.t_f)
         N, _, _ = adj.info()
         st = S.SnapStore(adj, N // 100 + 3, S.SWA_FP32)
         st.run_adjoint(100)
