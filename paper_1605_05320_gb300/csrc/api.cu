@@ -836,6 +836,10 @@ static int flag_dispatch(const swa_grid *g, const swa_snapstore *s, double t_s, 
     const swa_grid_desc &ad = s->adj->d;
     p.anx = ad.nx; p.any = ad.ny;
     p.ax_lo = ad.x_lo; p.ay_lo = ad.y_lo; p.adx = ad.dx; p.ady = ad.dy;
+    p.frx = (float)(g->d.dx / ad.dx);
+    p.fcx = (float)((g->d.x_lo - ad.x_lo) / ad.dx - 0.5);
+    p.fry = (float)(g->d.dy / ad.dy);
+    p.fcy = (float)((g->d.y_lo - ad.y_lo) / ad.dy - 0.5);
     p.same_grid = (ad.nx == g->d.nx && ad.ny == g->d.ny && ad.x_lo == g->d.x_lo &&
                    ad.y_lo == g->d.y_lo && ad.dx == g->d.dx && ad.dy == g->d.dy);
     p.awet = s->wet;

@@ -124,9 +124,10 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
     const int cur = p.clk->cur;
     const R *q0 = p.q[cur][0], *q1 = p.q[cur][1], *q2 = p.q[cur][2];
     const size_t n = (size_t)p.nx * p.ny;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     int f = 0;
-    if (i < n) {
+    // persistent grid: each block walks cells i, i + gridDim.x * 256, ...
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
         A m = A(0);
         const R a = q0[i], b = p.bath[i];
         R h, eta;
@@ -137,7 +138,31 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
         bool dry = !(h > p.dry_tol);
         size_t st[4] = {i, i, i, i};
         A wt[4] = {A(1), A(0), A(0), A(0)};
-        if (!SAME) {
+        if (!SAME && sizeof(A) == 4 && p.two_d) {
+            // FP32 pass: the stencil from the float map (FP64 is a small
+            // fraction of the FP32 rate on this GPU)
+            const int ix = (int)(i % p.nx), jy = (int)(i / p.nx);
+            float fx = fmaf((float)ix + 0.5f, p.frx, p.fcx);
+            fx = fminf(fmaxf(fx, 0.f), (float)(p.anx - 1));
+            int i0 = (int)floorf(fx);
+            if (i0 > p.anx - 2) i0 = p.anx - 2;
+            if (i0 < 0) i0 = 0;
+            float ax = fx - (float)i0;
+            const int i1 = p.anx > 1 ? i0 + 1 : i0;
+            if (p.anx == 1) ax = 0.f;
+            float fy = fmaf((float)jy + 0.5f, p.fry, p.fcy);
+            fy = fminf(fmaxf(fy, 0.f), (float)(p.any - 1));
+            int j0 = (int)floorf(fy);
+            if (j0 > p.any - 2) j0 = p.any - 2;
+            if (j0 < 0) j0 = 0;
+            float ay = fy - (float)j0;
+            const int j1 = p.any > 1 ? j0 + 1 : j0;
+            if (p.any == 1) ay = 0.f;
+            st[0] = (size_t)j0 * p.anx + i0; wt[0] = (A)__fmul_rn(1.f - ax, 1.f - ay);
+            st[1] = (size_t)j0 * p.anx + i1; wt[1] = (A)__fmul_rn(ax, 1.f - ay);
+            st[2] = (size_t)j1 * p.anx + i0; wt[2] = (A)__fmul_rn(1.f - ax, ay);
+            st[3] = (size_t)j1 * p.anx + i1; wt[3] = (A)__fmul_rn(ax, ay);
+        } else if (!SAME) {
             const int ix = (int)(i % p.nx), jy = (int)(i / p.nx);
             const double x = p.x_lo + ((double)ix + 0.5) * p.dx;
             const double y = p.y_lo + ((double)jy + 0.5) * p.dy;
@@ -255,12 +280,14 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
                 m = fabs(vl) > m ? fabs(vl) : m;
             }
         }
-        f = (!w.empty && !dry && m >= (A)p.tol) ? 1 : 0;
-        p.flags[i] = (uint8_t)f;
+        const int fi = (!w.empty && !dry && m >= (A)p.tol) ? 1 : 0;
+        p.flags[i] = (uint8_t)fi;
         if (!PRUNE && p.maxip) p.maxip[i] = (float)m;
+        f += fi;
     }
-    const int cnt = __syncthreads_count(f);
-    if (threadIdx.x == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
+    int cnt = f;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(p.count, (unsigned long long)cnt);
 }
 
 // FP32 forward state and FP32 snapshots on the same grid: the bandwidth-bound
@@ -456,12 +483,28 @@ static size_t persistent_flag_blocks() {
     return (size_t)per_sm * (size_t)sms;
 }
 
+// Blocks of a persistent generic flag pass, per instantiation.
+template <typename R, typename S, bool SAME, bool PRUNE>
+static unsigned generic_flag_blocks(size_t n) {
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flag_kernel<R, S, SAME, PRUNE>,
+                                                      256, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (sms < 1) sms = 1;
+    }
+    const size_t need = (n + 255) / 256, b = (size_t)per_sm * (size_t)sms;
+    return (unsigned)(need < b ? need : b);
+}
+
 template <typename R, typename S>
 int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
     const size_t n = (size_t)p.nx * p.ny;
     cudaError_t e = cudaMemsetAsync(p.count, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return swadj_host::cuda_check(e, "flag count reset");
-    const unsigned blocks = (unsigned)((n + 255) / 256);
     if (sizeof(R) == 4 && sizeof(S) == 4 && p.same_grid && p.two_d && (n & 3) == 0) {
         const size_t n4 = n >> 2;
         const FlagParams<float, float> &pf = *reinterpret_cast<const FlagParams<float, float> *>(&p);
@@ -474,12 +517,15 @@ int flag_launch(const FlagParams<R, S> &p, cudaStream_t st) {
             flag_kernel_f32x4<false><<<(unsigned)(need < b ? need : b), 256, 0, st>>>(pf);
         }
     } else if (p.same_grid) {
-        flag_kernel<R, S, true, false><<<blocks, 256, 0, st>>>(p);
+        flag_kernel<R, S, true, false>
+            <<<generic_flag_blocks<R, S, true, false>(n), 256, 0, st>>>(p);
     } else if (sizeof(R) == 4 && sizeof(S) == 4 && p.two_d && p.env && !p.maxip) {
-        flag_kernel<float, float, false, true><<<blocks, 256, 0, st>>>(
-            *reinterpret_cast<const FlagParams<float, float> *>(&p));
+        flag_kernel<float, float, false, true>
+            <<<generic_flag_blocks<float, float, false, true>(n), 256, 0, st>>>(
+                *reinterpret_cast<const FlagParams<float, float> *>(&p));
     } else {
-        flag_kernel<R, S, false, false><<<blocks, 256, 0, st>>>(p);
+        flag_kernel<R, S, false, false>
+            <<<generic_flag_blocks<R, S, false, false>(n), 256, 0, st>>>(p);
     }
     return swadj_host::cuda_check(cudaGetLastError(), "flag_kernel");
 }

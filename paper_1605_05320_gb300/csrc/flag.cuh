@@ -17,6 +17,10 @@ struct FlagParams {
     // adjoint grid and snapshots
     int anx, any, same_grid;
     double ax_lo, ay_lo, adx, ady;
+    // the same map in float for the FP32 pass: the adjoint-grid coordinate
+    // of forward cell i (in cell widths, from the first centre) is
+    // (i + 1/2) * frx + fcx; exact in float when the grids align
+    float frx, fcx, fry, fcy;
     const uint8_t *awet;     // 1 where the adjoint cell is wet
     const S *snaps;          // [K][ncomp][na]
     size_t snap_stride;      // ncomp * na
