@@ -542,3 +542,38 @@ def test_fused_gauge_recording_matches_per_step_sampling(S, precision):
     g2.step(2, 1e300)
     assert S.swa_grid_gauge_rows(g2.h) == 0
     assert S.swa_sync_status() == 0
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (29, 2), (5, 31), (33, 3)])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_degenerate_grids_forward_and_adjoint(S, nx, ny, bc):
+    """Grids narrower than a warp strip and only a few rows high: every
+    strip lane and row beyond the grid is index-mapped to a ghost cell.
+    FP64 forward and adjoint within 1e-12 of the oracle, the FP32 forward
+    within the perturbation-form tolerance after 40 steps, the FP32 adjoint
+    within 2e-5 of each component's maximum."""
+    sc = synth.small_2d(nx, ny, seed=40 + nx + ny, L=nx * 5e3)
+    st, t, n = run_gpu_forward(S, sc, S.SWA_FP64, 2, bc, 40)
+    h, hu, hv, t_ref, n_ref = run_oracle_forward(sc, 2, bc, 40)
+    assert n == n_ref == 40 and abs(t - t_ref) <= 1e-12 * t_ref
+    for got, ref in ((st["h"], h), (st["hu"], hu), (st["hv"], hv)):
+        assert np.abs(got - ref).max() <= 1e-12 * max(np.abs(ref).max(), 1.0)
+    st32, t32, n32 = run_gpu_forward(S, sc, S.SWA_FP32, 2, bc, 40)
+    Bf = bath_seen(sc.B, True)
+    h, hu, hv, _, _ = run_oracle_forward(sc, 2, bc, 40, B=Bf)
+    assert n32 == 40
+    assert np.abs(st32["eta"] - (h + Bf)).max() <= 1e-5
+    assert np.abs(st32["hu"] - hu).max() <= 1e-4 * max(np.abs(hu).max(), 1.0)
+    assert np.abs(st32["hv"] - hv).max() <= 1e-4 * max(np.abs(hv).max(), 1.0)
+    adj, store, (N, dt, K, tau), (snaps, tau_ref, N_ref, dt_ref) = \
+        _adjoint_pair(S, sc, S.SWA_FP64, 5, bc)
+    assert N == N_ref and np.array_equal(tau, tau_ref)
+    got = _read_snaps(S, store, S.SWA_FP64, 3, sc.adj_grid.n)
+    assert np.abs(got - snaps).max() <= 1e-12 * max(np.abs(snaps).max(), 1.0)
+    adj32, store32, (N32, _, _, tau32), _ = _adjoint_pair(S, sc, S.SWA_FP32, 5, bc)
+    assert N32 == N_ref and np.array_equal(tau32, tau_ref)
+    got32 = _read_snaps(S, store32, S.SWA_FP32, 3, sc.adj_grid.n)
+    for c in range(3):
+        assert np.abs(got32[:, c] - snaps[:, c]).max() <= \
+            2e-5 * max(np.abs(snaps[:, c]).max(), 1e-30) + 1e-30
+    assert S.swa_sync_status() == 0
