@@ -577,3 +577,22 @@ def test_degenerate_grids_forward_and_adjoint(S, nx, ny, bc):
         assert np.abs(got32[:, c] - snaps[:, c]).max() <= \
             2e-5 * max(np.abs(snaps[:, c]).max(), 1e-30) + 1e-30
     assert S.swa_sync_status() == 0
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 5), (4, 3), (29, 2), (33, 3), (8, 6)])
+def test_degenerate_grids_flags(S, nx, ny):
+    """Flag passes on grids of a few cells (cell counts that are and are not
+    multiples of 4 take the generic and the 4-cell kernels), against the
+    oracle in FP64 and FP32, pruned (no m output) in FP32."""
+    sc = synth.small_2d(nx, ny, seed=60 + nx + ny, L=nx * 5e3)
+    sc.tol = 1e-7
+    f, m, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP64, 0, 0.32 * sc.t_f, 20)
+    near = np.abs(m_ref - sc.tol) <= 1e-6 * sc.tol
+    assert np.array_equal(f[~near], f_ref[~near]) and f.sum() == c
+    assert np.abs(m - m_ref).max() <= 1e-6 * max(m_ref.max(), 1e-30)
+    for with_m in (True, False):
+        f, m, c, f_ref, m_ref, c_ref = _flag_compare(S, sc, S.SWA_FP32, 0, 0.32 * sc.t_f, 20,
+                                                     with_m=with_m)
+        near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
+        assert np.array_equal(f[~near], f_ref[~near]) and f.sum() == c
+    assert c_ref > 0
