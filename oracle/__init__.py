@@ -24,6 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 BC_EXTRAP, BC_WALL = 0, 1
 FLAG_INTERP, FLAG_BRACKET = 0, 1
+SCHEME_SPLIT, SCHEME_CTU = 0, 1   # 2D forward step: split, unsplit with transverse waves
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,8 @@ class _Grid(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("order", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("g", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("dry_tol", ctypes.c_double), ("lin_nu", ctypes.c_double * 2)]
+                ("dry_tol", ctypes.c_double), ("lin_nu", ctypes.c_double * 2),
+                ("scheme", ctypes.c_int), ("tw_scale", ctypes.c_double)]
 
 
 @dataclass
@@ -61,6 +63,8 @@ class Grid:
     g: float = 9.81
     cfl: float = 0.75
     dry_tol: float = 1e-3
+    scheme: int = SCHEME_SPLIT
+    tw_scale: float = 1.0   # transverse terms; tests set 0 / -1 to plant a mistake
 
     @property
     def n(self):
@@ -74,6 +78,7 @@ class Grid:
         for k in range(4):
             s.bc[k] = int(self.bc[k])
         s.g, s.cfl, s.dry_tol = self.g, self.cfl, self.dry_tol
+        s.scheme, s.tw_scale = int(self.scheme), float(self.tw_scale)
         return s
 
     @classmethod
@@ -94,6 +99,10 @@ def _load():
         G = ctypes.POINTER(_Grid)
         lib.orc_fwd_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
         lib.orc_fwd_step.restype = ctypes.c_int
+        lib.orc_fwd_step_ctu.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
+        lib.orc_fwd_step_ctu.restype = ctypes.c_int
+        lib.orc_ctu_tsplit.argtypes = [ctypes.c_double] * 3 + [_D, _D, _D]
+        lib.orc_ctu_tsplit.restype = None
         lib.orc_fwd_smax.argtypes = [G, _D, _D, _D]
         lib.orc_fwd_smax.restype = ctypes.c_double
         lib.orc_fwd_run.argtypes = [G, _D, _D, _D, _D, ctypes.c_long,
@@ -154,6 +163,14 @@ def fwd_step(grid: Grid, h, hu, hv, B, dt):
     if rc:
         raise FloatingPointError(f"oracle forward step unstable ({rc})")
     return h, hu, hv
+
+
+def ctu_tsplit(uhat, vhat, chat, a):
+    """Transverse split of a fluctuation a (edge frame) -> (bm, bp)."""
+    a = _f64(a).copy()
+    bm, bp = np.zeros(3), np.zeros(3)
+    _load().orc_ctu_tsplit(float(uhat), float(vhat), float(chat), _p(a), _p(bm), _p(bp))
+    return bm, bp
 
 
 def fwd_smax(grid: Grid, h, hu, hv):

@@ -18,6 +18,12 @@
  *                    second-order corrections (order 2); in 2D dimensionally
  *                    split: an x-sweep over every row, then a y-sweep over
  *                    every column of the x-swept state.
+ *   orc_fwd_step_ctu the unsplit 2D alternative (scheme 1): the
+ *                    wave-propagation update of the textbook the paper defers
+ *                    to for its methods (LeVeque 2002, the multidimensional
+ *                    chapters, cited in Sec. 6): x- and y-edge waves all from
+ *                    Q^n, MC-limited corrections, and transverse propagation
+ *                    of each fluctuation into the neighbouring edge fluxes.
  *   orc_fwd_smax     CFL number max over cells of max_dir (|u|+c)/d_dir.
  *   orc_lin_step     first-order update of Eq. (hyp_linear) (and its 2D form,
  *                    Sec. 5, x-sweep then y-sweep), used only by the
@@ -58,6 +64,10 @@ typedef struct {
     int bc[4];          /* x_lo, x_hi, y_lo, y_hi */
     double g, cfl, dry_tol;
     double lin_nu[2];   /* internal: dt/dx, dt/dy of the linear sweeps */
+    int scheme;         /* 2D forward step: 0 split, 1 unsplit with transverse waves */
+    double tw_scale;    /* factor on the transverse terms: 1 for the method; the
+                           tests set 0 or -1 to show their pins catch a dropped
+                           or sign-flipped term */
 } orc_grid;
 
 #define NG 2
@@ -143,6 +153,7 @@ static double dot3(const double *a, const double *b) {
 typedef struct {
     double s[3];
     double Z[3][3];
+    double uhat, vhat, chat;   /* Roe state of the forward solve (edge frame) */
 } edge_waves;
 
 /*
@@ -207,6 +218,7 @@ static void fwd_riemann(double g,
     double b3 = (df2 - s1 * df1) / (s3 - s1);
     double b2 = df3 - vhat * df1;
     w->s[0] = s1; w->s[1] = s2; w->s[2] = s3;
+    w->uhat = uhat; w->vhat = vhat; w->chat = chat;
     w->Z[0][0] = b1;  w->Z[0][1] = b1 * s1;  w->Z[0][2] = b1 * vhat;
     w->Z[1][0] = 0.0; w->Z[1][1] = 0.0;      w->Z[1][2] = b2;
     w->Z[2][0] = b3;  w->Z[2][1] = b3 * s3;  w->Z[2][2] = b3 * vhat;
@@ -266,16 +278,200 @@ static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double 
     free(ph); free(pu); free(pv); free(pB); free(nh); free(nu_); free(nv);
 }
 
+/* ------------------------------------------ unsplit step (scheme 1, 2D) */
+
+/*
+ * Ghost-padded copy with the corner ghosts filled too: fill_padded sets the
+ * interior and the side ghosts, then the x rule is applied to every ghost
+ * row, so a corner ghost takes both mappings and both sign factors (the
+ * unsplit update reads the corner cells through its transverse terms).
+ */
+static void fill_padded_corners(const orc_grid *G, const double *a, double *p,
+                                double sign_x, double sign_y) {
+    int nx = G->nx, ny = G->ny;
+    fill_padded(G, a, p, sign_x, sign_y);
+    for (int j = -NG; j < ny + NG; j++) {
+        if (j >= 0 && j < ny) continue;
+        for (int k = 1; k <= NG; k++) {
+            if (G->bc[0] == BC_WALL) p[pidx(G, -k, j)] = sign_x * p[pidx(G, k - 1, j)];
+            else p[pidx(G, -k, j)] = p[pidx(G, 0, j)];
+            if (G->bc[1] == BC_WALL) p[pidx(G, nx - 1 + k, j)] = sign_x * p[pidx(G, nx - k, j)];
+            else p[pidx(G, nx - 1 + k, j)] = p[pidx(G, nx - 1, j)];
+        }
+    }
+}
+
+/*
+ * Transverse splitting of a fluctuation a (edge frame: h, normal momentum,
+ * tangential momentum) into its parts moving with negative (bm) and positive
+ * (bp) speed along the tangential direction.  It uses the eigenstructure of
+ * the tangential flux Jacobian at the edge's Roe state (uhat normal and vhat
+ * tangential velocity, chat = sqrt(g hhat)): speeds vhat - chat, vhat,
+ * vhat + chat with vectors (1, uhat, vhat - chat), (0, 1, 0),
+ * (1, uhat, vhat + chat).  a = sum_p beta_p r_p; bm/bp = sum of
+ * speed_p beta_p r_p over the negative/positive speeds.
+ */
+void orc_ctu_tsplit(double uhat, double vhat, double chat, const double a[3],
+                    double bm[3], double bp[3]) {
+    double mu[3] = {vhat - chat, vhat, vhat + chat};
+    double r[3][3] = {{1.0, uhat, vhat - chat}, {0.0, 1.0, 0.0}, {1.0, uhat, vhat + chat}};
+    double beta[3];
+    beta[0] = ((vhat + chat) * a[0] - a[2]) / (2.0 * chat);
+    beta[1] = a[1] - uhat * a[0];
+    beta[2] = (a[2] - (vhat - chat) * a[0]) / (2.0 * chat);
+    for (int m = 0; m < 3; m++) { bm[m] = 0.0; bp[m] = 0.0; }
+    for (int p = 0; p < 3; p++) {
+        double c = mu[p] * beta[p];
+        for (int m = 0; m < 3; m++) {
+            if (mu[p] < 0.0) bm[m] += c * r[p][m];
+            else if (mu[p] > 0.0) bp[m] += c * r[p][m];
+        }
+    }
+}
+
+/* waves of the edge between padded cells a and b, in the frame of dir */
+static void ctu_edge(const orc_grid *G, int dir, const double *ph, const double *pu,
+                     const double *pv, const double *pB, size_t a, size_t b,
+                     edge_waves *w) {
+    if (dir == 0)
+        fwd_riemann(G->g, ph[a], pu[a], pv[a], pB[a], ph[b], pu[b], pv[b], pB[b], w);
+    else
+        fwd_riemann(G->g, ph[a], pv[a], pu[a], pB[a], ph[b], pv[b], pu[b], pB[b], w);
+}
+
+/* padded index of cell (i, j) shifted by s along dir and by t across it */
+static size_t ctu_at(const orc_grid *G, int dir, int i, int j, int s, int t) {
+    return dir == 0 ? pidx(G, i + s, j + t) : pidx(G, i + t, j + s);
+}
+
+/*
+ * For cell (i, j) and direction dir (0: x, 1: y), in dir's edge frame:
+ * the fluctuations entering the cell through its low edge (ap_lo) and its
+ * high edge (am_hi), and the low/high edge fluxes: the limited correction
+ * minus k times the transverse parts, coming from the other direction, of
+ * the four fluctuations that enter the cells beside the edge and move
+ * towards it.  k = tw_scale * nu_other / 2.
+ */
+static void ctu_dir(const orc_grid *G, int dir, const double *ph, const double *pu,
+                    const double *pv, const double *pB, int i, int j, double nu,
+                    double k, double ap_lo[3], double am_hi[3], double F_lo[3],
+                    double F_hi[3]) {
+    int o = 1 - dir;   /* the other direction */
+    edge_waves w[4];
+    for (int e = 0; e < 4; e++)
+        ctu_edge(G, dir, ph, pu, pv, pB, ctu_at(G, dir, i, j, e - 2, 0),
+                 ctu_at(G, dir, i, j, e - 1, 0), &w[e]);
+    double am_lo[3], ap_hi[3];
+    edge_fluxes(3, &w[0], &w[1], &w[2], nu, G->order, am_lo, ap_lo, F_lo);
+    edge_fluxes(3, &w[1], &w[2], &w[3], nu, G->order, am_hi, ap_hi, F_hi);
+    /*
+     * Fluctuations of the other direction's edges of the cells at offsets
+     * s = -1, 0, +1 along dir (frame of o): fl[s+1][0] enters the cell at s
+     * through its low o-edge, fl[s+1][1] through its high o-edge.  Their
+     * transverse split (along dir) with the o-edge's Roe state: the part
+     * moving in -dir reaches the cell's low dir-edge, the part in +dir its
+     * high dir-edge.
+     */
+    double tr_lo[3] = {0.0, 0.0, 0.0}, tr_hi[3] = {0.0, 0.0, 0.0};
+    for (int s = -1; s <= 1; s++) {
+        edge_waves a[3];
+        for (int e = 0; e < 3; e++)
+            ctu_edge(G, o, ph, pu, pv, pB, ctu_at(G, dir, i, j, s, e - 1),
+                     ctu_at(G, dir, i, j, s, e), &a[e]);
+        double amL[3], apL[3], FL[3], amH[3], apH[3], FH[3];
+        edge_fluxes(3, &a[0], &a[0], &a[1], nu, 1, amL, apL, FL);   /* low o-edge */
+        edge_fluxes(3, &a[1], &a[1], &a[2], nu, 1, amH, apH, FH);   /* high o-edge */
+        double pm[2][3], pp[2][3];
+        orc_ctu_tsplit(a[0].uhat, a[0].vhat, a[0].chat, apL, pm[0], pp[0]);
+        orc_ctu_tsplit(a[1].uhat, a[1].vhat, a[1].chat, amH, pm[1], pp[1]);
+        /* back to dir's frame: components 1 and 2 exchange */
+        for (int q = 0; q < 2; q++) {
+            if (s == -1) {         /* cell below the low edge: +dir part */
+                tr_lo[0] += pp[q][0]; tr_lo[1] += pp[q][2]; tr_lo[2] += pp[q][1];
+            } else if (s == 0) {   /* the cell itself: -dir part low, +dir part high */
+                tr_lo[0] += pm[q][0]; tr_lo[1] += pm[q][2]; tr_lo[2] += pm[q][1];
+                tr_hi[0] += pp[q][0]; tr_hi[1] += pp[q][2]; tr_hi[2] += pp[q][1];
+            } else {               /* cell above the high edge: -dir part */
+                tr_hi[0] += pm[q][0]; tr_hi[1] += pm[q][2]; tr_hi[2] += pm[q][1];
+            }
+        }
+    }
+    for (int m = 0; m < 3; m++) {
+        F_lo[m] = F_lo[m] - k * tr_lo[m];
+        F_hi[m] = F_hi[m] - k * tr_hi[m];
+    }
+}
+
+/*
+ * One unsplit forward step of size dt (2D), in place on (h, hu, hv).  Every
+ * x- and y-edge Riemann problem is solved from Q^n; with nu_x = dt/dx and
+ * nu_y = dt/dy,
+ *   Q_ij += -nu_x (A+dQ_{i-1/2,j} + A-dQ_{i+1/2,j}) - nu_x (F_{i+1/2,j} - F_{i-1/2,j})
+ *           -nu_y (B+dQ_{i,j-1/2} + B-dQ_{i,j+1/2}) - nu_y (G_{i,j+1/2} - G_{i,j-1/2})
+ * where an edge flux is its MC-limited correction minus (nu_other / 2) times
+ * the transverse parts of the fluctuations described at ctu_dir, e.g.
+ *   G_{i,j-1/2} = C_{i,j-1/2} - (nu_x/2) [B+A+dQ_{i-1/2,j-1} + B+A-dQ_{i+1/2,j-1}
+ *                                        + B-A+dQ_{i-1/2,j} + B-A-dQ_{i+1/2,j}].
+ * The sums run in the order written there (x-frame cell offsets -1, 0, +1;
+ * low edge before high edge).  Returns 0, or -5 on a non-positive or
+ * non-finite depth.
+ */
+int orc_fwd_step_ctu(const orc_grid *G, double *h, double *hu, double *hv,
+                     const double *B, double dt) {
+    int nx = G->nx, ny = G->ny;
+    size_t n = (size_t)nx * ny;
+    double *ph = padded(G), *pu = padded(G), *pv = padded(G), *pB = padded(G);
+    fill_padded_corners(G, h, ph, 1.0, 1.0);
+    fill_padded_corners(G, hu, pu, -1.0, 1.0);
+    fill_padded_corners(G, hv, pv, 1.0, -1.0);
+    fill_padded_corners(G, B, pB, 1.0, 1.0);
+    double *nh = (double *)malloc(n * sizeof(double));
+    double *nu_ = (double *)malloc(n * sizeof(double));
+    double *nv = (double *)malloc(n * sizeof(double));
+    double nux = dt / G->dx, nuy = dt / G->dy;
+    double kx = G->tw_scale * (0.5 * nuy);   /* on F: transverse parts of y-fluctuations */
+    double ky = G->tw_scale * (0.5 * nux);   /* on G: transverse parts of x-fluctuations */
+
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; j++) {
+        for (int i = 0; i < nx; i++) {
+            size_t c = pidx(G, i, j);
+            double apL[3], amR[3], FL[3], FR[3];
+            double bpB[3], bmT[3], GB[3], GT[3];
+            ctu_dir(G, 0, ph, pu, pv, pB, i, j, nux, kx, apL, amR, FL, FR);
+            ctu_dir(G, 1, ph, pu, pv, pB, i, j, nuy, ky, bpB, bmT, GB, GT);
+            double dx_[3], dy_[3];   /* x frame and y frame */
+            for (int m = 0; m < 3; m++) {
+                dx_[m] = -nux * (apL[m] + amR[m]) - nux * (FR[m] - FL[m]);
+                dy_[m] = -nuy * (bpB[m] + bmT[m]) - nuy * (GT[m] - GB[m]);
+            }
+            size_t o = (size_t)j * nx + i;
+            nh[o] = (ph[c] + dx_[0]) + dy_[0];
+            nu_[o] = (pu[c] + dx_[1]) + dy_[2];
+            nv[o] = (pv[c] + dx_[2]) + dy_[1];
+        }
+    }
+    memcpy(h, nh, n * sizeof(double));
+    memcpy(hu, nu_, n * sizeof(double));
+    memcpy(hv, nv, n * sizeof(double));
+    free(ph); free(pu); free(pv); free(pB); free(nh); free(nu_); free(nv);
+    int bad = 0;
+    for (size_t k = 0; k < n; k++)
+        if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(hv[k])) bad = 1;
+    return bad ? -5 : 0;
+}
+
 /*
  * One forward step of size dt, in place on (h, hu, hv): in 1D a single
  * x-sweep; in 2D an x-sweep of the whole grid, then a y-sweep of the x-swept
- * state (dimensional splitting).  hv may be NULL for ndim == 1 (treated as
- * zero and not written).  Returns 0, or -5 when a non-positive or
+ * state (dimensional splitting); with scheme 1 a 2D step is orc_fwd_step_ctu.
+ * hv may be NULL for ndim == 1 (treated as zero and not written).  Returns 0, or -5 when a non-positive or
  * non-finite depth appears.
  */
 int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
                  const double *B, double dt) {
     size_t n = (size_t)G->nx * G->ny;
+    if (G->ndim == 2 && G->scheme == 1 && hv) return orc_fwd_step_ctu(G, h, hu, hv, B, dt);
     double *v = hv;
     if (!hv) v = (double *)calloc(n, sizeof(double));
     fwd_sweep(G, 0, h, hu, v, B, dt);
