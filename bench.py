@@ -272,6 +272,38 @@ def compare_flags(scen, tstream):
                        for i, nm in enumerate(names)}}
 
 
+def compare_schemes(scen, stream, steps=100):
+    """Outside the timed region: the basin's 2D forward step under both
+    updates (dimensionally split, the scenario's; unsplit with transverse
+    waves), each on a fresh grid from the scenario's initial state, 3 warm-up
+    launches, then `steps` launches between CUDA events on the launching
+    stream.  The state (28 B per cell in FP32) fits in L2 here; both are
+    timed alike."""
+    S, torch = scen.S, scen.torch
+    hs = stream.cuda_stream
+    w = 4 if scen.p == S.SWA_FP32 else 8
+    out = {"steps": steps}
+    for name, scheme in (("split", S.SWA_SCHEME_SPLIT), ("ctu", S.SWA_SCHEME_CTU)):
+        g = S.Grid(scen.desc, scen.sc.B)
+        g.set_scheme(scheme)
+        g.set_state(scen.eta_d, scen.hu_d, scen.hv_d, 0.0, hs)
+        g.step(3, 1e12, hs)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(steps, 1e12, hs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / steps
+        out[name] = {"us_per_step": round(us, 2),
+                     "cell_updates_per_s": scen.n / (us * 1e-6),
+                     "hbm_gbs_algorithmic": round(7 * w * scen.n / (us * 1e-6) / 1e9, 1)}
+        del g
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("device status nonzero after the scheme comparison")
+    return out
+
+
 def cell_updates(sc_obj):
     return (sc_obj.n_fwd * sc_obj.n + sc_obj.N_adj * sc_obj.adj.n)
 
@@ -481,6 +513,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         with torch.cuda.stream(stream):
             out["flag_comparison"] = compare_flags(scen, stream)
+            out["forward_schemes"] = compare_schemes(scen, stream)
     return out
 
 

@@ -144,6 +144,29 @@ int swa_get_time(swa_grid *grid, double *t, double *dt_next,
 int swa_grid_set_strip_rows(swa_grid *grid, int rows);
 
 /*
+ * The 2D update that swa_step_forward applies.  The paper defers the theory
+ * of its finite volume methods to LeVeque (2002) (Sec. 6); both are that
+ * book's wave-propagation methods:
+ *   SWA_SCHEME_SPLIT (default): dimensionally split, as described above.
+ *   SWA_SCHEME_CTU: unsplit.  Every x- and y-edge Riemann problem is solved
+ *     from Q^n; each cell takes the fluctuations and the limited-correction
+ *     flux differences of its four edges, where an edge's flux also carries,
+ *     with weight -dt / (2 d_other), the transverse parts of the four
+ *     fluctuations of the other direction that enter the cells beside the
+ *     edge and move towards it (split by the tangential flux Jacobian at
+ *     their own edge's Roe state).  Second-order accurate for smooth flow
+ *     and stable for Courant numbers up to 1 in each direction.
+ * The CFL rule, the clock and gauges are the same for both.  1D grids accept
+ * either (the updates coincide there); patch sets always use the split step.
+ * Returns SWA_EINVAL for another value.  The FP64 unsplit step rounds like
+ * the FP64 reference of the same scheme; FP32 grids keep the perturbation
+ * form (eta, hu, hv).
+ */
+#define SWA_SCHEME_SPLIT 0
+#define SWA_SCHEME_CTU 1
+int swa_grid_set_scheme(swa_grid *grid, int scheme);
+
+/*
  * Device pointers of the current state arrays (read-only use), for gauge or
  * diagnostic kernels of the caller.  Synchronises (the current buffer is
  * device-resident).  precision tells the element type (double or float).

@@ -171,6 +171,7 @@ struct swa_grid {
     int step_blocks;
     int state_set;
     int strip_rows;        // FP32 launch shape (0 = default)
+    int scheme;            // 2D update: SWA_SCHEME_SPLIT or SWA_SCHEME_CTU
     long long *gauge_row;  // device row counter of the fused gauge recording
     GaugeRec gauges;       // fused gauge recording (n = 0: off)
 };
@@ -186,14 +187,23 @@ static int grid_step_blocks(const swa_grid_desc *d) {
     return fwd_step_blocks<float>(p);
 }
 
-// Reduction slots for the smallest strip height the FP32 kernel accepts.
+// Reduction slots for the smallest strip height the FP32 kernel accepts, or
+// for the unsplit step's tiles if there are more of those.
 static int grid_max_blocks(const swa_grid_desc *d) {
-    if (d->precision == SWA_FP32 && d->ndim == 2) {
+    int b = grid_step_blocks(d);
+    if (d->ndim != 2) return b;
+    int c;
+    if (d->precision == SWA_FP32) {
         FwdParams<float> p{};
         p.nx = d->nx; p.ny = d->ny; p.two_d = 1; p.fwd_rows = SWA_MIN_STRIP_ROWS;
-        return fwd_step_blocks<float>(p);
+        b = fwd_step_blocks<float>(p);
+        c = fwd_ctu_blocks<float>(p);
+    } else {
+        FwdParams<double> p{};
+        p.nx = d->nx; p.ny = d->ny; p.two_d = 1;
+        c = fwd_ctu_blocks<double>(p);
     }
-    return grid_step_blocks(d);
+    return b > c ? b : c;
 }
 
 static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
@@ -391,12 +401,15 @@ int swa_step_forward(swa_grid *g, int max_steps, double t_end, void *stream) {
     if (max_steps < 0) return set_error(SWA_EINVAL, "max_steps < 0");
     if (!g->state_set) return set_error(SWA_ESTATE, "state not set");
     cudaStream_t st = S(stream);
+    const bool ctu = g->scheme == SWA_SCHEME_CTU && g->d.ndim == 2;
     if (g->d.precision == SWA_FP64) {
         const FwdParams<double> p = fwd_params<double>(g, t_end);
-        for (int k = 0; k < max_steps; k++) TRY(fwd_launch_step<double>(p, st));
+        for (int k = 0; k < max_steps; k++)
+            TRY(ctu ? fwd_launch_ctu<double>(p, st) : fwd_launch_step<double>(p, st));
     } else {
         const FwdParams<float> p = fwd_params<float>(g, t_end);
-        for (int k = 0; k < max_steps; k++) TRY(fwd_launch_step<float>(p, st));
+        for (int k = 0; k < max_steps; k++)
+            TRY(ctu ? fwd_launch_ctu<float>(p, st) : fwd_launch_step<float>(p, st));
     }
     return SWA_OK;
 }
@@ -418,6 +431,14 @@ int swa_grid_set_strip_rows(swa_grid *g, int rows) {
     if (rows != 0 && rows != 16 && rows != 32 && rows != 64)
         return set_error(SWA_EINVAL, "strip rows must be 0, 16, 32 or 64");
     g->strip_rows = rows;
+    return SWA_OK;
+}
+
+int swa_grid_set_scheme(swa_grid *g, int scheme) {
+    if (!g) return set_error(SWA_EINVAL, "null grid");
+    if (scheme != SWA_SCHEME_SPLIT && scheme != SWA_SCHEME_CTU)
+        return set_error(SWA_EINVAL, "scheme must be SWA_SCHEME_SPLIT or SWA_SCHEME_CTU");
+    g->scheme = scheme;
     return SWA_OK;
 }
 

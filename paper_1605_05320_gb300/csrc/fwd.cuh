@@ -34,6 +34,15 @@ template <> int fwd_launch_step<double>(const FwdParams<double> &, cudaStream_t)
 template <> int fwd_launch_step<float>(const FwdParams<float> &, cudaStream_t);
 template <> int fwd_step_blocks<double>(const FwdParams<double> &);
 template <> int fwd_step_blocks<float>(const FwdParams<float> &);
+// unsplit 2D step with transverse waves (ctu_kernels.cuh)
+template <typename R>
+int fwd_launch_ctu(const FwdParams<R> &p, cudaStream_t st);
+template <typename R>
+int fwd_ctu_blocks(const FwdParams<R> &p);
+template <> int fwd_launch_ctu<double>(const FwdParams<double> &, cudaStream_t);
+template <> int fwd_launch_ctu<float>(const FwdParams<float> &, cudaStream_t);
+template <> int fwd_ctu_blocks<double>(const FwdParams<double> &);
+template <> int fwd_ctu_blocks<float>(const FwdParams<float> &);
 template <> int fwd_launch_clock_init<double>(const FwdParams<double> &, double, cudaStream_t);
 template <> int fwd_launch_clock_init<float>(const FwdParams<float> &, double, cudaStream_t);
 

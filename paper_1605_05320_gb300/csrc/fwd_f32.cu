@@ -10,6 +10,7 @@
 // fwd_edge.cuh); 1D grids run a one-thread-per-cell kernel.  The CFL maximum
 // is reduced in float (max is exact); the last block to finish turns it into
 // the next time step in double.
+#include "ctu_kernels.cuh"
 #include "strips.cuh"
 
 namespace swadj {
@@ -180,6 +181,16 @@ int fwd_step_blocks<float>(const FwdParams<float> &p) {
         return strip_blocks(p.nx, p.ny, req ? req : 16) + 1;   // + the gauge block
     }
     return (p.nx + 255) / 256;
+}
+
+template <>
+int fwd_launch_ctu<float>(const FwdParams<float> &p, cudaStream_t st) {
+    return ctu_launch<float, true, 32, 8>(p, st, "fwd_ctu_kernel<float>");
+}
+
+template <>
+int fwd_ctu_blocks<float>(const FwdParams<float> &p) {
+    return ctu_blocks<32, 8>(p.nx, p.ny);
 }
 
 template <>

@@ -5,7 +5,7 @@
 // 4000 m depth (4.5e-13 m) already moves the momentum by ~1e-11 per step
 // through g*hhat*(eta_R - eta_L); matching rounding is what keeps the FP64
 // path within 1e-12 of the reference after thousands of steps.
-#include "fwd_kernels.cuh"
+#include "ctu_kernels.cuh"
 
 namespace swadj {
 
@@ -27,6 +27,16 @@ template <>
 int fwd_step_blocks<double>(const FwdParams<double> &p) {
     if (p.two_d) return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
     return (p.nx + 127) / 128;
+}
+
+template <>
+int fwd_launch_ctu<double>(const FwdParams<double> &p, cudaStream_t st) {
+    return ctu_launch<double, false, 16, 8>(p, st, "fwd_ctu_kernel<double>");
+}
+
+template <>
+int fwd_ctu_blocks<double>(const FwdParams<double> &p) {
+    return ctu_blocks<16, 8>(p.nx, p.ny);
 }
 
 template <>

@@ -6,6 +6,8 @@ than the full scenario (no 101-snapshot store), so that a capture that saves
 and restores device memory between passes stays small:
 
   fwd   FP32 forward steps (fwd_f32_strips), ~120 MB on the device
+  ctu   FP32 unsplit forward steps with transverse waves (fwd_ctu_kernel),
+        ~120 MB
   adj   the full FP32 adjoint run (adj_f32_strips, ~2000 launches) with a
         fused snapshot every 100 steps, ~1.3 GB
   flag  FP32 adjoint-weighted flag passes without the m output (the
@@ -14,8 +16,8 @@ and restores device memory between passes stays small:
         runs the full pass; `--adj-n 1024` puts the adjoint on a coarser
         1024^2 grid (the pruned bilinear flag_kernel)
 
-Launch counts (for a profiler's -s / -c): `fwd` runs 1 initial-CFL launch then
-`--steps` step launches; `adj` runs 1 init launch then every adjoint step to
+Launch counts (for a profiler's -s / -c): `fwd` and `ctu` run 1 initial-CFL
+launch then `--steps` step launches; `adj` runs 1 init launch then every adjoint step to
 t_f; `flag` runs `--steps` flag passes after its set-up launches.
 
     python -m paper_1605_05320_gb300.profcase fwd --steps 120
@@ -32,7 +34,7 @@ def main(argv=None):
     from . import swadj as S
     from . import synth
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["fwd", "adj", "flag"])
+    ap.add_argument("kernel", choices=["fwd", "ctu", "adj", "flag"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--full", action="store_true")
@@ -45,8 +47,10 @@ def main(argv=None):
     sc = synth.config2(n=n, L=n * 1e3)
     d = S.make_desc(2, n, n, 0.0, 0.0, sc.grid.dx, sc.grid.dy, precision=S.SWA_FP32)
     out = {}
-    if a.kernel == "fwd":
+    if a.kernel in ("fwd", "ctu"):
         g = S.Grid(d, sc.B)
+        if a.kernel == "ctu":
+            g.set_scheme(S.SWA_SCHEME_CTU)
         g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
         g.step(a.steps, sc.t_f)
         out["t"] = g.time()[0]

@@ -25,6 +25,7 @@ SWA_FP64, SWA_FP32 = 0, 1
 SWA_BC_EXTRAP, SWA_BC_WALL = 0, 1
 SWA_FLAG_INTERP, SWA_FLAG_BRACKET = 0, 1
 SWA_HOST, SWA_DEVICE = 0, 1
+SWA_SCHEME_SPLIT, SWA_SCHEME_CTU = 0, 1
 
 # Every symbol declared in include/swadj.h.
 EXPORTS = [
@@ -32,6 +33,7 @@ EXPORTS = [
     "swa_grid_workspace_bytes", "swa_create_grid", "swa_destroy_grid",
     "swa_set_state", "swa_get_state", "swa_step_forward", "swa_get_time",
     "swa_grid_set_strip_rows",
+    "swa_grid_set_scheme",
     "swa_grid_arrays",
     "swa_adjoint_workspace_bytes", "swa_create_adjoint", "swa_destroy_adjoint",
     "swa_adjoint_info", "swa_step_adjoint", "swa_get_adjoint_state",
@@ -114,6 +116,7 @@ def load(path: str = LIB_PATH):
         "swa_get_time": ([_V, _P(_D), _P(_D), _P(ctypes.c_longlong), _V], _I),
         "swa_grid_arrays": ([_V, _P(_V), _P(_V), _P(_V), _P(_V), _V], _I),
         "swa_grid_set_strip_rows": ([_V, _I], _I),
+        "swa_grid_set_scheme": ([_V, _I], _I),
         "swa_adjoint_workspace_bytes": ([D], _SZ),
         "swa_create_adjoint": ([D, _V, _V, _D, _V, _SZ, _V, _P(_V)], _I),
         "swa_destroy_adjoint": ([_V], _I),
@@ -232,6 +235,10 @@ def swa_get_time(h, stream=None):
 
 def swa_grid_set_strip_rows(h, rows):
     return _chk(load().swa_grid_set_strip_rows(h, int(rows)))
+
+
+def swa_grid_set_scheme(h, scheme):
+    return _chk(load().swa_grid_set_scheme(h, int(scheme)))
 
 
 def swa_grid_arrays(h, stream=None):
@@ -452,6 +459,9 @@ class Grid:
 
     def step(self, max_steps, t_end, stream=None):
         swa_step_forward(self.h, max_steps, t_end, stream)
+
+    def set_scheme(self, scheme):
+        swa_grid_set_scheme(self.h, scheme)
 
     def time(self, stream=None):
         return swa_get_time(self.h, stream)

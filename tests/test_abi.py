@@ -92,6 +92,7 @@ def test_launch_shape_and_gauge_calls_check_their_arguments(lib):
     """Argument checks that need no GPU: null handles and strip heights the
     kernels do not offer are rejected before anything is enqueued."""
     assert lib.swa_grid_set_strip_rows(None, 32) == S.SWA_EINVAL
+    assert lib.swa_grid_set_scheme(None, S.SWA_SCHEME_CTU) == S.SWA_EINVAL
     assert lib.swa_patches_set_tile_rows(None, 1, 32) == S.SWA_EINVAL
     assert lib.swa_grid_record_gauges(None, 2, None, None, None, 10, None) == S.SWA_EINVAL
     rows = ctypes.c_longlong()
