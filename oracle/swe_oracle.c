@@ -366,13 +366,15 @@ static void ctu_dir(const orc_grid *G, int dir, const double *ph, const double *
     edge_fluxes(3, &w[1], &w[2], &w[3], nu, G->order, am_hi, ap_hi, F_hi);
     /*
      * Fluctuations of the other direction's edges of the cells at offsets
-     * s = -1, 0, +1 along dir (frame of o): fl[s+1][0] enters the cell at s
-     * through its low o-edge, fl[s+1][1] through its high o-edge.  Their
-     * transverse split (along dir) with the o-edge's Roe state: the part
-     * moving in -dir reaches the cell's low dir-edge, the part in +dir its
-     * high dir-edge.
+     * s = -1, 0, +1 along dir (frame of o): the one entering the cell at s
+     * through its low o-edge and the one entering through its high o-edge.
+     * Their transverse split (along dir) uses the o-edge's Roe state; per
+     * cell, P sums the parts moving in +dir (they reach the cell's high
+     * dir-edge) and M the parts moving in -dir (its low dir-edge), each in
+     * dir's frame (components 1 and 2 exchanged).  An edge's transverse term
+     * is P of the cell below it plus M of the cell above it.
      */
-    double tr_lo[3] = {0.0, 0.0, 0.0}, tr_hi[3] = {0.0, 0.0, 0.0};
+    double P[3][3], M[3][3];
     for (int s = -1; s <= 1; s++) {
         edge_waves a[3];
         for (int e = 0; e < 3; e++)
@@ -384,17 +386,16 @@ static void ctu_dir(const orc_grid *G, int dir, const double *ph, const double *
         double pm[2][3], pp[2][3];
         orc_ctu_tsplit(a[0].uhat, a[0].vhat, a[0].chat, apL, pm[0], pp[0]);
         orc_ctu_tsplit(a[1].uhat, a[1].vhat, a[1].chat, amH, pm[1], pp[1]);
-        /* back to dir's frame: components 1 and 2 exchange */
-        for (int q = 0; q < 2; q++) {
-            if (s == -1) {         /* cell below the low edge: +dir part */
-                tr_lo[0] += pp[q][0]; tr_lo[1] += pp[q][2]; tr_lo[2] += pp[q][1];
-            } else if (s == 0) {   /* the cell itself: -dir part low, +dir part high */
-                tr_lo[0] += pm[q][0]; tr_lo[1] += pm[q][2]; tr_lo[2] += pm[q][1];
-                tr_hi[0] += pp[q][0]; tr_hi[1] += pp[q][2]; tr_hi[2] += pp[q][1];
-            } else {               /* cell above the high edge: -dir part */
-                tr_hi[0] += pm[q][0]; tr_hi[1] += pm[q][2]; tr_hi[2] += pm[q][1];
-            }
+        static const int sw[3] = {0, 2, 1};
+        for (int m = 0; m < 3; m++) {
+            P[s + 1][m] = pp[0][sw[m]] + pp[1][sw[m]];
+            M[s + 1][m] = pm[0][sw[m]] + pm[1][sw[m]];
         }
+    }
+    double tr_lo[3], tr_hi[3];
+    for (int m = 0; m < 3; m++) {
+        tr_lo[m] = P[0][m] + M[1][m];
+        tr_hi[m] = P[1][m] + M[2][m];
     }
     for (int m = 0; m < 3; m++) {
         F_lo[m] = F_lo[m] - k * tr_lo[m];
@@ -412,9 +413,9 @@ static void ctu_dir(const orc_grid *G, int dir, const double *ph, const double *
  * the transverse parts of the fluctuations described at ctu_dir, e.g.
  *   G_{i,j-1/2} = C_{i,j-1/2} - (nu_x/2) [B+A+dQ_{i-1/2,j-1} + B+A-dQ_{i+1/2,j-1}
  *                                        + B-A+dQ_{i-1/2,j} + B-A-dQ_{i+1/2,j}].
- * The sums run in the order written there (x-frame cell offsets -1, 0, +1;
- * low edge before high edge).  Returns 0, or -5 on a non-positive or
- * non-finite depth.
+ * The four transverse terms of an edge are summed as (the two from the cell
+ * below) + (the two from the cell above), each pair low o-edge first.
+ * Returns 0, or -5 on a non-positive or non-finite depth.
  */
 int orc_fwd_step_ctu(const orc_grid *G, double *h, double *hu, double *hv,
                      const double *B, double dt) {
