@@ -185,12 +185,12 @@ int fwd_step_blocks<float>(const FwdParams<float> &p) {
 
 template <>
 int fwd_launch_ctu<float>(const FwdParams<float> &p, cudaStream_t st) {
-    return ctu_launch<float, true, 32, 8>(p, st, "fwd_ctu_kernel<float>");
+    return ctu_launch<float, true, 32, 16>(p, st, "fwd_ctu_kernel<float>");
 }
 
 template <>
 int fwd_ctu_blocks<float>(const FwdParams<float> &p) {
-    return ctu_blocks<32, 8>(p.nx, p.ny);
+    return ctu_blocks<32, 16>(p.nx, p.ny);
 }
 
 template <>
