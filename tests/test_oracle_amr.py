@@ -1,0 +1,212 @@
+"""Pins of the oracle's two-level AMR glue (oracle/amr.py): ring fills from
+siblings and from the coarse level (linear in time, limited-linear in space),
+r fine substeps per coarse step, averaging down.
+
+- r = 1: the hierarchy is the single grid, whatever the patches (overlapping,
+  adjacent, apart);
+- the ocean at rest stays exactly at rest for r = 2 and 4 over a bottom
+  sampled separately on each level;
+- a patch cut in two (the cut filled from the sibling) gives the patch;
+- refining a patch brings its region closer to a uniformly fine run than the
+  coarse grid alone; piecewise-constant coarse fills, or fills frozen at the
+  coarse step's start or end (mistakes planted in a subclass) do not.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.amr import RING, Hierarchy, Patch, fine_grid
+
+DX = 10e3
+H0 = 130.0
+
+
+def bottom(x, y):
+    return -100.0 - 20.0 * np.sin(x / 7e4) * np.cos(y / 9e4)
+
+
+def hump(x, y, L):
+    return 0.5 * np.exp(-((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2) / (3 * DX) ** 2)
+
+
+def fields(n, d):
+    x = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(x, x)
+    return X, Y
+
+
+def build(nc, r, patches, cls=Hierarchy, rest=False, seed=None):
+    """Coarse nc^2 basin with walls, fine patches sampled on the global fine
+    grid (so patches agree wherever they overlap), a hump at the centre."""
+    cg = O.Grid(2, nc, nc, 0.0, 0.0, DX, DX, order=2, bc=(1, 1, 1, 1))
+    L = nc * DX
+    X, Y = fields(nc, DX)
+    Bc = bottom(X, Y).ravel()
+    ec = np.zeros(nc * nc) if rest else hump(X, Y, L).ravel()
+    XF, YF = fields(nc * r, DX / r)
+    BF, EF = bottom(XF, YF), (np.zeros_like(XF) if rest else hump(XF, YF, L))
+    uc = np.zeros(nc * nc)
+    UF = np.zeros_like(XF)
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        uc = rng.uniform(-5, 5, nc * nc)
+        assert r == 1
+        UF = uc.reshape(nc, nc)
+    Bf, fine = [], []
+    for p in patches:
+        g = fine_grid(cg, p, r)
+        I0, J0 = p.i0 * r - RING, p.j0 * r - RING
+        sl = lambda a: a[J0:J0 + g.ny, I0:I0 + g.nx].ravel().copy()
+        Bf.append(sl(BF))
+        fine.append((sl(EF) - sl(BF), sl(UF), -sl(UF)))
+    H = cls(cg, Bc, patches, r, Bf)
+    H.set_state(ec - Bc, uc, -uc, fine, 0.0)
+    return H, cg, Bc, ec, BF, EF, uc
+
+
+def dt_coarse(cg):
+    return 0.6 * cg.cfl * cg.dx / np.sqrt(9.81 * H0)
+
+
+def test_ratio_one_is_the_single_grid():
+    patches = [Patch(5, 6, 6, 5), Patch(9, 8, 5, 7), Patch(14, 3, 4, 4)]
+    H, cg, Bc, ec, _, _, uc = build(24, 1, patches, seed=1)
+    h, hu, hv = ec - Bc, uc.copy(), -uc
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(10):
+        assert H.step(t, dt)
+        h, hu, hv = O.fwd_step(cg, h, hu, hv, Bc, (t + dt) - t)
+        t = t + dt
+    for a, b in ((H.h, h), (H.hu, hu), (H.hv, hv)):
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+    assert H.t_c == H.t_f == t
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_ocean_at_rest_stays_at_rest(r):
+    H, cg, Bc, *_ = build(16, r, [Patch(4, 4, 5, 6), Patch(7, 8, 4, 4)], rest=True)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(4):
+        assert H.step(t, dt)
+        t = t + dt
+    assert np.all(H.h + Bc == 0.0) and np.all(H.hu == 0) and np.all(H.hv == 0)
+    for f, b in zip(H.fine, H.Bf):
+        assert np.all(f[0] + b == 0.0) and np.all(f[1] == 0) and np.all(f[2] == 0)
+
+
+def test_a_patch_cut_in_two_gives_the_patch():
+    one, cg, *_ = build(24, 2, [Patch(8, 8, 8, 8)])
+    two, *_ = build(24, 2, [Patch(8, 8, 3, 8), Patch(11, 8, 5, 8)])
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(6):
+        assert one.step(t, dt) and two.step(t, dt)
+        t = t + dt
+    scale = np.abs(one.h + one.B).max()
+    assert np.abs((one.h - two.h)).max() <= 1e-12 * scale
+    assert np.abs(one.hu - two.hu).max() <= 1e-12 * np.abs(one.hu).max()
+    # the fine cells of the halves equal the whole patch's
+    g1 = one.grids[0]
+    for k, p in enumerate(two.patches):
+        g = two.grids[k]
+        for j in range(RING, g.ny - RING):
+            row1 = (j * g1.nx) + (p.i0 - 8) * 2
+            a = two.fine[k][0][j * g.nx + RING:(j + 1) * g.nx - RING]
+            b = one.fine[0][0][row1 + RING:row1 + RING + g.nx - 2 * RING]
+            assert np.abs(a - b).max() <= 1e-12 * 130.0
+
+
+def region_errors(r, steps, cls=Hierarchy, p=Patch(8, 8, 8, 8)):
+    """Max |eta - eta_fine| over the patch's coarse cells for the hierarchy
+    and for the coarse grid alone; eta_fine is a uniformly fine run averaged
+    to coarse cells."""
+    nc = 24
+    H, cg, Bc, ec, BF, EF, _ = build(nc, r, [p], cls=cls)
+    dt, t = dt_coarse(cg), 0.0
+    h, hu, hv = ec - Bc, 0 * ec, 0 * ec
+    for _ in range(steps):
+        assert H.step(t, dt)
+        h, hu, hv = O.fwd_step(cg, h, hu, hv, Bc, (t + dt) - t)
+        t = t + dt
+    fg = O.Grid(2, nc * r, nc * r, 0.0, 0.0, DX / r, DX / r, order=2, bc=(1, 1, 1, 1))
+    fh, fu, fv = (EF - BF).ravel(), 0 * EF.ravel(), 0 * EF.ravel()
+    for _ in range(steps * r):
+        fh, fu, fv = O.fwd_step(fg, fh, fu, fv, BF.ravel(), dt / r)
+    ref = (fh + BF.ravel()).reshape(nc, r, nc, r).mean(axis=(1, 3)).ravel()
+    m = np.zeros((nc, nc), bool)
+    m[p.j0:p.j0 + p.my, p.i0:p.i0 + p.mx] = True
+    m = m.ravel()
+    return np.abs(H.h + Bc - ref)[m].max(), np.abs(h + Bc - ref)[m].max()
+
+
+@pytest.mark.parametrize("r,steps,factor", [(2, 4, 0.3), (2, 12, 0.7), (4, 4, 0.5)])
+def test_refinement_moves_the_patch_towards_the_fine_solution(r, steps, factor):
+    amr, coarse = region_errors(r, steps)
+    assert amr < factor * coarse, (amr, coarse)
+
+
+class ConstantFill(Hierarchy):
+    """Planted mistake: coarse fills without the limited slopes."""
+
+    def fill(self, old, t_n, dt_c):
+        r, nxc = self.r, self.coarse.nx
+        a = min(max((self.t_f - t_n) / dt_c, 0.0), 1.0)
+        for k, (p, g) in enumerate(zip(self.patches, self.grids)):
+            fh, fu, fv = self.fine[k]
+            for j in range(g.ny):
+                for i in range(g.nx):
+                    if RING <= i < g.nx - RING and RING <= j < g.ny - RING:
+                        continue
+                    c = ((p.j0 * r - RING + j) // r) * nxc + (p.i0 * r - RING + i) // r
+                    o = j * g.nx + i
+                    eo, en = old[0][c] + self.B[c], self.h[c] + self.B[c]
+                    fh[o] = eo + a * (en - eo) - self.Bf[k][o]
+                    fu[o] = old[1][c] + a * (self.hu[c] - old[1][c])
+                    fv[o] = old[2][c] + a * (self.hv[c] - old[2][c])
+
+
+class FrozenStart(Hierarchy):
+    """Planted mistake: coarse fills always from the coarse step's start."""
+
+    def fill(self, old, t_n, dt_c):
+        t = self.t_f
+        self.t_f = t_n
+        super().fill(old, t_n, dt_c)
+        self.t_f = t
+
+
+class FrozenEnd(Hierarchy):
+    """Planted mistake: coarse fills always from the coarse step's end."""
+
+    def fill(self, old, t_n, dt_c):
+        t = self.t_f
+        self.t_f = t_n + dt_c
+        super().fill(old, t_n, dt_c)
+        self.t_f = t
+
+
+@pytest.mark.parametrize("cls", [ConstantFill, FrozenStart, FrozenEnd])
+def test_planted_fill_mistakes_lose_accuracy(cls):
+    # a small patch around the hump, which the waves leave within the run:
+    # what crosses its ring decides its accuracy
+    p = Patch(10, 10, 4, 4)
+    good, coarse = region_errors(4, 6, p=p)
+    bad = region_errors(4, 6, cls=cls, p=p)[0]
+    assert good < 0.5 * coarse, (good, coarse)
+    assert bad > 1.5 * good, (good, bad)
+
+
+def test_time_interpolation_at_mid_step():
+    """Halfway through a coarse step, a coarse-filled ring cell on a flat
+    field holds the mean of the coarse cell's old and new values."""
+    H, cg, Bc, *_ = build(12, 2, [Patch(4, 4, 4, 4)], rest=True)
+    old = (H.h.copy(), H.hu.copy(), H.hv.copy())
+    H.h = H.h + 0.25      # eta rises by 0.25 m everywhere
+    H.hu = H.hu + 3.0
+    H.t_f = 50.0
+    H.fill(old, 0.0, 100.0)
+    f, b = H.fine[0], H.Bf[0]
+    ring = np.ones(H.grids[0].n, bool)
+    g = H.grids[0]
+    ring.reshape(g.ny, g.nx)[RING:-RING, RING:-RING] = False
+    np.testing.assert_allclose((f[0] + b)[ring], 0.125, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(f[1][ring], 1.5, rtol=0, atol=1e-12)
