@@ -304,6 +304,80 @@ def compare_schemes(scen, stream, steps=100):
     return out
 
 
+def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
+    """Outside the timed region: the two-level AMR glue on the basin.  The
+    coarse level is the 2048^2 basin (1 km cells); the fine level is
+    tiles x tiles patches of side x side coarse cells refined by `ratio`,
+    tiling a square around the source (the basin fields sampled at 250 m).
+    Times `steps` hierarchy steps (coarse step, `ratio` fine substeps each
+    with its ring fill, averaging down) after 3 warm-up steps, and the coarse
+    step and the fine launch on their own, with CUDA events on the stream."""
+    import torch
+    from paper_1605_05320_gb300 import swadj as S
+    from paper_1605_05320_gb300 import synth
+    n, dx = 2048, 1e3
+    hs = stream.cuda_stream
+    B, eta = synth.patch_fields((1, 0.0, 0.0, n, n, dx, dx))
+    d = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=S.SWA_FP32)
+    src_i, src_j = 700, 1024                       # the source of the basin fields, in km
+    i0, j0 = src_i - tiles * side // 2, src_j - tiles * side // 2
+    dxf = dx / ratio
+    descs = []
+    for b in range(tiles):
+        for a in range(tiles):
+            pi, pj = i0 + a * side, j0 + b * side
+            descs.append((1, pi * dx - 2 * dxf, pj * dx - 2 * dxf, side * ratio + 4,
+                          side * ratio + 4, dxf, dxf))
+    fields = [synth.patch_fields(q) for q in descs]
+    fine_cells = sum(q[3] * q[4] for q in descs)
+    dt_c = 0.9 * 0.75 * dx / np.sqrt(9.81 * float(np.max(-B)))
+
+    def hierarchy():
+        g = S.Grid(d, B)
+        g.set_state(eta, np.zeros(n * n), np.zeros(n * n), 0.0, hs)
+        ps = S.PatchSet(descs, [f[0] for f in fields], d, stream=hs)
+        for k, f in enumerate(fields):
+            z = np.zeros_like(f[1])
+            ps.set_state(k, f[1], z, z, hs)
+        ps.start(1, 0.0, hs)
+        return g, ps, S.Amr(g, ps, 1, ratio, stream=hs)
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / k
+
+    g, ps, amr = hierarchy()
+    clock = {"t": 0.0}
+
+    def one_step():
+        amr.step(clock["t"], dt_c, 1, hs)
+        clock["t"] = clock["t"] + dt_c
+
+    for _ in range(3):
+        one_step()
+    us_step = timed(one_step, steps)
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("AMR hierarchy step reported an error")
+    g2, ps2, _ = hierarchy()
+    us_coarse = timed(lambda: g2.step(1, 1e12, hs), steps)
+    us_fine = timed(lambda: ps2.step(1, 1, 1e300, hs), steps * ratio)
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("device status nonzero after the AMR measurement")
+    updates = n * n + ratio * fine_cells
+    return {"coarse": f"{n}^2, {dx:g} m cells", "patches": len(descs), "ratio": ratio,
+            "fine_cells": fine_cells, "steps": steps,
+            "us_per_step": round(us_step, 1), "coarse_step_us": round(us_coarse, 1),
+            "fine_launch_us": round(us_fine, 1),
+            "glue_us_per_step": round(us_step - us_coarse - ratio * us_fine, 1),
+            "cell_updates_per_s": updates / (us_step * 1e-6)}
+
+
 def cell_updates(sc_obj):
     return (sc_obj.n_fwd * sc_obj.n + sc_obj.N_adj * sc_obj.adj.n)
 
@@ -514,6 +588,7 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             out["flag_comparison"] = compare_flags(scen, stream)
             out["forward_schemes"] = compare_schemes(scen, stream)
+            out["amr"] = measure_amr(stream)
     return out
 
 

@@ -82,7 +82,8 @@ const char *swa_last_error(void);
 
 /*
  * Synchronise `stream`, then read and clear the device error word shared by
- * all objects on the current device.  Returns SWA_OK or SWA_EUNSTABLE.
+ * all objects on the current device.  Returns SWA_OK, SWA_EUNSTABLE, or
+ * SWA_ESTATE after an AMR step whose levels fell short of its end time.
  */
 int swa_sync_status(void *stream);
 
@@ -358,6 +359,47 @@ int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches,
 /* Strip height of the level's kernel in rows: 16 or 32 (0 = default 32).
  * Results do not depend on it; throughput does (the autotuner picks it). */
 int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
+
+/* ========================= two-level AMR glue =============================
+ * One coarse grid (FP32, 2D) and one level of fine patches of a patch set,
+ * refined by an integer ratio r in space and in time: the AMR hierarchy the
+ * paper's runs use (Sec. 1, Sec. 6), one coarse level deep.
+ *
+ * Fine patches carry a 2-cell ring: a patch whose interior is mx x my
+ * coarse cells with lower-left coarse cell (i0, j0) is described with
+ * nx = mx r + 4, ny = my r + 4, dx = coarse dx / r, dy = coarse dy / r,
+ * x_lo = coarse x_lo + i0 dx_coarse - 2 dx, y_lo likewise, and its ring must
+ * lie inside the coarse domain.  The level step updates ring cells like any
+ * other (they enter the level's CFL maximum); the fill before each launch
+ * overwrites them.  Set the fine patches' states (ring included) and start
+ * the level at the coarse grid's time before the first step.
+ *
+ * swa_amr_step(amr, t_n, dt_c, m, stream), all stream-ordered, no host sync:
+ *   1. the coarse grid steps to t_n + dt_c (dt_c must not exceed its CFL
+ *      step, so that it takes exactly one);
+ *   2. the fine level takes r substeps, the k-th ending at
+ *      t_n + dt_c k / r, with m launches each (launches past the substep's
+ *      end are no-ops).  Before every launch each ring cell is filled: from
+ *      the lowest-index other patch of the level whose interior holds it,
+ *      else from the coarse level, linearly in time between the coarse
+ *      states at t_n and t_n + dt_c (alpha = (t - t_n) / dt_c in [0, 1],
+ *      eta and both momenta), then piecewise linearly in space within the
+ *      coarse cell holding it, with minmod slopes (zero at the domain edge);
+ *   3. every coarse cell under a patch interior (lowest patch index) takes
+ *      the mean of its r x r fine cells (eta and both momenta).
+ * If either level ends the step short of t_n + dt_c (the coarse CFL step
+ * was below dt_c, or m launches did not reach a substep's end), the next
+ * swa_sync_status returns SWA_ESTATE.
+ */
+typedef struct swa_amr swa_amr;
+size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
+                               int ratio);
+/* Checks the geometry (SWA_EINVAL) and uploads the fill and average maps.
+ * coarse and fine must outlive the hierarchy. */
+int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
+                   size_t ws_bytes, void *stream, swa_amr **out);
+int swa_destroy_amr(swa_amr *amr);
+int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
 
 /* ======================= allocation-free forward step =====================
  * The paper has no counterpart to this entry point; it is an integration aid.

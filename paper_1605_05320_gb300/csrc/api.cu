@@ -231,6 +231,17 @@ static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
     }
 }
 
+int swadj::grid_refs(const swa_grid *g, GridRefs *out) {
+    if (!g || !out) return set_error(SWA_EINVAL, "null grid");
+    out->d = g->d;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) out->q[b][k] = g->q[b][k];
+    out->bath = g->bath;
+    out->clk = g->clk;
+    out->state_set = g->state_set;
+    return SWA_OK;
+}
+
 template <typename R>
 static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     FwdParams<R> p{};
@@ -267,6 +278,8 @@ int swa_sync_status(void *stream) {
     TRY(cuda_check(cudaStreamSynchronize(st), "error word"));
     if (err & ERR_UNSTABLE)
         return set_error(SWA_EUNSTABLE, "device saw a non-finite state or depth <= 0");
+    if (err & ERR_LAG)
+        return set_error(SWA_ESTATE, "an AMR step ended before its levels reached its end time");
     return SWA_OK;
 }
 

@@ -472,3 +472,288 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows) {
 }
 
 }  // extern "C"
+
+// ======================================================= two-level AMR glue
+//
+// One coarse grid (FP32, 2D) and one level of fine patches refined by an
+// integer ratio r in space and time (the AMR hierarchy of Sec. 1, Sec. 6).
+// Each fine patch carries a 2-cell ring as ordinary cells; the level step
+// updates the ring like any cell (it enters only the level's CFL maximum)
+// and the fill before the next launch overwrites it.  The maps below are
+// built on the host at creation from the patch geometry:
+//   fill: per ring cell (patch, cell, source).  Source: the lowest-index
+//         other patch whose interior holds the cell (patch, cell), else the
+//         coarse cell containing it and the fine cell's position inside it.
+//   avg:  per coarse cell under a patch interior (lowest patch index): the
+//         patch and the index of its first fine cell.
+namespace swadj {
+namespace amr {
+
+constexpr int kRing = 2;
+
+using patches::PatchDevice;
+using patches::ew_blocks;
+
+struct AmrParams {
+    const PatchDevice *table;
+    const DevClock *lclk, *cclk;   // fine level, coarse grid
+    float *cq[2][3];               // coarse state buffers (eta, hu, hv)
+    int nxc, nyc, r;
+    const int4 *fill;
+    int nfill;
+    const int4 *avg;
+    int navg;
+    double t_n, dt_c, t_end;
+    int *err;
+};
+
+__device__ __forceinline__ float minmod(float a, float b) {
+    if (a * b <= 0.f) return 0.f;
+    return fabsf(a) < fabsf(b) ? a : b;
+}
+
+// Ring fill at the fine level's current time: sibling copy, or the coarse
+// level linear in time (alpha = (t - t_n) / dt_c in [0, 1]) then limited
+// linear in space within the coarse cell (minmod slopes, zero at the domain
+// edge).  Map entry (patch, cell, src, idx): src >= 0 is a sibling patch
+// and idx its cell; src < 0 is the coarse cell idx, with the fine cell at
+// (-src - 1) = sx + r sy inside it.
+__global__ void amr_fill_kernel(AmrParams p) {
+    volatile const DevClock *lc = p.lclk, *cc = p.cclk;
+    const int fcur = lc->cur, ccur = cc->cur;
+    double a = (lc->t - p.t_n) / p.dt_c;
+    a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+    const float af = (float)a;
+    const int r = p.r, nxc = p.nxc, nyc = p.nyc;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nfill; e += gridDim.x * blockDim.x) {
+        const int4 m = p.fill[e];
+        const PatchDevice &D = p.table[m.x];
+        if (m.z >= 0) {
+            const PatchDevice &S = p.table[m.z];
+#pragma unroll
+            for (int k = 0; k < 3; k++) D.q[fcur][k][m.y] = S.q[fcur][k][m.w];
+            continue;
+        }
+        const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
+        const int c = m.w, ic = c % nxc, jc = c / nxc;
+        const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
+        const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float *o = p.cq[ccur ^ 1][k], *n = p.cq[ccur][k];
+            auto at = [&](int i) { return fmaf(af, n[i] - o[i], o[i]); };
+            const float qc = at(c);
+            float s_x = 0.f, s_y = 0.f;
+            if (ic > 0 && ic < nxc - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
+            if (jc > 0 && jc < nyc - 1) s_y = minmod(qc - at(c - nxc), at(c + nxc) - qc);
+            D.q[fcur][k][m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
+        }
+    }
+}
+
+// Coarse cells under a patch := mean of their r x r fine cells (eta, hu, hv).
+// Entry (coarse cell, patch, first fine cell, 0).  Also checks that both
+// levels reached the step's end time.
+__global__ void amr_avg_kernel(AmrParams p) {
+    volatile const DevClock *lc = p.lclk, *cc = p.cclk;
+    const int fcur = lc->cur, ccur = cc->cur;
+    const int r = p.r;
+    const float inv = 1.f / (float)(r * r);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.navg; e += gridDim.x * blockDim.x) {
+        const int4 m = p.avg[e];
+        const PatchDevice &S = p.table[m.y];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float *f = S.q[fcur][k] + m.z;
+            float s = 0.f;
+            for (int jj = 0; jj < r; jj++)
+                for (int ii = 0; ii < r; ii++) s += f[jj * S.nx + ii];
+            p.cq[ccur][k][m.x] = s * inv;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double tol = 1e-12 * (fabs(p.t_end) > 1.0 ? fabs(p.t_end) : 1.0);
+        if (!(fabs(lc->t - p.t_end) <= tol) || !(fabs(cc->t - p.t_end) <= tol))
+            atomicOr(p.err, ERR_LAG);
+    }
+}
+
+// Geometry of one fine patch in global fine cells: array column 0 at
+// (I0, J0); interior [I0 + 2, I0 + nx - 2) x [J0 + 2, J0 + ny - 2).
+struct FineBox {
+    long long I0, J0;
+    int nx, ny;
+    bool interior(long long I, long long J) const {
+        return I >= I0 + kRing && I < I0 + nx - kRing && J >= J0 + kRing && J < J0 + ny - kRing;
+    }
+};
+
+// Check the hierarchy and build the maps (host).
+int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
+               std::vector<int4> &fill, std::vector<int4> &avg) {
+    const swa_grid_desc &d = c.d;
+    if (d.ndim != 2 || d.precision != SWA_FP32)
+        return set_error(SWA_EINVAL, "the coarse grid must be 2D FP32");
+    if (r < 1 || r > 64) return set_error(SWA_EINVAL, "ratio must be in [1, 64]");
+    if (level < 1 || level > SWA_MAX_LEVELS || ps->lev[level].npatches == 0)
+        return set_error(SWA_EINVAL, "level %d has no patches", level);
+    std::vector<int> ids;
+    std::vector<FineBox> box;
+    const double dxf = d.dx / r, dyf = d.dy / r;
+    for (int k = 0; k < ps->n; k++) {
+        const swa_patch_desc &q = ps->pd[k];
+        if (q.level != level) continue;
+        if (fabs(q.dx - dxf) > 1e-9 * dxf || fabs(q.dy - dyf) > 1e-9 * dyf)
+            return set_error(SWA_EINVAL, "patch %d: cell size is not the coarse size / %d", k, r);
+        // interior lower-left on a coarse cell corner
+        const double fi = (q.x_lo + kRing * q.dx - d.x_lo) / d.dx;
+        const double fj = (q.y_lo + kRing * q.dy - d.y_lo) / d.dy;
+        const long long i0 = llround(fi), j0 = llround(fj);
+        if (fabs(fi - (double)i0) > 1e-6 || fabs(fj - (double)j0) > 1e-6)
+            return set_error(SWA_EINVAL, "patch %d: interior not on coarse cell corners", k);
+        if (q.nx <= 2 * kRing || q.ny <= 2 * kRing || (q.nx - 2 * kRing) % r != 0 ||
+            (q.ny - 2 * kRing) % r != 0)
+            return set_error(SWA_EINVAL, "patch %d: interior not whole coarse cells", k);
+        FineBox b{i0 * r - kRing, j0 * r - kRing, q.nx, q.ny};
+        if (b.I0 < 0 || b.J0 < 0 || b.I0 + b.nx > (long long)d.nx * r ||
+            b.J0 + b.ny > (long long)d.ny * r)
+            return set_error(SWA_EINVAL, "patch %d: its ring leaves the coarse domain", k);
+        ids.push_back(k);
+        box.push_back(b);
+    }
+    const int np = (int)ids.size();
+    fill.clear();
+    avg.clear();
+    for (int a = 0; a < np; a++) {
+        const FineBox &b = box[a];
+        for (int j = 0; j < b.ny; j++)
+            for (int i = 0; i < b.nx; i++) {
+                if (i >= kRing && i < b.nx - kRing && j >= kRing && j < b.ny - kRing) continue;
+                const long long I = b.I0 + i, J = b.J0 + j;
+                int4 m = make_int4(ids[a], j * b.nx + i, 0, 0);
+                int src = -1;
+                for (int q = 0; q < np && src < 0; q++)
+                    if (q != a && box[q].interior(I, J)) src = q;
+                if (src >= 0) {
+                    const FineBox &s = box[src];
+                    m.z = ids[src];
+                    m.w = (int)((J - s.J0) * s.nx + (I - s.I0));
+                } else {
+                    const long long ic = I / r, jc = J / r;
+                    m.z = -1 - (int)((I - ic * r) + r * (J - jc * r));
+                    m.w = (int)(jc * d.nx + ic);
+                }
+                fill.push_back(m);
+            }
+    }
+    std::vector<char> taken((size_t)d.nx * d.ny, 0);
+    for (int a = 0; a < np; a++) {
+        const FineBox &b = box[a];
+        const long long i0 = (b.I0 + kRing) / r, j0 = (b.J0 + kRing) / r;
+        const int mx = (b.nx - 2 * kRing) / r, my = (b.ny - 2 * kRing) / r;
+        for (int jc = 0; jc < my; jc++)
+            for (int ic = 0; ic < mx; ic++) {
+                const size_t c = (size_t)(j0 + jc) * d.nx + (size_t)(i0 + ic);
+                if (taken[c]) continue;
+                taken[c] = 1;
+                avg.push_back(make_int4((int)c, ids[a],
+                                        (kRing + jc * r) * b.nx + kRing + ic * r, 0));
+            }
+    }
+    return SWA_OK;
+}
+
+}  // namespace amr
+}  // namespace swadj
+
+struct swa_amr {
+    swa_grid *coarse = nullptr;
+    swa_patchset *fine = nullptr;
+    int level = 0, r = 1;
+    int4 *fill = nullptr, *avg = nullptr;
+    int nfill = 0, navg = 0;
+};
+
+extern "C" {
+
+size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
+                               int ratio) {
+    GridRefs c;
+    if (!fine || grid_refs(coarse, &c) != SWA_OK) return 0;
+    std::vector<int4> f, a;
+    if (amr::build_maps(c, fine, level, ratio, f, a) != SWA_OK) return 0;
+    return ((sizeof(int4) * f.size() + 255) & ~(size_t)255) + sizeof(int4) * a.size() + 512;
+}
+
+int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
+                   size_t ws_bytes, void *stream, swa_amr **out) {
+    GridRefs c;
+    if (!fine || !ws || !out) return set_error(SWA_EINVAL, "null argument");
+    TRY(grid_refs(coarse, &c));
+    if (((uintptr_t)ws & 255) != 0) return set_error(SWA_EINVAL, "workspace must be 256-byte aligned");
+    std::vector<int4> f, a;
+    TRY(amr::build_maps(c, fine, level, ratio, f, a));
+    const size_t need = ((sizeof(int4) * f.size() + 255) & ~(size_t)255) + sizeof(int4) * a.size() + 512;
+    if (ws_bytes < need) return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, need);
+    swa_amr *A = new (std::nothrow) swa_amr();
+    if (!A) return set_error(SWA_ENOMEM, "host allocation failed");
+    A->coarse = coarse; A->fine = fine; A->level = level; A->r = ratio;
+    A->fill = (int4 *)ws;
+    A->avg = (int4 *)((char *)ws + ((sizeof(int4) * f.size() + 255) & ~(size_t)255));
+    A->nfill = (int)f.size();
+    A->navg = (int)a.size();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = SWA_OK;
+    if (!f.empty())
+        rc = cuda_check(cudaMemcpyAsync(A->fill, f.data(), sizeof(int4) * f.size(),
+                                        cudaMemcpyHostToDevice, st), "AMR fill map upload");
+    if (rc == SWA_OK && !a.empty())
+        rc = cuda_check(cudaMemcpyAsync(A->avg, a.data(), sizeof(int4) * a.size(),
+                                        cudaMemcpyHostToDevice, st), "AMR average map upload");
+    if (rc == SWA_OK) rc = cuda_check(cudaStreamSynchronize(st), "create_amr");
+    if (rc != SWA_OK) { delete A; return rc; }
+    *out = A;
+    return SWA_OK;
+}
+
+int swa_destroy_amr(swa_amr *A) {
+    delete A;
+    return SWA_OK;
+}
+
+int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *stream) {
+    if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
+    if (!(dt_c > 0.0)) return set_error(SWA_EINVAL, "dt_c must be > 0");
+    if (max_launches < 1) return set_error(SWA_EINVAL, "max_launches must be >= 1");
+    GridRefs c;
+    TRY(grid_refs(A->coarse, &c));
+    if (!c.state_set) return set_error(SWA_ESTATE, "coarse state not set");
+    if (!A->fine->lev[A->level].started) return set_error(SWA_ESTATE, "fine level not started");
+    cudaStream_t st = (cudaStream_t)stream;
+    amr::AmrParams p{};
+    p.table = A->fine->table;
+    p.lclk = A->fine->lev[A->level].clk;
+    p.cclk = c.clk;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) p.cq[b][k] = (float *)c.q[b][k];
+    p.nxc = c.d.nx; p.nyc = c.d.ny; p.r = A->r;
+    p.fill = A->fill; p.nfill = A->nfill;
+    p.avg = A->avg; p.navg = A->navg;
+    p.t_n = t_n; p.dt_c = dt_c; p.t_end = t_n + dt_c;
+    p.err = swadj_host::error_word();
+    const unsigned fb = ew_blocks((size_t)(A->nfill > 0 ? A->nfill : 1));
+    const unsigned ab = ew_blocks((size_t)(A->navg > 0 ? A->navg : 1));
+    TRY(swa_step_forward(A->coarse, 1, p.t_end, stream));
+    for (int k = 1; k <= A->r; k++) {
+        const double t_k = k == A->r ? p.t_end : t_n + dt_c * (double)k / (double)A->r;
+        for (int j = 0; j < max_launches; j++) {
+            amr::amr_fill_kernel<<<fb, 256, 0, st>>>(p);
+            TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
+            TRY(swa_step_level(A->fine, A->level, 1, t_k, stream));
+        }
+    }
+    amr::amr_avg_kernel<<<ab, 256, 0, st>>>(p);
+    return cuda_check(cudaGetLastError(), "amr_avg_kernel");
+}
+
+}  // extern "C"

@@ -21,8 +21,11 @@ struct DevClock {
     double smax;        // s_max(Q^n)
 };
 
-// Bit set in the device error word.
-enum : int { ERR_UNSTABLE = 1 };
+// Bits set in the device error word.
+enum : int {
+    ERR_UNSTABLE = 1,   // non-finite state or depth <= 0
+    ERR_LAG = 2         // an AMR step's levels did not reach its end time
+};
 
 struct BcSpec {
     int lo_x, hi_x, lo_y, hi_y;
@@ -111,6 +114,18 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 }  // namespace swadj
 
 // Host-side helpers shared by the translation units (defined in api.cu).
+namespace swadj {
+// Internal view of a forward grid (api.cu), for the AMR glue (patches.cu).
+struct GridRefs {
+    swa_grid_desc d;
+    void *q[2][3];      // ping-pong state buffers
+    const void *bath;   // B (FP64) or hbar = -B (FP32)
+    DevClock *clk;
+    int state_set;
+};
+int grid_refs(const swa_grid *g, GridRefs *out);
+}  // namespace swadj
+
 namespace swadj_host {
 int set_error(int code, const char *fmt, ...);
 int cuda_check(cudaError_t e, const char *what);

@@ -48,6 +48,7 @@ EXPORTS = [
     "swa_patches_set_state", "swa_patches_start_level", "swa_patches_get_state",
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
+    "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
 ]
 
 
@@ -147,6 +148,10 @@ def load(path: str = LIB_PATH):
         "swa_patches_get_time": ([_V, _I, _P(_D), _P(_D), _P(ctypes.c_longlong), _V], _I),
         "swa_patches_level_info": ([_V, _I, _P(_I), _P(_I), _P(ctypes.c_longlong)], _I),
         "swa_patches_set_tile_rows": ([_V, _I, _I], _I),
+        "swa_amr_workspace_bytes": ([_V, _V, _I, _I], _SZ),
+        "swa_create_amr": ([_V, _V, _I, _I, _V, _SZ, _V, _P(_V)], _I),
+        "swa_destroy_amr": ([_V], _I),
+        "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -537,6 +542,26 @@ class SnapStore:
             pass
 
 
+def swa_amr_workspace_bytes(coarse, fine, level, ratio):
+    return int(load().swa_amr_workspace_bytes(coarse, fine, int(level), int(ratio)))
+
+
+def swa_create_amr(coarse, fine, level, ratio, ws, ws_bytes, stream=None):
+    out = _V()
+    _chk(load().swa_create_amr(coarse, fine, int(level), int(ratio), _ptr(ws), int(ws_bytes),
+                               _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def swa_destroy_amr(h):
+    return _chk(load().swa_destroy_amr(h))
+
+
+def swa_amr_step(h, t_n, dt_c, max_launches=1, stream=None):
+    return _chk(load().swa_amr_step(h, float(t_n), float(dt_c), int(max_launches),
+                                    _stream(stream)))
+
+
 class PatchSet:
     """Batched patches; `patches` is a list of (level, x_lo, y_lo, nx, ny, dx, dy)."""
 
@@ -576,6 +601,30 @@ class PatchSet:
         try:
             if getattr(self, "h", None):
                 swa_destroy_patches(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+class Amr:
+    """Two-level AMR hierarchy over a Grid (coarse) and one level of a
+    PatchSet (fine, ringed patches); keeps both alive."""
+
+    def __init__(self, grid, patchset, level, ratio, device="cuda", stream=None):
+        self.grid, self.patchset, self.level, self.ratio = grid, patchset, level, ratio
+        self.nbytes = swa_amr_workspace_bytes(grid.h, patchset.h, level, ratio)
+        if self.nbytes == 0:
+            raise SwaError(SWA_EINVAL, swa_last_error())
+        self.ws = _workspace(self.nbytes, device)
+        self.h = swa_create_amr(grid.h, patchset.h, level, ratio, self.ws, self.nbytes, stream)
+
+    def step(self, t_n, dt_c, max_launches=1, stream=None):
+        swa_amr_step(self.h, t_n, dt_c, max_launches, stream)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                swa_destroy_amr(self.h)
                 self.h = None
         except Exception:
             pass

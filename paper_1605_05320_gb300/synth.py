@@ -301,3 +301,51 @@ def patch_fields(patch, L: float = 2048e3, seed: int = 1605, n_seamounts: int = 
     B = basin_bathymetry(g, L, seed, n_seamounts, seamount_params=sm)
     eta = gaussian_field(g, src[0], src[1], amp, width)
     return B, eta
+
+
+# ------------------------------------------------------------- AMR cases
+def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
+              seed: int | None = None):
+    """A walled nc x nc coarse basin (cell dx) with fine patches refined by r.
+
+    boxes: patch interiors in coarse cells, (i0, j0, mx, my); each patch is
+    returned with its 2-cell ring.  Bottom and surface are analytic (a
+    sinusoidal 80-120 m bottom, a 0.5 m Gaussian hump of width 3 dx at the
+    centre, or the ocean at rest), sampled at coarse centres and once on the
+    global fine grid, so patches agree wherever they overlap.  seed: uniform
+    random momenta in [-5, 5] (r = 1 only, where the levels share cells).
+    Returns a dict with the coarse fields (B, eta, hu, hv), per patch the
+    descriptor (level 1, x_lo, y_lo, nx, ny, dx, dy) and fields (B, eta, hu,
+    hv, ring included)."""
+    def bottom(x, y):
+        return -100.0 - 20.0 * np.sin(x / 7e4) * np.cos(y / 9e4)
+
+    L = nc * dx
+
+    def hump(x, y):
+        return 0.5 * np.exp(-((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2) / (3 * dx) ** 2)
+
+    xc = (np.arange(nc) + 0.5) * dx
+    X, Y = np.meshgrid(xc, xc)
+    xf = (np.arange(nc * r) + 0.5) * (dx / r)
+    XF, YF = np.meshgrid(xf, xf)
+    Bc, BF = bottom(X, Y), bottom(XF, YF)
+    ec = np.zeros_like(X) if rest else hump(X, Y)
+    EF = np.zeros_like(XF) if rest else hump(XF, YF)
+    uc = np.zeros_like(X)
+    UF = np.zeros_like(XF)
+    if seed is not None:
+        assert r == 1
+        uc = np.random.default_rng(seed).uniform(-5.0, 5.0, X.shape)
+        UF = uc
+    out = {"coarse": {"B": Bc.ravel(), "eta": ec.ravel(), "hu": uc.ravel(), "hv": -uc.ravel()},
+           "patches": [], "dx": dx, "nc": nc, "r": r}
+    dxf = dx / r
+    for (i0, j0, mx, my) in boxes:
+        nx, ny = mx * r + 4, my * r + 4
+        I0, J0 = i0 * r - 2, j0 * r - 2
+        sl = lambda a: a[J0:J0 + ny, I0:I0 + nx].ravel().copy()
+        desc = (1, i0 * dx - 2 * dxf, j0 * dx - 2 * dxf, nx, ny, dxf, dxf)
+        out["patches"].append({"box": (i0, j0, mx, my), "desc": desc, "B": sl(BF),
+                               "eta": sl(EF), "hu": sl(UF), "hv": -sl(UF)})
+    return out

@@ -93,6 +93,10 @@ def test_launch_shape_and_gauge_calls_check_their_arguments(lib):
     kernels do not offer are rejected before anything is enqueued."""
     assert lib.swa_grid_set_strip_rows(None, 32) == S.SWA_EINVAL
     assert lib.swa_grid_set_scheme(None, S.SWA_SCHEME_CTU) == S.SWA_EINVAL
+    assert lib.swa_amr_workspace_bytes(None, None, 1, 2) == 0
+    out = ctypes.c_void_p()
+    assert lib.swa_create_amr(None, None, 1, 2, None, 0, None, ctypes.byref(out)) == S.SWA_EINVAL
+    assert lib.swa_amr_step(None, 0.0, 1.0, 1, None) == S.SWA_EINVAL
     assert lib.swa_patches_set_tile_rows(None, 1, 32) == S.SWA_EINVAL
     assert lib.swa_grid_record_gauges(None, 2, None, None, None, 10, None) == S.SWA_EINVAL
     rows = ctypes.c_longlong()
