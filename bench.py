@@ -315,20 +315,9 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     import torch
     from paper_1605_05320_gb300 import swadj as S
     from paper_1605_05320_gb300 import synth
-    n, dx = 2048, 1e3
     hs = stream.cuda_stream
-    B, eta = synth.patch_fields((1, 0.0, 0.0, n, n, dx, dx))
+    B, eta, n, dx, descs, fields = synth.amr_basin_2048(ratio, side, tiles)
     d = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=S.SWA_FP32)
-    src_i, src_j = 700, 1024                       # the source of the basin fields, in km
-    i0, j0 = src_i - tiles * side // 2, src_j - tiles * side // 2
-    dxf = dx / ratio
-    descs = []
-    for b in range(tiles):
-        for a in range(tiles):
-            pi, pj = i0 + a * side, j0 + b * side
-            descs.append((1, pi * dx - 2 * dxf, pj * dx - 2 * dxf, side * ratio + 4,
-                          side * ratio + 4, dxf, dxf))
-    fields = [synth.patch_fields(q) for q in descs]
     fine_cells = sum(q[3] * q[4] for q in descs)
     dt_c = 0.9 * 0.75 * dx / np.sqrt(9.81 * float(np.max(-B)))
 

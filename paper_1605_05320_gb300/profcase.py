@@ -8,6 +8,9 @@ and restores device memory between passes stays small:
   fwd   FP32 forward steps (fwd_f32_strips), ~120 MB on the device
   ctu   FP32 unsplit forward steps with transverse waves (fwd_ctu_kernel),
         ~120 MB
+  amr   two-level AMR steps on the basin: the 2048^2 coarse grid and 64
+        patches refined by 4 around the source (fills, fine launches,
+        averaging), ~200 MB
   adj   the full FP32 adjoint run (adj_f32_strips, ~2000 launches) with a
         fused snapshot every 100 steps, ~1.3 GB
   flag  FP32 adjoint-weighted flag passes without the m output (the
@@ -17,7 +20,8 @@ and restores device memory between passes stays small:
         1024^2 grid (the pruned bilinear flag_kernel)
 
 Launch counts (for a profiler's -s / -c): `fwd` and `ctu` run 1 initial-CFL
-launch then `--steps` step launches; `adj` runs 1 init launch then every adjoint step to
+launch then `--steps` step launches; `amr` runs its set-up launches, then 10
+per step (coarse step, 4 x (fill, fine launch), averaging); `adj` runs 1 init launch then every adjoint step to
 t_f; `flag` runs `--steps` flag passes after its set-up launches.
 
     python -m paper_1605_05320_gb300.profcase fwd --steps 120
@@ -28,13 +32,14 @@ import argparse
 
 
 def main(argv=None):
+    import numpy as np
     import torch
 
     from . import build
     from . import swadj as S
     from . import synth
     ap = argparse.ArgumentParser()
-    ap.add_argument("kernel", choices=["fwd", "ctu", "adj", "flag"])
+    ap.add_argument("kernel", choices=["fwd", "ctu", "amr", "adj", "flag"])
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--full", action="store_true")
@@ -53,6 +58,23 @@ def main(argv=None):
             g.set_scheme(S.SWA_SCHEME_CTU)
         g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
         g.step(a.steps, sc.t_f)
+        out["t"] = g.time()[0]
+    elif a.kernel == "amr":
+        B, eta, n2, dx, descs, fields = synth.amr_basin_2048()
+        d2 = S.make_desc(2, n2, n2, 0.0, 0.0, dx, dx, precision=S.SWA_FP32)
+        g = S.Grid(d2, B)
+        z = np.zeros(n2 * n2)
+        g.set_state(eta, z, z, 0.0)
+        ps = S.PatchSet(descs, [f[0] for f in fields], d2)
+        for k, f in enumerate(fields):
+            ps.set_state(k, f[1], np.zeros_like(f[1]), np.zeros_like(f[1]))
+        ps.start(1, 0.0)
+        amr = S.Amr(g, ps, 1, 4)
+        dt_c = 0.9 * 0.75 * dx / np.sqrt(9.81 * float(np.max(-B)))
+        t = 0.0
+        for _ in range(a.steps):
+            amr.step(t, dt_c)
+            t = t + dt_c
         out["t"] = g.time()[0]
     elif a.kernel == "adj":
         adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)

@@ -349,3 +349,24 @@ def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
         out["patches"].append({"box": (i0, j0, mx, my), "desc": desc, "B": sl(BF),
                                "eta": sl(EF), "hu": sl(UF), "hv": -sl(UF)})
     return out
+
+
+def amr_basin_2048(ratio: int = 4, side: int = 32, tiles: int = 8):
+    """The basin of the 2D configurations as a two-level hierarchy: the
+    2048^2 coarse grid (1 km cells) and tiles x tiles fine patches of
+    side x side coarse cells refined by `ratio`, tiling a square centred on
+    the source of the basin fields (700 km, 1024 km), each with its 2-cell
+    ring, fields sampled at the fine cell centres.  Returns (B, eta, n, dx,
+    descs, fields) with fields[k] = (B, eta) of patch k."""
+    n, dx = 2048, 1e3
+    B, eta = patch_fields((1, 0.0, 0.0, n, n, dx, dx))
+    i0, j0 = 700 - tiles * side // 2, 1024 - tiles * side // 2
+    dxf = dx / ratio
+    descs = []
+    for b in range(tiles):
+        for a in range(tiles):
+            pi, pj = i0 + a * side, j0 + b * side
+            descs.append((1, pi * dx - 2 * dxf, pj * dx - 2 * dxf, side * ratio + 4,
+                          side * ratio + 4, dxf, dxf))
+    fields = [patch_fields(q) for q in descs]
+    return B, eta, n, dx, descs, fields
