@@ -517,59 +517,84 @@ __device__ __forceinline__ float minmod(float a, float b) {
 // linear in space within the coarse cell (minmod slopes, zero at the domain
 // edge).  Map entry (patch, cell, src, idx): src >= 0 is a sibling patch
 // and idx its cell; src < 0 is the coarse cell idx, with the fine cell at
-// (-src - 1) = sx + r sy inside it.
+// (-src - 1) = sx + r sy inside it.  One thread per (entry, component);
+// the clocks and alpha (FP64) are read and formed once per block.
 __global__ void amr_fill_kernel(AmrParams p) {
-    volatile const DevClock *lc = p.lclk, *cc = p.cclk;
-    const int fcur = lc->cur, ccur = cc->cur;
-    double a = (lc->t - p.t_n) / p.dt_c;
-    a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
-    const float af = (float)a;
+    __shared__ float s_a;
+    __shared__ int s_fcur, s_ccur;
+    if (threadIdx.x == 0) {
+        volatile const DevClock *lc = p.lclk, *cc = p.cclk;
+        double a = (lc->t - p.t_n) / p.dt_c;
+        a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+        s_a = (float)a;
+        s_fcur = lc->cur;
+        s_ccur = cc->cur;
+    }
+    __syncthreads();
+    const float af = s_a;
+    const int fcur = s_fcur, ccur = s_ccur;
     const int r = p.r, nxc = p.nxc, nyc = p.nyc;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nfill; e += gridDim.x * blockDim.x) {
-        const int4 m = p.fill[e];
-        const PatchDevice &D = p.table[m.x];
+    const int n = 3 * p.nfill;
+    for (int e3 = blockIdx.x * blockDim.x + threadIdx.x; e3 < n; e3 += gridDim.x * blockDim.x) {
+        const int e = e3 / 3, k = e3 - 3 * e;
+        const int4 m = __ldg(p.fill + e);
+        float *dst = p.table[m.x].q[fcur][k];
         if (m.z >= 0) {
-            const PatchDevice &S = p.table[m.z];
-#pragma unroll
-            for (int k = 0; k < 3; k++) D.q[fcur][k][m.y] = S.q[fcur][k][m.w];
+            dst[m.y] = p.table[m.z].q[fcur][k][m.w];
             continue;
         }
         const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
         const int c = m.w, ic = c % nxc, jc = c / nxc;
         const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
         const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const float *o = p.cq[ccur ^ 1][k], *n = p.cq[ccur][k];
-            auto at = [&](int i) { return fmaf(af, n[i] - o[i], o[i]); };
-            const float qc = at(c);
-            float s_x = 0.f, s_y = 0.f;
-            if (ic > 0 && ic < nxc - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
-            if (jc > 0 && jc < nyc - 1) s_y = minmod(qc - at(c - nxc), at(c + nxc) - qc);
-            D.q[fcur][k][m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
-        }
+        const float *o = p.cq[ccur ^ 1][k], *nw = p.cq[ccur][k];
+        auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
+        const float qc = at(c);
+        float s_x = 0.f, s_y = 0.f;
+        if (ic > 0 && ic < nxc - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
+        if (jc > 0 && jc < nyc - 1) s_y = minmod(qc - at(c - nxc), at(c + nxc) - qc);
+        dst[m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
     }
 }
 
+// Sum of an r x r block of fine cells, row by row (R > 0: r known at
+// compile time).
+template <int R>
+__device__ __forceinline__ float block_sum(const float *f, int nx, int r) {
+    float s = 0.f;
+    if (R > 0) {
+#pragma unroll
+        for (int jj = 0; jj < R; jj++)
+#pragma unroll
+            for (int ii = 0; ii < R; ii++) s += f[jj * nx + ii];
+    } else {
+        for (int jj = 0; jj < r; jj++)
+            for (int ii = 0; ii < r; ii++) s += f[jj * nx + ii];
+    }
+    return s;
+}
+
 // Coarse cells under a patch := mean of their r x r fine cells (eta, hu, hv).
-// Entry (coarse cell, patch, first fine cell, 0).  Also checks that both
-// levels reached the step's end time.
+// Entry (coarse cell, patch, first fine cell, 0); one thread per (entry,
+// component).  Also checks that both levels reached the step's end time.
+template <int R>
 __global__ void amr_avg_kernel(AmrParams p) {
     volatile const DevClock *lc = p.lclk, *cc = p.cclk;
-    const int fcur = lc->cur, ccur = cc->cur;
-    const int r = p.r;
+    __shared__ int s_fcur, s_ccur;
+    if (threadIdx.x == 0) {
+        s_fcur = lc->cur;
+        s_ccur = cc->cur;
+    }
+    __syncthreads();
+    const int fcur = s_fcur, ccur = s_ccur;
+    const int r = R > 0 ? R : p.r;
     const float inv = 1.f / (float)(r * r);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.navg; e += gridDim.x * blockDim.x) {
-        const int4 m = p.avg[e];
+    const int n = 3 * p.navg;
+    for (int e3 = blockIdx.x * blockDim.x + threadIdx.x; e3 < n; e3 += gridDim.x * blockDim.x) {
+        const int e = e3 / 3, k = e3 - 3 * e;
+        const int4 m = __ldg(p.avg + e);
         const PatchDevice &S = p.table[m.y];
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const float *f = S.q[fcur][k] + m.z;
-            float s = 0.f;
-            for (int jj = 0; jj < r; jj++)
-                for (int ii = 0; ii < r; ii++) s += f[jj * S.nx + ii];
-            p.cq[ccur][k][m.x] = s * inv;
-        }
+        p.cq[ccur][k][m.x] = block_sum<R>(S.q[fcur][k] + m.z, S.nx, r) * inv;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double tol = 1e-12 * (fabs(p.t_end) > 1.0 ? fabs(p.t_end) : 1.0);
@@ -741,8 +766,8 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     p.avg = A->avg; p.navg = A->navg;
     p.t_n = t_n; p.dt_c = dt_c; p.t_end = t_n + dt_c;
     p.err = swadj_host::error_word();
-    const unsigned fb = ew_blocks((size_t)(A->nfill > 0 ? A->nfill : 1));
-    const unsigned ab = ew_blocks((size_t)(A->navg > 0 ? A->navg : 1));
+    const unsigned fb = ew_blocks((size_t)3 * (A->nfill > 0 ? A->nfill : 1));
+    const unsigned ab = ew_blocks((size_t)3 * (A->navg > 0 ? A->navg : 1));
     TRY(swa_step_forward(A->coarse, 1, p.t_end, stream));
     for (int k = 1; k <= A->r; k++) {
         const double t_k = k == A->r ? p.t_end : t_n + dt_c * (double)k / (double)A->r;
@@ -752,7 +777,13 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
             TRY(swa_step_level(A->fine, A->level, 1, t_k, stream));
         }
     }
-    amr::amr_avg_kernel<<<ab, 256, 0, st>>>(p);
+    switch (A->r) {
+        case 1: amr::amr_avg_kernel<1><<<ab, 256, 0, st>>>(p); break;
+        case 2: amr::amr_avg_kernel<2><<<ab, 256, 0, st>>>(p); break;
+        case 4: amr::amr_avg_kernel<4><<<ab, 256, 0, st>>>(p); break;
+        case 8: amr::amr_avg_kernel<8><<<ab, 256, 0, st>>>(p); break;
+        default: amr::amr_avg_kernel<0><<<ab, 256, 0, st>>>(p); break;
+    }
     return cuda_check(cudaGetLastError(), "amr_avg_kernel");
 }
 
