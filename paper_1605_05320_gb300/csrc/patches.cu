@@ -605,12 +605,10 @@ __global__ void amr_avg_kernel(AmrParams p) {
 
 // Geometry of one fine patch in global fine cells: array column 0 at
 // (I0, J0); interior [I0 + 2, I0 + nx - 2) x [J0 + 2, J0 + ny - 2).
+// Building the maps costs O(coarse cells + ring cells + covered cells).
 struct FineBox {
     long long I0, J0;
     int nx, ny;
-    bool interior(long long I, long long J) const {
-        return I >= I0 + kRing && I < I0 + nx - kRing && J >= J0 + kRing && J < J0 + ny - kRing;
-    }
 };
 
 // Check the hierarchy and build the maps (host).
@@ -647,6 +645,21 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
         box.push_back(b);
     }
     const int np = (int)ids.size();
+    // Interiors are whole coarse cells, so a fine cell's owners are its
+    // coarse cell's: per coarse cell the two lowest-index patches (in the
+    // order above) whose interiors cover it, -1 if none.
+    std::vector<int2> own((size_t)d.nx * d.ny, make_int2(-1, -1));
+    for (int a = 0; a < np; a++) {
+        const FineBox &b = box[a];
+        const long long i0 = (b.I0 + kRing) / r, j0 = (b.J0 + kRing) / r;
+        const int mx = (b.nx - 2 * kRing) / r, my = (b.ny - 2 * kRing) / r;
+        for (int jc = 0; jc < my; jc++)
+            for (int ic = 0; ic < mx; ic++) {
+                int2 &o = own[(size_t)(j0 + jc) * d.nx + (size_t)(i0 + ic)];
+                if (o.x < 0) o.x = a;
+                else if (o.y < 0) o.y = a;
+            }
+    }
     fill.clear();
     avg.clear();
     for (int a = 0; a < np; a++) {
@@ -655,36 +668,29 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
             for (int i = 0; i < b.nx; i++) {
                 if (i >= kRing && i < b.nx - kRing && j >= kRing && j < b.ny - kRing) continue;
                 const long long I = b.I0 + i, J = b.J0 + j;
+                const long long ic = I / r, jc = J / r;
+                const int2 o = own[(size_t)jc * d.nx + (size_t)ic];
+                const int src = o.x != a ? o.x : o.y;   // lowest-index other owner
                 int4 m = make_int4(ids[a], j * b.nx + i, 0, 0);
-                int src = -1;
-                for (int q = 0; q < np && src < 0; q++)
-                    if (q != a && box[q].interior(I, J)) src = q;
                 if (src >= 0) {
                     const FineBox &s = box[src];
                     m.z = ids[src];
                     m.w = (int)((J - s.J0) * s.nx + (I - s.I0));
                 } else {
-                    const long long ic = I / r, jc = J / r;
                     m.z = -1 - (int)((I - ic * r) + r * (J - jc * r));
                     m.w = (int)(jc * d.nx + ic);
                 }
                 fill.push_back(m);
             }
     }
-    std::vector<char> taken((size_t)d.nx * d.ny, 0);
-    for (int a = 0; a < np; a++) {
-        const FineBox &b = box[a];
-        const long long i0 = (b.I0 + kRing) / r, j0 = (b.J0 + kRing) / r;
-        const int mx = (b.nx - 2 * kRing) / r, my = (b.ny - 2 * kRing) / r;
-        for (int jc = 0; jc < my; jc++)
-            for (int ic = 0; ic < mx; ic++) {
-                const size_t c = (size_t)(j0 + jc) * d.nx + (size_t)(i0 + ic);
-                if (taken[c]) continue;
-                taken[c] = 1;
-                avg.push_back(make_int4((int)c, ids[a],
-                                        (kRing + jc * r) * b.nx + kRing + ic * r, 0));
-            }
-    }
+    for (int jc = 0; jc < d.ny; jc++)
+        for (int ic = 0; ic < d.nx; ic++) {
+            const int a = own[(size_t)jc * d.nx + ic].x;
+            if (a < 0) continue;
+            const FineBox &b = box[a];
+            const long long li = (long long)ic * r - b.I0, lj = (long long)jc * r - b.J0;
+            avg.push_back(make_int4(jc * d.nx + ic, ids[a], (int)(lj * b.nx + li), 0));
+        }
     return SWA_OK;
 }
 
