@@ -24,6 +24,10 @@
  *                    chapters, cited in Sec. 6): x- and y-edge waves all from
  *                    Q^n, MC-limited corrections, and transverse propagation
  *                    of each fluctuation into the neighbouring edge fluxes.
+ *                    One detail is parity unpinned: which Roe state splits a
+ *                    fluctuation transversely (its own edge's here).  Any
+ *                    neighbouring edge's state gives an equally consistent
+ *                    scheme that passes the same pins.
  *   orc_fwd_smax     CFL number max over cells of max_dir (|u|+c)/d_dir.
  *   orc_lin_step     first-order update of Eq. (hyp_linear) (and its 2D form,
  *                    Sec. 5, x-sweep then y-sweep), used only by the
