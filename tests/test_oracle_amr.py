@@ -8,14 +8,15 @@ r fine substeps per coarse step, averaging down.
   sampled separately on each level;
 - a patch cut in two (the cut filled from the sibling) gives the patch;
 - refining a patch brings its region closer to a uniformly fine run than the
-  coarse grid alone; piecewise-constant coarse fills, or fills frozen at the
-  coarse step's start or end (mistakes planted in a subclass) do not.
+  coarse grid alone; piecewise-constant coarse fills, fills frozen at the
+  coarse step's start or end, slopes of the wrong sign, or an average over r
+  instead of r^2 cells (mistakes planted in subclasses) do not.
 """
 import numpy as np
 import pytest
 
 import oracle as O
-from oracle.amr import RING, Hierarchy, Patch, fine_grid
+from oracle.amr import RING, Hierarchy, Patch, fine_grid, minmod
 
 DX = 10e3
 H0 = 130.0
@@ -210,3 +211,79 @@ def test_time_interpolation_at_mid_step():
     ring.reshape(g.ny, g.nx)[RING:-RING, RING:-RING] = False
     np.testing.assert_allclose((f[0] + b)[ring], 0.125, rtol=0, atol=1e-12)
     np.testing.assert_allclose(f[1][ring], 1.5, rtol=0, atol=1e-12)
+
+
+class AverageByR(Hierarchy):
+    """Planted mistake: the average divides by r instead of r^2."""
+
+    def average(self):
+        r, nxc = self.r, self.coarse.nx
+        for jc in range(self.coarse.ny):
+            for ic in range(nxc):
+                src = self.owner(ic * r, jc * r)
+                if src is None:
+                    continue
+                q, base = src
+                g = self.grids[q]
+                fh, fu, fv = self.fine[q]
+                se = su = sv = 0.0
+                for jj in range(r):
+                    for ii in range(r):
+                        s = base + jj * g.nx + ii
+                        se += fh[s] + self.Bf[q][s]
+                        su += fu[s]
+                        sv += fv[s]
+                c = jc * nxc + ic
+                self.h[c] = se / r - self.B[c]
+                self.hu[c] = su / r
+                self.hv[c] = sv / r
+
+
+class FlippedSlopes(Hierarchy):
+    """Planted mistake: the coarse fill's limited slopes enter with the wrong
+    sign (the ring leans away from the coarse gradient)."""
+
+    def fill(self, old, t_n, dt_c):
+        r, nxc = self.r, self.coarse.nx
+        a = min(max((self.t_f - t_n) / dt_c, 0.0), 1.0)
+        eta_o, eta_n = old[0] + self.B, self.h + self.B
+        for k, (p, g) in enumerate(zip(self.patches, self.grids)):
+            fh, fu, fv = self.fine[k]
+            for j in range(g.ny):
+                for i in range(g.nx):
+                    if RING <= i < g.nx - RING and RING <= j < g.ny - RING:
+                        continue
+                    I, J = p.i0 * r - RING + i, p.j0 * r - RING + j
+                    o = j * g.nx + i
+                    src = self.owner(I, J, skip=k)
+                    if src is not None:
+                        q, s = src
+                        sh, su, sv = self.fine[q]
+                        fh[o] = sh[s] + self.Bf[q][s] - self.Bf[k][o]
+                        fu[o], fv[o] = su[s], sv[s]
+                        continue
+                    ic, jc = I // r, J // r
+                    xi = ((I - ic * r) + 0.5) / r - 0.5
+                    zeta = ((J - jc * r) + 0.5) / r - 0.5
+                    v = []
+                    for qo, qn in ((eta_o, eta_n), (old[1], self.hu), (old[2], self.hv)):
+                        at = lambda ii, jj: qo[jj * nxc + ii] + a * (qn[jj * nxc + ii] - qo[jj * nxc + ii])
+                        qc = at(ic, jc)
+                        sx = sy = 0.0
+                        if 0 < ic < nxc - 1:
+                            sx = minmod(qc - at(ic - 1, jc), at(ic + 1, jc) - qc)
+                        if 0 < jc < self.coarse.ny - 1:
+                            sy = minmod(qc - at(ic, jc - 1), at(ic, jc + 1) - qc)
+                        v.append(qc - sx * xi - sy * zeta)
+                    fh[o] = v[0] - self.Bf[k][o]
+                    fu[o], fv[o] = v[1], v[2]
+
+
+
+@pytest.mark.parametrize("cls", [AverageByR, FlippedSlopes])
+def test_planted_glue_mistakes_fail_the_accuracy_pins(cls):
+    fails = 0
+    for (r, steps, factor) in [(2, 4, 0.3), (2, 12, 0.7), (4, 4, 0.5)]:
+        amr, coarse = region_errors(r, steps, cls=cls)
+        fails += not (amr < factor * coarse)
+    assert fails >= 2
