@@ -371,8 +371,10 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  * x_lo = coarse x_lo + i0 dx_coarse - 2 dx, y_lo likewise, and its ring must
  * lie inside the coarse domain.  The level step updates ring cells like any
  * other (they enter the level's CFL maximum); the fill before each launch
- * overwrites them.  Set the fine patches' states (ring included) and start
- * the level at the coarse grid's time before the first step.
+ * overwrites them.  The patch set's boundary conditions act only beyond the
+ * ring, on ring cells: create it with SWA_BC_EXTRAP, the rule the
+ * hierarchy is defined with.  Set the fine patches' states (ring included)
+ * and start the level at the coarse grid's time before the first step.
  *
  * swa_amr_step(amr, t_n, dt_c, m, stream), all stream-ordered, no host sync:
  *   1. the coarse grid steps to t_n + dt_c (dt_c must not exceed its CFL

@@ -37,7 +37,9 @@ def gpu_hierarchy(S, case):
     grid = S.Grid(coarse_desc(S, case), case["coarse"]["B"])
     c = case["coarse"]
     grid.set_state(c["eta"], c["hu"], c["hv"], 0.0)
-    common = coarse_desc(S, case)
+    nc, dx = case["nc"], case["dx"]
+    # the fine level extrapolates beyond its rings, as the oracle's patches do
+    common = S.make_desc(2, nc, nc, 0.0, 0.0, dx, dx, precision=S.SWA_FP32)
     descs = [p["desc"] for p in case["patches"]]
     ps = S.PatchSet(descs, [p["B"] for p in case["patches"]], common)
     for k, p in enumerate(case["patches"]):
