@@ -394,13 +394,33 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  * swa_sync_status returns SWA_ESTATE.
  */
 typedef struct swa_amr swa_amr;
+/* Device workspace for the maps (16 bytes per ring cell and per covered
+ * coarse cell, plus padding); 0 if the geometry is invalid (the reason is in
+ * swa_last_error). */
 size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
                                int ratio);
-/* Checks the geometry (SWA_EINVAL) and uploads the fill and average maps.
- * coarse and fine must outlive the hierarchy. */
+/*
+ * coarse: a 2D FP32 grid; fine: a patch set whose patches of `level` are
+ * the fine level (other levels are ignored); ratio: r in [1, 64].  ws: device
+ * buffer of at least swa_amr_workspace_bytes, 256-byte aligned, owned by the
+ * caller for the hierarchy's lifetime; coarse and fine must outlive it too.
+ * Checks the geometry (SWA_EINVAL: level without patches, cell size not
+ * coarse / r, interior not on whole coarse cells, ring outside the domain),
+ * uploads the maps on `stream` and synchronises it.  SWA_ENOMEM if ws_bytes
+ * is too small.
+ */
 int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
                    size_t ws_bytes, void *stream, swa_amr **out);
+/* Host bookkeeping only; the workspace stays the caller's. */
 int swa_destroy_amr(swa_amr *amr);
+/*
+ * One coarse step of dt_c from t_n (the coarse grid's current time) with
+ * ratio substeps of the fine level, max_launches launches each, enqueued on
+ * `stream`.  SWA_EINVAL: null hierarchy, dt_c <= 0, max_launches < 1;
+ * SWA_ESTATE: coarse state not set or fine level not started; SWA_ECUDA: a
+ * launch failed.  A level falling short of t_n + dt_c shows up as
+ * SWA_ESTATE at the next swa_sync_status.
+ */
 int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
 
 /* ======================= allocation-free forward step =====================
