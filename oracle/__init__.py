@@ -11,6 +11,7 @@ pins that fix it are listed in the test modules `tests/test_oracle_*.py`.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -27,16 +28,34 @@ FLAG_INTERP, FLAG_BRACKET = 0, 1
 SCHEME_SPLIT, SCHEME_CTU = 0, 1   # 2D forward step: split, unsplit with transverse waves
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, no contraction, OpenMP)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
+def build(force: bool = False, out: str = _LIB, plant: int = 0) -> str:
+    """Compile the oracle with gcc (FP64, no contraction, OpenMP).  plant > 0
+    compiles one of the deliberately wrong variants listed at ORC_PLANT in
+    swe_oracle.c (used only by tests showing that a pin catches it)."""
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-           "-fopenmp", "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
+           "-fopenmp", "-shared", "-fPIC", f"-DORC_PLANT={int(plant)}",
+           "-o", out + ".tmp", _SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+    os.replace(out + ".tmp", out)
+    return out
+
+
+@contextlib.contextmanager
+def planted(plant: int, workdir: str):
+    """Run the block against the oracle compiled with mistake `plant`
+    (ORC_PLANT in swe_oracle.c), built into workdir."""
+    global _lib
+    path = os.path.join(workdir, f"liboracle_plant{int(plant)}.so")
+    build(force=True, out=path, plant=plant)
+    saved = _load()
+    _lib = _bind(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 class _Grid(ctypes.Structure):
@@ -95,43 +114,48 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        G = ctypes.POINTER(_Grid)
-        lib.orc_fwd_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
-        lib.orc_fwd_step.restype = ctypes.c_int
-        lib.orc_fwd_step_ctu.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
-        lib.orc_fwd_step_ctu.restype = ctypes.c_int
-        lib.orc_ctu_tsplit.argtypes = [ctypes.c_double] * 3 + [_D, _D, _D]
-        lib.orc_ctu_tsplit.restype = None
-        lib.orc_fwd_smax.argtypes = [G, _D, _D, _D]
-        lib.orc_fwd_smax.restype = ctypes.c_double
-        lib.orc_fwd_run.argtypes = [G, _D, _D, _D, _D, ctypes.c_long,
-                                    ctypes.c_double, _D]
-        lib.orc_fwd_run.restype = ctypes.c_long
-        lib.orc_lin_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
-        lib.orc_lin_step.restype = ctypes.c_int
-        lib.orc_adj_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
-        lib.orc_adj_step.restype = ctypes.c_int
-        lib.orc_adj_smax.argtypes = [G, _D]
-        lib.orc_adj_smax.restype = ctypes.c_double
-        lib.orc_adj_run.argtypes = [G, _D, _D, ctypes.c_double, ctypes.c_int,
-                                    ctypes.c_long, _D, _D,
-                                    ctypes.POINTER(ctypes.c_long), _D]
-        lib.orc_adj_run.restype = ctypes.c_long
-        lib.orc_flag.argtypes = [G, _D, _D, _D, _D, ctypes.c_double, G, _D, _D,
-                                 _D, ctypes.c_long, ctypes.c_double,
-                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                 ctypes.POINTER(ctypes.c_uint8), _D]
-        lib.orc_flag.restype = ctypes.c_long
-        lib.orc_flag_surface.argtypes = [G, _D, _D, ctypes.c_double,
-                                         ctypes.POINTER(ctypes.c_uint8)]
-        lib.orc_flag_surface.restype = ctypes.c_long
-        lib.orc_gauge.argtypes = [G, _D, _D, ctypes.c_long, _D, _D]
-        lib.orc_gauge.restype = None
-        lib.orc_num_threads.restype = ctypes.c_int
-        lib.orc_set_threads.argtypes = [ctypes.c_int]
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _bind(lib):
+    G = ctypes.POINTER(_Grid)
+    lib.orc_fwd_riemann.argtypes = [ctypes.c_double] * 9 + [_D]
+    lib.orc_fwd_riemann.restype = None
+    lib.orc_fwd_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
+    lib.orc_fwd_step.restype = ctypes.c_int
+    lib.orc_fwd_step_ctu.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
+    lib.orc_fwd_step_ctu.restype = ctypes.c_int
+    lib.orc_ctu_tsplit.argtypes = [ctypes.c_double] * 3 + [_D, _D, _D]
+    lib.orc_ctu_tsplit.restype = None
+    lib.orc_fwd_smax.argtypes = [G, _D, _D, _D]
+    lib.orc_fwd_smax.restype = ctypes.c_double
+    lib.orc_fwd_run.argtypes = [G, _D, _D, _D, _D, ctypes.c_long,
+                                ctypes.c_double, _D]
+    lib.orc_fwd_run.restype = ctypes.c_long
+    lib.orc_lin_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
+    lib.orc_lin_step.restype = ctypes.c_int
+    lib.orc_adj_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
+    lib.orc_adj_step.restype = ctypes.c_int
+    lib.orc_adj_smax.argtypes = [G, _D]
+    lib.orc_adj_smax.restype = ctypes.c_double
+    lib.orc_adj_run.argtypes = [G, _D, _D, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_long, _D, _D,
+                                ctypes.POINTER(ctypes.c_long), _D]
+    lib.orc_adj_run.restype = ctypes.c_long
+    lib.orc_flag.argtypes = [G, _D, _D, _D, _D, ctypes.c_double, G, _D, _D,
+                             _D, ctypes.c_long, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_uint8), _D]
+    lib.orc_flag.restype = ctypes.c_long
+    lib.orc_flag_surface.argtypes = [G, _D, _D, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_uint8)]
+    lib.orc_flag_surface.restype = ctypes.c_long
+    lib.orc_gauge.argtypes = [G, _D, _D, ctypes.c_long, _D, _D]
+    lib.orc_gauge.restype = None
+    lib.orc_num_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
+    return lib
 
 
 def _p(a):
@@ -163,6 +187,17 @@ def fwd_step(grid: Grid, h, hu, hv, B, dt):
     if rc:
         raise FloatingPointError(f"oracle forward step unstable ({rc})")
     return h, hu, hv
+
+
+def fwd_riemann(g, left, right):
+    """One forward Riemann solve (test-only view).  left/right = (h, normal
+    momentum, tangential momentum, B).  Returns dict(s [3], Z [3, 3] (wave p,
+    component m), uhat, vhat, chat)."""
+    out = np.zeros(15)
+    _load().orc_fwd_riemann(float(g), *[float(x) for x in left],
+                            *[float(x) for x in right], _p(out))
+    return dict(s=out[0:3].copy(), Z=out[3:12].reshape(3, 3).copy(),
+                uhat=out[12], vhat=out[13], chat=out[14])
 
 
 def ctu_tsplit(uhat, vhat, chat, a):

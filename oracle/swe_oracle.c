@@ -76,6 +76,21 @@ typedef struct {
 
 #define NG 2
 
+/*
+ * ORC_PLANT selects a deliberately wrong variant of one step, compiled only
+ * by the tests that show a pin catches that mistake (0, the default, is the
+ * method):
+ *   1  tangential wave strength formed with the normal Roe average
+ *      (beta2 = df3 - uhat df1)
+ *   2  tangential Roe average taken as the arithmetic mean of vL and vR
+ *   3  normal Roe average taken as the arithmetic mean of uL and uR
+ *   4  adjoint step count one more than ceil(t_f smax / cfl)
+ *   5  snapshot times recorded one snapshot interval late
+ */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+
 /* ---------------------------------------------------------------- helpers */
 
 static double *padded(const orc_grid *G) {
@@ -210,8 +225,16 @@ static void fwd_riemann(double g,
     double uR = mnR / hR, vR = mtR / hR;
     double hhat = 0.5 * (hL + hR);
     double sqL = sqrt(hL), sqR = sqrt(hR);
+#if ORC_PLANT == 3
+    double uhat = 0.5 * (uL + uR);
+#else
     double uhat = (sqL * uL + sqR * uR) / (sqL + sqR);
+#endif
+#if ORC_PLANT == 2
+    double vhat = 0.5 * (vL + vR);
+#else
     double vhat = (sqL * vL + sqR * vR) / (sqL + sqR);
+#endif
     double chat = sqrt(g * hhat);
     double s1 = uhat - chat, s2 = uhat, s3 = uhat + chat;
     double etaL = hL + BL, etaR = hR + BR;
@@ -220,12 +243,30 @@ static void fwd_riemann(double g,
     double df3 = mnR * vR - mnL * vL;
     double b1 = (s3 * df1 - df2) / (s3 - s1);
     double b3 = (df2 - s1 * df1) / (s3 - s1);
+#if ORC_PLANT == 1
+    double b2 = df3 - uhat * df1;
+#else
     double b2 = df3 - vhat * df1;
+#endif
     w->s[0] = s1; w->s[1] = s2; w->s[2] = s3;
     w->uhat = uhat; w->vhat = vhat; w->chat = chat;
     w->Z[0][0] = b1;  w->Z[0][1] = b1 * s1;  w->Z[0][2] = b1 * vhat;
     w->Z[1][0] = 0.0; w->Z[1][1] = 0.0;      w->Z[1][2] = b2;
     w->Z[2][0] = b3;  w->Z[2][1] = b3 * s3;  w->Z[2][2] = b3 * vhat;
+}
+
+/*
+ * Test-only view of one forward Riemann solve: out[0..2] the speeds,
+ * out[3..11] the f-waves Z[p][m] row by row, out[12..14] uhat, vhat, chat.
+ */
+void orc_fwd_riemann(double g, double hL, double mnL, double mtL, double BL,
+                     double hR, double mnR, double mtR, double BR, double *out) {
+    edge_waves w;
+    fwd_riemann(g, hL, mnL, mtL, BL, hR, mnR, mtR, BR, &w);
+    for (int p = 0; p < 3; p++) out[p] = w.s[p];
+    for (int p = 0; p < 3; p++)
+        for (int m = 0; m < 3; m++) out[3 + 3 * p + m] = w.Z[p][m];
+    out[12] = w.uhat; out[13] = w.vhat; out[14] = w.chat;
 }
 
 /* --------------------------------------------------------- forward step */
@@ -745,6 +786,9 @@ long orc_adj_run(const orc_grid *G, const double *hbar, const double *phi,
     int nc = G->ndim + 1;
     double smax = orc_adj_smax(G, hbar);
     long N = (long)ceil(t_f * smax / G->cfl);
+#if ORC_PLANT == 4
+    N = N + 1;
+#endif
     if (N < 1) N = 1;
     double dt = t_f / (double)N;
     double *e = (double *)malloc(n * sizeof(double));
@@ -767,7 +811,11 @@ long orc_adj_run(const orc_grid *G, const double *hbar, const double *phi,
             memcpy(snaps + (size_t)k * nc * n, e, n * sizeof(double));
             memcpy(snaps + (size_t)k * nc * n + n, m, n * sizeof(double));
             if (nc == 3) memcpy(snaps + (size_t)k * nc * n + 2 * n, gm, n * sizeof(double));
+#if ORC_PLANT == 5
+            tau[k++] = t_f - (double)(s - every) * dt;
+#else
             tau[k++] = t_f - (double)s * dt;
+#endif
         }
     }
     free(e); free(m); free(gm);
