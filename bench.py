@@ -651,9 +651,13 @@ _ORACLE_CASE = {}
 
 
 def oracle_sample(n, steps):
-    """The FP64 oracle on a bounded sample of the same workload: `steps`
-    forward and `steps` adjoint steps on the n x n basin, OpenMP on all host
-    cores.  Returns (cell-updates/s, seconds, threads)."""
+    """The FP64 oracle on a bounded sample of the same workload, OpenMP on
+    all host cores: `steps` forward and `steps` adjoint steps on the n x n
+    basin, plus the flag work those forward steps carry in the scenario (one
+    pass per FWD_BLOCK forward steps), i.e. one pass over a band of
+    steps / FWD_BLOCK of the basin's rows, against the scenario's number of
+    snapshots (seeded values: the oracle's cost does not depend on them).
+    Returns (cell-updates/s, seconds, threads, description)."""
     import oracle as O
     from paper_1605_05320_gb300 import synth
     O.build()
@@ -663,16 +667,32 @@ def oracle_sample(n, steps):
         og = O.Grid.from_spec(sc.grid)
         hbar = np.maximum(-sc.B_adj, 0.0)
         smax = O.adj_smax(og, hbar)
-        _ORACLE_CASE[n] = (sc, og, hbar, sc.t_f / np.ceil(sc.t_f * smax / og.cfl))
-    sc, og, hbar, dt_adj = _ORACLE_CASE[n]
+        N_adj = int(np.ceil(sc.t_f * smax / og.cfl))
+        K = N_adj // SNAP_EVERY + 2
+        rows = max(1, int(round(n * steps / FWD_BLOCK)))
+        j0 = (n - rows) // 2
+        bg = O.Grid(2, n, rows, sc.grid.x_lo, sc.grid.y_lo + j0 * sc.grid.dy,
+                    sc.grid.dx, sc.grid.dy)
+        sl = slice(j0 * n, (j0 + rows) * n)
+        rng = np.random.default_rng(2048)
+        snaps = 1e-3 * rng.standard_normal((K, 3, rows * n))
+        tau = np.linspace(sc.t_f, 0.0, K)
+        band = (bg, sl, snaps, tau)
+        _ORACLE_CASE[n] = (sc, og, hbar, sc.t_f / N_adj, band)
+    sc, og, hbar, dt_adj, (bg, sl, snaps, tau) = _ORACLE_CASE[n]
     h0 = sc.eta0 - sc.B
     t0 = time.perf_counter()
     O.fwd_run(og, h0, sc.hu0, sc.hv0, sc.B, steps, sc.t_f)
     e, m, gm = sc.phi[0], sc.phi[1], sc.phi[2]
     for _ in range(steps):
         e, m, gm = O.adj_step(og, e, m, gm, hbar, dt_adj)
+    O.flag(bg, h0[sl], sc.hu0[sl], sc.hv0[sl], sc.B[sl], 0.5 * sc.t_f, bg, hbar[sl], snaps,
+           tau, sc.t_s, sc.t_f, sc.tol, O.FLAG_INTERP)
     sec = time.perf_counter() - t0
-    return 2 * steps * sc.grid.n / sec, sec, O.num_threads()
+    what = (f"{steps} forward + {steps} adjoint FP64 oracle steps on the {n}x{n} basin and "
+            f"a flag pass over {bg.ny} of its rows against {snaps.shape[0]} snapshots "
+            f"(the flag work of {steps} forward steps)")
+    return 2 * steps * sc.grid.n / sec, sec, O.num_threads(), what
 
 
 def workload_config(n, world):
@@ -691,16 +711,15 @@ def run_reference(args, world=1):
     n = args.n
     per = 2
     for _ in range(args.warmup):
-        oracle_sample(n, 1)
+        oracle_sample(n, per)
     t0 = time.perf_counter()
     cells = 0
     for _ in range(args.steps):
-        v, sec, thr = oracle_sample(n, per)
+        v, sec, thr, what = oracle_sample(n, per)
         cells += 2 * per * n * n
     sec = time.perf_counter() - t0
     value = cells / sec
-    sample = (f"{per} forward + {per} adjoint FP64 oracle steps on the {n}x{n} basin "
-              f"per step (OpenMP, {thr} threads)")
+    sample = f"per step: {what} (OpenMP, {thr} threads)"
     return {
         "impl": "reference",
         "metric": "SWE cell-updates/s (forward + adjoint steps, whole scenario incl. flag passes and gauges)",
@@ -735,11 +754,10 @@ def main():
         out["patches"] = run_patches()
     if rank == 0:
         if not args.no_cpu_baseline:
-            v, sec, thr = oracle_sample(args.n, 2)
+            v, sec, thr, what = oracle_sample(args.n, 2)
             out["cpu_baseline"] = {
                 "value": v, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
-                "sample": f"2 forward + 2 adjoint FP64 oracle steps on the {args.n}x{args.n} "
-                          f"basin ({sec:.1f} s, OpenMP)"}
+                "sample": f"{what} ({sec:.1f} s, OpenMP)"}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

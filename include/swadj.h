@@ -450,11 +450,13 @@ int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *
  * reduction slots than the static array holds (SWA_STATIC_MAX_BLOCKS blocks;
  * 2048 x 2048 fits in both precisions); SWA_ECUDA for a runtime failure.
  * All calls share the static array and it keeps the last call's contents;
- * each call resets what must start at zero before its kernel runs.  Calls
- * whose kernels overlap on the GPU race on the array: issue them on one
- * stream.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.
+ * each call resets what must start at zero with a one-thread kernel on
+ * `stream` before its step kernel runs (no host memory is read, nothing
+ * synchronises).  Calls whose kernels overlap on the GPU race on the array:
+ * issue them on one stream.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  The cached address is not refreshed after a
+ * cudaDeviceReset: do not reset a device while the library is in use.
  */
 #define SWA_STATIC_MAX_BLOCKS 32768
 #define SWA_STATIC_SCRATCH_BYTES (256 + 8 * SWA_STATIC_MAX_BLOCKS)

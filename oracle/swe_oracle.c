@@ -893,6 +893,8 @@ long orc_flag(const orc_grid *F, const double *h, const double *hu,
     if (lo < tau[K - 1]) lo = tau[K - 1];
     if (hi > tau[0]) hi = tau[0];
     int empty = (K < 1) || (lo > hi) || (t > t_f);
+    /* cells are independent: rows are shared out among threads */
+#pragma omp parallel for schedule(static) reduction(+ : count)
     for (int j = 0; j < F->ny; j++) {
         for (int i = 0; i < F->nx; i++) {
             size_t o = (size_t)j * F->nx + i;

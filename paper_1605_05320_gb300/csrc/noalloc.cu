@@ -13,8 +13,9 @@
 // The array is loaded with the library: every GPU that loads libswadj.so
 // holds kStaticScratchBytes of device memory for it until the process exits.
 // All calls share it and it keeps the last call's contents; each call resets
-// the part that must start from zero (the clock and its block ticket) before
-// its kernel runs.  Calls whose kernels overlap on the GPU (two streams, or
+// the part that must start from zero (the clock and its block ticket) with a
+// one-thread kernel on the caller's stream before its step kernel runs, so a
+// call reads no host memory and does not synchronise.  Calls whose kernels overlap on the GPU (two streams, or
 // two host threads) race on the array and give wrong results: serialise
 // them on one stream.
 #include <mutex>
@@ -34,6 +35,17 @@ static_assert(kStaticScratchBytes == kStaticClockBytes + 8 * (size_t)kStaticMaxB
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+// Puts the static clock in the state a step starts from: time 0, the
+// caller's dt, buffer 0 holding the input, no steps, block ticket 0.
+__global__ void static_clock_reset(DevClock *clk, double dt) {
+    clk->t = 0.0;
+    clk->dt_cfl = dt;
+    clk->nsteps = 0;
+    clk->cur = 0;
+    clk->ticket = 0u;
+    clk->smax = 0.0;
+}
+
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -42,7 +54,9 @@ void *g_scratch_ptr[kMaxDevices];
 // Device address of the static scratch for the current device.  The first
 // call on a device looks it up (cudaGetSymbolAddress) and caches it; in host
 // code the array's name is only a host-side stand-in, never a device
-// address, so the kernels always get this looked-up pointer.
+// address, so the kernels always get this looked-up pointer.  The cache
+// outlives a cudaDeviceReset, after which the module may load elsewhere, so
+// resetting a device while the library is in use is not supported.
 int scratch_for_current_device(void **scratch, int **err) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -81,15 +95,10 @@ int run_static(const swa_grid_desc *d, const void *const q_in[3], void *const q_
     int *err = nullptr;
     int rc = scratch_for_current_device(&scratch, &err);
     if (rc != SWA_OK) return rc;
-    // reset the clock (t = 0, dt, buffer 0 = input, ticket 0) before the step
-    DevClock c{};
-    c.t = 0.0;
-    c.dt_cfl = dt;
-    c.nsteps = 0;
-    c.cur = 0;
-    c.ticket = 0u;
-    c.smax = 0.0;
-    cudaError_t e = cudaMemcpyAsync(scratch, &c, sizeof(c), cudaMemcpyHostToDevice, st);
+    // reset the clock (t = 0, dt, buffer 0 = input, ticket 0) before the step,
+    // from kernel arguments: no host memory is read
+    static_clock_reset<<<1, 1, 0, st>>>((DevClock *)scratch, dt);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return swadj_host::cuda_check(e, "static clock reset");
     for (int k = 0; k < 3; k++) {
         p.q[0][k] = (R *)q_in[k];

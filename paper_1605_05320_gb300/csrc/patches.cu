@@ -620,6 +620,13 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
     if (r < 1 || r > 64) return set_error(SWA_EINVAL, "ratio must be in [1, 64]");
     if (level < 1 || level > SWA_MAX_LEVELS || ps->lev[level].npatches == 0)
         return set_error(SWA_EINVAL, "level %d has no patches", level);
+    // the fills overwrite every ring cell before each launch, so the fine
+    // patches must extrapolate beyond their rings (a wall would change the
+    // ring's edge waves and the level's CFL step)
+    for (int k = 0; k < 4; k++)
+        if (ps->common.bc[k] != SWA_BC_EXTRAP)
+            return set_error(SWA_EINVAL,
+                             "the fine patch set must use SWA_BC_EXTRAP on all four sides");
     std::vector<int> ids;
     std::vector<FineBox> box;
     const double dxf = d.dx / r, dyf = d.dy / r;

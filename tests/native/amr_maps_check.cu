@@ -95,6 +95,8 @@ swa_patch_desc patch(const GridRefs &c, int level, int r, int i0, int j0, int mx
 void set_patches(swa_patchset &ps, const std::vector<swa_patch_desc> &pd) {
     ps.pd = pd;
     ps.n = (int)pd.size();
+    ps.common = swa_grid_desc{};
+    for (int k = 0; k < 4; k++) ps.common.bc[k] = SWA_BC_EXTRAP;
     for (int l = 0; l <= SWA_MAX_LEVELS; l++) ps.lev[l].npatches = 0;
     for (const auto &q : pd) ps.lev[q.level].npatches++;
 }
@@ -170,6 +172,17 @@ int main() {
         std::vector<int4> f, a;
         if (amr::build_maps(c64, &ps, 1, 2, f, a) != SWA_EINVAL) {
             printf("not rejected: FP64 coarse grid\n");
+            failures++;
+        }
+    }
+    {
+        // a fine level with a wall: the ring fills assume extrapolation
+        swa_patchset ps;
+        set_patches(ps, {patch(c, 1, 2, 5, 5, 4, 4)});
+        ps.common.bc[2] = SWA_BC_WALL;
+        std::vector<int4> f, a;
+        if (amr::build_maps(c, &ps, 1, 2, f, a) != SWA_EINVAL) {
+            printf("not rejected: fine patch set with a wall\n");
             failures++;
         }
     }
