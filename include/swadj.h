@@ -423,6 +423,28 @@ int swa_destroy_amr(swa_amr *amr);
  */
 int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
 
+/* ============================ ALU peak probes =============================
+ * Measurement aid (no counterpart in the paper): throughput probes of the
+ * arithmetic units that bound the step kernels, so that the FP64 and FP32
+ * rooflines are stated against peaks measured on the device at hand.
+ *
+ * swa_alu_probe launches `blocks` x `threads` threads (threads a multiple of
+ * 32 in [32, 256]), each running 8 independent chains of `iters` operations
+ * of one kind, on `stream`; sink_dev is a device float array of `blocks`
+ * entries that is written only if a chain takes an impossible value (it
+ * keeps the work from being optimised away).  Time the launch with CUDA
+ * events and divide swa_alu_probe_ops(kind, blocks, threads, iters), the
+ * operation count (flops for the FMA kinds: 2 per FMA, 4 per packed FMA;
+ * 1 per reciprocal square root), by it.  SWA_EINVAL for a bad shape, a null
+ * sink or an unknown kind; SWA_ECUDA if the launch fails.
+ */
+#define SWA_PROBE_FFMA64 0   /* fma.rn.f64 */
+#define SWA_PROBE_FFMA32 1   /* fma.rn.f32 */
+#define SWA_PROBE_FFMA32X2 2 /* fma.rn.f32x2 (packed pair) */
+#define SWA_PROBE_RSQRT32 3  /* rsqrt.approx.ftz.f32 (special-function unit) */
+double swa_alu_probe_ops(int kind, int blocks, int threads, int iters);
+int swa_alu_probe(int kind, int blocks, int threads, int iters, float *sink_dev, void *stream);
+
 /* ======================= allocation-free forward step =====================
  * The paper has no counterpart to this entry point; it is an integration aid.
  *

@@ -7,7 +7,8 @@
 // waves on 4000 m are resolved to float precision of eta, not of h.
 //
 // 2D grids run the warp strips of strips.cuh (per edge the arithmetic of
-// fwd_edge.cuh); 1D grids run a one-thread-per-cell kernel.  The CFL maximum
+// fwd_pair.cuh); 1D grids run a one-thread-per-cell kernel with the same
+// arithmetic.  The CFL maximum
 // is reduced in float (max is exact); the last block to finish turns it into
 // the next time step in double.
 #include "ctu_kernels.cuh"
@@ -16,7 +17,8 @@
 namespace swadj {
 namespace f32 {
 
-// 2D grids: the warp strips of strips.cuh, one strip per warp.
+
+// 2D grids: warp strips, one strip per warp.
 __global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<float> p, int rows) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<f
     // step starts from while the others step it
     if (p.gauges.n > 0 && blockIdx.x == gridDim.x - 1)
         record_gauges<float, strip::kThreads>(p.gauges, p.q[cur][0], p.bath, p.nx, p.ny, 1,
-                                              t_now);
+                                           t_now);
     const int nsx = (p.nx + strip::kOut - 1) / strip::kOut, nsy = (p.ny + rows - 1) / rows;
     const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     float smax = 0.f;
@@ -44,12 +46,12 @@ __global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<f
         v.nx = p.nx; v.ny = p.ny;
         v.rdx = 1.f / p.dx; v.rdy = 1.f / p.dy;
         v.bc = p.bc;
-        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order,
-                          smax, bad);
+        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order, smax,
+                       bad);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
-    fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
-                                        &am_last, t_now, dt, cur);
+    fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,
+                                     t_now, dt, cur);
 }
 
 // 1D grids: one thread per cell, solving the four edges it needs itself
@@ -72,34 +74,28 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
     float sm = 0.f;
     bool bad = false;
     if (i < p.nx) {
-        float h[5], mu[5], u[5], sq[5], eta[5];
+        fp::Cell<float> c[5];
 #pragma unroll
         for (int k = 0; k < 5; k++) {
             bool fx;
-            const int c = ghost_index(i - 2 + k, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
-            eta[k] = q0[c];
-            mu[k] = fx ? -q1[c] : q1[c];
-            h[k] = eta[k] + p.bath[c];
-            const float q = rsqrt_ftz(h[k]);
-            sq[k] = fwave::mul(h[k], q);
-            u[k] = fwave::mul(mu[k], fwave::mul(q, q));
+            const int ci = ghost_index(i - 2 + k, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
+            const float eta = q0[ci], mu = fx ? -q1[ci] : q1[ci];
+            c[k] = fp::derive(eta, fp::add(eta, p.bath[ci]), mu, 0.f);
         }
-        fwave::EdgeS w[4];
+        const float gh = 0.5f * g;
+        fp::Edge<float> w[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            w[k] = fwave::solve1(g, h[k], mu[k], 0.f, u[k], 0.f, sq[k], eta[k], h[k + 1],
-                                mu[k + 1], 0.f, u[k + 1], 0.f, sq[k + 1], eta[k + 1]);
-        float L0[3], R0[3], L1[3], R1[3];
-        if (fwave::sub1(w[1])) fwave::net1<true>(w[0], w[1], w[2], nux, p.order, L0, R0);
-        else fwave::net1<false>(w[0], w[1], w[2], nux, p.order, L0, R0);
-        if (fwave::sub1(w[2])) fwave::net1<true>(w[1], w[2], w[3], nux, p.order, L1, R1);
-        else fwave::net1<false>(w[1], w[2], w[3], nux, p.order, L1, R1);
-        const float d0 = fwave::mul(-nux, fwave::add(R0[0], L1[0]));
-        const float ne = fwave::add(eta[2], d0);
-        const float nmu = fwave::add(mu[2], fwave::mul(-nux, fwave::add(R0[1], L1[1])));
+        for (int k = 0; k < 4; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
+        const fp::Net<float> n0 =
+            fp::net3(w[0], w[1], w[2], nux, p.order, fp::subsonic(w[1].s1, w[1].s3));
+        const fp::Net<float> n1 =
+            fp::net3(w[1], w[2], w[3], nux, p.order, fp::subsonic(w[2].s1, w[2].s3));
+        const float d0 = fp::mul(-nux, fp::add(n0.R0, n1.L0));
+        const float ne = fp::add(c[2].eta, d0);
+        const float nmu = fp::add(c[2].mn, fp::mul(-nux, fp::add(n0.R1, n1.L1)));
         p.q[cur ^ 1][0][i] = ne;
         p.q[cur ^ 1][1][i] = nmu;
-        const float hn = fwave::add(h[2], d0);
+        const float hn = fp::add(c[2].h, d0);
         bad = !(hn > 0.f) || !isfinite(nmu);
         sm = cfl_f32(hn, nmu, 0.f, g, 1.f / p.dx, 1.f / p.dy, 0);
     }

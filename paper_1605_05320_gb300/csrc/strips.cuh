@@ -11,11 +11,12 @@
 // loaded one iteration ahead of their use.  Ghost cells outside the grid are
 // index-mapped on load (copy, or mirror with the normal momentum negated);
 // the x-sweep commutes with the y-mirror, so ghost rows may be x-swept like
-// any other.  Per edge the arithmetic is fwd_edge.cuh's, so results depend
+// any other.  Per edge the arithmetic is fwd_pair.cuh's, so results depend
 // neither on the strip height nor on how edges share a warp.
 #pragma once
 #include "fwd_edge.cuh"
 #include "fwd_kernels.cuh"
+#include "fwd_pair.cuh"
 
 namespace swadj {
 namespace strip {
@@ -34,56 +35,75 @@ struct View {
     BcSpec bc;
 };
 
-struct XCell {   // derived cell data
-    float h, mu, mv, u, v, sq, eta;
-};
-
-__device__ __forceinline__ XCell derive(float eta, float h, float mu, float mv) {
-    const float q = rsqrt_ftz(h);
-    const float ih = fwave::mul(q, q);
-    XCell c;
-    c.h = h; c.mu = mu; c.mv = mv;
-    c.u = fwave::mul(mu, ih); c.v = fwave::mul(mv, ih); c.sq = fwave::mul(h, q);
-    c.eta = eta;
-    return c;
-}
-
 __device__ __forceinline__ float dn(float x) { return __shfl_down_sync(kFull, x, 1); }
 __device__ __forceinline__ float up(float x) { return __shfl_up_sync(kFull, x, 1); }
 
-__device__ __forceinline__ fwave::EdgeS edge_dn(const fwave::EdgeS &w) {
-    fwave::EdgeS r;
-    r.s1 = dn(w.s1); r.s3 = dn(w.s3); r.vh = dn(w.vh);
-    r.b1 = dn(w.b1); r.b2 = dn(w.b2); r.b3 = dn(w.b3);
-    return r;
-}
-__device__ __forceinline__ fwave::EdgeS edge_up(const fwave::EdgeS &w) {
-    fwave::EdgeS r;
-    r.s1 = up(w.s1); r.s3 = up(w.s3); r.vh = up(w.vh);
-    r.b1 = up(w.b1); r.b2 = up(w.b2); r.b3 = up(w.b3);
-    return r;
+// How a lane reaches the cells and edges beside its own along x: one
+// column per lane, the neighbours are the lanes beside it (a policy, so the
+// x-sweep below serves other lane layouts too).  ok(): whether
+// the warp may take the SUB form, given this lane's edge (the nets of edges
+// (1|2) .. (29|30) are used).
+struct Nb1 {
+    typedef float V;
+    static __device__ __forceinline__ float l(float x) { return up(x); }
+    static __device__ __forceinline__ float r(float x) { return dn(x); }
+    static __device__ __forceinline__ bool ok(const fp::Edge<float> &w, int lane) {
+        return lane < 1 || lane > kLanes - 3 || fp::subsonic(w.s1, w.s3);
+    }
+};
+
+// Net fluxes of a lane's x-edge(s) w, fetching the neighbour edges the
+// limiter needs from the lanes beside it: in the SUB form only the upwind
+// values (wave 1 from the right edge, wave 3 from the left, both shear
+// strengths), otherwise both neighbours in full.
+template <class NB>
+__device__ __forceinline__ fp::Net<typename NB::V> xnet(const fp::Edge<typename NB::V> &w,
+                                                        typename NB::V nu, int order,
+                                                        bool all_sub) {
+    typedef typename NB::V V;
+    fp::Up<V> u1, u3;
+    if (all_sub) {
+        V b2l = w.b2, b2r = w.b2;
+        if (order >= 2) {
+            u1.s = NB::r(w.s1); u1.vh = NB::r(w.vh); u1.b = NB::r(w.b1);
+            u3.s = NB::l(w.s3); u3.vh = NB::l(w.vh); u3.b = NB::l(w.b3);
+            b2l = NB::l(w.b2); b2r = NB::r(w.b2);
+        }
+        return fp::net<V, true>(w, u1, u3, b2l, b2r, nu, order);
+    }
+    fp::Edge<V> wl = w, wr = w;
+    if (order >= 2) {
+        wl.s1 = NB::l(w.s1); wl.s3 = NB::l(w.s3); wl.vh = NB::l(w.vh);
+        wl.b1 = NB::l(w.b1); wl.b2 = NB::l(w.b2); wl.b3 = NB::l(w.b3);
+        wr.s1 = NB::r(w.s1); wr.s3 = NB::r(w.s3); wr.vh = NB::r(w.vh);
+        wr.b1 = NB::r(w.b1); wr.b2 = NB::r(w.b2); wr.b3 = NB::r(w.b3);
+    }
+    fp::upwind(w, wl, wr, u1, u3);
+    return fp::net<V, false>(w, u1, u3, wl.b2, wr.b2, nu, order);
 }
 
-// x-sweep of one row held across the warp; valid in lanes 2..29.
-__device__ __forceinline__ XCell xsweep(const XCell &c, float g, float nux, int order) {
-    const fwave::EdgeS w = fwave::solve1(g, c.h, c.mu, c.mv, c.u, c.v, c.sq, c.eta, dn(c.h),
-                                         dn(c.mu), dn(c.mv), dn(c.u), dn(c.v), dn(c.sq),
-                                         dn(c.eta));   // edge (l|l+1)
-    float4 lr;
-    float2 r;
-    fwave::net_of(edge_up(w), w, edge_dn(w), nux, order, lr, r);
-    // left edge of the cell -> R of edge (l-1|l), right edge -> L of edge (l|l+1)
-    const float d0 = fwave::mul(-nux, fwave::add(up(lr.w), lr.x));
-    const float d1 = fwave::mul(-nux, fwave::add(up(r.x), lr.y));
-    const float d2 = fwave::mul(-nux, fwave::add(up(r.y), lr.z));
-    return derive(fwave::add(c.eta, d0), fwave::add(c.h, d0), fwave::add(c.mu, d1),
-                  fwave::add(c.mv, d2));
-}
-
-// y-edge waves between x-swept cells a (below) and b (above), frame (h, hv, hu)
-__device__ __forceinline__ fwave::EdgeS ysolve(const XCell &a, const XCell &b, float g) {
-    return fwave::solve1(g, a.h, a.mv, a.mu, a.v, a.u, a.sq, a.eta, b.h, b.mv, b.mu, b.v, b.u,
-                         b.sq, b.eta);
+// x-sweep of one row held across the warp (x frame: mn = hu, mt = hv).
+// Returns the x-swept cell(s) in the y frame (mn = hv).  Lanes see their
+// right neighbour cells through NB::r; a cell takes R of the edge on its left
+// and L of the edge on its right.
+template <class NB>
+__device__ __forceinline__ fp::Cell<typename NB::V> xsweep(const fp::Cell<typename NB::V> &c,
+                                                           typename NB::V g_half, float nux,
+                                                           int order, int lane) {
+    typedef typename NB::V V;
+    fp::Cell<V> r;
+    r.h = NB::r(c.h); r.mn = NB::r(c.mn); r.mt = c.mt; r.sq = NB::r(c.sq);
+    r.su = NB::r(c.su); r.sv = NB::r(c.sv); r.P = NB::r(c.P); r.T = NB::r(c.T);
+    r.eta = NB::r(c.eta);
+    const fp::Edge<V> w = fp::solve(g_half, c, r);
+    const fp::Net<V> n =
+        xnet<NB>(w, fp::splat<V>(nux), order, __all_sync(kFull, NB::ok(w, lane)));
+    const V mnu = fp::splat<V>(-nux);
+    const V d0 = fp::mul(mnu, fp::add(NB::l(n.R0), n.L0));
+    const V d1 = fp::mul(mnu, fp::add(NB::l(n.R1), n.L1));
+    const V d2 = fp::mul(mnu, fp::add(NB::l(n.R2), n.L2));
+    return fp::derive(fp::add(c.eta, d0), fp::add(c.h, d0), fp::add(c.mt, d2),
+                      fp::add(c.mn, d1));
 }
 
 struct Raw4 {
@@ -114,10 +134,10 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
     bool fx, fy;
     const int col = ghost_index(gi, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
     const bool out = lane >= 2 && lane < kLanes - 2 && gi < v.nx;
-    XCell A = {}, B = {};            // x-swept rows j-2, j-1
-    fwave::EdgeS W1 = {}, W2 = {};   // y-edges (j-3|j-2), (j-2|j-1)
-    float4 nlr = make_float4(0.f, 0.f, 0.f, 0.f);   // y-net of edge (j-3|j-2)
-    float2 nr = make_float2(0.f, 0.f);
+    const float gh = 0.5f * g;
+    fp::Cell<float> A = {}, B = {};   // x-swept rows j-2, j-1 (y frame)
+    fp::Edge<float> W1 = {}, W2 = {};  // y-edges (j-3|j-2), (j-2|j-1)
+    fp::Net<float> N1 = {};            // net of edge (j-3|j-2)
     // strips away from the lower and upper boundary need no row mapping
     const bool yin = y0 - 2 >= 0 && ylast + 2 < v.ny;
     fy = false;
@@ -131,31 +151,34 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
             else row = ghost_index(j + 1, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
             Rn = load_raw(v, col, fx, row, fy);
         }
-        const XCell C = xsweep(derive(Rc.eta, Rc.eta + Rc.hb, Rc.mu, Rc.mv), g, nux, order);
-        fwave::EdgeS Wn = W2;
-        if (j >= y0 - 1) Wn = ysolve(B, C, g);   // edge (j-1|j)
-        float4 lr = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 r = make_float2(0.f, 0.f);
-        if (j >= y0 + 1) fwave::net_of(W1, W2, Wn, nuy, order, lr, r);   // edge (j-2|j-1)
+        const fp::Cell<float> C = xsweep<Nb1>(
+            fp::derive(Rc.eta, fp::add(Rc.eta, Rc.hb), Rc.mu, Rc.mv), gh, nux, order, lane);
+        fp::Edge<float> Wn = W2;
+        if (j >= y0 - 1) Wn = fp::solve(gh, B, C);   // edge (j-1|j)
+        fp::Net<float> N = {};
+        if (j >= y0 + 1) {   // net of edge (j-2|j-1), used by the output lanes
+            const bool all_sub = __all_sync(kFull, !out || fp::subsonic(W2.s1, W2.s3));
+            N = fp::net3(W1, W2, Wn, nuy, order, all_sub);
+        }
         if (j >= y0 + 2 && out) {
             // y-sweep of row j-2: lower edge -> R of the previous net, upper
-            // edge -> L of this one; nets are in (h, hv, hu) order
-            const float d0 = fwave::mul(-nuy, fwave::add(nlr.w, lr.x));
-            const float d2 = fwave::mul(-nuy, fwave::add(nr.x, lr.y));
-            const float d1 = fwave::mul(-nuy, fwave::add(nr.y, lr.z));
-            const float ne = fwave::add(A.eta, d0), nmu = fwave::add(A.mu, d1);
-            const float nmv = fwave::add(A.mv, d2);
+            // edge -> L of this one (y frame: component 1 is hv, 2 is hu)
+            const float d0 = fp::mul(-nuy, fp::add(N1.R0, N.L0));
+            const float d1 = fp::mul(-nuy, fp::add(N1.R1, N.L1));
+            const float d2 = fp::mul(-nuy, fp::add(N1.R2, N.L2));
+            const float ne = fp::add(A.eta, d0), nmv = fp::add(A.mn, d1);
+            const float nmu = fp::add(A.mt, d2);
             const size_t o = (size_t)(j - 2) * v.nx + gi;
             v.o0[o] = ne;
             v.o1[o] = nmu;
             v.o2[o] = nmv;
-            const float h = fwave::add(A.h, d0);
+            const float h = fp::add(A.h, d0);
             bad |= !(h > 0.f) || !isfinite(nmu) || !isfinite(nmv);
             smax = fmaxf(smax, cfl_f32(h, nmu, nmv, g, v.rdx, v.rdy, 1));
         }
         A = B; B = C;
         W1 = W2; W2 = Wn;
-        nlr = lr; nr = r;
+        N1 = N;
     }
 }
 

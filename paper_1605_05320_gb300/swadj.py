@@ -49,6 +49,7 @@ EXPORTS = [
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
+    "swa_alu_probe_ops", "swa_alu_probe",
 ]
 
 
@@ -152,6 +153,8 @@ def load(path: str = LIB_PATH):
         "swa_create_amr": ([_V, _V, _I, _I, _V, _SZ, _V, _P(_V)], _I),
         "swa_destroy_amr": ([_V], _I),
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
+        "swa_alu_probe_ops": ([_I, _I, _I, _I], _D),
+        "swa_alu_probe": ([_I, _I, _I, _I, _V, _V], _I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -348,6 +351,46 @@ def swa_grid_gauge_rows(grid, stream=None):
     r = ctypes.c_longlong()
     _chk(load().swa_grid_gauge_rows(grid, ctypes.byref(r), _stream(stream)))
     return int(r.value)
+
+
+SWA_PROBE_FFMA64, SWA_PROBE_FFMA32, SWA_PROBE_FFMA32X2, SWA_PROBE_RSQRT32 = 0, 1, 2, 3
+
+
+def swa_alu_probe_ops(kind, blocks, threads, iters):
+    return load().swa_alu_probe_ops(int(kind), int(blocks), int(threads), int(iters))
+
+
+def swa_alu_probe(kind, blocks, threads, iters, sink_dev, stream=None):
+    return _chk(load().swa_alu_probe(int(kind), int(blocks), int(threads), int(iters),
+                                     _ptr(sink_dev), _stream(stream)))
+
+
+def measure_alu_peaks(device=0, iters=4096, reps=3):
+    """Measured peaks on the current device, per second: FP64 and FP32 FMA
+    flops, packed FP32x2 FMA flops, FP32 reciprocal square roots.  Each probe
+    fills every SM (8 blocks of 256 threads per SM), best of `reps`."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    sink = torch.zeros(blocks, dtype=torch.float32, device="cuda")
+    out = {}
+    names = {SWA_PROBE_FFMA64: "fp64_fma_flops", SWA_PROBE_FFMA32: "fp32_fma_flops",
+             SWA_PROBE_FFMA32X2: "fp32x2_fma_flops", SWA_PROBE_RSQRT32: "fp32_rsqrt_ops"}
+    s = torch.cuda.current_stream()
+    for kind, name in names.items():
+        it = iters // 8 if kind == SWA_PROBE_FFMA64 else iters
+        swa_alu_probe(kind, blocks, threads, 16, sink, s)   # warm up
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            swa_alu_probe(kind, blocks, threads, it, sink, s)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = swa_alu_probe_ops(kind, blocks, threads, it) / (best * 1e-3)
+    return out
 
 
 def swa_step_forward_static(desc, q_in, q_out, bath, dt, smax_out_dev=None, stream=None):
