@@ -362,6 +362,7 @@ fwd_ctu_kernel(FwdParams<R> p) {
             clk->cur = cur ^ 1;
             clk->nsteps = clk->nsteps + 1;
             clk->ticket = 0u;
+            clk->work = 0u;
         }
     }
 }

@@ -66,6 +66,7 @@ __device__ __forceinline__ void finish_step(DevClock *clkp, double *partial, int
             clk->cur = cur ^ 1;
             clk->nsteps = clk->nsteps + 1;
             clk->ticket = 0u;
+            clk->work = 0u;
         }
     }
 }

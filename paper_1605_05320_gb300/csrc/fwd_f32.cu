@@ -18,40 +18,50 @@ namespace swadj {
 namespace f32 {
 
 
-// 2D grids: warp strips, one strip per warp.
-__global__ void __launch_bounds__(strip::kThreads, 5) fwd_f32_strips(FwdParams<float> p, int rows) {
+// 2D grids: persistent warps take work units from the clock's counter, one
+// unit a strip of 28 output columns by `rows` rows, in row-major order.
+// Where the ocean is at rest a unit costs little (strips.cuh), so units are
+// short and taken as warps free up: the active part of the domain spreads
+// over every SM instead of over the few warps whose strips it crosses.
+__global__ void __launch_bounds__(strip::kThreads, 5)
+    fwd_f32_strips(FwdParams<float> p, int rows, int nunits) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
     __shared__ float red[strip::kThreads / 32];
     __shared__ int am_last;
+    __shared__ strip::Ring ring[strip::kThreads / 32];
     double t_now = 0.0, dt = 0.0;
     if (!fwave::begin_step(p.clk, p.t_end, (double)p.dx, (double)p.dy, s_nu, &s_cur, &s_run,
                            t_now, dt))
         return;
     const int cur = s_cur;
-    // with gauge recording, one extra block (the last) samples the state the
-    // step starts from while the others step it
+    // with gauge recording, the last block first samples the state the step
+    // starts from (the others write the other buffer)
     if (p.gauges.n > 0 && blockIdx.x == gridDim.x - 1)
         record_gauges<float, strip::kThreads>(p.gauges, p.q[cur][0], p.bath, p.nx, p.ny, 1,
-                                           t_now);
-    const int nsx = (p.nx + strip::kOut - 1) / strip::kOut, nsy = (p.ny + rows - 1) / rows;
-    const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                                              t_now);
+    const int nsx = (p.nx + strip::kOut - 1) / strip::kOut;
+    strip::View v;
+    v.q0 = p.q[cur][0]; v.q1 = p.q[cur][1]; v.q2 = p.q[cur][2]; v.hb = p.bath;
+    v.o0 = p.q[cur ^ 1][0]; v.o1 = p.q[cur ^ 1][1]; v.o2 = p.q[cur ^ 1][2];
+    v.nx = p.nx; v.ny = p.ny;
+    v.rdx = 1.f / p.dx; v.rdy = 1.f / p.dy;
+    v.bc = p.bc;
     float smax = 0.f;
     bool bad = false;
-    if (unit < nsx * nsy) {   // warp-uniform
-        const int sy = unit / nsx, sx = unit - sy * nsx;
-        strip::View v;
-        v.q0 = p.q[cur][0]; v.q1 = p.q[cur][1]; v.q2 = p.q[cur][2]; v.hb = p.bath;
-        v.o0 = p.q[cur ^ 1][0]; v.o1 = p.q[cur ^ 1][1]; v.o2 = p.q[cur ^ 1][2];
-        v.nx = p.nx; v.ny = p.ny;
-        v.rdx = 1.f / p.dx; v.rdy = 1.f / p.dy;
-        v.bc = p.bc;
-        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order, smax,
-                       bad);
+    const int lane = threadIdx.x & 31;
+    for (;;) {   // warp-uniform
+        int u = 0;
+        if (lane == 0) u = (int)atomicAdd(&p.clk->work, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= nunits) break;
+        const int sy = u / nsx, sx = u - sy * nsx;
+        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order,
+                          ring[threadIdx.x >> 5], smax, bad);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,
-                                     t_now, dt, cur);
+                                        t_now, dt, cur);
 }
 
 // 1D grids: one thread per cell, solving the four edges it needs itself
@@ -106,60 +116,47 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
 
 }  // namespace f32
 
-static int strip_blocks(int nx, int ny, int rows) {
-    const long long units = (long long)((nx + strip::kOut - 1) / strip::kOut) *
-                            ((ny + rows - 1) / rows);
-    constexpr int wpb = strip::kThreads / 32;
-    return (int)((units + wpb - 1) / wpb);
+// Rows of a work unit of the FP32 2D step: the requested strip height (16,
+// 32 or 64), else kUnitRows.  All heights give the same results.
+constexpr int kUnitRows = 32;
+// Persistent blocks at most (reduction slots of the grid workspace).
+constexpr int kMaxStepBlocks = 4096;
+
+static int unit_rows(const FwdParams<float> &p) {
+    return (p.fwd_rows == 16 || p.fwd_rows == 32 || p.fwd_rows == 64) ? p.fwd_rows : kUnitRows;
 }
 
-// Strip height requested for the FP32 2D step (16, 32 or 64), else 0.
-static int requested_rows(const FwdParams<float> &p) {
-    return (p.fwd_rows == 16 || p.fwd_rows == 32 || p.fwd_rows == 64) ? p.fwd_rows : 0;
+static int strip_units(int nx, int ny, int rows) {
+    return ((nx + strip::kOut - 1) / strip::kOut) * ((ny + rows - 1) / rows);
 }
 
-// Default strip height.  Warps of one resident wave (all SMs full) hide
-// each other's latency best, so the default is the lowest height (at least
-// 16 rows) whose strips all fit in one wave, one block kept for the gauge
-// block; when none does (very large grids), the one of 16 .. 256 rows
-// minimising (waves of strips) x (rows + 4), the rows a strip x-sweeps.
-// All heights give the same results.
-static int default_rows(int nx, int ny) {
-    static long long slots = 0;
-    if (slots == 0) {
+// Blocks of one resident wave of the strip kernel on the current device.
+static int resident_blocks() {
+    static int blocks = 0;
+    if (blocks == 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32::fwd_f32_strips,
                                                       strip::kThreads, 0);
-        slots = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1) *
-                (strip::kThreads / 32);
+        blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+        if (blocks > kMaxStepBlocks) blocks = kMaxStepBlocks;
     }
-    const long long nsx = (nx + strip::kOut - 1) / strip::kOut;
-    const long long per_col = (slots - strip::kThreads / 32) / nsx;   // strips down a column
-    if (per_col >= 1) {
-        long long rows = (ny + per_col - 1) / per_col;
-        if (rows < 16) rows = 16;
-        if (rows <= 256) return (int)rows;
-    }
-    int best = 32;
-    long long best_cost = -1;
-    for (int rows : {256, 128, 64, 32, 16}) {
-        const long long units = nsx * ((ny + rows - 1) / rows);
-        const long long cost = ((units + slots - 1) / slots) * (rows + 4);
-        if (best_cost < 0 || cost < best_cost) { best = rows; best_cost = cost; }
-    }
-    return best;
+    return blocks;
 }
 
 template <>
 int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
     FwdParams<float> p = p0;
     if (p.two_d) {
-        const int req = requested_rows(p);
-        const int rows = req ? req : default_rows(p.nx, p.ny);
-        p.nblocks = strip_blocks(p.nx, p.ny, rows) + (p.gauges.n > 0 ? 1 : 0);
-        f32::fwd_f32_strips<<<p.nblocks, strip::kThreads, 0, st>>>(p, rows);
+        const int rows = unit_rows(p);
+        const int units = strip_units(p.nx, p.ny, rows);
+        constexpr int wpb = strip::kThreads / 32;
+        int blocks = (units + wpb - 1) / wpb;
+        const int wave = resident_blocks();
+        if (blocks > wave) blocks = wave;
+        p.nblocks = blocks + (p.gauges.n > 0 ? 1 : 0);
+        f32::fwd_f32_strips<<<p.nblocks, strip::kThreads, 0, st>>>(p, rows, units);
         return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
     }
     dim3 grid((p.nx + 255) / 256, 1);
@@ -170,11 +167,11 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
 
 template <>
 int fwd_step_blocks<float>(const FwdParams<float> &p) {
-    // one reduction slot per block: of the requested strip height, else of
-    // the lowest one (an upper bound for the default), and the gauge block
+    // one reduction slot per block: at most one block per 4 units (of the
+    // lowest height), at most kMaxStepBlocks, and the gauge block
     if (p.two_d) {
-        const int req = requested_rows(p);
-        return strip_blocks(p.nx, p.ny, req ? req : 16) + 1;   // + the gauge block
+        const int b = (strip_units(p.nx, p.ny, 16) + 3) / 4;
+        return (b < kMaxStepBlocks ? b : kMaxStepBlocks) + 1;
     }
     return (p.nx + 255) / 256;
 }

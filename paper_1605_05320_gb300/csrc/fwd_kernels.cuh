@@ -309,6 +309,7 @@ fwd_step_kernel(FwdParams<R> p) {
             clk->cur = cur ^ 1;
             clk->nsteps = clk->nsteps + 1;
             clk->ticket = 0u;
+            clk->work = 0u;
         }
     }
 }
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
             clk->cur = 0;
             clk->nsteps = 0;
             clk->ticket = 0u;
+            clk->work = 0u;
         }
     }
 }

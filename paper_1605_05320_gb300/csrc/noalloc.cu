@@ -36,13 +36,15 @@ static_assert(kStaticScratchBytes == kStaticClockBytes + 8 * (size_t)kStaticMaxB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 // Puts the static clock in the state a step starts from: time 0, the
-// caller's dt, buffer 0 holding the input, no steps, block ticket 0.
+// caller's dt, buffer 0 holding the input, no steps, block ticket and
+// work-unit counter 0.
 __global__ void static_clock_reset(DevClock *clk, double dt) {
     clk->t = 0.0;
     clk->dt_cfl = dt;
     clk->nsteps = 0;
     clk->cur = 0;
     clk->ticket = 0u;
+    clk->work = 0u;
     clk->smax = 0.0;
 }
 

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
     __shared__ int s_cur, s_run;
     __shared__ float red[strip::kThreads / 32];
     __shared__ int am_last;
+    __shared__ strip::Ring ring[strip::kThreads / 32];
     double t_now = 0.0, dt = 0.0;
     if (!fwave::begin_step(p.clk, p.t_end, p.dx, p.dy, s_nu, &s_cur, &s_run, t_now, dt)) return;
     const int cur = s_cur;
@@ -60,7 +61,8 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
         v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
         v.o0 = P.q[cur ^ 1][0]; v.o1 = P.q[cur ^ 1][1]; v.o2 = P.q[cur ^ 1][2];
         v.nx = P.nx; v.ny = P.ny; v.rdx = P.rdx; v.rdy = P.rdy; v.bc = P.bc;
-        strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order, smax, bad);
+        strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
+                          ring[threadIdx.x >> 5], smax, bad);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
@@ -99,6 +101,7 @@ __global__ void level_clock_kernel(DevClock *clk, const double *smax, double t0,
     clk->cur = 0;
     clk->nsteps = 0;
     clk->ticket = 0u;
+    clk->work = 0u;
 }
 
 __global__ void to_float_kernel(const double *src, float *dst, const double *sub, int negate,

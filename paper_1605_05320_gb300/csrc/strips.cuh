@@ -110,23 +110,42 @@ struct Raw4 {
     float eta, mu, mv, hb;
 };
 
-__device__ __forceinline__ Raw4 load_raw(const View &v, int col, bool fx, int row, bool fy) {
+// Rows are staged through a per-warp ring of shared memory by asynchronous
+// copies (cp.async), kRing rows in flight, so that a warp walking its strip
+// keeps enough loads outstanding to cover the memory latency.  Each lane
+// copies and later reads only its own column of a row, so the ring needs no
+// synchronisation beyond the lane's own wait for its copy groups.
+constexpr int kRing = 8;                 // rows in flight per warp (a power of 2)
+struct Ring {
+    float v[kRing][4][kLanes];           // [slot][eta, hu, hv, hbar][lane]
+};
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's newest copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fetch_row(Ring &R, int slot, const View &v, int col, int row,
+                                          int lane) {
     const size_t o = (size_t)row * v.nx + col;
-    Raw4 r;
-    r.eta = ld_early(v.q0 + o);
-    r.hb = ld_early(v.hb + o);
-    const float mu = ld_early(v.q1 + o), mv = ld_early(v.q2 + o);
-    r.mu = fx ? -mu : mu;
-    r.mv = fy ? -mv : mv;
-    return r;
+    cp_async4(&R.v[slot][0][lane], v.q0 + o);
+    cp_async4(&R.v[slot][1][lane], v.q1 + o);
+    cp_async4(&R.v[slot][2][lane], v.q2 + o);
+    cp_async4(&R.v[slot][3][lane], v.hb + o);
 }
 
 // One strip of view v: output columns x0 .. x0 + 27 and rows y0 .. y0 +
-// rows - 1 (clipped to the view).  Called by all 32 lanes of a warp.
-// Accumulates the CFL maximum of the new cells into smax and sets bad on a
-// non-positive depth or non-finite momentum.
+// rows - 1 (clipped to the view).  Called by all 32 lanes of a warp, with
+// the warp's own ring R.  Accumulates the CFL maximum of the new cells into
+// smax and sets bad on a non-positive depth or non-finite momentum.
 __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int rows, float nux,
-                                           float nuy, float g, int order, float &smax,
+                                           float nuy, float g, int order, Ring &R, float &smax,
                                            bool &bad) {
     const int lane = threadIdx.x & 31;
     const int ylast = (y0 + rows < v.ny ? y0 + rows : v.ny) - 1;
@@ -138,25 +157,62 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
     fp::Cell<float> A = {}, B = {};   // x-swept rows j-2, j-1 (y frame)
     fp::Edge<float> W1 = {}, W2 = {};  // y-edges (j-3|j-2), (j-2|j-1)
     fp::Net<float> N1 = {};            // net of edge (j-3|j-2)
+    // rest: bit k set when row j-k is exactly at rest (eta = hu = hv = 0) in
+    // every lane of the warp.  There every wave is exactly zero, so the
+    // x-sweep of such a row is the identity, an edge between two such rows
+    // has no waves, and a net whose three edges lie in such rows is zero:
+    // that work is skipped and its exact result used (the ocean ahead of a
+    // tsunami is at rest).  The record of a wave-free edge has zero
+    // strengths, so any limiter ratio formed with it is zero as well.
+    unsigned rest = 0;
+    fp::Edge<float> still = {};
+    still.s1 = -1.f;
+    still.s3 = 1.f;
     // strips away from the lower and upper boundary need no row mapping
     const bool yin = y0 - 2 >= 0 && ylast + 2 < v.ny;
-    fy = false;
-    int row = yin ? y0 - 2 : ghost_index(y0 - 2, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
-    Raw4 Rn = load_raw(v, col, fx, row, fy);
-#pragma unroll 3
-    for (int j = y0 - 2; j <= ylast + 2; j++) {
-        const Raw4 Rc = Rn;
-        if (j < ylast + 2) {
-            if (yin) row = j + 1;
-            else row = ghost_index(j + 1, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
-            Rn = load_raw(v, col, fx, row, fy);
+    const int jend = ylast + 2;
+    int jn = y0 - 2, sn = 0;   // next row to fetch and its ring slot
+#pragma unroll
+    for (int k = 0; k < kRing - 1; k++) {
+        if (jn <= jend) {
+            const int row = yin ? jn : ghost_index(jn, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+            fetch_row(R, sn, v, col, row, lane);
         }
-        const fp::Cell<float> C = xsweep<Nb1>(
-            fp::derive(Rc.eta, fp::add(Rc.eta, Rc.hb), Rc.mu, Rc.mv), gh, nux, order, lane);
+        cp_commit();
+        jn++;
+        sn = (sn + 1) & (kRing - 1);
+    }
+    int sc = 0;   // ring slot of row j
+#pragma unroll 3
+    for (int j = y0 - 2; j <= jend; j++) {
+        if (jn <= jend) {
+            const int row = yin ? jn : ghost_index(jn, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+            fetch_row(R, sn, v, col, row, lane);
+        }
+        cp_commit();
+        jn++;
+        sn = (sn + 1) & (kRing - 1);
+        cp_wait<kRing - 1>();   // row j has landed
+        fy = false;
+        if (!yin) ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+        Raw4 Rc;
+        Rc.eta = R.v[sc][0][lane];
+        const float mu = R.v[sc][1][lane], mv = R.v[sc][2][lane];
+        Rc.hb = R.v[sc][3][lane];
+        Rc.mu = fx ? -mu : mu;
+        Rc.mv = fy ? -mv : mv;
+        sc = (sc + 1) & (kRing - 1);
+        const bool at_rest = __all_sync(kFull, Rc.eta == 0.f && Rc.mu == 0.f && Rc.mv == 0.f);
+        rest = (rest << 1) | (at_rest ? 1u : 0u);
+        const float h = fp::add(Rc.eta, Rc.hb);
+        const fp::Cell<float> C = at_rest
+                                      ? fp::derive(Rc.eta, h, Rc.mv, Rc.mu)
+                                      : xsweep<Nb1>(fp::derive(Rc.eta, h, Rc.mu, Rc.mv), gh, nux,
+                                                    order, lane);
         fp::Edge<float> Wn = W2;
-        if (j >= y0 - 1) Wn = fp::solve(gh, B, C);   // edge (j-1|j)
+        if (j >= y0 - 1) Wn = (rest & 3u) == 3u ? still : fp::solve(gh, B, C);   // edge (j-1|j)
         fp::Net<float> N = {};
-        if (j >= y0 + 1) {   // net of edge (j-2|j-1), used by the output lanes
+        if (j >= y0 + 1 && (rest & 15u) != 15u) {   // net of edge (j-2|j-1)
             const bool all_sub = __all_sync(kFull, !out || fp::subsonic(W2.s1, W2.s3));
             N = fp::net3(W1, W2, Wn, nuy, order, all_sub);
         }

@@ -18,6 +18,7 @@ struct DevClock {
     long long nsteps;   // steps taken
     int cur;            // buffer index holding Q^n
     unsigned int ticket;  // last-block-done counter, 0 between launches
+    unsigned int work;    // next work unit of a persistent step kernel, 0 between launches
     double smax;        // s_max(Q^n)
 };
 
