@@ -304,6 +304,77 @@ def compare_schemes(scen, stream, steps=100):
     return out
 
 
+def measure_active_forward(scen, stream, steps=100, seed=7):
+    """Outside the timed region: the FP32 forward step on a state with no
+    cell at rest (the basin's initial surface plus seeded random momenta of
+    +-5 m^2/s everywhere), so no row can skip its wave arithmetic: the
+    step's cost where the whole ocean moves.  3 warm-up launches, then
+    `steps` launches between CUDA events on the launching stream."""
+    S, torch = scen.S, scen.torch
+    hs = stream.cuda_stream
+    rng = np.random.default_rng(seed)
+    n = scen.n
+    g = S.Grid(scen.desc, scen.sc.B)
+    g.set_state(scen.sc.eta0, rng.uniform(-5.0, 5.0, n), rng.uniform(-5.0, 5.0, n), 0.0, hs)
+    g.step(3, 1e12, hs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps, 1e12, hs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    peak, _ = load_peaks()
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("device status nonzero after the active-state forward steps")
+    del g
+    return {"steps": steps, "us_per_step": round(us, 2),
+            "cell_updates_per_s": n / (us * 1e-6),
+            "hbm_frac_of_measured": round(28.0 * n / (us * 1e-6) / 1e9 / peak, 4)}
+
+
+def measure_fp64(scen, stream, alu, steps=10):
+    """Outside the timed region: the FP64 forward and adjoint steps on the
+    same basin (the plain per-grid FP64 form), 2 warm-up launches then
+    `steps` launches each, against the measured FP64 FMA rate (counted
+    method flops per cell; a division or square root costs several FMA-pipe
+    slots, so the fraction is an upper bound of the real pipe use)."""
+    S, torch = scen.S, scen.torch
+    hs = stream.cuda_stream
+    sc = scen.sc
+    d = S.make_desc(2, sc.grid.nx, sc.grid.ny, 0.0, 0.0, sc.grid.dx, sc.grid.dy,
+                    precision=S.SWA_FP64)
+    g = S.Grid(d, sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0, hs)
+    g.step(2, 1e12, hs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps, 1e12, hs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_us = e0.elapsed_time(e1) * 1e3 / steps
+    del g
+    adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+    adj.step(2, hs)
+    e0.record(stream)
+    adj.step(steps, hs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    adj_us = e0.elapsed_time(e1) * 1e3 / steps
+    del adj
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("device status nonzero after the FP64 steps")
+    n = sc.grid.n
+    pk = alu["fp64_fma_flops"]
+    out = {"peak_fp64_tflops_measured": round(pk / 1e12, 3), "steps": steps}
+    for name, us, fl in (("fwd_step", fwd_us, FP64_FWD_FLOPS_PER_CELL),
+                         ("adj_step", adj_us, FP64_ADJ_FLOPS_PER_CELL)):
+        rate = fl * n / (us * 1e-6)
+        out[name] = {"us_per_step": round(us, 1), "flops_per_cell": fl,
+                     "tflops": round(rate / 1e12, 3), "frac_of_fp64_peak": round(rate / pk, 4),
+                     "hbm_gbs": round(56.0 * n / (us * 1e-6) / 1e9, 1)}
+    return out
+
+
 def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     """Outside the timed region: the two-level AMR glue on the basin.  The
     coarse level is the 2048^2 basin (1 km cells); the fine level is
@@ -408,15 +479,20 @@ def flag_bytes(sc_obj):
 # every edge solved and limited once (no halo recomputation): staging 6,
 # x-sweep 122 (Roe f-wave solve 29, net fluxes with MC limiter 78, update 10,
 # derived cell data 5), y-sweep 117, CFL term 12.
-FWD_OPS_PER_CELL = 257
+# FP32 operations per cell-update of the forward step in its subsonic form,
+# counted in the source (each add, mul, fma, min, max, select and special
+# function once; every edge solved and limited once): x-sweep 104 (cell
+# data 7, Roe solve 25, fluctuations and MC-limited net fluxes 62, update
+# 10), y-sweep 103, CFL term 11.
+FWD_OPS_PER_CELL = 218
+# FP64 operations per cell-update of the FP64 kernels, counted from the
+# oracle's formulas (division and square root as one): forward ~320 (per
+# sweep: Roe solve 49, fluctuations and limited corrections of three waves
+# 90, update 15; CFL 8), adjoint ~210 (per sweep: solve 20, two waves 78,
+# update 7).
+FP64_FWD_FLOPS_PER_CELL = 320
+FP64_ADJ_FLOPS_PER_CELL = 210
 ENV_GROUP = 8
-
-
-def alu_peak_tops(device_index, sm_max_mhz):
-    """FP32 lane-operation peak: SMs x 128 FP32 lanes x SM clock."""
-    import torch
-    sms = torch.cuda.get_device_properties(device_index).multi_processor_count
-    return sms * 128 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
 
 
 def run_ours(args, rank, world, local_rank):
@@ -518,24 +594,23 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(kern[dom]["frac"], 4), "traffic": traffic,
                 "bytes_per_launch": kern[dom]["bytes_per_launch"]}
     if args.precision == "fp32":
-        # the FP32 forward step needs more time at the FP32 lane peak than at
-        # the HBM peak: its roofline is the ALU one
+        # the FP32 forward step is compute-bound (it stays near its time with
+        # the loads taken out): its operation rate against the measured FP32
+        # peak, beside the HBM fraction the roofline object reports
         fw = kern["fwd_step"]
         ops = FWD_OPS_PER_CELL * scen.n
-        alu_peak = alu_peak_tops(local_rank, (clk or {}).get("sm_max_mhz"))
+        alu = S.measure_alu_peaks(local_rank)
+        fp32_ops_peak = alu["fp32_fma_flops"] / 2.0   # one lane operation per FMA-pipe slot
         fw["ops_per_launch"] = ops
         fw["tops"] = ops / (fw["avg_us"] * 1e-6) / 1e12
-        fw["alu_frac"] = fw["tops"] / alu_peak
+        fw["alu_frac"] = fw["tops"] * 1e12 / fp32_ops_peak
         fw["t_min_us"] = {"hbm": fw["bytes_per_launch"] / (peak * 1e9) * 1e6,
-                          "alu": ops / (alu_peak * 1e12) * 1e6}
-        if dom == "fwd_step":
-            roofline = {"bound": "alu", "kernel": dom, "achieved": round(fw["tops"], 3),
-                        "peak": round(alu_peak, 2),
-                        "peak_kind": "derived: SMs x 128 FP32 lanes x max SM clock",
-                        "unit": "T FP32 ops/s", "frac": round(fw["alu_frac"], 4),
-                        "traffic": traffic, "ops_per_launch": ops,
-                        "bytes_per_launch": fw["bytes_per_launch"],
-                        "hbm_frac_of_measured": round(fw["frac"], 4)}
+                          "alu": ops / fp32_ops_peak * 1e6}
+        roofline["alu"] = {"ops_per_cell": FWD_OPS_PER_CELL, "achieved_tops": round(fw["tops"], 3),
+                           "peak_tops": round(fp32_ops_peak / 1e12, 2),
+                           "peak_kind": "measured: FP32 FMA probe (swa_alu_probe), one op per "
+                                        "FMA slot", "frac": round(fw["alu_frac"], 4)}
+        roofline["measured_alu_peaks_tflops"] = {k: round(v / 1e12, 3) for k, v in alu.items()}
 
     # end-to-end through the C ABI with host buffers
     torch.cuda.synchronize()
@@ -577,6 +652,8 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             out["flag_comparison"] = compare_flags(scen, stream)
             out["forward_schemes"] = compare_schemes(scen, stream)
+            out["forward_active"] = measure_active_forward(scen, stream)
+            out["fp64"] = measure_fp64(scen, stream, alu=S.measure_alu_peaks(local_rank))
             out["amr"] = measure_amr(stream)
     return out
 

@@ -5,7 +5,9 @@ basin (1 km cells) through the public binding, with far less device memory
 than the full scenario (no 101-snapshot store), so that a capture that saves
 and restores device memory between passes stays small:
 
-  fwd   FP32 forward steps (fwd_f32_strips), ~120 MB on the device
+  fwd   FP32 forward steps (fwd_f32_strips), ~120 MB on the device; the
+        basin's initial state (the ocean at rest outside the source), or with
+        `--active` seeded random momenta everywhere (no cell at rest)
   ctu   FP32 unsplit forward steps with transverse waves (fwd_ctu_kernel),
         ~120 MB
   amr   two-level AMR steps on the basin: the 2048^2 coarse grid and 64
@@ -43,6 +45,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--steps", type=int, default=120)
     ap.add_argument("--full", action="store_true")
+    ap.add_argument("--active", action="store_true",
+                    help="fwd/ctu: random momenta of +-5 m^2/s in every cell")
     ap.add_argument("--adj-n", type=int, default=0,
                     help="flag: adjoint on a coarser adj_n^2 grid (bilinear stencil)")
     a = ap.parse_args(argv)
@@ -56,7 +60,11 @@ def main(argv=None):
         g = S.Grid(d, sc.B)
         if a.kernel == "ctu":
             g.set_scheme(S.SWA_SCHEME_CTU)
-        g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+        hu, hv = sc.hu0, sc.hv0
+        if a.active:
+            rng = np.random.default_rng(7)
+            hu, hv = rng.uniform(-5.0, 5.0, sc.grid.n), rng.uniform(-5.0, 5.0, sc.grid.n)
+        g.set_state(sc.eta0, hu, hv, 0.0)
         g.step(a.steps, sc.t_f)
         out["t"] = g.time()[0]
     elif a.kernel == "amr":
