@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patches", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -772,6 +773,153 @@ def oracle_sample(n, steps):
     return 2 * steps * sc.grid.n / sec, sec, O.num_threads(), what
 
 
+def precision_vs_oracle(n=256, L=2048e3, every=20, n_gauges=16, tol=1e-4):
+    """Oracle leg (host cores): the FP32 GPU path against the FP64 oracle over
+    a whole basin scenario on an n x n grid of the same generator (2048 km,
+    2000 CFL steps to t_f): a gauge sample and an adjoint-weighted flag pass
+    after every FWD_BLOCK forward steps on both sides, and the FP64 mass
+    audit (swa_grid_mass) of the FP32 state against the oracle's mass.  The
+    oracle is given the bathymetry FP32 storage holds.  At 8 km cells the
+    10 km target is coarsely resolved and m stays below 3e-4, so the flag
+    threshold is `tol` = 1e-4, inside the range m takes."""
+    import torch
+    import oracle as O
+    from paper_1605_05320_gb300 import swadj as S
+    from paper_1605_05320_gb300 import synth
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    sc = synth.config2(n=n, L=L, n_gauges=n_gauges)
+    sc.tol = tol
+    Bf = -(np.float32(-sc.B).astype(np.float64))
+    d = S.make_desc(2, n, n, 0.0, 0.0, sc.grid.dx, sc.grid.dy, precision=S.SWA_FP32)
+    g = S.Grid(d, sc.B)
+    g.set_state(sc.eta0, sc.hu0, sc.hv0, 0.0)
+    adj = S.Adjoint(d, sc.B_adj, sc.phi, sc.t_f)
+    N, _, _ = adj.info()
+    store = S.SnapStore(adj, N // every + 3, S.SWA_FP32)
+    store.run_adjoint(every)
+    og = O.Grid.from_spec(sc.grid)
+    hbar = np.maximum(-sc.B_adj, 0.0)
+    snaps, tau, _, _ = O.adj_run(og, hbar, sc.phi, sc.t_f, every)
+    xy = torch.tensor(sc.gauges, dtype=torch.float64, device="cuda")
+    gout = torch.zeros(len(sc.gauges), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(sc.grid.n, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mass = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.swa_grid_mass(g.h, mass)
+    m0 = float(mass.item())
+    area = sc.grid.dx * sc.grid.dy
+    h, hu, hv, t = sc.eta0 - Bf, sc.hu0.copy(), sc.hv0.copy(), 0.0
+    gerr, gmax, passes, differ, outside, flagged = 0.0, 0.0, 0, 0, 0, 0
+    while t < sc.t_f:
+        g.step(FWD_BLOCK, sc.t_f)
+        h, hu, hv, t, _ = O.fwd_run(og, h, hu, hv, Bf, FWD_BLOCK, sc.t_f, t)
+        S.swa_gauge_sample(g.h, len(sc.gauges), xy, gout)
+        S.swa_flag_cells(g.h, store.h, sc.t_s, sc.t_f, sc.tol, S.SWA_FLAG_INTERP, flags, None,
+                         cnt)
+        torch.cuda.synchronize()
+        g_ref = O.gauge(og, h, Bf, sc.gauges)
+        gerr = max(gerr, float(np.abs(gout.cpu().numpy() - g_ref).max()))
+        gmax = max(gmax, float(np.abs(g_ref).max()))
+        f_ref, m_ref, c_ref = O.flag(og, h, hu, hv, Bf, t, og, hbar, snaps, tau, sc.t_s,
+                                     sc.t_f, sc.tol, O.FLAG_INTERP)
+        f = flags.cpu().numpy()
+        near = np.abs(m_ref - sc.tol) <= 1e-3 * sc.tol
+        differ += int((f != f_ref).sum())
+        outside += int((f[~near] != f_ref[~near]).sum())
+        flagged += c_ref
+        passes += 1
+    S.swa_grid_mass(g.h, mass)
+    torch.cuda.synchronize()
+    if S.swa_sync_status() != 0:
+        raise RuntimeError("device status nonzero after the precision run")
+    m_ref = float(h.sum()) * area
+    return {"grid": f"{n}x{n} basin, {L / n / 1e3:.0f} km cells, FP32 perturbation form vs "
+                    f"FP64 oracle, whole run to t_f",
+            "forward_steps": int(g.time()[2]), "flag_passes": passes,
+            "gauges": len(sc.gauges), "gauge_max_abs_err_m": gerr,
+            "gauge_max_abs_m": gmax, "flag_cells_differing": differ,
+            "flag_cells_differing_outside_band": outside,
+            "flagged_cells_oracle": flagged, "tol": tol,
+            "mass_fp64_audit": {"initial": m0, "final": float(mass.item()),
+                                "drift_rel": abs(float(mass.item()) - m0) / m0,
+                                "oracle_final": m_ref,
+                                "rel_diff_vs_oracle": abs(float(mass.item()) - m_ref) / m_ref}}
+
+
+def serving_vs_plain(n_req=24, n_plain=4, rate=20.0, with_oracle=True):
+    """Served FP32 continuous batching on the first n_req requests of the
+    serving trace (Poisson at `rate`, sizes 512^2 .. 4096^2 over 2048 km)
+    against one resident 2048^2 adjoint with 150 FP32 snapshots, and the
+    plain per-grid FP64 form on the first n_plain requests of 512^2 or
+    1024^2 (an FP64 4096^2 scenario alone takes minutes), served again in
+    FP32 for the same-trace ratio; the gauge error of the served FP32
+    results against plain FP64, and of one served 512^2 request against
+    the FP64 oracle (oracle leg, host cores)."""
+    import torch
+    from paper_1605_05320_gb300 import serve as srv
+    from paper_1605_05320_gb300 import swadj as S
+    from paper_1605_05320_gb300 import synth
+    L = 2048e3
+    sc2 = synth.config2(n=256, L=L)
+    sc2.t_f = 2000.0 * 0.75 * 1e3 / np.sqrt(synth.G * 4000.0)
+    sc2.t_s = 0.32 * sc2.t_f
+    t0 = time.perf_counter()
+    adj = srv.ResidentAdjoint(2048, L, sc2.t_f, sc2.t_s, sc2.tol, sc2.meta["target"])
+    torch.cuda.synchronize()
+    adj_s = time.perf_counter() - t0
+    reqs = srv.trace_from_config(n_req, rate, (512, 1024, 2048, 4096))
+    res, st = srv.Server(adj).run(reqs)
+    small = [srv.Request(r.id, 0.0, r.n, r.amp, r.width, r.src_u, r.src_v)
+             for r in reqs if r.n <= 1024][:n_plain]
+    served_sub, sst = srv.Server(adj).run(small)
+    plain, pst = srv.run_plain(adj, small, precision=S.SWA_FP64)
+    gerr = 0.0
+    for p in plain:
+        q = next(x for x in served_sub if x.id == p.id)
+        k = min(len(q.gauges), len(p.gauges))
+        gerr = max(gerr, float(np.abs(q.gauges[:k] - p.gauges[:k]).max()))
+    # one served 512^2 request against the oracle (oracle leg)
+    orc = None
+    r512 = next((r for r in small if r.n == 512), None)
+    if r512 is not None and with_oracle:
+        import oracle as O
+        O.build()
+        O.set_threads(os.cpu_count() or 1)
+        out = next(x for x in served_sub if x.id == r512.id)
+        srv_ = srv.Server(adj)
+        n = 512
+        dx = L / n
+        spec = synth.GridSpec(2, n, n, 0.0, 0.0, dx, dx)
+        Bf = -(np.float32(-srv_.bathymetry(n)).astype(np.float64))
+        eta = synth.gaussian_field(spec, (0.1 + 0.6 * r512.src_u) * L,
+                                   (0.1 + 0.8 * r512.src_v) * L, r512.amp, r512.width)
+        og = O.Grid.from_spec(spec)
+        h, hu, hv, t = eta - Bf, np.zeros(spec.n), np.zeros(spec.n), 0.0
+        oerr = 0.0
+        for k in range(len(out.gauges)):
+            h, hu, hv, t, _ = O.fwd_run(og, h, hu, hv, Bf, srv.MACRO, adj.t_f, t)
+            oerr = max(oerr, float(np.abs(out.gauges[k] - O.gauge(og, h, Bf, srv_.gauges)).max()))
+        orc = {"request": r512.id, "gauges": len(srv_.gauges), "samples": len(out.gauges),
+               "gauge_max_abs_err_m": oerr}
+    lat_by = {}
+    for r in res:
+        lat_by.setdefault(r.n, []).append(r.latency)
+    return {"trace": {"requests": n_req, "rate_per_s": rate, "sizes": [512, 1024, 2048, 4096],
+                      "counts_by_size": {str(k): len(v) for k, v in sorted(lat_by.items())}},
+            "adjoint": {"grid": "2048x2048", "snapshots_fp32": adj.store.info()[0],
+                        "setup_s": round(adj_s, 3)},
+            "served_fp32": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in st.items()},
+            "p50_by_size_s": {str(k): round(float(np.percentile(v, 50)), 4)
+                              for k, v in sorted(lat_by.items())},
+            "same_requests": {"ids": [r.id for r in small], "sizes": [r.n for r in small],
+                              "served_fp32_scenarios_per_s": sst["scenarios_per_s"],
+                              "plain_fp64_scenarios_per_s": pst["scenarios_per_s"],
+                              "served_over_plain": sst["scenarios_per_s"] / pst["scenarios_per_s"],
+                              "gauge_max_abs_err_fp32_vs_fp64_m": gerr},
+            "vs_oracle": orc}
+
+
 def workload_config(n, world):
     """The workload both arms report (the reference arm times a bounded
     sample of it)."""
@@ -835,6 +983,11 @@ def main():
             out["cpu_baseline"] = {
                 "value": v, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
                 "sample": f"{what} ({sec:.1f} s, OpenMP)"}
+            # the rest of the oracle leg: precision of the FP32 path and the
+            # served form, each against the FP64 oracle on the host cores
+            out["precision"] = precision_vs_oracle()
+        if not args.no_serving:
+            out["serving"] = serving_vs_plain(with_oracle=not args.no_cpu_baseline)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -423,6 +423,20 @@ int swa_destroy_amr(swa_amr *amr);
  */
 int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
 
+/*
+ * FP64 audit of the conserved mass of the grid's current state: writes
+ * M = sum over interior cells of h dx dy (1D: h dx) to the device double
+ * *mass_dev, summed in double whatever the storage precision (FP32:
+ * h = (double) eta + (double) hbar), in a fixed order, so the same state
+ * always gives the same bits.  Between walls the conservative update keeps
+ * M constant (Eq. swe in conservation form); its drift measures the
+ * rounding of the step.  Asynchronous on `stream`; it uses the grid's
+ * reduction scratch, so issue it on the stream that steps the grid.
+ * SWA_EINVAL for a null argument, SWA_ESTATE before the state is set,
+ * SWA_ECUDA if a launch fails.
+ */
+int swa_grid_mass(const swa_grid *g, double *mass_dev, void *stream);
+
 /* ============================ ALU peak probes =============================
  * Measurement aid (no counterpart in the paper): throughput probes of the
  * arithmetic units that bound the step kernels, so that the FP64 and FP32

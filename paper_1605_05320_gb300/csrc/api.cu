@@ -961,6 +961,15 @@ int swa_grid_record_gauges(swa_grid *g, int n, const double *xy_dev, double *ser
     return SWA_OK;
 }
 
+int swa_grid_mass(const swa_grid *g, double *mass_dev, void *stream) {
+    if (!g || !mass_dev) return set_error(SWA_EINVAL, "null argument");
+    if (!g->state_set) return set_error(SWA_ESTATE, "grid state not set");
+    const void *q0[2] = {g->q[0][0], g->q[1][0]};
+    const double area = g->d.dx * (g->d.ndim == 2 ? g->d.dy : 1.0);
+    return mass_launch(q0, g->bath, g->d.precision == SWA_FP32, g->clk, g->n, area, g->partial,
+                       kInitBlocks, mass_dev, S(stream));
+}
+
 int swa_grid_gauge_rows(const swa_grid *g, long long *rows, void *stream) {
     if (!g || !rows) return set_error(SWA_EINVAL, "null argument");
     cudaStream_t st = S(stream);

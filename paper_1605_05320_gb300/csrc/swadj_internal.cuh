@@ -125,6 +125,10 @@ struct GridRefs {
     int state_set;
 };
 int grid_refs(const swa_grid *g, GridRefs *out);
+// FP64 mass audit (audit.cu)
+int mass_launch(const void *const q0[2], const void *bath, int fp32, const DevClock *clk,
+                size_t n, double area, double *partial, int max_blocks, double *out,
+                cudaStream_t st);
 }  // namespace swadj
 
 namespace swadj_host {

@@ -50,6 +50,7 @@ EXPORTS = [
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
     "swa_alu_probe_ops", "swa_alu_probe",
+    "swa_grid_mass",
 ]
 
 
@@ -154,6 +155,7 @@ def load(path: str = LIB_PATH):
         "swa_destroy_amr": ([_V], _I),
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
         "swa_alu_probe_ops": ([_I, _I, _I, _I], _D),
+        "swa_grid_mass": ([_V, _V, _V], _I),
         "swa_alu_probe": ([_I, _I, _I, _I, _V, _V], _I),
     }
     for name, (args, res) in sig.items():
@@ -345,6 +347,11 @@ def swa_gauge_sample(grid, n, xy_dev, eta_dev, stream=None):
 def swa_grid_record_gauges(grid, n, xy_dev, series_dev, times_dev, capacity, stream=None):
     return _chk(load().swa_grid_record_gauges(grid, int(n), _ptr(xy_dev), _ptr(series_dev),
                                               _ptr(times_dev), int(capacity), _stream(stream)))
+
+
+def swa_grid_mass(grid, mass_dev, stream=None):
+    """FP64 mass audit of the grid's current state into a device double."""
+    return _chk(load().swa_grid_mass(grid, _ptr(mass_dev), _stream(stream)))
 
 
 def swa_grid_gauge_rows(grid, stream=None):
