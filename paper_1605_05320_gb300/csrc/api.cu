@@ -171,6 +171,7 @@ struct swa_grid {
     int step_blocks;
     int state_set;
     int strip_rows;        // FP32 launch shape (0 = default)
+    int keep_rest;         // FP32 2D: compute wave-free rows in full
     int scheme;            // 2D update: SWA_SCHEME_SPLIT or SWA_SCHEME_CTU
     long long *gauge_row;  // device row counter of the fused gauge recording
     GaugeRec gauges;       // fused gauge recording (n = 0: off)
@@ -257,6 +258,7 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.nblocks = g->step_blocks;
     p.err = err_word();
     p.fwd_rows = g->strip_rows;
+    p.keep_rest = g->keep_rest;
     p.gauges = g->gauges;
     return p;
 }
@@ -444,6 +446,13 @@ int swa_grid_set_strip_rows(swa_grid *g, int rows) {
     if (rows != 0 && rows != 16 && rows != 32 && rows != 64)
         return set_error(SWA_EINVAL, "strip rows must be 0, 16, 32 or 64");
     g->strip_rows = rows;
+    return SWA_OK;
+}
+
+int swa_grid_set_rest_skip(swa_grid *g, int on) {
+    if (!g) return set_error(SWA_EINVAL, "null grid");
+    if (on != 0 && on != 1) return set_error(SWA_EINVAL, "rest skip must be 0 or 1");
+    g->keep_rest = !on;
     return SWA_OK;
 }
 

@@ -21,6 +21,7 @@ struct FwdParams {
     int nblocks;
     int *err;          // device error word (ERR_* bits)
     int fwd_rows;      // FP32 strip height (rows per block), 0 = default
+    int keep_rest;     // FP32 2D: 1 computes wave-free rows in full (no skipping)
     GaugeRec gauges;   // fused gauge recording (n = 0: off)
 };
 

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(strip::kThreads, 5)
         if (u >= nunits) break;
         const int sy = u / nsx, sx = u - sy * nsx;
         strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order,
-                          ring[threadIdx.x >> 5], smax, bad);
+                          ring[threadIdx.x >> 5], smax, bad, !p.keep_rest);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,

@@ -143,10 +143,12 @@ __device__ __forceinline__ void fetch_row(Ring &R, int slot, const View &v, int 
 // One strip of view v: output columns x0 .. x0 + 27 and rows y0 .. y0 +
 // rows - 1 (clipped to the view).  Called by all 32 lanes of a warp, with
 // the warp's own ring R.  Accumulates the CFL maximum of the new cells into
-// smax and sets bad on a non-positive depth or non-finite momentum.
+// smax and sets bad on a non-positive depth or non-finite momentum.  skip:
+// take the exact shortcut of wave-free rows (false computes them in full,
+// with the same result).
 __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int rows, float nux,
                                            float nuy, float g, int order, Ring &R, float &smax,
-                                           bool &bad) {
+                                           bool &bad, bool skip = true) {
     const int lane = threadIdx.x & 31;
     const int ylast = (y0 + rows < v.ny ? y0 + rows : v.ny) - 1;
     const int gi = x0 - 2 + lane;
@@ -202,7 +204,8 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
         Rc.mu = fx ? -mu : mu;
         Rc.mv = fy ? -mv : mv;
         sc = (sc + 1) & (kRing - 1);
-        const bool at_rest = __all_sync(kFull, Rc.eta == 0.f && Rc.mu == 0.f && Rc.mv == 0.f);
+        const bool at_rest =
+            __all_sync(kFull, skip && Rc.eta == 0.f && Rc.mu == 0.f && Rc.mv == 0.f);
         rest = (rest << 1) | (at_rest ? 1u : 0u);
         const float h = fp::add(Rc.eta, Rc.hb);
         const fp::Cell<float> C = at_rest

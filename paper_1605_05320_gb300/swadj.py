@@ -34,6 +34,7 @@ EXPORTS = [
     "swa_set_state", "swa_get_state", "swa_step_forward", "swa_get_time",
     "swa_grid_set_strip_rows",
     "swa_grid_set_scheme",
+    "swa_grid_set_rest_skip",
     "swa_grid_arrays",
     "swa_adjoint_workspace_bytes", "swa_create_adjoint", "swa_destroy_adjoint",
     "swa_adjoint_info", "swa_step_adjoint", "swa_get_adjoint_state",
@@ -120,6 +121,7 @@ def load(path: str = LIB_PATH):
         "swa_grid_arrays": ([_V, _P(_V), _P(_V), _P(_V), _P(_V), _V], _I),
         "swa_grid_set_strip_rows": ([_V, _I], _I),
         "swa_grid_set_scheme": ([_V, _I], _I),
+        "swa_grid_set_rest_skip": ([_V, _I], _I),
         "swa_adjoint_workspace_bytes": ([D], _SZ),
         "swa_create_adjoint": ([D, _V, _V, _D, _V, _SZ, _V, _P(_V)], _I),
         "swa_destroy_adjoint": ([_V], _I),
@@ -245,6 +247,10 @@ def swa_get_time(h, stream=None):
 
 def swa_grid_set_strip_rows(h, rows):
     return _chk(load().swa_grid_set_strip_rows(h, int(rows)))
+
+
+def swa_grid_set_rest_skip(h, on):
+    return _chk(load().swa_grid_set_rest_skip(h, int(on)))
 
 
 def swa_grid_set_scheme(h, scheme):
