@@ -208,6 +208,16 @@ int swa_adjoint_info(const swa_adjoint *adj, long long *n_steps, double *dt,
                      long long *steps_done);
 /* Take nsteps adjoint steps (clamped to the remaining N - steps_done). */
 int swa_step_adjoint(swa_adjoint *adj, int nsteps, void *stream);
+/*
+ * Temporal blocking of the fixed-dt adjoint (a 2D FP32 adjoint only): k = 2
+ * lets swa_step_adjoint and swa_run_adjoint take two steps per launch
+ * wherever no snapshot falls on the step between them (one pass over the
+ * state instead of two: each warp loads its strip once, with 4 halo rows and
+ * columns, and writes only the second step's state).  The states and
+ * snapshots are bit-identical to k = 1 (the default).  SWA_EINVAL for a
+ * null adjoint, k not 1 or 2, or k = 2 on an FP64 or 1D adjoint.
+ */
+int swa_adjoint_set_steps_per_pass(swa_adjoint *adj, int k);
 /* Read the adjoint state (FP64, (ndim+1) x n, component-major). */
 int swa_get_adjoint_state(swa_adjoint *adj, double *q, int where, void *stream);
 /*

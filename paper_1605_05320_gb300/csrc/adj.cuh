@@ -21,6 +21,9 @@ struct AdjParams {
     size_t snap_comp_stride;  // elements between components of one snapshot
     double *tau_dev;
     double tau_val;
+    // FP32 2D only: take two steps in this launch (the snapshot, if any, is
+    // of the state after both)
+    int two_steps;
 };
 
 template <typename R>

@@ -205,10 +205,175 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     }
 }
 
+// ------------------------------------------- two steps per pass (temporal blocking)
+// The adjoint's step is fixed, so two of its steps can be taken in one pass
+// over the state: a warp loads its strip once and feeds every row through
+// the y-then-x pipeline of the first step, whose finished rows feed the
+// same pipeline of the second step, and only the second step's rows are
+// written.  Each step needs two cells either side, so a strip of 32 lanes
+// outputs 24 columns and reads 4 halo rows above and below.  Every edge is
+// solved and limited by the same arithmetic as in the one-step kernel, and
+// the intermediate state's ghost cells are the index-mapped interior cells
+// the one-step path would load (a column mapped by a shuffle from the lane
+// holding its source, a row from the interior rows kept for it), so two
+// steps per pass give the one-step path's state bit for bit.
+constexpr int kOut2 = kLanes - 8;   // output columns per two-step strip
+constexpr int kRows2 = 32;          // output rows per two-step strip
+
+// One step's pipeline over the rows of a strip.  Rows are fed in order; the
+// feed of the fifth and every later row r completes row r - 2 (y-sweep, then
+// x-sweep across the warp), valid in lanes 2..29.
+struct Pipe {
+    CellA A, B;       // rows r-2, r-1
+    EdgeA W1, W2;     // y-edges (r-3|r-2), (r-2|r-1)
+    float rp0, rp1;   // R part of the net of edge (r-3|r-2)
+    int n;            // rows fed so far (warp-uniform)
+};
+
+__device__ __forceinline__ bool feed(Pipe &P, const CellA &C, float nux, float nuy, int order,
+                                     CellA &out) {
+    EdgeA Wn = P.W2;
+    if (P.n >= 1) Wn = solve_a(P.B.e, P.B.g, P.B.c, C.e, C.g, C.c);   // edge (r-1|r)
+    float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (P.n >= 3) nn = net_a(P.W1, P.W2, Wn, nuy, order);             // edge (r-2|r-1)
+    const bool done = P.n >= 4;
+    if (done) {
+        float e = P.A.e, g = P.A.g;
+        const float m = P.A.m, c = P.A.c;
+        if (c > 0.f) {
+            e = add(e, mul(-nuy, add(P.rp0, nn.x)));
+            g = add(g, mul(-nuy, add(P.rp1, nn.y)));
+        }
+        const float eR = __shfl_down_sync(kFull, e, 1);
+        const float mR = __shfl_down_sync(kFull, m, 1);
+        const float cR = __shfl_down_sync(kFull, c, 1);
+        const EdgeA X = solve_a(e, m, c, eR, mR, cR);
+        EdgeA XL = X, XR = X;
+        XL.b2 = __shfl_up_sync(kFull, X.b2, 1);
+        XL.cr = __shfl_up_sync(kFull, X.cr, 1);
+        XR.b1 = __shfl_down_sync(kFull, X.b1, 1);
+        XR.cl = __shfl_down_sync(kFull, X.cl, 1);
+        const float4 xn = net_a(XL, X, XR, nux, order);
+        const float xr0 = __shfl_up_sync(kFull, xn.z, 1);
+        const float xr1 = __shfl_up_sync(kFull, xn.w, 1);
+        float ne = e, nm = m;
+        if (c > 0.f) {
+            ne = add(ne, mul(-nux, add(xr0, xn.x)));
+            nm = add(nm, mul(-nux, add(xr1, xn.y)));
+        }
+        out.e = ne; out.m = nm; out.g = g; out.c = c;
+    }
+    P.A = P.B; P.B = C;
+    P.W1 = P.W2; P.W2 = Wn;
+    P.rp0 = nn.z; P.rp1 = nn.w;
+    P.n++;
+    return done;
+}
+
+// the ghost row the one-step path would load for row r < 0 or r >= ny, from
+// the interior rows lo0 = 0, lo1 = 1, hi0 = ny - 1, hi1 = ny - 2
+__device__ __forceinline__ CellA ghost_row(int r, int ny, int bc_lo, int bc_hi, const CellA &lo0,
+                                           const CellA &lo1, const CellA &hi0, const CellA &hi1) {
+    CellA q;
+    bool wall;
+    if (r < 0) {
+        wall = bc_lo == SWA_BC_WALL;
+        q = (wall && r == -2) ? lo1 : lo0;
+    } else {
+        wall = bc_hi == SWA_BC_WALL;
+        q = (wall && r == ny + 1) ? hi1 : hi0;
+    }
+    if (wall) q.g = -q.g;
+    return q;
+}
+
+__global__ void __launch_bounds__(256, 3) adj_f32_strips2(AdjParams<float> p) {
+    const int lane = threadIdx.x & 31;
+    const int nsx = (p.nx + kOut2 - 1) / kOut2, nsy = (p.ny + kRows2 - 1) / kRows2;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if ((p.snap_f || p.snap_d) && blockIdx.x == 0 && threadIdx.x == 0) *p.tau_dev = p.tau_val;
+    if (unit >= nsx * nsy) return;   // warp-uniform
+    const int sy = unit / nsx, sx = unit - sy * nsx;
+    const int x0 = sx * kOut2, y0 = sy * kRows2;
+    const int ny = p.ny;
+    const int ylast = (y0 + kRows2 < ny ? y0 + kRows2 : ny) - 1;
+    const int gi = x0 - 4 + lane;
+    bool fx;
+    const int col = ghost_index(gi, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
+    // the lane holding this lane's column of the intermediate state
+    const int src = (gi >= 0 && gi < p.nx) ? lane : col - (x0 - 4);
+    const bool out = lane >= 4 && lane < kLanes - 4 && gi < p.nx;
+    const float nux = p.nux, nuy = p.nuy;
+    const int order = p.order;
+    const bool yin = y0 - 4 >= 0 && ylast + 4 < ny;
+    auto load = [&](int j) -> CellA {
+        bool fy = false;
+        int row;
+        if (yin) row = j;
+        else row = ghost_index(j, ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        return load_cell(p, col, fx, row, fy);
+    };
+    Pipe P1, P2;
+    P1.n = 0; P2.n = 0;
+    P1.rp0 = P1.rp1 = P2.rp0 = P2.rp1 = 0.f;
+    CellA lo0 = {}, lo1 = {}, hi0 = {}, hi1 = {};
+    CellA Cn = load(y0 - 4);
+    for (int j = y0 - 4; j <= ylast + 4; j++) {   // input row j (warp-uniform)
+        const CellA C = Cn;
+        if (j < ylast + 4) Cn = load(j + 1);
+        CellA S;
+        if (!feed(P1, C, nux, nuy, order, S)) continue;
+        const int r = j - 2;   // the finished row of the first step
+        // its ghost columns: the mapped interior columns, as a load would give
+        S.e = __shfl_sync(kFull, S.e, src);
+        S.m = __shfl_sync(kFull, S.m, src);
+        S.g = __shfl_sync(kFull, S.g, src);
+        if (fx) S.m = -S.m;
+        if (r == 0) lo0 = S;
+        if (r == 1) lo1 = S;
+        if (r == ny - 1) hi0 = S;
+        if (r == ny - 2) hi1 = S;
+        // rows below the grid are fed once rows 0 and 1 are known
+        if (r < 0 || (y0 - 2 < 0 && r == 0)) continue;
+        int nfeed = 1, rf = r;
+        if (y0 - 2 < 0 && r == 1) { nfeed = 4; rf = -2; }   // rows -2, -1, 0, 1
+        for (int k = 0; k < nfeed; k++, rf++) {
+            CellA F = S;
+            if (rf < 0 || rf >= ny) F = ghost_row(rf, ny, p.bc.lo_y, p.bc.hi_y, lo0, lo1, hi0, hi1);
+            else if (rf != r) F = rf == 0 ? lo0 : lo1;
+            CellA Q;
+            if (!feed(P2, F, nux, nuy, order, Q)) continue;
+            const int ro = rf - 2;   // the finished row of the second step
+            if (out && ro >= y0 && ro <= ylast) {
+                const size_t o = (size_t)ro * p.nx + gi;
+                p.dst[0][o] = Q.e;
+                p.dst[1][o] = Q.m;
+                p.dst[2][o] = Q.g;
+                if (p.snap_f) {
+                    __stcs(p.snap_f + o, Q.e);
+                    __stcs(p.snap_f + p.snap_comp_stride + o, Q.m);
+                    __stcs(p.snap_f + 2 * p.snap_comp_stride + o, Q.g);
+                } else if (p.snap_d) {
+                    __stcs(p.snap_d + o, (double)Q.e);
+                    __stcs(p.snap_d + p.snap_comp_stride + o, (double)Q.m);
+                    __stcs(p.snap_d + 2 * p.snap_comp_stride + o, (double)Q.g);
+                }
+            }
+        }
+    }
+}
+
 }  // namespace adjt
 
 template <>
 int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
+    if (p.two_d && p.two_steps) {
+        const long long units = (long long)((p.nx + adjt::kOut2 - 1) / adjt::kOut2) *
+                                ((p.ny + adjt::kRows2 - 1) / adjt::kRows2);
+        const unsigned blocks = (unsigned)((units + 7) / 8);
+        adjt::adj_f32_strips2<<<blocks, 256, 0, st>>>(p);
+        return swadj_host::cuda_check(cudaGetLastError(), "adj_f32_strips2");
+    }
     if (p.two_d) {
         const long long units = (long long)((p.nx + adjt::kOut - 1) / adjt::kOut) *
                                 ((p.ny + adjt::kRows - 1) / adjt::kRows);

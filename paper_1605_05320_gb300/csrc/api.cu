@@ -494,6 +494,7 @@ struct swa_adjoint {
     double dt;
     long long steps_done;
     int cur;
+    int steps_per_pass;   // FP32 2D: 1 or 2 adjoint steps per launch
     double t_f;
 };
 
@@ -601,14 +602,16 @@ static int store_into(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
     return SWA_OK;
 }
 
-static int adj_one_step(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
+// ns (1 or 2) adjoint steps in one launch; s: store a snapshot of the state
+// after them.
+static int adj_steps(swa_adjoint *a, swa_snapstore *s, int ns, cudaStream_t st) {
     double tau = 0.0;
     float *sf = nullptr;
     double *sd = nullptr;
     if (s) {
         if (s->count >= s->max_snaps)
             return set_error(SWA_ENOMEM, "snapshot store full (%d)", s->max_snaps);
-        tau = a->t_f - (double)(a->steps_done + 1) * a->dt;
+        tau = a->t_f - (double)(a->steps_done + ns) * a->dt;
         const size_t esz = s->prec == SWA_FP64 ? 8 : 4;
         char *slot = (char *)s->data + (size_t)s->count * s->nc * s->na * esz;
         if (s->prec == SWA_FP32) sf = (float *)slot;
@@ -625,11 +628,12 @@ static int adj_one_step(swa_adjoint *a, swa_snapstore *s, cudaStream_t st) {
         p.snap_f = sf; p.snap_d = sd; p.snap_comp_stride = a->n;
         p.tau_dev = s ? s->tau_dev + s->count : nullptr;
         p.tau_val = tau;
+        p.two_steps = ns == 2;
         TRY(adj_launch_step<float>(p, st));
     }
     if (s) TRY(env_fold(s, s->count, st));
     a->cur ^= 1;
-    a->steps_done++;
+    a->steps_done += ns;
     if (s) { s->tau_host.push_back(tau); s->count++; }
     return SWA_OK;
 }
@@ -723,7 +727,20 @@ int swa_step_adjoint(swa_adjoint *a, int nsteps, void *stream) {
     if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
     long long left = a->N - a->steps_done;
     if (nsteps > left) nsteps = (int)left;
-    for (int k = 0; k < nsteps; k++) TRY(adj_one_step(a, nullptr, S(stream)));
+    for (int k = 0; k < nsteps;) {
+        const int ns = (a->steps_per_pass == 2 && k + 2 <= nsteps) ? 2 : 1;
+        TRY(adj_steps(a, nullptr, ns, S(stream)));
+        k += ns;
+    }
+    return SWA_OK;
+}
+
+int swa_adjoint_set_steps_per_pass(swa_adjoint *a, int k) {
+    if (!a) return set_error(SWA_EINVAL, "null adjoint");
+    if (k != 1 && k != 2) return set_error(SWA_EINVAL, "steps per pass must be 1 or 2");
+    if (k == 2 && (a->d.precision != SWA_FP32 || a->d.ndim != 2))
+        return set_error(SWA_EINVAL, "two steps per pass need a 2D FP32 adjoint");
+    a->steps_per_pass = k;
     return SWA_OK;
 }
 
@@ -840,8 +857,12 @@ int swa_run_adjoint(swa_adjoint *a, swa_snapstore *s, int every, void *stream) {
     if (first) TRY(store_into(a, s, st));
     while (a->steps_done < a->N) {
         const long long k = a->steps_done + 1;
-        const bool snap = (k % every == 0) || (k == a->N);
-        TRY(adj_one_step(a, snap ? s : nullptr, st));
+        const bool snap1 = (k % every == 0) || (k == a->N);
+        // two steps in one pass when no snapshot falls between them
+        const int ns = (a->steps_per_pass == 2 && !snap1 && k + 1 <= a->N) ? 2 : 1;
+        const long long kl = k + ns - 1;
+        const bool snap = (kl % every == 0) || (kl == a->N);
+        TRY(adj_steps(a, snap ? s : nullptr, ns, st));
     }
     return SWA_OK;
 }

@@ -37,7 +37,7 @@ EXPORTS = [
     "swa_grid_set_rest_skip",
     "swa_grid_arrays",
     "swa_adjoint_workspace_bytes", "swa_create_adjoint", "swa_destroy_adjoint",
-    "swa_adjoint_info", "swa_step_adjoint", "swa_get_adjoint_state",
+    "swa_adjoint_info", "swa_step_adjoint", "swa_adjoint_set_steps_per_pass", "swa_get_adjoint_state",
     "swa_set_adjoint_state", "swa_snapstore_clear",
     "swa_snapstore_workspace_bytes", "swa_create_snapstore",
     "swa_destroy_snapstore", "swa_store_snapshot", "swa_run_adjoint",
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
         "swa_destroy_adjoint": ([_V], _I),
         "swa_adjoint_info": ([_V, _P(ctypes.c_longlong), _P(_D), _P(ctypes.c_longlong)], _I),
         "swa_step_adjoint": ([_V, _I, _V], _I),
+        "swa_adjoint_set_steps_per_pass": ([_V, _I], _I),
         "swa_get_adjoint_state": ([_V, _V, _I, _V], _I),
         "swa_set_adjoint_state": ([_V, _V, _I, _V], _I),
         "swa_snapstore_clear": ([_V], _I),
@@ -287,6 +288,10 @@ def swa_adjoint_info(h):
 
 def swa_step_adjoint(h, nsteps, stream=None):
     return _chk(load().swa_step_adjoint(h, int(nsteps), _stream(stream)))
+
+
+def swa_adjoint_set_steps_per_pass(h, k):
+    return _chk(load().swa_adjoint_set_steps_per_pass(h, int(k)))
 
 
 def swa_get_adjoint_state(h, q, where, stream=None):
