@@ -124,6 +124,8 @@ def _bind(lib):
     lib.orc_fwd_riemann.restype = None
     lib.orc_fwd_step.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
     lib.orc_fwd_step.restype = ctypes.c_int
+    lib.orc_fwd_step_flux.argtypes = [G, _D, _D, _D, _D, ctypes.c_double, _D, _D, _D, _D]
+    lib.orc_fwd_step_flux.restype = ctypes.c_int
     lib.orc_fwd_step_ctu.argtypes = [G, _D, _D, _D, _D, ctypes.c_double]
     lib.orc_fwd_step_ctu.restype = ctypes.c_int
     lib.orc_ctu_tsplit.argtypes = [ctypes.c_double] * 3 + [_D, _D, _D]
@@ -198,6 +200,20 @@ def fwd_riemann(g, left, right):
                             *[float(x) for x in right], _p(out))
     return dict(s=out[0:3].copy(), Z=out[3:12].reshape(3, 3).copy(),
                 uhat=out[12], vhat=out[13], chat=out[14])
+
+
+def fwd_step_flux(grid: Grid, h, hu, hv, B, dt):
+    """One 2D split forward step that also returns the mass fluxes per cell:
+    (h, hu, hv, phi) with phi[0..3] = x low, x high, y low, y high edge flux
+    as the cell's update uses them (dh = -nu (phi_hi - phi_lo) per sweep)."""
+    h, hu, hv, B = _f64(h).copy(), _f64(hu).copy(), _f64(hv).copy(), _f64(B)
+    phi = np.zeros((4, h.size))
+    g = grid.c()
+    rc = _load().orc_fwd_step_flux(ctypes.byref(g), _p(h), _p(hu), _p(hv), _p(B), dt,
+                                   *[phi[k].ctypes.data_as(_D) for k in range(4)])
+    if rc:
+        raise FloatingPointError(f"oracle forward step failed ({rc})")
+    return h, hu, hv, phi
 
 
 def ctu_tsplit(uhat, vhat, chat, a):

@@ -24,7 +24,19 @@ grid and one level of fine patches, one coarse step at a time:
      eta - B_fine;
   3. every coarse cell under a patch interior (the lowest patch index wins)
      becomes the mean of its r x r fine cells: eta and both momenta, summed
-     row by row, divided by r^2; its depth is eta - B_coarse.
+     row by row, divided by r^2; its depth is eta - B_coarse;
+  4. refluxing (optional, on by default): every uncovered coarse cell U
+     beside a covered coarse cell V had its mass updated with the coarse
+     mass flux through the edge U|V, while the fine level moved mass across
+     the same edge with its own fluxes.  U's depth is corrected by the
+     difference, per sweep (x-edges in the x-sweep, y-edges in the y-sweep):
+       dh_U = (dt_c / dx_c) phi_c - sum_s sum_J (dt_s / dx_c) (1 / r) phi_f,
+     phi_c the coarse flux through the edge as U's update used it, phi_f the
+     flux through each of the r fine edges along it as the fine interior
+     cell's update used it, over the r fine substeps s (signs flipped when U
+     lies on the high side).  The total mass (uncovered coarse cells plus
+     the covered ones, which hold the fine means) is then conserved between
+     walls.
 
 Patches are aligned with the coarse grid (interior on whole coarse cells)
 and their rings lie inside the coarse domain.  A fine patch is stored with
@@ -40,7 +52,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import BC_EXTRAP, Grid, fwd_smax, fwd_step
+from . import BC_EXTRAP, Grid, fwd_smax, fwd_step, fwd_step_flux
 
 RING = 2
 
@@ -76,7 +88,12 @@ class Hierarchy:
     """Coarse grid state (h, hu, hv) with bottom B, fine patches with their
     own bottoms Bf[k] (ring included), refinement ratio r."""
 
-    def __init__(self, coarse: Grid, B, patches, r, Bf):
+    # the method's refluxing sign and fine-edge weight divisor (r); tests
+    # override them in subclasses to plant mistakes
+    reflux_sign = 1.0
+    fine_weight_is_one = False
+
+    def __init__(self, coarse: Grid, B, patches, r, Bf, reflux=True):
         self.coarse, self.r, self.patches = coarse, int(r), list(patches)
         self.B = np.asarray(B, dtype=np.float64)
         self.Bf = [np.asarray(b, dtype=np.float64) for b in Bf]
@@ -87,6 +104,42 @@ class Hierarchy:
                     and (p.j0 + p.my) * r + RING <= coarse.ny * r):
                 raise ValueError("a patch ring leaves the coarse domain")
         self.t_c = self.t_f = 0.0
+        self.reflux = bool(reflux)
+        self.cf_edges = self._coarse_fine_edges()
+
+    def _coarse_fine_edges(self):
+        """Edges between an uncovered coarse cell U and a covered one V:
+        (U, axis 0/1, side +1 if V lies on U's high side else -1, owner
+        patch q of V, fine cells of q along the edge inside V)."""
+        cg, r = self.coarse, self.r
+        covered = {}
+        for jc in range(cg.ny):
+            for ic in range(cg.nx):
+                src = self.owner(ic * r, jc * r)
+                if src is not None:
+                    covered[(ic, jc)] = src[0]
+        edges = []
+        for jc in range(cg.ny):
+            for ic in range(cg.nx):
+                if (ic, jc) in covered:
+                    continue
+                for axis, side in ((0, 1), (0, -1), (1, 1), (1, -1)):
+                    iv, jv = (ic + side, jc) if axis == 0 else (ic, jc + side)
+                    q = covered.get((iv, jv))
+                    if q is None:
+                        continue
+                    p, g = self.patches[q], self.grids[q]
+                    cells = []
+                    for k in range(r):
+                        if axis == 0:
+                            I = iv * r + (0 if side > 0 else r - 1)
+                            J = jv * r + k
+                        else:
+                            I = iv * r + k
+                            J = jv * r + (0 if side > 0 else r - 1)
+                        cells.append((J - p.j0 * r + RING) * g.nx + (I - p.i0 * r + RING))
+                    edges.append((jc * cg.nx + ic, axis, side, q, cells))
+        return edges
 
     def set_state(self, h, hu, hv, fine, t):
         """fine[k] = (h, hu, hv) of patch k, ring included."""
@@ -183,9 +236,16 @@ class Hierarchy:
         if t_end - self.t_c < dt:
             dt = t_end - self.t_c
         old = (self.h.copy(), self.hu.copy(), self.hv.copy())
+        dh = np.zeros(len(self.cf_edges))   # reflux correction per edge
         if dt > 0.0:
-            self.h, self.hu, self.hv = fwd_step(cg, self.h, self.hu, self.hv, self.B, dt)
+            self.h, self.hu, self.hv, phi = fwd_step_flux(cg, self.h, self.hu, self.hv, self.B, dt)
             self.t_c = self.t_c + dt
+            for e, (u, axis, side, q, cells) in enumerate(self.cf_edges):
+                d = cg.dx if axis == 0 else cg.dy
+                # U's update took -(dt/d) phi_hi for a high-side neighbour,
+                # +(dt/d) phi_lo for a low-side one
+                f = phi[2 * axis + 1][u] if side > 0 else -phi[2 * axis][u]
+                dh[e] += dt / d * f
         for k in range(1, r + 1):
             t_k = t_end if k == r else t_n + dt_c * k / r
             for _ in range(m):
@@ -194,9 +254,23 @@ class Hierarchy:
                     dtf = t_k - self.t_f
                 self.fill(old, t_n, dt_c)
                 if dtf > 0.0:
+                    phis = []
                     for q, g in enumerate(self.grids):
                         f = self.fine[q]
-                        self.fine[q] = list(fwd_step(g, f[0], f[1], f[2], self.Bf[q], dtf))
+                        nh, nu, nv, ph = fwd_step_flux(g, f[0], f[1], f[2], self.Bf[q], dtf)
+                        self.fine[q] = [nh, nu, nv]
+                        phis.append(ph)
                     self.t_f = self.t_f + dtf
+                    for e, (u, axis, side, q, cells) in enumerate(self.cf_edges):
+                        d = cg.dx if axis == 0 else cg.dy
+                        # mass entering the fine region across the edge: the
+                        # fine cells' low-edge flux (V on U's high side) or
+                        # high-edge flux with its sign flipped
+                        ph = phis[q][2 * axis] if side > 0 else -phis[q][2 * axis + 1]
+                        w = 1.0 if self.fine_weight_is_one else 1.0 / r
+                        dh[e] -= dtf / d * w * sum(ph[c] for c in cells)
         self.average()
+        if self.reflux:
+            for e, (u, axis, side, q, cells) in enumerate(self.cf_edges):
+                self.h[u] += self.reflux_sign * dh[e]
         return self.t_c == t_end and self.t_f == t_end

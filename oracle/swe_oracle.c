@@ -277,7 +277,7 @@ void orc_fwd_riemann(double g, double hL, double mnL, double mtL, double BL,
  * direction.  Along y the edge frame is (h, hv, hu).
  */
 static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double *hv,
-                      const double *B, double dt) {
+                      const double *B, double dt, double *phi_lo, double *phi_hi) {
     int nx = G->nx, ny = G->ny;
     size_t n = (size_t)nx * ny;
     double *ph = padded(G), *pu = padded(G), *pv = padded(G), *pB = padded(G);
@@ -315,6 +315,13 @@ static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double 
             nh[o] = ph[c] + dq[0];
             if (dir == 0) { nu_[o] = pu[c] + dq[1]; nv[o] = pv[c] + dq[2]; }
             else { nv[o] = pv[c] + dq[1]; nu_[o] = pu[c] + dq[2]; }
+            if (phi_lo) {
+                /* mass flux through the cell's low and high edge of this sweep
+                   as the cell's update sees it: dh = -nu (phi_hi - phi_lo) */
+                double mn = dir == 0 ? pu[c] : pv[c];
+                phi_lo[o] = mn - (apL[0] - FL[0]);
+                phi_hi[o] = mn + (amR[0] + FR[0]);
+            }
         }
     }
     memcpy(h, nh, n * sizeof(double));
@@ -520,12 +527,32 @@ int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
     if (G->ndim == 2 && G->scheme == 1 && hv) return orc_fwd_step_ctu(G, h, hu, hv, B, dt);
     double *v = hv;
     if (!hv) v = (double *)calloc(n, sizeof(double));
-    fwd_sweep(G, 0, h, hu, v, B, dt);
-    if (G->ndim == 2) fwd_sweep(G, 1, h, hu, v, B, dt);
+    fwd_sweep(G, 0, h, hu, v, B, dt, NULL, NULL);
+    if (G->ndim == 2) fwd_sweep(G, 1, h, hu, v, B, dt, NULL, NULL);
     int bad = 0;
     for (size_t k = 0; k < n; k++)
         if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(v[k])) bad = 1;
     if (!hv) free(v);
+    return bad ? -5 : 0;
+}
+
+/*
+ * A 2D split forward step, as orc_fwd_step with scheme 0, that also returns
+ * per cell the mass flux through its low and high x-edge (x-sweep, from Q^n)
+ * and y-edge (y-sweep, from the x-swept state), as the cell's update uses
+ * them: phi[0], phi[1] (x low, high) and phi[2], phi[3] (y low, high), n
+ * values each.  The refluxing of the AMR glue takes its fluxes from here.
+ */
+int orc_fwd_step_flux(const orc_grid *G, double *h, double *hu, double *hv, const double *B,
+                      double dt, double *phi_xlo, double *phi_xhi, double *phi_ylo,
+                      double *phi_yhi) {
+    size_t n = (size_t)G->nx * G->ny;
+    if (G->ndim != 2 || G->scheme != 0) return -1;
+    fwd_sweep(G, 0, h, hu, hv, B, dt, phi_xlo, phi_xhi);
+    fwd_sweep(G, 1, h, hu, hv, B, dt, phi_ylo, phi_yhi);
+    int bad = 0;
+    for (size_t k = 0; k < n; k++)
+        if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(hv[k])) bad = 1;
     return bad ? -5 : 0;
 }
 

@@ -11,6 +11,15 @@ r fine substeps per coarse step, averaging down.
   coarse grid alone; piecewise-constant coarse fills, fills frozen at the
   coarse step's start or end, slopes of the wrong sign, or an average over r
   instead of r^2 cells (mistakes planted in subclasses) do not.
+- refluxing: with coarse bottoms that are the means of the fine ones, the
+  total mass is conserved between walls (without refluxing it drifts); the
+  ocean stays at rest; r = 1 stays the single grid to rounding; refluxing
+  with a flipped sign or without the 1/r weight of a fine edge (planted)
+  does not conserve mass.
+
+The pins of the fills and of the average run with refluxing off: refluxing
+changes only the uncovered coarse cells beside a patch, and those pins were
+chosen to fix the fill and average rules.
 """
 import numpy as np
 import pytest
@@ -36,9 +45,12 @@ def fields(n, d):
     return X, Y
 
 
-def build(nc, r, patches, cls=Hierarchy, rest=False, seed=None):
+def build(nc, r, patches, cls=Hierarchy, rest=False, seed=None, reflux=False,
+          mean_bottom=False):
     """Coarse nc^2 basin with walls, fine patches sampled on the global fine
-    grid (so patches agree wherever they overlap), a hump at the centre."""
+    grid (so patches agree wherever they overlap), a hump at the centre.
+    mean_bottom: the coarse bottom and surface are the means of the fine
+    ones over each coarse cell (else sampled at the coarse centres)."""
     cg = O.Grid(2, nc, nc, 0.0, 0.0, DX, DX, order=2, bc=(1, 1, 1, 1))
     L = nc * DX
     X, Y = fields(nc, DX)
@@ -46,6 +58,9 @@ def build(nc, r, patches, cls=Hierarchy, rest=False, seed=None):
     ec = np.zeros(nc * nc) if rest else hump(X, Y, L).ravel()
     XF, YF = fields(nc * r, DX / r)
     BF, EF = bottom(XF, YF), (np.zeros_like(XF) if rest else hump(XF, YF, L))
+    if mean_bottom:
+        Bc = BF.reshape(nc, r, nc, r).mean(axis=(1, 3)).ravel()
+        ec = EF.reshape(nc, r, nc, r).mean(axis=(1, 3)).ravel()
     uc = np.zeros(nc * nc)
     UF = np.zeros_like(XF)
     if seed is not None:
@@ -60,7 +75,7 @@ def build(nc, r, patches, cls=Hierarchy, rest=False, seed=None):
         sl = lambda a: a[J0:J0 + g.ny, I0:I0 + g.nx].ravel().copy()
         Bf.append(sl(BF))
         fine.append((sl(EF) - sl(BF), sl(UF), -sl(UF)))
-    H = cls(cg, Bc, patches, r, Bf)
+    H = cls(cg, Bc, patches, r, Bf, reflux=reflux)
     H.set_state(ec - Bc, uc, -uc, fine, 0.0)
     return H, cg, Bc, ec, BF, EF, uc
 
@@ -287,3 +302,74 @@ def test_planted_glue_mistakes_fail_the_accuracy_pins(cls):
         amr, coarse = region_errors(r, steps, cls=cls)
         fails += not (amr < factor * coarse)
     assert fails >= 2
+
+
+# ----------------------------------------------------------------- refluxing
+PATCH_SETS = [(2, [Patch(8, 8, 8, 8)]),
+              (4, [Patch(6, 6, 5, 7), Patch(11, 9, 6, 4)]),
+              (3, [Patch(4, 4, 6, 6), Patch(10, 4, 4, 6), Patch(12, 7, 5, 5)])]
+
+
+def mass_drift(r, patches, cls=Hierarchy, reflux=True, steps=10):
+    H, cg, *_ = build(24, r, patches, cls=cls, reflux=reflux, mean_bottom=True)
+    dt, t = dt_coarse(cg), 0.0
+    m0 = H.h.sum()
+    for _ in range(steps):
+        assert H.step(t, dt)
+        t = t + dt
+    return abs(H.h.sum() - m0) / m0
+
+
+@pytest.mark.parametrize("r,patches", PATCH_SETS)
+def test_refluxing_conserves_mass(r, patches):
+    """Walls all round, coarse bottoms the means of the fine ones: the mass
+    of the hierarchy (uncovered coarse cells plus the covered ones, which
+    hold the fine means) stays constant with refluxing, and drifts without."""
+    assert mass_drift(r, patches) <= 1e-13
+    assert mass_drift(r, patches, reflux=False) > 1e-8
+
+
+class RefluxSign(Hierarchy):
+    """Planted mistake: the reflux correction applied with a flipped sign."""
+    reflux_sign = -1.0
+
+
+class RefluxWeight(Hierarchy):
+    """Planted mistake: each fine edge weighted as a whole coarse edge."""
+    fine_weight_is_one = True
+
+
+@pytest.mark.parametrize("cls", [RefluxSign, RefluxWeight])
+def test_planted_reflux_mistakes_break_conservation(cls):
+    r, patches = PATCH_SETS[1]
+    assert mass_drift(r, patches, cls=cls) > 1e-8
+
+
+def test_refluxing_keeps_the_ocean_at_rest_and_r1_the_single_grid():
+    H, cg, Bc, *_ = build(16, 4, [Patch(4, 4, 5, 6), Patch(7, 8, 4, 4)], rest=True,
+                          reflux=True)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(4):
+        assert H.step(t, dt)
+        t = t + dt
+    assert np.all(H.h + Bc == 0.0) and np.all(H.hu == 0) and np.all(H.hv == 0)
+    patches = [Patch(5, 6, 6, 5), Patch(9, 8, 5, 7), Patch(14, 3, 4, 4)]
+    H, cg, Bc, ec, _, _, uc = build(24, 1, patches, seed=1, reflux=True)
+    h, hu, hv = ec - Bc, uc.copy(), -uc
+    t = 0.0
+    for _ in range(10):
+        assert H.step(t, dt)
+        h, hu, hv = O.fwd_step(cg, h, hu, hv, Bc, (t + dt) - t)
+        t = t + dt
+    for a, b in ((H.h, h), (H.hu, hu), (H.hv, hv)):
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
+def test_refluxing_a_patch_cut_in_two_gives_the_patch():
+    one, cg, *_ = build(24, 2, [Patch(8, 8, 8, 8)], reflux=True)
+    two, *_ = build(24, 2, [Patch(8, 8, 3, 8), Patch(11, 8, 5, 8)], reflux=True)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(6):
+        assert one.step(t, dt) and two.step(t, dt)
+        t = t + dt
+    assert np.abs(one.h - two.h).max() <= 1e-12 * np.abs(one.h + one.B).max()
