@@ -407,15 +407,32 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  *      eta and both momenta), then piecewise linearly in space within the
  *      coarse cell holding it, with minmod slopes (zero at the domain edge);
  *   3. every coarse cell under a patch interior (lowest patch index) takes
- *      the mean of its r x r fine cells (eta and both momenta).
+ *      the mean of its r x r fine cells (eta and both momenta);
+ *   4. refluxing (on unless swa_amr_set_reflux turned it off): every
+ *      uncovered coarse cell U beside a covered cell V takes, for each such
+ *      edge, the mass its own update moved through the edge minus the mass
+ *      the fine level moved through it over the r substeps (the fine cells
+ *      of V's lowest-index patch along the edge, weighted 1 / r):
+ *        eta_U += dt_c / d phi_c - sum_launches dt_f / (d r) sum_fine phi_f
+ *      with phi the mass flux of the split step's update (x-edges from the
+ *      state, y-edges from the x-swept state; the normal momentum of the
+ *      cell below the edge plus the net the update gives it), signed into
+ *      V, and d the coarse cell width across the edge.  The fluxes are recomputed before
+ *      each launch by the step's own edge arithmetic, summed in FP64 per
+ *      edge and added to eta_U in FP32 after step 3.  With coarse bottoms
+ *      the means of the fine bottoms under them, the hierarchy then keeps
+ *      the mass of its cells (coarse uncovered plus coarse covered) to
+ *      rounding, as conservative refinement requires (Sec. 6 runs GeoClaw's
+ *      conservative AMR).  Only the mass is corrected.
  * If either level ends the step short of t_n + dt_c (the coarse CFL step
  * was below dt_c, or m launches did not reach a substep's end), the next
  * swa_sync_status returns SWA_ESTATE.
  */
 typedef struct swa_amr swa_amr;
-/* Device workspace for the maps (16 bytes per ring cell and per covered
- * coarse cell, plus padding); 0 if the geometry is invalid (the reason is in
- * swa_last_error). */
+/* Device workspace for the maps and the refluxing corrections (16 bytes per
+ * ring cell and per covered coarse cell, 24 per coarse-fine edge, 16 per
+ * uncovered coarse cell beside the fine level, plus padding); 0 if the
+ * geometry is invalid (the reason is in swa_last_error). */
 size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
                                int ratio);
 /*
@@ -441,6 +458,14 @@ int swa_destroy_amr(swa_amr *amr);
  * SWA_ESTATE at the next swa_sync_status.
  */
 int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
+/* Refluxing (step 4 above) on (on != 0, the default) or off.  Host state
+ * only; takes effect at the next swa_amr_step.  A step with refluxing on
+ * returns SWA_EINVAL if the coarse grid uses the unsplit scheme (the
+ * recomputed fluxes are the split step's). */
+int swa_amr_set_reflux(swa_amr *amr, int on);
+/* Sizes of the maps: ring cells filled per launch, covered coarse cells
+ * averaged, coarse-fine edges refluxed (any pointer may be null). */
+int swa_amr_info(const swa_amr *amr, int *nfill, int *navg, int *nedges);
 
 /*
  * FP64 audit of the conserved mass of the grid's current state: writes

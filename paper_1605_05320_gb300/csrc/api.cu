@@ -240,6 +240,7 @@ int swadj::grid_refs(const swa_grid *g, GridRefs *out) {
     out->bath = g->bath;
     out->clk = g->clk;
     out->state_set = g->state_set;
+    out->scheme = g->scheme;
     return SWA_OK;
 }
 

@@ -606,6 +606,168 @@ __global__ void amr_avg_kernel(AmrParams p) {
     }
 }
 
+// ------------------------------------------------------------ refluxing
+// Mass flux through an edge of cell (i, j), low (side < 0) or high (side >
+// 0), along `axis`, as the FP32 split step forms it: x-edges from the state
+// (x-sweep), y-edges from the x-swept state (y-sweep).  The edge's flux is
+// F = mn_L + L0, the normal momentum of the cell below it plus the net the
+// update gives that cell (in exact arithmetic also mn_R - R0, the cell
+// above it), so a cell's update is dh = -nu (F_high - F_low) per sweep and
+// both sides of an edge see the same number.  The edge arithmetic is the
+// strip kernel's (fwd_pair.cuh), each net in the form its own edge picks
+// (the warp-uniform choice of the kernel gives the same numbers).
+struct CellRaw {
+    float eta, mu, mv, hb;
+};
+
+__device__ __forceinline__ CellRaw raw_at(const strip::View &v, int i, int j) {
+    bool fx, fy;
+    const int ii = ghost_index(i, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
+    const int jj = ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+    const size_t o = (size_t)jj * v.nx + ii;
+    CellRaw c;
+    c.eta = v.q0[o];
+    c.hb = v.hb[o];
+    const float mu = v.q1[o], mv = v.q2[o];
+    c.mu = fx ? -mu : mu;
+    c.mv = fy ? -mv : mv;
+    return c;
+}
+
+// x-frame cell data of cell (i, j)
+__device__ __forceinline__ fp::Cell<float> xcell(const strip::View &v, int i, int j) {
+    const CellRaw c = raw_at(v, i, j);
+    return fp::derive(c.eta, fp::add(c.eta, c.hb), c.mu, c.mv);
+}
+
+// the x-swept cell (i, j) in the y frame, as the strip kernel's x-sweep
+// leaves it
+__device__ __forceinline__ fp::Cell<float> xswept(const strip::View &v, int i, int j, float gh,
+                                                  float nux, int order) {
+    fp::Cell<float> c[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) c[k] = xcell(v, i - 2 + k, j);
+    fp::Edge<float> w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
+    const fp::Net<float> nl = fp::net3(w[0], w[1], w[2], nux, order, fp::subsonic(w[1].s1, w[1].s3));
+    const fp::Net<float> nr = fp::net3(w[1], w[2], w[3], nux, order, fp::subsonic(w[2].s1, w[2].s3));
+    const float d0 = fp::mul(-nux, fp::add(nl.R0, nr.L0));
+    const float d1 = fp::mul(-nux, fp::add(nl.R1, nr.L1));
+    const float d2 = fp::mul(-nux, fp::add(nl.R2, nr.L2));
+    const fp::Cell<float> &a = c[2];
+    return fp::derive(fp::add(a.eta, d0), fp::add(a.h, d0), fp::add(a.mt, d2), fp::add(a.mn, d1));
+}
+
+__device__ __forceinline__ float cell_flux(const strip::View &v, int i, int j, int axis, int side,
+                                           float gh, float nux, float nuy, int order) {
+    fp::Cell<float> c[4];   // the cells of the edge's three-edge stencil
+    const int k0 = side > 0 ? -1 : -2;   // first cell relative to (i, j)
+    float nu;
+    if (axis == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) c[k] = xcell(v, i + k0 + k, j);
+        nu = nux;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) c[k] = xswept(v, i, j + k0 + k, gh, nux, order);
+        nu = nuy;
+    }
+    fp::Edge<float> w[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
+    const fp::Net<float> n = fp::net3(w[0], w[1], w[2], nu, order, fp::subsonic(w[1].s1, w[1].s3));
+    // the edge lies between c[1] and c[2]
+    return fp::add(c[1].mn, n.L0);
+}
+
+// Coarse-fine edge e = (U, patch, first fine cell, axis | (side > 0) << 1 |
+// stride << 2): the uncovered coarse cell U, the patch covering its
+// neighbour V and the r fine cells of that patch along the edge inside V.
+struct RefluxParams {
+    const PatchDevice *table;
+    const DevClock *lclk, *cclk;
+    float *cq[2][3];
+    const float *chb;
+    int nxc, nyc, r;
+    BcSpec cbc;
+    double dxc, dyc;     // coarse cell size (the correction's scale)
+    double nxc_d, nyc_d; // the coarse step's nu divisors (its FP32 cell size)
+    double dxf, dyf;     // the fine level's
+    float gc, gf;        // gravity of the coarse step and of the level step
+    int orderc, orderf;
+    const int4 *cf;   // edges
+    int ncf;
+    const int4 *cfu;  // (U, first edge, count, 0), edges of one U consecutive
+    int ncfu;
+    double *dh;       // per edge
+    double t_end;     // of the coming step (coarse) or substep (fine)
+};
+
+// the step the coming launch takes on this clock (as begin_step forms it)
+__device__ __forceinline__ double coming_dt(const DevClock *clk, double t_end) {
+    volatile const DevClock *c = clk;
+    double dt = c->dt_cfl;
+    if (t_end - c->t < dt) dt = t_end - c->t;
+    return dt > 0.0 ? dt : 0.0;
+}
+
+// Before the coarse step: dh[e] = (dt_c / d) phi_c, the coarse flux through
+// the edge as U's update will use it (sign: + for V on U's high side).
+__global__ void reflux_coarse_kernel(RefluxParams p) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.ncf) return;
+    const double dt = coming_dt(p.cclk, p.t_end);
+    const int cur = p.cclk->cur;
+    strip::View v;
+    v.q0 = p.cq[cur][0]; v.q1 = p.cq[cur][1]; v.q2 = p.cq[cur][2]; v.hb = p.chb;
+    v.nx = p.nxc; v.ny = p.nyc; v.bc = p.cbc;
+    const int4 m = p.cf[e];
+    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1;
+    const int i = m.x % p.nxc, j = m.x / p.nxc;
+    const float f = cell_flux(v, i, j, axis, side, 0.5f * p.gc, (float)(dt / p.nxc_d),
+                              (float)(dt / p.nyc_d), p.orderc);
+    p.dh[e] = dt / (axis == 0 ? p.dxc : p.dyc) * (double)(side > 0 ? f : -f);
+}
+
+// Before each fine launch (after the ring fill): dh[e] -= (dt_f / d) (1 / r)
+// sum of the fine fluxes into the fine region across the edge.
+__global__ void reflux_fine_kernel(RefluxParams p) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.ncf) return;
+    const double dt = coming_dt(p.lclk, p.t_end);
+    if (!(dt > 0.0)) return;
+    const int cur = p.lclk->cur;
+    const int4 m = p.cf[e];
+    const PatchDevice &P = p.table[m.y];
+    strip::View v;
+    v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
+    v.nx = P.nx; v.ny = P.ny; v.bc = P.bc;
+    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1, stride = m.w >> 2;
+    const float nux = (float)(dt / p.dxf), nuy = (float)(dt / p.dyf);
+    double s = 0.0;
+    for (int k = 0; k < p.r; k++) {
+        const int c = m.z + k * stride;
+        // V on U's high side: the fine cells' low-edge flux; else minus the
+        // high-edge one
+        const float f = cell_flux(v, c % P.nx, c / P.nx, axis, -side, 0.5f * p.gf, nux, nuy,
+                                  p.orderf);
+        s += (double)(side > 0 ? f : -f);
+    }
+    p.dh[e] -= dt / (axis == 0 ? p.dxc : p.dyc) / (double)p.r * s;
+}
+
+// After the averaging: U's surface takes its edges' corrections.
+__global__ void reflux_apply_kernel(RefluxParams p) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= p.ncfu) return;
+    const int4 g = p.cfu[u];
+    double s = 0.0;
+    for (int k = 0; k < g.z; k++) s += p.dh[g.y + k];
+    float *eta = p.cq[p.cclk->cur][0];
+    eta[g.x] = fp::add(eta[g.x], (float)s);
+}
+
 // Geometry of one fine patch in global fine cells: array column 0 at
 // (I0, J0); interior [I0 + 2, I0 + nx - 2) x [J0 + 2, J0 + ny - 2).
 // Building the maps costs O(coarse cells + ring cells + covered cells).
@@ -616,7 +778,8 @@ struct FineBox {
 
 // Check the hierarchy and build the maps (host).
 int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
-               std::vector<int4> &fill, std::vector<int4> &avg) {
+               std::vector<int4> &fill, std::vector<int4> &avg, std::vector<int4> &cf,
+               std::vector<int4> &cfu) {
     const swa_grid_desc &d = c.d;
     if (d.ndim != 2 || d.precision != SWA_FP32)
         return set_error(SWA_EINVAL, "the coarse grid must be 2D FP32");
@@ -701,7 +864,53 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
             const long long li = (long long)ic * r - b.I0, lj = (long long)jc * r - b.J0;
             avg.push_back(make_int4(jc * d.nx + ic, ids[a], (int)(lj * b.nx + li), 0));
         }
+    // coarse-fine edges: per uncovered coarse cell U, its covered neighbours
+    // V in the order (+x, -x, +y, -y); the r fine cells of V's owner along
+    // the edge, from the corner nearest the lower left
+    cf.clear();
+    cfu.clear();
+    static const int dirs[4][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}};
+    for (int jc = 0; jc < d.ny; jc++)
+        for (int ic = 0; ic < d.nx; ic++) {
+            if (own[(size_t)jc * d.nx + ic].x >= 0) continue;
+            const int first = (int)cf.size();
+            for (int k = 0; k < 4; k++) {
+                const int axis = dirs[k][0], side = dirs[k][1];
+                const int iv = axis == 0 ? ic + side : ic, jv = axis == 0 ? jc : jc + side;
+                if (iv < 0 || iv >= d.nx || jv < 0 || jv >= d.ny) continue;
+                const int a = own[(size_t)jv * d.nx + iv].x;
+                if (a < 0) continue;
+                const FineBox &b = box[a];
+                long long I = (long long)iv * r, J = (long long)jv * r;
+                if (axis == 0) I += side > 0 ? 0 : r - 1;
+                else J += side > 0 ? 0 : r - 1;
+                const int stride = axis == 0 ? b.nx : 1;
+                cf.push_back(make_int4(jc * d.nx + ic, ids[a], (int)((J - b.J0) * b.nx + (I - b.I0)),
+                                       axis | (side > 0 ? 2 : 0) | (stride << 2)));
+            }
+            if ((int)cf.size() > first)
+                cfu.push_back(make_int4(jc * d.nx + ic, first, (int)cf.size() - first, 0));
+        }
     return SWA_OK;
+}
+
+// Workspace layout: fill, avg, edge and edge-group maps (int4), then the
+// per-edge corrections (double), each on a 256-byte boundary.
+struct Layout {
+    size_t fill, avg, cf, cfu, dh, total;
+};
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+inline Layout layout_of(size_t nfill, size_t navg, size_t ncf, size_t ncfu) {
+    Layout L;
+    L.fill = 0;
+    L.avg = L.fill + round256(sizeof(int4) * nfill);
+    L.cf = L.avg + round256(sizeof(int4) * navg);
+    L.cfu = L.cf + round256(sizeof(int4) * ncf);
+    L.dh = L.cfu + round256(sizeof(int4) * ncfu);
+    L.total = L.dh + round256(sizeof(double) * ncf) + 256;
+    return L;
 }
 
 }  // namespace amr
@@ -711,8 +920,10 @@ struct swa_amr {
     swa_grid *coarse = nullptr;
     swa_patchset *fine = nullptr;
     int level = 0, r = 1;
-    int4 *fill = nullptr, *avg = nullptr;
-    int nfill = 0, navg = 0;
+    int4 *fill = nullptr, *avg = nullptr, *cf = nullptr, *cfu = nullptr;
+    double *dh = nullptr;
+    int nfill = 0, navg = 0, ncf = 0, ncfu = 0;
+    int reflux = 1;
 };
 
 extern "C" {
@@ -721,9 +932,9 @@ size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine,
                                int ratio) {
     GridRefs c;
     if (!fine || grid_refs(coarse, &c) != SWA_OK) return 0;
-    std::vector<int4> f, a;
-    if (amr::build_maps(c, fine, level, ratio, f, a) != SWA_OK) return 0;
-    return ((sizeof(int4) * f.size() + 255) & ~(size_t)255) + sizeof(int4) * a.size() + 512;
+    std::vector<int4> f, a, e, u;
+    if (amr::build_maps(c, fine, level, ratio, f, a, e, u) != SWA_OK) return 0;
+    return amr::layout_of(f.size(), a.size(), e.size(), u.size()).total;
 }
 
 int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
@@ -732,25 +943,34 @@ int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, v
     if (!fine || !ws || !out) return set_error(SWA_EINVAL, "null argument");
     TRY(grid_refs(coarse, &c));
     if (((uintptr_t)ws & 255) != 0) return set_error(SWA_EINVAL, "workspace must be 256-byte aligned");
-    std::vector<int4> f, a;
-    TRY(amr::build_maps(c, fine, level, ratio, f, a));
-    const size_t need = ((sizeof(int4) * f.size() + 255) & ~(size_t)255) + sizeof(int4) * a.size() + 512;
-    if (ws_bytes < need) return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, need);
+    std::vector<int4> f, a, e, u;
+    TRY(amr::build_maps(c, fine, level, ratio, f, a, e, u));
+    const amr::Layout L = amr::layout_of(f.size(), a.size(), e.size(), u.size());
+    if (ws_bytes < L.total)
+        return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, L.total);
     swa_amr *A = new (std::nothrow) swa_amr();
     if (!A) return set_error(SWA_ENOMEM, "host allocation failed");
     A->coarse = coarse; A->fine = fine; A->level = level; A->r = ratio;
-    A->fill = (int4 *)ws;
-    A->avg = (int4 *)((char *)ws + ((sizeof(int4) * f.size() + 255) & ~(size_t)255));
+    char *base = (char *)ws;
+    A->fill = (int4 *)(base + L.fill);
+    A->avg = (int4 *)(base + L.avg);
+    A->cf = (int4 *)(base + L.cf);
+    A->cfu = (int4 *)(base + L.cfu);
+    A->dh = (double *)(base + L.dh);
     A->nfill = (int)f.size();
     A->navg = (int)a.size();
+    A->ncf = (int)e.size();
+    A->ncfu = (int)u.size();
     cudaStream_t st = (cudaStream_t)stream;
     int rc = SWA_OK;
-    if (!f.empty())
-        rc = cuda_check(cudaMemcpyAsync(A->fill, f.data(), sizeof(int4) * f.size(),
-                                        cudaMemcpyHostToDevice, st), "AMR fill map upload");
-    if (rc == SWA_OK && !a.empty())
-        rc = cuda_check(cudaMemcpyAsync(A->avg, a.data(), sizeof(int4) * a.size(),
-                                        cudaMemcpyHostToDevice, st), "AMR average map upload");
+    const std::vector<int4> *src[4] = {&f, &a, &e, &u};
+    int4 *dst[4] = {A->fill, A->avg, A->cf, A->cfu};
+    const char *what[4] = {"AMR fill map upload", "AMR average map upload",
+                           "AMR edge map upload", "AMR edge group upload"};
+    for (int k = 0; k < 4 && rc == SWA_OK; k++)
+        if (!src[k]->empty())
+            rc = cuda_check(cudaMemcpyAsync(dst[k], src[k]->data(), sizeof(int4) * src[k]->size(),
+                                            cudaMemcpyHostToDevice, st), what[k]);
     if (rc == SWA_OK) rc = cuda_check(cudaStreamSynchronize(st), "create_amr");
     if (rc != SWA_OK) { delete A; return rc; }
     *out = A;
@@ -762,6 +982,20 @@ int swa_destroy_amr(swa_amr *A) {
     return SWA_OK;
 }
 
+int swa_amr_set_reflux(swa_amr *A, int on) {
+    if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
+    A->reflux = on != 0;
+    return SWA_OK;
+}
+
+int swa_amr_info(const swa_amr *A, int *nfill, int *navg, int *nedges) {
+    if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
+    if (nfill) *nfill = A->nfill;
+    if (navg) *navg = A->navg;
+    if (nedges) *nedges = A->ncf;
+    return SWA_OK;
+}
+
 int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *stream) {
     if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
     if (!(dt_c > 0.0)) return set_error(SWA_EINVAL, "dt_c must be > 0");
@@ -770,6 +1004,9 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     TRY(grid_refs(A->coarse, &c));
     if (!c.state_set) return set_error(SWA_ESTATE, "coarse state not set");
     if (!A->fine->lev[A->level].started) return set_error(SWA_ESTATE, "fine level not started");
+    const bool reflux = A->reflux && A->ncf > 0;
+    if (reflux && c.scheme != SWA_SCHEME_SPLIT)
+        return set_error(SWA_EINVAL, "refluxing needs the split scheme on the coarse grid");
     cudaStream_t st = (cudaStream_t)stream;
     amr::AmrParams p{};
     p.table = A->fine->table;
@@ -782,14 +1019,39 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     p.avg = A->avg; p.navg = A->navg;
     p.t_n = t_n; p.dt_c = dt_c; p.t_end = t_n + dt_c;
     p.err = swadj_host::error_word();
+    amr::RefluxParams q{};
+    q.table = p.table; q.lclk = p.lclk; q.cclk = p.cclk;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) q.cq[b][k] = p.cq[b][k];
+    q.chb = (const float *)c.bath;
+    q.nxc = c.d.nx; q.nyc = c.d.ny; q.r = A->r;
+    q.cbc = BcSpec{c.d.bc[0], c.d.bc[1], c.d.bc[2], c.d.bc[3]};
+    q.dxc = c.d.dx; q.dyc = c.d.dy;
+    q.nxc_d = (double)(float)c.d.dx; q.nyc_d = (double)(float)c.d.dy;
+    const patches::LevelParams lp = level_params(A->fine, A->level, t_n);
+    q.dxf = lp.dx; q.dyf = lp.dy;
+    q.gc = (float)c.d.g; q.gf = lp.g;
+    q.orderc = c.d.order; q.orderf = lp.order;
+    q.cf = A->cf; q.ncf = A->ncf; q.cfu = A->cfu; q.ncfu = A->ncfu; q.dh = A->dh;
     const unsigned fb = ew_blocks((size_t)3 * (A->nfill > 0 ? A->nfill : 1));
     const unsigned ab = ew_blocks((size_t)3 * (A->navg > 0 ? A->navg : 1));
+    const unsigned eb = (unsigned)((A->ncf + 127) / 128), ub = (unsigned)((A->ncfu + 127) / 128);
+    if (reflux) {
+        q.t_end = p.t_end;
+        amr::reflux_coarse_kernel<<<eb, 128, 0, st>>>(q);
+        TRY(cuda_check(cudaGetLastError(), "reflux_coarse_kernel"));
+    }
     TRY(swa_step_forward(A->coarse, 1, p.t_end, stream));
     for (int k = 1; k <= A->r; k++) {
         const double t_k = k == A->r ? p.t_end : t_n + dt_c * (double)k / (double)A->r;
+        q.t_end = t_k;
         for (int j = 0; j < max_launches; j++) {
             amr::amr_fill_kernel<<<fb, 256, 0, st>>>(p);
             TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
+            if (reflux) {
+                amr::reflux_fine_kernel<<<eb, 128, 0, st>>>(q);
+                TRY(cuda_check(cudaGetLastError(), "reflux_fine_kernel"));
+            }
             TRY(swa_step_level(A->fine, A->level, 1, t_k, stream));
         }
     }
@@ -800,7 +1062,12 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
         case 8: amr::amr_avg_kernel<8><<<ab, 256, 0, st>>>(p); break;
         default: amr::amr_avg_kernel<0><<<ab, 256, 0, st>>>(p); break;
     }
-    return cuda_check(cudaGetLastError(), "amr_avg_kernel");
+    TRY(cuda_check(cudaGetLastError(), "amr_avg_kernel"));
+    if (reflux) {
+        amr::reflux_apply_kernel<<<ub, 128, 0, st>>>(q);
+        TRY(cuda_check(cudaGetLastError(), "reflux_apply_kernel"));
+    }
+    return SWA_OK;
 }
 
 }  // extern "C"

@@ -123,6 +123,7 @@ struct GridRefs {
     const void *bath;   // B (FP64) or hbar = -B (FP32)
     DevClock *clk;
     int state_set;
+    int scheme;         // SWA_SCHEME_SPLIT or SWA_SCHEME_CTU
 };
 int grid_refs(const swa_grid *g, GridRefs *out);
 // FP64 mass audit (audit.cu)

@@ -50,6 +50,7 @@ EXPORTS = [
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
+    "swa_amr_set_reflux", "swa_amr_info",
     "swa_alu_probe_ops", "swa_alu_probe",
     "swa_grid_mass",
 ]
@@ -157,6 +158,8 @@ def load(path: str = LIB_PATH):
         "swa_create_amr": ([_V, _V, _I, _I, _V, _SZ, _V, _P(_V)], _I),
         "swa_destroy_amr": ([_V], _I),
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
+        "swa_amr_set_reflux": ([_V, _I], _I),
+        "swa_amr_info": ([_V, _P(_I), _P(_I), _P(_I)], _I),
         "swa_alu_probe_ops": ([_I, _I, _I, _I], _D),
         "swa_grid_mass": ([_V, _V, _V], _I),
         "swa_alu_probe": ([_I, _I, _I, _I, _V, _V], _I),
@@ -623,6 +626,16 @@ def swa_amr_step(h, t_n, dt_c, max_launches=1, stream=None):
                                     _stream(stream)))
 
 
+def swa_amr_set_reflux(h, on):
+    return _chk(load().swa_amr_set_reflux(h, int(bool(on))))
+
+
+def swa_amr_info(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _chk(load().swa_amr_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 class PatchSet:
     """Batched patches; `patches` is a list of (level, x_lo, y_lo, nx, ny, dx, dy)."""
 
@@ -681,6 +694,13 @@ class Amr:
 
     def step(self, t_n, dt_c, max_launches=1, stream=None):
         swa_amr_step(self.h, t_n, dt_c, max_launches, stream)
+
+    def set_reflux(self, on):
+        swa_amr_set_reflux(self.h, on)
+
+    def info(self):
+        """(ring cells filled, covered coarse cells, coarse-fine edges)."""
+        return swa_amr_info(self.h)
 
     def __del__(self):
         try:

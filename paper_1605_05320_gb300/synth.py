@@ -305,7 +305,7 @@ def patch_fields(patch, L: float = 2048e3, seed: int = 1605, n_seamounts: int = 
 
 # ------------------------------------------------------------- AMR cases
 def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
-              seed: int | None = None):
+              seed: int | None = None, mean_coarse: bool = False):
     """A walled nc x nc coarse basin (cell dx) with fine patches refined by r.
 
     boxes: patch interiors in coarse cells, (i0, j0, mx, my); each patch is
@@ -314,6 +314,9 @@ def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
     centre, or the ocean at rest), sampled at coarse centres and once on the
     global fine grid, so patches agree wherever they overlap.  seed: uniform
     random momenta in [-5, 5] (r = 1 only, where the levels share cells).
+    mean_coarse: the coarse bottom and surface are the means of the fine
+    samples over each coarse cell instead (a hierarchy whose covered coarse
+    cells already hold the fine means).
     Returns a dict with the coarse fields (B, eta, hu, hv), per patch the
     descriptor (level 1, x_lo, y_lo, nx, ny, dx, dy) and fields (B, eta, hu,
     hv, ring included)."""
@@ -332,6 +335,9 @@ def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
     Bc, BF = bottom(X, Y), bottom(XF, YF)
     ec = np.zeros_like(X) if rest else hump(X, Y)
     EF = np.zeros_like(XF) if rest else hump(XF, YF)
+    if mean_coarse:
+        Bc = BF.reshape(nc, r, nc, r).mean(axis=(1, 3))
+        ec = EF.reshape(nc, r, nc, r).mean(axis=(1, 3))
     uc = np.zeros_like(X)
     UF = np.zeros_like(XF)
     if seed is not None:

@@ -1,7 +1,7 @@
-// Host-only check of the AMR glue's map builder (no GPU needed): the fill
-// and average maps that build_maps produces from random patch layouts equal
-// those of a brute-force search over every patch, and bad geometry is
-// rejected.  Built and run by tests/test_amr_host.py.
+// Host-only check of the AMR glue's map builder (no GPU needed): the fill,
+// average and coarse-fine edge maps that build_maps produces from random
+// patch layouts equal those of a brute-force search over every patch, and
+// bad geometry is rejected.  Built and run by tests/test_amr_host.py.
 #include "patches.cu"
 
 #include <algorithm>
@@ -20,9 +20,12 @@ struct Box {
 };
 
 // The maps by definition: for each ring cell, search every patch in index
-// order; for each covered coarse cell, the first patch in index order.
+// order; for each covered coarse cell, the first patch in index order; for
+// each uncovered coarse cell, its neighbours (+x, -x, +y, -y) that some
+// patch covers, with the first such patch's fine cells along the edge.
 void brute_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
-                std::vector<int4> &fill, std::vector<int4> &avg) {
+                std::vector<int4> &fill, std::vector<int4> &avg, std::vector<int4> &cf,
+                std::vector<int4> &cfu) {
     const swa_grid_desc &d = c.d;
     std::vector<int> ids;
     std::vector<Box> box;
@@ -65,6 +68,43 @@ void brute_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
                                             (int)((jc * r - b.J0) * b.nx + (ic * r - b.I0)), 0));
                     break;
                 }
+    auto cover = [&](long long ic, long long jc) {
+        for (int a = 0; a < np; a++)
+            if (box[a].interior(ic * r, jc * r)) return a;
+        return -1;
+    };
+    for (int jc = 0; jc < d.ny; jc++)
+        for (int ic = 0; ic < d.nx; ic++) {
+            if (cover(ic, jc) >= 0) continue;
+            const int first = (int)cf.size();
+            const int step[4][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 1}, {0, -1, 1}};
+            for (const auto &s : step) {
+                const int iv = ic + s[0], jv = jc + s[1], axis = s[2];
+                if (iv < 0 || iv >= d.nx || jv < 0 || jv >= d.ny) continue;
+                const int a = cover(iv, jv);
+                if (a < 0) continue;
+                const Box &b = box[a];
+                const bool hi = s[0] + s[1] > 0;
+                // the fine cell of V touching U with the lowest coordinate
+                // along the edge, then steps of one fine cell along it
+                const long long I = axis == 0 ? (long long)iv * r + (hi ? 0 : r - 1) : (long long)iv * r;
+                const long long J = axis == 1 ? (long long)jv * r + (hi ? 0 : r - 1) : (long long)jv * r;
+                const int stride = axis == 0 ? b.nx : 1;
+                cf.push_back(make_int4(jc * d.nx + ic, ids[a],
+                                       (int)((J - b.J0) * b.nx + (I - b.I0)),
+                                       axis + 2 * (hi ? 1 : 0) + 4 * stride));
+            }
+            if ((int)cf.size() > first)
+                cfu.push_back(make_int4(jc * d.nx + ic, first, (int)cf.size() - first, 0));
+        }
+}
+
+bool same_in_order(const std::vector<int4> &u, const std::vector<int4> &v) {
+    if (u.size() != v.size()) return false;
+    for (size_t i = 0; i < u.size(); i++)
+        if (u[i].x != v[i].x || u[i].y != v[i].y || u[i].z != v[i].z || u[i].w != v[i].w)
+            return false;
+    return true;
 }
 
 bool same(std::vector<int4> u, std::vector<int4> v) {
@@ -106,6 +146,7 @@ void set_patches(swa_patchset &ps, const std::vector<swa_patch_desc> &pd) {
 int main() {
     std::mt19937 rng(1605);
     int checked = 0, failures = 0;
+    long long edges = 0;
     for (int trial = 0; trial < 300; trial++) {
         GridRefs c{};
         c.d.ndim = 2;
@@ -130,16 +171,21 @@ int main() {
         swa_patchset ps;
         set_patches(ps, pd);
         if (ps.lev[1].npatches == 0) continue;
-        std::vector<int4> f1, a1, f2, a2;
-        if (amr::build_maps(c, &ps, 1, r, f1, a1) != SWA_OK) {
+        std::vector<int4> f1, a1, e1, u1, f2, a2, e2, u2;
+        if (amr::build_maps(c, &ps, 1, r, f1, a1, e1, u1) != SWA_OK) {
             printf("trial %d rejected a valid layout: %s\n", trial, swa_last_error());
             failures++;
             continue;
         }
-        brute_maps(c, &ps, 1, r, f2, a2);
+        brute_maps(c, &ps, 1, r, f2, a2, e2, u2);
         checked++;
+        edges += (long long)e1.size();
         if (!same(f1, f2) || !same(a1, a2)) {
             printf("trial %d: maps differ\n", trial);
+            failures++;
+        }
+        if (!same_in_order(e1, e2) || !same_in_order(u1, u2)) {
+            printf("trial %d: edge maps differ (%zu vs %zu edges)\n", trial, e1.size(), e2.size());
             failures++;
         }
     }
@@ -158,8 +204,8 @@ int main() {
     for (auto &b : bad) {
         swa_patchset ps;
         set_patches(ps, {b.q});
-        std::vector<int4> f, a;
-        if (amr::build_maps(c, &ps, 1, b.r, f, a) != SWA_EINVAL) {
+        std::vector<int4> f, a, e, u;
+        if (amr::build_maps(c, &ps, 1, b.r, f, a, e, u) != SWA_EINVAL) {
             printf("not rejected: %s\n", b.what);
             failures++;
         }
@@ -169,8 +215,8 @@ int main() {
     {
         swa_patchset ps;
         set_patches(ps, {patch(c, 1, 2, 5, 5, 4, 4)});
-        std::vector<int4> f, a;
-        if (amr::build_maps(c64, &ps, 1, 2, f, a) != SWA_EINVAL) {
+        std::vector<int4> f, a, e, u;
+        if (amr::build_maps(c64, &ps, 1, 2, f, a, e, u) != SWA_EINVAL) {
             printf("not rejected: FP64 coarse grid\n");
             failures++;
         }
@@ -180,12 +226,12 @@ int main() {
         swa_patchset ps;
         set_patches(ps, {patch(c, 1, 2, 5, 5, 4, 4)});
         ps.common.bc[2] = SWA_BC_WALL;
-        std::vector<int4> f, a;
-        if (amr::build_maps(c, &ps, 1, 2, f, a) != SWA_EINVAL) {
+        std::vector<int4> f, a, e, u;
+        if (amr::build_maps(c, &ps, 1, 2, f, a, e, u) != SWA_EINVAL) {
             printf("not rejected: fine patch set with a wall\n");
             failures++;
         }
     }
-    printf("layouts checked %d, failures %d\n", checked, failures);
-    return failures == 0 && checked >= 100 ? 0 : 1;
+    printf("layouts checked %d, coarse-fine edges %lld, failures %d\n", checked, edges, failures);
+    return failures == 0 && checked >= 100 && edges > 1000 ? 0 : 1;
 }

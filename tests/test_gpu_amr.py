@@ -3,8 +3,12 @@ hierarchy (oracle/amr.py), through the C ABI.
 
 Tolerances: the GPU levels are FP32 (perturbation form), the oracle FP64:
 eta within 2e-5 m (a 0.5 m hump over 80-120 m), momenta within 2e-5 of their
-maximum, after the steps each test takes.  Exact where FP32 is exact: the
-ocean at rest, r = 1 against the single grid, a patch cut in two.
+maximum, after the steps each test takes, with refluxing on and off.  Exact
+where FP32 is exact: the ocean at rest, r = 1 against the single grid, a
+patch cut in two.  Mass (FP64 audit of the coarse grid, whose covered cells
+hold the fine means): with refluxing it stays within 1e-9 of its start
+(relative; FP32 rounding of the updates is near 1e-11), without it drifts by
+more than 1e-7 (the oracle drifts by 7e-7 to 2e-6 on these layouts).
 """
 import numpy as np
 import pytest
@@ -49,12 +53,12 @@ def gpu_hierarchy(S, case):
     return grid, ps, amr
 
 
-def oracle_hierarchy(case):
+def oracle_hierarchy(case, reflux=True):
     nc, dx, r = case["nc"], case["dx"], case["r"]
     cg = O.Grid(2, nc, nc, 0.0, 0.0, dx, dx, order=2, bc=(1, 1, 1, 1))
     c = case["coarse"]
     patches = [Patch(*p["box"]) for p in case["patches"]]
-    H = Hierarchy(cg, c["B"], patches, r, [p["B"] for p in case["patches"]])
+    H = Hierarchy(cg, c["B"], patches, r, [p["B"] for p in case["patches"]], reflux=reflux)
     H.set_state(c["eta"] - c["B"], c["hu"], c["hv"],
                 [(p["eta"] - p["B"], p["hu"], p["hv"]) for p in case["patches"]], 0.0)
     return H, cg
@@ -76,9 +80,11 @@ def dt_coarse(dx):
     return 0.6 * 0.75 * dx / np.sqrt(9.81 * 130.0)
 
 
-def run_both(S, case, steps, m=1):
+def run_both(S, case, steps, m=1, reflux=True):
     grid, ps, amr = gpu_hierarchy(S, case)
-    H, cg = oracle_hierarchy(case32(case))
+    amr.set_reflux(reflux)
+    H, cg = oracle_hierarchy(case32(case), reflux=reflux)
+    assert amr.info()[2] == len(H.cf_edges)
     dt, t = dt_coarse(case["dx"]), 0.0
     for _ in range(steps):
         amr.step(t, dt, m)
@@ -93,9 +99,10 @@ def run_both(S, case, steps, m=1):
     (4, [(6, 7, 5, 6), (10, 9, 6, 5), (15, 4, 3, 3)]),   # overlapping, adjacent, apart
     (3, [(7, 8, 4, 7), (11, 8, 5, 7)]),                   # odd ratio, siblings side by side
 ])
-def test_hierarchy_matches_the_oracle(S, r, boxes):
+@pytest.mark.parametrize("reflux", [True, False])
+def test_hierarchy_matches_the_oracle(S, r, boxes, reflux):
     case = synth.amr_basin(24, r, boxes)
-    grid, ps, H, t = run_both(S, case, 6)
+    grid, ps, H, t = run_both(S, case, 6, reflux=reflux)
     st = grid.get_state()
     Bc = case32(case)["coarse"]["B"]
     assert np.abs(st["eta"] - (H.h + Bc)).max() <= 2e-5
@@ -112,6 +119,52 @@ def test_hierarchy_matches_the_oracle(S, r, boxes):
         assert np.abs(f["hu"] - fu)[inner].max() <= 2e-5 * np.abs(fu).max()
         assert np.abs(f["hv"] - fv)[inner].max() <= 2e-5 * np.abs(fv).max()
     assert abs(grid.time()[0] - t) <= 1e-12 * t and abs(ps.time(1)[0] - t) <= 1e-12 * t
+
+
+MASS_SETS = [(2, [(8, 8, 8, 8)]),
+             (4, [(6, 6, 5, 7), (11, 9, 6, 4)]),
+             (3, [(4, 4, 6, 6), (10, 4, 4, 6), (12, 7, 5, 5)])]
+
+
+def coarse_mass(S, grid):
+    m = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.swa_grid_mass(grid.h, m)
+    torch.cuda.synchronize()
+    return m.item()
+
+
+@pytest.mark.parametrize("r,boxes", MASS_SETS)
+def test_refluxing_conserves_mass(S, r, boxes):
+    """Walls all round, coarse bottom and surface the means of the fine
+    samples: the coarse grid's mass (its covered cells hold the fine means)
+    stays constant over 10 coarse steps with refluxing and drifts without."""
+    drift = {}
+    for reflux in (True, False):
+        case = synth.amr_basin(24, r, boxes, mean_coarse=True)
+        grid, ps, amr = gpu_hierarchy(S, case)
+        amr.set_reflux(reflux)
+        dt, t = dt_coarse(case["dx"]), 0.0
+        m0 = coarse_mass(S, grid)
+        for _ in range(10):
+            amr.step(t, dt)
+            t = t + dt
+        assert S.swa_sync_status() == 0
+        drift[reflux] = abs(coarse_mass(S, grid) - m0) / m0
+    assert drift[True] <= 1e-9, drift
+    assert drift[False] > 1e-7, drift
+    print(f"r={r}: relative mass drift {drift[True]:.1e} with refluxing, "
+          f"{drift[False]:.1e} without")
+
+
+def test_refluxing_needs_the_split_scheme(S):
+    case = synth.amr_basin(16, 2, [(5, 5, 4, 4)])
+    grid, ps, amr = gpu_hierarchy(S, case)
+    grid.set_scheme(S.SWA_SCHEME_CTU)
+    with pytest.raises(S.SwaError):
+        amr.step(0.0, dt_coarse(case["dx"]))
+    amr.set_reflux(False)
+    amr.step(0.0, dt_coarse(case["dx"]))
+    assert S.swa_sync_status() == 0
 
 
 def test_ratio_one_is_the_single_grid_bit_for_bit(S):
