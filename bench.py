@@ -382,8 +382,9 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     tiles x tiles patches of side x side coarse cells refined by `ratio`,
     tiling a square around the source (the basin fields sampled at 250 m).
     Times `steps` hierarchy steps (coarse step, `ratio` fine substeps each
-    with its ring fill, averaging down) after 3 warm-up steps, and the coarse
-    step and the fine launch on their own, with CUDA events on the stream."""
+    with its ring fill, averaging down, refluxing) after 3 warm-up steps, the
+    same without refluxing, and the coarse step and the fine launch on their
+    own, with CUDA events on the stream."""
     import torch
     from paper_1605_05320_gb300 import swadj as S
     from paper_1605_05320_gb300 import synth
@@ -423,8 +424,12 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     for _ in range(3):
         one_step()
     us_step = timed(one_step, steps)
+    amr.set_reflux(False)
+    us_plain = timed(one_step, steps)
+    amr.set_reflux(True)
     if S.swa_sync_status(hs) != 0:
         raise RuntimeError("AMR hierarchy step reported an error")
+    nfill, navg, nedges = amr.info()
     g2, ps2, _ = hierarchy()
     us_coarse = timed(lambda: g2.step(1, 1e12, hs), steps)
     us_fine = timed(lambda: ps2.step(1, 1, 1e300, hs), steps * ratio)
@@ -436,6 +441,8 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
             "us_per_step": round(us_step, 1), "coarse_step_us": round(us_coarse, 1),
             "fine_launch_us": round(us_fine, 1),
             "glue_us_per_step": round(us_step - us_coarse - ratio * us_fine, 1),
+            "ring_cells": nfill, "covered_coarse_cells": navg, "coarse_fine_edges": nedges,
+            "us_per_step_without_refluxing": round(us_plain, 1),
             "cell_updates_per_s": updates / (us_step * 1e-6)}
 
 

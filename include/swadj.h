@@ -430,8 +430,8 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  */
 typedef struct swa_amr swa_amr;
 /* Device workspace for the maps and the refluxing corrections (16 bytes per
- * ring cell and per covered coarse cell, 24 per coarse-fine edge, 16 per
- * uncovered coarse cell beside the fine level, plus padding); 0 if the
+ * ring cell and per covered coarse cell, 24 + 8 r per coarse-fine edge, 16
+ * per uncovered coarse cell beside the fine level, plus padding); 0 if the
  * geometry is invalid (the reason is in swa_last_error). */
 size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
                                int ratio);

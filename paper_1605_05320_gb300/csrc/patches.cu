@@ -28,6 +28,108 @@ struct PatchDevice {
     BcSpec bc;
 };
 
+// ------------------------------------------------------------ refluxing
+// Mass flux through an edge of cell (i, j), low (side < 0) or high (side >
+// 0), along `axis`, as the FP32 split step forms it: x-edges from the state
+// (x-sweep), y-edges from the x-swept state (y-sweep).  The edge's flux is
+// F = mn_L + L0, the normal momentum of the cell below it plus the net the
+// update gives that cell (in exact arithmetic also mn_R - R0, the cell
+// above it), so a cell's update is dh = -nu (F_high - F_low) per sweep and
+// both sides of an edge see the same number.  The edge arithmetic is the
+// strip kernel's (fwd_pair.cuh), each net in the form its own edge picks
+// (the warp-uniform choice of the kernel gives the same numbers).
+namespace reflux {
+
+struct CellRaw {
+    float eta, mu, mv, hb;
+};
+
+__device__ __forceinline__ CellRaw raw_at(const strip::View &v, int i, int j) {
+    bool fx, fy;
+    const int ii = ghost_index(i, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
+    const int jj = ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+    const size_t o = (size_t)jj * v.nx + ii;
+    CellRaw c;
+    c.eta = v.q0[o];
+    c.hb = v.hb[o];
+    const float mu = v.q1[o], mv = v.q2[o];
+    c.mu = fx ? -mu : mu;
+    c.mv = fy ? -mv : mv;
+    return c;
+}
+
+// x-frame cell data of cell (i, j)
+__device__ __forceinline__ fp::Cell<float> xcell(const strip::View &v, int i, int j) {
+    const CellRaw c = raw_at(v, i, j);
+    return fp::derive(c.eta, fp::add(c.eta, c.hb), c.mu, c.mv);
+}
+
+// the x-swept cell (i, j) in the y frame, as the strip kernel's x-sweep
+// leaves it
+__device__ __forceinline__ fp::Cell<float> xswept(const strip::View &v, int i, int j, float gh,
+                                                  float nux, int order) {
+    fp::Cell<float> c[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) c[k] = xcell(v, i - 2 + k, j);
+    fp::Edge<float> w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
+    const fp::Net<float> nl = fp::net3(w[0], w[1], w[2], nux, order, fp::subsonic(w[1].s1, w[1].s3));
+    const fp::Net<float> nr = fp::net3(w[1], w[2], w[3], nux, order, fp::subsonic(w[2].s1, w[2].s3));
+    const float d0 = fp::mul(-nux, fp::add(nl.R0, nr.L0));
+    const float d1 = fp::mul(-nux, fp::add(nl.R1, nr.L1));
+    const float d2 = fp::mul(-nux, fp::add(nl.R2, nr.L2));
+    const fp::Cell<float> &a = c[2];
+    return fp::derive(fp::add(a.eta, d0), fp::add(a.h, d0), fp::add(a.mt, d2), fp::add(a.mn, d1));
+}
+
+// Flux of the edge between stencil cells 1 and 2 of the 4 cells at offsets
+// k0 .. k0 + 3 from (i, j) along `axis`, formed by a group of 4 lanes: lane
+// q = lane & 3 forms stencil cell q (x-sweeping its row first for a y-edge),
+// its edge to cell q + 1 and the neighbour edges come by shuffles, and the
+// result is valid on the lane with q == 1.  All 32 lanes must call it.
+__device__ __forceinline__ float group_flux(const strip::View &v, int i, int j, int axis, int k0,
+                                            float gh, float nux, float nuy, int order) {
+    using strip::dn;
+    using strip::up;
+    const int q = threadIdx.x & 3;
+    const fp::Cell<float> c =
+        axis == 0 ? xcell(v, i + k0 + q, j) : xswept(v, i, j + k0 + q, gh, nux, order);
+    fp::Cell<float> n = c;
+    n.h = dn(c.h); n.mn = dn(c.mn); n.sq = dn(c.sq); n.su = dn(c.su); n.sv = dn(c.sv);
+    n.P = dn(c.P); n.T = dn(c.T); n.eta = dn(c.eta);
+    const fp::Edge<float> w = fp::solve(gh, c, n);   // edge (q | q + 1)
+    fp::Edge<float> wl = w, wr = w;
+    wl.s1 = up(w.s1); wl.s3 = up(w.s3); wl.vh = up(w.vh);
+    wl.b1 = up(w.b1); wl.b2 = up(w.b2); wl.b3 = up(w.b3);
+    wr.s1 = dn(w.s1); wr.s3 = dn(w.s3); wr.vh = dn(w.vh);
+    wr.b1 = dn(w.b1); wr.b2 = dn(w.b2); wr.b3 = dn(w.b3);
+    const fp::Net<float> N =
+        fp::net3(wl, w, wr, axis == 0 ? nux : nuy, order, fp::subsonic(w.s1, w.s3));
+    return fp::add(c.mn, N.L0);
+}
+
+// the step the coming launch takes on this clock (as begin_step forms it)
+__device__ __forceinline__ double coming_dt(const DevClock *clk, double t_end) {
+    volatile const DevClock *c = clk;
+    double dt = c->dt_cfl;
+    if (t_end - c->t < dt) dt = t_end - c->t;
+    return dt > 0.0 ? dt : 0.0;
+}
+
+}  // namespace reflux
+
+// Refluxing work of a level launch inside the AMR glue: per coarse-fine
+// edge e and fine cell k along it (item e r + k), dhf[item] -= (dt_f / d)
+// (1 / r) F_f, the flux into the fine region across the edge over this
+// launch.  nitems = 0: none.
+struct LevelReflux {
+    const int4 *cf;   // edges (U, patch, first fine cell, axis | hi << 1 | stride << 2)
+    double *dhf;
+    int nitems, r;
+    double dxc, dyc;  // coarse cell size
+};
+
 struct LevelParams {
     const PatchDevice *table;
     const int4 *units;   // (patch, x0, y0, 0)
@@ -39,7 +141,32 @@ struct LevelParams {
     float g;
     int order;
     int *err;
+    LevelReflux rf;
 };
+
+// One task of a level launch's refluxing work: 8 items, 4 lanes each.
+__device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, int cur,
+                                               float nux, float nuy, double dt) {
+    const int lane = threadIdx.x & 31;
+    int item = task * 8 + (lane >> 2);
+    const bool live = item < p.rf.nitems;
+    if (!live) item = p.rf.nitems - 1;   // idle lanes redo the last item for the shuffles
+    const int e = item / p.rf.r, k = item - e * p.rf.r;
+    const int4 m = p.rf.cf[e];
+    const PatchDevice &P = p.table[m.y];
+    strip::View v;
+    v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
+    v.nx = P.nx; v.ny = P.ny; v.bc = P.bc;
+    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1, stride = m.w >> 2;
+    const int c = m.z + k * stride;
+    // V on U's high side: the fine cell's low edge (stencil from two cells
+    // below it); else its high edge (from one below)
+    const float f = reflux::group_flux(v, c % P.nx, c / P.nx, axis, side > 0 ? -2 : -1,
+                                       0.5f * p.g, nux, nuy, p.order);
+    if (live && (lane & 3) == 1)
+        p.rf.dhf[item] -= dt / (axis == 0 ? p.rf.dxc : p.rf.dyc) / (double)p.rf.r *
+                          (double)(side > 0 ? f : -f);
+}
 
 __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelParams p) {
     __shared__ float s_nu[2];
@@ -63,6 +190,15 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
         v.nx = P.nx; v.ny = P.ny; v.rdx = P.rdx; v.rdy = P.rdy; v.bc = P.bc;
         strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
                           ring[threadIdx.x >> 5], smax, bad);
+    }
+    if (p.rf.nitems > 0) {
+        // the warps with one strip fewer start on the refluxing tasks; the
+        // clock is not advanced before every block has finished them
+        const int total = gridDim.x * wpb, gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+        const int ntasks = (p.rf.nitems + 7) / 8, rem = p.nunits % total;
+        const double dt_now = reflux::coming_dt(p.clk, p.t_end);
+        for (int t = (gw + total - rem) % total; t < ntasks; t += total)
+            level_reflux_task(p, t, cur, s_nu[0], s_nu[1], dt_now);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
@@ -288,6 +424,25 @@ static LevelParams level_params(const swa_patchset *ps, int l, double t_end) {
     return p;
 }
 
+// nsteps launches of the level step, with the refluxing work rf in each.
+static int level_launch(swa_patchset *ps, int level, int nsteps, double t_end,
+                        const LevelReflux &rf, cudaStream_t st) {
+    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
+    Level &L = ps->lev[level];
+    if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
+    if (!L.started) return set_error(SWA_ESTATE, "level %d not started", level);
+    if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
+    LevelParams p = level_params(ps, level, t_end);
+    p.rf = rf;
+    constexpr int wpb = strip::kThreads / 32;
+    const int need = (p.nunits + wpb - 1) / wpb;
+    p.nblocks = occupancy_blocks();
+    if (p.nblocks > need) p.nblocks = need;
+    for (int s = 0; s < nsteps; s++)
+        level_strip_kernel<<<p.nblocks, strip::kThreads, 0, st>>>(p);
+    return cuda_check(cudaGetLastError(), "level_strip_kernel");
+}
+
 extern "C" {
 
 size_t swa_patches_workspace_bytes(int n, const swa_patch_desc *patches,
@@ -427,20 +582,7 @@ int swa_patches_get_state(swa_patchset *ps, int k, double *h, double *hu, double
 }
 
 int swa_step_level(swa_patchset *ps, int level, int nsteps, double t_end, void *stream) {
-    if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
-    Level &L = ps->lev[level];
-    if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
-    if (!L.started) return set_error(SWA_ESTATE, "level %d not started", level);
-    if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
-    cudaStream_t st = (cudaStream_t)stream;
-    LevelParams p = level_params(ps, level, t_end);
-    constexpr int wpb = strip::kThreads / 32;
-    const int need = (p.nunits + wpb - 1) / wpb;
-    p.nblocks = occupancy_blocks();
-    if (p.nblocks > need) p.nblocks = need;
-    for (int s = 0; s < nsteps; s++)
-        level_strip_kernel<<<p.nblocks, strip::kThreads, 0, st>>>(p);
-    return cuda_check(cudaGetLastError(), "level_strip_kernel");
+    return level_launch(ps, level, nsteps, t_end, LevelReflux{}, (cudaStream_t)stream);
 }
 
 int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next,
@@ -506,6 +648,9 @@ struct AmrParams {
     int nfill;
     const int4 *avg;
     int navg;
+    const int4 *cfu;   // refluxing: (U, first edge, edges, 0); ncfu = 0: none
+    int ncfu;
+    const double *dh, *dhf;
     double t_n, dt_c, t_end;
     int *err;
 };
@@ -579,7 +724,11 @@ __device__ __forceinline__ float block_sum(const float *f, int nx, int r) {
 
 // Coarse cells under a patch := mean of their r x r fine cells (eta, hu, hv).
 // Entry (coarse cell, patch, first fine cell, 0); one thread per (entry,
-// component).  Also checks that both levels reached the step's end time.
+// component).  Then, one thread per uncovered coarse cell U beside the fine
+// level (refluxing): eta_U += the FP64 sum of its edges' corrections, coarse
+// part plus fine parts, in a fixed order (U is never a covered cell, so the
+// two parts write different cells).  Also checks that both levels reached
+// the step's end time.
 template <int R>
 __global__ void amr_avg_kernel(AmrParams p) {
     volatile const DevClock *lc = p.lclk, *cc = p.cclk;
@@ -592,8 +741,20 @@ __global__ void amr_avg_kernel(AmrParams p) {
     const int fcur = s_fcur, ccur = s_ccur;
     const int r = R > 0 ? R : p.r;
     const float inv = 1.f / (float)(r * r);
-    const int n = 3 * p.navg;
+    const int n3 = 3 * p.navg, n = n3 + p.ncfu;
     for (int e3 = blockIdx.x * blockDim.x + threadIdx.x; e3 < n; e3 += gridDim.x * blockDim.x) {
+        if (e3 >= n3) {
+            const int4 g = __ldg(p.cfu + (e3 - n3));
+            double s = 0.0;
+            for (int e = g.y; e < g.y + g.z; e++) {
+                double f = p.dh[e];
+                for (int k = 0; k < r; k++) f += p.dhf[(size_t)e * r + k];
+                s += f;
+            }
+            float *eta = p.cq[ccur][0];
+            eta[g.x] = fp::add(eta[g.x], (float)s);
+            continue;
+        }
         const int e = e3 / 3, k = e3 - 3 * e;
         const int4 m = __ldg(p.avg + e);
         const PatchDevice &S = p.table[m.y];
@@ -606,166 +767,47 @@ __global__ void amr_avg_kernel(AmrParams p) {
     }
 }
 
-// ------------------------------------------------------------ refluxing
-// Mass flux through an edge of cell (i, j), low (side < 0) or high (side >
-// 0), along `axis`, as the FP32 split step forms it: x-edges from the state
-// (x-sweep), y-edges from the x-swept state (y-sweep).  The edge's flux is
-// F = mn_L + L0, the normal momentum of the cell below it plus the net the
-// update gives that cell (in exact arithmetic also mn_R - R0, the cell
-// above it), so a cell's update is dh = -nu (F_high - F_low) per sweep and
-// both sides of an edge see the same number.  The edge arithmetic is the
-// strip kernel's (fwd_pair.cuh), each net in the form its own edge picks
-// (the warp-uniform choice of the kernel gives the same numbers).
-struct CellRaw {
-    float eta, mu, mv, hb;
-};
-
-__device__ __forceinline__ CellRaw raw_at(const strip::View &v, int i, int j) {
-    bool fx, fy;
-    const int ii = ghost_index(i, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
-    const int jj = ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
-    const size_t o = (size_t)jj * v.nx + ii;
-    CellRaw c;
-    c.eta = v.q0[o];
-    c.hb = v.hb[o];
-    const float mu = v.q1[o], mv = v.q2[o];
-    c.mu = fx ? -mu : mu;
-    c.mv = fy ? -mv : mv;
-    return c;
-}
-
-// x-frame cell data of cell (i, j)
-__device__ __forceinline__ fp::Cell<float> xcell(const strip::View &v, int i, int j) {
-    const CellRaw c = raw_at(v, i, j);
-    return fp::derive(c.eta, fp::add(c.eta, c.hb), c.mu, c.mv);
-}
-
-// the x-swept cell (i, j) in the y frame, as the strip kernel's x-sweep
-// leaves it
-__device__ __forceinline__ fp::Cell<float> xswept(const strip::View &v, int i, int j, float gh,
-                                                  float nux, int order) {
-    fp::Cell<float> c[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) c[k] = xcell(v, i - 2 + k, j);
-    fp::Edge<float> w[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
-    const fp::Net<float> nl = fp::net3(w[0], w[1], w[2], nux, order, fp::subsonic(w[1].s1, w[1].s3));
-    const fp::Net<float> nr = fp::net3(w[1], w[2], w[3], nux, order, fp::subsonic(w[2].s1, w[2].s3));
-    const float d0 = fp::mul(-nux, fp::add(nl.R0, nr.L0));
-    const float d1 = fp::mul(-nux, fp::add(nl.R1, nr.L1));
-    const float d2 = fp::mul(-nux, fp::add(nl.R2, nr.L2));
-    const fp::Cell<float> &a = c[2];
-    return fp::derive(fp::add(a.eta, d0), fp::add(a.h, d0), fp::add(a.mt, d2), fp::add(a.mn, d1));
-}
-
-__device__ __forceinline__ float cell_flux(const strip::View &v, int i, int j, int axis, int side,
-                                           float gh, float nux, float nuy, int order) {
-    fp::Cell<float> c[4];   // the cells of the edge's three-edge stencil
-    const int k0 = side > 0 ? -1 : -2;   // first cell relative to (i, j)
-    float nu;
-    if (axis == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; k++) c[k] = xcell(v, i + k0 + k, j);
-        nu = nux;
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++) c[k] = xswept(v, i, j + k0 + k, gh, nux, order);
-        nu = nuy;
-    }
-    fp::Edge<float> w[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
-    const fp::Net<float> n = fp::net3(w[0], w[1], w[2], nu, order, fp::subsonic(w[1].s1, w[1].s3));
-    // the edge lies between c[1] and c[2]
-    return fp::add(c[1].mn, n.L0);
-}
-
-// Coarse-fine edge e = (U, patch, first fine cell, axis | (side > 0) << 1 |
-// stride << 2): the uncovered coarse cell U, the patch covering its
-// neighbour V and the r fine cells of that patch along the edge inside V.
+// Before the coarse step, per edge: dh[e] = (dt_c / d) F_c, the coarse
+// flux through the edge as U's update will use it (sign: + for V on U's
+// high side), and the edge's fine parts start at zero.  A group of 4 lanes
+// per edge, 8 edges per warp.
 struct RefluxParams {
-    const PatchDevice *table;
-    const DevClock *lclk, *cclk;
-    float *cq[2][3];
+    const DevClock *cclk;
+    const float *cq[2][3];
     const float *chb;
     int nxc, nyc, r;
     BcSpec cbc;
-    double dxc, dyc;     // coarse cell size (the correction's scale)
-    double nxc_d, nyc_d; // the coarse step's nu divisors (its FP32 cell size)
-    double dxf, dyf;     // the fine level's
-    float gc, gf;        // gravity of the coarse step and of the level step
-    int orderc, orderf;
-    const int4 *cf;   // edges
+    double dxc, dyc;      // coarse cell size (the correction's scale)
+    double nxc_d, nyc_d;  // the coarse step's nu divisors (its FP32 cell size)
+    float g;
+    int order;
+    const int4 *cf;
     int ncf;
-    const int4 *cfu;  // (U, first edge, count, 0), edges of one U consecutive
-    int ncfu;
-    double *dh;       // per edge
-    double t_end;     // of the coming step (coarse) or substep (fine)
+    double *dh, *dhf;
+    double t_end;
 };
 
-// the step the coming launch takes on this clock (as begin_step forms it)
-__device__ __forceinline__ double coming_dt(const DevClock *clk, double t_end) {
-    volatile const DevClock *c = clk;
-    double dt = c->dt_cfl;
-    if (t_end - c->t < dt) dt = t_end - c->t;
-    return dt > 0.0 ? dt : 0.0;
-}
-
-// Before the coarse step: dh[e] = (dt_c / d) phi_c, the coarse flux through
-// the edge as U's update will use it (sign: + for V on U's high side).
 __global__ void reflux_coarse_kernel(RefluxParams p) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p.ncf) return;
-    const double dt = coming_dt(p.cclk, p.t_end);
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int e = warp * 8 + (lane >> 2);
+    const bool live = e < p.ncf;
+    if (!live) e = p.ncf - 1;   // idle lanes redo the last edge for the shuffles
+    const double dt = reflux::coming_dt(p.cclk, p.t_end);
     const int cur = p.cclk->cur;
     strip::View v;
     v.q0 = p.cq[cur][0]; v.q1 = p.cq[cur][1]; v.q2 = p.cq[cur][2]; v.hb = p.chb;
     v.nx = p.nxc; v.ny = p.nyc; v.bc = p.cbc;
     const int4 m = p.cf[e];
     const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1;
-    const int i = m.x % p.nxc, j = m.x / p.nxc;
-    const float f = cell_flux(v, i, j, axis, side, 0.5f * p.gc, (float)(dt / p.nxc_d),
-                              (float)(dt / p.nyc_d), p.orderc);
-    p.dh[e] = dt / (axis == 0 ? p.dxc : p.dyc) * (double)(side > 0 ? f : -f);
-}
-
-// Before each fine launch (after the ring fill): dh[e] -= (dt_f / d) (1 / r)
-// sum of the fine fluxes into the fine region across the edge.
-__global__ void reflux_fine_kernel(RefluxParams p) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= p.ncf) return;
-    const double dt = coming_dt(p.lclk, p.t_end);
-    if (!(dt > 0.0)) return;
-    const int cur = p.lclk->cur;
-    const int4 m = p.cf[e];
-    const PatchDevice &P = p.table[m.y];
-    strip::View v;
-    v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
-    v.nx = P.nx; v.ny = P.ny; v.bc = P.bc;
-    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1, stride = m.w >> 2;
-    const float nux = (float)(dt / p.dxf), nuy = (float)(dt / p.dyf);
-    double s = 0.0;
-    for (int k = 0; k < p.r; k++) {
-        const int c = m.z + k * stride;
-        // V on U's high side: the fine cells' low-edge flux; else minus the
-        // high-edge one
-        const float f = cell_flux(v, c % P.nx, c / P.nx, axis, -side, 0.5f * p.gf, nux, nuy,
-                                  p.orderf);
-        s += (double)(side > 0 ? f : -f);
-    }
-    p.dh[e] -= dt / (axis == 0 ? p.dxc : p.dyc) / (double)p.r * s;
-}
-
-// After the averaging: U's surface takes its edges' corrections.
-__global__ void reflux_apply_kernel(RefluxParams p) {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= p.ncfu) return;
-    const int4 g = p.cfu[u];
-    double s = 0.0;
-    for (int k = 0; k < g.z; k++) s += p.dh[g.y + k];
-    float *eta = p.cq[p.cclk->cur][0];
-    eta[g.x] = fp::add(eta[g.x], (float)s);
+    // U's high edge: stencil from one cell below U; its low edge: from two
+    const float f = reflux::group_flux(v, m.x % p.nxc, m.x / p.nxc, axis, side > 0 ? -1 : -2,
+                                       0.5f * p.g, (float)(dt / p.nxc_d), (float)(dt / p.nyc_d),
+                                       p.order);
+    if (live && (lane & 3) == 0)
+        for (int k = 0; k < p.r; k++) p.dhf[(size_t)e * p.r + k] = 0.0;
+    if (live && (lane & 3) == 1)
+        p.dh[e] = (dt > 0.0 ? dt : 0.0) / (axis == 0 ? p.dxc : p.dyc) * (double)(side > 0 ? f : -f);
 }
 
 // Geometry of one fine patch in global fine cells: array column 0 at
@@ -897,19 +939,20 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
 // Workspace layout: fill, avg, edge and edge-group maps (int4), then the
 // per-edge corrections (double), each on a 256-byte boundary.
 struct Layout {
-    size_t fill, avg, cf, cfu, dh, total;
+    size_t fill, avg, cf, cfu, dh, dhf, total;
 };
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-inline Layout layout_of(size_t nfill, size_t navg, size_t ncf, size_t ncfu) {
+inline Layout layout_of(size_t nfill, size_t navg, size_t ncf, size_t ncfu, int r) {
     Layout L;
     L.fill = 0;
     L.avg = L.fill + round256(sizeof(int4) * nfill);
     L.cf = L.avg + round256(sizeof(int4) * navg);
     L.cfu = L.cf + round256(sizeof(int4) * ncf);
     L.dh = L.cfu + round256(sizeof(int4) * ncfu);
-    L.total = L.dh + round256(sizeof(double) * ncf) + 256;
+    L.dhf = L.dh + round256(sizeof(double) * ncf);
+    L.total = L.dhf + round256(sizeof(double) * ncf * (size_t)r) + 256;
     return L;
 }
 
@@ -921,7 +964,7 @@ struct swa_amr {
     swa_patchset *fine = nullptr;
     int level = 0, r = 1;
     int4 *fill = nullptr, *avg = nullptr, *cf = nullptr, *cfu = nullptr;
-    double *dh = nullptr;
+    double *dh = nullptr, *dhf = nullptr;
     int nfill = 0, navg = 0, ncf = 0, ncfu = 0;
     int reflux = 1;
 };
@@ -934,7 +977,7 @@ size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine,
     if (!fine || grid_refs(coarse, &c) != SWA_OK) return 0;
     std::vector<int4> f, a, e, u;
     if (amr::build_maps(c, fine, level, ratio, f, a, e, u) != SWA_OK) return 0;
-    return amr::layout_of(f.size(), a.size(), e.size(), u.size()).total;
+    return amr::layout_of(f.size(), a.size(), e.size(), u.size(), ratio).total;
 }
 
 int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
@@ -945,7 +988,9 @@ int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, v
     if (((uintptr_t)ws & 255) != 0) return set_error(SWA_EINVAL, "workspace must be 256-byte aligned");
     std::vector<int4> f, a, e, u;
     TRY(amr::build_maps(c, fine, level, ratio, f, a, e, u));
-    const amr::Layout L = amr::layout_of(f.size(), a.size(), e.size(), u.size());
+    if ((long long)e.size() * ratio > 0x7fffffffLL)
+        return set_error(SWA_EINVAL, "too many coarse-fine edges for ratio %d", ratio);
+    const amr::Layout L = amr::layout_of(f.size(), a.size(), e.size(), u.size(), ratio);
     if (ws_bytes < L.total)
         return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, L.total);
     swa_amr *A = new (std::nothrow) swa_amr();
@@ -957,6 +1002,7 @@ int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, v
     A->cf = (int4 *)(base + L.cf);
     A->cfu = (int4 *)(base + L.cfu);
     A->dh = (double *)(base + L.dh);
+    A->dhf = (double *)(base + L.dhf);
     A->nfill = (int)f.size();
     A->navg = (int)a.size();
     A->ncf = (int)e.size();
@@ -1020,7 +1066,7 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     p.t_n = t_n; p.dt_c = dt_c; p.t_end = t_n + dt_c;
     p.err = swadj_host::error_word();
     amr::RefluxParams q{};
-    q.table = p.table; q.lclk = p.lclk; q.cclk = p.cclk;
+    q.cclk = c.clk;
     for (int b = 0; b < 2; b++)
         for (int k = 0; k < 3; k++) q.cq[b][k] = p.cq[b][k];
     q.chb = (const float *)c.bath;
@@ -1028,31 +1074,30 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     q.cbc = BcSpec{c.d.bc[0], c.d.bc[1], c.d.bc[2], c.d.bc[3]};
     q.dxc = c.d.dx; q.dyc = c.d.dy;
     q.nxc_d = (double)(float)c.d.dx; q.nyc_d = (double)(float)c.d.dy;
-    const patches::LevelParams lp = level_params(A->fine, A->level, t_n);
-    q.dxf = lp.dx; q.dyf = lp.dy;
-    q.gc = (float)c.d.g; q.gf = lp.g;
-    q.orderc = c.d.order; q.orderf = lp.order;
-    q.cf = A->cf; q.ncf = A->ncf; q.cfu = A->cfu; q.ncfu = A->ncfu; q.dh = A->dh;
-    const unsigned fb = ew_blocks((size_t)3 * (A->nfill > 0 ? A->nfill : 1));
-    const unsigned ab = ew_blocks((size_t)3 * (A->navg > 0 ? A->navg : 1));
-    const unsigned eb = (unsigned)((A->ncf + 127) / 128), ub = (unsigned)((A->ncfu + 127) / 128);
+    q.g = (float)c.d.g; q.order = c.d.order;
+    q.cf = A->cf; q.ncf = A->ncf; q.dh = A->dh; q.dhf = A->dhf;
+    q.t_end = p.t_end;
+    patches::LevelReflux rf{};
     if (reflux) {
-        q.t_end = p.t_end;
+        rf.cf = A->cf; rf.dhf = A->dhf; rf.nitems = A->ncf * A->r; rf.r = A->r;
+        rf.dxc = c.d.dx; rf.dyc = c.d.dy;
+        p.cfu = A->cfu; p.ncfu = A->ncfu; p.dh = A->dh; p.dhf = A->dhf;
+    }
+    const unsigned fb = ew_blocks((size_t)3 * (A->nfill > 0 ? A->nfill : 1));
+    const size_t navg_items = (size_t)3 * A->navg + (size_t)p.ncfu;
+    const unsigned ab = ew_blocks(navg_items > 0 ? navg_items : 1);
+    if (reflux) {
+        const unsigned eb = (unsigned)((A->ncf + 31) / 32);   // 8 edges per warp, 4 warps
         amr::reflux_coarse_kernel<<<eb, 128, 0, st>>>(q);
         TRY(cuda_check(cudaGetLastError(), "reflux_coarse_kernel"));
     }
     TRY(swa_step_forward(A->coarse, 1, p.t_end, stream));
     for (int k = 1; k <= A->r; k++) {
         const double t_k = k == A->r ? p.t_end : t_n + dt_c * (double)k / (double)A->r;
-        q.t_end = t_k;
         for (int j = 0; j < max_launches; j++) {
             amr::amr_fill_kernel<<<fb, 256, 0, st>>>(p);
             TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
-            if (reflux) {
-                amr::reflux_fine_kernel<<<eb, 128, 0, st>>>(q);
-                TRY(cuda_check(cudaGetLastError(), "reflux_fine_kernel"));
-            }
-            TRY(swa_step_level(A->fine, A->level, 1, t_k, stream));
+            TRY(level_launch(A->fine, A->level, 1, t_k, rf, st));
         }
     }
     switch (A->r) {
@@ -1063,10 +1108,6 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
         default: amr::amr_avg_kernel<0><<<ab, 256, 0, st>>>(p); break;
     }
     TRY(cuda_check(cudaGetLastError(), "amr_avg_kernel"));
-    if (reflux) {
-        amr::reflux_apply_kernel<<<ub, 128, 0, st>>>(q);
-        TRY(cuda_check(cudaGetLastError(), "reflux_apply_kernel"));
-    }
     return SWA_OK;
 }
 
