@@ -1,0 +1,253 @@
+"""Pins of the oracle's AMR glue over nested levels (oracle/amr_levels.py).
+
+- one level: the two-level glue of oracle/amr.py (itself pinned in
+  test_oracle_amr.py), bit for bit, with and without refluxing;
+- ratios 1 at every level: the single grid, whatever the nesting;
+- the ocean at rest stays exactly at rest on three levels;
+- with every level's bottom and surface the means of the level below, the
+  total mass is conserved between walls with refluxing (it drifts without;
+  a flipped correction fails);
+- a level-2 patch cut in two gives the patch;
+- a second level brings its region closer to a uniformly fine run than one
+  level; filling level 2 from the coarse grid instead of level 1, or
+  interpolating it in time against the coarse step instead of its parent's
+  substep (both planted), does not;
+- rings that leave the parent level's interiors are refused.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.amr import Hierarchy
+from oracle.amr_levels import RING, LevelHierarchy, Patch
+
+DX = 10e3
+H0 = 130.0
+
+
+def bottom(x, y):
+    return -100.0 - 20.0 * np.sin(x / 7e4) * np.cos(y / 9e4)
+
+
+def hump(x, y, L):
+    return 0.5 * np.exp(-((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2) / (3 * DX) ** 2)
+
+
+def centres(n, d):
+    x = (np.arange(n) + 0.5) * d
+    return np.meshgrid(x, x)
+
+
+def level_fields(nc, ratios, rest=False, mean=False):
+    """Global (B, eta) per level, sampled at each level's centres, or (mean)
+    the finest level's sampled and the others the means of the level below."""
+    L = nc * DX
+    out, n, d = [], nc, DX
+    for l in range(len(ratios) + 1):
+        if l > 0:
+            n, d = n * ratios[l - 1], d / ratios[l - 1]
+        X, Y = centres(n, d)
+        out.append([bottom(X, Y), np.zeros_like(X) if rest else hump(X, Y, L)])
+    if mean:
+        for l in range(len(ratios) - 1, -1, -1):
+            r = ratios[l]
+            m = out[l + 1][0].shape[0] // r
+            out[l] = [a.reshape(m, r, m, r).mean(axis=(1, 3)) for a in out[l + 1]]
+    return out
+
+
+def build(nc, levels, cls=LevelHierarchy, rest=False, seed=None, reflux=True, mean=False):
+    """levels: [(r, [Patch, ...]), ...], patches in the parent level's global
+    cells.  seed: uniform random momenta (all ratios 1)."""
+    cg = O.Grid(2, nc, nc, 0.0, 0.0, DX, DX, order=2, bc=(1, 1, 1, 1))
+    ratios = [lv[0] for lv in levels]
+    F = level_fields(nc, ratios, rest, mean)
+    U = None
+    if seed is not None:
+        assert all(r == 1 for r in ratios)
+        U = np.random.default_rng(seed).uniform(-5, 5, (nc, nc))
+    spec, fine = [], []
+    for l, (r, patches) in enumerate(levels, start=1):
+        BF, EF = F[l]
+        UF = np.zeros_like(BF) if U is None else U
+        Bf, states = [], []
+        for p in patches:
+            I0, J0 = p.i0 * r - RING, p.j0 * r - RING
+            ny, nx = p.my * r + 2 * RING, p.mx * r + 2 * RING
+            sl = lambda a: a[J0:J0 + ny, I0:I0 + nx].ravel().copy()
+            Bf.append(sl(BF))
+            states.append((sl(EF) - sl(BF), sl(UF), -sl(UF)))
+        spec.append((patches, r, Bf))
+        fine.append(states)
+    Bc, ec = F[0][0].ravel(), F[0][1].ravel()
+    uc = np.zeros(nc * nc) if U is None else U.ravel()
+    H = cls(cg, Bc, spec, reflux=reflux)
+    H.set_state(ec - Bc, uc, -uc, fine, 0.0)
+    return H, cg, Bc, ec, uc, F
+
+
+def dt_coarse(cg):
+    return 0.6 * cg.cfl * cg.dx / np.sqrt(9.81 * H0)
+
+
+# two levels nested around the hump at the centre of a 24^2 basin
+L1 = [Patch(6, 6, 12, 12)]
+L2 = [Patch(20, 20, 8, 8)]
+
+
+@pytest.mark.parametrize("reflux", [True, False])
+def test_one_level_is_the_two_level_glue(reflux):
+    patches = [Patch(6, 7, 5, 6), Patch(10, 9, 6, 5), Patch(15, 4, 3, 3), Patch(9, 12, 4, 4)]
+    H, cg, Bc, ec, uc, F = build(24, [(4, patches)], reflux=reflux)
+    fine = [(s[0], s[1], s[2]) for s in (list(map(np.copy, q)) for q in H.q[1])]
+    T = Hierarchy(cg, Bc, patches, 4, H.Bf[1], reflux=reflux)
+    T.set_state(H.h, H.hu, H.hv, fine, 0.0)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(6):
+        assert H.step(t, dt) and T.step(t, dt)
+        t = t + dt
+    for a, b in ((H.h, T.h), (H.hu, T.hu), (H.hv, T.hv)):
+        assert np.array_equal(a, b)
+    for k in range(len(patches)):
+        for a, b in zip(H.q[1][k], T.fine[k]):
+            assert np.array_equal(a, b)
+
+
+def test_ratios_one_are_the_single_grid():
+    levels = [(1, [Patch(4, 5, 14, 12), Patch(15, 3, 6, 8)]),
+              (1, [Patch(7, 8, 6, 5), Patch(11, 10, 5, 5), Patch(17, 5, 2, 4)])]
+    H, cg, Bc, ec, uc, _ = build(24, levels, seed=1)
+    h, hu, hv = ec - Bc, uc.copy(), -uc
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(8):
+        assert H.step(t, dt)
+        h, hu, hv = O.fwd_step(cg, h, hu, hv, Bc, (t + dt) - t)
+        t = t + dt
+    for a, b in ((H.h, h), (H.hu, hu), (H.hv, hv)):
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+    assert H.t == [t, t, t]
+
+
+@pytest.mark.parametrize("ratios", [(2, 2), (4, 2)])
+def test_ocean_at_rest_stays_at_rest(ratios):
+    r1, r2 = ratios
+    l2 = [Patch(8 * r1 // 2 + 2, 8 * r1 // 2 + 2, 4, 5)]
+    H, cg, Bc, *_ = build(16, [(r1, [Patch(4, 4, 8, 8)]), (r2, l2)], rest=True)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(3):
+        assert H.step(t, dt)
+        t = t + dt
+    assert np.all(H.h + Bc == 0.0) and np.all(H.hu == 0) and np.all(H.hv == 0)
+    for l in (1, 2):
+        for f, b in zip(H.q[l], H.Bf[l]):
+            assert np.all(f[0] + b == 0.0) and np.all(f[1] == 0) and np.all(f[2] == 0)
+
+
+def mass_drift(cls=LevelHierarchy, reflux=True, levels=None, steps=6):
+    levels = levels or [(2, L1), (2, L2)]
+    H, cg, *_ = build(24, levels, cls=cls, reflux=reflux, mean=True)
+    dt, t = dt_coarse(cg), 0.0
+    m0 = H.h.sum()
+    for _ in range(steps):
+        assert H.step(t, dt)
+        t = t + dt
+    return abs(H.h.sum() - m0) / m0
+
+
+class RefluxSign(LevelHierarchy):
+    """Planted mistake: the reflux correction applied with a flipped sign."""
+    reflux_sign = -1.0
+
+
+@pytest.mark.parametrize("levels", [
+    [(2, L1), (2, L2)],
+    [(2, [Patch(5, 6, 7, 12), Patch(12, 6, 6, 12)]), (3, [Patch(14, 16, 6, 8), Patch(20, 16, 5, 8)])],
+])
+def test_refluxing_conserves_mass_on_three_levels(levels):
+    """Walls all round, every level's bottom and surface the means of the
+    level below: the coarse grid's mass (its covered cells hold the level-1
+    means, whose covered cells hold the level-2 means) stays constant with
+    refluxing, drifts without, and drifts with a flipped correction."""
+    assert mass_drift(levels=levels) <= 1e-13
+    assert mass_drift(levels=levels, reflux=False) > 1e-8
+    assert mass_drift(cls=RefluxSign, levels=levels) > 1e-8
+
+
+def test_a_level_two_patch_cut_in_two_gives_the_patch():
+    one, cg, *_ = build(24, [(2, L1), (2, [Patch(20, 20, 8, 8)])])
+    two, *_ = build(24, [(2, L1), (2, [Patch(20, 20, 3, 8), Patch(23, 20, 5, 8)])])
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(4):
+        assert one.step(t, dt) and two.step(t, dt)
+        t = t + dt
+    scale = np.abs(one.h + one.B).max()
+    assert np.abs(one.h - two.h).max() <= 1e-12 * scale
+    for a, b in zip(one.q[1][0], two.q[1][0]):
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(a).max(), 1.0)
+    whole = one.q[2][0][0].reshape(20, 20)
+    left = two.q[2][0][0].reshape(20, 10)
+    right = two.q[2][1][0].reshape(20, 14)
+    assert np.abs(left[2:-2, 2:-2] - whole[2:-2, 2:8]).max() <= 1e-12 * 130.0
+    assert np.abs(right[2:-2, 2:-2] - whole[2:-2, 8:18]).max() <= 1e-12 * 130.0
+
+
+class FillFromCoarse(LevelHierarchy):
+    """Planted mistake: level 2 filled from the coarse grid (piecewise
+    constant, frozen in time) instead of its parent level."""
+    skip_level_in_fill = True
+
+
+class AlphaFromCoarse(LevelHierarchy):
+    """Planted mistake: level 2 interpolated in time against the coarse step
+    instead of the level-1 substep it runs in."""
+    alpha_from_coarse_step = True
+
+
+def region_error(levels, steps, cls=LevelHierarchy, region=(16, 32)):
+    """Max |eta - eta_fine| over a region of level-1 cells (global indices
+    region[0] .. region[1] - 1 in x and y) for the hierarchy with the given
+    levels, read from its level-1 patch (whose covered cells hold the level-2
+    means when there is a second level); eta_fine is a uniformly fine run at
+    the finest resolution of (2, 2) averaged to level-1 cells."""
+    nc, R = 24, 4
+    H, cg, *_ = build(nc, levels, cls=cls, reflux=False)
+    dt, t = dt_coarse(cg), 0.0
+    for _ in range(steps):
+        assert H.step(t, dt)
+        t = t + dt
+    F = level_fields(nc, [2, 2])
+    BF, EF = F[2]
+    fg = O.Grid(2, nc * R, nc * R, 0.0, 0.0, DX / R, DX / R, order=2, bc=(1, 1, 1, 1))
+    fh, fu, fv = (EF - BF).ravel(), 0 * EF.ravel(), 0 * EF.ravel()
+    for _ in range(steps * R):
+        fh, fu, fv = O.fwd_step(fg, fh, fu, fv, BF.ravel(), dt / R)
+    a, b = region
+    ref = (fh + BF.ravel()).reshape(nc * 2, 2, nc * 2, 2).mean(axis=(1, 3))[a:b, a:b]
+    p1 = levels[0][1][0]
+    g = H.G[1][0]
+    e1 = (H.q[1][0][0] + H.Bf[1][0]).reshape(g.ny, g.nx)
+    i0 = a - (p1.i0 * 2 - RING)
+    got = e1[i0:i0 + b - a, i0:i0 + b - a]
+    return np.abs(got - ref).max()
+
+
+# a level-2 patch holding the hump's first kilometres of travel (80 km)
+L2_WIDE = [Patch(16, 16, 16, 16)]
+
+
+@pytest.mark.parametrize("steps", [4, 8])
+def test_a_second_level_moves_its_region_towards_the_fine_solution(steps):
+    one = region_error([(2, L1)], steps)
+    two = region_error([(2, L1), (2, L2_WIDE)], steps)
+    planted = region_error([(2, L1), (2, L2_WIDE)], steps, cls=FillFromCoarse)
+    late = region_error([(2, L1), (2, L2_WIDE)], steps, cls=AlphaFromCoarse)
+    assert two < 0.5 * one, (two, one)          # measured 0.19 and 0.28
+    assert planted > 5.0 * two, (planted, two)  # measured 19x
+    assert late > 1.4 * two, (late, two)        # measured 1.73x
+
+
+def test_rings_outside_the_parent_level_are_refused():
+    with pytest.raises(ValueError):
+        build(24, [(2, L1), (2, [Patch(12, 20, 6, 6)])])   # ring at level-1 cell 11
+    with pytest.raises(ValueError):
+        build(24, [(2, [Patch(0, 6, 6, 6)])])              # ring outside the domain
