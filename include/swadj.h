@@ -379,93 +379,120 @@ int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches,
  * Results do not depend on it; throughput does (the autotuner picks it). */
 int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
 
-/* ========================= two-level AMR glue =============================
- * One coarse grid (FP32, 2D) and one level of fine patches of a patch set,
- * refined by an integer ratio r in space and in time: the AMR hierarchy the
- * paper's runs use (Sec. 1, Sec. 6), one coarse level deep.
+/* ============================== AMR glue ===================================
+ * One coarse grid (FP32, 2D) and L nested levels of fine patches of a patch
+ * set, level l refined from level l - 1 by an integer ratio r_l in space and
+ * in time: the AMR hierarchy the paper's runs use (Sec. 1, Sec. 6; four
+ * levels in its Crescent City run).
  *
- * Fine patches carry a 2-cell ring: a patch whose interior is mx x my
- * coarse cells with lower-left coarse cell (i0, j0) is described with
- * nx = mx r + 4, ny = my r + 4, dx = coarse dx / r, dy = coarse dy / r,
- * x_lo = coarse x_lo + i0 dx_coarse - 2 dx, y_lo likewise, and its ring must
- * lie inside the coarse domain.  The level step updates ring cells like any
+ * Patches carry a 2-cell ring: a level-l patch whose interior is mx x my
+ * level-(l - 1) cells with lower-left level-(l - 1) cell (i0, j0) (counted on
+ * the uniform level-(l - 1) grid over the whole domain) is described with
+ * nx = mx r_l + 4, ny = my r_l + 4, dx = dx_(l - 1) / r_l, dy likewise,
+ * x_lo = coarse x_lo + i0 dx_(l - 1) - 2 dx, y_lo likewise.  Level-1 rings
+ * must lie inside the coarse domain; every cell of a level-l patch (ring
+ * included) must lie inside the interior of some level-(l - 1) patch for
+ * l >= 2 (proper nesting).  The level step updates ring cells like any
  * other (they enter the level's CFL maximum); the fill before each launch
  * overwrites them.  The patch set's boundary conditions act only beyond the
- * ring, on ring cells: create it with SWA_BC_EXTRAP, the rule the
- * hierarchy is defined with.  Set the fine patches' states (ring included)
- * and start the level at the coarse grid's time before the first step.
+ * ring, on ring cells: create it with SWA_BC_EXTRAP, the rule the hierarchy
+ * is defined with.  Set every patch's state (ring included) and start every
+ * level at the coarse grid's time before the first step.
  *
- * swa_amr_step(amr, t_n, dt_c, m, stream), all stream-ordered, no host sync:
+ * swa_amr_step(amr, t_n, dt_c, m, stream), all stream-ordered, no host sync
+ * (Berger-Oliger subcycling):
  *   1. the coarse grid steps to t_n + dt_c (dt_c must not exceed its CFL
  *      step, so that it takes exactly one);
- *   2. the fine level takes r substeps, the k-th ending at
- *      t_n + dt_c k / r, with m launches each (launches past the substep's
- *      end are no-ops).  Before every launch each ring cell is filled: from
- *      the lowest-index other patch of the level whose interior holds it,
- *      else from the coarse level, linearly in time between the coarse
- *      states at t_n and t_n + dt_c (alpha = (t - t_n) / dt_c in [0, 1],
- *      eta and both momenta), then piecewise linearly in space within the
- *      coarse cell holding it, with minmod slopes (zero at the domain edge);
- *   3. every coarse cell under a patch interior (lowest patch index) takes
- *      the mean of its r x r fine cells (eta and both momenta);
- *   4. refluxing (on unless swa_amr_set_reflux turned it off): every
- *      uncovered coarse cell U beside a covered cell V takes, for each such
- *      edge, the mass its own update moved through the edge minus the mass
- *      the fine level moved through it over the r substeps (the fine cells
- *      of V's lowest-index patch along the edge, weighted 1 / r):
- *        eta_U += dt_c / d phi_c - sum_launches dt_f / (d r) sum_fine phi_f
+ *   2. run(1) over the coarse step, where run(l) over a parent step [t_p,
+ *      t_p + dt_p] takes r_l substeps, the k-th ending at t_p + dt_p k /
+ *      r_l, with one launch each for a level with children (its CFL step
+ *      must cover the substep) and m launches each for the finest level
+ *      (launches past the substep's end are no-ops).  Before every launch
+ *      each ring cell is filled: from the lowest-index other patch of its
+ *      level whose interior holds it, else from its parent (the coarse grid
+ *      at level 1, else the lowest-index level-(l - 1) patch whose interior
+ *      holds it), linearly in time between the parent's states at t_p and
+ *      t_p + dt_p (alpha = (t - t_p) / dt_p in [0, 1], eta and both
+ *      momenta), then piecewise linearly in space within the parent cell
+ *      holding it, with minmod slopes from the parent's array (zero where a
+ *      neighbour lies outside it: the domain edge of the coarse grid).
+ *      After each substep of a level with children: run(l + 1) over it, then
+ *      steps 3 and 4 for level l + 1;
+ *   3. every copy of a level-(l - 1) cell under a level-l interior (the
+ *      coarse cell, or its cell in each level-(l - 1) patch whose interior
+ *      holds it) takes the mean of the r_l x r_l cells of the lowest-index
+ *      level-l patch over it (eta and both momenta);
+ *   4. refluxing (on unless swa_amr_set_reflux turned it off): every copy of
+ *      an uncovered level-(l - 1) cell U beside a covered cell V takes, for
+ *      each such edge, the mass its own updates moved through the edge minus
+ *      the mass level l moved through it over the parent step (the cells of
+ *      V's lowest-index level-l patch along the edge, weighted 1 / r_l):
+ *        eta_U += sum dt_p / d phi_U - sum_launches dt_l / (d r_l) sum phi_l
  *      with phi the mass flux of the split step's update (x-edges from the
  *      state, y-edges from the x-swept state; the normal momentum of the
  *      cell below the edge plus the net the update gives it), signed into
- *      V, and d the coarse cell width across the edge.  The fluxes are recomputed before
- *      each launch by the step's own edge arithmetic, summed in FP64 per
- *      edge and added to eta_U in FP32 after step 3.  With coarse bottoms
- *      the means of the fine bottoms under them, the hierarchy then keeps
- *      the mass of its cells (coarse uncovered plus coarse covered) to
- *      rounding, as conservative refinement requires (Sec. 6 runs GeoClaw's
- *      conservative AMR).  Only the mass is corrected.
- * If either level ends the step short of t_n + dt_c (the coarse CFL step
- * was below dt_c, or m launches did not reach a substep's end), the next
- * swa_sync_status returns SWA_ESTATE.
+ *      V, and d the level-(l - 1) cell width across the edge.  The fluxes
+ *      are recomputed before each launch by the step's own edge arithmetic,
+ *      summed in FP64 per edge and added to eta_U in FP32 after step 3.
+ *      With every level's bottoms the means of the bottoms under them, the
+ *      hierarchy then keeps its mass (the coarse grid's, whose covered cells
+ *      hold the means of the levels below) to rounding, as conservative
+ *      refinement requires (Sec. 6 runs GeoClaw's conservative AMR).  Only
+ *      the mass is corrected.
+ * If a level starts the step away from t_n or ends a parent step short of
+ * its end (a CFL step below its substep, or m launches that did not reach a
+ * substep's end), the next swa_sync_status returns SWA_ESTATE.
  */
 typedef struct swa_amr swa_amr;
-/* Device workspace for the maps and the refluxing corrections (16 bytes per
- * ring cell and per covered coarse cell, 24 + 8 r per coarse-fine edge, 16
- * per uncovered coarse cell beside the fine level, plus padding); 0 if the
- * geometry is invalid (the reason is in swa_last_error). */
+/* Device workspace for the maps and the refluxing slots (per level: 20
+ * bytes per ring cell, 16 per covered parent cell, 20 + 8 (1 + r) per
+ * coarse-fine edge, 16 per uncovered parent cell beside the level, plus
+ * padding); 0 if the geometry is invalid (the reason is in swa_last_error).
+ * levels[l - 1]: the patch-set level of hierarchy level l (1 .. nlevels);
+ * ratios[l - 1]: r_l in [1, 64]. */
+size_t swa_amr_levels_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine,
+                                      int nlevels, const int *levels, const int *ratios);
+/*
+ * coarse: a 2D FP32 grid; fine: a patch set whose patches of the listed
+ * levels form the hierarchy (other levels are ignored); nlevels in
+ * [1, SWA_MAX_LEVELS], no patch-set level listed twice.  ws: device buffer
+ * of at least swa_amr_levels_workspace_bytes, 256-byte aligned, owned by
+ * the caller for the hierarchy's lifetime; coarse and fine must outlive it
+ * too.  Checks the geometry (SWA_EINVAL: level without patches, cell size
+ * not the parent's / r, interior not on whole parent cells, ring outside the
+ * domain, a patch not nested in its parent level, a patch set without
+ * SWA_BC_EXTRAP), uploads the maps and clears the slots on `stream`, and
+ * synchronises it.  SWA_ENOMEM if ws_bytes is too small.
+ */
+int swa_create_amr_levels(swa_grid *coarse, swa_patchset *fine, int nlevels, const int *levels,
+                          const int *ratios, void *ws, size_t ws_bytes, void *stream,
+                          swa_amr **out);
+/* The two-level hierarchy: swa_amr_levels_workspace_bytes and
+ * swa_create_amr_levels with nlevels = 1, levels = {level}, ratios =
+ * {ratio}. */
 size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
                                int ratio);
-/*
- * coarse: a 2D FP32 grid; fine: a patch set whose patches of `level` are
- * the fine level (other levels are ignored); ratio: r in [1, 64].  ws: device
- * buffer of at least swa_amr_workspace_bytes, 256-byte aligned, owned by the
- * caller for the hierarchy's lifetime; coarse and fine must outlive it too.
- * Checks the geometry (SWA_EINVAL: level without patches, cell size not
- * coarse / r, interior not on whole coarse cells, ring outside the domain),
- * uploads the maps on `stream` and synchronises it.  SWA_ENOMEM if ws_bytes
- * is too small.
- */
 int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
                    size_t ws_bytes, void *stream, swa_amr **out);
 /* Host bookkeeping only; the workspace stays the caller's. */
 int swa_destroy_amr(swa_amr *amr);
 /*
- * One coarse step of dt_c from t_n (the coarse grid's current time) with
- * ratio substeps of the fine level, max_launches launches each, enqueued on
- * `stream`.  SWA_EINVAL: null hierarchy, dt_c <= 0, max_launches < 1;
- * SWA_ESTATE: coarse state not set or fine level not started; SWA_ECUDA: a
- * launch failed.  A level falling short of t_n + dt_c shows up as
- * SWA_ESTATE at the next swa_sync_status.
+ * One coarse step of dt_c from t_n (the time every level must be at) with
+ * the subcycled levels below it, max_launches launches per substep of the
+ * finest level, enqueued on `stream`.  SWA_EINVAL: null hierarchy, dt_c <=
+ * 0, max_launches < 1, refluxing on with the coarse grid on the unsplit
+ * scheme (the recomputed fluxes are the split step's); SWA_ESTATE: coarse
+ * state not set or a level not started; SWA_ECUDA: a launch failed.  Levels
+ * off their times show up as SWA_ESTATE at the next swa_sync_status.
  */
 int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *stream);
 /* Refluxing (step 4 above) on (on != 0, the default) or off.  Host state
- * only; takes effect at the next swa_amr_step.  A step with refluxing on
- * returns SWA_EINVAL if the coarse grid uses the unsplit scheme (the
- * recomputed fluxes are the split step's). */
+ * only; takes effect at the next swa_amr_step. */
 int swa_amr_set_reflux(swa_amr *amr, int on);
-/* Sizes of the maps: ring cells filled per launch, covered coarse cells
- * averaged, coarse-fine edges refluxed (any pointer may be null). */
-int swa_amr_info(const swa_amr *amr, int *nfill, int *navg, int *nedges);
+/* Sizes of hierarchy level `level`'s maps (1 .. nlevels): ring cells filled
+ * per launch, covered parent cell copies averaged, coarse-fine edges
+ * refluxed (any pointer may be null). */
+int swa_amr_info(const swa_amr *amr, int level, int *nfill, int *navg, int *nedges);
 
 /*
  * FP64 audit of the conserved mass of the grid's current state: writes

@@ -30,7 +30,8 @@ One coarse step of dt_c from t_n (Berger-Oliger subcycling):
   that patch's cell (lowest patch index wins).  Otherwise it interpolates its
   parent: the level-(l - 1) cell P holding it, in the lowest-index patch
   whose interior holds P (or the coarse grid at l = 1).  First linearly in
-  time between the parent's states at the start and end of its step (eta
+  time between the parent's states at the start and end of its step (the
+  state its step read, rings as filled for it, and the state it wrote; eta
   and both momenta, alpha = (t - t_p) / dt_p clamped to [0, 1]); then
   within P, q = q_P + s_x xi + s_y zeta with xi, zeta in (-1/2, 1/2) the
   fine centre's offset from P's centre in parent cells and minmod slopes
@@ -373,7 +374,7 @@ class LevelHierarchy:
         for k in range(1, r + 1):
             t_k = t_end if k == r else t_p + dt_p * k / r
             t_km1 = t_p if k == 1 else t_p + dt_p * (k - 1) / r
-            old_l = self.snapshot(l)
+            old_l = None
             dh_c = np.zeros(len(self.edges[l + 1])) if l < self.L else None
             for _ in range(launches):
                 dt = self.G[l][0].cfl / self.level_smax(l)
@@ -383,6 +384,10 @@ class LevelHierarchy:
                     self.fill(l, old_parent, *self._coarse_step)
                 else:
                     self.fill(l, old_parent, t_p, dt_p)
+                if old_l is None:
+                    # the state this level's step reads, rings as filled
+                    # for it: its children's start state
+                    old_l = self.snapshot(l)
                 if dt > 0.0:
                     phis = []
                     for q, g in enumerate(self.G[l]):

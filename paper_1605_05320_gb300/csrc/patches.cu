@@ -119,15 +119,29 @@ __device__ __forceinline__ double coming_dt(const DevClock *clk, double t_end) {
 
 }  // namespace reflux
 
-// Refluxing work of a level launch inside the AMR glue: per coarse-fine
-// edge e and fine cell k along it (item e r + k), dhf[item] -= (dt_f / d)
-// (1 / r) F_f, the flux into the fine region across the edge over this
-// launch.  nitems = 0: none.
+// Refluxing work of a level launch inside the AMR glue.  An edge e of
+// level l joins a copy of an uncovered level-(l - 1) cell U to a cell V
+// under a level-l patch interior: cf[e] = (U's patch or -1 for the coarse
+// grid, U's cell, V's owner patch, its first cell along the edge), cfw[e] =
+// axis | hi << 1 | stride << 2 (hi: V on U's high side; stride: from one of
+// the r cells along the edge to the next), and 1 + r FP64 slots: the coarse
+// part (level l - 1's own fluxes) then one fine part per cell along it.
+//   fine parts (this level as the child, its own edges): slot[e (1 + r) + 1
+//     + k] -= (dt / d) (1 / r) F_k, d the parent's cell width;
+//   coarse parts (this level as the parent, the next level's edges):
+//     slot2[e (1 + r2)] += (dt / d) F_U, d this level's cell width;
+// with F signed into V.  nfine = ncoarse = 0: none.
 struct LevelReflux {
-    const int4 *cf;   // edges (U, patch, first fine cell, axis | hi << 1 | stride << 2)
-    double *dhf;
-    int nitems, r;
-    double dxc, dyc;  // coarse cell size
+    const int4 *cf;
+    const int *cfw;
+    double *slot;
+    int nfine, r;           // items: edges x r
+    double dpx, dpy;        // parent cell size
+    const int4 *cf2;
+    const int *cfw2;
+    double *slot2;
+    int ncoarse, r2;        // items: the next level's edges
+    double dtx, dty;        // this level's cell size
 };
 
 struct LevelParams {
@@ -144,28 +158,41 @@ struct LevelParams {
     LevelReflux rf;
 };
 
-// One task of a level launch's refluxing work: 8 items, 4 lanes each.
+// One task of a level launch's refluxing work: 8 items, 4 lanes each;
+// tasks below ceil(nfine / 8) are fine parts, the rest coarse parts.
 __device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, int cur,
                                                float nux, float nuy, double dt) {
+    const LevelReflux &R = p.rf;
     const int lane = threadIdx.x & 31;
-    int item = task * 8 + (lane >> 2);
-    const bool live = item < p.rf.nitems;
-    if (!live) item = p.rf.nitems - 1;   // idle lanes redo the last item for the shuffles
-    const int e = item / p.rf.r, k = item - e * p.rf.r;
-    const int4 m = p.rf.cf[e];
-    const PatchDevice &P = p.table[m.y];
+    const int tf = (R.nfine + 7) / 8;
+    const bool fine = task < tf;
+    const int n = fine ? R.nfine : R.ncoarse;
+    int item = (fine ? task : task - tf) * 8 + (lane >> 2);
+    const bool live = item < n;
+    if (!live) item = n - 1;   // idle lanes redo the last item for the shuffles
+    const int e = fine ? item / R.r : item;
+    const int4 m = fine ? R.cf[e] : R.cf2[e];
+    const int w = fine ? R.cfw[e] : R.cfw2[e];
+    const int axis = w & 1, side = (w & 2) ? 1 : -1, stride = w >> 2;
+    // fine: a cell of V's patch along the edge, its low edge when V is on
+    // U's high side (stencil from two cells below it), else its high edge;
+    // coarse: U in its patch, its high edge when V is on its high side
+    const int pid = fine ? m.z : m.x;
+    const int c = fine ? m.w + (item - e * R.r) * stride : m.y;
+    const int k0 = fine ? (side > 0 ? -2 : -1) : (side > 0 ? -1 : -2);
+    const PatchDevice &P = p.table[pid];
     strip::View v;
     v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
     v.nx = P.nx; v.ny = P.ny; v.bc = P.bc;
-    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1, stride = m.w >> 2;
-    const int c = m.z + k * stride;
-    // V on U's high side: the fine cell's low edge (stencil from two cells
-    // below it); else its high edge (from one below)
-    const float f = reflux::group_flux(v, c % P.nx, c / P.nx, axis, side > 0 ? -2 : -1,
-                                       0.5f * p.g, nux, nuy, p.order);
-    if (live && (lane & 3) == 1)
-        p.rf.dhf[item] -= dt / (axis == 0 ? p.rf.dxc : p.rf.dyc) / (double)p.rf.r *
-                          (double)(side > 0 ? f : -f);
+    const float f =
+        reflux::group_flux(v, c % P.nx, c / P.nx, axis, k0, 0.5f * p.g, nux, nuy, p.order);
+    if (!live || (lane & 3) != 1) return;
+    const double fs = (double)(side > 0 ? f : -f);
+    if (fine)
+        R.slot[(size_t)e * (1 + R.r) + 1 + (item - e * R.r)] -=
+            dt / (axis == 0 ? R.dpx : R.dpy) / (double)R.r * fs;
+    else
+        R.slot2[(size_t)e * (1 + R.r2)] += dt / (axis == 0 ? R.dtx : R.dty) * fs;
 }
 
 __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelParams p) {
@@ -191,11 +218,12 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
         strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
                           ring[threadIdx.x >> 5], smax, bad);
     }
-    if (p.rf.nitems > 0) {
+    if (p.rf.nfine + p.rf.ncoarse > 0) {
         // the warps with one strip fewer start on the refluxing tasks; the
         // clock is not advanced before every block has finished them
         const int total = gridDim.x * wpb, gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-        const int ntasks = (p.rf.nitems + 7) / 8, rem = p.nunits % total;
+        const int ntasks = (p.rf.nfine + 7) / 8 + (p.rf.ncoarse + 7) / 8;
+        const int rem = p.nunits % total;
         const double dt_now = reflux::coming_dt(p.clk, p.t_end);
         for (int t = (gw + total - rem) % total; t < ntasks; t += total)
             level_reflux_task(p, t, cur, s_nu[0], s_nu[1], dt_now);
@@ -618,19 +646,29 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows) {
 
 }  // extern "C"
 
-// ======================================================= two-level AMR glue
+// ================================================================ AMR glue
 //
-// One coarse grid (FP32, 2D) and one level of fine patches refined by an
-// integer ratio r in space and time (the AMR hierarchy of Sec. 1, Sec. 6).
-// Each fine patch carries a 2-cell ring as ordinary cells; the level step
-// updates the ring like any cell (it enters only the level's CFL maximum)
-// and the fill before the next launch overwrites it.  The maps below are
-// built on the host at creation from the patch geometry:
-//   fill: per ring cell (patch, cell, source).  Source: the lowest-index
-//         other patch whose interior holds the cell (patch, cell), else the
-//         coarse cell containing it and the fine cell's position inside it.
-//   avg:  per coarse cell under a patch interior (lowest patch index): the
-//         patch and the index of its first fine cell.
+// A coarse grid (FP32, 2D) and L nested levels of ringed patches of one
+// patch set, level l refined from level l - 1 by an integer ratio r_l in
+// space and in time (the hierarchy of Sec. 1 and Sec. 6).  Level l's cells
+// are numbered on a virtual uniform grid over the domain ("global" level-l
+// cells, P_l = r_1 ... r_l per coarse cell).  Each patch carries a 2-cell
+// ring as ordinary cells; the level step updates the ring like any cell (it
+// enters only the level's CFL maximum) and the fill before the next launch
+// overwrites it.  Maps built on the host at creation, per level l:
+//   fill:  per ring cell of a level-l patch (patch, cell, src, idx): src >=
+//          0 the lowest-index other level-l patch whose interior holds the
+//          cell and idx its cell there; else idx the parent cell holding it
+//          (in the coarse grid at l = 1, else in the lowest-index level-(l -
+//          1) patch whose interior holds it: fill_par) and -src - 1 = sx + r
+//          sy the ring cell's position inside it.
+//   avg:   per copy of a level-(l - 1) cell under a level-l interior (the
+//          coarse cell, or the cell in each level-(l - 1) patch whose
+//          interior holds it): (parent patch or -1, its cell, the
+//          lowest-index level-l patch over it, that patch's first cell).
+//   edges: the refluxing edges of level l (LevelReflux) and, per copy of an
+//          uncovered level-(l - 1) cell with edges, the group (U's patch or
+//          -1, U's cell, first edge, edges).
 namespace swadj {
 namespace amr {
 
@@ -639,49 +677,45 @@ constexpr int kRing = 2;
 using patches::PatchDevice;
 using patches::ew_blocks;
 
-struct AmrParams {
-    const PatchDevice *table;
-    const DevClock *lclk, *cclk;   // fine level, coarse grid
-    float *cq[2][3];               // coarse state buffers (eta, hu, hv)
-    int nxc, nyc, r;
-    const int4 *fill;
-    int nfill;
-    const int4 *avg;
-    int navg;
-    const int4 *cfu;   // refluxing: (U, first edge, edges, 0); ncfu = 0: none
-    int ncfu;
-    const double *dh, *dhf;
-    double t_n, dt_c, t_end;
-    int *err;
-};
-
 __device__ __forceinline__ float minmod(float a, float b) {
     if (a * b <= 0.f) return 0.f;
     return fabsf(a) < fabsf(b) ? a : b;
 }
 
-// Ring fill at the fine level's current time: sibling copy, or the coarse
-// level linear in time (alpha = (t - t_n) / dt_c in [0, 1]) then limited
-// linear in space within the coarse cell (minmod slopes, zero at the domain
-// edge).  Map entry (patch, cell, src, idx): src >= 0 is a sibling patch
-// and idx its cell; src < 0 is the coarse cell idx, with the fine cell at
-// (-src - 1) = sx + r sy inside it.  One thread per (entry, component);
-// the clocks and alpha (FP64) are read and formed once per block.
-__global__ void amr_fill_kernel(AmrParams p) {
+struct FillParams {
+    const PatchDevice *table;
+    const DevClock *lclk;   // this level
+    const DevClock *pclk;   // its parent: the coarse grid's clock at l = 1
+    float *cq[2][3];        // the coarse grid's buffers (eta, hu, hv)
+    int nxc, nyc, r;
+    const int4 *fill;
+    const int *par;         // parent patch per entry (-1: the coarse grid)
+    int nfill;
+    double t_p, dt_p;       // the parent's step
+};
+
+// Ring fill at the level's current time: sibling copy, or the parent linear
+// in time between its buffers before and after its step (alpha = (t - t_p) /
+// dt_p in [0, 1]) then limited linear in space within the parent cell
+// (minmod slopes from the parent's array, zero where a neighbour lies
+// outside it: the domain edge of the coarse grid).  One thread per (entry,
+// component); the clocks and alpha (FP64) are read and formed once per
+// block.
+__global__ void amr_fill_kernel(FillParams p) {
     __shared__ float s_a;
-    __shared__ int s_fcur, s_ccur;
+    __shared__ int s_fcur, s_pcur;
     if (threadIdx.x == 0) {
-        volatile const DevClock *lc = p.lclk, *cc = p.cclk;
-        double a = (lc->t - p.t_n) / p.dt_c;
+        volatile const DevClock *lc = p.lclk, *pc = p.pclk;
+        double a = (lc->t - p.t_p) / p.dt_p;
         a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
         s_a = (float)a;
         s_fcur = lc->cur;
-        s_ccur = cc->cur;
+        s_pcur = pc->cur;
     }
     __syncthreads();
     const float af = s_a;
-    const int fcur = s_fcur, ccur = s_ccur;
-    const int r = p.r, nxc = p.nxc, nyc = p.nyc;
+    const int fcur = s_fcur, pcur = s_pcur;
+    const int r = p.r;
     const int n = 3 * p.nfill;
     for (int e3 = blockIdx.x * blockDim.x + threadIdx.x; e3 < n; e3 += gridDim.x * blockDim.x) {
         const int e = e3 / 3, k = e3 - 3 * e;
@@ -692,15 +726,23 @@ __global__ void amr_fill_kernel(AmrParams p) {
             continue;
         }
         const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
-        const int c = m.w, ic = c % nxc, jc = c / nxc;
+        const int par = __ldg(p.par + e);
+        const float *o, *nw;
+        int nx, ny;
+        if (par < 0) {
+            o = p.cq[pcur ^ 1][k]; nw = p.cq[pcur][k]; nx = p.nxc; ny = p.nyc;
+        } else {
+            const PatchDevice &Q = p.table[par];
+            o = Q.q[pcur ^ 1][k]; nw = Q.q[pcur][k]; nx = Q.nx; ny = Q.ny;
+        }
+        const int c = m.w, ic = c % nx, jc = c / nx;
         const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
         const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
-        const float *o = p.cq[ccur ^ 1][k], *nw = p.cq[ccur][k];
         auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
         const float qc = at(c);
         float s_x = 0.f, s_y = 0.f;
-        if (ic > 0 && ic < nxc - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
-        if (jc > 0 && jc < nyc - 1) s_y = minmod(qc - at(c - nxc), at(c + nxc) - qc);
+        if (ic > 0 && ic < nx - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
+        if (jc > 0 && jc < ny - 1) s_y = minmod(qc - at(c - nx), at(c + nx) - qc);
         dst[m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
     }
 }
@@ -722,23 +764,36 @@ __device__ __forceinline__ float block_sum(const float *f, int nx, int r) {
     return s;
 }
 
-// Coarse cells under a patch := mean of their r x r fine cells (eta, hu, hv).
-// Entry (coarse cell, patch, first fine cell, 0); one thread per (entry,
-// component).  Then, one thread per uncovered coarse cell U beside the fine
-// level (refluxing): eta_U += the FP64 sum of its edges' corrections, coarse
-// part plus fine parts, in a fixed order (U is never a covered cell, so the
-// two parts write different cells).  Also checks that both levels reached
-// the step's end time.
+struct AvgParams {
+    const PatchDevice *table;
+    const DevClock *lclk, *pclk;   // this level, its parent
+    float *cq[2][3];               // the coarse grid's buffers
+    int r;
+    const int4 *avg;
+    int navg;
+    const int4 *cfu;               // refluxing groups (ncfu = 0: none)
+    int ncfu;
+    double *slot;                  // 1 + r per edge
+    double t_end;                  // the parent's step end
+    int *err;
+};
+
+// Every copy of a parent cell under the level := mean of its r x r cells
+// (eta, hu, hv); one thread per (entry, component).  Then, one thread per
+// group (refluxing of the parent level): eta_U += the FP64 sum of its
+// edges' slots (coarse part, then the fine parts, edge by edge), and the
+// slots return to zero.  U is never under the level, so the two parts write
+// different cells.  Also checks that both levels reached the step's end.
 template <int R>
-__global__ void amr_avg_kernel(AmrParams p) {
-    volatile const DevClock *lc = p.lclk, *cc = p.cclk;
-    __shared__ int s_fcur, s_ccur;
+__global__ void amr_avg_kernel(AvgParams p) {
+    volatile const DevClock *lc = p.lclk, *pc = p.pclk;
+    __shared__ int s_fcur, s_pcur;
     if (threadIdx.x == 0) {
         s_fcur = lc->cur;
-        s_ccur = cc->cur;
+        s_pcur = pc->cur;
     }
     __syncthreads();
-    const int fcur = s_fcur, ccur = s_ccur;
+    const int fcur = s_fcur, pcur = s_pcur;
     const int r = R > 0 ? R : p.r;
     const float inv = 1.f / (float)(r * r);
     const int n3 = 3 * p.navg, n = n3 + p.ncfu;
@@ -746,48 +801,63 @@ __global__ void amr_avg_kernel(AmrParams p) {
         if (e3 >= n3) {
             const int4 g = __ldg(p.cfu + (e3 - n3));
             double s = 0.0;
-            for (int e = g.y; e < g.y + g.z; e++) {
-                double f = p.dh[e];
-                for (int k = 0; k < r; k++) f += p.dhf[(size_t)e * r + k];
+            for (int e = g.z; e < g.z + g.w; e++) {
+                double *sl = p.slot + (size_t)e * (1 + r);
+                double f = sl[0];
+                for (int k = 1; k <= r; k++) f += sl[k];
+                for (int k = 0; k <= r; k++) sl[k] = 0.0;
                 s += f;
             }
-            float *eta = p.cq[ccur][0];
-            eta[g.x] = fp::add(eta[g.x], (float)s);
+            float *eta = g.x < 0 ? p.cq[pcur][0] : p.table[g.x].q[pcur][0];
+            eta[g.y] = fp::add(eta[g.y], (float)s);
             continue;
         }
         const int e = e3 / 3, k = e3 - 3 * e;
         const int4 m = __ldg(p.avg + e);
-        const PatchDevice &S = p.table[m.y];
-        p.cq[ccur][k][m.x] = block_sum<R>(S.q[fcur][k] + m.z, S.nx, r) * inv;
+        const PatchDevice &S = p.table[m.z];
+        float *dst = m.x < 0 ? p.cq[pcur][k] : p.table[m.x].q[pcur][k];
+        dst[m.y] = block_sum<R>(S.q[fcur][k] + m.w, S.nx, r) * inv;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double tol = 1e-12 * (fabs(p.t_end) > 1.0 ? fabs(p.t_end) : 1.0);
-        if (!(fabs(lc->t - p.t_end) <= tol) || !(fabs(cc->t - p.t_end) <= tol))
+        if (!(fabs(lc->t - p.t_end) <= tol) || !(fabs(pc->t - p.t_end) <= tol))
             atomicOr(p.err, ERR_LAG);
     }
 }
 
-// Before the coarse step, per edge: dh[e] = (dt_c / d) F_c, the coarse
-// flux through the edge as U's update will use it (sign: + for V on U's
-// high side), and the edge's fine parts start at zero.  A group of 4 lanes
-// per edge, 8 edges per warp.
-struct RefluxParams {
+// Before the coarse step: checks that every level starts at t_n, then per
+// level-1 edge the coarse part, slot[e (1 + r)] += (dt_c / d) F_U, the
+// coarse flux through the edge as U's update will use it (signed into V).
+// A group of 4 lanes per edge, 8 edges per warp.
+struct CoarseReflux {
     const DevClock *cclk;
     const float *cq[2][3];
     const float *chb;
-    int nxc, nyc, r;
+    int nxc, nyc;
     BcSpec cbc;
     double dxc, dyc;      // coarse cell size (the correction's scale)
     double nxc_d, nyc_d;  // the coarse step's nu divisors (its FP32 cell size)
     float g;
     int order;
     const int4 *cf;
-    int ncf;
-    double *dh, *dhf;
-    double t_end;
+    const int *cfw;
+    double *slot;
+    int ncf, r;
+    double t_n, t_end;
+    const DevClock *lclk[SWA_MAX_LEVELS];
+    int nlev;
+    int *err;
 };
 
-__global__ void reflux_coarse_kernel(RefluxParams p) {
+__global__ void reflux_coarse_kernel(CoarseReflux p) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const double tol = 1e-12 * (fabs(p.t_n) > 1.0 ? fabs(p.t_n) : 1.0);
+        bool ok = fabs(((volatile const DevClock *)p.cclk)->t - p.t_n) <= tol;
+        for (int l = 0; l < p.nlev; l++)
+            ok = ok && fabs(((volatile const DevClock *)p.lclk[l])->t - p.t_n) <= tol;
+        if (!ok) atomicOr(p.err, ERR_LAG);
+    }
+    if (p.ncf == 0) return;
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int e = warp * 8 + (lane >> 2);
@@ -799,228 +869,423 @@ __global__ void reflux_coarse_kernel(RefluxParams p) {
     v.q0 = p.cq[cur][0]; v.q1 = p.cq[cur][1]; v.q2 = p.cq[cur][2]; v.hb = p.chb;
     v.nx = p.nxc; v.ny = p.nyc; v.bc = p.cbc;
     const int4 m = p.cf[e];
-    const int axis = m.w & 1, side = (m.w & 2) ? 1 : -1;
+    const int w = p.cfw[e];
+    const int axis = w & 1, side = (w & 2) ? 1 : -1;
     // U's high edge: stencil from one cell below U; its low edge: from two
-    const float f = reflux::group_flux(v, m.x % p.nxc, m.x / p.nxc, axis, side > 0 ? -1 : -2,
+    const float f = reflux::group_flux(v, m.y % p.nxc, m.y / p.nxc, axis, side > 0 ? -1 : -2,
                                        0.5f * p.g, (float)(dt / p.nxc_d), (float)(dt / p.nyc_d),
                                        p.order);
-    if (live && (lane & 3) == 0)
-        for (int k = 0; k < p.r; k++) p.dhf[(size_t)e * p.r + k] = 0.0;
     if (live && (lane & 3) == 1)
-        p.dh[e] = (dt > 0.0 ? dt : 0.0) / (axis == 0 ? p.dxc : p.dyc) * (double)(side > 0 ? f : -f);
+        p.slot[(size_t)e * (1 + p.r)] += (dt > 0.0 ? dt : 0.0) / (axis == 0 ? p.dxc : p.dyc) *
+                                         (double)(side > 0 ? f : -f);
 }
 
-// Geometry of one fine patch in global fine cells: array column 0 at
-// (I0, J0); interior [I0 + 2, I0 + nx - 2) x [J0 + 2, J0 + ny - 2).
-// Building the maps costs O(coarse cells + ring cells + covered cells).
+// ------------------------------------------------------------- host maps
+// One patch in its level's global cells: array column 0 at (I0, J0);
+// interior [I0 + 2, I0 + nx - 2) x [J0 + 2, J0 + ny - 2).
 struct FineBox {
     long long I0, J0;
     int nx, ny;
+    bool interior(long long I, long long J) const {
+        return I >= I0 + kRing && I < I0 + nx - kRing && J >= J0 + kRing && J < J0 + ny - kRing;
+    }
+    int local(long long I, long long J) const { return (int)((J - J0) * nx + (I - I0)); }
 };
 
-// Check the hierarchy and build the maps (host).
-int build_maps(const GridRefs &c, const swa_patchset *ps, int level, int r,
-               std::vector<int4> &fill, std::vector<int4> &avg, std::vector<int4> &cf,
-               std::vector<int4> &cfu) {
+// A hierarchy level's patches (patch-set indices ascending) and a bucket
+// index over the coarse cells: the patches whose interior meets each.
+struct LevelGeom {
+    std::vector<int> ids;
+    std::vector<FineBox> box;
+    long long per = 1;        // level cells per coarse cell, per axis
+    long long gnx = 0, gny = 0;
+    int r = 1;
+    double dx = 0, dy = 0;
+    std::vector<int> head, list;
+
+    // lowest-index patch (other than skip) whose interior holds global cell
+    // (I, J); -1 if none
+    int owner(long long I, long long J, int skip, int nxc) const {
+        if (I < 0 || J < 0 || I >= gnx || J >= gny) return -1;
+        const size_t c = (size_t)(J / per) * nxc + (size_t)(I / per);
+        for (int k = head[c]; k < head[c + 1]; k++) {
+            const int a = list[k];
+            if (a != skip && box[a].interior(I, J)) return a;
+        }
+        return -1;
+    }
+};
+
+struct HostMaps {
+    std::vector<int4> fill, avg, cf, cfu;
+    std::vector<int> par, cfw;
+};
+
+// Check the hierarchy and build every level's maps (host).  levels[l - 1]:
+// the patch-set level of hierarchy level l; ratios[l - 1]: r_l.
+int build_maps(const GridRefs &c, const swa_patchset *ps, int L, const int *levels,
+               const int *ratios, std::vector<HostMaps> &out) {
     const swa_grid_desc &d = c.d;
     if (d.ndim != 2 || d.precision != SWA_FP32)
         return set_error(SWA_EINVAL, "the coarse grid must be 2D FP32");
-    if (r < 1 || r > 64) return set_error(SWA_EINVAL, "ratio must be in [1, 64]");
-    if (level < 1 || level > SWA_MAX_LEVELS || ps->lev[level].npatches == 0)
-        return set_error(SWA_EINVAL, "level %d has no patches", level);
-    // the fills overwrite every ring cell before each launch, so the fine
-    // patches must extrapolate beyond their rings (a wall would change the
-    // ring's edge waves and the level's CFL step)
+    if (L < 1 || L > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "levels must be in [1, %d]",
+                                                      SWA_MAX_LEVELS);
+    // the fills overwrite every ring cell before each launch, so the patches
+    // must extrapolate beyond their rings (a wall would change the ring's
+    // edge waves and the level's CFL step)
     for (int k = 0; k < 4; k++)
         if (ps->common.bc[k] != SWA_BC_EXTRAP)
             return set_error(SWA_EINVAL,
                              "the fine patch set must use SWA_BC_EXTRAP on all four sides");
-    std::vector<int> ids;
-    std::vector<FineBox> box;
-    const double dxf = d.dx / r, dyf = d.dy / r;
-    for (int k = 0; k < ps->n; k++) {
-        const swa_patch_desc &q = ps->pd[k];
-        if (q.level != level) continue;
-        if (fabs(q.dx - dxf) > 1e-9 * dxf || fabs(q.dy - dyf) > 1e-9 * dyf)
-            return set_error(SWA_EINVAL, "patch %d: cell size is not the coarse size / %d", k, r);
-        // interior lower-left on a coarse cell corner
-        const double fi = (q.x_lo + kRing * q.dx - d.x_lo) / d.dx;
-        const double fj = (q.y_lo + kRing * q.dy - d.y_lo) / d.dy;
-        const long long i0 = llround(fi), j0 = llround(fj);
-        if (fabs(fi - (double)i0) > 1e-6 || fabs(fj - (double)j0) > 1e-6)
-            return set_error(SWA_EINVAL, "patch %d: interior not on coarse cell corners", k);
-        if (q.nx <= 2 * kRing || q.ny <= 2 * kRing || (q.nx - 2 * kRing) % r != 0 ||
-            (q.ny - 2 * kRing) % r != 0)
-            return set_error(SWA_EINVAL, "patch %d: interior not whole coarse cells", k);
-        FineBox b{i0 * r - kRing, j0 * r - kRing, q.nx, q.ny};
-        if (b.I0 < 0 || b.J0 < 0 || b.I0 + b.nx > (long long)d.nx * r ||
-            b.J0 + b.ny > (long long)d.ny * r)
-            return set_error(SWA_EINVAL, "patch %d: its ring leaves the coarse domain", k);
-        ids.push_back(k);
-        box.push_back(b);
-    }
-    const int np = (int)ids.size();
-    // Interiors are whole coarse cells, so a fine cell's owners are its
-    // coarse cell's: per coarse cell the two lowest-index patches (in the
-    // order above) whose interiors cover it, -1 if none.
-    std::vector<int2> own((size_t)d.nx * d.ny, make_int2(-1, -1));
-    for (int a = 0; a < np; a++) {
-        const FineBox &b = box[a];
-        const long long i0 = (b.I0 + kRing) / r, j0 = (b.J0 + kRing) / r;
-        const int mx = (b.nx - 2 * kRing) / r, my = (b.ny - 2 * kRing) / r;
-        for (int jc = 0; jc < my; jc++)
-            for (int ic = 0; ic < mx; ic++) {
-                int2 &o = own[(size_t)(j0 + jc) * d.nx + (size_t)(i0 + ic)];
-                if (o.x < 0) o.x = a;
-                else if (o.y < 0) o.y = a;
-            }
-    }
-    fill.clear();
-    avg.clear();
-    for (int a = 0; a < np; a++) {
-        const FineBox &b = box[a];
-        for (int j = 0; j < b.ny; j++)
-            for (int i = 0; i < b.nx; i++) {
-                if (i >= kRing && i < b.nx - kRing && j >= kRing && j < b.ny - kRing) continue;
-                const long long I = b.I0 + i, J = b.J0 + j;
-                const long long ic = I / r, jc = J / r;
-                const int2 o = own[(size_t)jc * d.nx + (size_t)ic];
-                const int src = o.x != a ? o.x : o.y;   // lowest-index other owner
-                int4 m = make_int4(ids[a], j * b.nx + i, 0, 0);
-                if (src >= 0) {
-                    const FineBox &s = box[src];
-                    m.z = ids[src];
-                    m.w = (int)((J - s.J0) * s.nx + (I - s.I0));
-                } else {
-                    m.z = -1 - (int)((I - ic * r) + r * (J - jc * r));
-                    m.w = (int)(jc * d.nx + ic);
-                }
-                fill.push_back(m);
-            }
-    }
-    for (int jc = 0; jc < d.ny; jc++)
-        for (int ic = 0; ic < d.nx; ic++) {
-            const int a = own[(size_t)jc * d.nx + ic].x;
-            if (a < 0) continue;
-            const FineBox &b = box[a];
-            const long long li = (long long)ic * r - b.I0, lj = (long long)jc * r - b.J0;
-            avg.push_back(make_int4(jc * d.nx + ic, ids[a], (int)(lj * b.nx + li), 0));
+    std::vector<LevelGeom> G(L + 1);
+    G[0].per = 1; G[0].gnx = d.nx; G[0].gny = d.ny; G[0].dx = d.dx; G[0].dy = d.dy;
+    long long per = 1;
+    for (int l = 1; l <= L; l++) {
+        const int lev = levels[l - 1], r = ratios[l - 1];
+        if (lev < 1 || lev > SWA_MAX_LEVELS || ps->lev[lev].npatches == 0)
+            return set_error(SWA_EINVAL, "level %d has no patches", lev);
+        for (int k = 1; k < l; k++)
+            if (levels[k - 1] == lev)
+                return set_error(SWA_EINVAL, "patch-set level %d used twice", lev);
+        if (r < 1 || r > 64) return set_error(SWA_EINVAL, "ratio must be in [1, 64]");
+        per *= r;
+        if (per > (1LL << 20)) return set_error(SWA_EINVAL, "refinement too deep");
+        LevelGeom &g = G[l];
+        g.r = r; g.per = per; g.gnx = d.nx * per; g.gny = d.ny * per;
+        g.dx = G[l - 1].dx / r; g.dy = G[l - 1].dy / r;
+        for (int k = 0; k < ps->n; k++) {
+            const swa_patch_desc &q = ps->pd[k];
+            if (q.level != lev) continue;
+            if (fabs(q.dx - g.dx) > 1e-9 * g.dx || fabs(q.dy - g.dy) > 1e-9 * g.dy)
+                return set_error(SWA_EINVAL, "patch %d: cell size is not the parent's / %d", k, r);
+            // interior lower-left on a parent cell corner
+            const double fi = (q.x_lo + kRing * q.dx - d.x_lo) / G[l - 1].dx;
+            const double fj = (q.y_lo + kRing * q.dy - d.y_lo) / G[l - 1].dy;
+            const long long i0 = llround(fi), j0 = llround(fj);
+            if (fabs(fi - (double)i0) > 1e-6 || fabs(fj - (double)j0) > 1e-6)
+                return set_error(SWA_EINVAL, "patch %d: interior not on parent cell corners", k);
+            if (q.nx <= 2 * kRing || q.ny <= 2 * kRing || (q.nx - 2 * kRing) % r != 0 ||
+                (q.ny - 2 * kRing) % r != 0)
+                return set_error(SWA_EINVAL, "patch %d: interior not whole parent cells", k);
+            FineBox b{i0 * r - kRing, j0 * r - kRing, q.nx, q.ny};
+            if (b.I0 < 0 || b.J0 < 0 || b.I0 + b.nx > g.gnx || b.J0 + b.ny > g.gny)
+                return set_error(SWA_EINVAL, "patch %d: its ring leaves the domain", k);
+            g.ids.push_back(k);
+            g.box.push_back(b);
         }
-    // coarse-fine edges: per uncovered coarse cell U, its covered neighbours
-    // V in the order (+x, -x, +y, -y); the r fine cells of V's owner along
-    // the edge, from the corner nearest the lower left
-    cf.clear();
-    cfu.clear();
+        // bucket index (CSR over coarse cells, patch order kept)
+        const size_t nc = (size_t)d.nx * d.ny;
+        g.head.assign(nc + 1, 0);
+        for (int pass = 0; pass < 2; pass++) {
+            std::vector<int> fillp;
+            if (pass == 1) {
+                for (size_t i = 0; i < nc; i++) g.head[i + 1] += g.head[i];
+                g.list.assign(g.head[nc], 0);
+                fillp.assign(g.head.begin(), g.head.end() - 1);
+            }
+            for (int a = 0; a < (int)g.box.size(); a++) {
+                const FineBox &b = g.box[a];
+                const long long x0 = (b.I0 + kRing) / per, x1 = (b.I0 + b.nx - kRing - 1) / per;
+                const long long y0 = (b.J0 + kRing) / per, y1 = (b.J0 + b.ny - kRing - 1) / per;
+                for (long long y = y0; y <= y1; y++)
+                    for (long long x = x0; x <= x1; x++) {
+                        const size_t cc = (size_t)y * d.nx + (size_t)x;
+                        if (pass == 0) g.head[cc + 1]++;
+                        else g.list[fillp[cc]++] = a;
+                    }
+            }
+        }
+    }
+    out.assign(L + 1, HostMaps());
     static const int dirs[4][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}};
-    for (int jc = 0; jc < d.ny; jc++)
-        for (int ic = 0; ic < d.nx; ic++) {
-            if (own[(size_t)jc * d.nx + ic].x >= 0) continue;
-            const int first = (int)cf.size();
+    for (int l = 1; l <= L; l++) {
+        const LevelGeom &g = G[l], &gp = G[l - 1];
+        const int r = g.r;
+        HostMaps &M = out[l];
+        // fills (and the nesting check of every array cell)
+        for (int a = 0; a < (int)g.box.size(); a++) {
+            const FineBox &b = g.box[a];
+            for (int j = 0; j < b.ny; j++)
+                for (int i = 0; i < b.nx; i++) {
+                    const bool ring =
+                        !(i >= kRing && i < b.nx - kRing && j >= kRing && j < b.ny - kRing);
+                    const long long I = b.I0 + i, J = b.J0 + j;
+                    const long long Ip = I / r, Jp = J / r;
+                    int pb = -1;
+                    if (l > 1) {
+                        pb = gp.owner(Ip, Jp, -1, d.nx);
+                        if (pb < 0)
+                            return set_error(SWA_EINVAL, "patch %d: not nested in level %d",
+                                             g.ids[a], levels[l - 2]);
+                    }
+                    if (!ring) continue;
+                    const int src = g.owner(I, J, a, d.nx);
+                    int4 m = make_int4(g.ids[a], j * b.nx + i, 0, 0);
+                    int par = -1;
+                    if (src >= 0) {
+                        m.z = g.ids[src];
+                        m.w = g.box[src].local(I, J);
+                    } else {
+                        m.z = -1 - (int)((I - Ip * r) + r * (J - Jp * r));
+                        if (l == 1) {
+                            m.w = (int)(Jp * d.nx + Ip);
+                        } else {
+                            m.w = gp.box[pb].local(Ip, Jp);
+                            par = gp.ids[pb];
+                        }
+                    }
+                    M.fill.push_back(m);
+                    M.par.push_back(par);
+                }
+        }
+        // copies of the parent level's interior cells, in order
+        auto each_copy = [&](auto fn) {
+            if (l == 1) {
+                for (int jc = 0; jc < d.ny; jc++)
+                    for (int ic = 0; ic < d.nx; ic++) fn(-1, jc * d.nx + ic, (long long)ic, (long long)jc);
+                return;
+            }
+            for (int b = 0; b < (int)gp.box.size(); b++) {
+                const FineBox &B = gp.box[b];
+                for (int j = kRing; j < B.ny - kRing; j++)
+                    for (int i = kRing; i < B.nx - kRing; i++)
+                        fn(gp.ids[b], j * B.nx + i, B.I0 + i, B.J0 + j);
+            }
+        };
+        each_copy([&](int pu, int u, long long I, long long J) {
+            const int a = g.owner(I * r, J * r, -1, d.nx);
+            if (a >= 0) {
+                M.avg.push_back(make_int4(pu, u, g.ids[a], g.box[a].local(I * r, J * r)));
+                return;
+            }
+            const int first = (int)M.cf.size();
             for (int k = 0; k < 4; k++) {
                 const int axis = dirs[k][0], side = dirs[k][1];
-                const int iv = axis == 0 ? ic + side : ic, jv = axis == 0 ? jc : jc + side;
-                if (iv < 0 || iv >= d.nx || jv < 0 || jv >= d.ny) continue;
-                const int a = own[(size_t)jv * d.nx + iv].x;
-                if (a < 0) continue;
-                const FineBox &b = box[a];
-                long long I = (long long)iv * r, J = (long long)jv * r;
-                if (axis == 0) I += side > 0 ? 0 : r - 1;
-                else J += side > 0 ? 0 : r - 1;
+                const long long Iv = axis == 0 ? I + side : I, Jv = axis == 0 ? J : J + side;
+                if (Iv < 0 || Iv >= gp.gnx || Jv < 0 || Jv >= gp.gny) continue;
+                const int q = g.owner(Iv * r, Jv * r, -1, d.nx);
+                if (q < 0) continue;
+                const FineBox &b = g.box[q];
+                long long If = Iv * r, Jf = Jv * r;
+                if (axis == 0) If += side > 0 ? 0 : r - 1;
+                else Jf += side > 0 ? 0 : r - 1;
                 const int stride = axis == 0 ? b.nx : 1;
-                cf.push_back(make_int4(jc * d.nx + ic, ids[a], (int)((J - b.J0) * b.nx + (I - b.I0)),
-                                       axis | (side > 0 ? 2 : 0) | (stride << 2)));
+                M.cf.push_back(make_int4(pu, u, g.ids[q], b.local(If, Jf)));
+                M.cfw.push_back(axis | (side > 0 ? 2 : 0) | (stride << 2));
             }
-            if ((int)cf.size() > first)
-                cfu.push_back(make_int4(jc * d.nx + ic, first, (int)cf.size() - first, 0));
-        }
+            if ((int)M.cf.size() > first)
+                M.cfu.push_back(make_int4(pu, u, first, (int)M.cf.size() - first));
+        });
+        if ((long long)M.cf.size() * (1 + r) > 0x7fffffffLL)
+            return set_error(SWA_EINVAL, "too many coarse-fine edges at level %d", levels[l - 1]);
+    }
     return SWA_OK;
 }
 
-// Workspace layout: fill, avg, edge and edge-group maps (int4), then the
-// per-edge corrections (double), each on a 256-byte boundary.
+// Workspace layout of one level's maps and slots, each on a 256-byte
+// boundary.
 struct Layout {
-    size_t fill, avg, cf, cfu, dh, dhf, total;
+    size_t fill, par, avg, cf, cfw, cfu, slot, end;
 };
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-inline Layout layout_of(size_t nfill, size_t navg, size_t ncf, size_t ncfu, int r) {
-    Layout L;
-    L.fill = 0;
-    L.avg = L.fill + round256(sizeof(int4) * nfill);
-    L.cf = L.avg + round256(sizeof(int4) * navg);
-    L.cfu = L.cf + round256(sizeof(int4) * ncf);
-    L.dh = L.cfu + round256(sizeof(int4) * ncfu);
-    L.dhf = L.dh + round256(sizeof(double) * ncf);
-    L.total = L.dhf + round256(sizeof(double) * ncf * (size_t)r) + 256;
-    return L;
+inline Layout layout_of(const HostMaps &M, int r, size_t at) {
+    Layout Lo;
+    Lo.fill = at;
+    Lo.par = Lo.fill + round256(sizeof(int4) * M.fill.size());
+    Lo.avg = Lo.par + round256(sizeof(int) * M.par.size());
+    Lo.cf = Lo.avg + round256(sizeof(int4) * M.avg.size());
+    Lo.cfw = Lo.cf + round256(sizeof(int4) * M.cf.size());
+    Lo.cfu = Lo.cfw + round256(sizeof(int) * M.cfw.size());
+    Lo.slot = Lo.cfu + round256(sizeof(int4) * M.cfu.size());
+    Lo.end = Lo.slot + round256(sizeof(double) * M.cf.size() * (size_t)(1 + r));
+    return Lo;
+}
+
+inline size_t total_bytes(const std::vector<HostMaps> &M, const int *ratios, int L) {
+    size_t at = 0;
+    for (int l = 1; l <= L; l++) at = layout_of(M[l], ratios[l - 1], at).end;
+    return at + 256;
 }
 
 }  // namespace amr
 }  // namespace swadj
 
+struct AmrLevel {
+    int lev = 0, r = 1;
+    int4 *fill = nullptr, *avg = nullptr, *cf = nullptr, *cfu = nullptr;
+    int *par = nullptr, *cfw = nullptr;
+    double *slot = nullptr;
+    int nfill = 0, navg = 0, ncf = 0, ncfu = 0;
+    double dx = 0, dy = 0;
+};
+
 struct swa_amr {
     swa_grid *coarse = nullptr;
     swa_patchset *fine = nullptr;
-    int level = 0, r = 1;
-    int4 *fill = nullptr, *avg = nullptr, *cf = nullptr, *cfu = nullptr;
-    double *dh = nullptr, *dhf = nullptr;
-    int nfill = 0, navg = 0, ncf = 0, ncfu = 0;
+    int L = 0;
+    AmrLevel lv[SWA_MAX_LEVELS + 1];   // 1 .. L
     int reflux = 1;
 };
 
-extern "C" {
+namespace {
 
-size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
-                               int ratio) {
-    GridRefs c;
-    if (!fine || grid_refs(coarse, &c) != SWA_OK) return 0;
-    std::vector<int4> f, a, e, u;
-    if (amr::build_maps(c, fine, level, ratio, f, a, e, u) != SWA_OK) return 0;
-    return amr::layout_of(f.size(), a.size(), e.size(), u.size(), ratio).total;
+// Averaging of level l into its parent (and the refluxing of the parent
+// from level l's edges), after the parent's step ending at t_end.
+int amr_average(swa_amr *A, const GridRefs &c, int l, double t_end, bool reflux,
+                cudaStream_t st) {
+    using namespace swadj;
+    AmrLevel &V = A->lv[l];
+    amr::AvgParams p{};
+    p.table = A->fine->table;
+    p.lclk = A->fine->lev[V.lev].clk;
+    p.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) p.cq[b][k] = (float *)c.q[b][k];
+    p.r = V.r;
+    p.avg = V.avg; p.navg = V.navg;
+    if (reflux) { p.cfu = V.cfu; p.ncfu = V.ncfu; }
+    p.slot = V.slot;
+    p.t_end = t_end;
+    p.err = swadj_host::error_word();
+    const size_t n = (size_t)3 * V.navg + (size_t)p.ncfu;
+    const unsigned ab = patches::ew_blocks(n > 0 ? n : 1);
+    switch (V.r) {
+        case 1: amr::amr_avg_kernel<1><<<ab, 256, 0, st>>>(p); break;
+        case 2: amr::amr_avg_kernel<2><<<ab, 256, 0, st>>>(p); break;
+        case 4: amr::amr_avg_kernel<4><<<ab, 256, 0, st>>>(p); break;
+        case 8: amr::amr_avg_kernel<8><<<ab, 256, 0, st>>>(p); break;
+        default: amr::amr_avg_kernel<0><<<ab, 256, 0, st>>>(p); break;
+    }
+    return cuda_check(cudaGetLastError(), "amr_avg_kernel");
 }
 
-int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
-                   size_t ws_bytes, void *stream, swa_amr **out) {
+// Level l of the hierarchy over the parent step [t_p, t_p + dt_p]
+// (Berger-Oliger): r_l substeps, each with its ring fills and launches
+// (one launch for a level with children, m for the finest), then the
+// children over the substep and their averaging (with the refluxing of
+// this level).
+int amr_run(swa_amr *A, const GridRefs &c, int l, double t_p, double dt_p, int m, bool reflux,
+            cudaStream_t st) {
+    using namespace swadj;
+    AmrLevel &V = A->lv[l];
+    const int r = V.r;
+    amr::FillParams f{};
+    f.table = A->fine->table;
+    f.lclk = A->fine->lev[V.lev].clk;
+    f.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) f.cq[b][k] = (float *)c.q[b][k];
+    f.nxc = c.d.nx; f.nyc = c.d.ny; f.r = r;
+    f.fill = V.fill; f.par = V.par; f.nfill = V.nfill;
+    f.t_p = t_p; f.dt_p = dt_p;
+    const unsigned fb = patches::ew_blocks((size_t)3 * (V.nfill > 0 ? V.nfill : 1));
+    patches::LevelReflux rf{};
+    const double dpx = l == 1 ? c.d.dx : A->lv[l - 1].dx, dpy = l == 1 ? c.d.dy : A->lv[l - 1].dy;
+    if (reflux) {
+        rf.cf = V.cf; rf.cfw = V.cfw; rf.slot = V.slot; rf.nfine = V.ncf * r; rf.r = r;
+        rf.dpx = dpx; rf.dpy = dpy;
+        if (l < A->L) {
+            const AmrLevel &W = A->lv[l + 1];
+            rf.cf2 = W.cf; rf.cfw2 = W.cfw; rf.slot2 = W.slot; rf.ncoarse = W.ncf; rf.r2 = W.r;
+            rf.dtx = V.dx; rf.dty = V.dy;
+        }
+    }
+    const int launches = l == A->L ? m : 1;
+    for (int k = 1; k <= r; k++) {
+        const double t_k = k == r ? t_p + dt_p : t_p + dt_p * (double)k / (double)r;
+        const double t_km1 = k == 1 ? t_p : t_p + dt_p * (double)(k - 1) / (double)r;
+        for (int j = 0; j < launches; j++) {
+            amr::amr_fill_kernel<<<fb, 256, 0, st>>>(f);
+            TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
+            TRY(level_launch(A->fine, V.lev, 1, t_k, rf, st));
+        }
+        if (l < A->L) {
+            TRY(amr_run(A, c, l + 1, t_km1, t_k - t_km1, m, reflux, st));
+            TRY(amr_average(A, c, l + 1, t_k, reflux, st));
+        }
+    }
+    return SWA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t swa_amr_levels_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine,
+                                      int nlevels, const int *levels, const int *ratios) {
     GridRefs c;
-    if (!fine || !ws || !out) return set_error(SWA_EINVAL, "null argument");
+    if (!fine || !levels || !ratios || grid_refs(coarse, &c) != SWA_OK) return 0;
+    std::vector<amr::HostMaps> M;
+    if (amr::build_maps(c, fine, nlevels, levels, ratios, M) != SWA_OK) return 0;
+    return amr::total_bytes(M, ratios, nlevels);
+}
+
+int swa_create_amr_levels(swa_grid *coarse, swa_patchset *fine, int nlevels, const int *levels,
+                          const int *ratios, void *ws, size_t ws_bytes, void *stream,
+                          swa_amr **out) {
+    GridRefs c;
+    if (!fine || !ws || !out || !levels || !ratios) return set_error(SWA_EINVAL, "null argument");
     TRY(grid_refs(coarse, &c));
     if (((uintptr_t)ws & 255) != 0) return set_error(SWA_EINVAL, "workspace must be 256-byte aligned");
-    std::vector<int4> f, a, e, u;
-    TRY(amr::build_maps(c, fine, level, ratio, f, a, e, u));
-    if ((long long)e.size() * ratio > 0x7fffffffLL)
-        return set_error(SWA_EINVAL, "too many coarse-fine edges for ratio %d", ratio);
-    const amr::Layout L = amr::layout_of(f.size(), a.size(), e.size(), u.size(), ratio);
-    if (ws_bytes < L.total)
-        return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, L.total);
+    std::vector<amr::HostMaps> M;
+    TRY(amr::build_maps(c, fine, nlevels, levels, ratios, M));
+    const size_t need = amr::total_bytes(M, ratios, nlevels);
+    if (ws_bytes < need)
+        return set_error(SWA_ENOMEM, "AMR workspace %zu bytes < %zu needed", ws_bytes, need);
     swa_amr *A = new (std::nothrow) swa_amr();
     if (!A) return set_error(SWA_ENOMEM, "host allocation failed");
-    A->coarse = coarse; A->fine = fine; A->level = level; A->r = ratio;
-    char *base = (char *)ws;
-    A->fill = (int4 *)(base + L.fill);
-    A->avg = (int4 *)(base + L.avg);
-    A->cf = (int4 *)(base + L.cf);
-    A->cfu = (int4 *)(base + L.cfu);
-    A->dh = (double *)(base + L.dh);
-    A->dhf = (double *)(base + L.dhf);
-    A->nfill = (int)f.size();
-    A->navg = (int)a.size();
-    A->ncf = (int)e.size();
-    A->ncfu = (int)u.size();
+    A->coarse = coarse; A->fine = fine; A->L = nlevels;
     cudaStream_t st = (cudaStream_t)stream;
+    char *base = (char *)ws;
+    size_t at = 0;
     int rc = SWA_OK;
-    const std::vector<int4> *src[4] = {&f, &a, &e, &u};
-    int4 *dst[4] = {A->fill, A->avg, A->cf, A->cfu};
-    const char *what[4] = {"AMR fill map upload", "AMR average map upload",
-                           "AMR edge map upload", "AMR edge group upload"};
-    for (int k = 0; k < 4 && rc == SWA_OK; k++)
-        if (!src[k]->empty())
-            rc = cuda_check(cudaMemcpyAsync(dst[k], src[k]->data(), sizeof(int4) * src[k]->size(),
-                                            cudaMemcpyHostToDevice, st), what[k]);
+    double dx = c.d.dx, dy = c.d.dy;
+    for (int l = 1; l <= nlevels && rc == SWA_OK; l++) {
+        const amr::HostMaps &H = M[l];
+        const amr::Layout Lo = amr::layout_of(H, ratios[l - 1], at);
+        at = Lo.end;
+        AmrLevel &V = A->lv[l];
+        V.lev = levels[l - 1]; V.r = ratios[l - 1];
+        dx /= V.r; dy /= V.r;
+        V.dx = dx; V.dy = dy;
+        V.fill = (int4 *)(base + Lo.fill); V.par = (int *)(base + Lo.par);
+        V.avg = (int4 *)(base + Lo.avg); V.cf = (int4 *)(base + Lo.cf);
+        V.cfw = (int *)(base + Lo.cfw); V.cfu = (int4 *)(base + Lo.cfu);
+        V.slot = (double *)(base + Lo.slot);
+        V.nfill = (int)H.fill.size(); V.navg = (int)H.avg.size();
+        V.ncf = (int)H.cf.size(); V.ncfu = (int)H.cfu.size();
+        struct Up { void *dst; const void *src; size_t bytes; const char *what; } up[] = {
+            {V.fill, H.fill.data(), sizeof(int4) * H.fill.size(), "AMR fill map upload"},
+            {V.par, H.par.data(), sizeof(int) * H.par.size(), "AMR fill parents upload"},
+            {V.avg, H.avg.data(), sizeof(int4) * H.avg.size(), "AMR average map upload"},
+            {V.cf, H.cf.data(), sizeof(int4) * H.cf.size(), "AMR edge map upload"},
+            {V.cfw, H.cfw.data(), sizeof(int) * H.cfw.size(), "AMR edge flags upload"},
+            {V.cfu, H.cfu.data(), sizeof(int4) * H.cfu.size(), "AMR edge group upload"},
+        };
+        for (const Up &u : up)
+            if (rc == SWA_OK && u.bytes > 0)
+                rc = cuda_check(cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st),
+                                u.what);
+        const size_t sb = sizeof(double) * (size_t)V.ncf * (size_t)(1 + V.r);
+        if (rc == SWA_OK && sb > 0)
+            rc = cuda_check(cudaMemsetAsync(V.slot, 0, sb, st), "AMR slot clear");
+    }
     if (rc == SWA_OK) rc = cuda_check(cudaStreamSynchronize(st), "create_amr");
     if (rc != SWA_OK) { delete A; return rc; }
     *out = A;
     return SWA_OK;
+}
+
+size_t swa_amr_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine, int level,
+                               int ratio) {
+    return swa_amr_levels_workspace_bytes(coarse, fine, 1, &level, &ratio);
+}
+
+int swa_create_amr(swa_grid *coarse, swa_patchset *fine, int level, int ratio, void *ws,
+                   size_t ws_bytes, void *stream, swa_amr **out) {
+    return swa_create_amr_levels(coarse, fine, 1, &level, &ratio, ws, ws_bytes, stream, out);
 }
 
 int swa_destroy_amr(swa_amr *A) {
@@ -1034,11 +1299,13 @@ int swa_amr_set_reflux(swa_amr *A, int on) {
     return SWA_OK;
 }
 
-int swa_amr_info(const swa_amr *A, int *nfill, int *navg, int *nedges) {
+int swa_amr_info(const swa_amr *A, int level, int *nfill, int *navg, int *nedges) {
     if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
-    if (nfill) *nfill = A->nfill;
-    if (navg) *navg = A->navg;
-    if (nedges) *nedges = A->ncf;
+    if (level < 1 || level > A->L) return set_error(SWA_EINVAL, "level must be in [1, %d]", A->L);
+    const AmrLevel &V = A->lv[level];
+    if (nfill) *nfill = V.nfill;
+    if (navg) *navg = V.navg;
+    if (nedges) *nedges = V.ncf;
     return SWA_OK;
 }
 
@@ -1049,66 +1316,39 @@ int swa_amr_step(swa_amr *A, double t_n, double dt_c, int max_launches, void *st
     GridRefs c;
     TRY(grid_refs(A->coarse, &c));
     if (!c.state_set) return set_error(SWA_ESTATE, "coarse state not set");
-    if (!A->fine->lev[A->level].started) return set_error(SWA_ESTATE, "fine level not started");
-    const bool reflux = A->reflux && A->ncf > 0;
-    if (reflux && c.scheme != SWA_SCHEME_SPLIT)
+    bool edges = false;
+    for (int l = 1; l <= A->L; l++) {
+        if (!A->fine->lev[A->lv[l].lev].started)
+            return set_error(SWA_ESTATE, "level %d not started", A->lv[l].lev);
+        edges = edges || A->lv[l].ncf > 0;
+    }
+    const bool reflux = A->reflux != 0;
+    if (reflux && edges && c.scheme != SWA_SCHEME_SPLIT)
         return set_error(SWA_EINVAL, "refluxing needs the split scheme on the coarse grid");
     cudaStream_t st = (cudaStream_t)stream;
-    amr::AmrParams p{};
-    p.table = A->fine->table;
-    p.lclk = A->fine->lev[A->level].clk;
-    p.cclk = c.clk;
-    for (int b = 0; b < 2; b++)
-        for (int k = 0; k < 3; k++) p.cq[b][k] = (float *)c.q[b][k];
-    p.nxc = c.d.nx; p.nyc = c.d.ny; p.r = A->r;
-    p.fill = A->fill; p.nfill = A->nfill;
-    p.avg = A->avg; p.navg = A->navg;
-    p.t_n = t_n; p.dt_c = dt_c; p.t_end = t_n + dt_c;
-    p.err = swadj_host::error_word();
-    amr::RefluxParams q{};
+    const double t_end = t_n + dt_c;
+    amr::CoarseReflux q{};
     q.cclk = c.clk;
     for (int b = 0; b < 2; b++)
-        for (int k = 0; k < 3; k++) q.cq[b][k] = p.cq[b][k];
+        for (int k = 0; k < 3; k++) q.cq[b][k] = (const float *)c.q[b][k];
     q.chb = (const float *)c.bath;
-    q.nxc = c.d.nx; q.nyc = c.d.ny; q.r = A->r;
+    q.nxc = c.d.nx; q.nyc = c.d.ny;
     q.cbc = BcSpec{c.d.bc[0], c.d.bc[1], c.d.bc[2], c.d.bc[3]};
     q.dxc = c.d.dx; q.dyc = c.d.dy;
     q.nxc_d = (double)(float)c.d.dx; q.nyc_d = (double)(float)c.d.dy;
     q.g = (float)c.d.g; q.order = c.d.order;
-    q.cf = A->cf; q.ncf = A->ncf; q.dh = A->dh; q.dhf = A->dhf;
-    q.t_end = p.t_end;
-    patches::LevelReflux rf{};
-    if (reflux) {
-        rf.cf = A->cf; rf.dhf = A->dhf; rf.nitems = A->ncf * A->r; rf.r = A->r;
-        rf.dxc = c.d.dx; rf.dyc = c.d.dy;
-        p.cfu = A->cfu; p.ncfu = A->ncfu; p.dh = A->dh; p.dhf = A->dhf;
-    }
-    const unsigned fb = ew_blocks((size_t)3 * (A->nfill > 0 ? A->nfill : 1));
-    const size_t navg_items = (size_t)3 * A->navg + (size_t)p.ncfu;
-    const unsigned ab = ew_blocks(navg_items > 0 ? navg_items : 1);
-    if (reflux) {
-        const unsigned eb = (unsigned)((A->ncf + 31) / 32);   // 8 edges per warp, 4 warps
-        amr::reflux_coarse_kernel<<<eb, 128, 0, st>>>(q);
-        TRY(cuda_check(cudaGetLastError(), "reflux_coarse_kernel"));
-    }
-    TRY(swa_step_forward(A->coarse, 1, p.t_end, stream));
-    for (int k = 1; k <= A->r; k++) {
-        const double t_k = k == A->r ? p.t_end : t_n + dt_c * (double)k / (double)A->r;
-        for (int j = 0; j < max_launches; j++) {
-            amr::amr_fill_kernel<<<fb, 256, 0, st>>>(p);
-            TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
-            TRY(level_launch(A->fine, A->level, 1, t_k, rf, st));
-        }
-    }
-    switch (A->r) {
-        case 1: amr::amr_avg_kernel<1><<<ab, 256, 0, st>>>(p); break;
-        case 2: amr::amr_avg_kernel<2><<<ab, 256, 0, st>>>(p); break;
-        case 4: amr::amr_avg_kernel<4><<<ab, 256, 0, st>>>(p); break;
-        case 8: amr::amr_avg_kernel<8><<<ab, 256, 0, st>>>(p); break;
-        default: amr::amr_avg_kernel<0><<<ab, 256, 0, st>>>(p); break;
-    }
-    TRY(cuda_check(cudaGetLastError(), "amr_avg_kernel"));
-    return SWA_OK;
+    q.cf = A->lv[1].cf; q.cfw = A->lv[1].cfw; q.slot = A->lv[1].slot;
+    q.ncf = reflux ? A->lv[1].ncf : 0; q.r = A->lv[1].r;
+    q.t_n = t_n; q.t_end = t_end;
+    for (int l = 1; l <= A->L; l++) q.lclk[l - 1] = A->fine->lev[A->lv[l].lev].clk;
+    q.nlev = A->L;
+    q.err = swadj_host::error_word();
+    const unsigned eb = (unsigned)(q.ncf > 0 ? (q.ncf + 31) / 32 : 1);   // 8 edges per warp
+    amr::reflux_coarse_kernel<<<eb, 128, 0, st>>>(q);
+    TRY(cuda_check(cudaGetLastError(), "reflux_coarse_kernel"));
+    TRY(swa_step_forward(A->coarse, 1, t_end, stream));
+    TRY(amr_run(A, c, 1, t_n, dt_c, max_launches, reflux, st));
+    return amr_average(A, c, 1, t_end, reflux, st);
 }
 
 }  // extern "C"

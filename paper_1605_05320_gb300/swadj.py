@@ -50,7 +50,8 @@ EXPORTS = [
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
-    "swa_amr_set_reflux", "swa_amr_info",
+    "swa_amr_set_reflux", "swa_amr_info", "swa_amr_levels_workspace_bytes",
+    "swa_create_amr_levels",
     "swa_alu_probe_ops", "swa_alu_probe",
     "swa_grid_mass",
 ]
@@ -159,7 +160,9 @@ def load(path: str = LIB_PATH):
         "swa_destroy_amr": ([_V], _I),
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
         "swa_amr_set_reflux": ([_V, _I], _I),
-        "swa_amr_info": ([_V, _P(_I), _P(_I), _P(_I)], _I),
+        "swa_amr_info": ([_V, _I, _P(_I), _P(_I), _P(_I)], _I),
+        "swa_amr_levels_workspace_bytes": ([_V, _V, _I, _P(_I), _P(_I)], _SZ),
+        "swa_create_amr_levels": ([_V, _V, _I, _P(_I), _P(_I), _V, _SZ, _V, _P(_V)], _I),
         "swa_alu_probe_ops": ([_I, _I, _I, _I], _D),
         "swa_grid_mass": ([_V, _V, _V], _I),
         "swa_alu_probe": ([_I, _I, _I, _I, _V, _V], _I),
@@ -630,10 +633,27 @@ def swa_amr_set_reflux(h, on):
     return _chk(load().swa_amr_set_reflux(h, int(bool(on))))
 
 
-def swa_amr_info(h):
+def swa_amr_info(h, level=1):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _chk(load().swa_amr_info(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    _chk(load().swa_amr_info(h, int(level), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def _ints(v):
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def swa_amr_levels_workspace_bytes(coarse, fine, levels, ratios):
+    return int(load().swa_amr_levels_workspace_bytes(coarse, fine, len(levels), _ints(levels),
+                                                     _ints(ratios)))
+
+
+def swa_create_amr_levels(coarse, fine, levels, ratios, ws, ws_bytes, stream=None):
+    out = _V()
+    _chk(load().swa_create_amr_levels(coarse, fine, len(levels), _ints(levels), _ints(ratios),
+                                      _ptr(ws), int(ws_bytes), _stream(stream),
+                                      ctypes.byref(out)))
+    return out
 
 
 class PatchSet:
@@ -681,16 +701,26 @@ class PatchSet:
 
 
 class Amr:
-    """Two-level AMR hierarchy over a Grid (coarse) and one level of a
-    PatchSet (fine, ringed patches); keeps both alive."""
+    """AMR hierarchy over a Grid (coarse) and levels of a PatchSet (ringed
+    patches): `level` and `ratio` are one patch-set level and its ratio (the
+    two-level glue) or equal-length sequences, level 1 first; keeps both
+    alive."""
 
     def __init__(self, grid, patchset, level, ratio, device="cuda", stream=None):
-        self.grid, self.patchset, self.level, self.ratio = grid, patchset, level, ratio
-        self.nbytes = swa_amr_workspace_bytes(grid.h, patchset.h, level, ratio)
+        self.grid, self.patchset = grid, patchset
+        levels = list(level) if hasattr(level, "__len__") else [level]
+        ratios = list(ratio) if hasattr(ratio, "__len__") else [ratio]
+        self.levels, self.ratios = levels, ratios
+        self.nbytes = swa_amr_levels_workspace_bytes(grid.h, patchset.h, levels, ratios)
         if self.nbytes == 0:
             raise SwaError(SWA_EINVAL, swa_last_error())
         self.ws = _workspace(self.nbytes, device)
-        self.h = swa_create_amr(grid.h, patchset.h, level, ratio, self.ws, self.nbytes, stream)
+        if len(levels) == 1:
+            self.h = swa_create_amr(grid.h, patchset.h, levels[0], ratios[0], self.ws,
+                                    self.nbytes, stream)
+        else:
+            self.h = swa_create_amr_levels(grid.h, patchset.h, levels, ratios, self.ws,
+                                           self.nbytes, stream)
 
     def step(self, t_n, dt_c, max_launches=1, stream=None):
         swa_amr_step(self.h, t_n, dt_c, max_launches, stream)
@@ -698,9 +728,10 @@ class Amr:
     def set_reflux(self, on):
         swa_amr_set_reflux(self.h, on)
 
-    def info(self):
-        """(ring cells filled, covered coarse cells, coarse-fine edges)."""
-        return swa_amr_info(self.h)
+    def info(self, level=1):
+        """Hierarchy level `level`: (ring cells filled, covered parent cell
+        copies, coarse-fine edges)."""
+        return swa_amr_info(self.h, level)
 
     def __del__(self):
         try:

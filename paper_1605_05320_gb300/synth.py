@@ -357,6 +357,64 @@ def amr_basin(nc: int, r: int, boxes, dx: float = 10e3, rest: bool = False,
     return out
 
 
+def amr_levels_basin(nc: int, levels, dx: float = 10e3, rest: bool = False,
+                     seed: int | None = None, mean_coarse: bool = False):
+    """The walled basin of amr_basin with nested levels.
+
+    levels: [(r, boxes), ...], level l's boxes (i0, j0, mx, my) in global
+    level-(l - 1) cells (the uniform grid of that level's cell size over the
+    whole domain).  Every level samples the bottom and surface at its own
+    centres, or (mean_coarse) the finest level samples them and every other
+    level holds the means of the level below.  seed: uniform random momenta
+    in [-5, 5] (all ratios 1).  Returns a dict with the coarse fields (B, eta,
+    hu, hv), per level "r" and "patches" (descriptor (l, x_lo, y_lo, nx, ny,
+    dx, dy) and fields B, eta, hu, hv, ring included)."""
+    def bottom(x, y):
+        return -100.0 - 20.0 * np.sin(x / 7e4) * np.cos(y / 9e4)
+
+    L = nc * dx
+
+    def hump(x, y):
+        return 0.5 * np.exp(-((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2) / (3 * dx) ** 2)
+
+    ratios = [lv[0] for lv in levels]
+    F, n, d = [], nc, dx
+    for l in range(len(levels) + 1):
+        if l > 0:
+            n, d = n * ratios[l - 1], d / ratios[l - 1]
+        xc = (np.arange(n) + 0.5) * d
+        X, Y = np.meshgrid(xc, xc)
+        F.append([bottom(X, Y), np.zeros_like(X) if rest else hump(X, Y)])
+    if mean_coarse:
+        for l in range(len(levels) - 1, -1, -1):
+            r = ratios[l]
+            m = F[l + 1][0].shape[0] // r
+            F[l] = [a.reshape(m, r, m, r).mean(axis=(1, 3)) for a in F[l + 1]]
+    U = None
+    if seed is not None:
+        assert all(r == 1 for r in ratios)
+        U = np.random.default_rng(seed).uniform(-5.0, 5.0, (nc, nc))
+    uc = np.zeros((nc, nc)) if U is None else U
+    out = {"coarse": {"B": F[0][0].ravel(), "eta": F[0][1].ravel(), "hu": uc.ravel(),
+                      "hv": -uc.ravel()}, "levels": [], "dx": dx, "nc": nc}
+    dp = dx
+    for l, (r, boxes) in enumerate(levels, start=1):
+        BF, EF = F[l]
+        UF = np.zeros_like(BF) if U is None else U
+        df = dp / r
+        pats = []
+        for (i0, j0, mx, my) in boxes:
+            nx, ny = mx * r + 4, my * r + 4
+            I0, J0 = i0 * r - 2, j0 * r - 2
+            sl = lambda a: a[J0:J0 + ny, I0:I0 + nx].ravel().copy()
+            desc = (l, i0 * dp - 2 * df, j0 * dp - 2 * df, nx, ny, df, df)
+            pats.append({"box": (i0, j0, mx, my), "desc": desc, "B": sl(BF), "eta": sl(EF),
+                         "hu": sl(UF), "hv": -sl(UF)})
+        out["levels"].append({"r": r, "patches": pats})
+        dp = df
+    return out
+
+
 def amr_basin_2048(ratio: int = 4, side: int = 32, tiles: int = 8):
     """The basin of the 2D configurations as a two-level hierarchy: the
     2048^2 coarse grid (1 km cells) and tiles x tiles fine patches of
