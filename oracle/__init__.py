@@ -65,7 +65,8 @@ class _Grid(ctypes.Structure):
                 ("order", ctypes.c_int), ("bc", ctypes.c_int * 4),
                 ("g", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("dry_tol", ctypes.c_double), ("lin_nu", ctypes.c_double * 2),
-                ("scheme", ctypes.c_int), ("tw_scale", ctypes.c_double)]
+                ("scheme", ctypes.c_int), ("tw_scale", ctypes.c_double),
+                ("wetdry", ctypes.c_int)]
 
 
 @dataclass
@@ -84,6 +85,7 @@ class Grid:
     dry_tol: float = 1e-3
     scheme: int = SCHEME_SPLIT
     tw_scale: float = 1.0   # transverse terms; tests set 0 / -1 to plant a mistake
+    wetdry: int = 0         # split step: shore solver at dry and transonic edges
 
     @property
     def n(self):
@@ -98,6 +100,7 @@ class Grid:
             s.bc[k] = int(self.bc[k])
         s.g, s.cfl, s.dry_tol = self.g, self.cfl, self.dry_tol
         s.scheme, s.tw_scale = int(self.scheme), float(self.tw_scale)
+        s.wetdry = int(self.wetdry)
         return s
 
     @classmethod

@@ -72,6 +72,8 @@ typedef struct {
     double tw_scale;    /* factor on the transverse terms: 1 for the method; the
                            tests set 0 or -1 to show their pins catch a dropped
                            or sign-flipped term */
+    int wetdry;         /* forward split step: 1 handles dry cells (h <= dry_tol)
+                           and transonic edges by the shore solver below */
 } orc_grid;
 
 #define NG 2
@@ -86,6 +88,10 @@ typedef struct {
  *   3  normal Roe average taken as the arithmetic mean of uL and uR
  *   4  adjoint step count one more than ceil(t_f smax / cfl)
  *   5  snapshot times recorded one snapshot interval late
+ *   6  shore solver: HLL flux of the cell states instead of the
+ *      hydrostatically reconstructed ones
+ *   7  shore solver used only at dry edges (transonic wet edges keep Roe)
+ *   8  shore solver: the hydrostatic-reconstruction pressure terms dropped
  */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
@@ -173,6 +179,8 @@ typedef struct {
     double s[3];
     double Z[3][3];
     double uhat, vhat, chat;   /* Roe state of the forward solve (edge frame) */
+    int shore;                 /* fluctuations given directly (shore solver) */
+    double amdq[3], apdq[3];
 } edge_waves;
 
 /*
@@ -185,6 +193,12 @@ static void edge_fluxes(int mw, const edge_waves *em, const edge_waves *e,
                         const edge_waves *ep, double nu, int order,
                         double amdq[3], double apdq[3], double F[3]) {
     for (int m = 0; m < 3; m++) { amdq[m] = 0.0; apdq[m] = 0.0; F[m] = 0.0; }
+    if (e->shore) {
+        /* first order at the shore; its waves are zero for the neighbours'
+           limiters */
+        for (int m = 0; m < 3; m++) { amdq[m] = e->amdq[m]; apdq[m] = e->apdq[m]; }
+        return;
+    }
     for (int p = 0; p < mw; p++) {
         double s = e->s[p];
         for (int m = 0; m < 3; m++) {
@@ -250,9 +264,105 @@ static void fwd_riemann(double g,
 #endif
     w->s[0] = s1; w->s[1] = s2; w->s[2] = s3;
     w->uhat = uhat; w->vhat = vhat; w->chat = chat;
+    w->shore = 0;
     w->Z[0][0] = b1;  w->Z[0][1] = b1 * s1;  w->Z[0][2] = b1 * vhat;
     w->Z[1][0] = 0.0; w->Z[1][1] = 0.0;      w->Z[1][2] = b2;
     w->Z[2][0] = b3;  w->Z[2][1] = b3 * s3;  w->Z[2][2] = b3 * vhat;
+}
+
+/*
+ * Shore solver (the reading of Sec. 6's "robust near shore and inundation"):
+ * at an edge with a dry cell (h <= dry_tol) or a transonic rarefaction the
+ * fluctuations come from the hydrostatic reconstruction of Audusse et al.
+ * (2004) with an HLL flux, first order.  Reconstructed depths h*_L =
+ * max(0, h_L + B_L - max(B_L, B_R)), h*_R likewise, with the cell velocities
+ * (zero in a dry cell); HLL speeds s_L = min(u_L - c_L, u_R - c_R), s_R =
+ * max(u_L + c_L, u_R + c_R) over the reconstructed states (c = 0 on a dry
+ * side, so no speed exceeds a wet cell's |u| + c and the cell CFL number
+ * bounds them: positivity of the scheme for CFL <= 1/2); flux
+ * F = (s_R F_L - s_L F_R + s_L s_R (Q_R - Q_L)) / (s_R - s_L) over the
+ * reconstructed states (F_L if s_L >= 0, F_R if s_R <= 0, zero when both are
+ * dry).  The cell beside the edge sees F plus the pressure difference
+ * g/2 (h^2 - h*^2) of its own side, so
+ *   amdq = F + (0, g/2 (h_L^2 - h*_L^2), 0) - f(Q_L),
+ *   apdq = f(Q_R) - F - (0, g/2 (h_R^2 - h*_R^2), 0),
+ * f the physical flux (hu, hu u + g/2 h^2, hu v): well balanced (the ocean
+ * at rest against dry land above it has zero fluctuations) and the mass flux
+ * is F's first component on both sides.
+ */
+static void shore_riemann(double g, double dry_tol,
+                          double hL, double mnL, double mtL, double BL,
+                          double hR, double mnR, double mtR, double BR, edge_waves *w) {
+    double uL = hL > dry_tol ? mnL / hL : 0.0, vL = hL > dry_tol ? mtL / hL : 0.0;
+    double uR = hR > dry_tol ? mnR / hR : 0.0, vR = hR > dry_tol ? mtR / hR : 0.0;
+    double Bm = BL > BR ? BL : BR;
+    double hLs = hL + BL - Bm, hRs = hR + BR - Bm;
+    if (hLs < 0.0) hLs = 0.0;
+    if (hRs < 0.0) hRs = 0.0;
+    double pL = 0.5 * g * (hL * hL), pR = 0.5 * g * (hR * hR);
+    double pLs = 0.5 * g * (hLs * hLs), pRs = 0.5 * g * (hRs * hRs);
+#if ORC_PLANT == 8
+    pLs = pL; pRs = pR;
+#endif
+#if ORC_PLANT == 6
+    double hLf = hL, hRf = hR, pLf = pL, pRf = pR;
+#else
+    double hLf = hLs, hRf = hRs, pLf = pLs, pRf = pRs;
+#endif
+    double FL[3] = {hLf * uL, hLf * uL * uL + pLf, hLf * uL * vL};
+    double FR[3] = {hRf * uR, hRf * uR * uR + pRf, hRf * uR * vR};
+    double QL[3] = {hLf, hLf * uL, hLf * vL}, QR[3] = {hRf, hRf * uR, hRf * vR};
+    double F[3] = {0.0, 0.0, 0.0};
+    if (hLf > 0.0 || hRf > 0.0) {
+        double cL = sqrt(g * hLf), cR = sqrt(g * hRf);
+        double sL = uL - cL < uR - cR ? uL - cL : uR - cR;
+        double sR = uL + cL > uR + cR ? uL + cL : uR + cR;
+        if (sL >= 0.0) {
+            for (int m = 0; m < 3; m++) F[m] = FL[m];
+        } else if (sR <= 0.0) {
+            for (int m = 0; m < 3; m++) F[m] = FR[m];
+        } else {
+            for (int m = 0; m < 3; m++)
+                F[m] = (sR * FL[m] - sL * FR[m] + sL * sR * (QR[m] - QL[m])) / (sR - sL);
+        }
+    }
+    double fL[3] = {mnL, mnL * uL + pL, mnL * vL}, fR[3] = {mnR, mnR * uR + pR, mnR * vR};
+    double SL[3] = {0.0, pL - pLs, 0.0}, SR[3] = {0.0, pR - pRs, 0.0};
+    for (int m = 0; m < 3; m++) {
+        w->amdq[m] = (F[m] + SL[m]) - fL[m];
+        w->apdq[m] = fR[m] - (F[m] + SR[m]);
+    }
+    w->shore = 1;
+    for (int p = 0; p < 3; p++) {
+        w->s[p] = 0.0;
+        for (int m = 0; m < 3; m++) w->Z[p][m] = 0.0;
+    }
+    w->uhat = 0.0; w->vhat = 0.0; w->chat = 0.0;
+}
+
+/*
+ * One forward edge: the Roe solver, or with wetdry the shore solver at an
+ * edge with a dry cell or a transonic rarefaction (u - c or u + c rising
+ * through zero from the left cell to the right one).
+ */
+static void fwd_edge(const orc_grid *G,
+                     double hL, double mnL, double mtL, double BL,
+                     double hR, double mnR, double mtR, double BR, edge_waves *w) {
+    if (G->wetdry) {
+        int shore = !(hL > G->dry_tol) || !(hR > G->dry_tol);
+#if ORC_PLANT != 7
+        if (!shore) {
+            double uL = mnL / hL, uR = mnR / hR;
+            double cL = sqrt(G->g * hL), cR = sqrt(G->g * hR);
+            shore = (uL - cL < 0.0 && uR - cR > 0.0) || (uL + cL < 0.0 && uR + cR > 0.0);
+        }
+#endif
+        if (shore) {
+            shore_riemann(G->g, G->dry_tol, hL, mnL, mtL, BL, hR, mnR, mtR, BR, w);
+            return;
+        }
+    }
+    fwd_riemann(G->g, hL, mnL, mtL, BL, hR, mnR, mtR, BR, w);
 }
 
 /*
@@ -262,6 +372,7 @@ static void fwd_riemann(double g,
 void orc_fwd_riemann(double g, double hL, double mnL, double mtL, double BL,
                      double hR, double mnR, double mtR, double BR, double *out) {
     edge_waves w;
+    memset(&w, 0, sizeof w);
     fwd_riemann(g, hL, mnL, mtL, BL, hR, mnR, mtR, BR, &w);
     for (int p = 0; p < 3; p++) out[p] = w.s[p];
     for (int p = 0; p < 3; p++)
@@ -301,9 +412,9 @@ static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double 
                 if (dir == 0) { a = pidx(G, i - 2 + e, j); b = pidx(G, i - 1 + e, j); }
                 else { a = pidx(G, i, j - 2 + e); b = pidx(G, i, j - 1 + e); }
                 if (dir == 0)
-                    fwd_riemann(G->g, ph[a], pu[a], pv[a], pB[a], ph[b], pu[b], pv[b], pB[b], &w[e]);
+                    fwd_edge(G, ph[a], pu[a], pv[a], pB[a], ph[b], pu[b], pv[b], pB[b], &w[e]);
                 else
-                    fwd_riemann(G->g, ph[a], pv[a], pu[a], pB[a], ph[b], pv[b], pu[b], pB[b], &w[e]);
+                    fwd_edge(G, ph[a], pv[a], pu[a], pB[a], ph[b], pv[b], pu[b], pB[b], &w[e]);
             }
             double amL[3], apL[3], FL[3], amR[3], apR[3], FR[3];
             edge_fluxes(3, &w[0], &w[1], &w[2], nu, G->order, amL, apL, FL);
@@ -315,6 +426,12 @@ static void fwd_sweep(const orc_grid *G, int dir, double *h, double *hu, double 
             nh[o] = ph[c] + dq[0];
             if (dir == 0) { nu_[o] = pu[c] + dq[1]; nv[o] = pv[c] + dq[2]; }
             else { nv[o] = pv[c] + dq[1]; nu_[o] = pu[c] + dq[2]; }
+            if (G->wetdry && !(nh[o] > G->dry_tol)) {
+                /* a dry cell keeps no momentum (and no negative depth) */
+                if (nh[o] < 0.0) nh[o] = 0.0;
+                nu_[o] = 0.0;
+                nv[o] = 0.0;
+            }
             if (phi_lo) {
                 /* mass flux through the cell's low and high edge of this sweep
                    as the cell's update sees it: dh = -nu (phi_hi - phi_lo) */
@@ -524,14 +641,18 @@ int orc_fwd_step_ctu(const orc_grid *G, double *h, double *hu, double *hv,
 int orc_fwd_step(const orc_grid *G, double *h, double *hu, double *hv,
                  const double *B, double dt) {
     size_t n = (size_t)G->nx * G->ny;
-    if (G->ndim == 2 && G->scheme == 1 && hv) return orc_fwd_step_ctu(G, h, hu, hv, B, dt);
+    if (G->ndim == 2 && G->scheme == 1 && hv) {
+        if (G->wetdry) return -1;   /* the shore solver is defined for the split step */
+        return orc_fwd_step_ctu(G, h, hu, hv, B, dt);
+    }
     double *v = hv;
     if (!hv) v = (double *)calloc(n, sizeof(double));
     fwd_sweep(G, 0, h, hu, v, B, dt, NULL, NULL);
     if (G->ndim == 2) fwd_sweep(G, 1, h, hu, v, B, dt, NULL, NULL);
     int bad = 0;
     for (size_t k = 0; k < n; k++)
-        if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(v[k])) bad = 1;
+        if (!(G->wetdry ? h[k] >= 0.0 : h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(v[k]))
+            bad = 1;
     if (!hv) free(v);
     return bad ? -5 : 0;
 }
@@ -552,7 +673,8 @@ int orc_fwd_step_flux(const orc_grid *G, double *h, double *hu, double *hv, cons
     fwd_sweep(G, 1, h, hu, hv, B, dt, phi_ylo, phi_yhi);
     int bad = 0;
     for (size_t k = 0; k < n; k++)
-        if (!(h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(hv[k])) bad = 1;
+        if (!(G->wetdry ? h[k] >= 0.0 : h[k] > 0.0) || !isfinite(hu[k]) || !isfinite(hv[k]))
+            bad = 1;
     return bad ? -5 : 0;
 }
 
@@ -565,6 +687,7 @@ double orc_fwd_smax(const orc_grid *G, const double *h, const double *hu,
     double smax = 0.0;
     size_t n = (size_t)G->nx * G->ny;
     for (size_t k = 0; k < n; k++) {
+        if (G->wetdry && !(h[k] > G->dry_tol)) continue;   /* dry: no waves */
         double c = sqrt(G->g * h[k]);
         double s = (fabs(hu[k] / h[k]) + c) / G->dx;
         if (G->ndim == 2) {
@@ -688,6 +811,7 @@ static void adj_riemann(double g, double eL, double mL, double hbL,
     double b1 = (dF1 + cR * dF2) / (cL + cR);
     double b2 = (cL * dF2 - dF1) / (cL + cR);
     w->s[0] = -cL; w->s[1] = cR; w->s[2] = 0.0;
+    w->shore = 0;
     w->Z[0][0] = b1 * cL;  w->Z[0][1] = b1;  w->Z[0][2] = 0.0;
     w->Z[1][0] = -b2 * cR; w->Z[1][1] = b2;  w->Z[1][2] = 0.0;
     w->Z[2][0] = 0.0;      w->Z[2][1] = 0.0; w->Z[2][2] = 0.0;
