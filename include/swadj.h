@@ -177,6 +177,30 @@ int swa_grid_set_rest_skip(swa_grid *g, int on);
 int swa_grid_set_scheme(swa_grid *grid, int scheme);
 
 /*
+ * Wet/dry option of the split step (on = 1; 0, the default, requires h > 0
+ * everywhere).  Sec. 6's solver reduces to the Roe solver away from the
+ * shore and handles inundation; the reading built here: at an edge with a
+ * dry cell (h <= desc.dry_tol) or a transonic rarefaction (u - c or u + c
+ * rising through zero from the left cell to the right one) the fluctuations
+ * come from the hydrostatic reconstruction of Audusse et al. (2004) with an
+ * HLL flux (speeds min/max of u -+ c over the reconstructed states), first
+ * order; every other edge keeps the Roe f-waves and their limited
+ * corrections.  After each sweep a cell at or below dry_tol keeps no
+ * momentum and no negative depth, and dry cells carry no waves in the CFL
+ * number.  Land is a cell with h = 0 (eta = B): set the state accordingly
+ * after turning the option on; a negative depth in the state set is
+ * reported as SWA_EUNSTABLE by the next swa_sync_status.  The ocean at rest
+ * against dry land stays exactly at rest, and the mass is conserved between
+ * walls as long as no depth goes negative, which the reconstruction
+ * guarantees for cfl <= 1/2 (above it a cell that would go negative is set
+ * dry, adding its deficit).  The option runs the tiled split kernel (FP64:
+ * the reference's rounding; FP32: the perturbation form), not the FP32
+ * strip kernel; with SWA_SCHEME_CTU a step returns SWA_EINVAL.  Host state
+ * only.
+ */
+int swa_grid_set_wetdry(swa_grid *grid, int on);
+
+/*
  * Device pointers of the current state arrays (read-only use), for gauge or
  * diagnostic kernels of the caller.  Synchronises (the current buffer is
  * device-resident).  precision tells the element type (double or float).

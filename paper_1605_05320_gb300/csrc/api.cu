@@ -173,6 +173,7 @@ struct swa_grid {
     int strip_rows;        // FP32 launch shape (0 = default)
     int keep_rest;         // FP32 2D: compute wave-free rows in full
     int scheme;            // 2D update: SWA_SCHEME_SPLIT or SWA_SCHEME_CTU
+    int wetdry;            // split step with the shore solver (dry cells allowed)
     long long *gauge_row;  // device row counter of the fused gauge recording
     GaugeRec gauges;       // fused gauge recording (n = 0: off)
 };
@@ -192,12 +193,23 @@ static int grid_step_blocks(const swa_grid_desc *d) {
 // for the unsplit step's tiles if there are more of those.
 static int grid_max_blocks(const swa_grid_desc *d) {
     int b = grid_step_blocks(d);
+    int w;
+    if (d->precision == SWA_FP32) {
+        FwdParams<float> p{};
+        p.nx = d->nx; p.ny = d->ny; p.two_d = d->ndim == 2;
+        w = fwd_wd_blocks<float>(p);
+    } else {
+        FwdParams<double> p{};
+        p.nx = d->nx; p.ny = d->ny; p.two_d = d->ndim == 2;
+        w = fwd_wd_blocks<double>(p);
+    }
+    if (w > b) b = w;
     if (d->ndim != 2) return b;
     int c;
     if (d->precision == SWA_FP32) {
         FwdParams<float> p{};
         p.nx = d->nx; p.ny = d->ny; p.two_d = 1; p.fwd_rows = SWA_MIN_STRIP_ROWS;
-        b = fwd_step_blocks<float>(p);
+        if (fwd_step_blocks<float>(p) > b) b = fwd_step_blocks<float>(p);
         c = fwd_ctu_blocks<float>(p);
     } else {
         FwdParams<double> p{};
@@ -261,6 +273,8 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.fwd_rows = g->strip_rows;
     p.keep_rest = g->keep_rest;
     p.gauges = g->gauges;
+    p.wetdry = g->wetdry;
+    p.dry_tol = (R)g->d.dry_tol;
     return p;
 }
 
@@ -292,6 +306,9 @@ size_t swa_grid_workspace_bytes(const swa_grid_desc *desc) {
     grid_layout(desc, c, nullptr);
     return c.off + 256;
 }
+
+static int set_state_impl(swa_grid *g, const double *eta, const double *hu, const double *hv,
+                          double t, int where, void *stream, bool check);
 
 int swa_create_grid(const swa_grid_desc *desc, const double *bathy_host, void *ws,
                     size_t ws_bytes, void *stream, swa_grid **out) {
@@ -331,7 +348,7 @@ int swa_create_grid(const swa_grid_desc *desc, const double *bathy_host, void *w
     if (rc == SWA_OK) rc = cuda_check(cudaStreamSynchronize(st), "create_grid");
     if (rc != SWA_OK) { delete g; return rc; }
     *out = g;
-    rc = swa_set_state(g, g->staging, g->staging, g->staging, 0.0, SWA_DEVICE, stream);
+    rc = set_state_impl(g, g->staging, g->staging, g->staging, 0.0, SWA_DEVICE, stream, false);
     if (rc != SWA_OK) { delete g; *out = nullptr; return rc; }
     return SWA_OK;
 }
@@ -341,8 +358,10 @@ int swa_destroy_grid(swa_grid *grid) {
     return SWA_OK;
 }
 
-int swa_set_state(swa_grid *g, const double *eta, const double *hu, const double *hv,
-                  double t, int where, void *stream) {
+// check = false: the ocean at rest a new grid starts from, whose land cells
+// (if any) have no valid depth yet, reports nothing to the error word.
+static int set_state_impl(swa_grid *g, const double *eta, const double *hu, const double *hv,
+                          double t, int where, void *stream, bool check) {
     if (!g || !eta || !hu) return set_error(SWA_EINVAL, "null argument");
     if (g->d.ndim == 2 && !hv) return set_error(SWA_EINVAL, "hv required for 2D grids");
     if (where != SWA_HOST && where != SWA_DEVICE) return set_error(SWA_EINVAL, "bad where");
@@ -365,12 +384,22 @@ int swa_set_state(swa_grid *g, const double *eta, const double *hu, const double
         TRY(cuda_check(cudaMemsetAsync(g->q[0][2], 0, g->n * g->esz, st), "hv clear"));
     }
     TRY(cuda_check(cudaMemsetAsync(g->q[1][2], 0, g->n * g->esz, st), "hv clear"));
-    if (g->d.precision == SWA_FP64)
-        TRY(fwd_launch_clock_init<double>(fwd_params<double>(g, 0.0), t, st));
-    else
-        TRY(fwd_launch_clock_init<float>(fwd_params<float>(g, 0.0), t, st));
+    if (g->d.precision == SWA_FP64) {
+        FwdParams<double> p = fwd_params<double>(g, 0.0);
+        if (!check) p.err = nullptr;
+        TRY(fwd_launch_clock_init<double>(p, t, st));
+    } else {
+        FwdParams<float> p = fwd_params<float>(g, 0.0);
+        if (!check) p.err = nullptr;
+        TRY(fwd_launch_clock_init<float>(p, t, st));
+    }
     g->state_set = 1;
     return SWA_OK;
+}
+
+int swa_set_state(swa_grid *g, const double *eta, const double *hu, const double *hv,
+                  double t, int where, void *stream) {
+    return set_state_impl(g, eta, hu, hv, t, where, stream, true);
 }
 
 int swa_get_state(swa_grid *g, double *h, double *hu, double *hv, double *eta, int where,
@@ -418,14 +447,18 @@ int swa_step_forward(swa_grid *g, int max_steps, double t_end, void *stream) {
     if (!g->state_set) return set_error(SWA_ESTATE, "state not set");
     cudaStream_t st = S(stream);
     const bool ctu = g->scheme == SWA_SCHEME_CTU && g->d.ndim == 2;
+    if (ctu && g->wetdry)
+        return set_error(SWA_EINVAL, "the wet/dry option needs the split scheme");
     if (g->d.precision == SWA_FP64) {
         const FwdParams<double> p = fwd_params<double>(g, t_end);
         for (int k = 0; k < max_steps; k++)
-            TRY(ctu ? fwd_launch_ctu<double>(p, st) : fwd_launch_step<double>(p, st));
+            TRY(ctu ? fwd_launch_ctu<double>(p, st)
+                    : g->wetdry ? fwd_launch_wd<double>(p, st) : fwd_launch_step<double>(p, st));
     } else {
         const FwdParams<float> p = fwd_params<float>(g, t_end);
         for (int k = 0; k < max_steps; k++)
-            TRY(ctu ? fwd_launch_ctu<float>(p, st) : fwd_launch_step<float>(p, st));
+            TRY(ctu ? fwd_launch_ctu<float>(p, st)
+                    : g->wetdry ? fwd_launch_wd<float>(p, st) : fwd_launch_step<float>(p, st));
     }
     return SWA_OK;
 }
@@ -454,6 +487,13 @@ int swa_grid_set_rest_skip(swa_grid *g, int on) {
     if (!g) return set_error(SWA_EINVAL, "null grid");
     if (on != 0 && on != 1) return set_error(SWA_EINVAL, "rest skip must be 0 or 1");
     g->keep_rest = !on;
+    return SWA_OK;
+}
+
+int swa_grid_set_wetdry(swa_grid *g, int on) {
+    if (!g) return set_error(SWA_EINVAL, "null grid");
+    if (on != 0 && on != 1) return set_error(SWA_EINVAL, "wet/dry must be 0 or 1");
+    g->wetdry = on;
     return SWA_OK;
 }
 

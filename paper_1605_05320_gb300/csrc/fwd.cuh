@@ -23,6 +23,8 @@ struct FwdParams {
     int fwd_rows;      // FP32 strip height (rows per block), 0 = default
     int keep_rest;     // FP32 2D: 1 computes wave-free rows in full (no skipping)
     GaugeRec gauges;   // fused gauge recording (n = 0: off)
+    int wetdry;        // 1: the shore solver at dry and transonic edges
+    R dry_tol;         // a cell with h <= dry_tol is dry
 };
 
 template <typename R>
@@ -44,6 +46,15 @@ template <> int fwd_launch_ctu<double>(const FwdParams<double> &, cudaStream_t);
 template <> int fwd_launch_ctu<float>(const FwdParams<float> &, cudaStream_t);
 template <> int fwd_ctu_blocks<double>(const FwdParams<double> &);
 template <> int fwd_ctu_blocks<float>(const FwdParams<float> &);
+// split step with the shore solver (fwd_kernels.cuh, WD)
+template <typename R>
+int fwd_launch_wd(const FwdParams<R> &p, cudaStream_t st);
+template <typename R>
+int fwd_wd_blocks(const FwdParams<R> &p);
+template <> int fwd_launch_wd<double>(const FwdParams<double> &, cudaStream_t);
+template <> int fwd_launch_wd<float>(const FwdParams<float> &, cudaStream_t);
+template <> int fwd_wd_blocks<double>(const FwdParams<double> &);
+template <> int fwd_wd_blocks<float>(const FwdParams<float> &);
 template <> int fwd_launch_clock_init<double>(const FwdParams<double> &, double, cudaStream_t);
 template <> int fwd_launch_clock_init<float>(const FwdParams<float> &, double, cudaStream_t);
 

@@ -176,6 +176,29 @@ int fwd_step_blocks<float>(const FwdParams<float> &p) {
     return (p.nx + 255) / 256;
 }
 
+// The wet/dry option runs the tiled split step (fwd_kernels.cuh) with the
+// shore solver, in the perturbation form.
+template <>
+int fwd_launch_wd<float>(const FwdParams<float> &p0, cudaStream_t st) {
+    FwdParams<float> p = p0;
+    if (p.two_d) {
+        dim3 grid((p.nx + 31) / 32, (p.ny + 3) / 4);
+        p.nblocks = (int)(grid.x * grid.y);
+        fwd_step_kernel<float, true, true, 32, 4, true><<<grid, dim3(32, 4), 0, st>>>(p);
+    } else {
+        dim3 grid((p.nx + 127) / 128, 1);
+        p.nblocks = (int)grid.x;
+        fwd_step_kernel<float, true, false, 128, 1, true><<<grid, dim3(128, 1), 0, st>>>(p);
+    }
+    return swadj_host::cuda_check(cudaGetLastError(), "fwd_step_kernel<float, wet/dry>");
+}
+
+template <>
+int fwd_wd_blocks<float>(const FwdParams<float> &p) {
+    if (p.two_d) return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
+    return (p.nx + 127) / 128;
+}
+
 template <>
 int fwd_launch_ctu<float>(const FwdParams<float> &p, cudaStream_t st) {
     return ctu_launch<float, true, 32, 16>(p, st, "fwd_ctu_kernel<float>");

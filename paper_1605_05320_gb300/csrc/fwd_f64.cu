@@ -9,11 +9,11 @@
 
 namespace swadj {
 
-template <typename R, bool PERT, bool TWO_D, int TX, int TY>
+template <typename R, bool PERT, bool TWO_D, int TX, int TY, bool WD = false>
 static int launch_step(FwdParams<R> p, cudaStream_t st) {
     dim3 grid((p.nx + TX - 1) / TX, TWO_D ? (p.ny + TY - 1) / TY : 1);
     p.nblocks = (int)(grid.x * grid.y);
-    fwd_step_kernel<R, PERT, TWO_D, TX, TY><<<grid, dim3(TX, TY), 0, st>>>(p);
+    fwd_step_kernel<R, PERT, TWO_D, TX, TY, WD><<<grid, dim3(TX, TY), 0, st>>>(p);
     return swadj_host::cuda_check(cudaGetLastError(), "fwd_step_kernel<double>");
 }
 
@@ -27,6 +27,17 @@ template <>
 int fwd_step_blocks<double>(const FwdParams<double> &p) {
     if (p.two_d) return ((p.nx + 31) / 32) * ((p.ny + 3) / 4);
     return (p.nx + 127) / 128;
+}
+
+template <>
+int fwd_launch_wd<double>(const FwdParams<double> &p, cudaStream_t st) {
+    if (p.two_d) return launch_step<double, false, true, 32, 4, true>(p, st);
+    return launch_step<double, false, false, 128, 1, true>(p, st);
+}
+
+template <>
+int fwd_wd_blocks<double>(const FwdParams<double> &p) {
+    return fwd_step_blocks<double>(p);
 }
 
 template <>

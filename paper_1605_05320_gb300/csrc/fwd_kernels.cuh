@@ -38,6 +38,67 @@ __device__ __forceinline__ void fwave_roe(R g, R hL, R mnL, R mtL, R unL, R utL,
     b2 = df3 - vhat * df1;
 }
 
+// Shore solver (the wet/dry option; the reading of Sec. 6's solver, robust
+// near shore and inundation and Roe away from it): at an edge with a dry
+// cell (h <= dry_tol) or a transonic rarefaction (u - c or u + c rising
+// through zero from the left cell to the right one) the fluctuations come
+// from the hydrostatic reconstruction of Audusse et al. (2004) with an HLL
+// flux, first order.  h*_L = max(0, eta_L - max(B_L, B_R)), h*_R likewise,
+// cell velocities (zero in a dry cell), speeds s_L = min(u_L - c_L, u_R -
+// c_R), s_R = max(u_L + c_L, u_R + c_R) over the reconstructed states;
+//   amdq = F + (0, g/2 (h_L^2 - h*_L^2), 0) - f(Q_L),
+//   apdq = f(Q_R) - F - (0, g/2 (h_R^2 - h*_R^2), 0),
+// F the HLL flux of the reconstructed states, f the physical flux.  Every
+// expression in the order of the FP64 reference solver.
+template <typename R>
+__device__ __forceinline__ bool shore_edge(R g, R tol, R hL, R mnL, R hR, R mnR) {
+    if (!(hL > tol) || !(hR > tol)) return true;
+    const R uL = mnL / hL, uR = mnR / hR;
+    const R cL = sqrt(g * hL), cR = sqrt(g * hR);
+    return (uL - cL < R(0) && uR - cR > R(0)) || (uL + cL < R(0) && uR + cR > R(0));
+}
+
+template <typename R>
+__device__ __forceinline__ void shore_fluct(R g, R tol, R hL, R mnL, R mtL, R etaL, R BL,
+                                            R hR, R mnR, R mtR, R etaR, R BR, R am[3],
+                                            R ap[3]) {
+    const R uL = hL > tol ? mnL / hL : R(0), vL = hL > tol ? mtL / hL : R(0);
+    const R uR = hR > tol ? mnR / hR : R(0), vR = hR > tol ? mtR / hR : R(0);
+    const R Bm = BL > BR ? BL : BR;
+    R hLs = etaL - Bm, hRs = etaR - Bm;
+    if (hLs < R(0)) hLs = R(0);
+    if (hRs < R(0)) hRs = R(0);
+    const R pL = R(0.5) * g * (hL * hL), pR = R(0.5) * g * (hR * hR);
+    const R pLs = R(0.5) * g * (hLs * hLs), pRs = R(0.5) * g * (hRs * hRs);
+    const R FL[3] = {hLs * uL, hLs * uL * uL + pLs, hLs * uL * vL};
+    const R FR[3] = {hRs * uR, hRs * uR * uR + pRs, hRs * uR * vR};
+    const R QL[3] = {hLs, hLs * uL, hLs * vL}, QR[3] = {hRs, hRs * uR, hRs * vR};
+    R F[3] = {R(0), R(0), R(0)};
+    if (hLs > R(0) || hRs > R(0)) {
+        const R cL = sqrt(g * hLs), cR = sqrt(g * hRs);
+        const R sL = uL - cL < uR - cR ? uL - cL : uR - cR;
+        const R sR = uL + cL > uR + cR ? uL + cL : uR + cR;
+        if (sL >= R(0)) {
+#pragma unroll
+            for (int m = 0; m < 3; m++) F[m] = FL[m];
+        } else if (sR <= R(0)) {
+#pragma unroll
+            for (int m = 0; m < 3; m++) F[m] = FR[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < 3; m++)
+                F[m] = (sR * FL[m] - sL * FR[m] + sL * sR * (QR[m] - QL[m])) / (sR - sL);
+        }
+    }
+    const R fL[3] = {mnL, mnL * uL + pL, mnL * vL}, fR[3] = {mnR, mnR * uR + pR, mnR * vR};
+    const R SL[3] = {R(0), pL - pLs, R(0)}, SR[3] = {R(0), pR - pRs, R(0)};
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        am[m] = (F[m] + SL[m]) - fL[m];
+        ap[m] = fR[m] - (F[m] + SR[m]);
+    }
+}
+
 // Fluctuations amdq (to the left cell), apdq (to the right cell) and the
 // second-order correction flux F at edge e, from the waves at e and at its
 // left/right neighbour edges (indices into wave arrays W[6][stride]).
@@ -110,7 +171,10 @@ __device__ __forceinline__ void edge_flux(const Wave6<R> &wm, const Wave6<R> &w,
 // x-sweep equals the x-sweep of the mirrored/copied interior row, which is
 // what ghost cells of the x-swept state hold.  Expressions follow the FP64
 // reference in order, so with contraction disabled the rounding matches it.
-template <typename R, bool PERT, bool TWO_D, int TX, int TY>
+// WD: the wet/dry option (shore solver at dry and transonic edges, a cell
+// at or below dry_tol keeps no momentum and no negative depth after each
+// sweep, dry cells carry no waves in the CFL number).
+template <typename R, bool PERT, bool TWO_D, int TX, int TY, bool WD = false>
 __global__ void __launch_bounds__(TX *TY)
 fwd_step_kernel(FwdParams<R> p) {
     constexpr int HX = 2, HY = TWO_D ? 2 : 0;
@@ -143,6 +207,7 @@ fwd_step_kernel(FwdParams<R> p) {
     R *o0 = p.q[cur ^ 1][0], *o1 = p.q[cur ^ 1][1], *o2 = p.q[cur ^ 1][2];
     const int nx = p.nx, ny = p.ny;
     const int i0 = blockIdx.x * TX - HX, j0 = blockIdx.y * TY - HY;
+    const R tol = p.dry_tol;
 
     // 1) tile + halo with corners into shared memory, ghost cells by mapping
     for (int r = tid; r < RX * RY; r += NT) {
@@ -162,22 +227,31 @@ fwd_step_kernel(FwdParams<R> p) {
         s_mu[ry][rx] = mu;
         s_mv[ry][rx] = mv;
         s_eta[ry][rx] = eta;
-        s_u[ry][rx] = mu / h;
-        s_v[ry][rx] = mv / h;
+        const bool wet = !WD || h > tol;
+        s_u[ry][rx] = wet ? mu / h : R(0);
+        s_v[ry][rx] = wet ? mv / h : R(0);
         s_sq[ry][rx] = sqrt(h);
         s_b[ry][rx] = b;
     }
     __syncthreads();
+    // bottom elevation of a staged cell (the shore solver's reconstruction)
+    auto bot = [&](int ry, int rx) { return PERT ? -s_b[ry][rx] : s_b[ry][rx]; };
 
     // 2) x-edge waves of every staged row
     for (int e = tid; e < RY * NEX; e += NT) {
         const int ry = e / NEX, k = e - ry * NEX;
         Wave6<R> w;
-        fwave_roe<R>(p.g, s_h[ry][k], s_mu[ry][k], s_mv[ry][k], s_u[ry][k],
-                     s_v[ry][k], s_sq[ry][k], s_eta[ry][k], s_h[ry][k + 1],
-                     s_mu[ry][k + 1], s_mv[ry][k + 1], s_u[ry][k + 1],
-                     s_v[ry][k + 1], s_sq[ry][k + 1], s_eta[ry][k + 1], w.uh,
-                     w.ch, w.b1, w.b2, w.b3, w.vh);
+        if (WD && shore_edge<R>(p.g, tol, s_h[ry][k], s_mu[ry][k], s_h[ry][k + 1],
+                                s_mu[ry][k + 1])) {
+            // a shore edge: no waves for the neighbours' limiters (ch < 0 marks it)
+            w.uh = R(0); w.ch = R(-1); w.b1 = R(0); w.b2 = R(0); w.b3 = R(0); w.vh = R(0);
+        } else {
+            fwave_roe<R>(p.g, s_h[ry][k], s_mu[ry][k], s_mv[ry][k], s_u[ry][k],
+                         s_v[ry][k], s_sq[ry][k], s_eta[ry][k], s_h[ry][k + 1],
+                         s_mu[ry][k + 1], s_mv[ry][k + 1], s_u[ry][k + 1],
+                         s_v[ry][k + 1], s_sq[ry][k + 1], s_eta[ry][k + 1], w.uh,
+                         w.ch, w.b1, w.b2, w.b3, w.vh);
+        }
         wb.x[ry][k] = w;
     }
     __syncthreads();
@@ -189,8 +263,21 @@ fwd_step_kernel(FwdParams<R> p) {
     for (int ry = ty; ry < RY; ry += TY) {
         const int cx = tx + HX;
         R am0[3], ap0[3], F0[3], am1[3], ap1[3], F1[3];
-        edge_flux<R>(wb.x[ry][tx], wb.x[ry][tx + 1], wb.x[ry][tx + 2], nux, p.order, am0, ap0, F0);
-        edge_flux<R>(wb.x[ry][tx + 1], wb.x[ry][tx + 2], wb.x[ry][tx + 3], nux, p.order, am1, ap1, F1);
+        // edge k of a staged row joins cells k and k + 1
+        auto xedge = [&](int k, R am[3], R ap[3], R F[3]) {
+            if (WD && wb.x[ry][k].ch < R(0)) {
+                shore_fluct<R>(p.g, tol, s_h[ry][k], s_mu[ry][k], s_mv[ry][k], s_eta[ry][k],
+                               bot(ry, k), s_h[ry][k + 1], s_mu[ry][k + 1], s_mv[ry][k + 1],
+                               s_eta[ry][k + 1], bot(ry, k + 1), am, ap);
+#pragma unroll
+                for (int m = 0; m < 3; m++) F[m] = R(0);
+            } else {
+                edge_flux<R>(wb.x[ry][k - 1], wb.x[ry][k], wb.x[ry][k + 1], nux, p.order, am,
+                             ap, F);
+            }
+        };
+        xedge(tx + 1, am0, ap0, F0);
+        xedge(tx + 2, am1, ap1, F1);
         R dq[3];
 #pragma unroll
         for (int m = 0; m < 3; m++) dq[m] = -nux * (ap0[m] + am1[m]) - nux * (F1[m] - F0[m]);
@@ -213,8 +300,16 @@ fwd_step_kernel(FwdParams<R> p) {
                 h = xs[0][k];
                 eta = h + s_b[ry][cx];
             }
-            const R mu = xs[1][k], mv = xs[2][k];
+            R mu = xs[1][k], mv = xs[2][k];
             k++;
+            if (WD && !(h > tol)) {   // a dry cell keeps no momentum, no negative depth
+                if (h < R(0)) {
+                    h = R(0);
+                    eta = PERT ? -s_b[ry][cx] : s_b[ry][cx];
+                }
+                mu = R(0);
+                mv = R(0);
+            }
             if (!TWO_D) {  // 1D: the x-swept state is the new state
                 s_h[ry][cx] = h; s_eta[ry][cx] = eta; s_mu[ry][cx] = mu; s_mv[ry][cx] = mv;
                 continue;
@@ -223,8 +318,9 @@ fwd_step_kernel(FwdParams<R> p) {
             s_mu[ry][cx] = mu;
             s_mv[ry][cx] = mv;
             s_eta[ry][cx] = eta;
-            s_u[ry][cx] = mu / h;
-            s_v[ry][cx] = mv / h;
+            const bool wet = !WD || h > tol;
+            s_u[ry][cx] = wet ? mu / h : R(0);
+            s_v[ry][cx] = wet ? mv / h : R(0);
             s_sq[ry][cx] = sqrt(h);
         }
     }
@@ -239,19 +335,37 @@ fwd_step_kernel(FwdParams<R> p) {
         for (int e = tid; e < NEY * TX; e += NT) {
             const int k = e / TX, col = e - k * TX, rx = col + HX;
             Wave6<R> w;
-            fwave_roe<R>(p.g, s_h[k][rx], s_mv[k][rx], s_mu[k][rx], s_v[k][rx],
-                         s_u[k][rx], s_sq[k][rx], s_eta[k][rx], s_h[k + 1][rx],
-                         s_mv[k + 1][rx], s_mu[k + 1][rx], s_v[k + 1][rx],
-                         s_u[k + 1][rx], s_sq[k + 1][rx], s_eta[k + 1][rx], w.uh,
-                         w.ch, w.b1, w.b2, w.b3, w.vh);
+            if (WD && shore_edge<R>(p.g, tol, s_h[k][rx], s_mv[k][rx], s_h[k + 1][rx],
+                                    s_mv[k + 1][rx])) {
+                w.uh = R(0); w.ch = R(-1); w.b1 = R(0); w.b2 = R(0); w.b3 = R(0); w.vh = R(0);
+            } else {
+                fwave_roe<R>(p.g, s_h[k][rx], s_mv[k][rx], s_mu[k][rx], s_v[k][rx],
+                             s_u[k][rx], s_sq[k][rx], s_eta[k][rx], s_h[k + 1][rx],
+                             s_mv[k + 1][rx], s_mu[k + 1][rx], s_v[k + 1][rx],
+                             s_u[k + 1][rx], s_sq[k + 1][rx], s_eta[k + 1][rx], w.uh,
+                             w.ch, w.b1, w.b2, w.b3, w.vh);
+            }
             wb.y[k][col] = w;
         }
         __syncthreads();
         // 5) y-sweep (edge frame (h, hv, hu))
         const R nuy = R(dt) / p.dy;
         R bm0[3], bp0[3], G0[3], bm1[3], bp1[3], G1[3];
-        edge_flux<R>(wb.y[ty][tx], wb.y[ty + 1][tx], wb.y[ty + 2][tx], nuy, p.order, bm0, bp0, G0);
-        edge_flux<R>(wb.y[ty + 1][tx], wb.y[ty + 2][tx], wb.y[ty + 3][tx], nuy, p.order, bm1, bp1, G1);
+        // y-edge k of the tile column joins staged rows k and k + 1
+        auto yedge = [&](int k, R am[3], R ap[3], R F[3]) {
+            if (WD && wb.y[k][tx].ch < R(0)) {
+                shore_fluct<R>(p.g, tol, s_h[k][cx], s_mv[k][cx], s_mu[k][cx], s_eta[k][cx],
+                               bot(k, cx), s_h[k + 1][cx], s_mv[k + 1][cx], s_mu[k + 1][cx],
+                               s_eta[k + 1][cx], bot(k + 1, cx), am, ap);
+#pragma unroll
+                for (int m = 0; m < 3; m++) F[m] = R(0);
+            } else {
+                edge_flux<R>(wb.y[k - 1][tx], wb.y[k][tx], wb.y[k + 1][tx], nuy, p.order, am, ap,
+                             F);
+            }
+        };
+        yedge(ty + 1, bm0, bp0, G0);
+        yedge(ty + 2, bm1, bp1, G1);
         R d[3];
 #pragma unroll
         for (int m = 0; m < 3; m++) d[m] = -nuy * (bp0[m] + bm1[m]) - nuy * (G1[m] - G0[m]);
@@ -268,11 +382,20 @@ fwd_step_kernel(FwdParams<R> p) {
     double s_cell = 0.0;
     if (valid) {
         const size_t o = (size_t)gj * nx + gi;
-        const R hn = PERT ? n0 + p.bath[o] : n0;
+        R hn = PERT ? n0 + p.bath[o] : n0;
+        if (WD && !(hn > tol)) {   // a dry cell keeps no momentum, no negative depth
+            if (hn < R(0)) {
+                hn = R(0);
+                n0 = PERT ? -p.bath[o] : R(0);
+            }
+            n1 = R(0);
+            n2 = R(0);
+        }
         o0[o] = n0;
         o1[o] = n1;
         if (TWO_D) o2[o] = n2;
-        if (!(hn > R(0)) || !isfinite(n1) || !isfinite(n2)) atomicOr(p.err, ERR_UNSTABLE);
+        if (!(WD ? hn >= R(0) : hn > R(0)) || !isfinite(n1) || !isfinite(n2))
+            atomicOr(p.err, ERR_UNSTABLE);
         // CFL number of the new state: max over directions of (|u|+c)/d
         const R c = sqrt(p.g * hn);
         R s = (fabs(n1 / hn) + c) / p.dx;
@@ -281,7 +404,7 @@ fwd_step_kernel(FwdParams<R> p) {
             if (sy > s) s = sy;
         }
         s_cell = (double)s;
-        if (!(s_cell >= 0.0)) s_cell = 0.0;
+        if (!(s_cell >= 0.0) || (WD && !(hn > tol))) s_cell = 0.0;
     }
 
     // 6) block max -> partial, last block reduces and advances the clock
@@ -326,6 +449,10 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
     for (size_t k = (size_t)blockIdx.x * 256 + tid; k < n; k += (size_t)gridDim.x * 256) {
         const R h = PERT ? q0[k] + p.bath[k] : q0[k];
         double sd;
+        if (p.wetdry && !(h > p.dry_tol)) {
+            if (p.err && !(h >= R(0))) atomicOr(p.err, ERR_UNSTABLE);
+            continue;   // a dry cell carries no waves
+        }
         if (PERT) {
             // the float rule of the fused step reduction (cfl_f32)
             sd = (double)cfl_f32((float)h, (float)q1[k], p.two_d ? (float)q2[k] : 0.f,
@@ -339,7 +466,7 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
             }
             sd = (double)s;
         }
-        if (!(h > R(0))) atomicOr(p.err, ERR_UNSTABLE);
+        if (p.err && !(h > R(0))) atomicOr(p.err, ERR_UNSTABLE);
         mx = sd > mx ? sd : mx;
     }
     const double bm = block_max<256>(mx, red);

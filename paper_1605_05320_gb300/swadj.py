@@ -50,7 +50,7 @@ EXPORTS = [
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
-    "swa_amr_set_reflux", "swa_amr_info", "swa_amr_levels_workspace_bytes",
+    "swa_amr_set_reflux", "swa_amr_info", "swa_grid_set_wetdry", "swa_amr_levels_workspace_bytes",
     "swa_create_amr_levels",
     "swa_alu_probe_ops", "swa_alu_probe",
     "swa_grid_mass",
@@ -160,6 +160,7 @@ def load(path: str = LIB_PATH):
         "swa_destroy_amr": ([_V], _I),
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
         "swa_amr_set_reflux": ([_V, _I], _I),
+        "swa_grid_set_wetdry": ([_V, _I], _I),
         "swa_amr_info": ([_V, _I, _P(_I), _P(_I), _P(_I)], _I),
         "swa_amr_levels_workspace_bytes": ([_V, _V, _I, _P(_I), _P(_I)], _SZ),
         "swa_create_amr_levels": ([_V, _V, _I, _P(_I), _P(_I), _V, _SZ, _V, _P(_V)], _I),
@@ -262,6 +263,10 @@ def swa_grid_set_rest_skip(h, on):
 
 def swa_grid_set_scheme(h, scheme):
     return _chk(load().swa_grid_set_scheme(h, int(scheme)))
+
+
+def swa_grid_set_wetdry(h, on):
+    return _chk(load().swa_grid_set_wetdry(h, int(bool(on))))
 
 
 def swa_grid_arrays(h, stream=None):
@@ -534,6 +539,9 @@ class Grid:
 
     def set_scheme(self, scheme):
         swa_grid_set_scheme(self.h, scheme)
+
+    def set_wetdry(self, on):
+        swa_grid_set_wetdry(self.h, on)
 
     def time(self, stream=None):
         return swa_get_time(self.h, stream)
