@@ -414,7 +414,13 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) * 1e3 / k
 
+    # the fine level's strip height, tuned on a copy (tuning steps it)
+    from paper_1605_05320_gb300 import tune
+    g2, ps2, _ = hierarchy()
+    with torch.cuda.stream(stream):
+        rows = tune.tune_patches(ps2)[1]
     g, ps, amr = hierarchy()
+    S.swa_patches_set_tile_rows(ps.h, 1, rows)
     clock = {"t": 0.0}
 
     def one_step():
@@ -430,7 +436,6 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     if S.swa_sync_status(hs) != 0:
         raise RuntimeError("AMR hierarchy step reported an error")
     nfill, navg, nedges = amr.info()
-    g2, ps2, _ = hierarchy()
     us_coarse = timed(lambda: g2.step(1, 1e12, hs), steps)
     us_fine = timed(lambda: ps2.step(1, 1, 1e300, hs), steps * ratio)
     if S.swa_sync_status(hs) != 0:
@@ -442,6 +447,7 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
             "fine_launch_us": round(us_fine, 1),
             "glue_us_per_step": round(us_step - us_coarse - ratio * us_fine, 1),
             "ring_cells": nfill, "covered_coarse_cells": navg, "coarse_fine_edges": nedges,
+            "fine_strip_rows": rows,
             "us_per_step_without_refluxing": round(us_plain, 1),
             "cell_updates_per_s": updates / (us_step * 1e-6)}
 

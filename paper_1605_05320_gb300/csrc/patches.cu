@@ -684,10 +684,10 @@ __device__ __forceinline__ float minmod(float a, float b) {
 
 struct FillParams {
     const PatchDevice *table;
+    const PatchDevice *coarse;   // the coarse grid's buffers, as a patch without ring
     const DevClock *lclk;   // this level
     const DevClock *pclk;   // its parent: the coarse grid's clock at l = 1
-    float *cq[2][3];        // the coarse grid's buffers (eta, hu, hv)
-    int nxc, nyc, r;
+    int r;
     const int4 *fill;
     const int *par;         // parent patch per entry (-1: the coarse grid)
     int nfill;
@@ -698,10 +698,10 @@ struct FillParams {
 // in time between its buffers before and after its step (alpha = (t - t_p) /
 // dt_p in [0, 1]) then limited linear in space within the parent cell
 // (minmod slopes from the parent's array, zero where a neighbour lies
-// outside it: the domain edge of the coarse grid).  One thread per (entry,
-// component); the clocks and alpha (FP64) are read and formed once per
-// block.
-__global__ void amr_fill_kernel(FillParams p) {
+// outside it: the domain edge of the coarse grid).  One thread per ring
+// cell, the three components in turn (independent loads); the clocks and
+// alpha (FP64) are read and formed once per block.
+__global__ void __launch_bounds__(128) amr_fill_kernel(FillParams p) {
     __shared__ float s_a;
     __shared__ int s_fcur, s_pcur;
     if (threadIdx.x == 0) {
@@ -716,34 +716,33 @@ __global__ void amr_fill_kernel(FillParams p) {
     const float af = s_a;
     const int fcur = s_fcur, pcur = s_pcur;
     const int r = p.r;
-    const int n = 3 * p.nfill;
-    for (int e3 = blockIdx.x * blockDim.x + threadIdx.x; e3 < n; e3 += gridDim.x * blockDim.x) {
-        const int e = e3 / 3, k = e3 - 3 * e;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nfill; e += gridDim.x * blockDim.x) {
         const int4 m = __ldg(p.fill + e);
-        float *dst = p.table[m.x].q[fcur][k];
+        const PatchDevice &D = p.table[m.x];
         if (m.z >= 0) {
-            dst[m.y] = p.table[m.z].q[fcur][k][m.w];
+            const PatchDevice &Sb = p.table[m.z];
+#pragma unroll
+            for (int k = 0; k < 3; k++) D.q[fcur][k][m.y] = Sb.q[fcur][k][m.w];
             continue;
         }
         const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
         const int par = __ldg(p.par + e);
-        const float *o, *nw;
-        int nx, ny;
-        if (par < 0) {
-            o = p.cq[pcur ^ 1][k]; nw = p.cq[pcur][k]; nx = p.nxc; ny = p.nyc;
-        } else {
-            const PatchDevice &Q = p.table[par];
-            o = Q.q[pcur ^ 1][k]; nw = Q.q[pcur][k]; nx = Q.nx; ny = Q.ny;
-        }
+        const PatchDevice &Q = par < 0 ? *p.coarse : p.table[par];
+        const int nx = Q.nx, ny = Q.ny;
         const int c = m.w, ic = c % nx, jc = c / nx;
         const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
         const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
-        auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
-        const float qc = at(c);
-        float s_x = 0.f, s_y = 0.f;
-        if (ic > 0 && ic < nx - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
-        if (jc > 0 && jc < ny - 1) s_y = minmod(qc - at(c - nx), at(c + nx) - qc);
-        dst[m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
+        const bool inx = ic > 0 && ic < nx - 1, iny = jc > 0 && jc < ny - 1;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float *o = Q.q[pcur ^ 1][k], *nw = Q.q[pcur][k];
+            auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
+            const float qc = at(c);
+            float s_x = 0.f, s_y = 0.f;
+            if (inx) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
+            if (iny) s_y = minmod(qc - at(c - nx), at(c + nx) - qc);
+            D.q[fcur][k][m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
+        }
     }
 }
 
@@ -766,8 +765,8 @@ __device__ __forceinline__ float block_sum(const float *f, int nx, int r) {
 
 struct AvgParams {
     const PatchDevice *table;
+    const PatchDevice *coarse;     // the coarse grid's buffers
     const DevClock *lclk, *pclk;   // this level, its parent
-    float *cq[2][3];               // the coarse grid's buffers
     int r;
     const int4 *avg;
     int navg;
@@ -808,14 +807,14 @@ __global__ void amr_avg_kernel(AvgParams p) {
                 for (int k = 0; k <= r; k++) sl[k] = 0.0;
                 s += f;
             }
-            float *eta = g.x < 0 ? p.cq[pcur][0] : p.table[g.x].q[pcur][0];
+            float *eta = (g.x < 0 ? *p.coarse : p.table[g.x]).q[pcur][0];
             eta[g.y] = fp::add(eta[g.y], (float)s);
             continue;
         }
         const int e = e3 / 3, k = e3 - 3 * e;
         const int4 m = __ldg(p.avg + e);
         const PatchDevice &S = p.table[m.z];
-        float *dst = m.x < 0 ? p.cq[pcur][k] : p.table[m.x].q[pcur][k];
+        float *dst = (m.x < 0 ? *p.coarse : p.table[m.x]).q[pcur][k];
         dst[m.y] = block_sum<R>(S.q[fcur][k] + m.w, S.nx, r) * inv;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1103,8 +1102,11 @@ inline Layout layout_of(const HostMaps &M, int r, size_t at) {
     return Lo;
 }
 
+// the coarse grid's descriptor heads the workspace
+constexpr size_t kCoarseDesc = (sizeof(PatchDevice) + 255) & ~(size_t)255;
+
 inline size_t total_bytes(const std::vector<HostMaps> &M, const int *ratios, int L) {
-    size_t at = 0;
+    size_t at = kCoarseDesc;
     for (int l = 1; l <= L; l++) at = layout_of(M[l], ratios[l - 1], at).end;
     return at + 256;
 }
@@ -1124,6 +1126,7 @@ struct AmrLevel {
 struct swa_amr {
     swa_grid *coarse = nullptr;
     swa_patchset *fine = nullptr;
+    swadj::patches::PatchDevice *coarse_pd = nullptr;   // device
     int L = 0;
     AmrLevel lv[SWA_MAX_LEVELS + 1];   // 1 .. L
     int reflux = 1;
@@ -1139,10 +1142,9 @@ int amr_average(swa_amr *A, const GridRefs &c, int l, double t_end, bool reflux,
     AmrLevel &V = A->lv[l];
     amr::AvgParams p{};
     p.table = A->fine->table;
+    p.coarse = A->coarse_pd;
     p.lclk = A->fine->lev[V.lev].clk;
     p.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
-    for (int b = 0; b < 2; b++)
-        for (int k = 0; k < 3; k++) p.cq[b][k] = (float *)c.q[b][k];
     p.r = V.r;
     p.avg = V.avg; p.navg = V.navg;
     if (reflux) { p.cfu = V.cfu; p.ncfu = V.ncfu; }
@@ -1173,14 +1175,14 @@ int amr_run(swa_amr *A, const GridRefs &c, int l, double t_p, double dt_p, int m
     const int r = V.r;
     amr::FillParams f{};
     f.table = A->fine->table;
+    f.coarse = A->coarse_pd;
     f.lclk = A->fine->lev[V.lev].clk;
     f.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
-    for (int b = 0; b < 2; b++)
-        for (int k = 0; k < 3; k++) f.cq[b][k] = (float *)c.q[b][k];
-    f.nxc = c.d.nx; f.nyc = c.d.ny; f.r = r;
+    f.r = r;
     f.fill = V.fill; f.par = V.par; f.nfill = V.nfill;
     f.t_p = t_p; f.dt_p = dt_p;
-    const unsigned fb = patches::ew_blocks((size_t)3 * (V.nfill > 0 ? V.nfill : 1));
+    size_t fbn = ((size_t)(V.nfill > 0 ? V.nfill : 1) + 127) / 128;
+    const unsigned fb = (unsigned)(fbn < 65535 ? fbn : 65535);
     patches::LevelReflux rf{};
     const double dpx = l == 1 ? c.d.dx : A->lv[l - 1].dx, dpy = l == 1 ? c.d.dy : A->lv[l - 1].dy;
     if (reflux) {
@@ -1197,7 +1199,7 @@ int amr_run(swa_amr *A, const GridRefs &c, int l, double t_p, double dt_p, int m
         const double t_k = k == r ? t_p + dt_p : t_p + dt_p * (double)k / (double)r;
         const double t_km1 = k == 1 ? t_p : t_p + dt_p * (double)(k - 1) / (double)r;
         for (int j = 0; j < launches; j++) {
-            amr::amr_fill_kernel<<<fb, 256, 0, st>>>(f);
+            amr::amr_fill_kernel<<<fb, 128, 0, st>>>(f);
             TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
             TRY(level_launch(A->fine, V.lev, 1, t_k, rf, st));
         }
@@ -1239,8 +1241,17 @@ int swa_create_amr_levels(swa_grid *coarse, swa_patchset *fine, int nlevels, con
     A->coarse = coarse; A->fine = fine; A->L = nlevels;
     cudaStream_t st = (cudaStream_t)stream;
     char *base = (char *)ws;
-    size_t at = 0;
+    size_t at = amr::kCoarseDesc;
     int rc = SWA_OK;
+    // the coarse grid as a ringless patch: its ping-pong buffers and size
+    patches::PatchDevice cpd{};
+    for (int b = 0; b < 2; b++)
+        for (int k = 0; k < 3; k++) cpd.q[b][k] = (float *)c.q[b][k];
+    cpd.hb = (const float *)c.bath;
+    cpd.nx = c.d.nx; cpd.ny = c.d.ny;
+    A->coarse_pd = (patches::PatchDevice *)base;
+    rc = cuda_check(cudaMemcpyAsync(A->coarse_pd, &cpd, sizeof(cpd), cudaMemcpyHostToDevice, st),
+                    "AMR coarse descriptor upload");
     double dx = c.d.dx, dy = c.d.dy;
     for (int l = 1; l <= nlevels && rc == SWA_OK; l++) {
         const amr::HostMaps &H = M[l];
