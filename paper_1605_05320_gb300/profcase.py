@@ -11,8 +11,9 @@ and restores device memory between passes stays small:
   ctu   FP32 unsplit forward steps with transverse waves (fwd_ctu_kernel),
         ~120 MB
   amr   two-level AMR steps on the basin: the 2048^2 coarse grid and 64
-        patches refined by 4 around the source (fills, fine launches,
-        averaging), ~200 MB
+        patches refined by 4 around the source (coarse fluxes for the
+        refluxing, fills, fine launches, averaging with the refluxing),
+        ~200 MB; `--rows 16` sets the fine level's strip height
   adj   the full FP32 adjoint run (adj_f32_strips, ~2000 launches) with a
         fused snapshot every 100 steps, ~1.3 GB
   flag  FP32 adjoint-weighted flag passes without the m output (the
@@ -22,8 +23,8 @@ and restores device memory between passes stays small:
         1024^2 grid (the pruned bilinear flag_kernel)
 
 Launch counts (for a profiler's -s / -c): `fwd` and `ctu` run 1 initial-CFL
-launch then `--steps` step launches; `amr` runs its set-up launches, then 10
-per step (coarse step, 4 x (fill, fine launch), averaging); `adj` runs 1 init launch then every adjoint step to
+launch then `--steps` step launches; `amr` runs its set-up launches, then 11
+per step (coarse fluxes, coarse step, 4 x (fill, fine launch), averaging); `adj` runs 1 init launch then every adjoint step to
 t_f; `flag` runs `--steps` flag passes after its set-up launches.
 
     python -m paper_1605_05320_gb300.profcase fwd --steps 120
@@ -49,6 +50,8 @@ def main(argv=None):
                     help="fwd/ctu: random momenta of +-5 m^2/s in every cell")
     ap.add_argument("--adj-n", type=int, default=0,
                     help="flag: adjoint on a coarser adj_n^2 grid (bilinear stencil)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="amr: strip height of the fine level (16 or 32; 0 = default)")
     a = ap.parse_args(argv)
     build.build()
     S.load()
@@ -77,6 +80,8 @@ def main(argv=None):
         for k, f in enumerate(fields):
             ps.set_state(k, f[1], np.zeros_like(f[1]), np.zeros_like(f[1]))
         ps.start(1, 0.0)
+        if a.rows:
+            S.swa_patches_set_tile_rows(ps.h, 1, a.rows)
         amr = S.Amr(g, ps, 1, 4)
         dt_c = 0.9 * 0.75 * dx / np.sqrt(9.81 * float(np.max(-B)))
         t = 0.0
