@@ -160,6 +160,12 @@ class Hierarchy:
                 return q, (J - p.j0 * r + RING) * g.nx + (I - p.i0 * r + RING)
         return None
 
+    @staticmethod
+    def sub_offset(I, ic, r):
+        """Offset of fine cell I's centre from its coarse cell ic's centre,
+        in coarse cells (in (-1/2, 1/2))."""
+        return ((I - ic * r) + 0.5) / r - 0.5
+
     def fill(self, old, t_n, dt_c):
         """Fill every ring from siblings or from the coarse states old (t_n)
         and current (t_n + dt_c), at the fine level's time t_f."""
@@ -183,8 +189,8 @@ class Hierarchy:
                         fu[o], fv[o] = su[s], sv[s]
                         continue
                     ic, jc = I // r, J // r
-                    xi = ((I - ic * r) + 0.5) / r - 0.5
-                    zeta = ((J - jc * r) + 0.5) / r - 0.5
+                    xi = self.sub_offset(I, ic, r)
+                    zeta = self.sub_offset(J, jc, r)
                     v = []
                     for qo, qn in ((eta_o, eta_n), (old[1], self.hu), (old[2], self.hv)):
                         def at(ii, jj):

@@ -258,13 +258,19 @@ class LevelHierarchy:
                     fh[o] = v[0] - self.Bf[l][k][o]
                     fu[o], fv[o] = v[1], v[2]
 
+    @staticmethod
+    def sub_offset(I, Ip, r):
+        """Offset of cell I's centre from its parent cell Ip's centre, in
+        parent cells (in (-1/2, 1/2))."""
+        return ((I - Ip * r) + 0.5) / r - 0.5
+
     def _interp_parent(self, lp, Ip, Jp, I, J, r, old, a):
         qp, c = self.owner(lp, Ip, Jp)
         h, hu, hv, Bp, nx, ny = self.level_arrays(lp, 0 if qp is None else qp)
         oh, ou, ov = old[0 if qp is None else qp]
         ic, jc = c % nx, c // nx
-        xi = ((I - Ip * r) + 0.5) / r - 0.5
-        zeta = ((J - Jp * r) + 0.5) / r - 0.5
+        xi = self.sub_offset(I, Ip, r)
+        zeta = self.sub_offset(J, Jp, r)
         v = []
         for qo, qn, add in ((oh, h, Bp), (ou, hu, None), (ov, hv, None)):
             def at(ii, jj):

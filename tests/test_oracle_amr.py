@@ -7,6 +7,9 @@ r fine substeps per coarse step, averaging down.
 - the ocean at rest stays exactly at rest for r = 2 and 4 over a bottom
   sampled separately on each level;
 - a patch cut in two (the cut filled from the sibling) gives the patch;
+- a field linear in x and y is filled exactly at the ring cells' centres
+  (pins the fine cell's offset inside its coarse cell and the slopes); the
+  offset taken at the fine cell's corner (planted) misses by half a cell;
 - refining a patch brings its region closer to a uniformly fine run than the
   coarse grid alone; piecewise-constant coarse fills, fills frozen at the
   coarse step's start or end, slopes of the wrong sign, or an average over r
@@ -226,6 +229,48 @@ def test_time_interpolation_at_mid_step():
     ring.reshape(g.ny, g.nx)[RING:-RING, RING:-RING] = False
     np.testing.assert_allclose((f[0] + b)[ring], 0.125, rtol=0, atol=1e-12)
     np.testing.assert_allclose(f[1][ring], 1.5, rtol=0, atol=1e-12)
+
+
+def linear_fill_error(cls=Hierarchy, r=3):
+    """A surface and momenta linear in x and y on the coarse grid: minmod
+    slopes of a linear field are its exact differences, so every
+    coarse-filled ring cell must hold the field at its own centre."""
+    nc = 16
+    H, cg, Bc, *_ = build(nc, r, [Patch(5, 6, 4, 3)], cls=cls, rest=True)
+    xc = (np.arange(nc) + 0.5) * DX
+    X, Y = np.meshgrid(xc, xc)
+    eta = (1e-3 * X / DX + 2e-3 * Y / DX).ravel()
+    H.h = eta - Bc
+    H.hu = (0.5 * X / DX - 0.25 * Y / DX).ravel()
+    H.hv = (0.1 * Y / DX).ravel()
+    H.fill((H.h.copy(), H.hu.copy(), H.hv.copy()), 0.0, 100.0)
+    g, p = H.grids[0], H.patches[0]
+    xf = g.x_lo + (np.arange(g.nx) + 0.5) * g.dx
+    yf = g.y_lo + (np.arange(g.ny) + 0.5) * g.dy
+    XF, YF = np.meshgrid(xf, yf)
+    ring = np.ones((g.ny, g.nx), bool)
+    ring[RING:-RING, RING:-RING] = False
+    f, b = H.fine[0], H.Bf[0]
+    want = [(1e-3 * XF / DX + 2e-3 * YF / DX), 0.5 * XF / DX - 0.25 * YF / DX, 0.1 * YF / DX]
+    got = [(f[0] + b).reshape(g.ny, g.nx), f[1].reshape(g.ny, g.nx), f[2].reshape(g.ny, g.nx)]
+    return max(float(np.abs(a - w)[ring].max()) for a, w in zip(got, want))
+
+
+class HalfCellOffset(Hierarchy):
+    """Planted mistake: the fine cell's offset inside its coarse cell taken
+    at its lower corner instead of its centre."""
+
+    @staticmethod
+    def sub_offset(I, ic, r):
+        return (I - ic * r) / r - 0.5
+
+
+def test_a_linear_field_is_filled_exactly_at_the_fine_centres():
+    """Pins the fine cell's position inside its coarse cell (xi, zeta) and the
+    slopes: exact to rounding for r = 2, 3, 4."""
+    for r in (2, 3, 4):
+        assert linear_fill_error(r=r) <= 1e-12
+        assert linear_fill_error(HalfCellOffset, r=r) > 1e-4   # half a fine cell of slope
 
 
 class AverageByR(Hierarchy):

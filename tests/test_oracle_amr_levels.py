@@ -12,6 +12,9 @@
   level; filling level 2 from the coarse grid instead of level 1, or
   interpolating it in time against the coarse step instead of its parent's
   substep (both planted), does not;
+- a field linear in x and y on every level is filled exactly at the level-2
+  ring cells' centres from their level-1 parent patch; the corner offset
+  (planted) misses;
 - rings that leave the parent level's interiors are refused.
 """
 import numpy as np
@@ -244,6 +247,49 @@ def test_a_second_level_moves_its_region_towards_the_fine_solution(steps):
     assert two < 0.5 * one, (two, one)          # measured 0.19 and 0.28
     assert planted > 5.0 * two, (planted, two)  # measured 19x
     assert late > 1.4 * two, (late, two)        # measured 1.73x
+
+
+class CornerOffset(LevelHierarchy):
+    """Planted mistake: a cell's offset inside its parent cell taken at its
+    lower corner instead of its centre."""
+
+    @staticmethod
+    def sub_offset(I, Ip, r):
+        return (I - Ip * r) / r - 0.5
+
+
+def linear_level_fill_error(cls=LevelHierarchy, r2=3):
+    """Linear surface and momenta on every level: the level-2 rings filled
+    from their level-1 parent patch must hold the field at their centres."""
+    nc = 24
+    H, cg, *_ = build(nc, [(2, L1), (r2, [Patch(20, 19, 6, 7)])], cls=cls, rest=True)
+    lin = lambda X, Y: (1e-3 * X / DX + 2e-3 * Y / DX, 0.5 * X / DX - 0.25 * Y / DX, 0.1 * Y / DX)
+    for l in (1, 2):
+        for q, g in enumerate(H.G[l]):
+            XF, YF = np.meshgrid(g.x_lo + (np.arange(g.nx) + 0.5) * g.dx,
+                                 g.y_lo + (np.arange(g.ny) + 0.5) * g.dy)
+            e, u, v = (a.ravel() for a in lin(XF, YF))
+            H.q[l][q] = [e - H.Bf[l][q], u, v]
+    H.fill(2, H.snapshot(1), 0.0, 100.0)
+    g = H.G[2][0]
+    XF, YF = np.meshgrid(g.x_lo + (np.arange(g.nx) + 0.5) * g.dx,
+                         g.y_lo + (np.arange(g.ny) + 0.5) * g.dy)
+    want = lin(XF, YF)
+    f = H.q[2][0]
+    got = ((f[0] + H.Bf[2][0]).reshape(g.ny, g.nx), f[1].reshape(g.ny, g.nx),
+           f[2].reshape(g.ny, g.nx))
+    ring = np.ones((g.ny, g.nx), bool)
+    ring[RING:-RING, RING:-RING] = False
+    return max(float(np.abs(a - w)[ring].max()) for a, w in zip(got, want))
+
+
+def test_a_linear_field_is_filled_exactly_from_a_patch_parent():
+    """Pins a cell's position inside its parent patch's cell and the slopes
+    from the parent's array: exact to rounding for r = 2, 3, 4; the corner
+    offset (planted) misses by half a cell of slope."""
+    for r2 in (2, 3, 4):
+        assert linear_level_fill_error(r2=r2) <= 1e-12
+        assert linear_level_fill_error(CornerOffset, r2=r2) > 1e-4
 
 
 def test_rings_outside_the_parent_level_are_refused():
