@@ -433,6 +433,9 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
     amr.set_reflux(False)
     us_plain = timed(one_step, steps)
     amr.set_reflux(True)
+    amr.set_fill_mode(S.SWA_AMR_FILL_FUSED)
+    us_fused = timed(one_step, steps)
+    amr.set_fill_mode(S.SWA_AMR_FILL_KERNEL)
     if S.swa_sync_status(hs) != 0:
         raise RuntimeError("AMR hierarchy step reported an error")
     nfill, navg, nedges = amr.info()
@@ -449,7 +452,69 @@ def measure_amr(stream, steps=20, ratio=4, side=32, tiles=8):
             "ring_cells": nfill, "covered_coarse_cells": navg, "coarse_fine_edges": nedges,
             "fine_strip_rows": rows,
             "us_per_step_without_refluxing": round(us_plain, 1),
+            "us_per_step_fills_in_the_level_launch": round(us_fused, 1),
             "cell_updates_per_s": updates / (us_step * 1e-6)}
+
+
+def measure_amr_nested(stream, steps=10, ratio=4):
+    """Outside the timed region: the AMR glue over two nested patch levels on
+    the basin (the 2048^2 coarse grid, level 1 as in measure_amr, level 2:
+    16 patches of 32 x 32 level-1 cells refined by `ratio` again around the
+    source).  Times `steps` hierarchy steps (each: the coarse step, 4 level-1
+    substeps, each with 4 level-2 substeps, averaging and refluxing at both
+    levels) after 3 warm-up steps, with the strip heights tuned per level."""
+    import torch
+    from paper_1605_05320_gb300 import swadj as S
+    from paper_1605_05320_gb300 import synth, tune
+    hs = stream.cuda_stream
+    B, eta, n, dx, descs, fields = synth.amr_basin_2048_nested(ratio)
+    d = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=S.SWA_FP32)
+    cells = {lv: sum(q[3] * q[4] for q in descs if q[0] == lv) for lv in (1, 2)}
+    dt_c = 0.9 * 0.75 * dx / np.sqrt(9.81 * float(np.max(-B)))
+
+    def hierarchy():
+        g = S.Grid(d, B)
+        g.set_state(eta, np.zeros(n * n), np.zeros(n * n), 0.0, hs)
+        ps = S.PatchSet(descs, [f[0] for f in fields], d, stream=hs)
+        for k, f in enumerate(fields):
+            z = np.zeros_like(f[1])
+            ps.set_state(k, f[1], z, z, hs)
+        ps.start(1, 0.0, hs)
+        ps.start(2, 0.0, hs)
+        return g, ps
+
+    g2, ps2 = hierarchy()
+    with torch.cuda.stream(stream):
+        rows = tune.tune_patches(ps2)
+    g, ps = hierarchy()
+    for lv in (1, 2):
+        S.swa_patches_set_tile_rows(ps.h, lv, rows[lv])
+    amr = S.Amr(g, ps, [1, 2], [ratio, ratio], stream=hs)
+    clock = {"t": 0.0}
+
+    def one_step():
+        amr.step(clock["t"], dt_c, 1, hs)
+        clock["t"] = clock["t"] + dt_c
+
+    for _ in range(3):
+        one_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / steps
+    if S.swa_sync_status(hs) != 0:
+        raise RuntimeError("nested AMR hierarchy step reported an error")
+    updates = n * n + ratio * cells[1] + ratio * ratio * cells[2]
+    return {"coarse": f"{n}^2, {dx:g} m cells", "ratios": [ratio, ratio],
+            "patches": [sum(1 for q in descs if q[0] == lv) for lv in (1, 2)],
+            "cells": [cells[1], cells[2]], "strip_rows": [rows[1], rows[2]],
+            "coarse_fine_edges": [amr.info(1)[2], amr.info(2)[2]], "steps": steps,
+            "us_per_step": round(us, 1), "cell_updates_per_s": updates / (us * 1e-6)}
 
 
 def cell_updates(sc_obj):
@@ -669,6 +734,7 @@ def run_ours(args, rank, world, local_rank):
             out["forward_active"] = measure_active_forward(scen, stream)
             out["fp64"] = measure_fp64(scen, stream, alu=S.measure_alu_peaks(local_rank))
             out["amr"] = measure_amr(stream)
+            out["amr_nested"] = measure_amr_nested(stream)
     return out
 
 

@@ -399,8 +399,10 @@ int swa_patches_get_time(swa_patchset *ps, int level, double *t, double *dt_next
  * strip height) and cells of a level (host bookkeeping). */
 int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches,
                            int *ntiles, long long *ncells);
-/* Strip height of the level's kernel in rows: 16 or 32 (0 = default 32).
- * Results do not depend on it; throughput does (the autotuner picks it). */
+/* Strip height of the level's kernel in rows: 16 or 32 (0 = default: 16
+ * when the level's 16-row strips are no more than the warps the launch keeps
+ * resident, else 32).  Results do not depend on it; throughput does (the
+ * autotuner picks it). */
 int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
 
 /* ============================== AMR glue ===================================
@@ -469,9 +471,9 @@ int swa_patches_set_tile_rows(swa_patchset *ps, int level, int rows);
  */
 typedef struct swa_amr swa_amr;
 /* Device workspace for the maps and the refluxing slots (per level: 20
- * bytes per ring cell, 16 per covered parent cell, 20 + 8 (1 + r) per
- * coarse-fine edge, 16 per uncovered parent cell beside the level, plus
- * padding); 0 if the geometry is invalid (the reason is in swa_last_error).
+ * bytes per ring cell, 4 per patch of the patch set, 16 per covered parent
+ * cell, 20 + 8 (1 + r) per coarse-fine edge, 16 per uncovered parent cell
+ * beside the level, plus padding); 0 if the geometry is invalid (the reason is in swa_last_error).
  * levels[l - 1]: the patch-set level of hierarchy level l (1 .. nlevels);
  * ratios[l - 1]: r_l in [1, 64]. */
 size_t swa_amr_levels_workspace_bytes(const swa_grid *coarse, const swa_patchset *fine,
@@ -513,6 +515,18 @@ int swa_amr_step(swa_amr *amr, double t_n, double dt_c, int max_launches, void *
 /* Refluxing (step 4 above) on (on != 0, the default) or off.  Host state
  * only; takes effect at the next swa_amr_step. */
 int swa_amr_set_reflux(swa_amr *amr, int on);
+/* Where the ring fills of step 2 run (results are the same bit for bit):
+ * SWA_AMR_FILL_KERNEL (the default) in a kernel of its own before each
+ * launch, one thread per ring cell; SWA_AMR_FILL_FUSED in the level launch
+ * itself: each strip first writes the ring cells inside its own stencil
+ * window (strips sharing a ring cell write the same value), and the
+ * launch's refluxing fluxes form the ring cells they read from the fill map.
+ * The fused form saves the kernel but puts the fills on the critical path
+ * of the strips at patch edges; on levels with about one strip per resident
+ * warp (latency-bound launches) it is slower.  Host state only. */
+#define SWA_AMR_FILL_FUSED 0
+#define SWA_AMR_FILL_KERNEL 1
+int swa_amr_set_fill_mode(swa_amr *amr, int mode);
 /* Sizes of hierarchy level `level`'s maps (1 .. nlevels): ring cells filled
  * per launch, covered parent cell copies averaged, coarse-fine edges
  * refluxed (any pointer may be null). */

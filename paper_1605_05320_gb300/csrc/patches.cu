@@ -28,6 +28,72 @@ struct PatchDevice {
     BcSpec bc;
 };
 
+// ------------------------------------------------------------ ring fills
+// The AMR glue's ring fill of one cell (see the AMR section below for the
+// maps): a sibling copy, or the parent linear in time between its buffers
+// before and after its step (alpha in [0, 1]) then limited linear in space
+// within the parent cell (minmod slopes from the parent's array, zero where
+// a neighbour lies outside it).  Entry m = (patch, cell, src, idx): src >= 0
+// a sibling patch and idx its cell; src < 0 the parent cell idx (in patch
+// par, or the coarse grid for par < 0) with the ring cell at -src - 1 = sx +
+// r sy inside it.  Used by the fill kernel and by level launches that fill
+// their own rings.
+struct RingFill {
+    const int4 *fill;           // the level's entries, patch by patch, ring cells row-major
+    const int *par;             // parent patch per entry (-1: the coarse grid)
+    const int *base;            // per patch-set patch: its first entry (-1: not on the level)
+    const PatchDevice *coarse;  // the coarse grid's buffers, as a patch without ring
+    const DevClock *pclk;       // the parent's clock (its current buffer)
+    int r;
+    double t_p, dt_p;           // the parent's step
+};
+
+// index of ring cell (i, j) among its patch's ring cells in row-major order
+__host__ __device__ __forceinline__ int ring_index(int i, int j, int nx, int ny) {
+    if (j < 2) return j * nx + i;
+    if (j >= ny - 2) return 2 * nx + (ny - 4) * 4 + (j - (ny - 2)) * nx + i;
+    return 2 * nx + (j - 2) * 4 + (i < 2 ? i : i - (nx - 4));
+}
+
+__host__ __device__ __forceinline__ bool ring_cell(int i, int j, int nx, int ny) {
+    return i < 2 || i >= nx - 2 || j < 2 || j >= ny - 2;
+}
+
+__device__ __forceinline__ float minmod(float a, float b) {
+    if (a * b <= 0.f) return 0.f;
+    return fabsf(a) < fabsf(b) ? a : b;
+}
+
+// component k of ring entry m at alpha af; fcur, pcur: the level's and the
+// parent's current buffers
+__device__ __forceinline__ float ring_value(const PatchDevice *table, const PatchDevice *coarse,
+                                            int4 m, int par, int k, int r, float af, int fcur,
+                                            int pcur) {
+    if (m.z >= 0) return table[m.z].q[fcur][k][m.w];
+    const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
+    const PatchDevice &Q = par < 0 ? *coarse : table[par];
+    const int nx = Q.nx, ny = Q.ny;
+    const int c = m.w, ic = c % nx, jc = c / nx;
+    const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
+    const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
+    const float *o = Q.q[pcur ^ 1][k], *nw = Q.q[pcur][k];
+    auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
+    const float qc = at(c);
+    float s_x = 0.f, s_y = 0.f;
+    if (ic > 0 && ic < nx - 1) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
+    if (jc > 0 && jc < ny - 1) s_y = minmod(qc - at(c - nx), at(c + nx) - qc);
+    return fmaf(s_y, zeta, fmaf(s_x, xi, qc));
+}
+
+// What a reader of a patch's current buffer needs to form its ring cells
+// itself, before the level launch's own fill of them is known to be done.
+struct RingCtx {
+    const PatchDevice *table;
+    const RingFill *rf;
+    int pid, fcur, pcur;
+    float af;
+};
+
 // ------------------------------------------------------------ refluxing
 // Mass flux through an edge of cell (i, j), low (side < 0) or high (side >
 // 0), along `axis`, as the FP32 split step forms it: x-edges from the state
@@ -44,33 +110,50 @@ struct CellRaw {
     float eta, mu, mv, hb;
 };
 
-__device__ __forceinline__ CellRaw raw_at(const strip::View &v, int i, int j) {
+// cell (i, j) of view v, ghost-mapped; with a ring context its ring cells
+// are formed from the fill map instead of read
+__device__ __forceinline__ CellRaw raw_at(const strip::View &v, int i, int j,
+                                          const RingCtx *rc = nullptr) {
     bool fx, fy;
     const int ii = ghost_index(i, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
     const int jj = ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
     const size_t o = (size_t)jj * v.nx + ii;
     CellRaw c;
-    c.eta = v.q0[o];
     c.hb = v.hb[o];
-    const float mu = v.q1[o], mv = v.q2[o];
+    float mu, mv;
+    if (rc && ring_cell(ii, jj, v.nx, v.ny)) {
+        const RingFill &F = *rc->rf;
+        const int e = F.base[rc->pid] + ring_index(ii, jj, v.nx, v.ny);
+        const int4 m = F.fill[e];
+        const int par = F.par[e];
+        c.eta = ring_value(rc->table, F.coarse, m, par, 0, F.r, rc->af, rc->fcur, rc->pcur);
+        mu = ring_value(rc->table, F.coarse, m, par, 1, F.r, rc->af, rc->fcur, rc->pcur);
+        mv = ring_value(rc->table, F.coarse, m, par, 2, F.r, rc->af, rc->fcur, rc->pcur);
+    } else {
+        c.eta = v.q0[o];
+        mu = v.q1[o];
+        mv = v.q2[o];
+    }
     c.mu = fx ? -mu : mu;
     c.mv = fy ? -mv : mv;
     return c;
 }
 
 // x-frame cell data of cell (i, j)
-__device__ __forceinline__ fp::Cell<float> xcell(const strip::View &v, int i, int j) {
-    const CellRaw c = raw_at(v, i, j);
+__device__ __forceinline__ fp::Cell<float> xcell(const strip::View &v, int i, int j,
+                                                 const RingCtx *rc = nullptr) {
+    const CellRaw c = raw_at(v, i, j, rc);
     return fp::derive(c.eta, fp::add(c.eta, c.hb), c.mu, c.mv);
 }
 
 // the x-swept cell (i, j) in the y frame, as the strip kernel's x-sweep
 // leaves it
 __device__ __forceinline__ fp::Cell<float> xswept(const strip::View &v, int i, int j, float gh,
-                                                  float nux, int order) {
+                                                  float nux, int order,
+                                                  const RingCtx *rc = nullptr) {
     fp::Cell<float> c[5];
 #pragma unroll
-    for (int k = 0; k < 5; k++) c[k] = xcell(v, i - 2 + k, j);
+    for (int k = 0; k < 5; k++) c[k] = xcell(v, i - 2 + k, j, rc);
     fp::Edge<float> w[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) w[k] = fp::solve(gh, c[k], c[k + 1]);
@@ -89,12 +172,13 @@ __device__ __forceinline__ fp::Cell<float> xswept(const strip::View &v, int i, i
 // its edge to cell q + 1 and the neighbour edges come by shuffles, and the
 // result is valid on the lane with q == 1.  All 32 lanes must call it.
 __device__ __forceinline__ float group_flux(const strip::View &v, int i, int j, int axis, int k0,
-                                            float gh, float nux, float nuy, int order) {
+                                            float gh, float nux, float nuy, int order,
+                                            const RingCtx *rc = nullptr) {
     using strip::dn;
     using strip::up;
     const int q = threadIdx.x & 3;
     const fp::Cell<float> c =
-        axis == 0 ? xcell(v, i + k0 + q, j) : xswept(v, i, j + k0 + q, gh, nux, order);
+        axis == 0 ? xcell(v, i + k0 + q, j, rc) : xswept(v, i, j + k0 + q, gh, nux, order, rc);
     fp::Cell<float> n = c;
     n.h = dn(c.h); n.mn = dn(c.mn); n.sq = dn(c.sq); n.su = dn(c.su); n.sv = dn(c.sv);
     n.P = dn(c.P); n.T = dn(c.T); n.eta = dn(c.eta);
@@ -156,12 +240,44 @@ struct LevelParams {
     int order;
     int *err;
     LevelReflux rf;
+    RingFill lf;       // the level fills its own rings (AMR glue) when fill_on
+    int fill_on;
 };
+
+// Fill the ring cells of patch pid inside the stencil window of the strip at
+// (x0, y0) (columns x0 - 2 .. x0 + 29, rows y0 - 2 .. the strip's last row +
+// 2, clipped to the array) in the current buffer, the warp's lanes taking
+// the window's cells in turn.  Strips of a patch share ring cells; each
+// writes the same value, so the writes of two strips agree, and a strip
+// reads only cells it has written itself.
+__device__ __noinline__ void fill_window(const LevelParams &p, int pid, int x0, int y0, int cur,
+                                         float af, int pcur) {
+    const PatchDevice &P = p.table[pid];
+    const int nx = P.nx, ny = P.ny;
+    const int ylast = (y0 + p.rows < ny ? y0 + p.rows : ny) - 1;
+    const int cx0 = x0 - 2 > 0 ? x0 - 2 : 0, cx1 = x0 + 29 < nx - 1 ? x0 + 29 : nx - 1;
+    const int ry0 = y0 - 2 > 0 ? y0 - 2 : 0, ry1 = ylast + 2 < ny - 1 ? ylast + 2 : ny - 1;
+    if (cx0 >= 2 && cx1 < nx - 2 && ry0 >= 2 && ry1 < ny - 2) return;   // no ring cell
+    const int W = cx1 - cx0 + 1, H = ry1 - ry0 + 1;
+    const int b = p.lf.base[pid];
+    for (int q = threadIdx.x & 31; q < W * H; q += 32) {
+        const int j = ry0 + q / W, i = cx0 + q % W;
+        if (!ring_cell(i, j, nx, ny)) continue;
+        const int e = b + ring_index(i, j, nx, ny);
+        const int4 m = __ldg(p.lf.fill + e);
+        const int par = __ldg(p.lf.par + e);
+        const size_t o = (size_t)j * nx + i;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            P.q[cur][k][o] = ring_value(p.table, p.lf.coarse, m, par, k, p.lf.r, af, cur, pcur);
+    }
+}
 
 // One task of a level launch's refluxing work: 8 items, 4 lanes each;
 // tasks below ceil(nfine / 8) are fine parts, the rest coarse parts.
 __device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, int cur,
-                                               float nux, float nuy, double dt) {
+                                               float nux, float nuy, double dt, float af,
+                                               int pcur) {
     const LevelReflux &R = p.rf;
     const int lane = threadIdx.x & 31;
     const int tf = (R.nfine + 7) / 8;
@@ -184,8 +300,11 @@ __device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, i
     strip::View v;
     v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
     v.nx = P.nx; v.ny = P.ny; v.bc = P.bc;
-    const float f =
-        reflux::group_flux(v, c % P.nx, c / P.nx, axis, k0, 0.5f * p.g, nux, nuy, p.order);
+    // with the level filling its own rings, ring cells are formed here (the
+    // strip that writes them may not have run yet)
+    RingCtx rc{p.table, &p.lf, pid, cur, pcur, af};
+    const float f = reflux::group_flux(v, c % P.nx, c / P.nx, axis, k0, 0.5f * p.g, nux, nuy,
+                                       p.order, p.fill_on ? &rc : nullptr);
     if (!live || (lane & 3) != 1) return;
     const double fs = (double)(side > 0 ? f : -f);
     if (fine)
@@ -201,8 +320,19 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
     __shared__ float red[strip::kThreads / 32];
     __shared__ int am_last;
     __shared__ strip::Ring ring[strip::kThreads / 32];
+    __shared__ float s_af;
+    __shared__ int s_pcur;
     double t_now = 0.0, dt = 0.0;
     if (!fwave::begin_step(p.clk, p.t_end, p.dx, p.dy, s_nu, &s_cur, &s_run, t_now, dt)) return;
+    if (p.fill_on) {   // block-uniform
+        if (threadIdx.x == 0) {
+            double a = (t_now - p.lf.t_p) / p.lf.dt_p;
+            a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+            s_af = (float)a;
+            s_pcur = ((volatile const DevClock *)p.lf.pclk)->cur;
+        }
+        __syncthreads();
+    }
     const int cur = s_cur;
     const int wpb = blockDim.x >> 5;
     float smax = 0.f;
@@ -215,6 +345,11 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
         v.q0 = P.q[cur][0]; v.q1 = P.q[cur][1]; v.q2 = P.q[cur][2]; v.hb = P.hb;
         v.o0 = P.q[cur ^ 1][0]; v.o1 = P.q[cur ^ 1][1]; v.o2 = P.q[cur ^ 1][2];
         v.nx = P.nx; v.ny = P.ny; v.rdx = P.rdx; v.rdy = P.rdy; v.bc = P.bc;
+        if (p.fill_on) {
+            fill_window(p, t.x, t.y, t.z, cur, s_af, s_pcur);
+            __threadfence_block();
+            __syncwarp();   // the window's writes before the strip's loads
+        }
         strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
                           ring[threadIdx.x >> 5], smax, bad);
     }
@@ -226,7 +361,8 @@ __global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelPa
         const int rem = p.nunits % total;
         const double dt_now = reflux::coming_dt(p.clk, p.t_end);
         for (int t = (gw + total - rem) % total; t < ntasks; t += total)
-            level_reflux_task(p, t, cur, s_nu[0], s_nu[1], dt_now);
+            level_reflux_task(p, t, cur, s_nu[0], s_nu[1], dt_now, p.fill_on ? s_af : 0.f,
+                              p.fill_on ? s_pcur : 0);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red,
@@ -437,7 +573,11 @@ static LevelParams level_params(const swa_patchset *ps, int l, double t_end) {
     const Level &L = ps->lev[l];
     LevelParams p{};
     p.table = ps->table;
-    p.rows = L.rows == 16 ? 16 : 32;
+    // default: 16-row strips when a level has few enough of them for every
+    // resident warp to take at most one (a latency-bound level, where
+    // shorter strips shorten the critical path), 32 otherwise
+    const int auto_rows = L.nunits16 <= occupancy_blocks() * (strip::kThreads / 32) ? 16 : 32;
+    p.rows = L.rows == 16 ? 16 : (L.rows == 32 ? 32 : auto_rows);
     p.units = p.rows == 16 ? L.units16 : L.units32;
     p.nunits = p.rows == 16 ? L.nunits16 : L.nunits32;
     p.clk = L.clk;
@@ -454,7 +594,7 @@ static LevelParams level_params(const swa_patchset *ps, int l, double t_end) {
 
 // nsteps launches of the level step, with the refluxing work rf in each.
 static int level_launch(swa_patchset *ps, int level, int nsteps, double t_end,
-                        const LevelReflux &rf, cudaStream_t st) {
+                        const LevelReflux &rf, cudaStream_t st, const RingFill *lf = nullptr) {
     if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
     Level &L = ps->lev[level];
     if (L.npatches == 0) return set_error(SWA_EINVAL, "level %d has no patches", level);
@@ -462,6 +602,10 @@ static int level_launch(swa_patchset *ps, int level, int nsteps, double t_end,
     if (nsteps < 0) return set_error(SWA_EINVAL, "nsteps < 0");
     LevelParams p = level_params(ps, level, t_end);
     p.rf = rf;
+    if (lf) {
+        p.lf = *lf;
+        p.fill_on = 1;
+    }
     constexpr int wpb = strip::kThreads / 32;
     const int need = (p.nunits + wpb - 1) / wpb;
     p.nblocks = occupancy_blocks();
@@ -631,7 +775,7 @@ int swa_patches_level_info(const swa_patchset *ps, int level, int *npatches, int
     if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
     const Level &L = ps->lev[level];
     if (npatches) *npatches = L.npatches;
-    if (ntiles) *ntiles = L.rows == 16 ? L.nunits16 : L.nunits32;
+    if (ntiles) *ntiles = L.npatches > 0 ? level_params(ps, level, 0.0).nunits : 0;
     if (ncells) *ncells = L.ncells;
     return SWA_OK;
 }
@@ -677,36 +821,23 @@ constexpr int kRing = 2;
 using patches::PatchDevice;
 using patches::ew_blocks;
 
-__device__ __forceinline__ float minmod(float a, float b) {
-    if (a * b <= 0.f) return 0.f;
-    return fabsf(a) < fabsf(b) ? a : b;
-}
-
 struct FillParams {
     const PatchDevice *table;
-    const PatchDevice *coarse;   // the coarse grid's buffers, as a patch without ring
+    RingFill rf;
     const DevClock *lclk;   // this level
-    const DevClock *pclk;   // its parent: the coarse grid's clock at l = 1
-    int r;
-    const int4 *fill;
-    const int *par;         // parent patch per entry (-1: the coarse grid)
     int nfill;
-    double t_p, dt_p;       // the parent's step
 };
 
-// Ring fill at the level's current time: sibling copy, or the parent linear
-// in time between its buffers before and after its step (alpha = (t - t_p) /
-// dt_p in [0, 1]) then limited linear in space within the parent cell
-// (minmod slopes from the parent's array, zero where a neighbour lies
-// outside it: the domain edge of the coarse grid).  One thread per ring
-// cell, the three components in turn (independent loads); the clocks and
-// alpha (FP64) are read and formed once per block.
+// Ring fill of a level at its current time as a kernel of its own (the
+// level launch can also fill its rings itself): one thread per ring cell,
+// the three components in turn (independent loads); the clocks and alpha
+// (FP64) are read and formed once per block.
 __global__ void __launch_bounds__(128) amr_fill_kernel(FillParams p) {
     __shared__ float s_a;
     __shared__ int s_fcur, s_pcur;
     if (threadIdx.x == 0) {
-        volatile const DevClock *lc = p.lclk, *pc = p.pclk;
-        double a = (lc->t - p.t_p) / p.dt_p;
+        volatile const DevClock *lc = p.lclk, *pc = p.rf.pclk;
+        double a = (lc->t - p.rf.t_p) / p.rf.dt_p;
         a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
         s_a = (float)a;
         s_fcur = lc->cur;
@@ -715,34 +846,14 @@ __global__ void __launch_bounds__(128) amr_fill_kernel(FillParams p) {
     __syncthreads();
     const float af = s_a;
     const int fcur = s_fcur, pcur = s_pcur;
-    const int r = p.r;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nfill; e += gridDim.x * blockDim.x) {
-        const int4 m = __ldg(p.fill + e);
+        const int4 m = __ldg(p.rf.fill + e);
+        const int par = __ldg(p.rf.par + e);
         const PatchDevice &D = p.table[m.x];
-        if (m.z >= 0) {
-            const PatchDevice &Sb = p.table[m.z];
 #pragma unroll
-            for (int k = 0; k < 3; k++) D.q[fcur][k][m.y] = Sb.q[fcur][k][m.w];
-            continue;
-        }
-        const int sub = -m.z - 1, sx = sub % r, sy = sub / r;
-        const int par = __ldg(p.par + e);
-        const PatchDevice &Q = par < 0 ? *p.coarse : p.table[par];
-        const int nx = Q.nx, ny = Q.ny;
-        const int c = m.w, ic = c % nx, jc = c / nx;
-        const float xi = (float)(2 * sx + 1 - r) / (float)(2 * r);
-        const float zeta = (float)(2 * sy + 1 - r) / (float)(2 * r);
-        const bool inx = ic > 0 && ic < nx - 1, iny = jc > 0 && jc < ny - 1;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const float *o = Q.q[pcur ^ 1][k], *nw = Q.q[pcur][k];
-            auto at = [&](int i) { return fmaf(af, nw[i] - o[i], o[i]); };
-            const float qc = at(c);
-            float s_x = 0.f, s_y = 0.f;
-            if (inx) s_x = minmod(qc - at(c - 1), at(c + 1) - qc);
-            if (iny) s_y = minmod(qc - at(c - nx), at(c + nx) - qc);
-            D.q[fcur][k][m.y] = fmaf(s_y, zeta, fmaf(s_x, xi, qc));
-        }
+        for (int k = 0; k < 3; k++)
+            D.q[fcur][k][m.y] =
+                patches::ring_value(p.table, p.rf.coarse, m, par, k, p.rf.r, af, fcur, pcur);
     }
 }
 
@@ -918,6 +1029,7 @@ struct LevelGeom {
 struct HostMaps {
     std::vector<int4> fill, avg, cf, cfu;
     std::vector<int> par, cfw;
+    std::vector<int> base;   // per patch-set patch: its first fill entry (-1: not on the level)
 };
 
 // Check the hierarchy and build every level's maps (host).  levels[l - 1]:
@@ -1001,9 +1113,11 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int L, const int *leve
         const LevelGeom &g = G[l], &gp = G[l - 1];
         const int r = g.r;
         HostMaps &M = out[l];
+        M.base.assign(ps->n, -1);
         // fills (and the nesting check of every array cell)
         for (int a = 0; a < (int)g.box.size(); a++) {
             const FineBox &b = g.box[a];
+            M.base[g.ids[a]] = (int)M.fill.size();
             for (int j = 0; j < b.ny; j++)
                 for (int i = 0; i < b.nx; i++) {
                     const bool ring =
@@ -1084,7 +1198,7 @@ int build_maps(const GridRefs &c, const swa_patchset *ps, int L, const int *leve
 // Workspace layout of one level's maps and slots, each on a 256-byte
 // boundary.
 struct Layout {
-    size_t fill, par, avg, cf, cfw, cfu, slot, end;
+    size_t fill, par, base, avg, cf, cfw, cfu, slot, end;
 };
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -1093,7 +1207,8 @@ inline Layout layout_of(const HostMaps &M, int r, size_t at) {
     Layout Lo;
     Lo.fill = at;
     Lo.par = Lo.fill + round256(sizeof(int4) * M.fill.size());
-    Lo.avg = Lo.par + round256(sizeof(int) * M.par.size());
+    Lo.base = Lo.par + round256(sizeof(int) * M.par.size());
+    Lo.avg = Lo.base + round256(sizeof(int) * M.base.size());
     Lo.cf = Lo.avg + round256(sizeof(int4) * M.avg.size());
     Lo.cfw = Lo.cf + round256(sizeof(int4) * M.cf.size());
     Lo.cfu = Lo.cfw + round256(sizeof(int) * M.cfw.size());
@@ -1117,7 +1232,7 @@ inline size_t total_bytes(const std::vector<HostMaps> &M, const int *ratios, int
 struct AmrLevel {
     int lev = 0, r = 1;
     int4 *fill = nullptr, *avg = nullptr, *cf = nullptr, *cfu = nullptr;
-    int *par = nullptr, *cfw = nullptr;
+    int *par = nullptr, *cfw = nullptr, *base = nullptr;
     double *slot = nullptr;
     int nfill = 0, navg = 0, ncf = 0, ncfu = 0;
     double dx = 0, dy = 0;
@@ -1130,6 +1245,7 @@ struct swa_amr {
     int L = 0;
     AmrLevel lv[SWA_MAX_LEVELS + 1];   // 1 .. L
     int reflux = 1;
+    int fill_mode = SWA_AMR_FILL_KERNEL;
 };
 
 namespace {
@@ -1173,14 +1289,16 @@ int amr_run(swa_amr *A, const GridRefs &c, int l, double t_p, double dt_p, int m
     using namespace swadj;
     AmrLevel &V = A->lv[l];
     const int r = V.r;
+    patches::RingFill lf{};
+    lf.fill = V.fill; lf.par = V.par; lf.base = V.base; lf.coarse = A->coarse_pd;
+    lf.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
+    lf.r = r; lf.t_p = t_p; lf.dt_p = dt_p;
+    const bool fused = A->fill_mode == SWA_AMR_FILL_FUSED;
     amr::FillParams f{};
     f.table = A->fine->table;
-    f.coarse = A->coarse_pd;
+    f.rf = lf;
     f.lclk = A->fine->lev[V.lev].clk;
-    f.pclk = l == 1 ? c.clk : A->fine->lev[A->lv[l - 1].lev].clk;
-    f.r = r;
-    f.fill = V.fill; f.par = V.par; f.nfill = V.nfill;
-    f.t_p = t_p; f.dt_p = dt_p;
+    f.nfill = V.nfill;
     size_t fbn = ((size_t)(V.nfill > 0 ? V.nfill : 1) + 127) / 128;
     const unsigned fb = (unsigned)(fbn < 65535 ? fbn : 65535);
     patches::LevelReflux rf{};
@@ -1199,9 +1317,11 @@ int amr_run(swa_amr *A, const GridRefs &c, int l, double t_p, double dt_p, int m
         const double t_k = k == r ? t_p + dt_p : t_p + dt_p * (double)k / (double)r;
         const double t_km1 = k == 1 ? t_p : t_p + dt_p * (double)(k - 1) / (double)r;
         for (int j = 0; j < launches; j++) {
-            amr::amr_fill_kernel<<<fb, 128, 0, st>>>(f);
-            TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
-            TRY(level_launch(A->fine, V.lev, 1, t_k, rf, st));
+            if (!fused) {
+                amr::amr_fill_kernel<<<fb, 128, 0, st>>>(f);
+                TRY(cuda_check(cudaGetLastError(), "amr_fill_kernel"));
+            }
+            TRY(level_launch(A->fine, V.lev, 1, t_k, rf, st, fused ? &lf : nullptr));
         }
         if (l < A->L) {
             TRY(amr_run(A, c, l + 1, t_km1, t_k - t_km1, m, reflux, st));
@@ -1262,6 +1382,7 @@ int swa_create_amr_levels(swa_grid *coarse, swa_patchset *fine, int nlevels, con
         dx /= V.r; dy /= V.r;
         V.dx = dx; V.dy = dy;
         V.fill = (int4 *)(base + Lo.fill); V.par = (int *)(base + Lo.par);
+        V.base = (int *)(base + Lo.base);
         V.avg = (int4 *)(base + Lo.avg); V.cf = (int4 *)(base + Lo.cf);
         V.cfw = (int *)(base + Lo.cfw); V.cfu = (int4 *)(base + Lo.cfu);
         V.slot = (double *)(base + Lo.slot);
@@ -1270,6 +1391,7 @@ int swa_create_amr_levels(swa_grid *coarse, swa_patchset *fine, int nlevels, con
         struct Up { void *dst; const void *src; size_t bytes; const char *what; } up[] = {
             {V.fill, H.fill.data(), sizeof(int4) * H.fill.size(), "AMR fill map upload"},
             {V.par, H.par.data(), sizeof(int) * H.par.size(), "AMR fill parents upload"},
+            {V.base, H.base.data(), sizeof(int) * H.base.size(), "AMR fill bases upload"},
             {V.avg, H.avg.data(), sizeof(int4) * H.avg.size(), "AMR average map upload"},
             {V.cf, H.cf.data(), sizeof(int4) * H.cf.size(), "AMR edge map upload"},
             {V.cfw, H.cfw.data(), sizeof(int) * H.cfw.size(), "AMR edge flags upload"},
@@ -1307,6 +1429,14 @@ int swa_destroy_amr(swa_amr *A) {
 int swa_amr_set_reflux(swa_amr *A, int on) {
     if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
     A->reflux = on != 0;
+    return SWA_OK;
+}
+
+int swa_amr_set_fill_mode(swa_amr *A, int mode) {
+    if (!A) return set_error(SWA_EINVAL, "null AMR hierarchy");
+    if (mode != SWA_AMR_FILL_FUSED && mode != SWA_AMR_FILL_KERNEL)
+        return set_error(SWA_EINVAL, "fill mode must be SWA_AMR_FILL_FUSED or SWA_AMR_FILL_KERNEL");
+    A->fill_mode = mode;
     return SWA_OK;
 }
 

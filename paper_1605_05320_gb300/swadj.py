@@ -50,7 +50,7 @@ EXPORTS = [
     "swa_step_level", "swa_patches_get_time", "swa_patches_level_info",
     "swa_patches_set_tile_rows",
     "swa_amr_workspace_bytes", "swa_create_amr", "swa_destroy_amr", "swa_amr_step",
-    "swa_amr_set_reflux", "swa_amr_info", "swa_grid_set_wetdry", "swa_amr_levels_workspace_bytes",
+    "swa_amr_set_reflux", "swa_amr_info", "swa_grid_set_wetdry", "swa_amr_set_fill_mode", "swa_amr_levels_workspace_bytes",
     "swa_create_amr_levels",
     "swa_alu_probe_ops", "swa_alu_probe",
     "swa_grid_mass",
@@ -161,6 +161,7 @@ def load(path: str = LIB_PATH):
         "swa_amr_step": ([_V, _D, _D, _I, _V], _I),
         "swa_amr_set_reflux": ([_V, _I], _I),
         "swa_grid_set_wetdry": ([_V, _I], _I),
+        "swa_amr_set_fill_mode": ([_V, _I], _I),
         "swa_amr_info": ([_V, _I, _P(_I), _P(_I), _P(_I)], _I),
         "swa_amr_levels_workspace_bytes": ([_V, _V, _I, _P(_I), _P(_I)], _SZ),
         "swa_create_amr_levels": ([_V, _V, _I, _P(_I), _P(_I), _V, _SZ, _V, _P(_V)], _I),
@@ -641,6 +642,13 @@ def swa_amr_set_reflux(h, on):
     return _chk(load().swa_amr_set_reflux(h, int(bool(on))))
 
 
+SWA_AMR_FILL_FUSED, SWA_AMR_FILL_KERNEL = 0, 1
+
+
+def swa_amr_set_fill_mode(h, mode):
+    return _chk(load().swa_amr_set_fill_mode(h, int(mode)))
+
+
 def swa_amr_info(h, level=1):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _chk(load().swa_amr_info(h, int(level), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
@@ -735,6 +743,9 @@ class Amr:
 
     def set_reflux(self, on):
         swa_amr_set_reflux(self.h, on)
+
+    def set_fill_mode(self, mode):
+        swa_amr_set_fill_mode(self.h, mode)
 
     def info(self, level=1):
         """Hierarchy level `level`: (ring cells filled, covered parent cell

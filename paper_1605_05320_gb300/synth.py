@@ -434,3 +434,26 @@ def amr_basin_2048(ratio: int = 4, side: int = 32, tiles: int = 8):
                           side * ratio + 4, dxf, dxf))
     fields = [patch_fields(q) for q in descs]
     return B, eta, n, dx, descs, fields
+
+
+def amr_basin_2048_nested(ratio: int = 4, side: int = 32, tiles: int = 8, side2: int = 32,
+                          tiles2: int = 4):
+    """amr_basin_2048 with a second level: tiles2 x tiles2 patches of side2 x
+    side2 level-1 cells refined by `ratio` again, tiling a square centred on
+    the source inside the level-1 square (level 2 of the patch set).
+    Returns (B, eta, n, dx, descs, fields) with the level-1 descriptors
+    first, then level 2's."""
+    B, eta, n, dx, descs, fields = amr_basin_2048(ratio, side, tiles)
+    dx1 = dx / ratio
+    dx2 = dx1 / ratio
+    # the source (700 km, 1024 km) in level-1 cells
+    c1, c2 = int(round(700e3 / dx1)), int(round(1024e3 / dx1))
+    i0, j0 = c1 - tiles2 * side2 // 2, c2 - tiles2 * side2 // 2
+    d2 = []
+    for b in range(tiles2):
+        for a in range(tiles2):
+            pi, pj = i0 + a * side2, j0 + b * side2
+            d2.append((2, pi * dx1 - 2 * dx2, pj * dx1 - 2 * dx2, side2 * ratio + 4,
+                       side2 * ratio + 4, dx2, dx2))
+    return B, eta, n, dx, descs + d2, fields + [patch_fields(q) for q in d2]
+

@@ -59,8 +59,10 @@ void brute_maps(const GridRefs &c, const swa_patchset *ps, int L, const int *lev
         const Lev &g = G[l], &gp = G[l - 1];
         const int r = g.r;
         amr::HostMaps &M = out[l];
+        M.base.assign(ps->n, -1);
         for (int a = 0; a < (int)g.box.size(); a++) {
             const Box &b = g.box[a];
+            M.base[g.ids[a]] = (int)M.fill.size();
             for (int j = 0; j < b.ny; j++)
                 for (int i = 0; i < b.nx; i++) {
                     if (i >= 2 && i < b.nx - 2 && j >= 2 && j < b.ny - 2) continue;
@@ -146,7 +148,8 @@ bool same4(std::vector<int4> u, std::vector<int4> v, bool sorted) {
 }
 
 bool same_maps(const amr::HostMaps &a, const amr::HostMaps &b) {
-    return same4(a.fill, b.fill, false) && a.par == b.par && same4(a.avg, b.avg, false) &&
+    return same4(a.fill, b.fill, false) && a.par == b.par && a.base == b.base &&
+           same4(a.avg, b.avg, false) &&
            same4(a.cf, b.cf, false) && a.cfw == b.cfw && same4(a.cfu, b.cfu, false);
 }
 
@@ -238,6 +241,19 @@ int main() {
         brute_maps(c, &ps, L, levels, ratios, M2);
         (two ? checked2 : checked)++;
         for (int l = 1; l <= L; l++) {
+            // a ring cell's entry is its patch's base plus its ring index
+            // (what a level launch filling its own rings looks up)
+            for (size_t e = 0; e < M1[l].fill.size(); e++) {
+                const int4 m = M1[l].fill[e];
+                const swa_patch_desc &q = ps.pd[m.x];
+                const int i = m.y % q.nx, j = m.y / q.nx;
+                if (!patches::ring_cell(i, j, q.nx, q.ny) ||
+                    M1[l].base[m.x] + patches::ring_index(i, j, q.nx, q.ny) != (int)e) {
+                    printf("trial %d level %d: entry %zu is not at its ring index\n", trial, l, e);
+                    failures++;
+                    break;
+                }
+            }
             (l == 2 ? edges2 : edges) += (long long)M1[l].cf.size();
             if (!same_maps(M1[l], M2[l])) {
                 printf("trial %d level %d: maps differ (%zu vs %zu edges)\n", trial, l,

@@ -129,6 +129,27 @@ def test_levels_match_the_oracle(S, layout, reflux):
         assert abs(ps.time(l)[0] - t) <= 1e-12 * t
 
 
+@pytest.mark.parametrize("layout", range(len(LAYOUTS)))
+def test_fills_in_the_level_launch_equal_the_fill_kernel(S, layout):
+    """The rings filled by the level launches themselves (the default) and by
+    a fill kernel before each launch give the same hierarchy bit for bit."""
+    out = []
+    for mode in (S.SWA_AMR_FILL_FUSED, S.SWA_AMR_FILL_KERNEL):
+        case = synth.amr_levels_basin(24, LAYOUTS[layout])
+        grid, ps, amr = gpu_levels(S, case)
+        amr.set_fill_mode(mode)
+        dt, t = dt_coarse(case["dx"]), 0.0
+        for _ in range(4):
+            amr.step(t, dt)
+            t = t + dt
+        assert S.swa_sync_status() == 0
+        npat = sum(len(lv["patches"]) for lv in case["levels"])
+        out.append([grid.get_state()] + [ps.get_state(k) for k in range(npat)])
+    for a, b in zip(*out):
+        for k in ("eta", "hu", "hv"):
+            assert np.array_equal(a[k], b[k]), k
+
+
 def coarse_mass(S, grid):
     m = torch.zeros(1, dtype=torch.float64, device="cuda")
     S.swa_grid_mass(grid.h, m)
