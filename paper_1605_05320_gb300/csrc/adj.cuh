@@ -24,6 +24,8 @@ struct AdjParams {
     // FP32 2D only: take two steps in this launch (the snapshot, if any, is
     // of the state after both)
     int two_steps;
+    // FP32 2D one-step kernel: no cell is dry (no wall edges to check)
+    int all_wet;
 };
 
 template <typename R>

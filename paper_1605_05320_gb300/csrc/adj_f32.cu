@@ -37,15 +37,21 @@ struct EdgeA {   // waves of one edge: strengths and the (substituted) speeds
 };
 
 // Waves at the edge between (eL, mL, cL) and (eR, mR, cR), m the normal
-// component; c = 0 marks a dry cell, mirrored from its wet neighbour.
+// component; c = 0 marks a dry cell, mirrored from its wet neighbour.  DRY =
+// false: the grid has no dry cell (no wall edges), which gives the same
+// numbers without the checks.
+template <bool DRY = true>
 __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR, float mR,
                                          float cR) {
     EdgeA w;
-    const bool dL = !(cL > 0.f), dR = !(cR > 0.f);
-    w.wall = dL || dR;
-    if (dL && dR) { w.b1 = 0.f; w.b2 = 0.f; w.cl = 0.f; w.cr = 0.f; return w; }
-    if (dL) { eL = eR; mL = -mR; cL = cR; }
-    if (dR) { eR = eL; mR = -mL; cR = cL; }
+    w.wall = false;
+    if (DRY) {
+        const bool dL = !(cL > 0.f), dR = !(cR > 0.f);
+        w.wall = dL || dR;
+        if (dL && dR) { w.b1 = 0.f; w.b2 = 0.f; w.cl = 0.f; w.cr = 0.f; return w; }
+        if (dL) { eL = eR; mL = -mR; cL = cR; }
+        if (dR) { eR = eL; mR = -mL; cR = cL; }
+    }
     // flux jump of F = -(g hbar m, eta), g hbar = c^2
     const float d1 = fmaf(mul(cL, cL), mL, -mul(mul(cR, cR), mR));
     const float d2 = sub(eL, eR);
@@ -60,10 +66,11 @@ __device__ __forceinline__ EdgeA solve_a(float eL, float mL, float cL, float eR,
 // Net fluxes of edge w (neighbour edges wl, wr) as (L0, L1, R0, R1): L into
 // the left cell, R into the right cell (Q -= nu * net); components
 // (eta~, normal).
+template <bool DRY = true>
 __device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const EdgeA &wr,
                                         float nu, int order) {
     float F0 = 0.f, F1 = 0.f;
-    if (order >= 2 && !w.wall) {
+    if (order >= 2 && (!DRY || !w.wall)) {
         // wave 1 (speed -cl) is upwinded from the right edge, wave 2 (+cr)
         // from the left edge
         const float r1 = mul(mul(wr.b1, fmaf(wr.cl, w.cl, 1.f)), rcpf(fmaf(w.cl, w.cl, 1.f)));
@@ -106,6 +113,7 @@ __device__ __forceinline__ CellA load_cell(const AdjParams<float> &p, int col, b
     return q;
 }
 
+template <bool DRY>
 __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     const int lane = threadIdx.x & 31;
     const int nsx = (p.nx + kOut - 1) / kOut, nsy = (p.ny + kRows - 1) / kRows;
@@ -137,15 +145,15 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     CellA A = load(y0 - 2);                                  // row y0-2
     CellA B = Cn;                                            // row y0-1
     Cn = load(y0);
-    EdgeA W1 = solve_a(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-2|y0-1)
+    EdgeA W1 = solve_a<DRY>(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-2|y0-1)
     A = B;
     B = Cn;                                                  // row y0
     Cn = load(y0 + 1);
-    EdgeA W2 = solve_a(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-1|y0)
+    EdgeA W2 = solve_a<DRY>(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-1|y0)
     CellA C = Cn;                                            // row y0+1
     Cn = load(y0 + 2);
-    EdgeA Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);        // edge (y0|y0+1)
-    float4 nn = net_a(W1, W2, Wn, nuy, order);               // edge (y0-1|y0)
+    EdgeA Wn = solve_a<DRY>(B.e, B.g, B.c, C.e, C.g, C.c);        // edge (y0|y0+1)
+    float4 nn = net_a<DRY>(W1, W2, Wn, nuy, order);               // edge (y0-1|y0)
     A = B; B = C;                                            // rows j-2, j-1
     W1 = W2; W2 = Wn;                                        // y-edges (j-3|j-2), (j-2|j-1)
     float rp0 = nn.z, rp1 = nn.w;   // R part of the y-net of edge (j-3|j-2)
@@ -154,14 +162,14 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
     for (int j = y0 + 2; j <= ylast + 2; j++) {
         C = Cn;
         Cn = load(j + 1);
-        Wn = solve_a(B.e, B.g, B.c, C.e, C.g, C.c);          // edge (j-1|j)
-        nn = net_a(W1, W2, Wn, nuy, order);                  // edge (j-2|j-1)
+        Wn = solve_a<DRY>(B.e, B.g, B.c, C.e, C.g, C.c);          // edge (j-1|j)
+        nn = net_a<DRY>(W1, W2, Wn, nuy, order);                  // edge (j-2|j-1)
         {
             // y-sweep of row r = j - 2: lower edge -> R of the previous net,
             // upper edge -> L of this one
             float e = A.e, g = A.g;
             const float m = A.m, c = A.c;
-            if (c > 0.f) {
+            if (!DRY || c > 0.f) {
                 e = add(e, mul(-nuy, add(rp0, nn.x)));
                 g = add(g, mul(-nuy, add(rp1, nn.y)));
             }
@@ -169,17 +177,17 @@ __global__ void __launch_bounds__(256) adj_f32_strips(AdjParams<float> p) {
             const float eR = __shfl_down_sync(kFull, e, 1);
             const float mR = __shfl_down_sync(kFull, m, 1);
             const float cR = __shfl_down_sync(kFull, c, 1);
-            const EdgeA X = solve_a(e, m, c, eR, mR, cR);
+            const EdgeA X = solve_a<DRY>(e, m, c, eR, mR, cR);
             EdgeA XL = X, XR = X;   // only the fields net_a reads are exchanged
             XL.b2 = __shfl_up_sync(kFull, X.b2, 1);
             XL.cr = __shfl_up_sync(kFull, X.cr, 1);
             XR.b1 = __shfl_down_sync(kFull, X.b1, 1);
             XR.cl = __shfl_down_sync(kFull, X.cl, 1);
-            const float4 xn = net_a(XL, X, XR, nux, order);
+            const float4 xn = net_a<DRY>(XL, X, XR, nux, order);
             const float xr0 = __shfl_up_sync(kFull, xn.z, 1);   // R of edge (l-1|l)
             const float xr1 = __shfl_up_sync(kFull, xn.w, 1);
             float ne = e, nm = m;
-            if (c > 0.f) {
+            if (!DRY || c > 0.f) {
                 ne = add(ne, mul(-nux, add(xr0, xn.x)));
                 nm = add(nm, mul(-nux, add(xr1, xn.y)));
             }
@@ -378,7 +386,10 @@ int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
         const long long units = (long long)((p.nx + adjt::kOut - 1) / adjt::kOut) *
                                 ((p.ny + adjt::kRows - 1) / adjt::kRows);
         const unsigned blocks = (unsigned)((units + 7) / 8);
-        adjt::adj_f32_strips<<<blocks, 256, 0, st>>>(p);
+        if (p.all_wet)
+            adjt::adj_f32_strips<false><<<blocks, 256, 0, st>>>(p);
+        else
+            adjt::adj_f32_strips<true><<<blocks, 256, 0, st>>>(p);
         return swadj_host::cuda_check(cudaGetLastError(), "adj_f32_strips");
     }
     dim3 grid((p.nx + 127) / 128, 1);

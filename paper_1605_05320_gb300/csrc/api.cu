@@ -536,6 +536,7 @@ struct swa_adjoint {
     long long steps_done;
     int cur;
     int steps_per_pass;   // FP32 2D: 1 or 2 adjoint steps per launch
+    int all_wet;          // no cell with hbar <= dry_tol (no wall edges)
     double t_f;
 };
 
@@ -571,6 +572,7 @@ static AdjParams<R> adj_params(const swa_adjoint *a) {
         p.dst[k] = (R *)a->q[a->cur ^ 1][k];
     }
     p.c = (const R *)a->c;
+    p.all_wet = a->all_wet;
     return p;
 }
 
@@ -705,6 +707,12 @@ int swa_create_adjoint(const swa_grid_desc *desc, const double *bathy_host,
     a->esz = desc->precision == SWA_FP64 ? 8 : 4;
     a->nc = desc->ndim + 1;
     a->t_f = t_f;
+    // the kernels' dry rule (hbar = max(-B, 0) <= dry_tol) on the host
+    a->all_wet = 1;
+    for (size_t k = 0; k < a->n && a->all_wet; k++) {
+        const double hb = bathy_host[k] < 0.0 ? -bathy_host[k] : 0.0;
+        if (!(hb > desc->dry_tol)) a->all_wet = 0;
+    }
     Carve c(ws);
     adj_layout(desc, c, a);
     cudaStream_t st = S(stream);
