@@ -9,9 +9,12 @@ fits the HBM budget, gives each admitted scenario its own CUDA stream, and
 keeps enqueuing "macro steps" (10 forward steps, a gauge sample, one adjoint-
 weighted flag pass) round-robin over the active scenarios, so the work of
 requests that arrived at different times overlaps on the GPU (continuous
-batching).  Small grids run on high-priority streams and keep more macro
-steps queued (shortest job first; the host tops queues up between passes).  Completion is detected by polling CUDA events, never by a
-device-wide synchronisation.  Results per request: gauge time series, flag
+batching).  Admission takes the arrived request with the least work first
+(a request that has waited longer than max_wait_s goes ahead of it); small
+grids run on high-priority streams and keep more macro steps queued (the
+host tops queues up only between its passes over the active scenarios).
+Completion is detected by polling CUDA events, never by a device-wide
+synchronisation.  Results per request: gauge time series, flag
 counts per pass, latency (completion minus arrival).
 
 Everything on the numerical path runs in libswadj's kernels; this module only
@@ -144,10 +147,15 @@ class Scenario:
 class Server:
     def __init__(self, adjoint: ResidentAdjoint, budget_bytes: float = 80e9,
                  max_slots: int = 16, precision=S.SWA_FP32, n_gauges: int = 16,
-                 device="cuda", seed: int = 2026):
+                 device="cuda", seed: int = 2026, policy: str = "sjf",
+                 max_wait_s: float = 30.0):
         self.adjoint = adjoint
         self.budget = budget_bytes
         self.max_slots = max_slots
+        if policy not in ("sjf", "fifo"):
+            raise ValueError("policy must be 'sjf' or 'fifo'")
+        self.policy = policy
+        self.max_wait_s = max_wait_s
         self.precision = precision
         self.device = device
         self._bathy = {}
@@ -215,11 +223,22 @@ class Server:
         peak_bytes = used
         while pending or active:
             now = time.perf_counter() - t0
-            # admit
-            while (pending and pending[0].arrival * time_scale <= now
-                   and len(active) < self.max_slots
-                   and used + self.footprint(pending[0].n, self.precision) <= self.budget):
-                r = pending.pop(0)
+            # admit: the arrived request with the least work first (shortest
+            # job first), unless one has waited longer than max_wait_s (then
+            # the longest-waiting one), while a slot and the budget allow
+            while pending and len(active) < self.max_slots:
+                now = time.perf_counter() - t0
+                arrived = [r for r in pending if r.arrival * time_scale <= now]
+                if not arrived:
+                    break
+                if self.policy == "fifo":
+                    r = arrived[0]
+                else:
+                    old = [r for r in arrived if now - r.arrival * time_scale > self.max_wait_s]
+                    r = old[0] if old else min(arrived, key=lambda q: (q.n, q.arrival))
+                if used + self.footprint(r.n, self.precision) > self.budget:
+                    break
+                pending.remove(r)
                 sc = Scenario(r, self, self.device)
                 sc.admitted = time.perf_counter() - t0
                 used += sc.bytes
@@ -315,6 +334,8 @@ def main(argv=None):
     ap.add_argument("--sizes", default="512,1024")
     ap.add_argument("--adjoint-n", type=int, default=2048)
     ap.add_argument("--plain-requests", type=int, default=8)
+    ap.add_argument("--prepare-gb", type=float, default=4.0,
+                    help="host memory for request payloads formed before the clock")
     a = ap.parse_args(argv)
     build.build()
     S.load()
@@ -331,7 +352,12 @@ def main(argv=None):
     torch.cuda.synchronize()
     adj_s = time.perf_counter() - t0
     reqs = trace_from_config(a.requests, a.rate, sizes)
-    res, st = Server(adj).run(reqs)
+    server = Server(adj)
+    t0 = time.perf_counter()
+    server.prepare(reqs, max_bytes=a.prepare_gb * 1e9)
+    prep_s = time.perf_counter() - t0
+    res, st = server.run(reqs)
+    st["host_prepare_s"] = prep_s
     lat_by = {}
     for r in res:
         lat_by.setdefault(r.n, []).append(r.latency)
