@@ -23,7 +23,7 @@ namespace f32 {
 // Where the ocean is at rest a unit costs little (strips.cuh), so units are
 // short and taken as warps free up: the active part of the domain spreads
 // over every SM instead of over the few warps whose strips it crosses.
-__global__ void __launch_bounds__(strip::kThreads, 5)
+__global__ void __launch_bounds__(strip::kThreads, 4)
     fwd_f32_strips(FwdParams<float> p, int rows, int nunits) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
