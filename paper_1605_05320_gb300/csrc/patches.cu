@@ -314,7 +314,7 @@ __device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, i
         R.slot2[(size_t)e * (1 + R.r2)] += dt / (axis == 0 ? R.dtx : R.dty) * fs;
 }
 
-__global__ void __launch_bounds__(strip::kThreads, 5) level_strip_kernel(LevelParams p) {
+__global__ void __launch_bounds__(strip::kThreads, 4) level_strip_kernel(LevelParams p) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
     __shared__ float red[strip::kThreads / 32];
