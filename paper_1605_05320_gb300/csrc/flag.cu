@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) flag_kernel(FlagParams<R, S> p) {
 // m differs (it may omit values below tol), hence PRUNE only without maxip.
 // Ahead of the forward wave q = 0 exactly: such a quad reads its state only.
 template <bool PRUNE>
-__global__ void __launch_bounds__(256) flag_kernel_f32x4(FlagParams<float, float> p) {
+__global__ void __launch_bounds__(256, 4) flag_kernel_f32x4(FlagParams<float, float> p) {
     __shared__ Window sw;
     if (threadIdx.x == 0) sw = make_window(p.tau, p.K, p.clk->t, p.t_s, p.t_f, p.mode);
     __syncthreads();
