@@ -26,10 +26,16 @@ struct AdjParams {
     int two_steps;
     // FP32 2D one-step kernel: no cell is dry (no wall edges to check)
     int all_wet;
+    // FP32 2D one-step kernel: 1 = the unit has had a nonzero value at an
+    // earlier step (it skips the quiet scan); null: no quiet scan
+    unsigned char *umap;
+    int umap_n;
 };
 
 template <typename R>
 int adj_launch_step(const AdjParams<R> &p, cudaStream_t st);
+// entries of the FP32 2D adjoint's unit map
+int adj_f32_unit_map_bytes(int nx, int ny);
 template <> int adj_launch_step<double>(const AdjParams<double> &, cudaStream_t);
 template <> int adj_launch_step<float>(const AdjParams<float> &, cudaStream_t);
 

@@ -176,6 +176,9 @@ struct swa_grid {
     int wetdry;            // split step with the shore solver (dry cells allowed)
     long long *gauge_row;  // device row counter of the fused gauge recording
     GaugeRec gauges;       // fused gauge recording (n = 0: off)
+    float *rest_tab;       // FP32 2D: rest CFL table of the step's quiet units
+    unsigned char *umap;   // FP32 2D: units that have had waves (quiet-unit hint)
+    int umap_n;
 };
 
 static int grid_step_blocks(const swa_grid_desc *d) {
@@ -232,7 +235,18 @@ static void grid_layout(const swa_grid_desc *d, Carve &c, swa_grid *g) {
     int blocks = grid_max_blocks(d);
     if (blocks < kInitBlocks) blocks = kInitBlocks;
     double *partial = (double *)c.take((size_t)blocks * 8);
+    float *rest_tab = nullptr;
+    unsigned char *umap = nullptr;
+    int umap_n = 0;
+    if (d->precision == SWA_FP32 && d->ndim == 2) {
+        rest_tab = (float *)c.take(fwd_f32_rest_table_floats(d->nx, d->ny) * sizeof(float));
+        umap_n = fwd_f32_unit_map_bytes(d->nx, d->ny);
+        umap = (unsigned char *)c.take((size_t)umap_n);
+    }
     if (g) {
+        g->rest_tab = rest_tab;
+        g->umap = umap;
+        g->umap_n = umap_n;
         for (int b = 0; b < 2; b++)
             for (int k = 0; k < 3; k++) g->q[b][k] = q[b][k];
         g->bath = bath;
@@ -272,6 +286,9 @@ static FwdParams<R> fwd_params(const swa_grid *g, double t_end) {
     p.err = err_word();
     p.fwd_rows = g->strip_rows;
     p.keep_rest = g->keep_rest;
+    p.rest_tab = g->rest_tab;
+    p.umap = g->umap;
+    p.umap_n = g->umap_n;
     p.gauges = g->gauges;
     p.wetdry = g->wetdry;
     p.dry_tol = (R)g->d.dry_tol;
@@ -338,6 +355,8 @@ int swa_create_grid(const swa_grid_desc *desc, const double *bathy_host, void *w
         } else {
             rc = conv_in<float>(g->staging, (float *)g->bath, nullptr, 2, g->n, st);
             g->Bd = nullptr;
+            if (rc == SWA_OK && g->rest_tab)
+                rc = fwd_f32_rest_table(fwd_params<float>(g, 0.0), g->rest_tab, st);
         }
     }
     // ocean at rest until swa_set_state: surface 0, no momentum
@@ -538,6 +557,8 @@ struct swa_adjoint {
     int steps_per_pass;   // FP32 2D: 1 or 2 adjoint steps per launch
     int all_wet;          // no cell with hbar <= dry_tol (no wall edges)
     double t_f;
+    unsigned char *umap;  // FP32 2D: units that have had a nonzero value (quiet-unit hint)
+    int umap_n;
 };
 
 static void adj_layout(const swa_grid_desc *d, Carve &c, swa_adjoint *a) {
@@ -549,9 +570,17 @@ static void adj_layout(const swa_grid_desc *d, Carve &c, swa_adjoint *a) {
     void *cc = c.take(n * esz);
     double *staging = (double *)c.take(n * 8);
     double *smax = (double *)c.take(8);
+    unsigned char *umap = nullptr;
+    int umap_n = 0;
+    if (d->precision == SWA_FP32 && d->ndim == 2) {
+        umap_n = adj_f32_unit_map_bytes(d->nx, d->ny);
+        umap = (unsigned char *)c.take((size_t)umap_n);
+    }
     if (a) {
         for (int b = 0; b < 2; b++)
             for (int k = 0; k < 3; k++) a->q[b][k] = q[b][k];
+        a->umap = umap;
+        a->umap_n = umap_n;
         a->c = cc;
         a->staging = staging;
         a->smax_dev = smax;
@@ -573,6 +602,8 @@ static AdjParams<R> adj_params(const swa_adjoint *a) {
     }
     p.c = (const R *)a->c;
     p.all_wet = a->all_wet;
+    p.umap = a->umap;
+    p.umap_n = a->umap_n;
     return p;
 }
 
@@ -827,6 +858,8 @@ int swa_set_adjoint_state(swa_adjoint *a, const double *phi, int where, void *st
         else
             TRY(conv_in<float>(src, (float *)a->q[0][k], nullptr, 0, a->n, st));
     }
+    if (a->umap)   // a new state: no unit has had a nonzero value yet
+        TRY(cuda_check(cudaMemsetAsync(a->umap, 0, (size_t)a->umap_n, st), "unit map clear"));
     a->cur = 0;
     a->steps_done = 0;
     return SWA_OK;

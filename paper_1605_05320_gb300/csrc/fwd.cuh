@@ -22,6 +22,9 @@ struct FwdParams {
     int *err;          // device error word (ERR_* bits)
     int fwd_rows;      // FP32 strip height (rows per block), 0 = default
     int keep_rest;     // FP32 2D: 1 computes wave-free rows in full (no skipping)
+    const float *rest_tab;   // FP32 2D grid: rest CFL table of quiet units (null: none)
+    unsigned char *umap;     // FP32 2D grid: 1 = unit had waves at an earlier step
+    int umap_n;              // entries of umap
     GaugeRec gauges;   // fused gauge recording (n = 0: off)
     int wetdry;        // 1: the shore solver at dry and transonic edges
     R dry_tol;         // a cell with h <= dry_tol is dry
@@ -29,6 +32,10 @@ struct FwdParams {
 
 template <typename R>
 int fwd_launch_step(const FwdParams<R> &p, cudaStream_t st);
+// rest CFL table of the FP32 2D grid step (floats, and the kernel filling it)
+size_t fwd_f32_rest_table_floats(int nx, int ny);
+int fwd_f32_unit_map_bytes(int nx, int ny);
+int fwd_f32_rest_table(const FwdParams<float> &p, float *tab, cudaStream_t st);
 template <typename R>
 int fwd_step_blocks(const FwdParams<R> &p);
 template <typename R>

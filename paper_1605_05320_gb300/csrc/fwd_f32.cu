@@ -50,12 +50,22 @@ __global__ void __launch_bounds__(strip::kThreads, 4)
     float smax = 0.f;
     bool bad = false;
     const int lane = threadIdx.x & 31;
+    const bool quiet = p.rest_tab && p.umap && !p.keep_rest;
     for (;;) {   // warp-uniform
         int u = 0;
         if (lane == 0) u = (int)atomicAdd(&p.clk->work, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= nunits) break;
         const int sy = u / nsx, sx = u - sy * nsx;
+        // A unit that had waves at an earlier step keeps them (the ocean does
+        // not return exactly to rest behind a wave): it skips the quiet scan.
+        // The map is only a hint; the scan alone decides that a unit is quiet.
+        if (quiet && (u >= p.umap_n || p.umap[u] == 0)) {
+            if (strip::quiet_unit<true>(v, p.rest_tab, sx, sx * strip::kOut, sy * rows, rows, p.g,
+                                        smax))
+                continue;
+            if (lane == 0 && u < p.umap_n) p.umap[u] = 1;
+        }
         strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order,
                           ring[threadIdx.x >> 5], smax, bad, !p.keep_rest);
     }
@@ -114,7 +124,47 @@ __global__ void __launch_bounds__(256) fwd_f32_1d(FwdParams<float> p) {
                             cur);
 }
 
+// The rest CFL table of quiet units (strips.cuh): per strip sx and row j,
+// the maximum over the strip's output columns of cfl_f32(hbar, 0, 0), the
+// step's CFL term of a cell at rest, with the step's own 1/dx and 1/dy; NaN
+// where a column has hbar <= 0.
+__global__ void rest_cfl_table(FwdParams<float> p, float *tab) {
+    const int nsx = (p.nx + strip::kOut - 1) / strip::kOut;
+    const float rdx = 1.f / p.dx, rdy = 1.f / p.dy;
+    const size_t n = (size_t)nsx * p.ny;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int sx = (int)(k / p.ny), j = (int)(k - (size_t)sx * p.ny);
+        const int x1 = (sx + 1) * strip::kOut < p.nx ? (sx + 1) * strip::kOut : p.nx;
+        float t = 0.f;
+        bool ok = true;
+        for (int i = sx * strip::kOut; i < x1; i++) {
+            const float hb = p.bath[(size_t)j * p.nx + i];
+            ok = ok && hb > 0.f;
+            t = fmaxf(t, cfl_f32(hb, 0.f, 0.f, p.g, rdx, rdy, 1));
+        }
+        tab[k] = ok ? t : __int_as_float(0x7fc00000);
+    }
+}
+
 }  // namespace f32
+
+// Entries of the unit map: units of the lowest strip height (16 rows).
+int fwd_f32_unit_map_bytes(int nx, int ny) {
+    return ((nx + strip::kOut - 1) / strip::kOut) * ((ny + 15) / 16);
+}
+
+size_t fwd_f32_rest_table_floats(int nx, int ny) {
+    return (size_t)((nx + strip::kOut - 1) / strip::kOut) * ny;
+}
+
+int fwd_f32_rest_table(const FwdParams<float> &p, float *tab, cudaStream_t st) {
+    const size_t n = fwd_f32_rest_table_floats(p.nx, p.ny);
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    f32::rest_cfl_table<<<blocks, 256, 0, st>>>(p, tab);
+    return swadj_host::cuda_check(cudaGetLastError(), "rest_cfl_table");
+}
 
 // Rows of a work unit of the FP32 2D step: the requested strip height (16,
 // 32 or 64), else kUnitRows.  All heights give the same results.

@@ -445,6 +445,8 @@ __global__ void __launch_bounds__(256) clock_init_kernel(FwdParams<R> p, double 
     const int tid = threadIdx.x;
     const size_t n = (size_t)p.nx * p.ny;
     const R *q0 = p.q[0][0], *q1 = p.q[0][1], *q2 = p.q[0][2];
+    // a new state: no unit has had waves yet (the quiet-unit hint)
+    for (int k = blockIdx.x * 256 + tid; k < p.umap_n; k += gridDim.x * 256) p.umap[k] = 0;
     double mx = 0.0;
     for (size_t k = (size_t)blockIdx.x * 256 + tid; k < n; k += (size_t)gridDim.x * 256) {
         const R h = PERT ? q0[k] + p.bath[k] : q0[k];

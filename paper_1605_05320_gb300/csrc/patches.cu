@@ -230,7 +230,7 @@ struct LevelReflux {
 
 struct LevelParams {
     const PatchDevice *table;
-    const int4 *units;   // (patch, x0, y0, 0)
+    int4 *units;         // (patch, x0, y0, hint): hint 1 = the strip has had waves
     int nunits, rows;
     DevClock *clk;
     double *partial;
@@ -349,6 +349,12 @@ __global__ void __launch_bounds__(strip::kThreads, 4) level_strip_kernel(LevelPa
             fill_window(p, t.x, t.y, t.z, cur, s_af, s_pcur);
             __threadfence_block();
             __syncwarp();   // the window's writes before the strip's loads
+        }
+        // A strip that has had waves keeps them: it skips the quiet scan (the
+        // hint only; the scan alone decides that a strip is quiet).
+        if (t.w == 0) {
+            if (strip::quiet_unit<false>(v, nullptr, 0, t.y, t.z, p.rows, p.g, smax)) continue;
+            if ((threadIdx.x & 31) == 0) p.units[u].w = 1;
         }
         strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
                           ring[threadIdx.x >> 5], smax, bad);
@@ -710,6 +716,12 @@ int swa_patches_set_state(swa_patchset *ps, int k, const double *eta, const doub
     return SWA_OK;
 }
 
+// A level's new state: no strip has had waves yet (the quiet-strip hint).
+__global__ void clear_hint_kernel(int4 *u, int n) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        u[k].w = 0;
+}
+
 int swa_patches_start_level(swa_patchset *ps, int level, double t, void *stream) {
     if (!ps || level < 1 || level > SWA_MAX_LEVELS) return set_error(SWA_EINVAL, "bad level");
     Level &L = ps->lev[level];
@@ -717,6 +729,11 @@ int swa_patches_start_level(swa_patchset *ps, int level, double t, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     LevelParams p = level_params(ps, level, 0.0);
     TRY(cuda_check(cudaMemsetAsync(L.smax, 0, 8, st), "smax clear"));
+    if (L.nunits16 > 0)
+        clear_hint_kernel<<<(L.nunits16 + 255) / 256, 256, 0, st>>>(L.units16, L.nunits16);
+    if (L.nunits32 > 0)
+        clear_hint_kernel<<<(L.nunits32 + 255) / 256, 256, 0, st>>>(L.units32, L.nunits32);
+    TRY(cuda_check(cudaGetLastError(), "clear_hint_kernel"));
     int blocks = p.nunits < 2048 ? p.nunits : 2048;
     level_smax_kernel<<<blocks, 256, 0, st>>>(p, L.smax);
     TRY(cuda_check(cudaGetLastError(), "level_smax_kernel"));

@@ -241,5 +241,114 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
     }
 }
 
+// ------------------------------------------------------------ quiet units
+// A unit is quiet when every cell its step reads (its own cells and the two
+// rows and columns around them, ghost cells index-mapped) is exactly at rest
+// (eta = hu = hv = 0).  Every wave of such a window is zero, so the step
+// leaves the unit's cells at rest, and the CFL term of each is that of the
+// ocean at rest on its depth, cfl_f32(hbar, 0, 0), a function of the
+// bathymetry alone.  quiet_unit() decides this from one streaming pass over
+// the window (batches of three or six rows, two batches of loads in flight per lane,
+// a warp vote per batch, leaving at the first batch with a wave), then
+// writes the unit's cells at rest and takes their CFL maximum from rest_tab,
+// the single grid's table of those rest terms (per strip sx and row j, the
+// maximum over the strip's output columns, NaN where a column has hbar <=
+// 0), or, for patches, forms them from hbar loaded with the window.  A unit
+// with a cell of hbar <= 0 takes the full path, which flags the depth.  The
+// unit gets the state and the maximum the
+// full path gives, up to the sign of an exact zero, at a fraction of the
+// instructions: the ocean ahead of a tsunami is at rest.
+// Loads of one batch of NB rows of a quiet scan: eta, hu, hv (and hbar when
+// HB) of rows j0 .. j0 + NB - 1 (clipped to jend; a short last batch
+// re-reads jend) in column col, rows index-mapped unless the window lies
+// inside the grid.
+template <bool HB, int NB>
+struct QuietBatch {
+    float e[NB], a[NB], b[NB], h[HB ? NB : 1];
+    __device__ __forceinline__ void load(const View &v, int col, int j0, int jend, bool yin) {
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            const int j = j0 + k <= jend ? j0 + k : jend;
+            bool fy;
+            const int row = yin ? j : ghost_index(j, v.ny, v.bc.lo_y, v.bc.hi_y, &fy);
+            const size_t o = (size_t)row * v.nx + col;
+            e[k] = ld_early(v.q0 + o);
+            a[k] = ld_early(v.q1 + o);
+            b[k] = ld_early(v.q2 + o);
+            if (HB) h[HB ? k : 0] = ld_early(v.hb + o);
+        }
+    }
+    // Whether the batch is at rest in every lane of the warp.  With HB, also
+    // the rest CFL terms of its output cells (rows y0 .. ylast, output lanes)
+    // into t, and ok cleared where such a cell has hbar <= 0.
+    __device__ __forceinline__ bool rest(const View &v, int j0, int y0, int ylast, bool outl,
+                                         float g, float &t, bool &ok) const {
+        bool r = true;
+#pragma unroll
+        for (int k = 0; k < NB; k++) {
+            r = r && e[k] == 0.f && a[k] == 0.f && b[k] == 0.f;
+            if (HB && outl && j0 + k >= y0 && j0 + k <= ylast) {
+                const float hb = h[HB ? k : 0];
+                ok = ok && hb > 0.f;
+                t = fmaxf(t, cfl_f32(hb, 0.f, 0.f, g, v.rdx, v.rdy, 1));
+            }
+        }
+        return __all_sync(kFull, r);
+    }
+};
+
+// TAB: rest_tab is the single grid's table of rest CFL terms (per strip sx
+// and row); otherwise the terms are formed from hbar, loaded with the window
+// (patches).
+template <bool TAB>
+__device__ __forceinline__ bool quiet_unit(const View &v, const float *rest_tab, int sx, int x0,
+                                           int y0, int rows, float g, float &smax) {
+    constexpr int NB = TAB ? 6 : 3;   // rows per batch
+    const int lane = threadIdx.x & 31;
+    const int ylast = (y0 + rows < v.ny ? y0 + rows : v.ny) - 1;
+    const int gi = x0 - 2 + lane;
+    bool fx;
+    const int col = ghost_index(gi, v.nx, v.bc.lo_x, v.bc.hi_x, &fx);
+    const bool yin = y0 - 2 >= 0 && ylast + 2 < v.ny;
+    const bool outl = lane >= 2 && lane < kLanes - 2 && gi < v.nx;
+    const int jend = ylast + 2;
+    float t = 0.f;
+    bool ok = true;
+    if (TAB) {   // the rest CFL terms of the unit's rows, loaded first
+        for (int j = y0 + lane; j <= ylast; j += kLanes) {
+            const float c = rest_tab[(size_t)sx * v.ny + j];
+            ok = ok && c == c;
+            t = fmaxf(t, c);
+        }
+    }
+    // the window, two batches of rows in flight
+    QuietBatch<!TAB, NB> P, Q;
+    int j0 = y0 - 2;
+    P.load(v, col, j0, jend, yin);
+    for (;;) {
+        bool more = j0 + NB <= jend;
+        if (more) Q.load(v, col, j0 + NB, jend, yin);
+        if (!P.rest(v, j0, y0, ylast, outl, g, t, ok)) return false;
+        if (!more) break;
+        j0 += NB;
+        more = j0 + NB <= jend;
+        if (more) P.load(v, col, j0 + NB, jend, yin);
+        if (!Q.rest(v, j0, y0, ylast, outl, g, t, ok)) return false;
+        if (!more) break;
+        j0 += NB;
+    }
+    if (!__all_sync(kFull, ok)) return false;
+    if (outl) {
+        for (int j = y0; j <= ylast; j++) {
+            const size_t o = (size_t)j * v.nx + gi;
+            v.o0[o] = 0.f;
+            v.o1[o] = 0.f;
+            v.o2[o] = 0.f;
+        }
+    }
+    smax = fmaxf(smax, t);
+    return true;
+}
+
 }  // namespace strip
 }  // namespace swadj
