@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-patches", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the untimed side measurements (flag comparison, schemes, "
+                         "fully active step, FP64 kernels, AMR): for profiler launch lists")
     return ap.parse_args()
 
 
@@ -727,7 +730,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "flagged_cells_per_pass_mean": float(scen.counts.double().mean().item()),
     }
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         with torch.cuda.stream(stream):
             out["flag_comparison"] = compare_flags(scen, stream)
             out["forward_schemes"] = compare_schemes(scen, stream)

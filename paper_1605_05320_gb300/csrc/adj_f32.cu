@@ -164,8 +164,14 @@ __device__ __forceinline__ bool quiet_a(const AdjParams<float> &p, int col, int 
     }
 }
 
+constexpr int kRingA = 8;   // rows in flight per warp (a power of 2)
+struct RingA {
+    float v[kRingA][4][kLanes];   // [slot][eta~, mu~, gamma~, c][lane]
+};
+
 template <bool DRY>
 __global__ void __launch_bounds__(256, 4) adj_f32_strips(AdjParams<float> p) {
+    __shared__ RingA ring[8];   // one per warp of the 256-thread block
     const int lane = threadIdx.x & 31;
     const int nsx = (p.nx + kOut - 1) / kOut, nsy = (p.ny + kRows - 1) / kRows;
     const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -208,25 +214,61 @@ __global__ void __launch_bounds__(256, 4) adj_f32_strips(AdjParams<float> p) {
         return;
     }
     if (scan && lane == 0 && unit < p.umap_n) p.umap[unit] = 1;
-    auto load = [&](int j) -> CellA {
-        bool fy = false;
-        int row;
-        if (yin) row = j < p.ny ? j : p.ny - 1;
-        else row = ghost_index(j, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
-        return load_cell(p, col, fx, row, fy);
+    // Rows stream through the warp's ring of shared memory by cp.async,
+    // kRingA - 1 rows ahead of the one read, in the order they are used:
+    // y0 - 2, y0 - 1, ..., ylast + 3 (past the last row the fetch is
+    // clamped and its values unused).  Each lane copies and reads only its
+    // own column, so the ring needs no synchronisation beyond the lane's own
+    // wait for its copy groups.
+    RingA &R = ring[threadIdx.x >> 5];
+    int jf = y0 - 2, sf = 0;   // next row to fetch, its slot
+    int jc = y0 - 2, sc = 0;   // next row to read, its slot
+    const int jlast = ylast + 3;
+    auto fetch = [&]() {
+        if (jf <= jlast) {
+            bool fy;
+            int row;
+            if (yin) row = jf < p.ny ? jf : p.ny - 1;
+            else row = ghost_index(jf, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+            const size_t o = (size_t)row * p.nx + col;
+            cp_async4(&R.v[sf][0][lane], p.src[0] + o);
+            cp_async4(&R.v[sf][1][lane], p.src[1] + o);
+            cp_async4(&R.v[sf][2][lane], p.src[2] + o);
+            cp_async4(&R.v[sf][3][lane], p.c + o);
+        }
+        cp_commit();
+        jf++;
+        sf = (sf + 1) & (kRingA - 1);
     };
-    // prologue, rows y0-2 .. y0+1 (rows are loaded one step ahead of use)
-    CellA Cn = load(y0 - 1);
-    CellA A = load(y0 - 2);                                  // row y0-2
+#pragma unroll
+    for (int k = 0; k < kRingA - 1; k++) fetch();
+    auto load = [&]() -> CellA {
+        fetch();
+        cp_wait<kRingA - 1>();   // row jc has landed
+        bool fy = false;
+        if (!yin) ghost_index(jc, p.ny, p.bc.lo_y, p.bc.hi_y, &fy);
+        CellA q;
+        q.e = R.v[sc][0][lane];
+        const float mu = R.v[sc][1][lane], ga = R.v[sc][2][lane];
+        q.m = fx ? -mu : mu;
+        q.g = fy ? -ga : ga;
+        q.c = R.v[sc][3][lane];
+        jc++;
+        sc = (sc + 1) & (kRingA - 1);
+        return q;
+    };
+    // prologue, rows y0-2 .. y0+1 (rows are read one step ahead of use)
+    CellA A = load();                                        // row y0-2
+    CellA Cn = load();
     CellA B = Cn;                                            // row y0-1
-    Cn = load(y0);
+    Cn = load();
     EdgeA W1 = solve_a<DRY>(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-2|y0-1)
     A = B;
     B = Cn;                                                  // row y0
-    Cn = load(y0 + 1);
+    Cn = load();
     EdgeA W2 = solve_a<DRY>(A.e, A.g, A.c, B.e, B.g, B.c);        // edge (y0-1|y0)
     CellA C = Cn;                                            // row y0+1
-    Cn = load(y0 + 2);
+    Cn = load();
     EdgeA Wn = solve_a<DRY>(B.e, B.g, B.c, C.e, C.g, C.c);        // edge (y0|y0+1)
     float4 nn = net_a<DRY>(W1, W2, Wn, nuy, order);               // edge (y0-1|y0)
     A = B; B = C;                                            // rows j-2, j-1
@@ -236,7 +278,7 @@ __global__ void __launch_bounds__(256, 4) adj_f32_strips(AdjParams<float> p) {
 #pragma unroll 3
     for (int j = y0 + 2; j <= ylast + 2; j++) {
         C = Cn;
-        Cn = load(j + 1);
+        Cn = load();                                          // row j+1
         Wn = solve_a<DRY>(B.e, B.g, B.c, C.e, C.g, C.c);          // edge (j-1|j)
         nn = net_a<DRY>(W1, W2, Wn, nuy, order);                  // edge (j-2|j-1)
         {

@@ -120,16 +120,6 @@ struct Ring {
     float v[kRing][4][kLanes];           // [slot][eta, hu, hv, hbar][lane]
 };
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most N of this thread's newest copy groups are pending
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 __device__ __forceinline__ void fetch_row(Ring &R, int slot, const View &v, int col, int row,
                                           int lane) {

@@ -59,6 +59,18 @@ __device__ __forceinline__ float ld_early(const float *p) {
     return v;
 }
 
+// Asynchronous 4-byte copy global -> shared (cp.async), its commit and the
+// wait until at most N of this thread's newest copy groups are pending.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // One-instruction approximate reciprocal and reciprocal square root
 // (hand-written PTX) with subnormals flushed to zero.  Their inputs in the
 // FP32 kernels are positive normal numbers: depths, sums of square roots of
