@@ -147,10 +147,13 @@ int swa_grid_set_strip_rows(swa_grid *grid, int rows);
 /*
  * FP32 2D grids: on = 1 (the default) lets the step skip the wave arithmetic
  * of rows that are exactly at rest (eta = hu = hv = 0 across a warp's strip
- * row), where every wave is zero and the exact result is known; on = 0
- * computes them in full.  Both give the same state (up to the sign of an
- * exact zero); the switch exists to show that and to time the step without
- * the shortcut.  SWA_EINVAL for a null grid or on not 0 or 1.
+ * row), where every wave is zero and the exact result is known, and write a
+ * strip unit whose whole stencil window is at rest straight back at rest
+ * (its CFL terms from a table of the bathymetry's rest terms, formed when
+ * the grid is created); on = 0 computes them in full.  Both give the same
+ * state and time step (up to the sign of an exact zero); the switch exists
+ * to show that and to time the step without the shortcut.  SWA_EINVAL for a
+ * null grid or on not 0 or 1.
  */
 int swa_grid_set_rest_skip(swa_grid *g, int on);
 /*
