@@ -93,6 +93,42 @@ def test_single_patch_is_bit_identical_to_grid(S):
     assert ps.time(1)[0] == g.time()[0]
 
 
+def test_quiet_strips_of_patch_and_grid_match_the_full_path(S):
+    """A compact source on an ocean at rest, so that most strips are quiet
+    at first: one patch (quiet strips, rest CFL terms formed from hbar), the
+    same grid (quiet units, rest CFL terms from the grid's table) and the
+    grid with the shortcuts off give the same state, and the same time after
+    every step (the CFL maximum over cells at rest is exact on each path)."""
+    p = (1, 500e3, 800e3, 150, 97, 2000.0, 2000.0)
+    B, eta = synth.patch_fields(p, src=(650e3, 890e3), amp=0.8, width=8e3)
+    eta = np.where(np.abs(eta) < 1e-6, 0.0, eta)
+    z = np.zeros(p[3] * p[4])
+    common = S.make_desc(2, 2, 2, 0, 0, 1, 1, precision=S.SWA_FP32)
+    ps = S.PatchSet([p], [B], common)
+    ps.set_state(0, eta, z, z)
+    ps.start(1)
+    d = S.make_desc(2, p[3], p[4], p[1], p[2], p[5], p[6], precision=S.SWA_FP32)
+    grids = []
+    for skip in (1, 0):
+        g = S.Grid(d, B)
+        S.swa_grid_set_rest_skip(g.h, skip)
+        g.set_state(eta, z, z, 0.0)
+        grids.append(g)
+    for _ in range(30):
+        ps.step(1, 1)
+        for g in grids:
+            g.step(1, 1e300)
+        t = [ps.time(1)[0]] + [g.time()[0] for g in grids]
+        assert t[0] == t[1] == t[2], t
+    assert S.swa_sync_status() == 0
+    a = ps.get_state(0)
+    for g in grids:
+        b = g.get_state()
+        for f in ("eta", "hu", "hv"):
+            assert np.array_equal(a[f], b[f]), f
+    assert np.abs(a["eta"]).max() > 1e-3 and (a["eta"] == 0).mean() > 0.2   # both parts present
+
+
 def test_single_patch_matches_grid_with_supersonic_band(S):
     """Shallow (10 m) water with a band flowing at 1.5 c among subsonic cells,
     stepped as a grid (strips of 64 rows) and as one patch (strips of 16
