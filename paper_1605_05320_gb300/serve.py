@@ -67,6 +67,24 @@ class Result:
         self.latency = self.done - self.arrival
 
 
+def pick_next(arrived, now, policy="sjf", max_wait_s=30.0, time_scale=1.0):
+    """The request to admit next among `arrived` (requests that have arrived
+    by `now`, in arrival order): "fifo" takes the first; "sjf" takes the one
+    with the least work (the smallest grid, then the earliest), unless some
+    have waited longer than max_wait_s, of which it takes the first."""
+    if not arrived:
+        return None
+    if policy == "fifo":
+        return arrived[0]
+    old = [r for r in arrived if now - r.arrival * time_scale > max_wait_s]
+    return old[0] if old else min(arrived, key=lambda q: (q.n, q.arrival))
+
+
+def fits(used_bytes, n, budget_bytes, precision=S.SWA_FP32):
+    """Whether an n x n scenario fits next to used_bytes of device memory."""
+    return used_bytes + Server.footprint(n, precision) <= budget_bytes
+
+
 class ResidentAdjoint:
     """The adjoint for one target, solved once, snapshots kept on device."""
 
@@ -231,12 +249,8 @@ class Server:
                 arrived = [r for r in pending if r.arrival * time_scale <= now]
                 if not arrived:
                     break
-                if self.policy == "fifo":
-                    r = arrived[0]
-                else:
-                    old = [r for r in arrived if now - r.arrival * time_scale > self.max_wait_s]
-                    r = old[0] if old else min(arrived, key=lambda q: (q.n, q.arrival))
-                if used + self.footprint(r.n, self.precision) > self.budget:
+                r = pick_next(arrived, now, self.policy, self.max_wait_s, time_scale)
+                if not fits(used, r.n, self.budget, self.precision):
                     break
                 pending.remove(r)
                 sc = Scenario(r, self, self.device)
