@@ -169,7 +169,9 @@ struct RingA {
     float v[kRingA][4][kLanes];   // [slot][eta~, mu~, gamma~, c][lane]
 };
 
-template <bool DRY>
+// DRY: the grid has dry cells (wall checks on); ORD: the order of the
+// scheme (1 or 2), fixed at compile time.
+template <bool DRY, int ORD>
 __global__ void __launch_bounds__(256, 4) adj_f32_strips(AdjParams<float> p) {
     __shared__ RingA ring[8];   // one per warp of the 256-thread block
     const int lane = threadIdx.x & 31;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(256, 4) adj_f32_strips(AdjParams<float> p) {
     const int col = ghost_index(gi, p.nx, p.bc.lo_x, p.bc.hi_x, &fx);
     const bool out = lane >= 2 && lane < kLanes - 2 && gi < p.nx;
     const float nux = p.nux, nuy = p.nuy;
-    const int order = p.order;
+    const int order = ORD;
     // row j of the strip, index-mapped (strips away from the lower and
     // upper boundary need no mapping; past the last row the load is clamped
     // and its values unused)
@@ -507,10 +509,14 @@ int adj_launch_step<float>(const AdjParams<float> &p, cudaStream_t st) {
         const long long units = (long long)((p.nx + adjt::kOut - 1) / adjt::kOut) *
                                 ((p.ny + adjt::kRows - 1) / adjt::kRows);
         const unsigned blocks = (unsigned)((units + 7) / 8);
-        if (p.all_wet)
-            adjt::adj_f32_strips<false><<<blocks, 256, 0, st>>>(p);
+        if (p.all_wet && p.order == 2)
+            adjt::adj_f32_strips<false, 2><<<blocks, 256, 0, st>>>(p);
+        else if (p.all_wet)
+            adjt::adj_f32_strips<false, 1><<<blocks, 256, 0, st>>>(p);
+        else if (p.order == 2)
+            adjt::adj_f32_strips<true, 2><<<blocks, 256, 0, st>>>(p);
         else
-            adjt::adj_f32_strips<true><<<blocks, 256, 0, st>>>(p);
+            adjt::adj_f32_strips<true, 1><<<blocks, 256, 0, st>>>(p);
         return swadj_host::cuda_check(cudaGetLastError(), "adj_f32_strips");
     }
     dim3 grid((p.nx + 127) / 128, 1);

@@ -23,6 +23,8 @@ namespace f32 {
 // Where the ocean is at rest a unit costs little (strips.cuh), so units are
 // short and taken as warps free up: the active part of the domain spreads
 // over every SM instead of over the few warps whose strips it crosses.
+// ORD: the order of the scheme (1 or 2), fixed at compile time.
+template <int ORD>
 __global__ void __launch_bounds__(strip::kThreads, 4)
     fwd_f32_strips(FwdParams<float> p, int rows, int nunits) {
     __shared__ float s_nu[2];
@@ -66,8 +68,10 @@ __global__ void __launch_bounds__(strip::kThreads, 4)
                 continue;
             if (lane == 0 && u < p.umap_n) p.umap[u] = 1;
         }
-        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, p.order,
-                          ring[threadIdx.x >> 5], smax, bad, !p.keep_rest);
+        // Units with waves take the full path: quiet units cover the ocean
+        // at rest, and the strip loop without its row skipping is leaner.
+        strip::strip_unit(v, sx * strip::kOut, sy * rows, rows, s_nu[0], s_nu[1], p.g, ORD,
+                          ring[threadIdx.x >> 5], smax, bad, false);
     }
     if (bad) atomicOr(p.err, ERR_UNSTABLE);
     fwave::finish_step<strip::kThreads>(p.clk, p.partial, p.nblocks, p.cfl, smax, red, &am_last,
@@ -187,7 +191,7 @@ static int resident_blocks() {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32::fwd_f32_strips,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32::fwd_f32_strips<2>,
                                                       strip::kThreads, 0);
         blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
         if (blocks > kMaxStepBlocks) blocks = kMaxStepBlocks;
@@ -206,7 +210,10 @@ int fwd_launch_step<float>(const FwdParams<float> &p0, cudaStream_t st) {
         const int wave = resident_blocks();
         if (blocks > wave) blocks = wave;
         p.nblocks = blocks + (p.gauges.n > 0 ? 1 : 0);
-        f32::fwd_f32_strips<<<p.nblocks, strip::kThreads, 0, st>>>(p, rows, units);
+        if (p.order == 2)
+            f32::fwd_f32_strips<2><<<p.nblocks, strip::kThreads, 0, st>>>(p, rows, units);
+        else
+            f32::fwd_f32_strips<1><<<p.nblocks, strip::kThreads, 0, st>>>(p, rows, units);
         return swadj_host::cuda_check(cudaGetLastError(), "fwd_f32_strips");
     }
     dim3 grid((p.nx + 255) / 256, 1);
