@@ -314,6 +314,8 @@ __device__ __noinline__ void level_reflux_task(const LevelParams &p, int task, i
         R.slot2[(size_t)e * (1 + R.r2)] += dt / (axis == 0 ? R.dtx : R.dty) * fs;
 }
 
+// ORD: the order of the scheme (1 or 2), fixed at compile time.
+template <int ORD>
 __global__ void __launch_bounds__(strip::kThreads, 4) level_strip_kernel(LevelParams p) {
     __shared__ float s_nu[2];
     __shared__ int s_cur, s_run;
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(strip::kThreads, 4) level_strip_kernel(LevelPa
             if (strip::quiet_unit<false>(v, nullptr, 0, t.y, t.z, p.rows, p.g, smax)) continue;
             if ((threadIdx.x & 31) == 0) p.units[u].w = 1;
         }
-        strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, p.order,
+        strip::strip_unit(v, t.y, t.z, p.rows, s_nu[0], s_nu[1], p.g, ORD,
                           ring[threadIdx.x >> 5], smax, bad);
     }
     if (p.rf.nfine + p.rf.ncoarse > 0) {
@@ -453,7 +455,7 @@ int occupancy_blocks() {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_strip_kernel,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_strip_kernel<2>,
                                                       strip::kThreads, 0);
         if (per_sm < 1) per_sm = 1;
         if (sms < 1) sms = 1;
@@ -617,7 +619,10 @@ static int level_launch(swa_patchset *ps, int level, int nsteps, double t_end,
     p.nblocks = occupancy_blocks();
     if (p.nblocks > need) p.nblocks = need;
     for (int s = 0; s < nsteps; s++)
-        level_strip_kernel<<<p.nblocks, strip::kThreads, 0, st>>>(p);
+        if (p.order == 2)
+            level_strip_kernel<2><<<p.nblocks, strip::kThreads, 0, st>>>(p);
+        else
+            level_strip_kernel<1><<<p.nblocks, strip::kThreads, 0, st>>>(p);
     return cuda_check(cudaGetLastError(), "level_strip_kernel");
 }
 
