@@ -91,7 +91,9 @@ __device__ __forceinline__ float4 net_a(const EdgeA &wl, const EdgeA &w, const E
 // once); every y-swept row is then x-swept across the warp with shuffles
 // (each x-edge solved and limited once by the lane on its left).  Lanes 0-1
 // and 30-31 are the x-halo: their y-swept values feed the output lanes' x
-// edges.  No shared memory and no barriers.
+// edges.  Rows arrive through the warp's own ring of shared memory
+// (cp.async, 8 rows in flight); there are no barriers.  The two-step kernel
+// further down keeps one row of register prefetch.
 constexpr int kLanes = 32;
 constexpr int kOut = kLanes - 4;   // output columns per strip
 constexpr int kRows = 32;          // output rows per strip

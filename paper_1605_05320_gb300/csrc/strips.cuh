@@ -238,16 +238,17 @@ __device__ __forceinline__ void strip_unit(const View &v, int x0, int y0, int ro
 // leaves the unit's cells at rest, and the CFL term of each is that of the
 // ocean at rest on its depth, cfl_f32(hbar, 0, 0), a function of the
 // bathymetry alone.  quiet_unit() decides this from one streaming pass over
-// the window (batches of three or six rows, two batches of loads in flight per lane,
-// a warp vote per batch, leaving at the first batch with a wave), then
-// writes the unit's cells at rest and takes their CFL maximum from rest_tab,
-// the single grid's table of those rest terms (per strip sx and row j, the
-// maximum over the strip's output columns, NaN where a column has hbar <=
-// 0), or, for patches, forms them from hbar loaded with the window.  A unit
-// with a cell of hbar <= 0 takes the full path, which flags the depth.  The
-// unit gets the state and the maximum the
-// full path gives, up to the sign of an exact zero, at a fraction of the
-// instructions: the ocean ahead of a tsunami is at rest.
+// the window (batches of three or six rows, two batches of loads in flight
+// per lane, a warp vote per batch, leaving at the first batch with a wave),
+// then writes the unit's cells at rest and takes their CFL maximum from
+// rest_tab, the single grid's table of those rest terms (per strip sx and
+// row j, the maximum over the strip's output columns, NaN where a column has
+// hbar <= 0), or, for patches, forms them from hbar loaded with the window.
+// A unit with a cell of hbar <= 0 takes the full path, which flags the
+// depth.  The unit gets the state and the maximum the full path gives, up to
+// the sign of an exact zero, at a fraction of the instructions: the ocean
+// ahead of a tsunami is at rest.
+
 // Loads of one batch of NB rows of a quiet scan: eta, hu, hv (and hbar when
 // HB) of rows j0 .. j0 + NB - 1 (clipped to jend; a short last batch
 // re-reads jend) in column col, rows index-mapped unless the window lies
