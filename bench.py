@@ -113,24 +113,32 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sms, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sms.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sms:
-            return None
-        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sms)}
+        with open(self.path) as f:
+            return summarize_clocks(f)
+
+
+def summarize_clocks(lines):
+    """Median SM clock under load, the maximum clock and the throttle reasons
+    seen, from nvidia-smi CSV lines of ClockSampler.Q (noheader, nounits);
+    None without a sample."""
+    sms, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sms.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sms:
+        return None
+    return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx,
+            "reasons": sorted(reasons), "samples": len(sms)}
 
 
 # ------------------------------------------------------------------ our arm

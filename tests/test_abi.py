@@ -116,3 +116,23 @@ def test_bench_arms_report_the_same_workload():
     assert a == b and a["cells"] == 2048 * 2048
     assert "flag pass every 10" in a["workload"]
     assert bench.whole_job_rate(100.0, 4, 2, 1000.0) == 800.0
+
+
+def test_clock_summary_of_nvidia_smi_samples():
+    """The bench's clock record: median SM clock, maximum, and the throttle
+    reasons that were active in any sample (a run with hw_slowdown or a
+    thermal slowdown is rejected; sw_power_cap is kept and noted)."""
+    import bench
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    c = bench.summarize_clocks(lines)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    hot = lines[:1] + ["0, 1500, 2070, 800.0, 0x8, Active, Not Active, Active, Not Active"]
+    assert bench.summarize_clocks(hot)["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.summarize_clocks([]) is None
